@@ -1,0 +1,215 @@
+"""Seeded synthetic workloads (inputs only; none of the method's arithmetic).
+
+Both the CPU oracle and the CUDA path draw their inputs from this module and
+from nowhere else.  Units: free-space wavelength 1, so k = 2*pi.  The five
+workloads mirror the paper's test geometries (Numerical Results: PEC plates and
+dielectric spheres of growing electrical size) with brick meshes:
+
+  1  unit cube 12^3, sphere r=0.25 eps=4, 2x2x1 equal subdomains, 1 plane wave
+  2  3-wavelength cube 32^3, lossy sphere eps=4-0.1j (r = L/4), 4x4x2 jittered
+     subdomains, 64 plane waves on a seeded 8x8 angle grid
+  3  2-wavelength cube 20^3, per-cell eps ~ U[1,3], 2x2x2 equal subdomains,
+     1 plane wave, 16 probe edges and 20 finite-difference cells
+  4  4x4x2-wavelength box 48x48x24 with a centred 2x2-wavelength PEC plate
+     (tangential edges removed), 4x4x2 jittered subdomains, 8 plane waves
+  5  6-wavelength cube 64^3, sphere r = L/4 with per-cell eps' ~ U[2,6] and
+     loss tangent 0.01, 4x4x4 jittered subdomains, 128 plane waves
+
+Random draws, in this order, from numpy.random.default_rng(seed): interior
+cut jitter (x cuts, then y, then z; integers in [-3, 3]), per-cell
+permittivities, plane-wave angles and polarisations, probe edges, FD cells.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+K0 = 2.0 * math.pi  # free-space wavenumber for wavelength 1
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    lx: float
+    ly: float
+    lz: float
+    k: float
+    eps: np.ndarray            # complex128, n_cells, x-fastest (i + nx*(j + ny*k))
+    pec_edge: np.ndarray | None  # uint8 per global edge (1 = removed) or None
+    cx: np.ndarray             # int32 cut cell indices, length px+1, 0..nx
+    cy: np.ndarray
+    cz: np.ndarray
+    khat: np.ndarray           # (nrhs, 3) unit propagation directions
+    pol: np.ndarray            # (nrhs, 3) complex polarisations, pol . khat = 0
+    probes: np.ndarray | None = None    # int64 global edge ids (objective)
+    fd_cells: np.ndarray | None = None  # int64 cell ids (finite differences)
+    seed: int = 0
+
+    @property
+    def n_cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_edges(self) -> int:
+        nx, ny, nz = self.nx, self.ny, self.nz
+        return nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
+
+    @property
+    def nrhs(self) -> int:
+        return self.khat.shape[0]
+
+    @property
+    def partition(self) -> tuple[int, int, int]:
+        return len(self.cx) - 1, len(self.cy) - 1, len(self.cz) - 1
+
+    def khat_pol6(self) -> np.ndarray:
+        """(nrhs, 9) float64 rows: 3 direction components, then the complex
+        polarisation as (re x, im x, re y, im y, re z, im z)."""
+        out = np.zeros((self.nrhs, 9))
+        out[:, :3] = self.khat
+        out[:, 3::2] = self.pol.real
+        out[:, 4::2] = self.pol.imag
+        return out
+
+
+def cuts(n: int, p: int, rng: np.random.Generator | None, jit: int = 3) -> np.ndarray:
+    """Cut cell indices round(i n / p) (+ jitter in [-jit, jit] when rng is given)."""
+    c = [0]
+    for i in range(1, p):
+        v = int(round(i * n / p))
+        if rng is not None:
+            v += int(rng.integers(-jit, jit + 1))
+        c.append(v)
+    c.append(n)
+    c = np.asarray(c, dtype=np.int32)
+    if np.any(np.diff(c) < 1):
+        raise ValueError(f"degenerate cuts {c}")
+    return c
+
+
+def _angles_to_waves(theta, phi, psi):
+    st, ct, sp_, cp = np.sin(theta), np.cos(theta), np.sin(phi), np.cos(phi)
+    khat = np.stack([st * cp, st * sp_, ct], axis=1)
+    th_hat = np.stack([ct * cp, ct * sp_, -st], axis=1)
+    ph_hat = np.stack([-sp_, cp, np.zeros_like(phi)], axis=1)
+    pol = np.cos(psi)[:, None] * th_hat + np.sin(psi)[:, None] * ph_hat
+    return khat, pol.astype(np.complex128)
+
+
+def _grid_waves(rng, nth, nph):
+    u, v = rng.random(), rng.random()
+    th = (np.arange(nth) + u) * math.pi / nth
+    ph = (np.arange(nph) + v) * 2 * math.pi / nph
+    theta = np.repeat(th, nph)
+    phi = np.tile(ph, nth)
+    psi = rng.random(nth * nph) * 2 * math.pi
+    return _angles_to_waves(theta, phi, psi)
+
+
+def _random_waves(rng, n):
+    ct = rng.uniform(-1.0, 1.0, n)
+    phi = rng.uniform(0.0, 2 * math.pi, n)
+    psi = rng.uniform(0.0, 2 * math.pi, n)
+    return _angles_to_waves(np.arccos(ct), phi, psi)
+
+
+def _cell_centres(nx, ny, nz, lx, ly, lz):
+    i = (np.arange(nx) + 0.5) * lx / nx
+    j = (np.arange(ny) + 0.5) * ly / ny
+    k = (np.arange(nz) + 0.5) * lz / nz
+    kk, jj, ii = np.meshgrid(k, j, i, indexing="ij")
+    return ii.ravel(), jj.ravel(), kk.ravel()   # x-fastest order
+
+
+def _sphere_mask(nx, ny, nz, lx, ly, lz, r):
+    x, y, z = _cell_centres(nx, ny, nz, lx, ly, lz)
+    return (x - lx / 2) ** 2 + (y - ly / 2) ** 2 + (z - lz / 2) ** 2 <= r * r
+
+
+def pec_plate_mask(nx, ny, nz, i0, i1, j0, j1, kp) -> np.ndarray:
+    """Edge mask of a zero-thickness PEC plate in the plane of node layer kp,
+    covering node range [i0, i1] x [j0, j1] (rim included): every x- and
+    y-edge lying in it is marked.  Global edge numbering: x-edges, then
+    y-edges, then z-edges, each x-fastest over its own (i, j, k) box."""
+    nex = nx * (ny + 1) * (nz + 1)
+    ney = (nx + 1) * ny * (nz + 1)
+    nez = (nx + 1) * (ny + 1) * nz
+    m = np.zeros(nex + ney + nez, dtype=np.uint8)
+    for j in range(j0, j1 + 1):
+        for i in range(i0, i1):
+            m[i + nx * (j + (ny + 1) * kp)] = 1
+    for j in range(j0, j1):
+        for i in range(i0, i1 + 1):
+            m[nex + i + (nx + 1) * (j + ny * kp)] = 1
+    return m
+
+
+def make(index: int, seed: int | None = None) -> Workload:
+    """Workload 1..5 (see module docstring); seed defaults to the index."""
+    seed = index if seed is None else seed
+    rng = np.random.default_rng(seed)
+    pec = None
+    probes = fd = None
+    if index == 1:
+        n, L = 12, 1.0
+        dims = (n, n, n, L, L, L)
+        cx, cy, cz = cuts(n, 2, None), cuts(n, 2, None), cuts(n, 1, None)
+        eps = np.ones(n ** 3, np.complex128)
+        eps[_sphere_mask(*dims, 0.25)] = 4.0
+        khat, pol = _random_waves(rng, 1)
+    elif index == 2:
+        n, L = 32, 3.0
+        dims = (n, n, n, L, L, L)
+        cx, cy, cz = cuts(n, 4, rng), cuts(n, 4, rng), cuts(n, 2, rng)
+        eps = np.ones(n ** 3, np.complex128)
+        eps[_sphere_mask(*dims, L / 4)] = 4.0 - 0.1j
+        khat, pol = _grid_waves(rng, 8, 8)
+    elif index == 3:
+        n, L = 20, 2.0
+        dims = (n, n, n, L, L, L)
+        cx, cy, cz = cuts(n, 2, None), cuts(n, 2, None), cuts(n, 2, None)
+        eps = rng.uniform(1.0, 3.0, n ** 3).astype(np.complex128)
+        khat, pol = _random_waves(rng, 1)
+    elif index == 4:
+        dims = (48, 48, 24, 4.0, 4.0, 2.0)
+        cx, cy, cz = cuts(48, 4, rng), cuts(48, 4, rng), cuts(24, 2, rng)
+        eps = np.ones(48 * 48 * 24, np.complex128)
+        pec = pec_plate_mask(48, 48, 24, 12, 36, 12, 36, 12)
+        khat, pol = _grid_waves(rng, 2, 4)
+    elif index == 5:
+        n, L = 64, 6.0
+        dims = (n, n, n, L, L, L)
+        cx, cy, cz = cuts(n, 4, rng), cuts(n, 4, rng), cuts(n, 4, rng)
+        eps = np.ones(n ** 3, np.complex128)
+        m = _sphere_mask(*dims, L / 4)
+        eps[m] = rng.uniform(2.0, 6.0, int(m.sum())) * (1.0 - 0.01j)
+        khat, pol = _grid_waves(rng, 8, 16)
+    else:
+        raise ValueError(index)
+    w = Workload(f"config{index}", *dims, K0, eps, pec, cx, cy, cz, khat, pol, seed=seed)
+    if index == 3:
+        w.probes = np.sort(rng.choice(w.n_edges, 16, replace=False)).astype(np.int64)
+        w.fd_cells = np.sort(rng.choice(w.n_cells, 20, replace=False)).astype(np.int64)
+    return w
+
+
+def tiny(nx, ny, nz, px, py, pz, seed=0, lossy=True, nrhs=1, pec=None, jitter=False,
+         h=0.1) -> Workload:
+    """Small seeded mesh for unit tests: random per-cell eps (lossy if asked),
+    equal or jittered (+-1 cell) cuts, random plane waves."""
+    rng = np.random.default_rng(seed)
+    cx = cuts(nx, px, rng if jitter else None, 1)
+    cy = cuts(ny, py, rng if jitter else None, 1)
+    cz = cuts(nz, pz, rng if jitter else None, 1)
+    eps = rng.uniform(1.0, 3.0, nx * ny * nz).astype(np.complex128)
+    if lossy:
+        eps = eps * (1.0 - 0.05j)
+    khat, pol = _random_waves(rng, nrhs)
+    w = Workload(f"tiny{nx}x{ny}x{nz}", nx, ny, nz, nx * h, ny * h, nz * h, K0, eps, pec,
+                 cx, cy, cz, khat, pol, seed=seed)
+    return w
