@@ -1,0 +1,229 @@
+/*
+ * d3m.h -- C ABI of the GB300 D^3M library (Direct Domain Decomposition Method
+ * for finite-element electromagnetics, Moshfegh & Vouvakis, ICEAA 2016).
+ *
+ * Problem (Theory section, decomposed BVP): curl curl E - k^2 eps_r E = 0 in
+ * an axis-aligned box meshed by nx*ny*nz bricks with lowest-order Nedelec
+ * edge elements, a first-order absorbing boundary condition on the whole
+ * outer boundary driven by incident plane waves, mu_r = 1.  The box is cut
+ * into px*py*pz subdomains; the library assembles the decomposed system of
+ * Eq. (1), [[A, D], [D^T, 0]] [E; lambda] = [f; 0], and factors it with the
+ * paper's seven main steps: dense domain matrices K_D, assembly of the
+ * block-sparse K = sum D_i^T A_i^{-1} D_i, block nested-dissection ordering of
+ * its clique graph, symbolic factorisation, block LDL^T with restricted
+ * Bunch-Kaufman pivots (Algorithm 1, in its multifrontal form), substitution
+ * for lambda and recovery of E.
+ *
+ * Conventions for every entry point:
+ *  - complex numbers are pairs of doubles (re, im) in consecutive memory;
+ *  - global edge numbering: x-edges, then y-edges, then z-edges; each family
+ *    runs its start node (i, j, k) x-fastest: x-edge (i,j,k) = i + nx*(j +
+ *    (ny+1)*k), y-edge = NX + i + (nx+1)*(j + ny*k), z-edge = NX + NY + i +
+ *    (nx+1)*(j + (ny+1)*k), NX = nx(ny+1)(nz+1), NY = (nx+1)ny(nz+1); every
+ *    edge is oriented along +axis;
+ *  - cells are numbered i + nx*(j + ny*k); subdomains ix + px*(iy + py*iz);
+ *  - RHS / solution blocks are column-major n_edges x nrhs with a leading
+ *    dimension >= n_edges, in global edge numbering with PEC edges present
+ *    (their solution rows are returned as 0);
+ *  - every call returns D3M_OK (0) or an error code; a message is available
+ *    from d3m_last_error(ctx).  No call aborts the process or traps the GPU;
+ *    device-side waits are bounded and report D3M_ETIMEOUT.
+ *  - all device work is ordered on d3m_options.stream (a cudaStream_t, NULL =
+ *    the legacy default stream); calls return after the work is complete.
+ */
+#ifndef D3M_H
+#define D3M_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum d3m_status {
+  D3M_OK = 0,
+  D3M_EINVAL = 1,     /* bad argument (sizes, cuts, pointers) */
+  D3M_ENOMEM = 2,     /* host or device allocation failed */
+  D3M_ESINGULAR = 3,  /* a pivot column of a diagonal block is exactly zero */
+  D3M_ENOCONV = 4,    /* iterative refinement did not reach refine_tol */
+  D3M_ETIMEOUT = 5,   /* a bounded device-side wait expired */
+  D3M_ECUDA = 6,      /* a CUDA runtime call failed */
+  D3M_ESTATE = 7      /* call out of order (e.g. solve before factor) */
+};
+
+enum d3m_precision {
+  D3M_FP64 = 0,       /* factors and substitutions in complex128 */
+  D3M_MIXED = 1       /* factors in complex64 (pivot choice and 1x1/2x2
+                         inverses in fp64), fp64 residuals and iterative
+                         refinement against the fp64 sparse operator */
+};
+
+typedef struct d3m_ctx d3m_ctx;
+
+/* Axis-aligned brick grid [0,lx] x [0,ly] x [0,lz], nx*ny*nz cells. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double lx, ly, lz;
+} d3m_mesh;
+
+/* Materials.  eps_r: 2*n_cells doubles (re, im) per cell, time convention
+ * e^{jwt} so losses have negative imaginary part.  pec_edge: n_edges bytes or
+ * NULL; 1 marks an edge whose tangential field is zero (its dof is removed:
+ * a Dirichlet condition, used for the paper's PEC plates). */
+typedef struct {
+  const double *eps_r;
+  const uint8_t *pec_edge;
+} d3m_materials;
+
+/* Subdomain cuts: cx has px+1 strictly increasing cell indices from 0 to nx
+ * (likewise cy, cz).  Edges on an interior cut plane are copied into every
+ * subdomain containing them. */
+typedef struct {
+  int32_t px, py, pz;
+  const int32_t *cx, *cy, *cz;
+} d3m_partition;
+
+typedef struct {
+  int32_t precision;    /* d3m_precision */
+  int32_t leaf_max;     /* nested-dissection leaf size (edges); 0 -> 64 */
+  double refine_tol;    /* mixed: stop when ||f - A x||_inf / ||f||_inf <= tol;
+                           0 -> 1e-10 */
+  int32_t max_refine;   /* mixed: refinement step cap; 0 -> 10 */
+  void *stream;         /* cudaStream_t */
+} d3m_options;
+
+/* Per-solve report: per column relative residual (Numerical Results
+ * section's ||A x - f||_inf / ||f||_inf) and refinement steps taken. */
+typedef struct {
+  double *resid;        /* caller array of nrhs doubles, or NULL */
+  int32_t iters;        /* refinement steps (0 for FP64) */
+  double max_resid;
+} d3m_solve_info;
+
+/* Sizes and counts of a set-up problem. */
+typedef struct {
+  int64_t n_edges, n_free, n_lm, n_blocks, n_subdomains;
+  int64_t n_m;            /* order of the saddle matrix [[A, D], [D^T, 0]] */
+  int64_t n_fronts, n_levels, max_front;
+  int64_t arena_bytes;    /* front storage of the chosen precision */
+  double flops_interior;  /* real flops (8 per complex MAC) of the interior fronts */
+  double flops_domain;    /* ... of the interface fronts (domain matrices K_D) */
+  double flops_k;         /* ... of the fronts of K (Algorithm 1) */
+  int64_t n_2x2;          /* 2x2 pivots taken by the last factorisation */
+  double min_pivot_ratio; /* smallest |d| / max|column| seen (diagnostic) */
+} d3m_stats;
+
+/*
+ * d3m_setup -- host-only analysis (no CUDA call is made).
+ * Builds the element matrices, the subdomain matrices A_i with interface
+ * loss/gain +-jk T_f (sign + on the side facing the higher subdomain index),
+ * the signed multiplier map D (one multiplier per extra copy, tied to the
+ * lowest-index face neighbour), the orderings (nested dissection inside each
+ * subdomain with interface dofs last; block nested dissection of the clique
+ * graph of K, main step 3) and the supernodal symbolic factorisation (main
+ * step 4).  Host inputs are copied; the caller keeps ownership.  k is the
+ * wavenumber (2*pi for wavelength 1).  Returns D3M_EINVAL on inconsistent
+ * sizes or cuts.  *out receives a context to pass to d3m_free.
+ */
+int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double k,
+              const d3m_partition *part, const d3m_options *opt, d3m_ctx **out);
+
+/*
+ * d3m_factor -- numeric factorisation on the GPU (main steps 1, 2, 5).
+ * First call uploads the plan and allocates the device arena (all device
+ * memory is owned by the context).  Runs, level by level over the assembly
+ * tree, the front assembly (extend-add), restricted Bunch-Kaufman panels and
+ * trailing updates of every front: subdomain interiors, interface fronts whose
+ * contribution blocks are -K_D^(i), and the fronts of K.  D3M_ESINGULAR if a
+ * pivot column is exactly zero.
+ */
+int d3m_factor(d3m_ctx *ctx);
+
+/*
+ * d3m_solve -- main steps 6-7 for nrhs excitations, DEVICE pointers.
+ * rhs: n_edges x nrhs complex column-major (ld >= n_edges), read only.
+ * x:   n_edges x nrhs complex column-major (ld >= n_edges), written.
+ * Multiplier values can be read afterwards with d3m_structure(D3M_LAMBDA).
+ * MIXED precision refines until the residual criterion holds (D3M_ENOCONV
+ * otherwise; x then holds the last iterate).  info may be NULL.
+ */
+int d3m_solve(d3m_ctx *ctx, const double *rhs, int64_t ldb, double *x, int64_t ldx,
+              int32_t nrhs, d3m_solve_info *info);
+
+/* d3m_solve_host -- as d3m_solve with HOST pointers (pinned memory gives
+ * asynchronous copies); the host<->device copies run on the context stream. */
+int d3m_solve_host(d3m_ctx *ctx, const double *rhs, int64_t ldb, double *x, int64_t ldx,
+                   int32_t nrhs, d3m_solve_info *info);
+
+/*
+ * d3m_rhs_planewave -- host computation of the ABC right-hand side for
+ * incident plane waves E_inc = p exp(-jk khat.r):  f_v = -sum over outer
+ * faces of int (n x curl E_inc - jk E_inc,t) . N_v dS, 3x3 Gauss-Legendre
+ * points per face.  khat_pol: nrhs rows of 9 doubles (khat xyz, then p as
+ * re x, im x, re y, im y, re z, im z).  rhs: host, n_edges x nrhs complex,
+ * column-major, ld >= n_edges.
+ */
+int d3m_rhs_planewave(d3m_ctx *ctx, const double *khat_pol, int32_t nrhs, double *rhs,
+                      int64_t ldb);
+
+/* Structure / diagnostics export (host memory).  Call with buf = NULL to get
+ * the size in bytes in *bytes; then with a buffer of that size. */
+enum d3m_structure_kind {
+  D3M_SN_RANGE = 0,    /* int64 [n_fronts][2]: pivot range [start, end) in M order */
+  D3M_SN_PARENT = 1,   /* int64 [n_fronts]: supernodal elimination tree, -1 = root */
+  D3M_SN_KIND = 2,     /* int64 [n_fronts][2]: kind (0 interior ND node, 1 interface
+                          dofs B_i, 2 block of K) and owner (subdomain or block id) */
+  D3M_SN_STRUCT = 3,   /* int64 [n_fronts + 1] offsets, then the concatenated sorted
+                          update-row lists (M indices) */
+  D3M_M_MAP = 4,       /* int64 [n_m][2]: (subdomain, global edge) of each M index,
+                          (-1, multiplier id) for multipliers */
+  D3M_LM = 5,          /* int64 [n_lm][3]: (global edge, + subdomain, - subdomain) */
+  D3M_BLOCKS = 6,      /* int64 [n_blocks][3]: (a, b, first multiplier id) in block order */
+  D3M_LAMBDA = 7,      /* double [n_lm][nrhs][2]: multipliers of the last solve,
+                          column-major complex */
+  D3M_STATS = 8,       /* d3m_stats */
+  D3M_M_ENTRIES = 9    /* double [nnz][4]: (row, col, re, im) of the lower triangle of
+                          M = [[A, D], [D^T, 0]] in M order, as assembled */
+};
+int d3m_structure(d3m_ctx *ctx, int32_t which, void *buf, size_t *bytes);
+
+/*
+ * d3m_dense_ldlt -- the front kernel alone: restricted Bunch-Kaufman partial
+ * LDL^T of `batch` dense complex-symmetric m x m matrices (DEVICE pointers,
+ * column-major, lower triangle read, consecutive matrices m*m complex apart),
+ * pivots restricted to the leading p x p block (the paper's block-restricted
+ * pivoting).  On return, in place: columns 0..p-1 hold unit-lower L in pivot
+ * order (rows 0..m-1; the diagonal holds the diagonal of D and the (k+1,k)
+ * entry of a 2x2 block is 0), rows/cols p..m-1 hold the Schur complement C
+ * (lower).
+ * perm (device int32, batch*m): pivot position -> original index.
+ * dinv (device double, batch*p*6): per pivot (re,im) of D^{-1}(k,k), of the
+ * coupling entry of its 2x2 block (0 for 1x1) and a block-size code
+ * (1, 2 = first of a pair, -2 = second) in the real slot of the third pair.
+ * info (device int32, batch): 0 or 1 + first zero-pivot column.
+ * fp64 only; stream as in d3m_options.  Does not need a context.
+ */
+int d3m_dense_ldlt(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm, double *dinv,
+                   int32_t *info, void *stream);
+
+/*
+ * d3m_export_front -- diagnostics: copy front `front` (M-order supernode id)
+ * of the last factorisation to host memory.  F: m*m complex (column-major,
+ * after factorisation: L in the pivot columns, D on the diagonal / 2x2
+ * couplings, contribution block below-right), perm: p int32 (pivot position
+ * -> local index), dinv: 6*p doubles as in d3m_dense_ldlt.  Any pointer may be
+ * NULL.  Values are widened to fp64 for the MIXED precision.  *m_out, *p_out
+ * receive the front sizes (call with NULL buffers first to size them).
+ */
+int d3m_export_front(d3m_ctx *ctx, int64_t front, int32_t *m_out, int32_t *p_out, double *F,
+                     int32_t *perm, double *dinv);
+
+int d3m_stats_get(d3m_ctx *ctx, d3m_stats *out);
+const char *d3m_last_error(const d3m_ctx *ctx);
+void d3m_free(d3m_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* D3M_H */

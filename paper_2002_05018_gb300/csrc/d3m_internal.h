@@ -1,0 +1,103 @@
+// Internal state shared by the host set-up (host_setup.cpp) and the device
+// factor/solve engine (engine.cu).  Not part of the public ABI.
+#pragma once
+
+#include <array>
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/d3m.h"
+
+namespace d3m {
+
+using cplx = std::complex<double>;
+
+struct DeviceState;  // engine.cu
+
+struct Plan {
+  // ---- problem
+  int nx = 0, ny = 0, nz = 0;
+  double lx = 0, ly = 0, lz = 0, k = 0, h[3] = {0, 0, 0};
+  std::vector<cplx> eps;
+  std::vector<uint8_t> pec;  // per edge, 1 = removed
+  int parts[3] = {1, 1, 1};
+  std::vector<int> cuts[3];
+  int64_t nex = 0, ney = 0, nez = 0, n_edges = 0, n_free = 0;
+
+  // ---- decomposition
+  int nsub = 0;
+  std::vector<std::array<int, 3>> sub_lo, sub_hi;
+  std::vector<std::vector<int64_t>> sub_edges;  // sorted global ids of free edges
+  std::vector<int64_t> lm_edge, lm_plus, lm_minus;  // multipliers in block order
+  std::vector<std::array<int64_t, 3>> blocks;       // (a, b, first multiplier)
+
+  // ---- ordering of M = [[A, D], [D^T, 0]]
+  int64_t n_m = 0;
+  std::vector<int64_t> m_sub, m_edge;  // (subdomain, edge) or (-1, multiplier)
+  std::vector<int64_t> owner_m;        // per global edge: M index of its owner copy, -1 for PEC
+  int64_t lam_start = 0;               // M index of multiplier 0
+
+  // ---- supernodes == fronts (same ids, elimination order)
+  std::vector<int64_t> sn_start, sn_end, sn_kind, sn_owner, parent;
+  std::vector<int64_t> struct_ptr, struct_idx;  // update rows per front (sorted M indices)
+  std::vector<int32_t> emap;                    // per struct entry: local row in the parent front
+  std::vector<int32_t> child_rank;              // position among the parent's children
+  std::vector<int32_t> level;                   // height in the assembly tree
+  int n_levels = 0;
+  std::vector<int32_t> level_fronts, level_ptr;   // fronts grouped by level
+  std::vector<int32_t> ea_child, ea_ptr;          // per (level, pass): children to extend-add
+  std::vector<int32_t> ea_pass_ptr;               // level -> first pass index into ea_ptr
+  std::vector<int64_t> front_off;                 // element offset of the m x m front in the arena
+  std::vector<int64_t> piv_off, y_off;            // offsets in pivot arrays / solve buffers
+  int64_t arena_elems = 0, piv_total = 0, y_rows = 0;
+  int max_front = 0;
+
+  // ---- original entries of M, lower triangle, grouped by level
+  std::vector<int64_t> ent_off;   // arena element offset
+  std::vector<cplx> ent_val;
+  std::vector<int64_t> ent_ptr;   // per level
+  std::vector<int64_t> ent_row, ent_col;  // M indices of each entry (diagnostics)
+
+  // ---- global operator A (free edges, full CSR, global numbering) for residuals
+  std::vector<int64_t> csr_ptr;
+  std::vector<int32_t> csr_col;
+  std::vector<cplx> csr_val;
+
+  // ---- flop counts
+  double flops[3] = {0, 0, 0};
+};
+
+struct Ctx {
+  Plan plan;
+  d3m_options opt{};
+  std::string err;
+  DeviceState *dev = nullptr;
+  d3m_stats stats{};
+  std::vector<cplx> lambda_host;  // last solve's multipliers, column-major n_lm x nrhs
+  int32_t lambda_nrhs = 0;
+  bool factored = false;
+};
+
+// host_setup.cpp
+int build_plan(Ctx &c, const d3m_mesh *mesh, const d3m_materials *mat, double k,
+               const d3m_partition *part);
+void element_matrices(const double h[3], double S[12][12], double M[12][12]);
+void face_matrix(const double h[3], int axis, int side, double T[12][12]);
+void cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[12]);
+int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb);
+
+// engine.cu
+int dev_factor(Ctx &c);
+int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, int nrhs,
+              d3m_solve_info *info, bool host_ptrs);
+void dev_free(Ctx &c);
+int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, int32_t *info,
+               void *stream, std::string &err);
+
+}  // namespace d3m
+
+struct d3m_ctx {
+  d3m::Ctx c;
+};

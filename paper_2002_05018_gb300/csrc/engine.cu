@@ -1,0 +1,1346 @@
+// Device engine of the D^3M library: numeric factorisation (main steps 1, 2
+// and 5) and substitution (main steps 6-7) on one GB300.
+//
+// The decomposed system of Eq. (1), M = [[A, D], [D^T, 0]], is factored as one
+// sparse complex-symmetric LDL^T in the multifrontal form that the paper
+// allows for Algorithm 1.  The ordering puts, per subdomain, its interior
+// (nested dissection) then its interface dofs B_i, and finally the interface
+// blocks of K; fronts are processed level by level (all subdomains at once):
+//   - interior fronts: partial LDL^T, Schur complement passed up;
+//   - interface fronts [B_i ; lambda_i]: eliminating B_i leaves the
+//     contribution -D_i^T A_i^{-1} D_i = -K_D^(i) on the multipliers (main
+//     step 1), which extend-add scatters into the fronts of K (main step 2);
+//   - fronts of K: block LDL^T with Bunch-Kaufman pivots restricted to the
+//     block (main step 5, Algorithm 1).
+// Every front is dense, column-major, lower triangle, in one arena.  A front
+// is factored by panels of NB columns (restricted Bunch-Kaufman with
+// left-looking updates inside the panel, one CTA per front) followed by a
+// trailing update of all fronts of the level (64x64 tiles).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "d3m_internal.h"
+
+namespace d3m {
+
+// ------------------------------------------------------------ complex helpers
+template <typename T>
+struct cx {
+  T re, im;
+};
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mk(T r, T i) {
+  cx<T> z;
+  z.re = r;
+  z.im = i;
+  return z;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// a - b*c
+template <typename T>
+__device__ __forceinline__ cx<T> cfms(cx<T> a, cx<T> b, cx<T> c) {
+  a.re -= b.re * c.re;
+  a.re += b.im * c.im;
+  a.im -= b.re * c.im;
+  a.im -= b.im * c.re;
+  return a;
+}
+// a + b*c
+template <typename T>
+__device__ __forceinline__ cx<T> cfma(cx<T> a, cx<T> b, cx<T> c) {
+  a.re += b.re * c.re;
+  a.re -= b.im * c.im;
+  a.im += b.re * c.im;
+  a.im += b.im * c.re;
+  return a;
+}
+template <typename T>
+__device__ __forceinline__ double cabs1(cx<T> a) {
+  return fabs((double)a.re) + fabs((double)a.im);
+}
+__device__ __forceinline__ double2 zdiv1(double2 a) {  // 1 / a
+  double d = a.x * a.x + a.y * a.y;
+  return make_double2(a.x / d, -a.y / d);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ double2 to_d(cx<T> a) {
+  return make_double2((double)a.re, (double)a.im);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> from_d(double2 a) {
+  return mk<T>((T)a.x, (T)a.y);
+}
+
+#define CUDA_TRY(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      c.err = std::string("CUDA error ") + cudaGetErrorString(e_) + " at " #call; \
+      return D3M_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+constexpr int NB = 32;         // panel width (columns per panel kernel)
+constexpr int UT = 64;         // trailing-update tile edge
+constexpr int UK = 16;         // trailing-update k chunk
+constexpr int PANEL_THREADS = 256;
+constexpr double BK_ALPHA = 0.6403882032022076;  // (1 + sqrt(17)) / 8
+
+// ------------------------------------------------------------ front tables
+struct FrontTab {
+  const int32_t *m, *p;
+  const int64_t *off, *piv, *soff, *start, *yoff;
+  const int32_t *parent;
+};
+
+// ------------------------------------------------------------ assembly kernels
+template <typename T>
+__global__ void k_assemble(int64_t n, const int64_t *__restrict__ off, const double2 *__restrict__ val,
+                           cx<T> *__restrict__ arena) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) arena[off[i]] = from_d<T>(val[i]);
+}
+
+// pass: children list; adds child contribution blocks (lower) into parents
+template <typename T>
+__global__ void __launch_bounds__(256) k_extend_add(const int32_t *__restrict__ kids, FrontTab ft,
+                                                    const int32_t *__restrict__ emap,
+                                                    cx<T> *__restrict__ arena) {
+  const int c = kids[blockIdx.y];
+  const int mc = ft.m[c], pc = ft.p[c], n = mc - pc;
+  const int nt = (n + 31) / 32;
+  const int t = blockIdx.x;
+  if (t >= nt * (nt + 1) / 2) return;
+  int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > t) --I;
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  const int J = t - I * (I + 1) / 2;
+  const int q = ft.parent[c];
+  const int mq = ft.m[q];
+  const cx<T> *C = arena + ft.off[c];
+  cx<T> *F = arena + ft.off[q];
+  const int32_t *map = emap + ft.soff[c];
+  const int i = I * 32 + (threadIdx.x & 31);
+  if (i >= n) return;
+  const int64_t ri = map[i];
+  for (int jj = threadIdx.x >> 5; jj < 32; jj += 8) {
+    int j = J * 32 + jj;
+    if (j > i || j >= n) continue;
+    cx<T> v = C[(int64_t)(pc + i) + (int64_t)(pc + j) * mc];
+    cx<T> *dst = F + ri + (int64_t)map[j] * mq;
+    dst->re += v.re;
+    dst->im += v.im;
+  }
+}
+
+// ------------------------------------------------------------ block reductions
+struct ArgMax {
+  double v;
+  int i;
+};
+__device__ __forceinline__ ArgMax amax(ArgMax a, ArgMax b) {
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+__device__ ArgMax block_argmax(ArgMax x, ArgMax *sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMax y;
+    y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+    y.i = __shfl_down_sync(0xffffffffu, x.i, o);
+    x = amax(x, y);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    x = l < (int)(blockDim.x >> 5) ? sh[l] : ArgMax{-1.0, 0x7fffffff};
+    for (int o = 16; o > 0; o >>= 1) {
+      ArgMax y;
+      y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+      y.i = __shfl_down_sync(0xffffffffu, x.i, o);
+      x = amax(x, y);
+    }
+    if (l == 0) sh[0] = x;
+  }
+  __syncthreads();
+  ArgMax r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------ panel kernel
+// Restricted Bunch-Kaufman factorisation of up to NB columns of each front
+// of the level (one CTA per front).  Left-looking inside the panel: the
+// updated column k is W[:, j] = F[:, k] - L[:, k0:k] W[k, 0:j]^T with
+// W = L D.  Pivot candidates are rows k+1 .. p-1 only (the pivot block); no
+// pivot is delayed.  Interchanges are applied to all previously factored
+// columns of the front so L ends in pivot order.
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+    k_panel(const int32_t *__restrict__ lvl, FrontTab ft, const int64_t *__restrict__ wofs,
+            cx<T> *__restrict__ arena, cx<T> *__restrict__ Wbuf, int32_t *__restrict__ perm,
+            double2 *__restrict__ dinv_d, double2 *__restrict__ dinv_o, int8_t *__restrict__ psize,
+            int32_t *__restrict__ st_k0, int32_t *__restrict__ st_kb, int32_t *__restrict__ st_info,
+            double *__restrict__ st_minpiv) {
+  const int f = lvl[blockIdx.x];
+  const int m = ft.m[f], p = ft.p[f];
+  const int k0 = st_k0[f];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (k0 >= p) {
+    if (tid == 0) st_kb[f] = 0;
+    return;
+  }
+  cx<T> *F = arena + ft.off[f];
+  cx<T> *W = Wbuf + wofs[blockIdx.x];
+  int32_t *pv = perm + ft.piv[f];
+  double2 *dd = dinv_d + ft.piv[f];
+  double2 *dof = dinv_o + ft.piv[f];
+  int8_t *ps = psize + ft.piv[f];
+  const int64_t ld = m;
+  __shared__ cx<T> wrow[NB];
+  __shared__ ArgMax red[32];
+  __shared__ int s_kp, s_kstep, s_imax;
+  __shared__ double s_minpiv;
+  if (tid == 0) s_minpiv = 1e300;
+  int k = k0, j = 0;
+  while (k < p && j < NB - 1) {
+    // (1) updated column k -> W[:, j]
+    if (tid < j) wrow[tid] = W[k + (int64_t)tid * ld];
+    __syncthreads();
+    for (int i = k + tid; i < m; i += nth) {
+      cx<T> acc = F[i + (int64_t)k * ld];
+      for (int t = 0; t < j; ++t) acc = cfms(acc, F[i + (int64_t)(k0 + t) * ld], wrow[t]);
+      W[i + (int64_t)j * ld] = acc;
+    }
+    __syncthreads();
+    // (2) pivot test on the restricted column
+    ArgMax loc{-1.0, 0x7fffffff};
+    for (int i = k + 1 + tid; i < p; i += nth) loc = amax(loc, ArgMax{cabs1(W[i + (int64_t)j * ld]), i});
+    ArgMax cm = block_argmax(loc, red);
+    const double absakk = cabs1(W[k + (int64_t)j * ld]);
+    const double colmax = cm.i < p ? cm.v : 0.0;
+    const int imax = cm.i;
+    if (tid == 0) {
+      s_kstep = 1;
+      s_kp = k;
+      s_imax = imax;
+    }
+    if (fmax(absakk, colmax) == 0.0) {
+      if (tid == 0 && st_info[f] == 0) st_info[f] = k + 1;
+    } else if (absakk < BK_ALPHA * colmax) {
+      // (3) updated column imax -> W[:, j+1]
+      if (tid < j) wrow[tid] = W[imax + (int64_t)tid * ld];
+      __syncthreads();
+      for (int i = k + tid; i < m; i += nth) {
+        cx<T> acc = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
+        for (int t = 0; t < j; ++t) acc = cfms(acc, F[i + (int64_t)(k0 + t) * ld], wrow[t]);
+        W[i + (int64_t)(j + 1) * ld] = acc;
+      }
+      __syncthreads();
+      ArgMax rl{-1.0, 0x7fffffff};
+      for (int i = k + tid; i < p; i += nth)
+        if (i != imax) rl = amax(rl, ArgMax{cabs1(W[i + (int64_t)(j + 1) * ld]), i});
+      ArgMax rm = block_argmax(rl, red);
+      const double rowmax = rm.v > 0 ? rm.v : 0.0;
+      if (tid == 0) {
+        if (absakk * rowmax >= BK_ALPHA * colmax * colmax) {
+          s_kp = k;
+        } else if (cabs1(W[imax + (int64_t)(j + 1) * ld]) >= BK_ALPHA * rowmax) {
+          s_kp = imax;
+          s_kstep = -1;  // 1x1 at imax: copy column j+1 into j below
+        } else {
+          s_kp = imax;
+          s_kstep = 2;
+        }
+      }
+      __syncthreads();
+      if (s_kstep == -1) {
+        for (int i = k + tid; i < m; i += nth) W[i + (int64_t)j * ld] = W[i + (int64_t)(j + 1) * ld];
+      }
+    }
+    __syncthreads();
+    const int kstep = s_kstep == 2 ? 2 : 1;
+    const int kp = s_kp;
+    const int kk = k + kstep - 1;
+    if (kp != kk) {
+      // copy the non-updated column kk into position kp (its old content is in W)
+      if (tid == 0) F[kp + (int64_t)kp * ld] = F[kk + (int64_t)kk * ld];
+      for (int i = kk + 1 + tid; i < kp; i += nth) F[kp + (int64_t)i * ld] = F[i + (int64_t)kk * ld];
+      for (int i = kp + 1 + tid; i < m; i += nth) F[i + (int64_t)kp * ld] = F[i + (int64_t)kk * ld];
+      __syncthreads();
+      // interchange rows kk and kp in the factored columns and in W
+      for (int cidx = tid; cidx < kk; cidx += nth) {
+        cx<T> a = F[kk + (int64_t)cidx * ld], b = F[kp + (int64_t)cidx * ld];
+        F[kk + (int64_t)cidx * ld] = b;
+        F[kp + (int64_t)cidx * ld] = a;
+      }
+      for (int t = tid; t < j + kstep; t += nth) {
+        cx<T> a = W[kk + (int64_t)t * ld], b = W[kp + (int64_t)t * ld];
+        W[kk + (int64_t)t * ld] = b;
+        W[kp + (int64_t)t * ld] = a;
+      }
+      if (tid == 0) {
+        int32_t a = pv[kk];
+        pv[kk] = pv[kp];
+        pv[kp] = a;
+      }
+    }
+    __syncthreads();
+    if (kstep == 1) {
+      cx<T> d = W[k + (int64_t)j * ld];
+      double2 dd0 = to_d(d);
+      bool zero = dd0.x == 0.0 && dd0.y == 0.0;
+      double2 di = zero ? make_double2(0.0, 0.0) : zdiv1(dd0);
+      cx<T> dinv = from_d<T>(di);
+      for (int i = k + 1 + tid; i < m; i += nth) F[i + (int64_t)k * ld] = cmul(W[i + (int64_t)j * ld], dinv);
+      if (tid == 0) {
+        F[k + (int64_t)k * ld] = d;
+        dd[k] = di;
+        dof[k] = make_double2(0.0, 0.0);
+        ps[k] = 1;
+        double r = colmax > 0 ? (fabs(dd0.x) + fabs(dd0.y)) / colmax : 1e300;
+        s_minpiv = fmin(s_minpiv, r);
+      }
+    } else {
+      double2 d11 = to_d(W[k + (int64_t)j * ld]);
+      double2 d21 = to_d(W[k + 1 + (int64_t)j * ld]);
+      double2 d22 = to_d(W[k + 1 + (int64_t)(j + 1) * ld]);
+      double2 det = zmul(d11, d22);
+      double2 d2 = zmul(d21, d21);
+      det.x -= d2.x;
+      det.y -= d2.y;
+      double2 idet = zdiv1(det);
+      double2 i11 = zmul(d22, idet), i22 = zmul(d11, idet), i21 = zmul(d21, idet);
+      i21.x = -i21.x;
+      i21.y = -i21.y;
+      cx<T> a11 = from_d<T>(i11), a21 = from_d<T>(i21), a22 = from_d<T>(i22);
+      for (int i = k + 2 + tid; i < m; i += nth) {
+        cx<T> w1 = W[i + (int64_t)j * ld], w2 = W[i + (int64_t)(j + 1) * ld];
+        cx<T> l1 = cfma(cmul(w1, a11), w2, a21);
+        cx<T> l2 = cfma(cmul(w1, a21), w2, a22);
+        F[i + (int64_t)k * ld] = l1;
+        F[i + (int64_t)(k + 1) * ld] = l2;
+      }
+      if (tid == 0) {
+        // D on the diagonal; L(k+1, k) of a 2x2 pair is 0 (the coupling of D
+        // lives only in the inverse arrays), so every consumer may read the
+        // pivot columns as a plain unit-lower L
+        F[k + (int64_t)k * ld] = W[k + (int64_t)j * ld];
+        F[k + 1 + (int64_t)k * ld] = mk<T>(0, 0);
+        F[k + 1 + (int64_t)(k + 1) * ld] = W[k + 1 + (int64_t)(j + 1) * ld];
+        dd[k] = i11;
+        dd[k + 1] = i22;
+        dof[k] = i21;
+        dof[k + 1] = i21;
+        ps[k] = 2;
+        ps[k + 1] = -2;
+      }
+    }
+    __syncthreads();
+    k += kstep;
+    j += kstep;
+  }
+  if (tid == 0) {
+    st_k0[f] = k;
+    st_kb[f] = j;
+    if (s_minpiv < st_minpiv[f]) st_minpiv[f] = s_minpiv;
+  }
+}
+
+// ------------------------------------------------------------ trailing update
+// F[i, c] -= sum_t L[i, k0+t] W[c, t] for k0+kb <= c <= i < m (lower triangle)
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_update(const int32_t *__restrict__ lvl, FrontTab ft, const int64_t *__restrict__ wofs,
+             cx<T> *__restrict__ arena, const cx<T> *__restrict__ Wbuf,
+             const int32_t *__restrict__ st_k0, const int32_t *__restrict__ st_kb) {
+  const int f = lvl[blockIdx.y];
+  const int kb = st_kb[f];
+  if (kb == 0) return;
+  const int c0 = st_k0[f];
+  const int k0 = c0 - kb;
+  const int m = ft.m[f];
+  const int I0 = c0 / UT;
+  const int nt = (m + UT - 1) / UT - I0;
+  const int t = blockIdx.x;
+  if (nt <= 0 || t >= nt * (nt + 1) / 2) return;
+  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while (ii * (ii + 1) / 2 > t) --ii;
+  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+  const int jj = t - ii * (ii + 1) / 2;
+  const int r0 = (I0 + ii) * UT, cc0 = (I0 + jj) * UT;
+  cx<T> *F = arena + ft.off[f];
+  const cx<T> *W = Wbuf + wofs[blockIdx.y];
+  const int64_t ld = m;
+  __shared__ cx<T> Ls[UK][UT + 1];
+  __shared__ cx<T> Ws[UK][UT + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<T> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = mk<T>(0, 0);
+  for (int t0 = 0; t0 < kb; t0 += UK) {
+    for (int e = threadIdx.x; e < UK * UT; e += 256) {
+      int r = e % UT, tt = e / UT;
+      int gi = r0 + r, gc = cc0 + r;
+      bool ok = tt + t0 < kb;
+      Ls[tt][r] = (ok && gi < m) ? F[gi + (int64_t)(k0 + t0 + tt) * ld] : mk<T>(0, 0);
+      Ws[tt][r] = (ok && gc < m) ? W[gc + (int64_t)(t0 + tt) * ld] : mk<T>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int tt = 0; tt < UK; ++tt) {
+      cx<T> lv[4], wv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) lv[a] = Ls[tt][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) wv[b] = Ws[tt][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = cfma(acc[a][b], lv[a], wv[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int i = r0 + ty + 16 * a;
+    if (i >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int cidx = cc0 + tx + 16 * b;
+      if (cidx < c0 || cidx > i) continue;
+      cx<T> *dst = F + i + (int64_t)cidx * ld;
+      cx<T> v = *dst;
+      v.re -= acc[a][b].re;
+      v.im -= acc[a][b].im;
+      *dst = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------ solve kernels
+// Vectors in M space and front-local vectors are row-major (RHS fastest).
+template <typename T>
+__global__ void k_fwd_init(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ perm,
+                           const cx<T> *__restrict__ bM, cx<T> *__restrict__ Y, int r) {
+  const int f = lvl[blockIdx.y];
+  const int m = ft.m[f], p = ft.p[f];
+  const int64_t n = (int64_t)m * r;
+  cx<T> *Yf = Y + ft.yoff[f] * r;
+  const int32_t *pv = perm + ft.piv[f];
+  const int64_t st = ft.start[f];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / r), c = (int)(e % r);
+    Yf[e] = i < p ? bM[(st + pv[i]) * r + c] : mk<T>(0, 0);
+  }
+}
+
+template <typename T>
+__global__ void k_fwd_ea(const int32_t *__restrict__ kids, FrontTab ft, const int32_t *__restrict__ emap,
+                         const int32_t *__restrict__ iperm, cx<T> *__restrict__ Y, int r) {
+  const int c = kids[blockIdx.y];
+  const int q = ft.parent[c];
+  const int mc = ft.m[c], pc = ft.p[c], pq = ft.p[q];
+  const int64_t n = (int64_t)(mc - pc) * r;
+  const cx<T> *Yc = Y + (ft.yoff[c] + pc) * r;
+  cx<T> *Yq = Y + ft.yoff[q] * r;
+  const int32_t *map = emap + ft.soff[c];
+  const int32_t *ip = iperm + ft.piv[q];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / r), cc = (int)(e % r);
+    int tgt = map[i];
+    if (tgt < pq) tgt = ip[tgt];
+    cx<T> v = Yc[e];
+    cx<T> *d = Yq + (int64_t)tgt * r + cc;
+    d->re += v.re;
+    d->im += v.im;
+  }
+}
+
+// Forward substitution with unit-lower L11, update of the front's update
+// rows, then z = D^{-1} y written to zM in pivot order.
+template <typename T, int RC>
+__global__ void __launch_bounds__(256) k_fwd_solve(const int32_t *__restrict__ lvl, FrontTab ft,
+                                                   const cx<T> *__restrict__ arena,
+                                                   const double2 *__restrict__ dinv_d,
+                                                   const double2 *__restrict__ dinv_o,
+                                                   const int8_t *__restrict__ psize, cx<T> *__restrict__ Y,
+                                                   cx<T> *__restrict__ zM, int r) {
+  const int f = lvl[blockIdx.y];
+  const int m = ft.m[f], p = ft.p[f];
+  const int c0 = blockIdx.x * RC;
+  const int nc = min(RC, r - c0);
+  const cx<T> *F = arena + ft.off[f];
+  const int64_t ld = m;
+  cx<T> *Yf = Y + ft.yoff[f] * r;
+  const int8_t *ps = psize + ft.piv[f];
+  __shared__ cx<T> Ld[32][33];
+  __shared__ cx<T> ys[32][RC];
+  const int tid = threadIdx.x;
+  for (int kb0 = 0; kb0 < p; kb0 += 32) {
+    const int nbk = min(32, p - kb0);
+    for (int e = tid; e < 32 * 32; e += 256) {
+      int a = e % 32, b = e / 32;
+      cx<T> v = mk<T>(0, 0);
+      if (a < nbk && b < nbk && a > b) {
+        v = F[kb0 + a + (int64_t)(kb0 + b) * ld];
+        if (a == b + 1 && ps[kb0 + b] == 2) v = mk<T>(0, 0);
+      }
+      Ld[a][b] = v;
+    }
+    for (int e = tid; e < 32 * RC; e += 256) {
+      int a = e / RC, cc = e % RC;
+      ys[a][cc] = (a < nbk && cc < nc) ? Yf[(int64_t)(kb0 + a) * r + c0 + cc] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    for (int b = 0; b < nbk - 1; ++b) {
+      for (int e = tid; e < 32 * RC; e += 256) {
+        int a = e / RC, cc = e % RC;
+        if (a > b && a < nbk) ys[a][cc] = cfms(ys[a][cc], Ld[a][b], ys[b][cc]);
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < nbk * RC; e += 256) {
+      int a = e / RC, cc = e % RC;
+      if (cc < nc) Yf[(int64_t)(kb0 + a) * r + c0 + cc] = ys[a][cc];
+    }
+    // rows below the block
+    for (int i = kb0 + nbk + tid; i < m; i += 256) {
+      cx<T> acc[RC];
+#pragma unroll
+      for (int cc = 0; cc < RC; ++cc) acc[cc] = mk<T>(0, 0);
+      for (int b = 0; b < nbk; ++b) {
+        cx<T> l = F[i + (int64_t)(kb0 + b) * ld];
+#pragma unroll
+        for (int cc = 0; cc < RC; ++cc) acc[cc] = cfma(acc[cc], l, ys[b][cc]);
+      }
+      cx<T> *yi = Yf + (int64_t)i * r + c0;
+#pragma unroll
+      for (int cc = 0; cc < RC; ++cc)
+        if (cc < nc) {
+          cx<T> v = yi[cc];
+          v.re -= acc[cc].re;
+          v.im -= acc[cc].im;
+          yi[cc] = v;
+        }
+    }
+    __syncthreads();
+  }
+  // z = D^{-1} y (block diagonal), pivot order
+  const double2 *di = dinv_d + ft.piv[f];
+  const double2 *dof = dinv_o + ft.piv[f];
+  const int64_t st = ft.start[f];
+  for (int e = tid; e < p * RC; e += 256) {
+    int k = e / RC, cc = e % RC;
+    if (cc >= nc) continue;
+    double2 y = to_d(Yf[(int64_t)k * r + c0 + cc]);
+    double2 z = zmul(di[k], y);
+    int s = ps[k];
+    if (s == 2 || s == -2) {
+      int o = s == 2 ? k + 1 : k - 1;
+      double2 yo = to_d(Yf[(int64_t)o * r + c0 + cc]);
+      double2 t2 = zmul(dof[k], yo);
+      z.x += t2.x;
+      z.y += t2.y;
+    }
+    zM[(st + k) * r + c0 + cc] = from_d<T>(z);
+  }
+}
+
+// Backward substitution with L^T: x_piv = L11^{-T} (z - L21^T x_upd), written
+// to xM at the original (un-permuted) positions.
+template <typename T, int RC>
+__global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ lvl, FrontTab ft,
+                                                   const cx<T> *__restrict__ arena,
+                                                   const int32_t *__restrict__ perm,
+                                                   const int8_t *__restrict__ psize,
+                                                   const int64_t *__restrict__ sidx, cx<T> *__restrict__ Y,
+                                                   const cx<T> *__restrict__ zM, cx<T> *__restrict__ xM, int r) {
+  const int f = lvl[blockIdx.y];
+  const int m = ft.m[f], p = ft.p[f];
+  const int c0 = blockIdx.x * RC;
+  const int nc = min(RC, r - c0);
+  const cx<T> *F = arena + ft.off[f];
+  const int64_t ld = m;
+  cx<T> *Yf = Y + ft.yoff[f] * r;
+  const int8_t *ps = psize + ft.piv[f];
+  const int32_t *pv = perm + ft.piv[f];
+  const int64_t *rows = sidx + ft.soff[f];
+  const int64_t st = ft.start[f];
+  const int tid = threadIdx.x;
+  // gather x at the update rows
+  for (int e = tid; e < (m - p) * RC; e += 256) {
+    int i = e / RC, cc = e % RC;
+    if (cc < nc) Yf[(int64_t)(p + i) * r + c0 + cc] = xM[rows[i] * r + c0 + cc];
+  }
+  __syncthreads();
+  __shared__ cx<T> Ls[32][33];
+  __shared__ cx<T> Xs[32][RC];
+  __shared__ cx<T> v[32][RC];
+  const int last = ((p - 1) / 32) * 32;
+  const int b = tid / RC, cc = tid % RC;  // 32 x RC threads own (pivot col, rhs)
+  for (int kb0 = last; kb0 >= 0; kb0 -= 32) {
+    const int nbk = min(32, p - kb0);
+    cx<T> acc = mk<T>(0, 0);
+    for (int i0 = kb0 + nbk; i0 < m; i0 += 32) {
+      const int nr = min(32, m - i0);
+      for (int e = tid; e < 32 * 32; e += 256) {
+        int rr = e % 32, col = e / 32;
+        Ls[rr][col] = (rr < nr && col < nbk) ? F[i0 + rr + (int64_t)(kb0 + col) * ld] : mk<T>(0, 0);
+      }
+      for (int e = tid; e < 32 * RC; e += 256) {
+        int rr = e / RC, c2 = e % RC;
+        Xs[rr][c2] = (rr < nr && c2 < nc) ? Yf[(int64_t)(i0 + rr) * r + c0 + c2] : mk<T>(0, 0);
+      }
+      __syncthreads();
+      if (b < 32) {
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) acc = cfma(acc, Ls[rr][b], Xs[rr][cc]);
+      }
+      __syncthreads();
+    }
+    if (b < nbk && cc < nc) {
+      cx<T> z = zM[(st + kb0 + b) * r + c0 + cc];
+      z.re -= acc.re;
+      z.im -= acc.im;
+      v[b][cc] = z;
+    } else if (b < 32) {
+      v[b][cc] = mk<T>(0, 0);
+    }
+    // diagonal block of L (strict lower, 2x2 couplings excluded)
+    for (int e = tid; e < 32 * 32; e += 256) {
+      int a = e % 32, col = e / 32;
+      cx<T> val = mk<T>(0, 0);
+      if (a < nbk && col < nbk && a > col) {
+        val = F[kb0 + a + (int64_t)(kb0 + col) * ld];
+        if (a == col + 1 && ps[kb0 + col] == 2) val = mk<T>(0, 0);
+      }
+      Ls[a][col] = val;
+    }
+    __syncthreads();
+    for (int a = nbk - 1; a > 0; --a) {
+      if (b < a && cc < nc) v[b][cc] = cfms(v[b][cc], Ls[a][b], v[a][cc]);
+      __syncthreads();
+    }
+    if (b < nbk && cc < nc) {
+      Yf[(int64_t)(kb0 + b) * r + c0 + cc] = v[b][cc];
+      xM[(st + pv[kb0 + b]) * r + c0 + cc] = v[b][cc];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ edge-space kernels
+__global__ void k_cm_to_rm(const double2 *__restrict__ in, int64_t ld, double2 *__restrict__ out, int64_t n,
+                           int r) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / r;
+    int c = (int)(e % r);
+    out[e] = in[i + ld * c];
+  }
+}
+__global__ void k_rm_to_cm(const double2 *__restrict__ in, double2 *__restrict__ out, int64_t ld, int64_t n,
+                           int r, const uint8_t *__restrict__ pec) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / r;
+    int c = (int)(e % r);
+    out[i + ld * c] = pec[i] ? make_double2(0.0, 0.0) : in[e];
+  }
+}
+template <typename T>
+__global__ void k_scatter(const double2 *__restrict__ fe, const int64_t *__restrict__ owner, cx<T> *__restrict__ bM,
+                          int64_t n, int r) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / r;
+    int c = (int)(e % r);
+    int64_t v = owner[i];
+    if (v >= 0) bM[v * r + c] = from_d<T>(fe[e]);
+  }
+}
+// x_e (+)= xM[owner]
+template <typename T>
+__global__ void k_gather(const cx<T> *__restrict__ xM, const int64_t *__restrict__ owner, double2 *__restrict__ xe,
+                         int64_t n, int r, int accumulate) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / r;
+    int c = (int)(e % r);
+    int64_t v = owner[i];
+    double2 val = v >= 0 ? to_d(xM[v * r + c]) : make_double2(0.0, 0.0);
+    if (accumulate) {
+      double2 o = xe[e];
+      val.x += o.x;
+      val.y += o.y;
+    }
+    xe[e] = val;
+  }
+}
+template <typename T>
+__global__ void k_lambda_acc(const cx<T> *__restrict__ xM, int64_t lam0, int64_t nlm, int r, double2 *__restrict__ lam,
+                             int accumulate) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nlm * r; e += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = to_d(xM[lam0 * r + e]);
+    if (accumulate) {
+      v.x += lam[e].x;
+      v.y += lam[e].y;
+    }
+    lam[e] = v;
+  }
+}
+
+__device__ __forceinline__ void atomic_max_pos(double *addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// r = f - A x (fp64), per-column max |r| and max |f|; one warp per row
+__global__ void k_residual(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                           const double2 *__restrict__ val, const double2 *__restrict__ x,
+                           const double2 *__restrict__ f, double2 *__restrict__ res, int r,
+                           double *__restrict__ rnorm, double *__restrict__ fnorm) {
+  int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  int64_t a = ptr[row], b = ptr[row + 1];
+  for (int c = lane; c < r; c += 32) {
+    double2 acc = f[row * r + c];
+    double fm = fabs(acc.x) > 0 || fabs(acc.y) > 0 ? sqrt(acc.x * acc.x + acc.y * acc.y) : 0.0;
+    for (int64_t q = a; q < b; ++q) {
+      double2 av = val[q];
+      double2 xv = x[(int64_t)col[q] * r + c];
+      acc.x -= av.x * xv.x - av.y * xv.y;
+      acc.y -= av.x * xv.y + av.y * xv.x;
+    }
+    res[row * r + c] = acc;
+    if (a < b) {
+      atomic_max_pos(rnorm + c, sqrt(acc.x * acc.x + acc.y * acc.y));
+      atomic_max_pos(fnorm + c, fm);
+    }
+  }
+}
+
+// ------------------------------------------------------------ device state
+struct DeviceState {
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  // plan tables
+  int32_t *f_m = nullptr, *f_p = nullptr, *f_parent = nullptr;
+  int64_t *f_off = nullptr, *f_piv = nullptr, *f_soff = nullptr, *f_start = nullptr, *f_y = nullptr;
+  int32_t *lvl_fronts = nullptr, *ea_child = nullptr, *emap = nullptr;
+  int64_t *sidx = nullptr, *ent_off = nullptr, *wofs = nullptr, *owner = nullptr;
+  double2 *ent_val = nullptr;
+  // factors
+  void *arena = nullptr;
+  int32_t *perm = nullptr, *iperm = nullptr;
+  double2 *dinv_d = nullptr, *dinv_o = nullptr;
+  int8_t *psize = nullptr;
+  int32_t *st_k0 = nullptr, *st_kb = nullptr, *st_info = nullptr;
+  double *st_minpiv = nullptr;
+  void *W = nullptr;
+  // operator for residuals
+  int64_t *csr_ptr = nullptr;
+  int32_t *csr_col = nullptr;
+  double2 *csr_val = nullptr;
+  uint8_t *pec = nullptr;
+  // solve buffers (capacity in RHS)
+  int cap = 0;
+  void *bM = nullptr, *zM = nullptr, *xM = nullptr, *Y = nullptr;
+  double2 *fe = nullptr, *xe = nullptr, *re = nullptr, *ucm = nullptr, *lam = nullptr;
+  double *norms = nullptr;
+  // host launch data
+  std::vector<int64_t> w_level_base;  // per level: index of first front in wofs (== level_ptr)
+  std::vector<int> level_steps;
+  std::vector<std::vector<int>> update_grid;  // per level, per step: grid.x upper bound
+  std::vector<int> ea_grid;                   // per pass: grid.x (tiles) upper bound
+  std::vector<int> level_maxm, pass_maxn;
+  std::vector<void *> allocs;
+};
+
+template <class X>
+static cudaError_t dalloc(DeviceState *d, X **ptr, size_t count) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X));
+  if (e == cudaSuccess) {
+    d->allocs.push_back(p);
+    *ptr = (X *)p;
+  }
+  return e;
+}
+template <class X>
+static cudaError_t upload(DeviceState *d, X **ptr, const std::vector<X> &v) {
+  cudaError_t e = dalloc(d, ptr, v.size());
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*ptr, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice);
+  return e;
+}
+
+static FrontTab tab(const DeviceState *d) {
+  FrontTab t;
+  t.m = d->f_m;
+  t.p = d->f_p;
+  t.off = d->f_off;
+  t.piv = d->f_piv;
+  t.soff = d->f_soff;
+  t.start = d->f_start;
+  t.yoff = d->f_y;
+  t.parent = d->f_parent;
+  return t;
+}
+
+static int dev_init(Ctx &c) {
+  if (c.dev) return D3M_OK;
+  const Plan &P = c.plan;
+  DeviceState *d = new DeviceState();
+  c.dev = d;
+  d->precision = c.opt.precision;
+  d->stream = (cudaStream_t)c.opt.stream;
+  const int64_t nsn = (int64_t)P.sn_start.size();
+  std::vector<int32_t> m(nsn), pp(nsn), par(nsn);
+  std::vector<int64_t> soff(nsn);
+  for (int64_t s = 0; s < nsn; ++s) {
+    pp[s] = (int32_t)(P.sn_end[s] - P.sn_start[s]);
+    m[s] = pp[s] + (int32_t)(P.struct_ptr[s + 1] - P.struct_ptr[s]);
+    par[s] = (int32_t)P.parent[s];
+    soff[s] = P.struct_ptr[s];
+  }
+  CUDA_TRY(upload(d, &d->f_m, m));
+  CUDA_TRY(upload(d, &d->f_p, pp));
+  CUDA_TRY(upload(d, &d->f_parent, par));
+  CUDA_TRY(upload(d, &d->f_off, P.front_off));
+  CUDA_TRY(upload(d, &d->f_piv, P.piv_off));
+  CUDA_TRY(upload(d, &d->f_soff, soff));
+  CUDA_TRY(upload(d, &d->f_start, P.sn_start));
+  CUDA_TRY(upload(d, &d->f_y, P.y_off));
+  CUDA_TRY(upload(d, &d->lvl_fronts, P.level_fronts));
+  CUDA_TRY(upload(d, &d->ea_child, P.ea_child));
+  CUDA_TRY(upload(d, &d->emap, P.emap));
+  CUDA_TRY(upload(d, &d->sidx, P.struct_idx));
+  CUDA_TRY(upload(d, &d->ent_off, P.ent_off));
+  CUDA_TRY(upload(d, &d->owner, P.owner_m));
+  {
+    std::vector<double2> v(P.ent_val.size());
+    for (size_t i = 0; i < v.size(); ++i) v[i] = make_double2(P.ent_val[i].real(), P.ent_val[i].imag());
+    CUDA_TRY(upload(d, &d->ent_val, v));
+    std::vector<double2> cv(P.csr_val.size());
+    for (size_t i = 0; i < cv.size(); ++i) cv[i] = make_double2(P.csr_val[i].real(), P.csr_val[i].imag());
+    CUDA_TRY(upload(d, &d->csr_val, cv));
+  }
+  CUDA_TRY(upload(d, &d->csr_ptr, P.csr_ptr));
+  CUDA_TRY(upload(d, &d->csr_col, P.csr_col));
+  CUDA_TRY(upload(d, &d->pec, P.pec));
+  // W offsets: per level, fronts laid out one after the other (m x NB each)
+  std::vector<int64_t> wofs(nsn);
+  int64_t wmax = 0;
+  d->level_steps.assign(P.n_levels, 0);
+  d->update_grid.assign(P.n_levels, {});
+  d->level_maxm.assign(P.n_levels, 0);
+  for (int l = 0; l < P.n_levels; ++l) {
+    int64_t w = 0;
+    int steps = 0, maxm = 0;
+    for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+      int s = P.level_fronts[i];
+      wofs[i] = w;
+      w += (int64_t)m[s] * NB;
+      steps = std::max(steps, (pp[s] + NB - 2) / (NB - 1));
+      maxm = std::max(maxm, m[s]);
+    }
+    wmax = std::max(wmax, w);
+    d->level_steps[l] = steps;
+    d->level_maxm[l] = maxm;
+    for (int stp = 0; stp < steps; ++stp) {
+      int g = 0;
+      for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+        int s = P.level_fronts[i];
+        int cmin = std::min<int>(pp[s], (stp + 1) * (NB - 1));
+        int nt = (m[s] + UT - 1) / UT - cmin / UT;
+        g = std::max(g, nt * (nt + 1) / 2);
+      }
+      d->update_grid[l].push_back(std::max(g, 1));
+    }
+  }
+  CUDA_TRY(upload(d, &d->wofs, wofs));
+  const size_t esz = c.opt.precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
+  CUDA_TRY(cudaMalloc(&d->W, std::max<int64_t>(wmax, 1) * esz));
+  d->allocs.push_back(d->W);
+  CUDA_TRY(cudaMalloc(&d->arena, std::max<int64_t>(P.arena_elems, 1) * esz));
+  d->allocs.push_back(d->arena);
+  CUDA_TRY(dalloc(d, &d->perm, P.piv_total));
+  CUDA_TRY(dalloc(d, &d->iperm, P.piv_total));
+  CUDA_TRY(dalloc(d, &d->dinv_d, P.piv_total));
+  CUDA_TRY(dalloc(d, &d->dinv_o, P.piv_total));
+  CUDA_TRY(dalloc(d, &d->psize, P.piv_total));
+  CUDA_TRY(dalloc(d, &d->st_k0, nsn));
+  CUDA_TRY(dalloc(d, &d->st_kb, nsn));
+  CUDA_TRY(dalloc(d, &d->st_info, nsn));
+  CUDA_TRY(dalloc(d, &d->st_minpiv, nsn));
+  // extend-add grids
+  d->ea_grid.clear();
+  for (size_t q = 0; q + 1 < P.ea_ptr.size(); ++q) {
+    int g = 1;
+    for (int i = P.ea_ptr[q]; i < P.ea_ptr[q + 1]; ++i) {
+      int s = P.ea_child[i];
+      int n = m[s] - pp[s];
+      int nt = (n + 31) / 32;
+      g = std::max(g, nt * (nt + 1) / 2);
+    }
+    d->ea_grid.push_back(g);
+  }
+  return D3M_OK;
+}
+
+__global__ void k_init_perm(int64_t nsn, const int32_t *__restrict__ fp, const int64_t *__restrict__ fpiv,
+                            int32_t *__restrict__ perm) {
+  int64_t s = blockIdx.x;
+  if (s >= nsn) return;
+  for (int i = threadIdx.x; i < fp[s]; i += blockDim.x) perm[fpiv[s] + i] = i;
+}
+__global__ void k_iperm(int64_t nsn, const int32_t *__restrict__ fp, const int64_t *__restrict__ fpiv,
+                        const int32_t *__restrict__ perm, int32_t *__restrict__ iperm) {
+  int64_t s = blockIdx.x;
+  if (s >= nsn) return;
+  for (int i = threadIdx.x; i < fp[s]; i += blockDim.x) iperm[fpiv[s] + perm[fpiv[s] + i]] = i;
+}
+__global__ void k_fill_double(double *x, int64_t n, double v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+template <typename T>
+static int factor_t(Ctx &c) {
+  const Plan &P = c.plan;
+  DeviceState *d = c.dev;
+  cudaStream_t s = d->stream;
+  const int64_t nsn = (int64_t)P.sn_start.size();
+  cx<T> *arena = (cx<T> *)d->arena;
+  cx<T> *W = (cx<T> *)d->W;
+  FrontTab ft = tab(d);
+  CUDA_TRY(cudaMemsetAsync(d->st_k0, 0, nsn * sizeof(int32_t), s));
+  CUDA_TRY(cudaMemsetAsync(d->st_kb, 0, nsn * sizeof(int32_t), s));
+  CUDA_TRY(cudaMemsetAsync(d->st_info, 0, nsn * sizeof(int32_t), s));
+  k_fill_double<<<(unsigned)((nsn + 255) / 256), 256, 0, s>>>(d->st_minpiv, nsn, 1e300);
+  k_init_perm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm);
+  for (int l = 0; l < P.n_levels; ++l) {
+    const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
+    const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
+    // zero the level's fronts (contiguous) and assemble the entries of M
+    int64_t first = P.front_off[P.level_fronts[P.level_ptr[l]]];
+    int last_s = P.level_fronts[P.level_ptr[l + 1] - 1];
+    int64_t mlast = (P.sn_end[last_s] - P.sn_start[last_s]) + (P.struct_ptr[last_s + 1] - P.struct_ptr[last_s]);
+    int64_t end = P.front_off[last_s] + mlast * mlast;
+    CUDA_TRY(cudaMemsetAsync(arena + first, 0, (end - first) * sizeof(cx<T>), s));
+    int64_t ne = P.ent_ptr[l + 1] - P.ent_ptr[l];
+    if (ne > 0)
+      k_assemble<T><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(ne, d->ent_off + P.ent_ptr[l],
+                                                                  d->ent_val + P.ent_ptr[l], arena);
+    for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
+      int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
+      if (nk == 0) continue;
+      dim3 g(d->ea_grid[q], nk);
+      k_extend_add<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, arena);
+    }
+    const int64_t *wofs = d->wofs + P.level_ptr[l];
+    for (int stp = 0; stp < d->level_steps[l]; ++stp) {
+      k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, d->perm, d->dinv_d, d->dinv_o, d->psize,
+                                              d->st_k0, d->st_kb, d->st_info, d->st_minpiv);
+      dim3 g(d->update_grid[l][stp], nf);
+      k_update<T><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, d->st_k0, d->st_kb);
+    }
+  }
+  k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int32_t> info(nsn);
+  std::vector<double> mp(nsn);
+  CUDA_TRY(cudaMemcpy(info.data(), d->st_info, nsn * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(mp.data(), d->st_minpiv, nsn * sizeof(double), cudaMemcpyDeviceToHost));
+  std::vector<int8_t> ps(P.piv_total);
+  CUDA_TRY(cudaMemcpy(ps.data(), d->psize, P.piv_total, cudaMemcpyDeviceToHost));
+  int64_t n2 = 0;
+  for (int8_t v : ps) n2 += v == 2;
+  c.stats.n_2x2 = n2;
+  double mn = 1e300;
+  for (double v : mp) mn = std::min(mn, v);
+  c.stats.min_pivot_ratio = mn;
+  for (int64_t q = 0; q < nsn; ++q)
+    if (info[q] != 0) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "d3m_factor: zero pivot column %d in front %lld (kind %lld)", info[q] - 1,
+               (long long)q, (long long)P.sn_kind[q]);
+      c.err = buf;
+      return D3M_ESINGULAR;
+    }
+  return D3M_OK;
+}
+
+int dev_factor(Ctx &c) {
+  int rc = dev_init(c);
+  if (rc) return rc;
+  rc = c.opt.precision == D3M_FP64 ? factor_t<double>(c) : factor_t<float>(c);
+  c.factored = rc == D3M_OK;
+  return rc;
+}
+
+static int ensure_rhs(Ctx &c, int r) {
+  DeviceState *d = c.dev;
+  if (d->cap >= r) return D3M_OK;
+  const Plan &P = c.plan;
+  for (void *p : {d->bM, d->zM, d->xM, d->Y, (void *)d->fe, (void *)d->xe, (void *)d->re, (void *)d->ucm,
+                  (void *)d->lam, (void *)d->norms})
+    if (p) {
+      cudaFree(p);
+      d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), p), d->allocs.end());
+    }
+  const size_t esz = d->precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
+  auto A = [&](void **p, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) d->allocs.push_back(*p);
+    return e;
+  };
+  CUDA_TRY(A(&d->bM, P.n_m * r * esz));
+  CUDA_TRY(A(&d->zM, P.n_m * r * esz));
+  CUDA_TRY(A(&d->xM, P.n_m * r * esz));
+  CUDA_TRY(A(&d->Y, P.y_rows * r * esz));
+  CUDA_TRY(A((void **)&d->fe, P.n_edges * r * sizeof(double2)));
+  CUDA_TRY(A((void **)&d->xe, P.n_edges * r * sizeof(double2)));
+  CUDA_TRY(A((void **)&d->re, P.n_edges * r * sizeof(double2)));
+  CUDA_TRY(A((void **)&d->ucm, P.n_edges * r * sizeof(double2)));
+  CUDA_TRY(A((void **)&d->lam, (int64_t)P.lm_edge.size() * r * sizeof(double2)));
+  CUDA_TRY(A((void **)&d->norms, 2 * r * sizeof(double)));
+  d->cap = r;
+  return D3M_OK;
+}
+
+// One pass of the factored operator: xM = M^{-1} bM (in the factor precision)
+template <typename T>
+static void apply_inverse(Ctx &c, int r) {
+  const Plan &P = c.plan;
+  DeviceState *d = c.dev;
+  cudaStream_t s = d->stream;
+  FrontTab ft = tab(d);
+  cx<T> *arena = (cx<T> *)d->arena;
+  cx<T> *Y = (cx<T> *)d->Y;
+  constexpr int RC = sizeof(T) == 8 ? 8 : 8;
+  const int gx = (r + RC - 1) / RC;
+  for (int l = 0; l < P.n_levels; ++l) {
+    const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
+    const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
+    int64_t work = (int64_t)d->level_maxm[l] * r;
+    dim3 gi((unsigned)std::min<int64_t>((work + 255) / 256, 64), nf);
+    k_fwd_init<T><<<gi, 256, 0, s>>>(lvl, ft, d->perm, (const cx<T> *)d->bM, Y, r);
+    for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
+      int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
+      if (nk == 0) continue;
+      dim3 g((unsigned)std::min<int64_t>(((int64_t)d->level_maxm[l] * r + 255) / 256, 64), nk);
+      k_fwd_ea<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, d->iperm, Y, r);
+    }
+    dim3 gs(gx, nf);
+    k_fwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->dinv_d, d->dinv_o, d->psize, Y, (cx<T> *)d->zM, r);
+  }
+  for (int l = P.n_levels - 1; l >= 0; --l) {
+    const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
+    const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
+    dim3 gs(gx, nf);
+    k_bwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->perm, d->psize, d->sidx, Y, (const cx<T> *)d->zM,
+                                          (cx<T> *)d->xM, r);
+  }
+}
+
+static unsigned grid1(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+template <typename T>
+static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, int r,
+                   d3m_solve_info *info, bool host_ptrs) {
+  const Plan &P = c.plan;
+  DeviceState *d = c.dev;
+  cudaStream_t s = d->stream;
+  const int64_t n = P.n_edges;
+  const int64_t nlm = (int64_t)P.lm_edge.size();
+  const size_t esz = sizeof(cx<T>);
+  // user RHS -> row-major fp64 edge vector fe
+  if (host_ptrs) {
+    CUDA_TRY(cudaMemcpy2DAsync(d->ucm, n * sizeof(double2), rhs, ldb * sizeof(double2), n * sizeof(double2), r,
+                               cudaMemcpyHostToDevice, s));
+    k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>(d->ucm, n, d->fe, n, r);
+  } else {
+    k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>((const double2 *)rhs, ldb, d->fe, n, r);
+  }
+  // first solve from f
+  CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
+  k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->fe, d->owner, (cx<T> *)d->bM, n, r);
+  apply_inverse<T>(c, r);
+  k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 0);
+  if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 0);
+  std::vector<double> nh(2 * r);
+  int iters = 0;
+  double maxres = 0;
+  const bool refine = d->precision == D3M_MIXED;
+  for (;;) {
+    CUDA_TRY(cudaMemsetAsync(d->norms, 0, 2 * r * sizeof(double), s));
+    k_residual<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(n, d->csr_ptr, d->csr_col, d->csr_val, d->xe,
+                                                                 d->fe, d->re, r, d->norms, d->norms + r);
+    CUDA_TRY(cudaMemcpyAsync(nh.data(), d->norms, 2 * r * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    maxres = 0;
+    for (int q = 0; q < r; ++q) {
+      double rr = nh[r + q] > 0 ? nh[q] / nh[r + q] : nh[q];
+      if (info && info->resid) info->resid[q] = rr;
+      maxres = std::max(maxres, rr);
+    }
+    if (!refine || maxres <= c.opt.refine_tol || iters >= c.opt.max_refine) break;
+    // correction: solve with the residual, accumulate in fp64
+    CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
+    k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->re, d->owner, (cx<T> *)d->bM, n, r);
+    apply_inverse<T>(c, r);
+    k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 1);
+    if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 1);
+    ++iters;
+  }
+  if (host_ptrs) {
+    k_rm_to_cm<<<grid1(n * r), 256, 0, s>>>(d->xe, d->ucm, n, n, r, d->pec);
+    CUDA_TRY(cudaMemcpy2DAsync(x, ldx * sizeof(double2), d->ucm, n * sizeof(double2), n * sizeof(double2), r,
+                               cudaMemcpyDeviceToHost, s));
+  } else {
+    k_rm_to_cm<<<grid1(n * r), 256, 0, s>>>(d->xe, (double2 *)x, ldx, n, r, d->pec);
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->max_resid = maxres;
+  }
+  c.lambda_nrhs = 0;
+  if (refine && maxres > c.opt.refine_tol) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "d3m_solve: refinement stopped at residual %.3e after %d steps", maxres, iters);
+    c.err = buf;
+    return D3M_ENOCONV;
+  }
+  return D3M_OK;
+}
+
+int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, int nrhs, d3m_solve_info *info,
+              bool host_ptrs) {
+  if (!c.factored) {
+    c.err = "d3m_solve: call d3m_factor first";
+    return D3M_ESTATE;
+  }
+  int rc = ensure_rhs(c, nrhs);
+  if (rc) return rc;
+  rc = c.opt.precision == D3M_FP64 ? solve_t<double>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs)
+                                   : solve_t<float>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs);
+  // keep the multipliers for d3m_structure(D3M_LAMBDA)
+  const int64_t nlm = (int64_t)c.plan.lm_edge.size();
+  if (rc == D3M_OK || rc == D3M_ENOCONV) {
+    std::vector<double2> tmp(nlm * nrhs);
+    if (nlm) {
+      cudaError_t e = cudaMemcpy(tmp.data(), c.dev->lam, nlm * nrhs * sizeof(double2), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        c.err = cudaGetErrorString(e);
+        return D3M_ECUDA;
+      }
+    }
+    c.lambda_host.assign(nlm * nrhs, cplx(0));
+    for (int64_t l = 0; l < nlm; ++l)
+      for (int q = 0; q < nrhs; ++q) c.lambda_host[l + nlm * q] = cplx(tmp[l * nrhs + q].x, tmp[l * nrhs + q].y);
+    c.lambda_nrhs = nrhs;
+  }
+  return rc;
+}
+
+void dev_free(Ctx &c) {
+  if (!c.dev) return;
+  for (void *p : c.dev->allocs) cudaFree(p);
+  delete c.dev;
+  c.dev = nullptr;
+}
+
+// ------------------------------------------------------------ dense entry
+int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, int32_t *info, void *stream,
+               std::string &err) {
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> fm(batch, m), fp(batch, p), par(batch, -1), lvl(batch);
+  std::vector<int64_t> off(batch), piv(batch), wofs(batch), zero(batch, 0);
+  for (int b = 0; b < batch; ++b) {
+    lvl[b] = b;
+    off[b] = (int64_t)b * m * m;
+    piv[b] = (int64_t)b * p;
+    wofs[b] = (int64_t)b * m * NB;
+  }
+  DeviceState tmp;
+  Ctx c;  // for CUDA_TRY error text
+  auto fail = [&](int rc) {
+    for (void *q : tmp.allocs) cudaFree(q);
+    err = c.err;
+    return rc;
+  };
+#define DTRY(call)                                                       \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) {                                             \
+      c.err = std::string("CUDA error ") + cudaGetErrorString(e_);       \
+      return fail(D3M_ECUDA);                                            \
+    }                                                                    \
+  } while (0)
+  DTRY(upload(&tmp, &tmp.f_m, fm));
+  DTRY(upload(&tmp, &tmp.f_p, fp));
+  DTRY(upload(&tmp, &tmp.f_parent, par));
+  DTRY(upload(&tmp, &tmp.f_off, off));
+  DTRY(upload(&tmp, &tmp.f_piv, piv));
+  DTRY(upload(&tmp, &tmp.f_soff, zero));
+  DTRY(upload(&tmp, &tmp.f_start, zero));
+  DTRY(upload(&tmp, &tmp.f_y, zero));
+  DTRY(upload(&tmp, &tmp.lvl_fronts, lvl));
+  DTRY(upload(&tmp, &tmp.wofs, wofs));
+  cx<double> *W = nullptr;
+  DTRY(dalloc(&tmp, &W, (size_t)batch * m * NB));
+  int32_t *pv = nullptr, *k0 = nullptr, *kb = nullptr;
+  double2 *dd = nullptr, *dof = nullptr;
+  int8_t *ps = nullptr;
+  double *mp = nullptr;
+  DTRY(dalloc(&tmp, &pv, (size_t)batch * p));
+  DTRY(dalloc(&tmp, &dd, (size_t)batch * p));
+  DTRY(dalloc(&tmp, &dof, (size_t)batch * p));
+  DTRY(dalloc(&tmp, &ps, (size_t)batch * p));
+  DTRY(dalloc(&tmp, &k0, batch));
+  DTRY(dalloc(&tmp, &kb, batch));
+  DTRY(dalloc(&tmp, &mp, batch));
+  DTRY(cudaMemsetAsync(k0, 0, batch * sizeof(int32_t), s));
+  DTRY(cudaMemsetAsync(kb, 0, batch * sizeof(int32_t), s));
+  DTRY(cudaMemsetAsync(info, 0, batch * sizeof(int32_t), s));
+  k_fill_double<<<(batch + 255) / 256, 256, 0, s>>>(mp, batch, 1e300);
+  FrontTab ft = tab(&tmp);
+  k_init_perm<<<batch, 128, 0, s>>>(batch, tmp.f_p, tmp.f_piv, pv);
+  int steps = (p + NB - 2) / (NB - 1);
+  cx<double> *arena = (cx<double> *)A;
+  for (int stp = 0; stp < steps; ++stp) {
+    k_panel<double><<<batch, PANEL_THREADS, 0, s>>>(tmp.lvl_fronts, ft, tmp.wofs, arena, W, pv, dd, dof, ps, k0, kb,
+                                                    info, mp);
+    int cmin = std::min(p, (stp + 1) * (NB - 1));
+    int nt = (m + UT - 1) / UT - cmin / UT;
+    dim3 g(std::max(1, nt * (nt + 1) / 2), batch);
+    k_update<double><<<g, 256, 0, s>>>(tmp.lvl_fronts, ft, tmp.wofs, arena, W, k0, kb);
+  }
+  DTRY(cudaGetLastError());
+  DTRY(cudaStreamSynchronize(s));
+  // outputs
+  std::vector<int32_t> hp((size_t)batch * p), out((size_t)batch * m);
+  std::vector<double2> hd((size_t)batch * p), ho((size_t)batch * p);
+  std::vector<int8_t> hs((size_t)batch * p);
+  DTRY(cudaMemcpy(hp.data(), pv, hp.size() * 4, cudaMemcpyDeviceToHost));
+  DTRY(cudaMemcpy(hd.data(), dd, hd.size() * 16, cudaMemcpyDeviceToHost));
+  DTRY(cudaMemcpy(ho.data(), dof, ho.size() * 16, cudaMemcpyDeviceToHost));
+  DTRY(cudaMemcpy(hs.data(), ps, hs.size(), cudaMemcpyDeviceToHost));
+  std::vector<double> hdi((size_t)batch * p * 6);
+  for (int b = 0; b < batch; ++b) {
+    for (int i = 0; i < m; ++i) out[(size_t)b * m + i] = i < p ? hp[(size_t)b * p + i] : i;
+    for (int i = 0; i < p; ++i) {
+      size_t q = (size_t)b * p + i;
+      hdi[6 * q + 0] = hd[q].x;
+      hdi[6 * q + 1] = hd[q].y;
+      hdi[6 * q + 2] = ho[q].x;
+      hdi[6 * q + 3] = ho[q].y;
+      hdi[6 * q + 4] = hs[q];
+      hdi[6 * q + 5] = 0;
+    }
+  }
+  DTRY(cudaMemcpy(perm, out.data(), out.size() * 4, cudaMemcpyHostToDevice));
+  DTRY(cudaMemcpy(dinv, hdi.data(), hdi.size() * 8, cudaMemcpyHostToDevice));
+  for (void *q : tmp.allocs) cudaFree(q);
+  return D3M_OK;
+#undef DTRY
+}
+
+}  // namespace d3m
+
+// ============================================================ C ABI (device part)
+extern "C" int d3m_factor(d3m_ctx *h) {
+  if (!h) return D3M_EINVAL;
+  try {
+    return d3m::dev_factor(h->c);
+  } catch (const std::bad_alloc &) {
+    h->c.err = "d3m_factor: host allocation failed";
+    return D3M_ENOMEM;
+  }
+}
+
+extern "C" int d3m_solve(d3m_ctx *h, const double *rhs, int64_t ldb, double *x, int64_t ldx, int32_t nrhs,
+                         d3m_solve_info *info) {
+  if (!h || !rhs || !x || nrhs <= 0 || ldb < h->c.plan.n_edges || ldx < h->c.plan.n_edges) return D3M_EINVAL;
+  return d3m::dev_solve(h->c, rhs, ldb, x, ldx, nrhs, info, false);
+}
+
+extern "C" int d3m_solve_host(d3m_ctx *h, const double *rhs, int64_t ldb, double *x, int64_t ldx, int32_t nrhs,
+                              d3m_solve_info *info) {
+  if (!h || !rhs || !x || nrhs <= 0 || ldb < h->c.plan.n_edges || ldx < h->c.plan.n_edges) return D3M_EINVAL;
+  return d3m::dev_solve(h->c, rhs, ldb, x, ldx, nrhs, info, true);
+}
+
+extern "C" int d3m_export_front(d3m_ctx *h, int64_t front, int32_t *m_out, int32_t *p_out, double *F,
+                                int32_t *perm, double *dinv) {
+  if (!h || front < 0 || front >= (int64_t)h->c.plan.sn_start.size()) return D3M_EINVAL;
+  d3m::Ctx &c = h->c;
+  const d3m::Plan &P = c.plan;
+  int64_t p = P.sn_end[front] - P.sn_start[front];
+  int64_t m = p + P.struct_ptr[front + 1] - P.struct_ptr[front];
+  if (m_out) *m_out = (int32_t)m;
+  if (p_out) *p_out = (int32_t)p;
+  if (!F && !perm && !dinv) return D3M_OK;
+  if (!c.factored || !c.dev) {
+    c.err = "d3m_export_front: no factorisation";
+    return D3M_ESTATE;
+  }
+  d3m::DeviceState *d = c.dev;
+  cudaError_t e = cudaSuccess;
+  if (F) {
+    if (d->precision == D3M_FP64) {
+      e = cudaMemcpy(F, (d3m::cx<double> *)d->arena + P.front_off[front], m * m * 16, cudaMemcpyDeviceToHost);
+    } else {
+      std::vector<float> tmp(2 * m * m);
+      e = cudaMemcpy(tmp.data(), (d3m::cx<float> *)d->arena + P.front_off[front], m * m * 8, cudaMemcpyDeviceToHost);
+      for (int64_t i = 0; i < 2 * m * m; ++i) F[i] = tmp[i];
+    }
+  }
+  if (e == cudaSuccess && perm) e = cudaMemcpy(perm, d->perm + P.piv_off[front], p * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && dinv) {
+    std::vector<double2> dd(p), dof(p);
+    std::vector<int8_t> ps(p);
+    e = cudaMemcpy(dd.data(), d->dinv_d + P.piv_off[front], p * 16, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dof.data(), d->dinv_o + P.piv_off[front], p * 16, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(ps.data(), d->psize + P.piv_off[front], p, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i < p; ++i) {
+      dinv[6 * i] = dd[i].x;
+      dinv[6 * i + 1] = dd[i].y;
+      dinv[6 * i + 2] = dof[i].x;
+      dinv[6 * i + 3] = dof[i].y;
+      dinv[6 * i + 4] = ps[i];
+      dinv[6 * i + 5] = 0;
+    }
+  }
+  if (e != cudaSuccess) {
+    c.err = cudaGetErrorString(e);
+    return D3M_ECUDA;
+  }
+  return D3M_OK;
+}
+
+extern "C" int d3m_dense_ldlt(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm, double *dinv,
+                              int32_t *info, void *stream) {
+  if (m <= 0 || p < 0 || p > m || batch <= 0 || !A || !perm || !dinv || !info) return D3M_EINVAL;
+  std::string err;
+  int rc = d3m::dense_ldlt(m, p, batch, A, perm, dinv, info, stream, err);
+  if (rc) fprintf(stderr, "d3m_dense_ldlt: %s\n", err.c_str());
+  return rc;
+}

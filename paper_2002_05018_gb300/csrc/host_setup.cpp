@@ -1,0 +1,985 @@
+// Host-side set-up of the D^3M plan (no CUDA calls): discretisation of the
+// decomposed BVP (Theory section), the multiplier map D of Eq. (1), the
+// orderings of main step 3 and the symbolic factorisation of main step 4.
+// Everything here runs once per problem; the numeric work is in engine.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+#include <stdexcept>
+
+#include "d3m_internal.h"
+
+namespace d3m {
+
+// ------------------------------------------------------------ element algebra
+// 1-D integrals of the linear hat pair phi_0 = 1 - t, phi_1 = t on [0, 1]:
+// int phi_a phi_b = m1(a, b); phi_a' = sgn(a).
+static inline double m1(int a, int b) { return a == b ? 1.0 / 3.0 : 1.0 / 6.0; }
+static inline double sgn(int a) { return a ? 1.0 : -1.0; }
+static const int OFF[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
+
+// Closed-form stiffness int curl N_a . curl N_b and mass int N_a . N_b of the
+// 12 edge functions of a brick (x-edges (a,b): x^ phi_a(y) phi_b(z); y-edges:
+// y^ phi_a(x) phi_b(z); z-edges: z^ phi_a(x) phi_b(y)).
+void element_matrices(const double h[3], double S[12][12], double M[12][12]) {
+  const double hx = h[0], hy = h[1], hz = h[2], vol = hx * hy * hz;
+  std::memset(S, 0, sizeof(double) * 144);
+  std::memset(M, 0, sizeof(double) * 144);
+  // second derivative scale per family: (first curl term axis, second term axis)
+  const double dA[3] = {hz, hz, hy};  // term with m_aa' s_b s_b'
+  const double dB[3] = {hy, hx, hx};  // term with s_a s_a' m_bb'
+  for (int f = 0; f < 3; ++f)
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        int a = OFF[i][0], b = OFF[i][1], a2 = OFF[j][0], b2 = OFF[j][1];
+        M[4 * f + i][4 * f + j] = vol * m1(a, a2) * m1(b, b2);
+        S[4 * f + i][4 * f + j] = vol * (m1(a, a2) * sgn(b) * sgn(b2) / (dA[f] * dA[f]) +
+                                         sgn(a) * sgn(a2) * m1(b, b2) / (dB[f] * dB[f]));
+      }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int a = OFF[i][0], b = OFF[i][1], a2 = OFF[j][0], b2 = OFF[j][1];
+      double xy = -sgn(a) * sgn(a2) * m1(b, b2) * vol / (hx * hy);
+      double xz = -sgn(b) * sgn(a2) * m1(a, b2) * vol / (hz * hx);
+      double yz = -sgn(b) * sgn(b2) * m1(a, a2) * vol / (hz * hy);
+      S[i][4 + j] = S[4 + j][i] = xy;
+      S[i][8 + j] = S[8 + j][i] = xz;
+      S[4 + i][8 + j] = S[8 + j][4 + i] = yz;
+    }
+}
+
+// Tangential face mass int_face N_t . N_t dS on face {axis = side}.
+void face_matrix(const double h[3], int axis, int side, double T[12][12]) {
+  std::memset(T, 0, sizeof(double) * 144);
+  const double hx = h[0], hy = h[1], hz = h[2];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int a = OFF[i][0], b = OFF[i][1], a2 = OFF[j][0], b2 = OFF[j][1];
+      if (axis == 2) {  // x-edges and y-edges with z-offset == side
+        if (b == side && b2 == side) {
+          T[i][j] = hx * hy * m1(a, a2);
+          T[4 + i][4 + j] = hx * hy * m1(a, a2);
+        }
+      } else if (axis == 1) {  // x-edges with y-offset == side, z-edges with y-offset == side
+        if (a == side && a2 == side) T[i][j] = hx * hz * m1(b, b2);
+        if (b == side && b2 == side) T[8 + i][8 + j] = hx * hz * m1(a, a2);
+      } else {  // y-edges and z-edges with x-offset == side
+        if (a == side && a2 == side) {
+          T[4 + i][4 + j] = hy * hz * m1(b, b2);
+          T[8 + i][8 + j] = hy * hz * m1(b, b2);
+        }
+      }
+    }
+}
+
+static inline int64_t EX(const Plan &p, int64_t i, int64_t j, int64_t k) {
+  return i + p.nx * (j + (int64_t)(p.ny + 1) * k);
+}
+static inline int64_t EY(const Plan &p, int64_t i, int64_t j, int64_t k) {
+  return p.nex + i + (int64_t)(p.nx + 1) * (j + (int64_t)p.ny * k);
+}
+static inline int64_t EZ(const Plan &p, int64_t i, int64_t j, int64_t k) {
+  return p.nex + p.ney + i + (int64_t)(p.nx + 1) * (j + (int64_t)(p.ny + 1) * k);
+}
+
+void cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[12]) {
+  for (int q = 0; q < 4; ++q) {
+    int a = OFF[q][0], b = OFF[q][1];
+    e[q] = EX(p, ci, cj + a, ck + b);
+    e[4 + q] = EY(p, ci + a, cj, ck + b);
+    e[8 + q] = EZ(p, ci + a, cj + b, ck);
+  }
+}
+
+// direction and start node of an edge
+static inline void edge_info(const Plan &p, int64_t e, int &d, int64_t &i, int64_t &j,
+                             int64_t &k) {
+  if (e < p.nex) {
+    d = 0;
+    i = e % p.nx;
+    int64_t r = e / p.nx;
+    j = r % (p.ny + 1);
+    k = r / (p.ny + 1);
+  } else if (e < p.nex + p.ney) {
+    d = 1;
+    int64_t q = e - p.nex;
+    i = q % (p.nx + 1);
+    int64_t r = q / (p.nx + 1);
+    j = r % p.ny;
+    k = r / p.ny;
+  } else {
+    d = 2;
+    int64_t q = e - p.nex - p.ney;
+    i = q % (p.nx + 1);
+    int64_t r = q / (p.nx + 1);
+    j = r % (p.ny + 1);
+    k = r / (p.ny + 1);
+  }
+}
+
+// All edges of the cells in box [lo, hi), increasing global id.
+template <class F>
+static void for_box_edges(const Plan &p, const int lo[3], const int hi[3], F &&fn) {
+  for (int64_t k = lo[2]; k <= hi[2]; ++k)
+    for (int64_t j = lo[1]; j <= hi[1]; ++j)
+      for (int64_t i = lo[0]; i < hi[0]; ++i) fn(EX(p, i, j, k));
+  for (int64_t k = lo[2]; k <= hi[2]; ++k)
+    for (int64_t j = lo[1]; j < hi[1]; ++j)
+      for (int64_t i = lo[0]; i <= hi[0]; ++i) fn(EY(p, i, j, k));
+  for (int64_t k = lo[2]; k < hi[2]; ++k)
+    for (int64_t j = lo[1]; j <= hi[1]; ++j)
+      for (int64_t i = lo[0]; i <= hi[0]; ++i) fn(EZ(p, i, j, k));
+}
+
+static inline int sub_id(const Plan &p, int x, int y, int z) {
+  return x + p.parts[0] * (y + p.parts[1] * z);
+}
+static inline void sub_pos(const Plan &p, int s, int pos[3]) {
+  pos[0] = s % p.parts[0];
+  pos[1] = (s / p.parts[0]) % p.parts[1];
+  pos[2] = s / (p.parts[0] * p.parts[1]);
+}
+static bool face_adj(const Plan &p, int a, int b) {
+  int pa[3], pb[3];
+  sub_pos(p, a, pa);
+  sub_pos(p, b, pb);
+  int diff = 0, tot = 0;
+  for (int q = 0; q < 3; ++q) {
+    int d = std::abs(pa[q] - pb[q]);
+    tot += d;
+    diff += d != 0;
+  }
+  return tot == 1 && diff == 1;
+}
+
+// ------------------------------------------------------------ orderings
+// Block nested dissection of the subdomain grid (main step 3 reading).
+static void block_nd(const Plan &p, const std::set<std::pair<int, int>> &pairs, int lo[3],
+                     int hi[3], std::vector<std::pair<int, int>> &out) {
+  int ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+  int axis = 0;
+  for (int q = 1; q < 3; ++q)
+    if (ext[q] > ext[axis]) axis = q;
+  if (ext[axis] <= 1) return;
+  int mid = lo[axis] + ext[axis] / 2;
+  std::vector<std::pair<int, int>> sep;
+  int r0[3] = {lo[0], lo[1], lo[2]}, r1[3] = {hi[0], hi[1], hi[2]};
+  r0[axis] = mid - 1;
+  r1[axis] = mid;
+  for (int z = r0[2]; z < r1[2]; ++z)
+    for (int y = r0[1]; y < r1[1]; ++y)
+      for (int x = r0[0]; x < r1[0]; ++x) {
+        int q[3] = {x, y, z};
+        int a = sub_id(p, q[0], q[1], q[2]);
+        q[axis] += 1;
+        int b = sub_id(p, q[0], q[1], q[2]);
+        if (pairs.count({a, b})) sep.push_back({a, b});
+      }
+  int lhi[3] = {hi[0], hi[1], hi[2]}, rlo[3] = {lo[0], lo[1], lo[2]};
+  lhi[axis] = mid;
+  rlo[axis] = mid;
+  block_nd(p, pairs, lo, lhi, out);
+  block_nd(p, pairs, rlo, hi, out);
+  std::sort(sep.begin(), sep.end());
+  out.insert(out.end(), sep.begin(), sep.end());
+}
+
+// Geometric nested dissection of a subdomain's non-interface edges.
+static void sub_nd(const Plan &p, std::vector<char> &avail, const int lo[3], const int hi[3],
+                   int leaf_max, std::vector<std::vector<int64_t>> &nodes) {
+  std::vector<int64_t> E;
+  for_box_edges(p, lo, hi, [&](int64_t e) {
+    if (avail[e]) E.push_back(e);
+  });
+  int ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+  int axis = 0;
+  for (int q = 1; q < 3; ++q)
+    if (ext[q] > ext[axis]) axis = q;
+  if ((int64_t)E.size() <= leaf_max || ext[axis] < 2) {
+    if (!E.empty()) {
+      for (int64_t e : E) avail[e] = 0;
+      std::sort(E.begin(), E.end());
+      nodes.push_back(std::move(E));
+    }
+    return;
+  }
+  int c = lo[axis] + ext[axis] / 2;
+  std::vector<int64_t> sep;
+  for (int64_t e : E) {
+    int d;
+    int64_t ijk[3];
+    edge_info(p, e, d, ijk[0], ijk[1], ijk[2]);
+    if (d != axis && ijk[axis] == c) sep.push_back(e);
+  }
+  for (int64_t e : sep) avail[e] = 0;
+  int lhi[3] = {hi[0], hi[1], hi[2]}, rlo[3] = {lo[0], lo[1], lo[2]};
+  lhi[axis] = c;
+  rlo[axis] = c;
+  sub_nd(p, avail, lo, lhi, leaf_max, nodes);
+  sub_nd(p, avail, rlo, hi, leaf_max, nodes);
+  if (!sep.empty()) {
+    std::sort(sep.begin(), sep.end());
+    nodes.push_back(std::move(sep));
+  }
+}
+
+// ------------------------------------------------------------ assembly helpers
+struct Trip {
+  int64_t r, c;
+  cplx v;
+};
+
+// Which subdomain interval(s) along one axis contain node coordinate x
+// (closed intervals) -- 1 or 2 results; cell-interval for an along-edge axis.
+static int node_intervals(const std::vector<int> &cut, int64_t x, int out[2]) {
+  int n = (int)cut.size() - 1;
+  int cnt = 0;
+  for (int q = 0; q < n; ++q)
+    if (cut[q] <= x && x <= cut[q + 1]) out[cnt++] = q;
+  return cnt;
+}
+static int cell_interval(const std::vector<int> &cut, int64_t x) {
+  int n = (int)cut.size() - 1;
+  for (int q = 0; q < n; ++q)
+    if (cut[q] <= x && x < cut[q + 1]) return q;
+  return -1;
+}
+
+// ------------------------------------------------------------ build
+int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double k,
+               const d3m_partition *part) {
+  Plan &p = ctx.plan;
+  const int leaf_max = ctx.opt.leaf_max > 0 ? ctx.opt.leaf_max : 64;
+  p.nx = mesh->nx;
+  p.ny = mesh->ny;
+  p.nz = mesh->nz;
+  p.lx = mesh->lx;
+  p.ly = mesh->ly;
+  p.lz = mesh->lz;
+  p.k = k;
+  if (p.nx < 1 || p.ny < 1 || p.nz < 1 || !(p.lx > 0) || !(p.ly > 0) || !(p.lz > 0)) {
+    ctx.err = "d3m_setup: mesh sizes must be positive";
+    return D3M_EINVAL;
+  }
+  p.h[0] = p.lx / p.nx;
+  p.h[1] = p.ly / p.ny;
+  p.h[2] = p.lz / p.nz;
+  p.nex = (int64_t)p.nx * (p.ny + 1) * (p.nz + 1);
+  p.ney = (int64_t)(p.nx + 1) * p.ny * (p.nz + 1);
+  p.nez = (int64_t)(p.nx + 1) * (p.ny + 1) * p.nz;
+  p.n_edges = p.nex + p.ney + p.nez;
+  const int64_t ncell = (int64_t)p.nx * p.ny * p.nz;
+  if (!mat || !mat->eps_r) {
+    ctx.err = "d3m_setup: eps_r is required";
+    return D3M_EINVAL;
+  }
+  p.eps.resize(ncell);
+  for (int64_t c = 0; c < ncell; ++c) p.eps[c] = cplx(mat->eps_r[2 * c], mat->eps_r[2 * c + 1]);
+  p.pec.assign(p.n_edges, 0);
+  if (mat->pec_edge)
+    for (int64_t e = 0; e < p.n_edges; ++e) p.pec[e] = mat->pec_edge[e] ? 1 : 0;
+  p.parts[0] = part->px;
+  p.parts[1] = part->py;
+  p.parts[2] = part->pz;
+  const int32_t *cp[3] = {part->cx, part->cy, part->cz};
+  const int nn[3] = {p.nx, p.ny, p.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (p.parts[a] < 1 || !cp[a]) {
+      ctx.err = "d3m_setup: partition counts must be >= 1 with cut arrays";
+      return D3M_EINVAL;
+    }
+    p.cuts[a].assign(cp[a], cp[a] + p.parts[a] + 1);
+    if (p.cuts[a].front() != 0 || p.cuts[a].back() != nn[a]) {
+      ctx.err = "d3m_setup: cuts must start at 0 and end at the cell count";
+      return D3M_EINVAL;
+    }
+    for (int q = 0; q < p.parts[a]; ++q)
+      if (p.cuts[a][q + 1] <= p.cuts[a][q]) {
+        ctx.err = "d3m_setup: cuts must be strictly increasing";
+        return D3M_EINVAL;
+      }
+  }
+  p.nsub = p.parts[0] * p.parts[1] * p.parts[2];
+  p.n_free = 0;
+  for (int64_t e = 0; e < p.n_edges; ++e) p.n_free += !p.pec[e];
+
+  // ---- subdomain boxes and edges
+  p.sub_lo.resize(p.nsub);
+  p.sub_hi.resize(p.nsub);
+  p.sub_edges.assign(p.nsub, {});
+  for (int s = 0; s < p.nsub; ++s) {
+    int pos[3];
+    sub_pos(p, s, pos);
+    for (int a = 0; a < 3; ++a) {
+      p.sub_lo[s][a] = p.cuts[a][pos[a]];
+      p.sub_hi[s][a] = p.cuts[a][pos[a] + 1];
+    }
+    for_box_edges(p, p.sub_lo[s].data(), p.sub_hi[s].data(), [&](int64_t e) {
+      if (!p.pec[e]) p.sub_edges[s].push_back(e);
+    });
+  }
+
+  // ---- copies of each edge (sorted subdomain lists) and multipliers
+  // copies are only needed for edges on interior cut planes
+  std::vector<int> ncopy(p.n_edges, 0);
+  std::vector<std::array<int, 4>> copies(p.n_edges);
+  for (int64_t e = 0; e < p.n_edges; ++e) {
+    if (p.pec[e]) continue;
+    int d;
+    int64_t ijk[3];
+    edge_info(p, e, d, ijk[0], ijk[1], ijk[2]);
+    int iv[3][2], cnt[3];
+    for (int a = 0; a < 3; ++a) {
+      if (a == d) {
+        iv[a][0] = cell_interval(p.cuts[a], ijk[a]);
+        cnt[a] = 1;
+      } else {
+        cnt[a] = node_intervals(p.cuts[a], ijk[a], iv[a]);
+      }
+    }
+    std::vector<int> lst;
+    for (int z = 0; z < cnt[2]; ++z)
+      for (int y = 0; y < cnt[1]; ++y)
+        for (int x = 0; x < cnt[0]; ++x) lst.push_back(sub_id(p, iv[0][x], iv[1][y], iv[2][z]));
+    std::sort(lst.begin(), lst.end());
+    ncopy[e] = (int)lst.size();
+    for (size_t q = 0; q < lst.size(); ++q) copies[e][q] = lst[q];
+  }
+  std::map<std::pair<int, int>, std::vector<int64_t>> pair_edges;
+  for (int64_t e = 0; e < p.n_edges; ++e) {
+    for (int kk = 1; kk < ncopy[e]; ++kk) {
+      int sk = copies[e][kk], sj = -1;
+      for (int j = 0; j < kk; ++j)
+        if (face_adj(p, copies[e][j], sk)) {
+          sj = copies[e][j];
+          break;
+        }
+      if (sj < 0) {
+        ctx.err = "d3m_setup: internal error (copy without face neighbour)";
+        return D3M_EINVAL;
+      }
+      pair_edges[{sj, sk}].push_back(e);
+    }
+  }
+  std::set<std::pair<int, int>> pairs;
+  for (auto &kv : pair_edges) pairs.insert(kv.first);
+  std::vector<std::pair<int, int>> border;
+  {
+    int lo[3] = {0, 0, 0}, hi[3] = {p.parts[0], p.parts[1], p.parts[2]};
+    block_nd(p, pairs, lo, hi, border);
+  }
+  p.lm_edge.clear();
+  p.lm_plus.clear();
+  p.lm_minus.clear();
+  p.blocks.clear();
+  for (auto &ab : border) {
+    auto &es = pair_edges[ab];  // already increasing
+    p.blocks.push_back({ab.first, ab.second, (int64_t)p.lm_edge.size()});
+    for (int64_t e : es) {
+      p.lm_edge.push_back(e);
+      p.lm_plus.push_back(ab.first);
+      p.lm_minus.push_back(ab.second);
+    }
+  }
+  const int64_t n_lm = (int64_t)p.lm_edge.size();
+
+  // ---- M ordering and supernodes
+  p.m_sub.clear();
+  p.m_edge.clear();
+  p.sn_start.clear();
+  p.sn_end.clear();
+  p.sn_kind.clear();
+  p.sn_owner.clear();
+  std::vector<char> avail(p.n_edges, 0);
+  std::vector<int64_t> sub_m0(p.nsub);  // first M index of each subdomain
+  std::vector<std::vector<int64_t>> sub_mindex(p.nsub);  // M index of each local edge
+  for (int s = 0; s < p.nsub; ++s) {
+    sub_m0[s] = (int64_t)p.m_sub.size();
+    for (int64_t e : p.sub_edges[s]) avail[e] = ncopy[e] < 2;  // interface dofs excluded
+    std::vector<std::vector<int64_t>> nodes;
+    sub_nd(p, avail, p.sub_lo[s].data(), p.sub_hi[s].data(), leaf_max, nodes);
+    for (auto &nd : nodes) {
+      p.sn_start.push_back((int64_t)p.m_sub.size());
+      for (int64_t e : nd) {
+        p.m_sub.push_back(s);
+        p.m_edge.push_back(e);
+      }
+      p.sn_end.push_back((int64_t)p.m_sub.size());
+      p.sn_kind.push_back(0);
+      p.sn_owner.push_back(s);
+    }
+    for (int64_t e : p.sub_edges[s]) avail[e] = 0;
+    std::vector<int64_t> B;
+    for (int64_t e : p.sub_edges[s])
+      if (ncopy[e] >= 2) B.push_back(e);
+    if (!B.empty()) {
+      p.sn_start.push_back((int64_t)p.m_sub.size());
+      for (int64_t e : B) {
+        p.m_sub.push_back(s);
+        p.m_edge.push_back(e);
+      }
+      p.sn_end.push_back((int64_t)p.m_sub.size());
+      p.sn_kind.push_back(1);
+      p.sn_owner.push_back(s);
+    }
+  }
+  p.lam_start = (int64_t)p.m_sub.size();
+  for (size_t b = 0; b < p.blocks.size(); ++b) {
+    int64_t first = p.blocks[b][2];
+    int64_t last = b + 1 < p.blocks.size() ? p.blocks[b + 1][2] : n_lm;
+    p.sn_start.push_back((int64_t)p.m_sub.size());
+    for (int64_t l = first; l < last; ++l) {
+      p.m_sub.push_back(-1);
+      p.m_edge.push_back(l);
+    }
+    p.sn_end.push_back((int64_t)p.m_sub.size());
+    p.sn_kind.push_back(2);
+    p.sn_owner.push_back((int64_t)b);
+  }
+  p.n_m = (int64_t)p.m_sub.size();
+  const int64_t nsn = (int64_t)p.sn_start.size();
+  std::vector<int64_t> sn_of(p.n_m);
+  for (int64_t s = 0; s < nsn; ++s)
+    for (int64_t v = p.sn_start[s]; v < p.sn_end[s]; ++v) sn_of[v] = s;
+
+  // per subdomain: global edge -> M index (dense scratch reused)
+  std::vector<int64_t> gm(p.n_edges, -1);
+  p.owner_m.assign(p.n_edges, -1);
+  for (int64_t v = 0; v < p.lam_start; ++v) {
+    int64_t e = p.m_edge[v];
+    int s = (int)p.m_sub[v];
+    if (ncopy[e] >= 1 && copies[e][0] == s) p.owner_m[e] = v;
+  }
+
+  // ---- entries of M (lower triangle), per subdomain
+  double S[12][12], Me[12][12], T[6][12][12];
+  element_matrices(p.h, S, Me);
+  for (int axis = 0; axis < 3; ++axis)
+    for (int side = 0; side < 2; ++side) face_matrix(p.h, axis, side, T[2 * axis + side]);
+  const cplx jk(0.0, k);
+  std::vector<Trip> trips;
+  for (int s = 0; s < p.nsub; ++s) {
+    int64_t m0 = sub_m0[s];
+    int64_t m1_ = s + 1 < p.nsub ? sub_m0[s + 1] : p.lam_start;
+    for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = v;
+    auto add_block = [&](const int64_t e[12], const double (*X)[12], cplx coef) {
+      for (int a = 0; a < 12; ++a) {
+        int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
+        if (ra < 0) continue;
+        for (int b = 0; b < 12; ++b) {
+          if (X[a][b] == 0.0) continue;
+          int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
+          if (rb < 0 || ra < rb) continue;
+          trips.push_back({ra, rb, coef * X[a][b]});
+        }
+      }
+    };
+    const auto &lo = p.sub_lo[s];
+    const auto &hi = p.sub_hi[s];
+    int pos[3];
+    sub_pos(p, s, pos);
+    for (int ck = lo[2]; ck < hi[2]; ++ck)
+      for (int cj = lo[1]; cj < hi[1]; ++cj)
+        for (int ci = lo[0]; ci < hi[0]; ++ci) {
+          int64_t e[12];
+          cell_edges(p, ci, cj, ck, e);
+          cplx eps = p.eps[ci + (int64_t)p.nx * (cj + (int64_t)p.ny * ck)];
+          for (int a = 0; a < 12; ++a) {
+            int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
+            if (ra < 0) continue;
+            for (int b = 0; b < 12; ++b) {
+              int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
+              if (rb < 0 || ra < rb) continue;
+              cplx v = S[a][b] - k * k * eps * Me[a][b];
+              if (v != cplx(0.0)) trips.push_back({ra, rb, v});
+            }
+          }
+          int c3[3] = {ci, cj, ck};
+          for (int axis = 0; axis < 3; ++axis)
+            for (int side = 0; side < 2; ++side) {
+              int layer = side ? hi[axis] - 1 : lo[axis];
+              if (c3[axis] != layer) continue;
+              int node = side ? hi[axis] : lo[axis];
+              if (node == 0 || node == nn[axis]) {
+                add_block(e, T[2 * axis + side], jk);  // first-order ABC
+              } else {
+                int npos[3] = {pos[0], pos[1], pos[2]};
+                npos[axis] += side ? 1 : -1;
+                int nb = sub_id(p, npos[0], npos[1], npos[2]);
+                add_block(e, T[2 * axis + side], nb > s ? jk : -jk);  // interface loss / gain
+              }
+            }
+        }
+    for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = -1;
+  }
+  // multiplier couplings (+1 on the lower-index copy, -1 on the other)
+  {
+    // M index of copy (s, e): binary search in the subdomain's M range is
+    // avoided with a per-subdomain scratch pass
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> by_sub(p.nsub);  // (edge, lm)
+    for (int64_t l = 0; l < n_lm; ++l) {
+      by_sub[p.lm_plus[l]].push_back({p.lm_edge[l], l});
+      by_sub[p.lm_minus[l]].push_back({p.lm_edge[l], ~l});
+    }
+    for (int s = 0; s < p.nsub; ++s) {
+      int64_t m0 = sub_m0[s];
+      int64_t m1_ = s + 1 < p.nsub ? sub_m0[s + 1] : p.lam_start;
+      for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = v;
+      for (auto &q : by_sub[s]) {
+        int64_t l = q.second >= 0 ? q.second : ~q.second;
+        double sign = q.second >= 0 ? 1.0 : -1.0;
+        trips.push_back({p.lam_start + l, gm[q.first], cplx(sign, 0.0)});
+      }
+      for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = -1;
+    }
+  }
+  std::sort(trips.begin(), trips.end(), [](const Trip &a, const Trip &b) {
+    return a.c != b.c ? a.c < b.c : a.r < b.r;
+  });
+  {
+    size_t w = 0;
+    for (size_t i = 0; i < trips.size(); ++i) {
+      if (w > 0 && trips[w - 1].r == trips[i].r && trips[w - 1].c == trips[i].c)
+        trips[w - 1].v += trips[i].v;
+      else
+        trips[w++] = trips[i];
+    }
+    trips.resize(w);
+  }
+  std::vector<int64_t> col_ptr(p.n_m + 1, 0);
+  for (auto &t : trips) col_ptr[t.c + 1]++;
+  for (int64_t c = 0; c < p.n_m; ++c) col_ptr[c + 1] += col_ptr[c];
+
+  // ---- supernodal symbolic factorisation (child-merge)
+  p.parent.assign(nsn, -1);
+  std::vector<std::vector<int64_t>> children(nsn), st(nsn);
+  std::vector<int64_t> mark(p.n_m, -1);
+  for (int64_t s = 0; s < nsn; ++s) {
+    int64_t a = p.sn_start[s], b = p.sn_end[s];
+    auto &L = st[s];
+    for (int64_t c = a; c < b; ++c)
+      for (int64_t q = col_ptr[c]; q < col_ptr[c + 1]; ++q) {
+        int64_t r = trips[q].r;
+        if (r >= b && mark[r] != s) {
+          mark[r] = s;
+          L.push_back(r);
+        }
+      }
+    for (int64_t ch : children[s])
+      for (int64_t r : st[ch])
+        if (r >= b && mark[r] != s) {
+          mark[r] = s;
+          L.push_back(r);
+        }
+    std::sort(L.begin(), L.end());
+    if (!L.empty()) {
+      p.parent[s] = sn_of[L[0]];
+      children[p.parent[s]].push_back(s);
+    }
+  }
+  p.struct_ptr.assign(nsn + 1, 0);
+  for (int64_t s = 0; s < nsn; ++s) p.struct_ptr[s + 1] = p.struct_ptr[s] + (int64_t)st[s].size();
+  p.struct_idx.resize(p.struct_ptr[nsn]);
+  for (int64_t s = 0; s < nsn; ++s)
+    std::copy(st[s].begin(), st[s].end(), p.struct_idx.begin() + p.struct_ptr[s]);
+
+  // ---- extend-add maps, child ranks, levels
+  p.emap.assign(p.struct_idx.size(), -1);
+  p.child_rank.assign(nsn, -1);
+  p.level.assign(nsn, 0);
+  for (int64_t s = 0; s < nsn; ++s) {
+    int64_t q = p.parent[s];
+    if (q < 0) continue;
+    int64_t pq = p.sn_end[q] - p.sn_start[q];
+    const int64_t *qs = p.struct_idx.data() + p.struct_ptr[q];
+    int64_t nq = p.struct_ptr[q + 1] - p.struct_ptr[q];
+    for (int64_t t = p.struct_ptr[s]; t < p.struct_ptr[s + 1]; ++t) {
+      int64_t v = p.struct_idx[t];
+      int64_t loc;
+      if (v < p.sn_end[q]) {
+        loc = v - p.sn_start[q];
+      } else {
+        const int64_t *it = std::lower_bound(qs, qs + nq, v);
+        if (it == qs + nq || *it != v) {
+          ctx.err = "d3m_setup: internal error (child row missing in parent front)";
+          return D3M_EINVAL;
+        }
+        loc = pq + (it - qs);
+      }
+      p.emap[t] = (int32_t)loc;
+    }
+  }
+  for (int64_t s = 0; s < nsn; ++s) {
+    for (size_t r = 0; r < children[s].size(); ++r) p.child_rank[children[s][r]] = (int32_t)r;
+    int lv = 0;
+    for (int64_t ch : children[s]) lv = std::max(lv, p.level[ch] + 1);
+    p.level[s] = lv;
+  }
+  p.n_levels = 0;
+  for (int64_t s = 0; s < nsn; ++s) p.n_levels = std::max(p.n_levels, p.level[s] + 1);
+  p.level_ptr.assign(p.n_levels + 1, 0);
+  for (int64_t s = 0; s < nsn; ++s) p.level_ptr[p.level[s] + 1]++;
+  for (int l = 0; l < p.n_levels; ++l) p.level_ptr[l + 1] += p.level_ptr[l];
+  p.level_fronts.resize(nsn);
+  {
+    std::vector<int32_t> fill(p.level_ptr.begin(), p.level_ptr.end() - 1);
+    for (int64_t s = 0; s < nsn; ++s) p.level_fronts[fill[p.level[s]]++] = (int32_t)s;
+  }
+  // extend-add passes: pass r of level l adds the r-th child of each front
+  p.ea_pass_ptr.assign(p.n_levels + 1, 0);
+  p.ea_ptr.assign(1, 0);
+  p.ea_child.clear();
+  for (int l = 0; l < p.n_levels; ++l) {
+    size_t maxc = 0;
+    for (int i = p.level_ptr[l]; i < p.level_ptr[l + 1]; ++i)
+      maxc = std::max(maxc, children[p.level_fronts[i]].size());
+    for (size_t r = 0; r < maxc; ++r) {
+      for (int i = p.level_ptr[l]; i < p.level_ptr[l + 1]; ++i) {
+        auto &ch = children[p.level_fronts[i]];
+        if (r < ch.size()) p.ea_child.push_back((int32_t)ch[r]);
+      }
+      p.ea_ptr.push_back((int32_t)p.ea_child.size());
+    }
+    p.ea_pass_ptr[l + 1] = (int32_t)p.ea_ptr.size() - 1;
+  }
+
+  // ---- arena layout (level-major, so a level's fronts are contiguous)
+  p.front_off.assign(nsn, 0);
+  p.piv_off.assign(nsn, 0);
+  p.y_off.assign(nsn, 0);
+  int64_t off = 0, poff = 0, yoff = 0;
+  p.max_front = 0;
+  for (int i = 0; i < (int)nsn; ++i) {
+    int32_t s = p.level_fronts[i];
+    int64_t pp = p.sn_end[s] - p.sn_start[s];
+    int64_t m = pp + p.struct_ptr[s + 1] - p.struct_ptr[s];
+    p.front_off[s] = off;
+    off += m * m;
+    p.piv_off[s] = poff;
+    poff += pp;
+    p.y_off[s] = yoff;
+    yoff += m;
+    p.max_front = std::max<int>(p.max_front, (int)m);
+    // algorithmic flops of the partial LDL^T: sum_{k<p} (m-k-1)(m-k)/2 complex MACs
+    double cm = 0;
+    for (int64_t kk = 0; kk < pp; ++kk) cm += 0.5 * double(m - kk - 1) * double(m - kk);
+    p.flops[p.sn_kind[s]] += 8.0 * cm;
+  }
+  p.arena_elems = off;
+  p.piv_total = poff;
+  p.y_rows = yoff;
+
+  // ---- entries grouped by level with arena offsets
+  {
+    std::vector<int64_t> cnt(p.n_levels + 1, 0);
+    for (auto &t : trips) cnt[p.level[sn_of[t.c]] + 1]++;
+    for (int l = 0; l < p.n_levels; ++l) cnt[l + 1] += cnt[l];
+    p.ent_ptr = cnt;
+    p.ent_off.resize(trips.size());
+    p.ent_val.resize(trips.size());
+    p.ent_row.resize(trips.size());
+    p.ent_col.resize(trips.size());
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (auto &t : trips) {
+      int64_t s = sn_of[t.c];
+      int64_t a = p.sn_start[s], b = p.sn_end[s];
+      int64_t pp = b - a;
+      int64_t m = pp + p.struct_ptr[s + 1] - p.struct_ptr[s];
+      int64_t lr;
+      if (t.r < b) {
+        lr = t.r - a;
+      } else {
+        const int64_t *qs = p.struct_idx.data() + p.struct_ptr[s];
+        const int64_t *it = std::lower_bound(qs, qs + (m - pp), t.r);
+        lr = pp + (it - qs);
+      }
+      int64_t lc = t.c - a;
+      int64_t slot = fill[p.level[s]]++;
+      p.ent_off[slot] = p.front_off[s] + lc * m + lr;
+      p.ent_val[slot] = t.v;
+      p.ent_row[slot] = t.r;
+      p.ent_col[slot] = t.c;
+    }
+  }
+
+  // ---- global operator A on free edges (full CSR) for fp64 residuals
+  {
+    std::vector<Trip> g;
+    g.reserve((size_t)ncell * 144);
+    for (int ck = 0; ck < p.nz; ++ck)
+      for (int cj = 0; cj < p.ny; ++cj)
+        for (int ci = 0; ci < p.nx; ++ci) {
+          int64_t e[12];
+          cell_edges(p, ci, cj, ck, e);
+          cplx eps = p.eps[ci + (int64_t)p.nx * (cj + (int64_t)p.ny * ck)];
+          int c3[3] = {ci, cj, ck};
+          for (int a = 0; a < 12; ++a) {
+            if (p.pec[e[a]]) continue;
+            for (int b = 0; b < 12; ++b) {
+              if (p.pec[e[b]]) continue;
+              cplx v = S[a][b] - k * k * eps * Me[a][b];
+              for (int axis = 0; axis < 3; ++axis) {
+                if (c3[axis] == 0) v += jk * T[2 * axis][a][b];
+                if (c3[axis] == nn[axis] - 1) v += jk * T[2 * axis + 1][a][b];
+              }
+              if (v != cplx(0.0)) g.push_back({e[a], e[b], v});
+            }
+          }
+        }
+    std::sort(g.begin(), g.end(), [](const Trip &a, const Trip &b) {
+      return a.r != b.r ? a.r < b.r : a.c < b.c;
+    });
+    p.csr_ptr.assign(p.n_edges + 1, 0);
+    p.csr_col.clear();
+    p.csr_val.clear();
+    for (size_t i = 0; i < g.size();) {
+      size_t j = i;
+      cplx v = 0;
+      while (j < g.size() && g[j].r == g[i].r && g[j].c == g[i].c) v += g[j++].v;
+      p.csr_col.push_back((int32_t)g[i].c);
+      p.csr_val.push_back(v);
+      p.csr_ptr[g[i].r + 1]++;
+      i = j;
+    }
+    for (int64_t r = 0; r < p.n_edges; ++r) p.csr_ptr[r + 1] += p.csr_ptr[r];
+  }
+  return D3M_OK;
+}
+
+// ------------------------------------------------------------ plane-wave RHS
+int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
+  const double gq[3] = {0.5 - 0.5 * std::sqrt(0.6), 0.5, 0.5 + 0.5 * std::sqrt(0.6)};
+  const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  const int nn[3] = {p.nx, p.ny, p.nz};
+  const cplx J(0.0, 1.0);
+  for (int r = 0; r < nrhs; ++r)
+    for (int64_t e = 0; e < p.n_edges; ++e) {
+      rhs[2 * (e + ldb * r)] = 0.0;
+      rhs[2 * (e + ldb * r) + 1] = 0.0;
+    }
+  for (int axis = 0; axis < 3; ++axis) {
+    int u = axis == 0 ? 1 : 0, v = axis == 2 ? 1 : 2;
+    double area = p.h[u] * p.h[v];
+    for (int side = 0; side < 2; ++side) {
+      double nvec[3] = {0, 0, 0};
+      nvec[axis] = side ? 1.0 : -1.0;
+      int layer = side ? nn[axis] - 1 : 0;
+      int lim[3] = {p.nx, p.ny, p.nz};
+      for (int ck = 0; ck < lim[2]; ++ck)
+        for (int cj = 0; cj < lim[1]; ++cj)
+          for (int ci = 0; ci < lim[0]; ++ci) {
+            int c3[3] = {ci, cj, ck};
+            if (c3[axis] != layer) continue;
+            int64_t e[12];
+            cell_edges(p, ci, cj, ck, e);
+            for (int qa = 0; qa < 3; ++qa)
+              for (int qb = 0; qb < 3; ++qb) {
+                double ref[3];
+                ref[axis] = side;
+                ref[u] = gq[qa];
+                ref[v] = gq[qb];
+                double xyz[3] = {(ci + ref[0]) * p.h[0], (cj + ref[1]) * p.h[1],
+                                 (ck + ref[2]) * p.h[2]};
+                // basis values at the point (12 x 3)
+                double N[12][3] = {};
+                for (int q = 0; q < 4; ++q) {
+                  int a = OFF[q][0], b = OFF[q][1];
+                  auto ph = [](double t, int s) { return s ? t : 1.0 - t; };
+                  N[q][0] = ph(ref[1], a) * ph(ref[2], b);
+                  N[4 + q][1] = ph(ref[0], a) * ph(ref[2], b);
+                  N[8 + q][2] = ph(ref[0], a) * ph(ref[1], b);
+                }
+                double w = gw[qa] * gw[qb] * area;
+                for (int r = 0; r < nrhs; ++r) {
+                  const double *kp = khat_pol + 9 * r;
+                  cplx pol[3] = {cplx(kp[3], kp[4]), cplx(kp[5], kp[6]), cplx(kp[7], kp[8])};
+                  double kr = kp[0] * xyz[0] + kp[1] * xyz[1] + kp[2] * xyz[2];
+                  cplx ph = std::exp(-J * p.k * kr);
+                  cplx E[3] = {pol[0] * ph, pol[1] * ph, pol[2] * ph};
+                  // curl E = -jk khat x E
+                  cplx cE[3] = {-J * p.k * (kp[1] * E[2] - kp[2] * E[1]),
+                                -J * p.k * (kp[2] * E[0] - kp[0] * E[2]),
+                                -J * p.k * (kp[0] * E[1] - kp[1] * E[0])};
+                  cplx ndotE = nvec[0] * E[0] + nvec[1] * E[1] + nvec[2] * E[2];
+                  cplx U[3];
+                  cplx nxc[3] = {nvec[1] * cE[2] - nvec[2] * cE[1], nvec[2] * cE[0] - nvec[0] * cE[2],
+                                 nvec[0] * cE[1] - nvec[1] * cE[0]};
+                  for (int a = 0; a < 3; ++a) U[a] = nxc[a] - J * p.k * (E[a] - nvec[a] * ndotE);
+                  for (int a = 0; a < 12; ++a) {
+                    cplx dot = U[0] * N[a][0] + U[1] * N[a][1] + U[2] * N[a][2];
+                    if (dot == cplx(0.0)) continue;
+                    int64_t idx = e[a] + ldb * r;
+                    rhs[2 * idx] -= w * dot.real();
+                    rhs[2 * idx + 1] -= w * dot.imag();
+                  }
+                }
+              }
+          }
+    }
+  }
+  return D3M_OK;
+}
+
+}  // namespace d3m
+
+// ============================================================ C ABI (host part)
+using d3m::Ctx;
+
+extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double k,
+                         const d3m_partition *part, const d3m_options *opt, d3m_ctx **out) {
+  if (!out) return D3M_EINVAL;
+  *out = nullptr;
+  if (!mesh || !mat || !part) return D3M_EINVAL;
+  d3m_ctx *h = nullptr;
+  try {
+    h = new d3m_ctx();
+  } catch (...) {
+    return D3M_ENOMEM;
+  }
+  Ctx &c = h->c;
+  if (opt) c.opt = *opt;
+  if (c.opt.refine_tol <= 0) c.opt.refine_tol = 1e-10;
+  if (c.opt.max_refine <= 0) c.opt.max_refine = 10;
+  if (c.opt.precision != D3M_FP64 && c.opt.precision != D3M_MIXED) {
+    c.err = "d3m_setup: unknown precision";
+    *out = h;
+    return D3M_EINVAL;
+  }
+  int rc;
+  try {
+    rc = d3m::build_plan(c, mesh, mat, k, part);
+  } catch (const std::bad_alloc &) {
+    c.err = "d3m_setup: host allocation failed";
+    rc = D3M_ENOMEM;
+  }
+  const d3m::Plan &p = c.plan;
+  if (rc == D3M_OK) {
+    d3m_stats &st = c.stats;
+    st.n_edges = p.n_edges;
+    st.n_free = p.n_free;
+    st.n_lm = (int64_t)p.lm_edge.size();
+    st.n_blocks = (int64_t)p.blocks.size();
+    st.n_subdomains = p.nsub;
+    st.n_m = p.n_m;
+    st.n_fronts = (int64_t)p.sn_start.size();
+    st.n_levels = p.n_levels;
+    st.max_front = p.max_front;
+    st.arena_bytes = p.arena_elems * (c.opt.precision == D3M_FP64 ? 16 : 8);
+    st.flops_interior = p.flops[0];
+    st.flops_domain = p.flops[1];
+    st.flops_k = p.flops[2];
+    st.min_pivot_ratio = 0;
+  }
+  *out = h;
+  return rc;
+}
+
+extern "C" int d3m_rhs_planewave(d3m_ctx *h, const double *khat_pol, int32_t nrhs, double *rhs,
+                                 int64_t ldb) {
+  if (!h || !khat_pol || !rhs || nrhs < 0 || ldb < h->c.plan.n_edges) return D3M_EINVAL;
+  return d3m::rhs_planewave(h->c.plan, khat_pol, nrhs, rhs, ldb);
+}
+
+template <class T>
+static int put(void *buf, size_t *bytes, const std::vector<T> &v) {
+  size_t need = v.size() * sizeof(T);
+  if (!buf) {
+    *bytes = need;
+    return D3M_OK;
+  }
+  if (*bytes < need) return D3M_EINVAL;
+  std::memcpy(buf, v.data(), need);
+  *bytes = need;
+  return D3M_OK;
+}
+
+extern "C" int d3m_structure(d3m_ctx *h, int32_t which, void *buf, size_t *bytes) {
+  if (!h || !bytes) return D3M_EINVAL;
+  const d3m::Plan &p = h->c.plan;
+  const size_t nsn = p.sn_start.size();
+  std::vector<int64_t> v;
+  switch (which) {
+    case D3M_SN_RANGE:
+      for (size_t s = 0; s < nsn; ++s) {
+        v.push_back(p.sn_start[s]);
+        v.push_back(p.sn_end[s]);
+      }
+      return put(buf, bytes, v);
+    case D3M_SN_PARENT:
+      return put(buf, bytes, p.parent);
+    case D3M_SN_KIND:
+      for (size_t s = 0; s < nsn; ++s) {
+        v.push_back(p.sn_kind[s]);
+        v.push_back(p.sn_owner[s]);
+      }
+      return put(buf, bytes, v);
+    case D3M_SN_STRUCT:
+      v = p.struct_ptr;
+      v.insert(v.end(), p.struct_idx.begin(), p.struct_idx.end());
+      return put(buf, bytes, v);
+    case D3M_M_MAP:
+      for (int64_t i = 0; i < p.n_m; ++i) {
+        v.push_back(p.m_sub[i]);
+        v.push_back(p.m_edge[i]);
+      }
+      return put(buf, bytes, v);
+    case D3M_LM:
+      for (size_t l = 0; l < p.lm_edge.size(); ++l) {
+        v.push_back(p.lm_edge[l]);
+        v.push_back(p.lm_plus[l]);
+        v.push_back(p.lm_minus[l]);
+      }
+      return put(buf, bytes, v);
+    case D3M_BLOCKS:
+      for (auto &b : p.blocks) {
+        v.push_back(b[0]);
+        v.push_back(b[1]);
+        v.push_back(b[2]);
+      }
+      return put(buf, bytes, v);
+    case D3M_LAMBDA: {
+      std::vector<double> d(2 * h->c.lambda_host.size());
+      for (size_t i = 0; i < h->c.lambda_host.size(); ++i) {
+        d[2 * i] = h->c.lambda_host[i].real();
+        d[2 * i + 1] = h->c.lambda_host[i].imag();
+      }
+      return put(buf, bytes, d);
+    }
+    case D3M_M_ENTRIES: {
+      std::vector<double> d(4 * p.ent_val.size());
+      for (size_t i = 0; i < p.ent_val.size(); ++i) {
+        d[4 * i] = (double)p.ent_row[i];
+        d[4 * i + 1] = (double)p.ent_col[i];
+        d[4 * i + 2] = p.ent_val[i].real();
+        d[4 * i + 3] = p.ent_val[i].imag();
+      }
+      return put(buf, bytes, d);
+    }
+    case D3M_STATS: {
+      std::vector<d3m_stats> s(1, h->c.stats);
+      return put(buf, bytes, s);
+    }
+    default:
+      return D3M_EINVAL;
+  }
+}
+
+extern "C" int d3m_stats_get(d3m_ctx *h, d3m_stats *out) {
+  if (!h || !out) return D3M_EINVAL;
+  *out = h->c.stats;
+  return D3M_OK;
+}
+
+extern "C" const char *d3m_last_error(const d3m_ctx *h) {
+  if (!h) return "null context";
+  return h->c.err.c_str();
+}
+
+extern "C" void d3m_free(d3m_ctx *h) {
+  if (!h) return;
+  d3m::dev_free(h->c);
+  delete h;
+}

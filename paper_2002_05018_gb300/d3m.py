@@ -1,0 +1,255 @@
+"""Python binding of the D^3M C ABI (include/d3m.h): argument marshalling only.
+
+Every numeric step runs in libd3m.so (host set-up in C++, factorisation and
+substitution in CUDA kernels).  There is no CPU fallback: if the library is
+missing, importing raises; if no GPU is present, d3m_factor / d3m_solve fail
+with D3M_ECUDA.  PyTorch supplies device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libd3m.so")
+
+D3M_OK, D3M_EINVAL, D3M_ENOMEM, D3M_ESINGULAR, D3M_ENOCONV, D3M_ETIMEOUT, D3M_ECUDA, D3M_ESTATE = range(8)
+FP64, MIXED = 0, 1
+SN_RANGE, SN_PARENT, SN_KIND, SN_STRUCT, M_MAP, LM, BLOCKS, LAMBDA, STATS, M_ENTRIES = range(10)
+
+_SYMBOLS = ["d3m_setup", "d3m_factor", "d3m_solve", "d3m_solve_host", "d3m_rhs_planewave",
+            "d3m_structure", "d3m_dense_ldlt", "d3m_export_front", "d3m_stats_get", "d3m_last_error",
+            "d3m_free"]
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class Materials(ctypes.Structure):
+    _fields_ = [("eps_r", ctypes.POINTER(ctypes.c_double)), ("pec_edge", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class Partition(ctypes.Structure):
+    _fields_ = [("px", ctypes.c_int32), ("py", ctypes.c_int32), ("pz", ctypes.c_int32),
+                ("cx", ctypes.POINTER(ctypes.c_int32)), ("cy", ctypes.POINTER(ctypes.c_int32)),
+                ("cz", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
+                ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("resid", ctypes.POINTER(ctypes.c_double)), ("iters", ctypes.c_int32),
+                ("max_resid", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_edges", "n_free", "n_lm", "n_blocks", "n_subdomains", "n_m",
+                                               "n_fronts", "n_levels", "max_front", "arena_bytes")] + \
+               [(n, ctypes.c_double) for n in ("flops_interior", "flops_domain", "flops_k")] + \
+               [("n_2x2", ctypes.c_int64), ("min_pivot_ratio", ctypes.c_double)]
+
+    def asdict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class D3MError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"D3M error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libd3m.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.d3m_setup.argtypes = [ctypes.POINTER(Mesh), ctypes.POINTER(Materials), ctypes.c_double,
+                              ctypes.POINTER(Partition), ctypes.POINTER(Options), ctypes.POINTER(P)]
+    lib.d3m_factor.argtypes = [P]
+    lib.d3m_solve.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(SolveInfo)]
+    lib.d3m_solve_host.argtypes = lib.d3m_solve.argtypes
+    lib.d3m_rhs_planewave.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int64]
+    lib.d3m_structure.argtypes = [P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.d3m_dense_ldlt.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P]
+    lib.d3m_stats_get.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.d3m_export_front.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32), P, P, P]
+    lib.d3m_last_error.argtypes = [P]
+    lib.d3m_last_error.restype = ctypes.c_char_p
+    lib.d3m_free.argtypes = [P]
+    lib.d3m_free.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Solver:
+    """One D^3M problem: set-up on construction (host), factor() and solve()
+    on the GPU.  Names follow the paper: K, K_D, D, lambda."""
+
+    def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
+                 leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None):
+        self.lib = load()
+        self.n_cells = nx * ny * nz
+        self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
+        self._eps = np.ascontiguousarray(np.asarray(eps, np.complex128).view(np.float64))
+        self._cuts = [np.ascontiguousarray(np.asarray(c, np.int32)) for c in (cx, cy, cz)]
+        self._pec = None if pec is None else np.ascontiguousarray(np.asarray(pec, np.uint8))
+        mesh = Mesh(nx, ny, nz, lx, ly, lz)
+        mat = Materials(_ptr(self._eps, ctypes.c_double),
+                        None if self._pec is None else _ptr(self._pec, ctypes.c_uint8))
+        part = Partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, *[_ptr(c, ctypes.c_int32) for c in self._cuts])
+        self.precision = precision
+        self.stream = stream
+        opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream))
+        h = ctypes.c_void_p()
+        rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
+                                ctypes.byref(opt), ctypes.byref(h))
+        self.h = h
+        self._check(rc)
+
+    @classmethod
+    def from_workload(cls, w, precision=FP64, **kw):
+        return cls(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.eps, w.k, w.cx, w.cy, w.cz, pec=w.pec_edge,
+                   precision=precision, **kw)
+
+    def _check(self, rc):
+        if rc != D3M_OK:
+            msg = self.lib.d3m_last_error(self.h) if self.h else b""
+            raise D3MError(rc, (msg or b"").decode())
+
+    def factor(self):
+        self._check(self.lib.d3m_factor(self.h))
+
+    def solve(self, rhs, x=None, resid=True):
+        """rhs: torch complex128 CUDA tensor (n_edges, nrhs) with column-major
+        layout (e.g. a .t() view of an (nrhs, n_edges) tensor) or any tensor
+        (copied to that layout).  Returns (x, info dict)."""
+        import torch
+        if rhs.dim() == 1:
+            rhs = rhs[:, None]
+        r = rhs.shape[1]
+        if rhs.stride(0) != 1:
+            rhs = rhs.t().contiguous().t()
+        if x is None:
+            x = torch.empty((r, self.n_edges), dtype=torch.complex128, device=rhs.device).t()
+        res = np.zeros(r)
+        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0)
+        rc = self.lib.d3m_solve(self.h, ctypes.c_void_p(rhs.data_ptr()), rhs.stride(1),
+                                ctypes.c_void_p(x.data_ptr()), x.stride(1), r, ctypes.byref(info))
+        self._check(rc)
+        return x, dict(resid=res, iters=info.iters, max_resid=info.max_resid)
+
+    def solve_host(self, rhs, x):
+        """Host (ideally pinned) column-major complex128 arrays/tensors."""
+        r = rhs.shape[1]
+        res = np.zeros(r)
+        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0)
+        rp = rhs.data_ptr() if hasattr(rhs, "data_ptr") else rhs.ctypes.data
+        xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+        ld_r = rhs.stride(1) if hasattr(rhs, "data_ptr") else rhs.strides[1] // 16
+        ld_x = x.stride(1) if hasattr(x, "data_ptr") else x.strides[1] // 16
+        rc = self.lib.d3m_solve_host(self.h, ctypes.c_void_p(rp), ld_r, ctypes.c_void_p(xp), ld_x, r,
+                                     ctypes.byref(info))
+        self._check(rc)
+        return dict(resid=res, iters=info.iters, max_resid=info.max_resid)
+
+    def rhs_planewave(self, khat_pol6):
+        kp = np.ascontiguousarray(np.asarray(khat_pol6, np.float64))
+        r = kp.shape[0]
+        out = np.zeros((self.n_edges, r), np.complex128, order="F")
+        self._check(self.lib.d3m_rhs_planewave(self.h, kp.ctypes.data, r, out.ctypes.data, self.n_edges))
+        return out
+
+    def structure(self, which):
+        n = ctypes.c_size_t(0)
+        self._check(self.lib.d3m_structure(self.h, which, None, ctypes.byref(n)))
+        dt = np.float64 if which in (LAMBDA, M_ENTRIES) else np.int64
+        buf = np.zeros(max(n.value // 8, 1), dt)
+        self._check(self.lib.d3m_structure(self.h, which, buf.ctypes.data, ctypes.byref(n)))
+        buf = buf[: n.value // 8]
+        if which in (SN_RANGE, SN_KIND, M_MAP):
+            return buf.reshape(-1, 2)
+        if which in (LM, BLOCKS):
+            return buf.reshape(-1, 3)
+        if which == LAMBDA:
+            return buf.view(np.complex128)
+        if which == M_ENTRIES:
+            return buf.reshape(-1, 4)
+        return buf
+
+    def lam(self, nrhs):
+        v = self.structure(LAMBDA)
+        return v.reshape(nrhs, -1).T
+
+    def export_front(self, q):
+        """(F (m, m) row-major view of the factored front, perm, dinv (p, 6))."""
+        m, p = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.d3m_export_front(self.h, q, ctypes.byref(m), ctypes.byref(p), None, None, None))
+        F = np.zeros((m.value, m.value), np.complex128)
+        perm = np.zeros(max(p.value, 1), np.int32)
+        dinv = np.zeros((max(p.value, 1), 6))
+        self._check(self.lib.d3m_export_front(self.h, q, None, None, F.ctypes.data, perm.ctypes.data,
+                                              dinv.ctypes.data))
+        return F.T.copy(), perm[: p.value], dinv[: p.value]
+
+    def stats(self):
+        s = Stats()
+        self._check(self.lib.d3m_stats_get(self.h, ctypes.byref(s)))
+        return s.asdict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.d3m_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dense_ldlt(A, p, stream=None):
+    """Restricted Bunch-Kaufman partial LDL^T of a batch of complex-symmetric
+    matrices (torch complex128 CUDA tensor (batch, m, m), lower triangle of
+    each column-major matrix read: pass A.transpose(1, 2) layout, i.e. element
+    (i, j) at A[b, j, i]).  Returns (A in place, perm, dinv, info)."""
+    import torch
+    lib = load()
+    if A.dim() != 3 or A.dtype != torch.complex128 or not A.is_cuda or not A.is_contiguous():
+        raise ValueError("dense_ldlt wants a contiguous complex128 CUDA tensor (batch, m, m)")
+    b, m, _ = A.shape
+    perm = torch.empty((b, m), dtype=torch.int32, device=A.device)
+    dinv = torch.empty((b, max(p, 1), 6), dtype=torch.float64, device=A.device)
+    info = torch.empty((b,), dtype=torch.int32, device=A.device)
+    rc = lib.d3m_dense_ldlt(m, p, b, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(perm.data_ptr()),
+                            ctypes.c_void_p(dinv.data_ptr()), ctypes.c_void_p(info.data_ptr()),
+                            _stream_handle(stream))
+    if rc != D3M_OK:
+        raise D3MError(rc, "d3m_dense_ldlt failed")
+    return A, perm, dinv, info

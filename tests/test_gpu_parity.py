@@ -1,0 +1,158 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: relative solution error <= 1e-10 for the fp64 path and <= 1e-8
+for the mixed path after refinement; relative residual
+||A x - f||_inf / ||f||_inf <= 1e-12 (fp64) and <= 1e-10 (mixed) with A
+assembled by the oracle (independent of the library's own operator)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bk, d3m as od3m, fem  # noqa: E402
+from paper_2002_05018_gb300 import d3m, workloads as W  # noqa: E402
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _sym(n, rng, diag_scale=1.0):
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = A + A.T
+    A[np.diag_indices(n)] *= diag_scale
+    return A
+
+
+@pytest.mark.parametrize("m,p,scale", [(1, 1, 1.0), (40, 40, 1.0), (100, 37, 1.0), (257, 129, 0.05),
+                                       (300, 300, 0.0), (130, 64, 0.0)])
+def test_dense_front_kernel(m, p, scale):
+    """Restricted Bunch-Kaufman partial LDL^T of dense fronts: reconstruction
+    and the Schur complement (unique) against the oracle."""
+    _need_gpu()
+    rng = np.random.default_rng(m * 7 + p)
+    mats = [_sym(m, rng, scale) for _ in range(3)]
+    # column-major per matrix: element (i, j) at [b, j, i]
+    A = torch.tensor(np.ascontiguousarray(np.stack([M.T for M in mats])), device="cuda")
+    A, perm, dinv, info = d3m.dense_ldlt(A, p)
+    torch.cuda.synchronize()
+    out = A.cpu().numpy()
+    perm = perm.cpu().numpy()
+    dv = dinv.cpu().numpy()
+    assert np.all(info.cpu().numpy() == 0)
+    for b, F in enumerate(mats):
+        G = out[b].T                       # back to row-major (i, j)
+        pv = perm[b]
+        assert sorted(pv[:p]) == list(range(p)) and np.all(pv[p:] == np.arange(p, m))
+        L = np.tril(G[:, :p], -1)
+        L[np.arange(p), np.arange(p)] = 1.0
+        D = np.zeros((p, p), complex)
+        k = 0
+        while k < p:
+            code = int(dv[b, k, 4])
+            if code == 1:
+                D[k, k] = 1.0 / (dv[b, k, 0] + 1j * dv[b, k, 1])
+                k += 1
+            else:
+                assert code == 2
+                Di = np.array([[dv[b, k, 0] + 1j * dv[b, k, 1], dv[b, k, 2] + 1j * dv[b, k, 3]],
+                               [dv[b, k, 2] + 1j * dv[b, k, 3], dv[b, k + 1, 0] + 1j * dv[b, k + 1, 1]]])
+                D[k:k + 2, k:k + 2] = np.linalg.inv(Di)
+                L[k + 1, k] = 0.0
+                k += 2
+        R = L @ D @ L.T
+        C = np.tril(G[p:, p:])
+        R[p:, p:] += C + np.tril(C, -1).T
+        PF = F[np.ix_(pv, pv)]
+        assert np.abs(PF - R).max() < 1e-11 * np.abs(F).max()
+        _, _, _, Co, _ = bk.ldlt_restricted(F, p)
+        if p < m:
+            assert np.abs(np.tril(C - Co)).max() < 1e-10 * max(1.0, np.abs(Co).max())
+
+
+def _solve_case(w, precision, f=None):
+    s = d3m.Solver.from_workload(w, precision=precision)
+    s.factor()
+    f = fem.rhs_planewave(w) if f is None else f
+    rhs = torch.tensor(np.asfortranarray(f).T.copy(), device="cuda").t()
+    x, info = s.solve(rhs)
+    return s, x.cpu().numpy(), info, f
+
+
+TINY = [
+    lambda: W.tiny(4, 4, 4, 2, 2, 2, seed=1, nrhs=2),
+    lambda: W.tiny(9, 7, 5, 3, 2, 2, seed=4, jitter=True, nrhs=3),
+    lambda: W.tiny(6, 6, 6, 1, 1, 1, seed=2),            # no interface at all
+    lambda: W.tiny(10, 4, 4, 5, 1, 1, seed=3, nrhs=2),   # a chain of subdomains
+]
+
+
+@pytest.mark.parametrize("mk", TINY)
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_tiny_meshes(mk, precision):
+    _need_gpu()
+    w = mk()
+    s, x, info, f = _solve_case(w, precision)
+    xg = fem.solve_global(w, f)
+    err = np.abs(x - xg).max() / np.abs(xg).max()
+    tol = 1e-10 if precision == d3m.FP64 else 1e-8
+    assert err < tol
+    assert fem.rel_residual(w, x, f).max() < (1e-12 if precision == d3m.FP64 else 1e-10)
+
+
+def test_pec_plate_on_cut_plane():
+    _need_gpu()
+    w = W.tiny(8, 8, 6, 2, 2, 2, seed=5, nrhs=2)
+    w.pec_edge = W.pec_plate_mask(8, 8, 6, 2, 6, 2, 6, 3)
+    s, x, info, f = _solve_case(w, d3m.FP64)
+    xg = fem.solve_global(w, f)
+    assert np.abs(x - xg).max() < 1e-10 * np.abs(xg).max()
+    assert np.all(x[w.pec_edge == 1] == 0)
+
+
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_config1_against_oracle(precision):
+    _need_gpu()
+    w = W.make(1)
+    s, x, info, f = _solve_case(w, precision)
+    ref = od3m.solve(w, f, return_all=True)
+    xg = fem.solve_global(w, f)
+    tol = 1e-10 if precision == d3m.FP64 else 1e-8
+    assert np.abs(x - xg).max() < tol * np.abs(xg).max()
+    assert np.abs(x - ref["x"]).max() < tol * np.abs(xg).max()
+    # multipliers: fp64 path to the solution tolerance; the mixed path refines
+    # the primal residual only, so its multipliers keep the factor precision
+    lam = s.lam(f.shape[1])
+    ltol = 1e-9 if precision == d3m.FP64 else 1e-4
+    assert np.abs(lam - ref["lam"]).max() < ltol * np.abs(ref["lam"]).max()
+    assert info["max_resid"] < (1e-12 if precision == d3m.FP64 else 1e-10)
+
+
+def test_config3_fp64():
+    _need_gpu()
+    w = W.make(3)
+    s, x, info, f = _solve_case(w, d3m.FP64)
+    xg = fem.solve_global(w, f)
+    assert np.abs(x - xg).max() < 1e-10 * np.abs(xg).max()
+
+
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_config2_full_size_residual(precision):
+    """Full-size 32^3 / 64-RHS workload in the bench configuration; checked
+    through the residual of the oracle's own assembled operator."""
+    _need_gpu()
+    w = W.make(2)
+    s = d3m.Solver.from_workload(w, precision=precision)
+    s.factor()
+    f = s.rhs_planewave(w.khat_pol6())
+    cols = [0, 17, 63]
+    fo = fem.rhs_planewave(w, which=cols)
+    assert np.abs(f[:, cols] - fo).max() < 1e-12 * np.abs(fo).max()
+    rhs = torch.tensor(f.T.copy(), device="cuda").t()
+    x, info = s.solve(rhs)
+    x = x.cpu().numpy()
+    res = fem.rel_residual(w, x[:, cols], fo)
+    assert res.max() < 1e-10
+    assert info["max_resid"] < 1e-10

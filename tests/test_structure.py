@@ -1,0 +1,78 @@
+"""Host symbolic stage of the library vs the oracle: bit-exact structure.
+
+Runs on CPU (d3m_setup makes no CUDA call).  Compares the ordering of the
+saddle matrix, supernode ranges and kinds, the supernodal elimination tree,
+every front's update-row list, the multiplier map and the block order."""
+import numpy as np
+import pytest
+
+from oracle import decomp, ordering
+from paper_2002_05018_gb300 import d3m, workloads as W
+
+CASES = [
+    ("config1", lambda: W.make(1), 64),
+    ("tiny-2x2x2", lambda: W.tiny(4, 4, 4, 2, 2, 2, seed=1), 16),
+    ("tiny-jitter", lambda: W.tiny(9, 7, 5, 3, 2, 2, seed=4, jitter=True), 24),
+    ("tiny-pec", lambda: _pec_case(), 32),
+]
+
+
+def _pec_case():
+    w = W.tiny(8, 8, 6, 2, 2, 2, seed=5)
+    w.pec_edge = W.pec_plate_mask(8, 8, 6, 2, 6, 2, 6, 3)   # plate on the z cut plane
+    return w
+
+
+@pytest.mark.parametrize("name,make,leaf", CASES)
+def test_structure_bit_exact(name, make, leaf):
+    w = make()
+    dec = decomp.decompose(w)
+    plan = ordering.build_plan(dec, leaf_max=leaf)
+    r, c = ordering.saddle_pattern(dec, plan)
+    ordering.symbolic(plan, r, c)
+    s = d3m.Solver.from_workload(w, leaf_max=leaf)
+    rng = s.structure(d3m.SN_RANGE)
+    assert np.array_equal(rng[:, 0], plan.sn_start) and np.array_equal(rng[:, 1], plan.sn_end)
+    kind = s.structure(d3m.SN_KIND)
+    assert np.array_equal(kind[:, 0], plan.sn_kind) and np.array_equal(kind[:, 1], plan.sn_owner)
+    assert np.array_equal(s.structure(d3m.SN_PARENT), plan.parent)
+    st = s.structure(d3m.SN_STRUCT)
+    n = len(plan.sn_start)
+    ptr, idx = st[: n + 1], st[n + 1:]
+    for q in range(n):
+        assert np.array_equal(idx[ptr[q]:ptr[q + 1]], plan.struct[q]), q
+    mm = s.structure(d3m.M_MAP)
+    assert np.array_equal(mm[:, 0], plan.m_sub) and np.array_equal(mm[:, 1], plan.m_edge)
+    lm = s.structure(d3m.LM)
+    assert np.array_equal(lm[:, 0], dec.lm_edge)
+    assert np.array_equal(lm[:, 1], dec.lm_plus) and np.array_equal(lm[:, 2], dec.lm_minus)
+    bl = s.structure(d3m.BLOCKS)
+    assert [tuple(x) for x in bl[:, :2]] == [tuple(b) for b in dec.blocks]
+    s.close()
+
+
+def test_library_exports_every_declared_symbol():
+    import os
+    import re
+    lib = d3m.load()
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "d3m.h")).read()
+    names = set(re.findall(r"\b(d3m_[a-z_]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    for nme in names:
+        assert hasattr(lib, nme), nme
+
+
+def test_setup_rejects_bad_input():
+    w = W.tiny(4, 4, 4, 2, 1, 1)
+    with pytest.raises(d3m.D3MError) as e:
+        d3m.Solver(4, 4, 4, 1, 1, 1, w.eps, w.k, [0, 4, 4], [0, 4], [0, 4])
+    assert e.value.code == d3m.D3M_EINVAL
+
+
+def test_rhs_planewave_matches_oracle():
+    from oracle import fem
+    w = W.tiny(5, 4, 3, 1, 1, 1, seed=8, nrhs=3)
+    s = d3m.Solver.from_workload(w)
+    f = s.rhs_planewave(w.khat_pol6())
+    fo = fem.rhs_planewave(w)
+    assert np.abs(f - fo).max() < 1e-13 * np.abs(fo).max()
