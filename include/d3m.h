@@ -91,6 +91,8 @@ typedef struct {
                            0 -> 1e-10 */
   int32_t max_refine;   /* mixed: refinement step cap; 0 -> 10 */
   void *stream;         /* cudaStream_t */
+  int32_t profile;      /* 1: time every kernel class with CUDA events on `stream`
+                           (results in d3m_stats); 0: off */
 } d3m_options;
 
 /* Per-solve report: per column relative residual (Numerical Results
@@ -112,6 +114,13 @@ typedef struct {
   double flops_k;         /* ... of the fronts of K (Algorithm 1) */
   int64_t n_2x2;          /* 2x2 pivots taken by the last factorisation */
   double min_pivot_ratio; /* smallest |d| / max|column| seen (diagnostic) */
+  /* last factorisation / solve (kernel launches always; times with profile=1) */
+  int64_t launches_factor, launches_solve;
+  double flops_update;    /* exact real flops of the trailing updates (device-counted) */
+  double flops_panel;     /* exact real flops of the panel column updates */
+  double ms_assemble, ms_panel, ms_update;        /* summed kernel durations */
+  double ms_fwd, ms_bwd, ms_residual;             /* last solve, all refinement steps */
+  double solve_flops;     /* real flops of the last solve's substitutions */
 } d3m_stats;
 
 /*

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
             cx<T> *__restrict__ arena, cx<T> *__restrict__ Wbuf, int32_t *__restrict__ perm,
             double2 *__restrict__ dinv_d, double2 *__restrict__ dinv_o, int8_t *__restrict__ psize,
             int32_t *__restrict__ st_k0, int32_t *__restrict__ st_kb, int32_t *__restrict__ st_info,
-            double *__restrict__ st_minpiv) {
+            double *__restrict__ st_minpiv, double *__restrict__ flop_cnt) {
   const int f = lvl[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f];
   const int k0 = st_k0[f];
@@ -212,8 +212,11 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   __shared__ cx<T> wrow[NB];
   __shared__ ArgMax red[32];
   __shared__ int s_kp, s_kstep, s_imax;
-  __shared__ double s_minpiv;
-  if (tid == 0) s_minpiv = 1e300;
+  __shared__ double s_minpiv, s_cmac;
+  if (tid == 0) {
+    s_minpiv = 1e300;
+    s_cmac = 0.0;
+  }
   int k = k0, j = 0;
   while (k < p && j < NB - 1) {
     // (1) updated column k -> W[:, j]
@@ -236,6 +239,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
       s_kstep = 1;
       s_kp = k;
       s_imax = imax;
+      s_cmac += (double)(m - k) * (j + 1);
     }
     if (fmax(absakk, colmax) == 0.0) {
       if (tid == 0 && st_info[f] == 0) st_info[f] = k + 1;
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
       ArgMax rm = block_argmax(rl, red);
       const double rowmax = rm.v > 0 ? rm.v : 0.0;
       if (tid == 0) {
+        s_cmac += (double)(m - k) * j;
         if (absakk * rowmax >= BK_ALPHA * colmax * colmax) {
           s_kp = k;
         } else if (cabs1(W[imax + (int64_t)(j + 1) * ld]) >= BK_ALPHA * rowmax) {
@@ -356,6 +361,11 @@ __global__ void __launch_bounds__(PANEL_THREADS)
     st_k0[f] = k;
     st_kb[f] = j;
     if (s_minpiv < st_minpiv[f]) st_minpiv[f] = s_minpiv;
+    if (flop_cnt) {
+      const double n = (double)(m - k);
+      atomicAdd(flop_cnt, 8.0 * j * n * (n + 1.0) * 0.5);  // trailing update of this panel
+      atomicAdd(flop_cnt + 1, 8.0 * s_cmac);                 // column updates inside the panel
+    }
   }
 }
 
@@ -732,8 +742,64 @@ __global__ void k_residual(int64_t n, const int64_t *__restrict__ ptr, const int
   }
 }
 
+// ------------------------------------------------------------ profiling
+// CUDA events around each launch group, on the launching stream; durations
+// are summed per kernel class after the stream is synchronised.
+enum ProfClass { PC_ASSEMBLE = 0, PC_PANEL, PC_UPDATE, PC_FWD, PC_BWD, PC_RESID, PC_N };
+struct Profiler {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  size_t used = 0;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int cls, cudaEvent_t &e0) {
+    if (!on) return;
+    e0 = get();
+    cudaEventRecord(e0, s);
+    (void)cls;
+  }
+  void end(int cls, cudaEvent_t e0) {
+    if (!on) return;
+    cudaEvent_t e1 = get();
+    cudaEventRecord(e1, s);
+    marks.push_back({cls, {e0, e1}});
+  }
+  void reset() {
+    marks.clear();
+    used = 0;
+  }
+  void collect(double ms[PC_N]) {
+    for (int q = 0; q < PC_N; ++q) ms[q] = 0;
+    for (auto &mk : marks) {
+      float t = 0;
+      cudaEventElapsedTime(&t, mk.second.first, mk.second.second);
+      ms[mk.first] += t;
+    }
+    reset();
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+#define PROF_BEGIN(cls)   \
+  cudaEvent_t pe_##cls{}; \
+  d->prof.begin(cls, pe_##cls)
+#define PROF_END(cls) d->prof.end(cls, pe_##cls)
+
 // ------------------------------------------------------------ device state
 struct DeviceState {
+  Profiler prof;
+  double *flop_cnt = nullptr;  // [0] trailing-update flops, [1] panel flops
+  int64_t launches = 0;
+  double solve_flops_per_rhs = 0;
   int precision = 0;
   cudaStream_t stream = nullptr;
   // plan tables
@@ -886,6 +952,12 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(dalloc(d, &d->st_kb, nsn));
   CUDA_TRY(dalloc(d, &d->st_info, nsn));
   CUDA_TRY(dalloc(d, &d->st_minpiv, nsn));
+  CUDA_TRY(dalloc(d, &d->flop_cnt, 2));
+  d->prof.on = c.opt.profile != 0;
+  d->prof.s = d->stream;
+  d->solve_flops_per_rhs = 0;
+  for (int64_t s = 0; s < nsn; ++s)  // forward + backward, 8 real flops per complex MAC
+    d->solve_flops_per_rhs += 16.0 * (0.5 * pp[s] * (pp[s] - 1.0) + (double)(m[s] - pp[s]) * pp[s]);
   // extend-add grids
   d->ea_grid.clear();
   for (size_t q = 0; q + 1 < P.ea_ptr.size(); ++q) {
@@ -930,8 +1002,12 @@ static int factor_t(Ctx &c) {
   CUDA_TRY(cudaMemsetAsync(d->st_k0, 0, nsn * sizeof(int32_t), s));
   CUDA_TRY(cudaMemsetAsync(d->st_kb, 0, nsn * sizeof(int32_t), s));
   CUDA_TRY(cudaMemsetAsync(d->st_info, 0, nsn * sizeof(int32_t), s));
+  CUDA_TRY(cudaMemsetAsync(d->flop_cnt, 0, 2 * sizeof(double), s));
+  d->prof.reset();
+  int64_t nl = 0;
   k_fill_double<<<(unsigned)((nsn + 255) / 256), 256, 0, s>>>(d->st_minpiv, nsn, 1e300);
   k_init_perm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm);
+  nl += 2;
   for (int l = 0; l < P.n_levels; ++l) {
     const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
     const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
@@ -940,26 +1016,45 @@ static int factor_t(Ctx &c) {
     int last_s = P.level_fronts[P.level_ptr[l + 1] - 1];
     int64_t mlast = (P.sn_end[last_s] - P.sn_start[last_s]) + (P.struct_ptr[last_s + 1] - P.struct_ptr[last_s]);
     int64_t end = P.front_off[last_s] + mlast * mlast;
-    CUDA_TRY(cudaMemsetAsync(arena + first, 0, (end - first) * sizeof(cx<T>), s));
-    int64_t ne = P.ent_ptr[l + 1] - P.ent_ptr[l];
-    if (ne > 0)
-      k_assemble<T><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(ne, d->ent_off + P.ent_ptr[l],
-                                                                  d->ent_val + P.ent_ptr[l], arena);
-    for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
-      int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
-      if (nk == 0) continue;
-      dim3 g(d->ea_grid[q], nk);
-      k_extend_add<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, arena);
+    {
+      PROF_BEGIN(PC_ASSEMBLE);
+      CUDA_TRY(cudaMemsetAsync(arena + first, 0, (end - first) * sizeof(cx<T>), s));
+      int64_t ne = P.ent_ptr[l + 1] - P.ent_ptr[l];
+      if (ne > 0) {
+        k_assemble<T><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(ne, d->ent_off + P.ent_ptr[l],
+                                                                    d->ent_val + P.ent_ptr[l], arena);
+        ++nl;
+      }
+      for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
+        int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
+        if (nk == 0) continue;
+        dim3 g(d->ea_grid[q], nk);
+        k_extend_add<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, arena);
+        ++nl;
+      }
+      PROF_END(PC_ASSEMBLE);
     }
     const int64_t *wofs = d->wofs + P.level_ptr[l];
     for (int stp = 0; stp < d->level_steps[l]; ++stp) {
-      k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, d->perm, d->dinv_d, d->dinv_o, d->psize,
-                                              d->st_k0, d->st_kb, d->st_info, d->st_minpiv);
-      dim3 g(d->update_grid[l][stp], nf);
-      k_update<T><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, d->st_k0, d->st_kb);
+      {
+        PROF_BEGIN(PC_PANEL);
+        k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, d->perm, d->dinv_d, d->dinv_o,
+                                                d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv,
+                                                d->flop_cnt);
+        PROF_END(PC_PANEL);
+      }
+      {
+        PROF_BEGIN(PC_UPDATE);
+        dim3 g(d->update_grid[l][stp], nf);
+        k_update<T><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, d->st_k0, d->st_kb);
+        PROF_END(PC_UPDATE);
+      }
+      nl += 2;
     }
   }
   k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
+  ++nl;
+  c.stats.launches_factor = nl;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
   std::vector<int32_t> info(nsn);
@@ -974,6 +1069,17 @@ static int factor_t(Ctx &c) {
   double mn = 1e300;
   for (double v : mp) mn = std::min(mn, v);
   c.stats.min_pivot_ratio = mn;
+  double fc[2];
+  CUDA_TRY(cudaMemcpy(fc, d->flop_cnt, sizeof fc, cudaMemcpyDeviceToHost));
+  c.stats.flops_update = fc[0];
+  c.stats.flops_panel = fc[1];
+  if (d->prof.on) {
+    double ms[PC_N];
+    d->prof.collect(ms);
+    c.stats.ms_assemble = ms[PC_ASSEMBLE];
+    c.stats.ms_panel = ms[PC_PANEL];
+    c.stats.ms_update = ms[PC_UPDATE];
+  }
   for (int64_t q = 0; q < nsn; ++q)
     if (info[q] != 0) {
       char buf[160];
@@ -1025,7 +1131,7 @@ static int ensure_rhs(Ctx &c, int r) {
 
 // One pass of the factored operator: xM = M^{-1} bM (in the factor precision)
 template <typename T>
-static void apply_inverse(Ctx &c, int r) {
+static int64_t apply_inverse(Ctx &c, int r) {
   const Plan &P = c.plan;
   DeviceState *d = c.dev;
   cudaStream_t s = d->stream;
@@ -1034,10 +1140,13 @@ static void apply_inverse(Ctx &c, int r) {
   cx<T> *Y = (cx<T> *)d->Y;
   constexpr int RC = sizeof(T) == 8 ? 8 : 8;
   const int gx = (r + RC - 1) / RC;
+  int64_t nl = 0;
+  PROF_BEGIN(PC_FWD);
   for (int l = 0; l < P.n_levels; ++l) {
     const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
     const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
     int64_t work = (int64_t)d->level_maxm[l] * r;
+    ++nl;
     dim3 gi((unsigned)std::min<int64_t>((work + 255) / 256, 64), nf);
     k_fwd_init<T><<<gi, 256, 0, s>>>(lvl, ft, d->perm, (const cx<T> *)d->bM, Y, r);
     for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
@@ -1045,17 +1154,24 @@ static void apply_inverse(Ctx &c, int r) {
       if (nk == 0) continue;
       dim3 g((unsigned)std::min<int64_t>(((int64_t)d->level_maxm[l] * r + 255) / 256, 64), nk);
       k_fwd_ea<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, d->iperm, Y, r);
+      ++nl;
     }
     dim3 gs(gx, nf);
     k_fwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->dinv_d, d->dinv_o, d->psize, Y, (cx<T> *)d->zM, r);
+    ++nl;
   }
+  PROF_END(PC_FWD);
+  PROF_BEGIN(PC_BWD);
   for (int l = P.n_levels - 1; l >= 0; --l) {
     const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
     const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
     dim3 gs(gx, nf);
     k_bwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->perm, d->psize, d->sidx, Y, (const cx<T> *)d->zM,
                                           (cx<T> *)d->xM, r);
+    ++nl;
   }
+  PROF_END(PC_BWD);
+  return nl;
 }
 
 static unsigned grid1(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
@@ -1078,9 +1194,12 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
     k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>((const double2 *)rhs, ldb, d->fe, n, r);
   }
   // first solve from f
+  d->prof.reset();
+  int64_t nl = 3;
+  int napply = 1;
   CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
   k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->fe, d->owner, (cx<T> *)d->bM, n, r);
-  apply_inverse<T>(c, r);
+  nl += apply_inverse<T>(c, r);
   k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 0);
   if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 0);
   std::vector<double> nh(2 * r);
@@ -1089,8 +1208,13 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   const bool refine = d->precision == D3M_MIXED;
   for (;;) {
     CUDA_TRY(cudaMemsetAsync(d->norms, 0, 2 * r * sizeof(double), s));
-    k_residual<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(n, d->csr_ptr, d->csr_col, d->csr_val, d->xe,
-                                                                 d->fe, d->re, r, d->norms, d->norms + r);
+    {
+      PROF_BEGIN(PC_RESID);
+      k_residual<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(n, d->csr_ptr, d->csr_col, d->csr_val, d->xe,
+                                                                   d->fe, d->re, r, d->norms, d->norms + r);
+      PROF_END(PC_RESID);
+    }
+    ++nl;
     CUDA_TRY(cudaMemcpyAsync(nh.data(), d->norms, 2 * r * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     maxres = 0;
@@ -1103,7 +1227,8 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
     // correction: solve with the residual, accumulate in fp64
     CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
     k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->re, d->owner, (cx<T> *)d->bM, n, r);
-    apply_inverse<T>(c, r);
+    nl += apply_inverse<T>(c, r) + 3;
+    ++napply;
     k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 1);
     if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 1);
     ++iters;
@@ -1120,6 +1245,15 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   if (info) {
     info->iters = iters;
     info->max_resid = maxres;
+  }
+  c.stats.launches_solve = nl + 2;
+  c.stats.solve_flops = d->solve_flops_per_rhs * r * napply;
+  if (d->prof.on) {
+    double ms[PC_N];
+    d->prof.collect(ms);
+    c.stats.ms_fwd = ms[PC_FWD];
+    c.stats.ms_bwd = ms[PC_BWD];
+    c.stats.ms_residual = ms[PC_RESID];
   }
   c.lambda_nrhs = 0;
   if (refine && maxres > c.opt.refine_tol) {
@@ -1227,7 +1361,7 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
   cx<double> *arena = (cx<double> *)A;
   for (int stp = 0; stp < steps; ++stp) {
     k_panel<double><<<batch, PANEL_THREADS, 0, s>>>(tmp.lvl_fronts, ft, tmp.wofs, arena, W, pv, dd, dof, ps, k0, kb,
-                                                    info, mp);
+                                                    info, mp, nullptr);
     int cmin = std::min(p, (stp + 1) * (NB - 1));
     int nt = (m + UT - 1) / UT - cmin / UT;
     dim3 g(std::max(1, nt * (nt + 1) / 2), batch);

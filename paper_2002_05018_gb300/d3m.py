@@ -42,7 +42,7 @@ class Partition(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -54,7 +54,10 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_edges", "n_free", "n_lm", "n_blocks", "n_subdomains", "n_m",
                                                "n_fronts", "n_levels", "max_front", "arena_bytes")] + \
                [(n, ctypes.c_double) for n in ("flops_interior", "flops_domain", "flops_k")] + \
-               [("n_2x2", ctypes.c_int64), ("min_pivot_ratio", ctypes.c_double)]
+               [("n_2x2", ctypes.c_int64), ("min_pivot_ratio", ctypes.c_double),
+                ("launches_factor", ctypes.c_int64), ("launches_solve", ctypes.c_int64)] + \
+               [(n, ctypes.c_double) for n in ("flops_update", "flops_panel", "ms_assemble", "ms_panel",
+                                               "ms_update", "ms_fwd", "ms_bwd", "ms_residual", "solve_flops")]
 
     def asdict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -112,7 +115,7 @@ class Solver:
     on the GPU.  Names follow the paper: K, K_D, D, lambda."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
-                 leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None):
+                 leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -125,7 +128,7 @@ class Solver:
         part = Partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, *[_ptr(c, ctypes.c_int32) for c in self._cuts])
         self.precision = precision
         self.stream = stream
-        opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream))
+        opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile))
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))
