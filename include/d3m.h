@@ -93,6 +93,9 @@ typedef struct {
   void *stream;         /* cudaStream_t */
   int32_t profile;      /* 1: time every kernel class with CUDA events on `stream`
                            (results in d3m_stats); 0: off */
+  int32_t panel_kernel; /* 0: thread-block-cluster panels where the front fits the
+                           cluster's shared memory (default); 1: always the
+                           single-CTA global-memory panel (same arithmetic) */
 } d3m_options;
 
 /* Per-solve report: per column relative residual (Numerical Results
@@ -211,10 +214,10 @@ int d3m_structure(d3m_ctx *ctx, int32_t which, void *buf, size_t *bytes);
  * coupling entry of its 2x2 block (0 for 1x1) and a block-size code
  * (1, 2 = first of a pair, -2 = second) in the real slot of the third pair.
  * info (device int32, batch): 0 or 1 + first zero-pivot column.
- * fp64 only; stream as in d3m_options.  Does not need a context.
+ * fp64 only; stream and panel_kernel as in d3m_options.  Does not need a context.
  */
 int d3m_dense_ldlt(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm, double *dinv,
-                   int32_t *info, void *stream);
+                   int32_t *info, void *stream, int32_t panel_kernel);
 
 /*
  * d3m_export_front -- diagnostics: copy front `front` (M-order supernode id)

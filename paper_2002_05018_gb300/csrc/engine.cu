@@ -16,6 +16,7 @@
 // is factored by panels of NB columns (restricted Bunch-Kaufman with
 // left-looking updates inside the panel, one CTA per front) followed by a
 // trailing update of all fronts of the level (64x64 tiles).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -92,9 +93,10 @@ __device__ __forceinline__ cx<T> from_d(double2 a) {
   } while (0)
 
 constexpr int NB = 32;         // panel width (columns per panel kernel)
+constexpr int LSTR = NB + 1;   // shared-memory row stride of the cluster panel (bank spread)
 constexpr int UT = 64;         // trailing-update tile edge
 constexpr int UK = 16;         // trailing-update k chunk
-constexpr int PANEL_THREADS = 256;
+constexpr int PANEL_THREADS = 512;
 constexpr double BK_ALPHA = 0.6403882032022076;  // (1 + sqrt(17)) / 8
 
 // ------------------------------------------------------------ front tables
@@ -220,11 +222,18 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   int k = k0, j = 0;
   while (k < p && j < NB - 1) {
     // (1) updated column k -> W[:, j]
-    if (tid < j) wrow[tid] = W[k + (int64_t)tid * ld];
+    if (tid < NB) wrow[tid] = tid < j ? W[k + (int64_t)tid * ld] : mk<T>(0, 0);
     __syncthreads();
     for (int i = k + tid; i < m; i += nth) {
       cx<T> acc = F[i + (int64_t)k * ld];
-      for (int t = 0; t < j; ++t) acc = cfms(acc, F[i + (int64_t)(k0 + t) * ld], wrow[t]);
+      const cx<T> *Li = F + i + (int64_t)k0 * ld;
+      for (int t0 = 0; t0 < j; t0 += 8) {  // 8 independent loads in flight
+        cx<T> l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) l[u] = t0 + u < j ? Li[(int64_t)(t0 + u) * ld] : mk<T>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = cfms(acc, l[u], wrow[min(t0 + u, NB - 1)]);
+      }
       W[i + (int64_t)j * ld] = acc;
     }
     __syncthreads();
@@ -245,11 +254,18 @@ __global__ void __launch_bounds__(PANEL_THREADS)
       if (tid == 0 && st_info[f] == 0) st_info[f] = k + 1;
     } else if (absakk < BK_ALPHA * colmax) {
       // (3) updated column imax -> W[:, j+1]
-      if (tid < j) wrow[tid] = W[imax + (int64_t)tid * ld];
+      if (tid < NB) wrow[tid] = tid < j ? W[imax + (int64_t)tid * ld] : mk<T>(0, 0);
       __syncthreads();
       for (int i = k + tid; i < m; i += nth) {
         cx<T> acc = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
-        for (int t = 0; t < j; ++t) acc = cfms(acc, F[i + (int64_t)(k0 + t) * ld], wrow[t]);
+        const cx<T> *Li = F + i + (int64_t)k0 * ld;
+        for (int t0 = 0; t0 < j; t0 += 8) {
+          cx<T> l[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) l[u] = t0 + u < j ? Li[(int64_t)(t0 + u) * ld] : mk<T>(0, 0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc = cfms(acc, l[u], wrow[min(t0 + u, NB - 1)]);
+        }
         W[i + (int64_t)(j + 1) * ld] = acc;
       }
       __syncthreads();
@@ -369,6 +385,427 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   }
 }
 
+// ------------------------------------------------------------ cluster panel kernel
+// The same restricted Bunch-Kaufman panel as k_panel, run by a thread-block
+// cluster of CS CTAs per front with the panel's L rows resident in the
+// cluster's distributed shared memory.  The rows [k0, m) of the front are
+// split into CS contiguous slot ranges; row interchanges only permute the
+// replicated logical-row <-> slot tables (data stays in its slot), while the
+// global front keeps its rows in logical order (previous columns, the
+// trailing part and the panel's own columns are swapped there as before).
+// Per column: every CTA updates its slots of the column (original column from
+// global, L from its shared memory, the pivot row of L from the owner CTA via
+// DSMEM), posts its local pivot-search result in a mailbox, and after one
+// cluster barrier every CTA reads all mailboxes and takes the same decision.
+namespace cg = cooperative_groups;
+
+struct PanelBox {
+  double cmax;   // local max |w_i| over candidate rows
+  int cidx;      // its logical row
+  int has;       // 1 if this CTA owns the queried row(s)
+  double2 v0, v1, v2;  // owner-published values (see use)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+    k_panel_cl(const int32_t *__restrict__ lvl, FrontTab ft, const int64_t *__restrict__ wofs,
+               cx<T> *__restrict__ arena, cx<T> *__restrict__ Wbuf, int32_t *__restrict__ perm,
+               double2 *__restrict__ dinv_d, double2 *__restrict__ dinv_o, int8_t *__restrict__ psize,
+               int32_t *__restrict__ st_k0, int32_t *__restrict__ st_kb, int32_t *__restrict__ st_info,
+               double *__restrict__ st_minpiv, double *__restrict__ flop_cnt, int rcap, int mcap) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int fi = blockIdx.x / CS;
+  const int f = lvl[fi];
+  const int m = ft.m[f], p = ft.p[f];
+  const int k0 = st_k0[f];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (k0 >= p) {  // uniform over the cluster
+    if (rank == 0 && tid == 0) st_kb[f] = 0;
+    return;
+  }
+  cx<T> *F = arena + ft.off[f];
+  cx<T> *W = Wbuf + wofs[fi];
+  int32_t *pv = perm + ft.piv[f];
+  double2 *dd = dinv_d + ft.piv[f];
+  double2 *dof = dinv_o + ft.piv[f];
+  int8_t *ps = psize + ft.piv[f];
+  const int64_t ld = m;
+  const int nr = m - k0;
+  const int R = (nr + CS - 1) / CS;
+  const int s_lo = rank * R;                 // first global slot of this CTA
+  const int ns = max(0, min(R, nr - s_lo));  // slots owned
+  // shared memory layout
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *Ls = reinterpret_cast<cx<T> *>(smem_raw);       // [rcap][LSTR]
+  cx<T> *wk = Ls + (size_t)rcap * LSTR;                   // [rcap]
+  cx<T> *wr = wk + rcap;                                  // [rcap]
+  int *spos = reinterpret_cast<int *>(wr + rcap);         // [rcap] logical row of each own slot
+  int *p2s = spos + rcap;                                 // [mcap] logical row - k0 -> global slot
+  __shared__ PanelBox box[2];
+  __shared__ cx<T> wrow[NB], wrow2[NB];
+  __shared__ double2 Dd[NB], Do[NB];  // D of the panel's pivots: diag / 2x2 coupling
+  __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
+  __shared__ ArgMax red[32];
+  __shared__ double s_minpiv, s_cmac, bc_cmax;
+  __shared__ int bc_imax;
+  __shared__ double2 bc_v0, bc_v1;
+  for (int q = tid; q < nr; q += nth) p2s[q] = q;  // slot q holds row k0 + q initially
+  for (int q = tid; q < ns; q += nth) spos[q] = k0 + s_lo + q;
+  if (tid == 0) {
+    s_minpiv = 1e300;
+    s_cmac = 0.0;
+  }
+  __syncthreads();
+  cl.sync();
+  int k = k0, j = 0;
+  // W row of logical row `row` for the panel columns 0..j-1: L[row, :] D
+  auto load_wrow = [&](int row, cx<T> *dst) {
+    int g = p2s[row - k0];
+    int o = g / R, sl = g - o * R;
+    const cx<T> *Lr = cl.map_shared_rank(Ls, o) + (size_t)sl * LSTR;
+    if (tid < NB) {
+      cx<T> v = mk<T>(0, 0);
+      if (tid < j) {
+        int t = tid;
+        double2 l = to_d(Lr[t]);
+        double2 acc;
+        if (Dz[t] == 1) {
+          acc = zmul(l, Dd[t]);
+        } else if (Dz[t] == 2) {  // [l_t l_t+1] [[d11 d21][d21 d22]] column t
+          double2 l1 = to_d(Lr[t + 1]);
+          double2 a = zmul(l, Dd[t]), b = zmul(l1, Do[t]);
+          acc = make_double2(a.x + b.x, a.y + b.y);
+        } else {  // second of a pair: column t = [d21 d22]^T
+          double2 l0 = to_d(Lr[t - 1]);
+          double2 a = zmul(l0, Do[t]), b = zmul(l, Dd[t]);
+          acc = make_double2(a.x + b.x, a.y + b.y);
+        }
+        v = from_d<T>(acc);
+      }
+      dst[tid] = v;
+    }
+  };
+  while (k < p && j < NB - 1) {
+    // ---- (1) updated column k for own slots, local pivot search
+    load_wrow(k, wrow);
+    __syncthreads();
+    ArgMax loc{-1.0, 0x7fffffff};
+    for (int q = tid; q < ns; q += nth) {
+      int i = spos[q];
+      if (i < k) continue;
+      cx<T> acc = F[i + (int64_t)k * ld];
+      const cx<T> *Lq = Ls + (size_t)q * LSTR;
+#pragma unroll 8
+      for (int t = 0; t < NB - 1; ++t)
+        if (t < j) acc = cfms(acc, Lq[t], wrow[t]);
+      wk[q] = acc;
+      if (i > k && i < p) loc = amax(loc, ArgMax{cabs1(acc), i});
+    }
+    ArgMax cm = block_argmax(loc, red);
+    {
+      int g = p2s[k - k0];
+      int o = g / R;
+      if (tid == 0) {
+        box[0].cmax = cm.v;
+        box[0].cidx = cm.i;
+        box[0].has = o == rank;
+        box[0].v0 = o == rank ? to_d(wk[g - o * R]) : make_double2(0, 0);
+      }
+    }
+    if (tid == 0) s_cmac += (double)(m - k) * (j + 1);
+    cl.sync();  // #1
+    if (tid == 0) {
+      double cmx = -1.0;
+      int imx = 0x7fffffff;
+      double2 a = make_double2(0, 0);
+      for (int c = 0; c < CS; ++c) {
+        const PanelBox *b = cl.map_shared_rank(&box[0], c);
+        ArgMax y = amax(ArgMax{cmx, imx}, ArgMax{b->cmax, b->cidx});
+        cmx = y.v;
+        imx = y.i;
+        if (b->has) a = b->v0;
+      }
+      bc_cmax = cmx;
+      bc_imax = imx;
+      bc_v0 = a;
+    }
+    __syncthreads();
+    double colmax = bc_cmax;
+    int imax = bc_imax;
+    double2 akk = bc_v0;
+    if (!(imax < p)) {
+      colmax = 0.0;
+      imax = k;
+    }
+    const double absakk = fabs(akk.x) + fabs(akk.y);
+    int kstep = 1, kp = k;
+    bool use_r = false;
+    bool singular = fmax(absakk, colmax) == 0.0;
+    double2 d11 = akk, d21 = make_double2(0, 0), d22 = make_double2(0, 0);
+    if (!singular && absakk < BK_ALPHA * colmax) {
+      // ---- (2) updated column imax for own slots
+      load_wrow(imax, wrow2);
+      __syncthreads();
+      ArgMax rl{-1.0, 0x7fffffff};
+      int gi = p2s[imax - k0];
+      int oi = gi / R;
+      for (int q = tid; q < ns; q += nth) {
+        int i = spos[q];
+        if (i < k) continue;
+        cx<T> acc = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
+        const cx<T> *Lq = Ls + (size_t)q * LSTR;
+#pragma unroll 8
+        for (int t = 0; t < NB - 1; ++t)
+          if (t < j) acc = cfms(acc, Lq[t], wrow2[t]);
+        wr[q] = acc;
+        if (i != imax && i < p) rl = amax(rl, ArgMax{cabs1(acc), i});
+      }
+      ArgMax rm = block_argmax(rl, red);
+      if (tid == 0) {
+        box[1].cmax = rm.v;
+        box[1].cidx = rm.i;
+        box[1].has = oi == rank;
+        box[1].v1 = oi == rank ? to_d(wk[gi - oi * R]) : make_double2(0, 0);  // w_k at row imax
+        box[1].v2 = oi == rank ? to_d(wr[gi - oi * R]) : make_double2(0, 0);  // w_r at row imax
+        s_cmac += (double)(m - k) * j;
+      }
+      cl.sync();  // #2
+      if (tid == 0) {
+        double rmx = 0.0;
+        double2 a = make_double2(0, 0), b2 = make_double2(0, 0);
+        for (int c = 0; c < CS; ++c) {
+          const PanelBox *b = cl.map_shared_rank(&box[1], c);
+          if (b->cmax > rmx) rmx = b->cmax;
+          if (b->has) {
+            a = b->v1;
+            b2 = b->v2;
+          }
+        }
+        bc_cmax = rmx;
+        bc_v0 = a;
+        bc_v1 = b2;
+      }
+      __syncthreads();
+      double rowmax = bc_cmax;
+      double2 wki = bc_v0, wri = bc_v1;
+      if (absakk * rowmax >= BK_ALPHA * colmax * colmax) {
+        kp = k;
+      } else if (fabs(wri.x) + fabs(wri.y) >= BK_ALPHA * rowmax) {
+        kp = imax;
+        use_r = true;
+        d11 = wri;
+      } else {
+        kp = imax;
+        kstep = 2;
+        d21 = wki;
+        d22 = wri;
+      }
+    }
+    const int kk = k + kstep - 1;
+    if (kp != kk) {
+      // ---- interchange kk <-> kp in the global front (logical order) and in the tables
+      // (a) the non-updated column kk moves to position kp; each thread handles the
+      //     rows of its own slots so that its later writes to those rows stay ordered
+      for (int q = tid; q < ns; q += nth) {
+        int i = spos[q];
+        if (i > kk && i < kp) F[kp + (int64_t)i * ld] = F[i + (int64_t)kk * ld];
+        else if (i > kp) F[i + (int64_t)kp * ld] = F[i + (int64_t)kk * ld];
+        else if (i == kk) F[kp + (int64_t)kp * ld] = F[kk + (int64_t)kk * ld];
+      }
+      // (b) rows kk and kp of the factored columns [0, k) (column k itself is
+      //     rewritten below), split over the cluster
+      for (int c = rank * nth + tid; c < k; c += CS * nth) {
+        cx<T> a = F[kk + (int64_t)c * ld], b = F[kp + (int64_t)c * ld];
+        F[kk + (int64_t)c * ld] = b;
+        F[kp + (int64_t)c * ld] = a;
+      }
+      if (rank == 0 && tid == 0) {
+        int32_t a = pv[kk];
+        pv[kk] = pv[kp];
+        pv[kp] = a;
+      }
+      cl.sync();  // copies done before the tables change and column k is rewritten
+      if (tid == 0) {
+        int ga = p2s[kk - k0], gb = p2s[kp - k0];
+        p2s[kk - k0] = gb;
+        p2s[kp - k0] = ga;
+        if (ga / R == rank) spos[ga - rank * R] = kp;
+        if (gb / R == rank) spos[gb - rank * R] = kk;
+      }
+      __syncthreads();
+    }
+    // ---- scale: L columns for own slots (logical order after the interchange)
+    if (singular) {
+      if (rank == 0 && tid == 0 && st_info[f] == 0) st_info[f] = k + 1;
+    }
+    if (kstep == 1) {
+      double2 di = (d11.x == 0.0 && d11.y == 0.0) ? make_double2(0, 0) : zdiv1(d11);
+      cx<T> dinv = from_d<T>(di);
+      const cx<T> *src = use_r ? wr : wk;
+      for (int q = tid; q < ns; q += nth) {
+        int i = spos[q];
+        if (i < k) continue;
+        cx<T> l = i == k ? mk<T>(1, 0) : cmul(src[q], dinv);
+        Ls[(size_t)q * LSTR + j] = l;
+        if (i > k) F[i + (int64_t)k * ld] = l;
+        else F[k + (int64_t)k * ld] = from_d<T>(d11);
+      }
+      if (tid == 0) {
+        Dd[j] = d11;
+        Do[j] = make_double2(0, 0);
+        Dz[j] = 1;
+        if (colmax > 0) s_minpiv = fmin(s_minpiv, (fabs(d11.x) + fabs(d11.y)) / colmax);
+      }
+      if (rank == 0 && tid == 0) {
+        dd[k] = di;
+        dof[k] = make_double2(0, 0);
+        ps[k] = 1;
+      }
+    } else {
+      double2 det = zmul(d11, d22), d2 = zmul(d21, d21);
+      det.x -= d2.x;
+      det.y -= d2.y;
+      double2 idet = zdiv1(det);
+      double2 i11 = zmul(d22, idet), i22 = zmul(d11, idet), i21 = zmul(d21, idet);
+      i21.x = -i21.x;
+      i21.y = -i21.y;
+      cx<T> a11 = from_d<T>(i11), a21 = from_d<T>(i21), a22 = from_d<T>(i22);
+      for (int q = tid; q < ns; q += nth) {
+        int i = spos[q];
+        if (i < k) continue;
+        cx<T> l1, l2;
+        if (i == k) {
+          l1 = mk<T>(1, 0);
+          l2 = mk<T>(0, 0);
+          F[k + (int64_t)k * ld] = from_d<T>(d11);
+        } else if (i == k + 1) {
+          l1 = mk<T>(0, 0);
+          l2 = mk<T>(1, 0);
+          F[k + 1 + (int64_t)k * ld] = mk<T>(0, 0);
+          F[k + 1 + (int64_t)(k + 1) * ld] = from_d<T>(d22);
+        } else {
+          cx<T> w1 = wk[q], w2 = wr[q];
+          l1 = cfma(cmul(w1, a11), w2, a21);
+          l2 = cfma(cmul(w1, a21), w2, a22);
+          F[i + (int64_t)k * ld] = l1;
+          F[i + (int64_t)(k + 1) * ld] = l2;
+        }
+        Ls[(size_t)q * LSTR + j] = l1;
+        Ls[(size_t)q * LSTR + j + 1] = l2;
+      }
+      if (tid == 0) {
+        Dd[j] = d11;
+        Dd[j + 1] = d22;
+        Do[j] = d21;
+        Do[j + 1] = d21;
+        Dz[j] = 2;
+        Dz[j + 1] = -2;
+      }
+      if (rank == 0 && tid == 0) {
+        dd[k] = i11;
+        dd[k + 1] = i22;
+        dof[k] = i21;
+        dof[k + 1] = i21;
+        ps[k] = 2;
+        ps[k + 1] = -2;
+      }
+    }
+    cl.sync();  // #3: L rows, tables and the global front are consistent for the next column
+    k += kstep;
+    j += kstep;
+  }
+  // ---- W = L D for the rows below the panel (trailing update input)
+  for (int q = tid; q < ns; q += nth) {
+    int i = spos[q];
+    if (i < k) continue;
+    const cx<T> *Lq = Ls + (size_t)q * LSTR;
+    for (int t = 0; t < j; ++t) {
+      double2 l = to_d(Lq[t]), acc;
+      if (Dz[t] == 1) {
+        acc = zmul(l, Dd[t]);
+      } else if (Dz[t] == 2) {
+        double2 a = zmul(l, Dd[t]), b = zmul(to_d(Lq[t + 1]), Do[t]);
+        acc = make_double2(a.x + b.x, a.y + b.y);
+      } else {
+        double2 a = zmul(to_d(Lq[t - 1]), Do[t]), b = zmul(l, Dd[t]);
+        acc = make_double2(a.x + b.x, a.y + b.y);
+      }
+      W[i + (int64_t)t * ld] = from_d<T>(acc);
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    st_k0[f] = k;
+    st_kb[f] = j;
+  }
+  if (tid == 0) {
+    if (flop_cnt && rank == 0) {
+      const double n = (double)(m - k);
+      atomicAdd(flop_cnt, 8.0 * j * n * (n + 1.0) * 0.5);
+      atomicAdd(flop_cnt + 1, 8.0 * s_cmac);
+    }
+    if (s_minpiv < 1e300) atomicMin(reinterpret_cast<unsigned long long *>(st_minpiv + f),
+                                    (unsigned long long)__double_as_longlong(s_minpiv));
+  }
+  cl.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+static size_t panel_cl_smem(int rcap, int mcap, size_t esz) {
+  return (size_t)rcap * LSTR * esz + 2 * (size_t)rcap * esz + (size_t)rcap * 4 + (size_t)mcap * 4;
+}
+
+constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+// Cluster size for a level whose largest front has mmax rows: the smallest of
+// 1, 2, 4, 8, 16 whose per-CTA shared memory fits; 0 = use the global panel.
+static int panel_cluster_size(int mmax, size_t esz) {
+  for (int cs = 1; cs <= 16; cs *= 2) {
+    int rcap = (mmax + cs - 1) / cs;
+    if (panel_cl_smem(rcap, mmax, esz) <= PANEL_SMEM_MAX) return cs;
+  }
+  return 0;
+}
+
+template <typename T>
+static cudaError_t panel_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PANEL_SMEM_MAX);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  done = e == cudaSuccess;
+  return e;
+}
+
+// One panel step for the nf fronts listed at lvl.
+template <typename T>
+static cudaError_t launch_panel(int cs, int mmax, int nf, const int32_t *lvl, FrontTab ft, const int64_t *wofs,
+                                cx<T> *arena, cx<T> *W, int32_t *perm, double2 *dd, double2 *dof, int8_t *ps,
+                                int32_t *k0, int32_t *kb, int32_t *info, double *minpiv, double *flops,
+                                cudaStream_t s) {
+  if (cs <= 0) {
+    k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv, flops);
+    return cudaGetLastError();
+  }
+  cudaError_t e = panel_attrs<T>();
+  if (e != cudaSuccess) return e;
+  int rcap = (mmax + cs - 1) / cs;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nf * cs));
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = panel_cl_smem(rcap, mmax, sizeof(cx<T>));
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_panel_cl<T>, lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv,
+                            flops, rcap, mmax);
+}
+
 // ------------------------------------------------------------ trailing update
 // F[i, c] -= sum_t L[i, k0+t] W[c, t] for k0+kb <= c <= i < m (lower triangle)
 template <typename T>
@@ -481,8 +918,8 @@ __global__ void k_fwd_ea(const int32_t *__restrict__ kids, FrontTab ft, const in
   }
 }
 
-// Forward substitution with unit-lower L11, update of the front's update
-// rows, then z = D^{-1} y written to zM in pivot order.
+// Forward substitution with unit-lower L11 (pivot rows only), then
+// z = D^{-1} y written to zM in pivot order.  One CTA per (front, RC RHS).
 template <typename T, int RC>
 __global__ void __launch_bounds__(256) k_fwd_solve(const int32_t *__restrict__ lvl, FrontTab ft,
                                                    const cx<T> *__restrict__ arena,
@@ -528,15 +965,20 @@ __global__ void __launch_bounds__(256) k_fwd_solve(const int32_t *__restrict__ l
       int a = e / RC, cc = e % RC;
       if (cc < nc) Yf[(int64_t)(kb0 + a) * r + c0 + cc] = ys[a][cc];
     }
-    // rows below the block
-    for (int i = kb0 + nbk + tid; i < m; i += 256) {
+    // pivot rows below the block (the update rows are done by k_fwd_gemm)
+    for (int i = kb0 + nbk + tid; i < p; i += 256) {
       cx<T> acc[RC];
 #pragma unroll
       for (int cc = 0; cc < RC; ++cc) acc[cc] = mk<T>(0, 0);
-      for (int b = 0; b < nbk; ++b) {
-        cx<T> l = F[i + (int64_t)(kb0 + b) * ld];
+      const cx<T> *Li = F + i + (int64_t)kb0 * ld;
+      for (int b0 = 0; b0 < nbk; b0 += 8) {
+        cx<T> l[8];
 #pragma unroll
-        for (int cc = 0; cc < RC; ++cc) acc[cc] = cfma(acc[cc], l, ys[b][cc]);
+        for (int u = 0; u < 8; ++u) l[u] = b0 + u < nbk ? Li[(int64_t)(b0 + u) * ld] : mk<T>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int cc = 0; cc < RC; ++cc) acc[cc] = cfma(acc[cc], l[u], ys[min(b0 + u, 31)][cc]);
       }
       cx<T> *yi = Yf + (int64_t)i * r + c0;
 #pragma unroll
@@ -571,67 +1013,53 @@ __global__ void __launch_bounds__(256) k_fwd_solve(const int32_t *__restrict__ l
   }
 }
 
-// Backward substitution with L^T: x_piv = L11^{-T} (z - L21^T x_upd), written
-// to xM at the original (un-permuted) positions.
+// Backward substitution with L11^T on the pivot rows, right-looking: start
+// from w = z - sum_s part_s (the split partial products L21^T x_upd of
+// k_bwd_gemm), then for each 32-block from the last: solve the diagonal
+// block, publish x, and subtract L[blk, k]^T x_blk from every earlier pivot
+// row k.  x is written to xM at the original (un-permuted) positions.
 template <typename T, int RC>
 __global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ lvl, FrontTab ft,
                                                    const cx<T> *__restrict__ arena,
                                                    const int32_t *__restrict__ perm,
                                                    const int8_t *__restrict__ psize,
-                                                   const int64_t *__restrict__ sidx, cx<T> *__restrict__ Y,
+                                                   const int32_t *__restrict__ nsplit,
+                                                   const int64_t *__restrict__ part_off,
+                                                   const cx<T> *__restrict__ part, cx<T> *__restrict__ Y,
                                                    const cx<T> *__restrict__ zM, cx<T> *__restrict__ xM, int r) {
   const int f = lvl[blockIdx.y];
   const int m = ft.m[f], p = ft.p[f];
+  (void)m;
   const int c0 = blockIdx.x * RC;
   const int nc = min(RC, r - c0);
   const cx<T> *F = arena + ft.off[f];
-  const int64_t ld = m;
+  const int64_t ld = ft.m[f];
   cx<T> *Yf = Y + ft.yoff[f] * r;
   const int8_t *ps = psize + ft.piv[f];
   const int32_t *pv = perm + ft.piv[f];
-  const int64_t *rows = sidx + ft.soff[f];
   const int64_t st = ft.start[f];
   const int tid = threadIdx.x;
-  // gather x at the update rows
-  for (int e = tid; e < (m - p) * RC; e += 256) {
-    int i = e / RC, cc = e % RC;
-    if (cc < nc) Yf[(int64_t)(p + i) * r + c0 + cc] = xM[rows[i] * r + c0 + cc];
+  const int S = nsplit[blockIdx.y];
+  const cx<T> *pt = part + part_off[blockIdx.y] * r;
+  for (int e = tid; e < p * RC; e += 256) {
+    int k = e / RC, cc = e % RC;
+    if (cc >= nc) continue;
+    cx<T> w = zM[(st + k) * r + c0 + cc];
+    for (int q = 0; q < S; ++q) {
+      cx<T> u = pt[((int64_t)q * p + k) * r + c0 + cc];
+      w.re -= u.re;
+      w.im -= u.im;
+    }
+    Yf[(int64_t)k * r + c0 + cc] = w;
   }
   __syncthreads();
   __shared__ cx<T> Ls[32][33];
-  __shared__ cx<T> Xs[32][RC];
   __shared__ cx<T> v[32][RC];
   const int last = ((p - 1) / 32) * 32;
-  const int b = tid / RC, cc = tid % RC;  // 32 x RC threads own (pivot col, rhs)
+  const int b = tid / RC, cc = tid % RC;  // 32 x RC threads own (pivot, rhs)
   for (int kb0 = last; kb0 >= 0; kb0 -= 32) {
     const int nbk = min(32, p - kb0);
-    cx<T> acc = mk<T>(0, 0);
-    for (int i0 = kb0 + nbk; i0 < m; i0 += 32) {
-      const int nr = min(32, m - i0);
-      for (int e = tid; e < 32 * 32; e += 256) {
-        int rr = e % 32, col = e / 32;
-        Ls[rr][col] = (rr < nr && col < nbk) ? F[i0 + rr + (int64_t)(kb0 + col) * ld] : mk<T>(0, 0);
-      }
-      for (int e = tid; e < 32 * RC; e += 256) {
-        int rr = e / RC, c2 = e % RC;
-        Xs[rr][c2] = (rr < nr && c2 < nc) ? Yf[(int64_t)(i0 + rr) * r + c0 + c2] : mk<T>(0, 0);
-      }
-      __syncthreads();
-      if (b < 32) {
-#pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr) acc = cfma(acc, Ls[rr][b], Xs[rr][cc]);
-      }
-      __syncthreads();
-    }
-    if (b < nbk && cc < nc) {
-      cx<T> z = zM[(st + kb0 + b) * r + c0 + cc];
-      z.re -= acc.re;
-      z.im -= acc.im;
-      v[b][cc] = z;
-    } else if (b < 32) {
-      v[b][cc] = mk<T>(0, 0);
-    }
-    // diagonal block of L (strict lower, 2x2 couplings excluded)
+    if (b < 32) v[b][cc] = (b < nbk && cc < nc) ? Yf[(int64_t)(kb0 + b) * r + c0 + cc] : mk<T>(0, 0);
     for (int e = tid; e < 32 * 32; e += 256) {
       int a = e % 32, col = e / 32;
       cx<T> val = mk<T>(0, 0);
@@ -650,7 +1078,157 @@ __global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ l
       Yf[(int64_t)(kb0 + b) * r + c0 + cc] = v[b][cc];
       xM[(st + pv[kb0 + b]) * r + c0 + cc] = v[b][cc];
     }
+    // earlier pivot rows: w[k] -= sum_b L[kb0+b, k] x[kb0+b]
+    for (int k = tid; k < kb0; k += 256) {
+      cx<T> acc[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mk<T>(0, 0);
+      const cx<T> *Lk = F + kb0 + (int64_t)k * ld;
+      for (int b0 = 0; b0 < nbk; b0 += 8) {
+        cx<T> l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) l[u] = b0 + u < nbk ? Lk[b0 + u] : mk<T>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int q = 0; q < RC; ++q) acc[q] = cfma(acc[q], l[u], v[min(b0 + u, 31)][q]);
+      }
+      cx<T> *yk = Yf + (int64_t)k * r + c0;
+#pragma unroll
+      for (int q = 0; q < RC; ++q)
+        if (q < nc) {
+          cx<T> t = yk[q];
+          t.re -= acc[q].re;
+          t.im -= acc[q].im;
+          yk[q] = t;
+        }
+    }
     __syncthreads();
+  }
+}
+
+// Forward update of a front's update rows: Y[p+i, c] -= sum_k L21[i, k] y[k, c]
+// (all fronts of a level; 64 rows x 32 RHS per CTA, k in chunks of 16).
+constexpr int GR = 64, GC = 32, GK = 16;
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_gemm(const int32_t *__restrict__ lvl, FrontTab ft,
+                                                  const cx<T> *__restrict__ arena, cx<T> *__restrict__ Y, int r) {
+  const int f = lvl[blockIdx.y];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nrt = (m - p + GR - 1) / GR, nct = (r + GC - 1) / GC;
+  if ((int)blockIdx.x >= nrt * nct) return;
+  const int rt = blockIdx.x % nrt, ct = blockIdx.x / nrt;
+  const int i0 = p + rt * GR, c0 = ct * GC;
+  const cx<T> *F = arena + ft.off[f];
+  const int64_t ld = m;
+  cx<T> *Yf = Y + ft.yoff[f] * r;
+  __shared__ cx<T> Ls[GK][GR + 1];
+  __shared__ cx<T> Ys[GK][GC + 1];
+  const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
+  cx<T> acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = mk<T>(0, 0);
+  for (int k0 = 0; k0 < p; k0 += GK) {
+    for (int e = threadIdx.x; e < GK * GR; e += 256) {
+      int rr = e % GR, kk = e / GR;
+      int i = i0 + rr, k = k0 + kk;
+      Ls[kk][rr] = (i < m && k < p) ? F[i + (int64_t)k * ld] : mk<T>(0, 0);
+    }
+    for (int e = threadIdx.x; e < GK * GC; e += 256) {
+      int cc = e % GC, kk = e / GC;
+      int k = k0 + kk, c = c0 + cc;
+      Ys[kk][cc] = (k < p && c < r) ? Yf[(int64_t)k * r + c] : mk<T>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      cx<T> y0 = Ys[kk][tc], y1 = Ys[kk][tc + 16];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        cx<T> l = Ls[kk][tr + 16 * a];
+        acc[a][0] = cfma(acc[a][0], l, y0);
+        acc[a][1] = cfma(acc[a][1], l, y1);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int i = i0 + tr + 16 * a;
+    if (i >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int c = c0 + tc + 16 * b;
+      if (c >= r) continue;
+      cx<T> *d = Yf + (int64_t)i * r + c;
+      cx<T> v = *d;
+      v.re -= acc[a][b].re;
+      v.im -= acc[a][b].im;
+      *d = v;
+    }
+  }
+}
+
+// Backward update, split over the update rows: part[q][k][c] = sum over rows i
+// of split q of L21[i, k] x[struct_i, c] (BSPLIT rows per split), for every
+// pivot k of the fronts of a level; k_bwd_solve subtracts the partials.
+constexpr int BSPLIT = 512;
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_gemm(const int32_t *__restrict__ lvl, FrontTab ft,
+                                                  const cx<T> *__restrict__ arena, const int64_t *__restrict__ sidx,
+                                                  const cx<T> *__restrict__ xM, const int64_t *__restrict__ part_off,
+                                                  cx<T> *__restrict__ part, int r) {
+  const int f = lvl[blockIdx.y];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nrt = (p + GR - 1) / GR, nct = (r + GC - 1) / GC;
+  const int S = (m - p + BSPLIT - 1) / BSPLIT;
+  if ((int)blockIdx.x >= nrt * nct * S) return;
+  const int rt = blockIdx.x % nrt, ct = (blockIdx.x / nrt) % nct, q = blockIdx.x / (nrt * nct);
+  const int k0 = rt * GR, c0 = ct * GC;
+  const int ib = p + q * BSPLIT, ie = min(m, ib + BSPLIT);
+  const cx<T> *F = arena + ft.off[f];
+  const int64_t ld = m;
+  const int64_t *rows = sidx + ft.soff[f];
+  cx<T> *pt = part + part_off[blockIdx.y] * r + (int64_t)q * p * r;
+  __shared__ cx<T> Ls[GK][GR + 1];  // [i][k]
+  __shared__ cx<T> Xs[GK][GC + 1];  // [i][c]
+  const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
+  cx<T> acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = mk<T>(0, 0);
+  for (int i0 = ib; i0 < ie; i0 += GK) {
+    for (int e = threadIdx.x; e < GK * GR; e += 256) {
+      int ii = e % GK, kk = e / GK;
+      int i = i0 + ii, k = k0 + kk;
+      Ls[ii][kk] = (i < ie && k < p) ? F[i + (int64_t)k * ld] : mk<T>(0, 0);
+    }
+    for (int e = threadIdx.x; e < GK * GC; e += 256) {
+      int cc = e % GC, ii = e / GC;
+      int i = i0 + ii, c = c0 + cc;
+      Xs[ii][cc] = (i < ie && c < r) ? xM[rows[i - p] * r + c] : mk<T>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < GK; ++ii) {
+      cx<T> x0 = Xs[ii][tc], x1 = Xs[ii][tc + 16];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        cx<T> l = Ls[ii][tr + 16 * a];
+        acc[a][0] = cfma(acc[a][0], l, x0);
+        acc[a][1] = cfma(acc[a][1], l, x1);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int k = k0 + tr + 16 * a;
+    if (k >= p) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int c = c0 + tc + 16 * b;
+      if (c < r) pt[(int64_t)k * r + c] = acc[a][b];
+    }
   }
 }
 
@@ -832,6 +1410,11 @@ struct DeviceState {
   std::vector<std::vector<int>> update_grid;  // per level, per step: grid.x upper bound
   std::vector<int> ea_grid;                   // per pass: grid.x (tiles) upper bound
   std::vector<int> level_maxm, pass_maxn;
+  std::vector<int> level_gemm_upd, level_gemm_piv;  // solve GEMM grid.x / (RHS tiles), max over the level
+  int32_t *nsplit = nullptr;     // per level position: row splits of k_bwd_gemm
+  int64_t *part_off = nullptr;   // per level position: partial-buffer offset (units of r)
+  int64_t part_rows = 0;         // max over levels of sum(nsplit * p)
+  void *part = nullptr;
   std::vector<void *> allocs;
 };
 
@@ -913,7 +1496,23 @@ static int dev_init(Ctx &c) {
   d->level_steps.assign(P.n_levels, 0);
   d->update_grid.assign(P.n_levels, {});
   d->level_maxm.assign(P.n_levels, 0);
+  std::vector<int32_t> nsplit_h(nsn, 0);
+  std::vector<int64_t> part_off_h(nsn, 0);
+  d->part_rows = 0;
+  d->level_gemm_upd.assign(P.n_levels, 0);
+  d->level_gemm_piv.assign(P.n_levels, 0);
   for (int l = 0; l < P.n_levels; ++l) {
+    int64_t prow = 0;
+    for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+      int s = P.level_fronts[i];
+      int S = (m[s] - pp[s] + BSPLIT - 1) / BSPLIT;
+      nsplit_h[i] = S;
+      part_off_h[i] = prow;
+      prow += (int64_t)S * pp[s];
+      d->level_gemm_upd[l] = std::max(d->level_gemm_upd[l], (m[s] - pp[s] + GR - 1) / GR);
+      d->level_gemm_piv[l] = std::max(d->level_gemm_piv[l], S * ((pp[s] + GR - 1) / GR));
+    }
+    d->part_rows = std::max(d->part_rows, prow);
     int64_t w = 0;
     int steps = 0, maxm = 0;
     for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
@@ -938,6 +1537,8 @@ static int dev_init(Ctx &c) {
     }
   }
   CUDA_TRY(upload(d, &d->wofs, wofs));
+  CUDA_TRY(upload(d, &d->nsplit, nsplit_h));
+  CUDA_TRY(upload(d, &d->part_off, part_off_h));
   const size_t esz = c.opt.precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
   CUDA_TRY(cudaMalloc(&d->W, std::max<int64_t>(wmax, 1) * esz));
   d->allocs.push_back(d->W);
@@ -1038,9 +1639,9 @@ static int factor_t(Ctx &c) {
     for (int stp = 0; stp < d->level_steps[l]; ++stp) {
       {
         PROF_BEGIN(PC_PANEL);
-        k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, d->perm, d->dinv_d, d->dinv_o,
-                                                d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv,
-                                                d->flop_cnt);
+        int cs = c.opt.panel_kernel == 1 ? 0 : panel_cluster_size(d->level_maxm[l], sizeof(cx<T>));
+        CUDA_TRY(launch_panel<T>(cs, d->level_maxm[l], nf, lvl, ft, wofs, arena, W, d->perm, d->dinv_d, d->dinv_o,
+                                 d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv, d->flop_cnt, s));
         PROF_END(PC_PANEL);
       }
       {
@@ -1103,7 +1704,7 @@ static int ensure_rhs(Ctx &c, int r) {
   DeviceState *d = c.dev;
   if (d->cap >= r) return D3M_OK;
   const Plan &P = c.plan;
-  for (void *p : {d->bM, d->zM, d->xM, d->Y, (void *)d->fe, (void *)d->xe, (void *)d->re, (void *)d->ucm,
+  for (void *p : {d->bM, d->zM, d->xM, d->Y, d->part, (void *)d->fe, (void *)d->xe, (void *)d->re, (void *)d->ucm,
                   (void *)d->lam, (void *)d->norms})
     if (p) {
       cudaFree(p);
@@ -1119,6 +1720,7 @@ static int ensure_rhs(Ctx &c, int r) {
   CUDA_TRY(A(&d->zM, P.n_m * r * esz));
   CUDA_TRY(A(&d->xM, P.n_m * r * esz));
   CUDA_TRY(A(&d->Y, P.y_rows * r * esz));
+  CUDA_TRY(A(&d->part, std::max<int64_t>(d->part_rows, 1) * r * esz));
   CUDA_TRY(A((void **)&d->fe, P.n_edges * r * sizeof(double2)));
   CUDA_TRY(A((void **)&d->xe, P.n_edges * r * sizeof(double2)));
   CUDA_TRY(A((void **)&d->re, P.n_edges * r * sizeof(double2)));
@@ -1159,15 +1761,27 @@ static int64_t apply_inverse(Ctx &c, int r) {
     dim3 gs(gx, nf);
     k_fwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->dinv_d, d->dinv_o, d->psize, Y, (cx<T> *)d->zM, r);
     ++nl;
+    if (d->level_gemm_upd[l] > 0) {
+      dim3 gg(d->level_gemm_upd[l] * ((r + GC - 1) / GC), nf);
+      k_fwd_gemm<T><<<gg, 256, 0, s>>>(lvl, ft, arena, Y, r);
+      ++nl;
+    }
   }
   PROF_END(PC_FWD);
   PROF_BEGIN(PC_BWD);
   for (int l = P.n_levels - 1; l >= 0; --l) {
     const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
     const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
+    const int32_t *ns = d->nsplit + P.level_ptr[l];
+    const int64_t *po = d->part_off + P.level_ptr[l];
+    if (d->level_gemm_piv[l] > 0) {
+      dim3 gb(d->level_gemm_piv[l] * ((r + GC - 1) / GC), nf);
+      k_bwd_gemm<T><<<gb, 256, 0, s>>>(lvl, ft, arena, d->sidx, (const cx<T> *)d->xM, po, (cx<T> *)d->part, r);
+      ++nl;
+    }
     dim3 gs(gx, nf);
-    k_bwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->perm, d->psize, d->sidx, Y, (const cx<T> *)d->zM,
-                                          (cx<T> *)d->xM, r);
+    k_bwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->perm, d->psize, ns, po, (const cx<T> *)d->part, Y,
+                                          (const cx<T> *)d->zM, (cx<T> *)d->xM, r);
     ++nl;
   }
   PROF_END(PC_BWD);
@@ -1303,7 +1917,7 @@ void dev_free(Ctx &c) {
 
 // ------------------------------------------------------------ dense entry
 int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, int32_t *info, void *stream,
-               std::string &err) {
+               int panel_kernel, std::string &err) {
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<int32_t> fm(batch, m), fp(batch, p), par(batch, -1), lvl(batch);
   std::vector<int64_t> off(batch), piv(batch), wofs(batch), zero(batch, 0);
@@ -1360,8 +1974,9 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
   int steps = (p + NB - 2) / (NB - 1);
   cx<double> *arena = (cx<double> *)A;
   for (int stp = 0; stp < steps; ++stp) {
-    k_panel<double><<<batch, PANEL_THREADS, 0, s>>>(tmp.lvl_fronts, ft, tmp.wofs, arena, W, pv, dd, dof, ps, k0, kb,
-                                                    info, mp, nullptr);
+    int cs = panel_kernel == 1 ? 0 : panel_cluster_size(m, sizeof(cx<double>));
+    DTRY(launch_panel<double>(cs, m, batch, tmp.lvl_fronts, ft, tmp.wofs, arena, W, pv, dd, dof, ps, k0, kb, info,
+                              mp, nullptr, s));
     int cmin = std::min(p, (stp + 1) * (NB - 1));
     int nt = (m + UT - 1) / UT - cmin / UT;
     dim3 g(std::max(1, nt * (nt + 1) / 2), batch);
@@ -1471,10 +2086,10 @@ extern "C" int d3m_export_front(d3m_ctx *h, int64_t front, int32_t *m_out, int32
 }
 
 extern "C" int d3m_dense_ldlt(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm, double *dinv,
-                              int32_t *info, void *stream) {
+                              int32_t *info, void *stream, int32_t panel_kernel) {
   if (m <= 0 || p < 0 || p > m || batch <= 0 || !A || !perm || !dinv || !info) return D3M_EINVAL;
   std::string err;
-  int rc = d3m::dense_ldlt(m, p, batch, A, perm, dinv, info, stream, err);
+  int rc = d3m::dense_ldlt(m, p, batch, A, perm, dinv, info, stream, panel_kernel, err);
   if (rc) fprintf(stderr, "d3m_dense_ldlt: %s\n", err.c_str());
   return rc;
 }

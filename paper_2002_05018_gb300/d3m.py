@@ -42,7 +42,7 @@ class Partition(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32), ("panel_kernel", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -88,7 +88,7 @@ def load():
     lib.d3m_solve_host.argtypes = lib.d3m_solve.argtypes
     lib.d3m_rhs_planewave.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int64]
     lib.d3m_structure.argtypes = [P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t)]
-    lib.d3m_dense_ldlt.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P]
+    lib.d3m_dense_ldlt.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32]
     lib.d3m_stats_get.argtypes = [P, ctypes.POINTER(Stats)]
     lib.d3m_export_front.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32), P, P, P]
@@ -115,7 +115,7 @@ class Solver:
     on the GPU.  Names follow the paper: K, K_D, D, lambda."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
-                 leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False):
+                 leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -128,7 +128,8 @@ class Solver:
         part = Partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, *[_ptr(c, ctypes.c_int32) for c in self._cuts])
         self.precision = precision
         self.stream = stream
-        opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile))
+        opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile),
+                      int(panel_kernel))
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))
@@ -237,7 +238,7 @@ class Solver:
             pass
 
 
-def dense_ldlt(A, p, stream=None):
+def dense_ldlt(A, p, stream=None, panel_kernel=0):
     """Restricted Bunch-Kaufman partial LDL^T of a batch of complex-symmetric
     matrices (torch complex128 CUDA tensor (batch, m, m), lower triangle of
     each column-major matrix read: pass A.transpose(1, 2) layout, i.e. element
@@ -252,7 +253,7 @@ def dense_ldlt(A, p, stream=None):
     info = torch.empty((b,), dtype=torch.int32, device=A.device)
     rc = lib.d3m_dense_ldlt(m, p, b, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(perm.data_ptr()),
                             ctypes.c_void_p(dinv.data_ptr()), ctypes.c_void_p(info.data_ptr()),
-                            _stream_handle(stream))
+                            _stream_handle(stream), int(panel_kernel))
     if rc != D3M_OK:
         raise D3MError(rc, "d3m_dense_ldlt failed")
     return A, perm, dinv, info

@@ -26,9 +26,58 @@ def _sym(n, rng, diag_scale=1.0):
     return A
 
 
+def _factors(G, dv, p):
+    L = np.tril(G[:, :p], -1)
+    L[np.arange(p), np.arange(p)] = 1.0
+    D = np.zeros((p, p), complex)
+    k = 0
+    while k < p:
+        code = int(dv[k, 4])
+        if code == 1:
+            D[k, k] = 1.0 / (dv[k, 0] + 1j * dv[k, 1])
+            k += 1
+        else:
+            assert code == 2
+            Di = np.array([[dv[k, 0] + 1j * dv[k, 1], dv[k, 2] + 1j * dv[k, 3]],
+                           [dv[k, 2] + 1j * dv[k, 3], dv[k + 1, 0] + 1j * dv[k + 1, 1]]])
+            D[k:k + 2, k:k + 2] = np.linalg.inv(Di)
+            assert L[k + 1, k] == 0
+            k += 2
+    return L, D
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("m,p,scale", [(600, 600, 0.2), (1000, 500, 1.0), (2000, 300, 0.0), (4000, 200, 0.5)])
+def test_dense_front_kernel_large(m, p, scale, kernel):
+    """Large fronts (cluster sizes 2..16 for the cluster panel): reconstruction
+    checked on random vectors, Schur complement against the library-free formula."""
+    _need_gpu()
+    rng = np.random.default_rng(m + p)
+    F = _sym(m, rng, scale)
+    A = torch.tensor(np.ascontiguousarray(F.T[None]), device="cuda")
+    A, perm, dinv, info = d3m.dense_ldlt(A, p, panel_kernel=kernel)
+    torch.cuda.synchronize()
+    assert info.item() == 0
+    G = A.cpu().numpy()[0].T
+    pv = perm.cpu().numpy()[0]
+    L, D = _factors(G, dinv.cpu().numpy()[0], p)
+    PF = F[np.ix_(pv, pv)]
+    X = rng.standard_normal((m, 3)) + 1j * rng.standard_normal((m, 3))
+    C = np.tril(G[p:, p:])
+    C = C + np.tril(C, -1).T
+    lhs = PF @ X
+    rhs = L @ (D @ (L.T @ X))
+    rhs[p:] += C @ X[p:]
+    assert np.abs(lhs - rhs).max() < 1e-10 * np.abs(lhs).max()
+    if p < m:
+        Cs = F[p:, p:] - F[p:, :p] @ np.linalg.solve(F[:p, :p], F[:p, p:])
+        assert np.abs(C - Cs).max() < 1e-9 * np.abs(Cs).max()
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("m,p,scale", [(1, 1, 1.0), (40, 40, 1.0), (100, 37, 1.0), (257, 129, 0.05),
                                        (300, 300, 0.0), (130, 64, 0.0)])
-def test_dense_front_kernel(m, p, scale):
+def test_dense_front_kernel(m, p, scale, kernel):
     """Restricted Bunch-Kaufman partial LDL^T of dense fronts: reconstruction
     and the Schur complement (unique) against the oracle."""
     _need_gpu()
@@ -36,7 +85,7 @@ def test_dense_front_kernel(m, p, scale):
     mats = [_sym(m, rng, scale) for _ in range(3)]
     # column-major per matrix: element (i, j) at [b, j, i]
     A = torch.tensor(np.ascontiguousarray(np.stack([M.T for M in mats])), device="cuda")
-    A, perm, dinv, info = d3m.dense_ldlt(A, p)
+    A, perm, dinv, info = d3m.dense_ldlt(A, p, panel_kernel=kernel)
     torch.cuda.synchronize()
     out = A.cpu().numpy()
     perm = perm.cpu().numpy()
@@ -72,8 +121,8 @@ def test_dense_front_kernel(m, p, scale):
             assert np.abs(np.tril(C - Co)).max() < 1e-10 * max(1.0, np.abs(Co).max())
 
 
-def _solve_case(w, precision, f=None):
-    s = d3m.Solver.from_workload(w, precision=precision)
+def _solve_case(w, precision, f=None, **kw):
+    s = d3m.Solver.from_workload(w, precision=precision, **kw)
     s.factor()
     f = fem.rhs_planewave(w) if f is None else f
     rhs = torch.tensor(np.asfortranarray(f).T.copy(), device="cuda").t()
@@ -95,6 +144,21 @@ def test_tiny_meshes(mk, precision):
     _need_gpu()
     w = mk()
     s, x, info, f = _solve_case(w, precision)
+    _check_tiny(w, x, f, precision)
+
+
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_global_panel_variant(precision):
+    _need_gpu()
+    w = TINY[1]()
+    s = d3m.Solver.from_workload(w, precision=precision, panel_kernel=1)
+    s.factor()
+    f = fem.rhs_planewave(w)
+    x, info = s.solve(torch.tensor(f.T.copy(), device="cuda").t())
+    _check_tiny(w, x.cpu().numpy(), f, precision)
+
+
+def _check_tiny(w, x, f, precision):
     xg = fem.solve_global(w, f)
     err = np.abs(x - xg).max() / np.abs(xg).max()
     tol = 1e-10 if precision == d3m.FP64 else 1e-8
