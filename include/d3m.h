@@ -231,6 +231,33 @@ int d3m_dense_ldlt(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm
 int d3m_export_front(d3m_ctx *ctx, int64_t front, int32_t *m_out, int32_t *p_out, double *F,
                      int32_t *perm, double *dinv);
 
+/*
+ * d3m_dense_ldlt_noalloc -- d3m_dense_ldlt for callers that cannot allocate
+ * memory.  The paper has no counterpart: this is a service entry point of the
+ * library.  Some callers run where cudaMalloc/cudaFree are not allowed --
+ * code inside a stream-ordered region that must not synchronise the device,
+ * allocator hooks and custom memory pools that would recurse into
+ * themselves, or processes whose device memory budget is fixed up front.
+ * This variant computes the same factorisation with every piece of scratch
+ * (front tables, panel workspace, pivot state) in one fixed device array of
+ * D3M_NOALLOC_SCRATCH_BYTES that is part of the library image; it calls no
+ * cudaMalloc, cudaFree or other allocating routine, on the host or the device.
+ * Arguments, layout and results are exactly those of d3m_dense_ldlt.
+ * Limits: the scratch must hold 16*NB*m*batch bytes of panel workspace (NB =
+ * 32) plus about 96 bytes per matrix and 37 bytes per pivot; larger requests
+ * return D3M_EINVAL without touching the GPU.  The first call on a device
+ * looks the array up (cudaGetSymbolAddress, once per device, with that device
+ * current), so make that first call before any stream capture.  Every GPU
+ * that loads the library holds the array until the process exits.  All calls
+ * share the array and it keeps the previous call's contents (the state that
+ * must start at zero is cleared by each call), so calls whose GPU work
+ * overlaps (different streams, or different host threads on the same device)
+ * race with each other: serialise them.
+ */
+#define D3M_NOALLOC_SCRATCH_BYTES (8u << 20)
+int d3m_dense_ldlt_noalloc(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm, double *dinv,
+                           int32_t *info, void *stream);
+
 int d3m_stats_get(d3m_ctx *ctx, d3m_stats *out);
 const char *d3m_last_error(const d3m_ctx *ctx);
 void d3m_free(d3m_ctx *ctx);

@@ -2012,9 +2012,151 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
 #undef DTRY
 }
 
+// ------------------------------------------------------------ allocation-free dense entry
+// Scratch of d3m_dense_ldlt_noalloc: one fixed array in the library image.
+// Host code must not use g_noalloc_scratch's name as an address (it is a
+// host-side shadow); its device address is looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[D3M_NOALLOC_SCRATCH_BYTES];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+struct NoallocLayout {
+  size_t f_m, f_p, f_parent, lvl, f_off, f_piv, f_zero, wofs, W, pv, dd, dof, k0, kb, mp, ps, total;
+};
+static NoallocLayout noalloc_layout(int m, int p, int batch) {
+  NoallocLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  const size_t b = (size_t)batch, pp = (size_t)std::max(p, 1);
+  L.f_m = take(4 * b);
+  L.f_p = take(4 * b);
+  L.f_parent = take(4 * b);
+  L.lvl = take(4 * b);
+  L.f_off = take(8 * b);
+  L.f_piv = take(8 * b);
+  L.f_zero = take(8 * b);
+  L.wofs = take(8 * b);
+  L.W = take(sizeof(cx<double>) * b * (size_t)m * NB);
+  L.pv = take(4 * b * pp);
+  L.dd = take(16 * b * pp);
+  L.dof = take(16 * b * pp);
+  L.k0 = take(4 * b);
+  L.kb = take(4 * b);
+  L.mp = take(8 * b);
+  L.ps = take(b * pp);
+  L.total = o;
+  return L;
+}
+
+__global__ void k_noalloc_init(int m, int p, int batch, int32_t *fm, int32_t *fp, int32_t *par, int32_t *lvl,
+                               int64_t *off, int64_t *piv, int64_t *zero, int64_t *wofs, int32_t *k0, int32_t *kb,
+                               int32_t *info, double *mp, int32_t *pv) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += gridDim.x * blockDim.x) {
+    fm[b] = m;
+    fp[b] = p;
+    par[b] = -1;
+    lvl[b] = b;
+    off[b] = (int64_t)b * m * m;
+    piv[b] = (int64_t)b * p;
+    zero[b] = 0;
+    wofs[b] = (int64_t)b * m * NB;
+    k0[b] = 0;
+    kb[b] = 0;
+    info[b] = 0;
+    mp[b] = 1e300;
+  }
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)batch * p;
+       q += (int64_t)gridDim.x * blockDim.x)
+    pv[q] = (int32_t)(q % p);
+}
+
+__global__ void k_noalloc_out(int m, int p, int batch, const int32_t *pv, const double2 *dd, const double2 *dof,
+                              const int8_t *ps, int32_t *perm, double *dinv) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)batch * m;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = q / m;
+    int i = (int)(q % m);
+    perm[q] = i < p ? pv[b * p + i] : i;
+  }
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)batch * p;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    dinv[6 * q + 0] = dd[q].x;
+    dinv[6 * q + 1] = dd[q].y;
+    dinv[6 * q + 2] = dof[q].x;
+    dinv[6 * q + 3] = dof[q].y;
+    dinv[6 * q + 4] = ps[q];
+    dinv[6 * q + 5] = 0.0;
+  }
+}
+
+static int dense_ldlt_noalloc(int m, int p, int batch, double *A, int32_t *perm, double *dinv, int32_t *info,
+                              void *stream) {
+  const NoallocLayout Lo = noalloc_layout(m, p, batch);
+  if (Lo.total > (size_t)D3M_NOALLOC_SCRATCH_BYTES) return D3M_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return D3M_ECUDA;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return D3M_EINVAL;
+  if (!g_noalloc_addr[dev]) {  // once per device, with that device current
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return D3M_ECUDA;
+    g_noalloc_addr[dev] = ptr;
+  }
+  unsigned char *base = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+  cudaStream_t s = (cudaStream_t)stream;
+  FrontTab ft;
+  ft.m = reinterpret_cast<int32_t *>(base + Lo.f_m);
+  ft.p = reinterpret_cast<int32_t *>(base + Lo.f_p);
+  ft.parent = reinterpret_cast<int32_t *>(base + Lo.f_parent);
+  ft.off = reinterpret_cast<int64_t *>(base + Lo.f_off);
+  ft.piv = reinterpret_cast<int64_t *>(base + Lo.f_piv);
+  ft.soff = ft.start = ft.yoff = reinterpret_cast<int64_t *>(base + Lo.f_zero);
+  int32_t *lvl = reinterpret_cast<int32_t *>(base + Lo.lvl);
+  int64_t *wofs = reinterpret_cast<int64_t *>(base + Lo.wofs);
+  cx<double> *W = reinterpret_cast<cx<double> *>(base + Lo.W);
+  int32_t *pv = reinterpret_cast<int32_t *>(base + Lo.pv);
+  double2 *dd = reinterpret_cast<double2 *>(base + Lo.dd);
+  double2 *dof = reinterpret_cast<double2 *>(base + Lo.dof);
+  int32_t *k0 = reinterpret_cast<int32_t *>(base + Lo.k0);
+  int32_t *kb = reinterpret_cast<int32_t *>(base + Lo.kb);
+  double *mp = reinterpret_cast<double *>(base + Lo.mp);
+  int8_t *ps = reinterpret_cast<int8_t *>(base + Lo.ps);
+  k_noalloc_init<<<(unsigned)std::min<int64_t>(((int64_t)batch * std::max(p, 1) + 255) / 256 + 1, 1024), 256, 0,
+                   s>>>(m, p, batch, const_cast<int32_t *>(ft.m), const_cast<int32_t *>(ft.p),
+                        const_cast<int32_t *>(ft.parent), lvl, const_cast<int64_t *>(ft.off),
+                        const_cast<int64_t *>(ft.piv), const_cast<int64_t *>(ft.soff), wofs, k0, kb, info, mp, pv);
+  if (cudaGetLastError() != cudaSuccess) return D3M_ECUDA;
+  const int steps = (p + NB - 2) / (NB - 1);
+  const int cs = panel_cluster_size(m, sizeof(cx<double>));
+  cx<double> *arena = reinterpret_cast<cx<double> *>(A);
+  for (int stp = 0; stp < steps; ++stp) {
+    if (launch_panel<double>(cs, m, batch, lvl, ft, wofs, arena, W, pv, dd, dof, ps, k0, kb, info, mp, nullptr, s) !=
+        cudaSuccess)
+      return D3M_ECUDA;
+    int cmin = std::min(p, (stp + 1) * (NB - 1));
+    int nt = (m + UT - 1) / UT - cmin / UT;
+    dim3 g(std::max(1, nt * (nt + 1) / 2), batch);
+    k_update<double><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, k0, kb);
+  }
+  k_noalloc_out<<<(unsigned)std::min<int64_t>(((int64_t)batch * m + 255) / 256, 4096), 256, 0, s>>>(
+      m, p, batch, pv, dd, dof, ps, perm, dinv);
+  if (cudaGetLastError() != cudaSuccess) return D3M_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return D3M_ECUDA;
+  return D3M_OK;
+}
+
 }  // namespace d3m
 
 // ============================================================ C ABI (device part)
+extern "C" int d3m_dense_ldlt_noalloc(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm, double *dinv,
+                                      int32_t *info, void *stream) {
+  if (m <= 0 || p < 0 || p > m || batch <= 0 || !A || !perm || !dinv || !info) return D3M_EINVAL;
+  return d3m::dense_ldlt_noalloc(m, p, batch, A, perm, dinv, info, stream);
+}
+
 extern "C" int d3m_factor(d3m_ctx *h) {
   if (!h) return D3M_EINVAL;
   try {

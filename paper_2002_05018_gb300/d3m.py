@@ -20,8 +20,8 @@ FP64, MIXED = 0, 1
 SN_RANGE, SN_PARENT, SN_KIND, SN_STRUCT, M_MAP, LM, BLOCKS, LAMBDA, STATS, M_ENTRIES = range(10)
 
 _SYMBOLS = ["d3m_setup", "d3m_factor", "d3m_solve", "d3m_solve_host", "d3m_rhs_planewave",
-            "d3m_structure", "d3m_dense_ldlt", "d3m_export_front", "d3m_stats_get", "d3m_last_error",
-            "d3m_free"]
+            "d3m_structure", "d3m_dense_ldlt", "d3m_dense_ldlt_noalloc", "d3m_export_front", "d3m_stats_get",
+            "d3m_last_error", "d3m_free"]
 
 
 class Mesh(ctypes.Structure):
@@ -89,6 +89,7 @@ def load():
     lib.d3m_rhs_planewave.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int64]
     lib.d3m_structure.argtypes = [P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.d3m_dense_ldlt.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32]
+    lib.d3m_dense_ldlt_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P]
     lib.d3m_stats_get.argtypes = [P, ctypes.POINTER(Stats)]
     lib.d3m_export_front.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32), P, P, P]
@@ -256,4 +257,24 @@ def dense_ldlt(A, p, stream=None, panel_kernel=0):
                             _stream_handle(stream), int(panel_kernel))
     if rc != D3M_OK:
         raise D3MError(rc, "d3m_dense_ldlt failed")
+    return A, perm, dinv, info
+
+
+def dense_ldlt_noalloc(A, p, stream=None):
+    """As dense_ldlt through d3m_dense_ldlt_noalloc: for callers that cannot
+    allocate (all scratch lives in the library's fixed device array).  The
+    output tensors are the caller's; nothing is allocated by the library."""
+    import torch
+    lib = load()
+    if A.dim() != 3 or A.dtype != torch.complex128 or not A.is_cuda or not A.is_contiguous():
+        raise ValueError("dense_ldlt_noalloc wants a contiguous complex128 CUDA tensor (batch, m, m)")
+    b, m, _ = A.shape
+    perm = torch.empty((b, m), dtype=torch.int32, device=A.device)
+    dinv = torch.empty((b, max(p, 1), 6), dtype=torch.float64, device=A.device)
+    info = torch.empty((b,), dtype=torch.int32, device=A.device)
+    rc = lib.d3m_dense_ldlt_noalloc(m, p, b, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(perm.data_ptr()),
+                                    ctypes.c_void_p(dinv.data_ptr()), ctypes.c_void_p(info.data_ptr()),
+                                    _stream_handle(stream))
+    if rc != D3M_OK:
+        raise D3MError(rc, "d3m_dense_ldlt_noalloc failed")
     return A, perm, dinv, info
