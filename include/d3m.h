@@ -169,6 +169,31 @@ int d3m_solve_host(d3m_ctx *ctx, const double *rhs, int64_t ldb, double *x, int6
                    int32_t nrhs, d3m_solve_info *info);
 
 /*
+ * d3m_solve_adjoint -- y = A^{-H} b with the same factors (DEVICE pointers,
+ * layouts as d3m_solve).  A is complex symmetric (A = A^T, the paper's
+ * discussion of K), so A^{-H} b = conj(A^{-1} conj(b)): the conjugations are
+ * applied inside the library and the factorisation is reused as it is.  This
+ * is the adjoint solve of a field objective's gradient; MIXED precision
+ * refines it like d3m_solve.
+ */
+int d3m_solve_adjoint(d3m_ctx *ctx, const double *rhs, int64_t ldb, double *y, int64_t ldy,
+                      int32_t nrhs, d3m_solve_info *info);
+
+/*
+ * d3m_grad_eps -- per-cell gradient of a real objective J(x) of the solution
+ * with respect to the real part of eps_r:
+ *   grad[c] = k^2 * Re( sum_r conj(y_r)_c^T M_c x_r,c ),
+ * where x = A^{-1} f is the forward solution, y = A^{-H} (dJ/dx) the adjoint
+ * solution from d3m_solve_adjoint (dJ/dx in PyTorch's convention, e.g. 2 x at
+ * the probes for J = sum |x_probe|^2), M_c the 12x12 mass matrix of cell c
+ * (dA/deps_c = -k^2 M_c) and the sum runs over the nrhs columns.  DEVICE
+ * pointers: x, y as in d3m_solve (PEC rows ignored), grad: n_cells doubles,
+ * overwritten.  FP64 regardless of the factor precision.
+ */
+int d3m_grad_eps(d3m_ctx *ctx, const double *x, int64_t ldx, const double *y, int64_t ldy,
+                 int32_t nrhs, double *grad);
+
+/*
  * d3m_rhs_planewave -- host computation of the ABC right-hand side for
  * incident plane waves E_inc = p exp(-jk khat.r):  f_v = -sum over outer
  * faces of int (n x curl E_inc - jk E_inc,t) . N_v dS, 3x3 Gauss-Legendre

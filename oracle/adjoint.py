@@ -1,0 +1,36 @@
+"""Adjoint gradient of a field objective -- oracle, test only.
+
+Objective J = sum_{m in probes} |x_m|^2 with x = A(eps)^{-1} f and A =
+S - k^2 sum_c eps_c M_c + jk T (Theory section discretisation).  With
+dA/d(Re eps_c) = -k^2 M_c and A = A^T,
+    dJ/d(Re eps_c) = 2 k^2 Re( u_c^T M_c x_c ),   u = A^{-1} (P conj(x)),
+P the probe selector, u_c and x_c the 12 local edge values of cell c.  The
+adjoint solve is a plain second sparse LU solve; no code is shared with the
+library.  Pinned by central finite differences (tests/test_oracle_adjoint.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import fem
+
+
+def objective(x, probes):
+    return float(np.sum(np.abs(x[probes]) ** 2))
+
+
+def gradient(w, f, probes):
+    """(J, dJ/d Re eps (n_cells,)) summed over the RHS columns of f."""
+    g = fem.Grid.of(w)
+    x = fem.solve_global(w, f)
+    rhs = np.zeros_like(x)
+    rhs[probes] = np.conj(x[probes])
+    u = fem.solve_global(w, rhs)
+    _, M = fem.element_matrices(g.h)
+    ce = g.cell_edges()
+    grad = np.zeros(g.n_cells)
+    for col in range(x.shape[1]):
+        xc = x[ce, col]          # (ncell, 12)
+        uc = u[ce, col]
+        grad += 2.0 * w.k ** 2 * np.real(np.einsum("ca,ab,cb->c", uc, M, xc))
+    return objective(x, probes), grad

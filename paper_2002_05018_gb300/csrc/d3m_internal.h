@@ -91,7 +91,9 @@ int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, 
 // engine.cu
 int dev_factor(Ctx &c);
 int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, int nrhs,
-              d3m_solve_info *info, bool host_ptrs);
+              d3m_solve_info *info, bool host_ptrs, bool adjoint = false);
+int dev_grad_eps(Ctx &c, const double *x, int64_t ldx, const double *y, int64_t ldy, int nrhs,
+                 double *grad);
 void dev_free(Ctx &c);
 int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, int32_t *info,
                void *stream, std::string &err);

@@ -1233,20 +1233,64 @@ __global__ void __launch_bounds__(256) k_bwd_gemm(const int32_t *__restrict__ lv
 }
 
 // ------------------------------------------------------------ edge-space kernels
+// column-major user block -> row-major edge vector (conjugated for the adjoint)
 __global__ void k_cm_to_rm(const double2 *__restrict__ in, int64_t ld, double2 *__restrict__ out, int64_t n,
-                           int r) {
+                           int r, int conj) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / r;
     int c = (int)(e % r);
-    out[e] = in[i + ld * c];
+    double2 v = in[i + ld * c];
+    if (conj) v.y = -v.y;
+    out[e] = v;
   }
 }
 __global__ void k_rm_to_cm(const double2 *__restrict__ in, double2 *__restrict__ out, int64_t ld, int64_t n,
-                           int r, const uint8_t *__restrict__ pec) {
+                           int r, const uint8_t *__restrict__ pec, int conj) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / r;
     int c = (int)(e % r);
-    out[i + ld * c] = pec[i] ? make_double2(0.0, 0.0) : in[e];
+    double2 v = pec[i] ? make_double2(0.0, 0.0) : in[e];
+    if (conj) v.y = -v.y;
+    out[i + ld * c] = v;
+  }
+}
+
+// grad[c] = k^2 Re( sum_r conj(y)_c^T M_e x_c ), one thread per cell, fp64
+struct ElemMass {
+  double M[12][12];
+};
+__global__ void k_grad_eps(int nx, int ny, int nz, double k2, ElemMass Me, const double2 *__restrict__ x, int64_t ldx,
+                           const double2 *__restrict__ y, int64_t ldy, int r, const uint8_t *__restrict__ pec,
+                           double *__restrict__ grad) {
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  const int64_t nex = (int64_t)nx * (ny + 1) * (nz + 1), ney = (int64_t)(nx + 1) * ny * (nz + 1);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    int ci = (int)(c % nx), cj = (int)((c / nx) % ny), ck = (int)(c / ((int64_t)nx * ny));
+    int64_t e[12];
+    for (int q = 0; q < 4; ++q) {
+      int a = q & 1, b = q >> 1;
+      e[q] = (ci) + (int64_t)nx * ((cj + a) + (int64_t)(ny + 1) * (ck + b));
+      e[4 + q] = nex + (ci + a) + (int64_t)(nx + 1) * (cj + (int64_t)ny * (ck + b));
+      e[8 + q] = nex + ney + (ci + a) + (int64_t)(nx + 1) * ((cj + b) + (int64_t)(ny + 1) * ck);
+    }
+    double acc = 0.0;
+    for (int rr = 0; rr < r; ++rr) {
+      double2 xv[12], yv[12];
+      for (int a = 0; a < 12; ++a) {
+        bool z = pec[e[a]] != 0;
+        xv[a] = z ? make_double2(0, 0) : x[e[a] + ldx * rr];
+        yv[a] = z ? make_double2(0, 0) : y[e[a] + ldy * rr];
+      }
+      for (int a = 0; a < 12; ++a) {
+        double2 mx = make_double2(0, 0);
+        for (int b = 0; b < 12; ++b) {
+          mx.x += Me.M[a][b] * xv[b].x;
+          mx.y += Me.M[a][b] * xv[b].y;
+        }
+        acc += yv[a].x * mx.x + yv[a].y * mx.y;  // Re(conj(y) * mx)
+      }
+    }
+    grad[c] = k2 * acc;
   }
 }
 template <typename T>
@@ -1792,7 +1836,8 @@ static unsigned grid1(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) 
 
 template <typename T>
 static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, int r,
-                   d3m_solve_info *info, bool host_ptrs) {
+                   d3m_solve_info *info, bool host_ptrs, bool adjoint) {
+  const int cj = adjoint ? 1 : 0;
   const Plan &P = c.plan;
   DeviceState *d = c.dev;
   cudaStream_t s = d->stream;
@@ -1803,9 +1848,9 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   if (host_ptrs) {
     CUDA_TRY(cudaMemcpy2DAsync(d->ucm, n * sizeof(double2), rhs, ldb * sizeof(double2), n * sizeof(double2), r,
                                cudaMemcpyHostToDevice, s));
-    k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>(d->ucm, n, d->fe, n, r);
+    k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>(d->ucm, n, d->fe, n, r, cj);
   } else {
-    k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>((const double2 *)rhs, ldb, d->fe, n, r);
+    k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>((const double2 *)rhs, ldb, d->fe, n, r, cj);
   }
   // first solve from f
   d->prof.reset();
@@ -1848,11 +1893,11 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
     ++iters;
   }
   if (host_ptrs) {
-    k_rm_to_cm<<<grid1(n * r), 256, 0, s>>>(d->xe, d->ucm, n, n, r, d->pec);
+    k_rm_to_cm<<<grid1(n * r), 256, 0, s>>>(d->xe, d->ucm, n, n, r, d->pec, cj);
     CUDA_TRY(cudaMemcpy2DAsync(x, ldx * sizeof(double2), d->ucm, n * sizeof(double2), n * sizeof(double2), r,
                                cudaMemcpyDeviceToHost, s));
   } else {
-    k_rm_to_cm<<<grid1(n * r), 256, 0, s>>>(d->xe, (double2 *)x, ldx, n, r, d->pec);
+    k_rm_to_cm<<<grid1(n * r), 256, 0, s>>>(d->xe, (double2 *)x, ldx, n, r, d->pec, cj);
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1880,15 +1925,15 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
 }
 
 int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, int nrhs, d3m_solve_info *info,
-              bool host_ptrs) {
+              bool host_ptrs, bool adjoint) {
   if (!c.factored) {
     c.err = "d3m_solve: call d3m_factor first";
     return D3M_ESTATE;
   }
   int rc = ensure_rhs(c, nrhs);
   if (rc) return rc;
-  rc = c.opt.precision == D3M_FP64 ? solve_t<double>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs)
-                                   : solve_t<float>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs);
+  rc = c.opt.precision == D3M_FP64 ? solve_t<double>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs, adjoint)
+                                   : solve_t<float>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs, adjoint);
   // keep the multipliers for d3m_structure(D3M_LAMBDA)
   const int64_t nlm = (int64_t)c.plan.lm_edge.size();
   if (rc == D3M_OK || rc == D3M_ENOCONV) {
@@ -1906,6 +1951,22 @@ int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, in
     c.lambda_nrhs = nrhs;
   }
   return rc;
+}
+
+int dev_grad_eps(Ctx &c, const double *x, int64_t ldx, const double *y, int64_t ldy, int nrhs, double *grad) {
+  int rc = dev_init(c);
+  if (rc) return rc;
+  const Plan &P = c.plan;
+  ElemMass Me;
+  double S[12][12];
+  element_matrices(P.h, S, Me.M);
+  cudaStream_t s = c.dev->stream;
+  const int64_t ncell = (int64_t)P.nx * P.ny * P.nz;
+  k_grad_eps<<<grid1(ncell), 256, 0, s>>>(P.nx, P.ny, P.nz, P.k * P.k, Me, (const double2 *)x, ldx,
+                                          (const double2 *)y, ldy, nrhs, c.dev->pec, grad);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return D3M_OK;
 }
 
 void dev_free(Ctx &c) {
@@ -2225,6 +2286,18 @@ extern "C" int d3m_export_front(d3m_ctx *h, int64_t front, int32_t *m_out, int32
     return D3M_ECUDA;
   }
   return D3M_OK;
+}
+
+extern "C" int d3m_solve_adjoint(d3m_ctx *h, const double *rhs, int64_t ldb, double *y, int64_t ldy,
+                                 int32_t nrhs, d3m_solve_info *info) {
+  if (!h || !rhs || !y || nrhs <= 0 || ldb < h->c.plan.n_edges || ldy < h->c.plan.n_edges) return D3M_EINVAL;
+  return d3m::dev_solve(h->c, rhs, ldb, y, ldy, nrhs, info, false, true);
+}
+
+extern "C" int d3m_grad_eps(d3m_ctx *h, const double *x, int64_t ldx, const double *y, int64_t ldy, int32_t nrhs,
+                            double *grad) {
+  if (!h || !x || !y || !grad || nrhs <= 0 || ldx < h->c.plan.n_edges || ldy < h->c.plan.n_edges) return D3M_EINVAL;
+  return d3m::dev_grad_eps(h->c, x, ldx, y, ldy, nrhs, grad);
 }
 
 extern "C" int d3m_dense_ldlt(int32_t m, int32_t p, int32_t batch, double *A, int32_t *perm, double *dinv,

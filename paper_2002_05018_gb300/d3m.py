@@ -21,7 +21,7 @@ SN_RANGE, SN_PARENT, SN_KIND, SN_STRUCT, M_MAP, LM, BLOCKS, LAMBDA, STATS, M_ENT
 
 _SYMBOLS = ["d3m_setup", "d3m_factor", "d3m_solve", "d3m_solve_host", "d3m_rhs_planewave",
             "d3m_structure", "d3m_dense_ldlt", "d3m_dense_ldlt_noalloc", "d3m_export_front", "d3m_stats_get",
-            "d3m_last_error", "d3m_free"]
+            "d3m_last_error", "d3m_free", "d3m_solve_adjoint", "d3m_grad_eps"]
 
 
 class Mesh(ctypes.Structure):
@@ -86,6 +86,8 @@ def load():
     lib.d3m_factor.argtypes = [P]
     lib.d3m_solve.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(SolveInfo)]
     lib.d3m_solve_host.argtypes = lib.d3m_solve.argtypes
+    lib.d3m_solve_adjoint.argtypes = lib.d3m_solve.argtypes
+    lib.d3m_grad_eps.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int32, P]
     lib.d3m_rhs_planewave.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int64]
     lib.d3m_structure.argtypes = [P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.d3m_dense_ldlt.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32]
@@ -109,6 +111,17 @@ def _stream_handle(stream):
     if stream is None:
         return None
     return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _colmajor(t, n):
+    """(tensor, ld): t as an n x r column-major block (copy only if needed)."""
+    if t.dim() == 1:
+        t = t[:, None]
+    r = t.shape[1]
+    if t.stride(0) == 1 and (r == 1 or t.stride(1) >= n):
+        return t, max(n, t.stride(1) if r > 1 else n)
+    t = t.t().contiguous().t()
+    return t, n
 
 
 class Solver:
@@ -155,19 +168,43 @@ class Solver:
         layout (e.g. a .t() view of an (nrhs, n_edges) tensor) or any tensor
         (copied to that layout).  Returns (x, info dict)."""
         import torch
-        if rhs.dim() == 1:
-            rhs = rhs[:, None]
+        rhs, ldb = _colmajor(rhs, self.n_edges)
         r = rhs.shape[1]
-        if rhs.stride(0) != 1:
-            rhs = rhs.t().contiguous().t()
         if x is None:
             x = torch.empty((r, self.n_edges), dtype=torch.complex128, device=rhs.device).t()
         res = np.zeros(r)
         info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0)
-        rc = self.lib.d3m_solve(self.h, ctypes.c_void_p(rhs.data_ptr()), rhs.stride(1),
-                                ctypes.c_void_p(x.data_ptr()), x.stride(1), r, ctypes.byref(info))
+        ldx = x.stride(1) if r > 1 else self.n_edges
+        rc = self.lib.d3m_solve(self.h, ctypes.c_void_p(rhs.data_ptr()), ldb,
+                                ctypes.c_void_p(x.data_ptr()), ldx, r, ctypes.byref(info))
         self._check(rc)
         return x, dict(resid=res, iters=info.iters, max_resid=info.max_resid)
+
+    def solve_adjoint(self, rhs, y=None):
+        """y = A^{-H} rhs with the same factors (device tensors, layout as solve)."""
+        import torch
+        rhs, ldb = _colmajor(rhs, self.n_edges)
+        r = rhs.shape[1]
+        if y is None:
+            y = torch.empty((r, self.n_edges), dtype=torch.complex128, device=rhs.device).t()
+        res = np.zeros(r)
+        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0)
+        ldy = y.stride(1) if r > 1 else self.n_edges
+        rc = self.lib.d3m_solve_adjoint(self.h, ctypes.c_void_p(rhs.data_ptr()), ldb,
+                                        ctypes.c_void_p(y.data_ptr()), ldy, r, ctypes.byref(info))
+        self._check(rc)
+        return y, dict(resid=res, iters=info.iters, max_resid=info.max_resid)
+
+    def grad_eps(self, x, y):
+        """grad[c] = k^2 Re(sum_r conj(y)_c^T M_c x_c) on the device (float64, n_cells)."""
+        import torch
+        x, ldx = _colmajor(x, self.n_edges)
+        y, ldy = _colmajor(y, self.n_edges)
+        g = torch.empty(self.n_cells, dtype=torch.float64, device=x.device)
+        rc = self.lib.d3m_grad_eps(self.h, ctypes.c_void_p(x.data_ptr()), ldx, ctypes.c_void_p(y.data_ptr()),
+                                   ldy, x.shape[1], ctypes.c_void_p(g.data_ptr()))
+        self._check(rc)
+        return g
 
     def solve_host(self, rhs, x):
         """Host (ideally pinned) column-major complex128 arrays/tensors."""
