@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   __shared__ ArgMax red[32];
   __shared__ int s_kp, s_kstep, s_imax;
   __shared__ double s_minpiv, s_cmac;
+  __shared__ double2 s_dinv;
   if (tid == 0) {
     s_minpiv = 1e300;
     s_cmac = 0.0;
@@ -322,8 +323,9 @@ __global__ void __launch_bounds__(PANEL_THREADS)
     if (kstep == 1) {
       cx<T> d = W[k + (int64_t)j * ld];
       double2 dd0 = to_d(d);
-      bool zero = dd0.x == 0.0 && dd0.y == 0.0;
-      double2 di = zero ? make_double2(0.0, 0.0) : zdiv1(dd0);
+      if (tid == 0) s_dinv = (dd0.x == 0.0 && dd0.y == 0.0) ? make_double2(0.0, 0.0) : zdiv1(dd0);
+      __syncthreads();
+      double2 di = s_dinv;
       cx<T> dinv = from_d<T>(di);
       for (int i = k + 1 + tid; i < m; i += nth) F[i + (int64_t)k * ld] = cmul(W[i + (int64_t)j * ld], dinv);
       if (tid == 0) {
@@ -412,7 +414,8 @@ __global__ void __launch_bounds__(512)
                cx<T> *__restrict__ arena, cx<T> *__restrict__ Wbuf, int32_t *__restrict__ perm,
                double2 *__restrict__ dinv_d, double2 *__restrict__ dinv_o, int8_t *__restrict__ psize,
                int32_t *__restrict__ st_k0, int32_t *__restrict__ st_kb, int32_t *__restrict__ st_info,
-               double *__restrict__ st_minpiv, double *__restrict__ flop_cnt, int rcap, int mcap) {
+               double *__restrict__ st_minpiv, double *__restrict__ flop_cnt, int2 *__restrict__ swp, int rcap,
+               int mcap) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(512)
   double2 *dof = dinv_o + ft.piv[f];
   int8_t *ps = psize + ft.piv[f];
   const int64_t ld = m;
-  const int nr = m - k0;
+  const int nr = p - k0;  // pivot rows only: update rows (>= p) are done by k_l21
   const int R = (nr + CS - 1) / CS;
   const int s_lo = rank * R;                 // first global slot of this CTA
   const int ns = max(0, min(R, nr - s_lo));  // slots owned
@@ -445,20 +448,29 @@ __global__ void __launch_bounds__(512)
   int *p2s = spos + rcap;                                 // [mcap] logical row - k0 -> global slot
   __shared__ PanelBox box[2];
   __shared__ cx<T> wrow[NB], wrow2[NB];
-  __shared__ double2 Dd[NB], Do[NB];  // D of the panel's pivots: diag / 2x2 coupling
+  __shared__ cx<T> Dd[NB], Do[NB];    // D of the panel's pivots: diag / 2x2 coupling
+  __shared__ double2 s_inv[3];         // fp64 inverse of the current pivot block (one thread)
   __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
   __shared__ ArgMax red[32];
   __shared__ double s_minpiv, s_cmac, bc_cmax;
   __shared__ int bc_imax;
   __shared__ double2 bc_v0, bc_v1;
   for (int q = tid; q < nr; q += nth) p2s[q] = q;  // slot q holds row k0 + q initially
+  if (rank == 0 && tid < NB) swp[(int64_t)fi * NB + tid] = make_int2(-1, -1);
   for (int q = tid; q < ns; q += nth) spos[q] = k0 + s_lo + q;
   if (tid == 0) {
     s_minpiv = 1e300;
     s_cmac = 0.0;
   }
   __syncthreads();
-  cl.sync();
+  if (CS > 1) cl.sync();
+  // a cluster of one synchronises like a plain block
+  auto csync = [&]() {
+    if (CS == 1)
+      __syncthreads();
+    else
+      cl.sync();
+  };
   int k = k0, j = 0;
   // W row of logical row `row` for the panel columns 0..j-1: L[row, :] D
   auto load_wrow = [&](int row, cx<T> *dst) {
@@ -469,20 +481,14 @@ __global__ void __launch_bounds__(512)
       cx<T> v = mk<T>(0, 0);
       if (tid < j) {
         int t = tid;
-        double2 l = to_d(Lr[t]);
-        double2 acc;
+        cx<T> l = Lr[t];
         if (Dz[t] == 1) {
-          acc = zmul(l, Dd[t]);
+          v = cmul(l, Dd[t]);
         } else if (Dz[t] == 2) {  // [l_t l_t+1] [[d11 d21][d21 d22]] column t
-          double2 l1 = to_d(Lr[t + 1]);
-          double2 a = zmul(l, Dd[t]), b = zmul(l1, Do[t]);
-          acc = make_double2(a.x + b.x, a.y + b.y);
+          v = cfma(cmul(l, Dd[t]), Lr[t + 1], Do[t]);
         } else {  // second of a pair: column t = [d21 d22]^T
-          double2 l0 = to_d(Lr[t - 1]);
-          double2 a = zmul(l0, Do[t]), b = zmul(l, Dd[t]);
-          acc = make_double2(a.x + b.x, a.y + b.y);
+          v = cfma(cmul(Lr[t - 1], Do[t]), l, Dd[t]);
         }
-        v = from_d<T>(acc);
       }
       dst[tid] = v;
     }
@@ -514,8 +520,8 @@ __global__ void __launch_bounds__(512)
         box[0].v0 = o == rank ? to_d(wk[g - o * R]) : make_double2(0, 0);
       }
     }
-    if (tid == 0) s_cmac += (double)(m - k) * (j + 1);
-    cl.sync();  // #1
+    if (tid == 0) s_cmac += (double)(p - k) * (j + 1);
+    csync();  // #1
     if (tid == 0) {
       double cmx = -1.0;
       int imx = 0x7fffffff;
@@ -569,9 +575,9 @@ __global__ void __launch_bounds__(512)
         box[1].has = oi == rank;
         box[1].v1 = oi == rank ? to_d(wk[gi - oi * R]) : make_double2(0, 0);  // w_k at row imax
         box[1].v2 = oi == rank ? to_d(wr[gi - oi * R]) : make_double2(0, 0);  // w_r at row imax
-        s_cmac += (double)(m - k) * j;
+        s_cmac += (double)(p - k) * j;
       }
-      cl.sync();  // #2
+      csync();  // #2
       if (tid == 0) {
         double rmx = 0.0;
         double2 a = make_double2(0, 0), b2 = make_double2(0, 0);
@@ -625,8 +631,9 @@ __global__ void __launch_bounds__(512)
         int32_t a = pv[kk];
         pv[kk] = pv[kp];
         pv[kp] = a;
+        swp[(int64_t)fi * NB + j] = make_int2(kk, kp);  // replayed on the update rows by k_l21
       }
-      cl.sync();  // copies done before the tables change and column k is rewritten
+      csync();  // copies done before the tables change and column k is rewritten
       if (tid == 0) {
         int ga = p2s[kk - k0], gb = p2s[kp - k0];
         p2s[kk - k0] = gb;
@@ -640,8 +647,23 @@ __global__ void __launch_bounds__(512)
     if (singular) {
       if (rank == 0 && tid == 0 && st_info[f] == 0) st_info[f] = k + 1;
     }
+    if (tid == 0) {  // fp64 inverse of the pivot block, computed once
+      if (kstep == 1) {
+        s_inv[0] = (d11.x == 0.0 && d11.y == 0.0) ? make_double2(0, 0) : zdiv1(d11);
+      } else {
+        double2 det = zmul(d11, d22), d2 = zmul(d21, d21);
+        det.x -= d2.x;
+        det.y -= d2.y;
+        double2 idet = zdiv1(det);
+        s_inv[0] = zmul(d22, idet);
+        s_inv[2] = zmul(d11, idet);
+        double2 t21 = zmul(d21, idet);
+        s_inv[1] = make_double2(-t21.x, -t21.y);
+      }
+    }
+    __syncthreads();
     if (kstep == 1) {
-      double2 di = (d11.x == 0.0 && d11.y == 0.0) ? make_double2(0, 0) : zdiv1(d11);
+      const double2 di = s_inv[0];
       cx<T> dinv = from_d<T>(di);
       const cx<T> *src = use_r ? wr : wk;
       for (int q = tid; q < ns; q += nth) {
@@ -653,8 +675,8 @@ __global__ void __launch_bounds__(512)
         else F[k + (int64_t)k * ld] = from_d<T>(d11);
       }
       if (tid == 0) {
-        Dd[j] = d11;
-        Do[j] = make_double2(0, 0);
+        Dd[j] = from_d<T>(d11);
+        Do[j] = mk<T>(0, 0);
         Dz[j] = 1;
         if (colmax > 0) s_minpiv = fmin(s_minpiv, (fabs(d11.x) + fabs(d11.y)) / colmax);
       }
@@ -664,13 +686,7 @@ __global__ void __launch_bounds__(512)
         ps[k] = 1;
       }
     } else {
-      double2 det = zmul(d11, d22), d2 = zmul(d21, d21);
-      det.x -= d2.x;
-      det.y -= d2.y;
-      double2 idet = zdiv1(det);
-      double2 i11 = zmul(d22, idet), i22 = zmul(d11, idet), i21 = zmul(d21, idet);
-      i21.x = -i21.x;
-      i21.y = -i21.y;
+      const double2 i11 = s_inv[0], i21 = s_inv[1], i22 = s_inv[2];
       cx<T> a11 = from_d<T>(i11), a21 = from_d<T>(i21), a22 = from_d<T>(i22);
       for (int q = tid; q < ns; q += nth) {
         int i = spos[q];
@@ -696,10 +712,10 @@ __global__ void __launch_bounds__(512)
         Ls[(size_t)q * LSTR + j + 1] = l2;
       }
       if (tid == 0) {
-        Dd[j] = d11;
-        Dd[j + 1] = d22;
-        Do[j] = d21;
-        Do[j + 1] = d21;
+        Dd[j] = from_d<T>(d11);
+        Dd[j + 1] = from_d<T>(d22);
+        Do[j] = from_d<T>(d21);
+        Do[j + 1] = from_d<T>(d21);
         Dz[j] = 2;
         Dz[j + 1] = -2;
       }
@@ -712,7 +728,7 @@ __global__ void __launch_bounds__(512)
         ps[k + 1] = -2;
       }
     }
-    cl.sync();  // #3: L rows, tables and the global front are consistent for the next column
+    csync();  // #3: L rows, tables and the global front are consistent for the next column
     k += kstep;
     j += kstep;
   }
@@ -722,17 +738,15 @@ __global__ void __launch_bounds__(512)
     if (i < k) continue;
     const cx<T> *Lq = Ls + (size_t)q * LSTR;
     for (int t = 0; t < j; ++t) {
-      double2 l = to_d(Lq[t]), acc;
+      cx<T> l = Lq[t], acc;
       if (Dz[t] == 1) {
-        acc = zmul(l, Dd[t]);
+        acc = cmul(l, Dd[t]);
       } else if (Dz[t] == 2) {
-        double2 a = zmul(l, Dd[t]), b = zmul(to_d(Lq[t + 1]), Do[t]);
-        acc = make_double2(a.x + b.x, a.y + b.y);
+        acc = cfma(cmul(l, Dd[t]), Lq[t + 1], Do[t]);
       } else {
-        double2 a = zmul(to_d(Lq[t - 1]), Do[t]), b = zmul(l, Dd[t]);
-        acc = make_double2(a.x + b.x, a.y + b.y);
+        acc = cfma(cmul(Lq[t - 1], Do[t]), l, Dd[t]);
       }
-      W[i + (int64_t)t * ld] = from_d<T>(acc);
+      W[i + (int64_t)t * ld] = acc;
     }
   }
   if (rank == 0 && tid == 0) {
@@ -748,11 +762,99 @@ __global__ void __launch_bounds__(512)
     if (s_minpiv < 1e300) atomicMin(reinterpret_cast<unsigned long long *>(st_minpiv + f),
                                     (unsigned long long)__double_as_longlong(s_minpiv));
   }
-  cl.sync();  // no CTA leaves while others may still read its shared memory
+  csync();  // no CTA leaves while others may still read its shared memory
 }
 
 static size_t panel_cl_smem(int rcap, int mcap, size_t esz) {
   return (size_t)rcap * LSTR * esz + 2 * (size_t)rcap * esz + (size_t)rcap * 4 + (size_t)mcap * 4;
+}
+
+// Update rows of the panel's columns (rows p..m-1), Algorithm 1's triangular
+// solve: replay the panel's interchanges on the row, then w = a L11^{-T}
+// (forward substitution with the panel's unit-lower block), L21 = w D^{-1};
+// L21 goes to the front, w (= L21 D) to the workspace for the trailing update.
+// One thread per update row, all fronts of the level.
+template <typename T>
+__global__ void __launch_bounds__(128) k_l21(const int32_t *__restrict__ lvl, FrontTab ft,
+                                             const int64_t *__restrict__ wofs, cx<T> *__restrict__ arena,
+                                             cx<T> *__restrict__ Wbuf, const double2 *__restrict__ dinv_d,
+                                             const double2 *__restrict__ dinv_o, const int8_t *__restrict__ psize,
+                                             const int32_t *__restrict__ st_k0, const int32_t *__restrict__ st_kb,
+                                             const int2 *__restrict__ swp, double *__restrict__ flop_cnt) {
+  const int fi = blockIdx.y;
+  const int f = lvl[fi];
+  const int kb = st_kb[f];
+  if (kb == 0) return;
+  const int m = ft.m[f], p = ft.p[f];
+  const int r = p + blockIdx.x * blockDim.x + threadIdx.x;
+  if (p + (int)(blockIdx.x * blockDim.x) >= m) return;  // uniform per CTA
+  const int k0 = st_k0[f] - kb;
+  cx<T> *F = arena + ft.off[f];
+  cx<T> *W = Wbuf + wofs[fi];
+  const int64_t ld = m;
+  __shared__ cx<T> L11[NB][NB + 1];
+  __shared__ cx<T> Di[NB], Do[NB];
+  __shared__ int Dz[NB];
+  __shared__ int2 sw[NB];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    int a = e % NB, b = e / NB;
+    L11[a][b] = (a < kb && b < a) ? F[k0 + a + (int64_t)(k0 + b) * ld] : mk<T>(0, 0);
+  }
+  if (threadIdx.x < NB) {
+    int t = threadIdx.x;
+    sw[t] = t < kb ? swp[(int64_t)fi * NB + t] : make_int2(-1, -1);
+    if (t < kb) {
+      Di[t] = from_d<T>(dinv_d[ft.piv[f] + k0 + t]);
+      Do[t] = from_d<T>(dinv_o[ft.piv[f] + k0 + t]);
+      Dz[t] = psize[ft.piv[f] + k0 + t];
+    }
+  }
+  __syncthreads();
+  // 2x2 couplings inside L11 are zero by construction (stored as 0)
+  if (r < m) {
+    // replay the panel's interchanges on this row (columns kk <-> kp, in order;
+    // the thread owns the row, so plain loads/stores keep the order)
+    for (int t = 0; t < kb; ++t) {
+      int2 q = sw[t];
+      if (q.x < 0) continue;
+      cx<T> *fa = F + r + (int64_t)q.x * ld, *fb = F + r + (int64_t)q.y * ld;
+      cx<T> va = *fa, vb = *fb;
+      *fa = vb;
+      *fb = va;
+    }
+    cx<T> a[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) a[t] = t < kb ? F[r + (int64_t)(k0 + t) * ld] : mk<T>(0, 0);
+    // forward substitution: w[t] = a[t] - sum_{u<t} L11[t][u] w[u]
+#pragma unroll
+    for (int t = 1; t < NB; ++t) {
+      if (t < kb) {
+        cx<T> acc = a[t];
+#pragma unroll
+        for (int u = 0; u < NB - 1; ++u)
+          if (u < t) acc = cfms(acc, L11[t][u], a[u]);
+        a[t] = acc;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      if (t < kb) {
+        W[r + (int64_t)t * ld] = a[t];
+        cx<T> l;
+        if (Dz[t] == 1) {
+          l = cmul(a[t], Di[t]);
+        } else if (Dz[t] == 2) {
+          l = cfma(cmul(a[t], Di[t]), a[min(t + 1, NB - 1)], Do[t]);
+        } else {
+          l = cfma(cmul(a[max(t - 1, 0)], Do[t]), a[t], Di[t]);
+        }
+        F[r + (int64_t)(k0 + t) * ld] = l;
+      }
+    }
+  }
+  if (flop_cnt && threadIdx.x == 0 && blockIdx.x == 0) {
+    atomicAdd(flop_cnt + 1, 8.0 * (double)(m - p) * (0.5 * kb * (kb - 1) + kb));
+  }
 }
 
 constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
@@ -778,22 +880,27 @@ static cudaError_t panel_attrs() {
 }
 
 // One panel step for the nf fronts listed at lvl.
+// One panel step for the nf fronts listed at lvl.  cs > 0: cluster panel on
+// the pivot rows (pmax = largest pivot block of the level) followed by k_l21
+// on the update rows (mmax = largest front); cs == 0: single-CTA panel over
+// all rows.
 template <typename T>
-static cudaError_t launch_panel(int cs, int mmax, int nf, const int32_t *lvl, FrontTab ft, const int64_t *wofs,
-                                cx<T> *arena, cx<T> *W, int32_t *perm, double2 *dd, double2 *dof, int8_t *ps,
-                                int32_t *k0, int32_t *kb, int32_t *info, double *minpiv, double *flops,
-                                cudaStream_t s) {
+static cudaError_t launch_panel(int cs, int pmax, int mmax, int nf, const int32_t *lvl, FrontTab ft,
+                                const int64_t *wofs, cx<T> *arena, cx<T> *W, int32_t *perm, double2 *dd,
+                                double2 *dof, int8_t *ps, int32_t *k0, int32_t *kb, int32_t *info, double *minpiv,
+                                double *flops, int2 *swp, cudaStream_t s) {
   if (cs <= 0) {
     k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv, flops);
     return cudaGetLastError();
   }
   cudaError_t e = panel_attrs<T>();
   if (e != cudaSuccess) return e;
-  int rcap = (mmax + cs - 1) / cs;
+  int rcap = (pmax + cs - 1) / cs;
+  const int mcap = pmax;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nf * cs));
   cfg.blockDim = dim3(512);
-  cfg.dynamicSmemBytes = panel_cl_smem(rcap, mmax, sizeof(cx<T>));
+  cfg.dynamicSmemBytes = panel_cl_smem(rcap, mcap, sizeof(cx<T>));
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -802,8 +909,15 @@ static cudaError_t launch_panel(int cs, int mmax, int nf, const int32_t *lvl, Fr
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_panel_cl<T>, lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv,
-                            flops, rcap, mmax);
+  e = cudaLaunchKernelEx(&cfg, k_panel_cl<T>, lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv,
+                         flops, swp, rcap, mcap);
+  if (e != cudaSuccess) return e;
+  if (mmax > 0) {
+    dim3 g((unsigned)std::max(1, (mmax + 127) / 128), (unsigned)nf);
+    k_l21<T><<<g, 128, 0, s>>>(lvl, ft, wofs, arena, W, dd, dof, ps, k0, kb, swp, flops);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 // ------------------------------------------------------------ trailing update
@@ -1455,6 +1569,8 @@ struct DeviceState {
   std::vector<int> ea_grid;                   // per pass: grid.x (tiles) upper bound
   std::vector<int> level_maxm, pass_maxn;
   std::vector<int> level_gemm_upd, level_gemm_piv;  // solve GEMM grid.x / (RHS tiles), max over the level
+  int2 *swp = nullptr;           // per level position: interchanges of the current panel (NB each)
+  std::vector<int> level_maxp;   // largest pivot block per level
   int32_t *nsplit = nullptr;     // per level position: row splits of k_bwd_gemm
   int64_t *part_off = nullptr;   // per level position: partial-buffer offset (units of r)
   int64_t part_rows = 0;         // max over levels of sum(nsplit * p)
@@ -1598,6 +1714,11 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(dalloc(d, &d->st_info, nsn));
   CUDA_TRY(dalloc(d, &d->st_minpiv, nsn));
   CUDA_TRY(dalloc(d, &d->flop_cnt, 2));
+  CUDA_TRY(dalloc(d, &d->swp, (size_t)nsn * NB));
+  d->level_maxp.assign(P.n_levels, 0);
+  for (int l = 0; l < P.n_levels; ++l)
+    for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i)
+      d->level_maxp[l] = std::max(d->level_maxp[l], pp[P.level_fronts[i]]);
   d->prof.on = c.opt.profile != 0;
   d->prof.s = d->stream;
   d->solve_flops_per_rhs = 0;
@@ -1683,9 +1804,10 @@ static int factor_t(Ctx &c) {
     for (int stp = 0; stp < d->level_steps[l]; ++stp) {
       {
         PROF_BEGIN(PC_PANEL);
-        int cs = c.opt.panel_kernel == 1 ? 0 : panel_cluster_size(d->level_maxm[l], sizeof(cx<T>));
-        CUDA_TRY(launch_panel<T>(cs, d->level_maxm[l], nf, lvl, ft, wofs, arena, W, d->perm, d->dinv_d, d->dinv_o,
-                                 d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv, d->flop_cnt, s));
+        int cs = c.opt.panel_kernel == 1 ? 0 : panel_cluster_size(d->level_maxp[l], sizeof(cx<T>));
+        CUDA_TRY(launch_panel<T>(cs, d->level_maxp[l], d->level_maxm[l], nf, lvl, ft, wofs, arena, W, d->perm,
+                                 d->dinv_d, d->dinv_o, d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv,
+                                 d->flop_cnt, d->swp + (int64_t)P.level_ptr[l] * NB, s));
         PROF_END(PC_PANEL);
       }
       {
@@ -2016,6 +2138,7 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
   cx<double> *W = nullptr;
   DTRY(dalloc(&tmp, &W, (size_t)batch * m * NB));
   int32_t *pv = nullptr, *k0 = nullptr, *kb = nullptr;
+  int2 *swp = nullptr;
   double2 *dd = nullptr, *dof = nullptr;
   int8_t *ps = nullptr;
   double *mp = nullptr;
@@ -2026,6 +2149,7 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
   DTRY(dalloc(&tmp, &k0, batch));
   DTRY(dalloc(&tmp, &kb, batch));
   DTRY(dalloc(&tmp, &mp, batch));
+  DTRY(dalloc(&tmp, &swp, (size_t)batch * NB));
   DTRY(cudaMemsetAsync(k0, 0, batch * sizeof(int32_t), s));
   DTRY(cudaMemsetAsync(kb, 0, batch * sizeof(int32_t), s));
   DTRY(cudaMemsetAsync(info, 0, batch * sizeof(int32_t), s));
@@ -2035,9 +2159,9 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
   int steps = (p + NB - 2) / (NB - 1);
   cx<double> *arena = (cx<double> *)A;
   for (int stp = 0; stp < steps; ++stp) {
-    int cs = panel_kernel == 1 ? 0 : panel_cluster_size(m, sizeof(cx<double>));
-    DTRY(launch_panel<double>(cs, m, batch, tmp.lvl_fronts, ft, tmp.wofs, arena, W, pv, dd, dof, ps, k0, kb, info,
-                              mp, nullptr, s));
+    int cs = panel_kernel == 1 ? 0 : panel_cluster_size(p, sizeof(cx<double>));
+    DTRY(launch_panel<double>(cs, p, m, batch, tmp.lvl_fronts, ft, tmp.wofs, arena, W, pv, dd, dof, ps, k0, kb, info,
+                              mp, nullptr, swp, s));
     int cmin = std::min(p, (stp + 1) * (NB - 1));
     int nt = (m + UT - 1) / UT - cmin / UT;
     dim3 g(std::max(1, nt * (nt + 1) / 2), batch);
@@ -2082,7 +2206,7 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
 struct NoallocLayout {
-  size_t f_m, f_p, f_parent, lvl, f_off, f_piv, f_zero, wofs, W, pv, dd, dof, k0, kb, mp, ps, total;
+  size_t f_m, f_p, f_parent, lvl, f_off, f_piv, f_zero, wofs, W, pv, dd, dof, k0, kb, mp, ps, swp, total;
 };
 static NoallocLayout noalloc_layout(int m, int p, int batch) {
   NoallocLayout L{};
@@ -2109,6 +2233,7 @@ static NoallocLayout noalloc_layout(int m, int p, int batch) {
   L.kb = take(4 * b);
   L.mp = take(8 * b);
   L.ps = take(b * pp);
+  L.swp = take(8 * b * NB);
   L.total = o;
   return L;
 }
@@ -2191,11 +2316,12 @@ static int dense_ldlt_noalloc(int m, int p, int batch, double *A, int32_t *perm,
                         const_cast<int64_t *>(ft.piv), const_cast<int64_t *>(ft.soff), wofs, k0, kb, info, mp, pv);
   if (cudaGetLastError() != cudaSuccess) return D3M_ECUDA;
   const int steps = (p + NB - 2) / (NB - 1);
-  const int cs = panel_cluster_size(m, sizeof(cx<double>));
+  const int cs = panel_cluster_size(p, sizeof(cx<double>));
   cx<double> *arena = reinterpret_cast<cx<double> *>(A);
+  int2 *swp = reinterpret_cast<int2 *>(base + Lo.swp);
   for (int stp = 0; stp < steps; ++stp) {
-    if (launch_panel<double>(cs, m, batch, lvl, ft, wofs, arena, W, pv, dd, dof, ps, k0, kb, info, mp, nullptr, s) !=
-        cudaSuccess)
+    if (launch_panel<double>(cs, p, m, batch, lvl, ft, wofs, arena, W, pv, dd, dof, ps, k0, kb, info, mp, nullptr,
+                             swp, s) != cudaSuccess)
       return D3M_ECUDA;
     int cmin = std::min(p, (stp + 1) * (NB - 1));
     int nt = (m + UT - 1) / UT - cmin / UT;
@@ -2308,3 +2434,4 @@ extern "C" int d3m_dense_ldlt(int32_t m, int32_t p, int32_t batch, double *A, in
   if (rc) fprintf(stderr, "d3m_dense_ldlt: %s\n", err.c_str());
   return rc;
 }
+
