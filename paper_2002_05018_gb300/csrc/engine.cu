@@ -146,7 +146,67 @@ __global__ void __launch_bounds__(256) k_extend_add(const int32_t *__restrict__ 
   }
 }
 
+// ------------------------------------------------------------ reciprocal
+// 1/s for s > 0 in fp64 by Newton-Raphson from an fp32 seed: r <- r (2 - s r)
+// doubles the correct bits per step (24 -> 48 -> 96), so two steps reach
+// fp64 accuracy with a handful of fp64 FMAs instead of a full fp64 divide.
+// Outside the fp32 range the plain fp64 division is used.
+__device__ __forceinline__ double recip_nr(double s) {
+  if (!(s > 1e-30 && s < 1e30)) return 1.0 / s;
+  double r = (double)(1.0f / (float)s);
+  r = r * fma(-s, r, 2.0);
+  r = r * fma(-s, r, 2.0);
+  return r;
+}
+__device__ __forceinline__ double2 zinv_nr(double2 a) {  // 1 / a, a != 0
+  double rs = recip_nr(fma(a.x, a.x, a.y * a.y));
+  return make_double2(a.x * rs, -a.y * rs);
+}
+
 // ------------------------------------------------------------ block reductions
+// Arg-max in the factor precision T (magnitudes |Re|+|Im| of T values),
+// lowest index on ties.
+template <typename T>
+struct ArgMaxT {
+  T v;
+  int i;
+};
+template <typename T>
+__device__ __forceinline__ ArgMaxT<T> amaxT(ArgMaxT<T> a, ArgMaxT<T> b) {
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+template <typename T>
+__device__ __forceinline__ T cabs1T(cx<T> a) {
+  return fabs(a.re) + fabs(a.im);
+}
+template <typename T>
+__device__ ArgMaxT<T> block_argmaxT(ArgMaxT<T> x, ArgMaxT<T> *sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMaxT<T> y;
+    y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+    y.i = __shfl_down_sync(0xffffffffu, x.i, o);
+    x = amaxT(x, y);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    x = l < (int)(blockDim.x >> 5) ? sh[l] : ArgMaxT<T>{(T)-1, 0x7fffffff};
+    for (int o = 16; o > 0; o >>= 1) {
+      ArgMaxT<T> y;
+      y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+      y.i = __shfl_down_sync(0xffffffffu, x.i, o);
+      x = amaxT(x, y);
+    }
+    if (l == 0) sh[0] = x;
+  }
+  __syncthreads();
+  ArgMaxT<T> r = sh[0];
+  __syncthreads();
+  return r;
+}
 struct ArgMax {
   double v;
   int i;
@@ -402,10 +462,11 @@ __global__ void __launch_bounds__(PANEL_THREADS)
 namespace cg = cooperative_groups;
 
 struct PanelBox {
-  double cmax;   // local max |w_i| over candidate rows
+  double cmax;   // local max |w_i| over candidate rows (factor precision, widened)
   int cidx;      // its logical row
   int has;       // 1 if this CTA owns the queried row(s)
   double2 v0, v1, v2;  // owner-published values (see use)
+  double2 vmax;  // the winning element itself (exact fp64 magnitude for the tests)
 };
 
 template <typename T>
@@ -451,7 +512,7 @@ __global__ void __launch_bounds__(512)
   __shared__ cx<T> Dd[NB], Do[NB];    // D of the panel's pivots: diag / 2x2 coupling
   __shared__ double2 s_inv[3];         // fp64 inverse of the current pivot block (one thread)
   __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
-  __shared__ ArgMax red[32];
+  __shared__ ArgMaxT<T> red[32];
   __shared__ double s_minpiv, s_cmac, bc_cmax;
   __shared__ int bc_imax;
   __shared__ double2 bc_v0, bc_v1;
@@ -464,6 +525,13 @@ __global__ void __launch_bounds__(512)
   }
   __syncthreads();
   if (CS > 1) cl.sync();
+  // original data of the column being processed, for the first two own slots,
+  // prefetched during the previous column's scale phase
+  cx<T> pre[2] = {mk<T>(0, 0), mk<T>(0, 0)};
+  {
+    int qi = 0;
+    for (int q = tid; q < ns && qi < 2; q += nth, ++qi) pre[qi] = F[spos[q] + (int64_t)k0 * ld];
+  }
   // a cluster of one synchronises like a plain block
   auto csync = [&]() {
     if (CS == 1)
@@ -497,27 +565,32 @@ __global__ void __launch_bounds__(512)
     // ---- (1) updated column k for own slots, local pivot search
     load_wrow(k, wrow);
     __syncthreads();
-    ArgMax loc{-1.0, 0x7fffffff};
-    for (int q = tid; q < ns; q += nth) {
-      int i = spos[q];
-      if (i < k) continue;
-      cx<T> acc = F[i + (int64_t)k * ld];
-      const cx<T> *Lq = Ls + (size_t)q * LSTR;
+    ArgMaxT<T> loc{(T)-1, 0x7fffffff};
+    {
+      int qi = 0;
+      for (int q = tid; q < ns; q += nth, ++qi) {
+        int i = spos[q];
+        if (i < k) continue;
+        cx<T> acc = qi < 2 ? pre[qi] : F[i + (int64_t)k * ld];
+        const cx<T> *Lq = Ls + (size_t)q * LSTR;
 #pragma unroll 8
-      for (int t = 0; t < NB - 1; ++t)
-        if (t < j) acc = cfms(acc, Lq[t], wrow[t]);
-      wk[q] = acc;
-      if (i > k && i < p) loc = amax(loc, ArgMax{cabs1(acc), i});
+        for (int t = 0; t < NB - 1; ++t)
+          if (t < j) acc = cfms(acc, Lq[t], wrow[t]);
+        wk[q] = acc;
+        if (i > k && i < p) loc = amaxT(loc, ArgMaxT<T>{cabs1T(acc), i});
+      }
     }
-    ArgMax cm = block_argmax(loc, red);
+    ArgMaxT<T> cm = block_argmaxT(loc, red);
     {
       int g = p2s[k - k0];
       int o = g / R;
       if (tid == 0) {
-        box[0].cmax = cm.v;
+        box[0].cmax = (double)cm.v;
         box[0].cidx = cm.i;
         box[0].has = o == rank;
         box[0].v0 = o == rank ? to_d(wk[g - o * R]) : make_double2(0, 0);
+        box[0].vmax = make_double2(0, 0);
+        if (cm.i < p) box[0].vmax = to_d(wk[p2s[cm.i - k0] - rank * R]);
       }
     }
     if (tid == 0) s_cmac += (double)(p - k) * (j + 1);
@@ -525,15 +598,17 @@ __global__ void __launch_bounds__(512)
     if (tid == 0) {
       double cmx = -1.0;
       int imx = 0x7fffffff;
-      double2 a = make_double2(0, 0);
+      double2 a = make_double2(0, 0), vm = make_double2(0, 0);
       for (int c = 0; c < CS; ++c) {
         const PanelBox *b = cl.map_shared_rank(&box[0], c);
-        ArgMax y = amax(ArgMax{cmx, imx}, ArgMax{b->cmax, b->cidx});
-        cmx = y.v;
-        imx = y.i;
+        if (b->cmax > cmx || (b->cmax == cmx && b->cidx < imx)) {
+          cmx = b->cmax;
+          imx = b->cidx;
+          vm = b->vmax;
+        }
         if (b->has) a = b->v0;
       }
-      bc_cmax = cmx;
+      bc_cmax = fabs(vm.x) + fabs(vm.y);  // exact fp64 magnitude of the winner
       bc_imax = imx;
       bc_v0 = a;
     }
@@ -554,7 +629,7 @@ __global__ void __launch_bounds__(512)
       // ---- (2) updated column imax for own slots
       load_wrow(imax, wrow2);
       __syncthreads();
-      ArgMax rl{-1.0, 0x7fffffff};
+      ArgMaxT<T> rl{(T)-1, 0x7fffffff};
       int gi = p2s[imax - k0];
       int oi = gi / R;
       for (int q = tid; q < ns; q += nth) {
@@ -566,12 +641,16 @@ __global__ void __launch_bounds__(512)
         for (int t = 0; t < NB - 1; ++t)
           if (t < j) acc = cfms(acc, Lq[t], wrow2[t]);
         wr[q] = acc;
-        if (i != imax && i < p) rl = amax(rl, ArgMax{cabs1(acc), i});
+        if (i != imax && i < p) rl = amaxT(rl, ArgMaxT<T>{cabs1T(acc), i});
       }
-      ArgMax rm = block_argmax(rl, red);
+      ArgMaxT<T> rm = block_argmaxT(rl, red);
       if (tid == 0) {
-        box[1].cmax = rm.v;
         box[1].cidx = rm.i;
+        box[1].cmax = -1.0;
+        if (rm.i < p) {  // exact fp64 magnitude of the local winner
+          double2 v = to_d(wr[p2s[rm.i - k0] - rank * R]);
+          box[1].cmax = fabs(v.x) + fabs(v.y);
+        }
         box[1].has = oi == rank;
         box[1].v1 = oi == rank ? to_d(wk[gi - oi * R]) : make_double2(0, 0);  // w_k at row imax
         box[1].v2 = oi == rank ? to_d(wr[gi - oi * R]) : make_double2(0, 0);  // w_r at row imax
@@ -649,12 +728,12 @@ __global__ void __launch_bounds__(512)
     }
     if (tid == 0) {  // fp64 inverse of the pivot block, computed once
       if (kstep == 1) {
-        s_inv[0] = (d11.x == 0.0 && d11.y == 0.0) ? make_double2(0, 0) : zdiv1(d11);
+        s_inv[0] = (d11.x == 0.0 && d11.y == 0.0) ? make_double2(0, 0) : zinv_nr(d11);
       } else {
         double2 det = zmul(d11, d22), d2 = zmul(d21, d21);
         det.x -= d2.x;
         det.y -= d2.y;
-        double2 idet = zdiv1(det);
+        double2 idet = zinv_nr(det);
         s_inv[0] = zmul(d22, idet);
         s_inv[2] = zmul(d11, idet);
         double2 t21 = zmul(d21, idet);
@@ -678,7 +757,7 @@ __global__ void __launch_bounds__(512)
         Dd[j] = from_d<T>(d11);
         Do[j] = mk<T>(0, 0);
         Dz[j] = 1;
-        if (colmax > 0) s_minpiv = fmin(s_minpiv, (fabs(d11.x) + fabs(d11.y)) / colmax);
+        if (colmax > 0) s_minpiv = fmin(s_minpiv, (double)((float)(fabs(d11.x) + fabs(d11.y)) / (float)colmax));
       }
       if (rank == 0 && tid == 0) {
         dd[k] = di;
@@ -726,6 +805,13 @@ __global__ void __launch_bounds__(512)
         dof[k + 1] = i21;
         ps[k] = 2;
         ps[k + 1] = -2;
+      }
+    }
+    if (k + kstep < p) {  // prefetch the next column (this step's interchanges are done)
+      int qi = 0;
+      for (int q = tid; q < ns && qi < 2; q += nth, ++qi) {
+        int i = spos[q];
+        if (i >= k + kstep) pre[qi] = F[i + (int64_t)(k + kstep) * ld];
       }
     }
     csync();  // #3: L rows, tables and the global front are consistent for the next column
