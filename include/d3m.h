@@ -124,6 +124,7 @@ typedef struct {
   double ms_assemble, ms_panel, ms_update;        /* summed kernel durations */
   double ms_fwd, ms_bwd, ms_residual;             /* last solve, all refinement steps */
   double solve_flops;     /* real flops of the last solve's substitutions */
+  double ms_inverse;      /* factor: building L11^{-1} of every front (profile=1) */
 } d3m_stats;
 
 /*

@@ -1312,7 +1312,8 @@ __global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ l
 constexpr int GR = 64, GC = 32, GK = 16;
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_gemm(const int32_t *__restrict__ lvl, FrontTab ft,
-                                                  const cx<T> *__restrict__ arena, cx<T> *__restrict__ Y, int r) {
+                                                  const cx<T> *__restrict__ arena, cx<T> *__restrict__ Y,
+                                                  const cx<T> *__restrict__ Ysrc, int r) {
   const int f = lvl[blockIdx.y];
   const int m = ft.m[f], p = ft.p[f];
   const int nrt = (m - p + GR - 1) / GR, nct = (r + GC - 1) / GC;
@@ -1337,7 +1338,7 @@ __global__ void __launch_bounds__(256) k_fwd_gemm(const int32_t *__restrict__ lv
     for (int e = threadIdx.x; e < GK * GC; e += 256) {
       int cc = e % GC, kk = e / GC;
       int k = k0 + kk, c = c0 + cc;
-      Ys[kk][cc] = (k < p && c < r) ? Yf[(int64_t)k * r + c] : mk<T>(0, 0);
+      Ys[kk][cc] = (k < p && c < r) ? Ysrc[ft.yoff[f] * r + (int64_t)k * r + c] : mk<T>(0, 0);
     }
     __syncthreads();
 #pragma unroll 4
@@ -1429,6 +1430,195 @@ __global__ void __launch_bounds__(256) k_bwd_gemm(const int32_t *__restrict__ lv
       int c = c0 + tc + 16 * b;
       if (c < r) pt[(int64_t)k * r + c] = acc[a][b];
     }
+  }
+}
+
+// ------------------------------------------------------------ batched tile GEMM
+// C = alpha op(A) B (+ C), over a list of items of all fronts of a level.
+// Operands are addressed by (row stride, column stride) into one of four
+// buffers, so column-major fronts, row-major RHS blocks and transposed views
+// all fit.  Triangular operands (stored with explicit zeros) bound the k
+// range per output tile: mode 1 A lower (k <= i), 2 B lower (k >= j), 3 A
+// upper (k >= i).
+struct GemmItem {
+  int64_t a, b, c;
+  int32_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
+  int32_t M, N, K, mode, abuf, bbuf, cbuf, beta;
+  float alpha;
+  int32_t tile0;
+};
+constexpr int TG = 64, TGK = 16;
+template <typename T>
+__global__ void __launch_bounds__(256) k_tgemm(const GemmItem *__restrict__ items, int nitems, int ntiles,
+                                               cx<T> *b0, cx<T> *b1, cx<T> *b2, cx<T> *b3) {
+  const int t = blockIdx.x;
+  if (t >= ntiles) return;
+  int lo = 0, hi = nitems - 1;  // last item with tile0 <= t
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (items[mid].tile0 <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmItem it = items[lo];
+  cx<T> *bufs[4] = {b0, b1, b2, b3};
+  const cx<T> *A = bufs[it.abuf] + it.a;
+  const cx<T> *B = bufs[it.bbuf] + it.b;
+  cx<T> *C = bufs[it.cbuf] + it.c;
+  const int ntm = (it.M + TG - 1) / TG;
+  const int ti = t - it.tile0, tm = ti % ntm, tn = ti / ntm;
+  const int i0 = tm * TG, j0 = tn * TG;
+  int klo = 0, khi = it.K;
+  if (it.mode == 1) khi = min(it.K, i0 + TG);
+  if (it.mode == 2) klo = j0;
+  if (it.mode == 3) klo = i0;
+  __shared__ cx<T> As[TGK][TG + 1];
+  __shared__ cx<T> Bs[TGK][TG + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  cx<T> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = mk<T>(0, 0);
+  for (int k0 = klo; k0 < khi; k0 += TGK) {
+    for (int e = threadIdx.x; e < TGK * TG; e += 256) {
+      int x = e % TG, kk = e / TG;
+      int i = i0 + x, k = k0 + kk;
+      As[kk][x] = (i < it.M && k < khi) ? A[(int64_t)i * it.a_rs + (int64_t)k * it.a_cs] : mk<T>(0, 0);
+    }
+    for (int e = threadIdx.x; e < TGK * TG; e += 256) {
+      int x = e % TG, kk = e / TG;
+      int j = j0 + x, k = k0 + kk;
+      Bs[kk][x] = (j < it.N && k < khi) ? B[(int64_t)k * it.b_rs + (int64_t)j * it.b_cs] : mk<T>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TGK; ++kk) {
+      cx<T> av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = cfma(acc[a][b], av[a], bv[b]);
+    }
+    __syncthreads();
+  }
+  const T al = (T)it.alpha;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int i = i0 + ty + 16 * a;
+    if (i >= it.M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int j = j0 + tx + 16 * b;
+      if (j >= it.N) continue;
+      cx<T> *d = C + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
+      cx<T> v = mk<T>(al * acc[a][b].re, al * acc[a][b].im);
+      if (it.beta) {
+        v.re += d->re;
+        v.im += d->im;
+      }
+      *d = v;
+    }
+  }
+}
+
+// Inverse of each 32x32 unit-lower diagonal block of L11 (2x2 couplings are
+// zero in L), written to the front's L11^{-1} (p x p, column-major, zeros
+// above the diagonal).  One CTA per (front, block); thread j builds column j.
+template <typename T>
+__global__ void __launch_bounds__(32) k_trinv_diag(const int32_t *__restrict__ lvl, FrontTab ft,
+                                                   const cx<T> *__restrict__ arena, const int64_t *__restrict__ loff,
+                                                   cx<T> *__restrict__ Linv) {
+  const int f = lvl[blockIdx.y];
+  const int p = ft.p[f], m = ft.m[f];
+  const int b0 = blockIdx.x * 32;
+  if (b0 >= p) return;
+  const int nb = min(32, p - b0);
+  const cx<T> *F = arena + ft.off[f];
+  cx<T> *X = Linv + loff[blockIdx.y];
+  __shared__ cx<T> Ls[32][33];
+  __shared__ cx<T> Xs[32][33];
+  const int jj = threadIdx.x;
+  for (int a = 0; a < 32; ++a)
+    Ls[a][jj] = (a < nb && jj < nb && a > jj) ? F[b0 + a + (int64_t)(b0 + jj) * m] : mk<T>(0, 0);
+  __syncthreads();
+  // column jj: X[jj][jj] = 1, X[i][jj] = -sum_{k=jj}^{i-1} L[i][k] X[k][jj]
+  for (int a = 0; a < 32; ++a) Xs[a][jj] = a == jj ? mk<T>(1, 0) : mk<T>(0, 0);
+  for (int i = jj + 1; i < nb; ++i) {
+    cx<T> acc = mk<T>(0, 0);
+    for (int k = jj; k < i; ++k) acc = cfma(acc, Ls[i][k], Xs[k][jj]);
+    Xs[i][jj] = mk<T>(-acc.re, -acc.im);
+  }
+  __syncthreads();
+  for (int a = 0; a < nb; ++a)
+    if (jj < nb) X[b0 + a + (int64_t)(b0 + jj) * p] = Xs[a][jj];
+}
+
+// z = D^{-1} y for the pivot rows (y in Y2, pivot order) -> zM
+template <typename T>
+__global__ void k_fwd_dinv(const int32_t *__restrict__ lvl, FrontTab ft, const double2 *__restrict__ dinv_d,
+                           const double2 *__restrict__ dinv_o, const int8_t *__restrict__ psize,
+                           const cx<T> *__restrict__ Y2, cx<T> *__restrict__ zM, int r) {
+  const int f = lvl[blockIdx.y];
+  const int p = ft.p[f];
+  const cx<T> *Yf = Y2 + ft.yoff[f] * r;
+  const double2 *di = dinv_d + ft.piv[f];
+  const double2 *dof = dinv_o + ft.piv[f];
+  const int8_t *ps = psize + ft.piv[f];
+  const int64_t st = ft.start[f];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)p * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(e / r), c = (int)(e % r);
+    cx<T> z = cmul(Yf[(int64_t)k * r + c], from_d<T>(di[k]));
+    int sz = ps[k];
+    if (sz == 2 || sz == -2) {
+      int o = sz == 2 ? k + 1 : k - 1;
+      z = cfma(z, Yf[(int64_t)o * r + c], from_d<T>(dof[k]));
+    }
+    zM[(st + k) * r + c] = z;
+  }
+}
+
+// w = z - sum_s part_s into Yf[0:p] (pivot order)
+template <typename T>
+__global__ void k_bwd_w(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ nsplit,
+                        const int64_t *__restrict__ part_off, const cx<T> *__restrict__ part,
+                        const cx<T> *__restrict__ zM, cx<T> *__restrict__ Y, int r) {
+  const int f = lvl[blockIdx.y];
+  const int p = ft.p[f];
+  cx<T> *Yf = Y + ft.yoff[f] * r;
+  const int S = nsplit[blockIdx.y];
+  const cx<T> *pt = part + part_off[blockIdx.y] * r;
+  const int64_t st = ft.start[f];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)p * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(e / r), c = (int)(e % r);
+    cx<T> w = zM[(st + k) * r + c];
+    for (int q = 0; q < S; ++q) {
+      cx<T> u = pt[((int64_t)q * p + k) * r + c];
+      w.re -= u.re;
+      w.im -= u.im;
+    }
+    Yf[(int64_t)k * r + c] = w;
+  }
+}
+
+// x (pivot order, in Y2) -> xM at the original positions
+template <typename T>
+__global__ void k_bwd_out(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ perm,
+                          const cx<T> *__restrict__ Y2, cx<T> *__restrict__ xM, int r) {
+  const int f = lvl[blockIdx.y];
+  const int p = ft.p[f];
+  const cx<T> *Yf = Y2 + ft.yoff[f] * r;
+  const int32_t *pv = perm + ft.piv[f];
+  const int64_t st = ft.start[f];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)p * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(e / r), c = (int)(e % r);
+    xM[(st + pv[k]) * r + c] = Yf[(int64_t)k * r + c];
   }
 }
 
@@ -1567,7 +1757,7 @@ __global__ void k_residual(int64_t n, const int64_t *__restrict__ ptr, const int
 // ------------------------------------------------------------ profiling
 // CUDA events around each launch group, on the launching stream; durations
 // are summed per kernel class after the stream is synchronised.
-enum ProfClass { PC_ASSEMBLE = 0, PC_PANEL, PC_UPDATE, PC_FWD, PC_BWD, PC_RESID, PC_N };
+enum ProfClass { PC_ASSEMBLE = 0, PC_PANEL, PC_UPDATE, PC_FWD, PC_BWD, PC_RESID, PC_INV, PC_N };
 struct Profiler {
   bool on = false;
   cudaStream_t s = nullptr;
@@ -1619,6 +1809,7 @@ struct Profiler {
 // ------------------------------------------------------------ device state
 struct DeviceState {
   Profiler prof;
+  int64_t inv_launches = 0;
   double *flop_cnt = nullptr;  // [0] trailing-update flops, [1] panel flops
   int64_t launches = 0;
   double solve_flops_per_rhs = 0;
@@ -1655,6 +1846,17 @@ struct DeviceState {
   std::vector<int> ea_grid;                   // per pass: grid.x (tiles) upper bound
   std::vector<int> level_maxm, pass_maxn;
   std::vector<int> level_gemm_upd, level_gemm_piv;  // solve GEMM grid.x / (RHS tiles), max over the level
+  // explicit L11^{-1} of every front (p x p column-major), built after each level
+  void *linv = nullptr;
+  int64_t *linv_off = nullptr;                 // per level position
+  std::vector<int64_t> linv_off_h;
+  void *tmp_inv = nullptr;                     // doubling-stage temporaries
+  GemmItem *inv_items = nullptr;               // all factor-time doubling items
+  std::vector<std::vector<std::array<int, 4>>> inv_stage;  // per level: (item0, nitems, ntiles, unused)
+  GemmItem *sol_items = nullptr;               // solve items for sol_r RHS (fwd then bwd per level)
+  std::vector<std::array<int, 6>> sol_lvl;     // per level: fwd (item0, n, tiles), bwd (item0, n, tiles)
+  int sol_r = 0;
+  void *Y2 = nullptr;
   int2 *swp = nullptr;           // per level position: interchanges of the current panel (NB each)
   std::vector<int> level_maxp;   // largest pivot block per level
   int32_t *nsplit = nullptr;     // per level position: row splits of k_bwd_gemm
@@ -1783,6 +1985,74 @@ static int dev_init(Ctx &c) {
     }
   }
   CUDA_TRY(upload(d, &d->wofs, wofs));
+  {
+    // L11^{-1} storage (level-major) and the factor-time doubling stages:
+    // for blocks A = [i0, i0+s), C = [i0+s, i0+2s) of the pivot range,
+    //   T1 = L[C, A] A^{-1}  (mode 2),   L^{-1}[C, A] = -C^{-1} T1  (mode 1)
+    std::vector<GemmItem> items;
+    d->linv_off_h.assign(nsn, 0);
+    int64_t lo = 0, tmax = 0;
+    for (int i = 0; i < (int)nsn; ++i) {
+      int s = P.level_fronts[i];
+      d->linv_off_h[i] = lo;
+      lo += (int64_t)pp[s] * pp[s];
+    }
+    d->inv_stage.assign(P.n_levels, {});
+    for (int l = 0; l < P.n_levels; ++l) {
+      int pmax = 0;
+      for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) pmax = std::max(pmax, pp[P.level_fronts[i]]);
+      for (int sz = 32; sz < pmax; sz *= 2) {
+        std::vector<GemmItem> g1, g2;
+        int64_t toff = 0;
+        int t1 = 0, t2 = 0;
+        for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+          int f = P.level_fronts[i];
+          int pf = pp[f], mf = m[f];
+          int64_t lf = d->linv_off_h[i];
+          for (int i0 = 0; i0 + sz < pf; i0 += 2 * sz) {
+            int cs = std::min(sz, pf - i0 - sz);
+            GemmItem a{};
+            a.a = P.front_off[f] + (i0 + sz) + (int64_t)i0 * mf;  // L[C, A]
+            a.a_rs = 1; a.a_cs = mf;
+            a.b = lf + i0 + (int64_t)i0 * pf;                      // A^{-1}
+            a.b_rs = 1; a.b_cs = pf;
+            a.c = toff;                                            // T1 (cs x sz, column-major)
+            a.c_rs = 1; a.c_cs = cs;
+            a.M = cs; a.N = sz; a.K = sz; a.mode = 2;
+            a.abuf = 0; a.bbuf = 1; a.cbuf = 2; a.beta = 0; a.alpha = 1.f;
+            a.tile0 = t1;
+            t1 += ((cs + TG - 1) / TG) * ((sz + TG - 1) / TG);
+            g1.push_back(a);
+            GemmItem b{};
+            b.a = lf + (i0 + sz) + (int64_t)(i0 + sz) * pf;      // C^{-1}
+            b.a_rs = 1; b.a_cs = pf;
+            b.b = toff; b.b_rs = 1; b.b_cs = cs;                   // T1
+            b.c = lf + (i0 + sz) + (int64_t)i0 * pf;               // L^{-1}[C, A]
+            b.c_rs = 1; b.c_cs = pf;
+            b.M = cs; b.N = sz; b.K = cs; b.mode = 1;
+            b.abuf = 1; b.bbuf = 2; b.cbuf = 1; b.beta = 0; b.alpha = -1.f;
+            b.tile0 = t2;
+            t2 += ((cs + TG - 1) / TG) * ((sz + TG - 1) / TG);
+            g2.push_back(b);
+            toff += (int64_t)cs * sz;
+          }
+        }
+        tmax = std::max(tmax, toff);
+        if (g1.empty()) continue;
+        d->inv_stage[l].push_back({(int)items.size(), (int)g1.size(), t1, 0});
+        items.insert(items.end(), g1.begin(), g1.end());
+        d->inv_stage[l].push_back({(int)items.size(), (int)g2.size(), t2, 0});
+        items.insert(items.end(), g2.begin(), g2.end());
+      }
+    }
+    const size_t esz0 = c.opt.precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
+    CUDA_TRY(cudaMalloc(&d->linv, std::max<int64_t>(lo, 1) * esz0));
+    d->allocs.push_back(d->linv);
+    CUDA_TRY(cudaMalloc(&d->tmp_inv, std::max<int64_t>(tmax, 1) * esz0));
+    d->allocs.push_back(d->tmp_inv);
+    CUDA_TRY(upload(d, &d->inv_items, items));
+    CUDA_TRY(upload(d, &d->linv_off, d->linv_off_h));
+  }
   CUDA_TRY(upload(d, &d->nsplit, nsplit_h));
   CUDA_TRY(upload(d, &d->part_off, part_off_h));
   const size_t esz = c.opt.precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
@@ -1904,10 +2174,34 @@ static int factor_t(Ctx &c) {
       }
       nl += 2;
     }
+    // L11^{-1} of the level's fronts (mixed precision only: it turns every
+    // substitution into tile GEMMs; the fp64 path keeps the triangular-solve
+    // kernels, since on the fp64 pipe the extra p^3/6 flops cost more than
+    // the sequential blocks): diagonal 32-blocks, then doubling stages
+    if (sizeof(T) == 4) {
+      PROF_BEGIN(PC_INV);
+      cx<T> *Li = (cx<T> *)d->linv;
+      int lf = P.level_fronts[P.level_ptr[l]];
+      int ll = P.level_fronts[P.level_ptr[l + 1] - 1];
+      int64_t a0 = d->linv_off_h[P.level_ptr[l]];
+      int64_t pl = P.sn_end[ll] - P.sn_start[ll];
+      int64_t a1 = d->linv_off_h[P.level_ptr[l + 1] - 1] + pl * pl;
+      (void)lf;
+      CUDA_TRY(cudaMemsetAsync(Li + a0, 0, (a1 - a0) * sizeof(cx<T>), s));
+      dim3 gd((unsigned)((d->level_maxp[l] + 31) / 32), nf);
+      k_trinv_diag<T><<<gd, 32, 0, s>>>(lvl, ft, arena, d->linv_off + P.level_ptr[l], Li);
+      ++nl;
+      for (auto &st : d->inv_stage[l]) {
+        k_tgemm<T><<<st[2], 256, 0, s>>>(d->inv_items + st[0], st[1], st[2], arena, Li, (cx<T> *)d->tmp_inv,
+                                         nullptr);
+        ++nl;
+      }
+      PROF_END(PC_INV);
+    }
   }
   k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
   ++nl;
-  c.stats.launches_factor = nl;
+  c.stats.launches_factor = nl + d->inv_launches;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
   std::vector<int32_t> info(nsn);
@@ -1932,6 +2226,7 @@ static int factor_t(Ctx &c) {
     c.stats.ms_assemble = ms[PC_ASSEMBLE];
     c.stats.ms_panel = ms[PC_PANEL];
     c.stats.ms_update = ms[PC_UPDATE];
+    c.stats.ms_inverse = ms[PC_INV];
   }
   for (int64_t q = 0; q < nsn; ++q)
     if (info[q] != 0) {
@@ -1956,7 +2251,7 @@ static int ensure_rhs(Ctx &c, int r) {
   DeviceState *d = c.dev;
   if (d->cap >= r) return D3M_OK;
   const Plan &P = c.plan;
-  for (void *p : {d->bM, d->zM, d->xM, d->Y, d->part, (void *)d->fe, (void *)d->xe, (void *)d->re, (void *)d->ucm,
+  for (void *p : {d->bM, d->zM, d->xM, d->Y, d->Y2, d->part, (void *)d->fe, (void *)d->xe, (void *)d->re, (void *)d->ucm,
                   (void *)d->lam, (void *)d->norms})
     if (p) {
       cudaFree(p);
@@ -1972,6 +2267,7 @@ static int ensure_rhs(Ctx &c, int r) {
   CUDA_TRY(A(&d->zM, P.n_m * r * esz));
   CUDA_TRY(A(&d->xM, P.n_m * r * esz));
   CUDA_TRY(A(&d->Y, P.y_rows * r * esz));
+  CUDA_TRY(A(&d->Y2, P.y_rows * r * esz));
   CUDA_TRY(A(&d->part, std::max<int64_t>(d->part_rows, 1) * r * esz));
   CUDA_TRY(A((void **)&d->fe, P.n_edges * r * sizeof(double2)));
   CUDA_TRY(A((void **)&d->xe, P.n_edges * r * sizeof(double2)));
@@ -1980,6 +2276,51 @@ static int ensure_rhs(Ctx &c, int r) {
   CUDA_TRY(A((void **)&d->lam, (int64_t)P.lm_edge.size() * r * sizeof(double2)));
   CUDA_TRY(A((void **)&d->norms, 2 * r * sizeof(double)));
   d->cap = r;
+  return D3M_OK;
+}
+
+// Work lists of the solve GEMMs for r right-hand sides: per level, the
+// forward items Y2[0:p] = L11^{-1} Y[0:p] and the backward items
+// Y2[0:p] = L11^{-T} Y[0:p] (buffers: 1 = L^{-1}, 2 = Y, 3 = Y2).
+static int solve_items(Ctx &c, int r) {
+  DeviceState *d = c.dev;
+  if (d->sol_r == r && d->sol_items) return D3M_OK;
+  const Plan &P = c.plan;
+  std::vector<GemmItem> items;
+  d->sol_lvl.assign(P.n_levels, {});
+  for (int l = 0; l < P.n_levels; ++l) {
+    for (int dir = 0; dir < 2; ++dir) {
+      int first = (int)items.size(), tiles = 0;
+      for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+        int f = P.level_fronts[i];
+        int pf = (int)(P.sn_end[f] - P.sn_start[f]);
+        GemmItem g{};
+        g.a = d->linv_off_h[i];
+        if (dir == 0) {
+          g.a_rs = 1; g.a_cs = pf; g.mode = 1;
+        } else {
+          g.a_rs = pf; g.a_cs = 1; g.mode = 3;
+        }
+        g.b = P.y_off[f] * r; g.b_rs = r; g.b_cs = 1;
+        g.c = P.y_off[f] * r; g.c_rs = r; g.c_cs = 1;
+        g.M = pf; g.N = r; g.K = pf;
+        g.abuf = 1; g.bbuf = 2; g.cbuf = 3; g.beta = 0; g.alpha = 1.f;
+        g.tile0 = tiles;
+        tiles += ((pf + TG - 1) / TG) * ((r + TG - 1) / TG);
+        items.push_back(g);
+      }
+      d->sol_lvl[l][3 * dir + 0] = first;
+      d->sol_lvl[l][3 * dir + 1] = (int)items.size() - first;
+      d->sol_lvl[l][3 * dir + 2] = tiles;
+    }
+  }
+  if (d->sol_items) {
+    cudaFree(d->sol_items);
+    d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), (void *)d->sol_items), d->allocs.end());
+    d->sol_items = nullptr;
+  }
+  CUDA_TRY(upload(d, &d->sol_items, items));
+  d->sol_r = r;
   return D3M_OK;
 }
 
@@ -1992,8 +2333,10 @@ static int64_t apply_inverse(Ctx &c, int r) {
   FrontTab ft = tab(d);
   cx<T> *arena = (cx<T> *)d->arena;
   cx<T> *Y = (cx<T> *)d->Y;
-  constexpr int RC = sizeof(T) == 8 ? 8 : 8;
-  const int gx = (r + RC - 1) / RC;
+  cx<T> *Y2 = (cx<T> *)d->Y2;
+  cx<T> *Li = (cx<T> *)d->linv;
+  const bool use_inv = sizeof(T) == 4;  // L11^{-1} exists for the mixed factors only
+  constexpr int RC = 8;
   int64_t nl = 0;
   PROF_BEGIN(PC_FWD);
   for (int l = 0; l < P.n_levels; ++l) {
@@ -2010,12 +2353,22 @@ static int64_t apply_inverse(Ctx &c, int r) {
       k_fwd_ea<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, d->iperm, Y, r);
       ++nl;
     }
-    dim3 gs(gx, nf);
-    k_fwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->dinv_d, d->dinv_o, d->psize, Y, (cx<T> *)d->zM, r);
-    ++nl;
+    const cx<T> *ysrc;
+    if (use_inv) {
+      const auto &sl = d->sol_lvl[l];
+      k_tgemm<T><<<sl[2], 256, 0, s>>>(d->sol_items + sl[0], sl[1], sl[2], arena, Li, Y, Y2);
+      dim3 gdv((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
+      k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
+      ysrc = Y2;
+    } else {
+      dim3 gs((r + RC - 1) / RC, nf);
+      k_fwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->dinv_d, d->dinv_o, d->psize, Y, (cx<T> *)d->zM, r);
+      ysrc = Y;
+    }
+    nl += 2;
     if (d->level_gemm_upd[l] > 0) {
       dim3 gg(d->level_gemm_upd[l] * ((r + GC - 1) / GC), nf);
-      k_fwd_gemm<T><<<gg, 256, 0, s>>>(lvl, ft, arena, Y, r);
+      k_fwd_gemm<T><<<gg, 256, 0, s>>>(lvl, ft, arena, Y, ysrc, r);
       ++nl;
     }
   }
@@ -2031,10 +2384,19 @@ static int64_t apply_inverse(Ctx &c, int r) {
       k_bwd_gemm<T><<<gb, 256, 0, s>>>(lvl, ft, arena, d->sidx, (const cx<T> *)d->xM, po, (cx<T> *)d->part, r);
       ++nl;
     }
-    dim3 gs(gx, nf);
-    k_bwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->perm, d->psize, ns, po, (const cx<T> *)d->part, Y,
-                                          (const cx<T> *)d->zM, (cx<T> *)d->xM, r);
-    ++nl;
+    if (use_inv) {
+      dim3 gw((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
+      k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
+      const auto &sl = d->sol_lvl[l];
+      k_tgemm<T><<<sl[5], 256, 0, s>>>(d->sol_items + sl[3], sl[4], sl[5], arena, Li, Y, Y2);
+      k_bwd_out<T><<<gw, 256, 0, s>>>(lvl, ft, d->perm, Y2, (cx<T> *)d->xM, r);
+      nl += 3;
+    } else {
+      dim3 gs((r + RC - 1) / RC, nf);
+      k_bwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->perm, d->psize, ns, po, (const cx<T> *)d->part, Y,
+                                            (const cx<T> *)d->zM, (cx<T> *)d->xM, r);
+      ++nl;
+    }
   }
   PROF_END(PC_BWD);
   return nl;
@@ -2139,6 +2501,8 @@ int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, in
     return D3M_ESTATE;
   }
   int rc = ensure_rhs(c, nrhs);
+  if (rc) return rc;
+  rc = solve_items(c, nrhs);
   if (rc) return rc;
   rc = c.opt.precision == D3M_FP64 ? solve_t<double>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs, adjoint)
                                    : solve_t<float>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs, adjoint);

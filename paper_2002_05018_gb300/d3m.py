@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                [("n_2x2", ctypes.c_int64), ("min_pivot_ratio", ctypes.c_double),
                 ("launches_factor", ctypes.c_int64), ("launches_solve", ctypes.c_int64)] + \
                [(n, ctypes.c_double) for n in ("flops_update", "flops_panel", "ms_assemble", "ms_panel",
-                                               "ms_update", "ms_fwd", "ms_bwd", "ms_residual", "solve_flops")]
+                                               "ms_update", "ms_fwd", "ms_bwd", "ms_residual", "solve_flops",
+                                               "ms_inverse")]
 
     def asdict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
