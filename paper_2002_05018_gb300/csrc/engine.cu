@@ -1815,6 +1815,8 @@ struct DeviceState {
   double solve_flops_per_rhs = 0;
   int precision = 0;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;       // created here when the caller passed the legacy NULL stream
+  cudaEvent_t legacy_ev = nullptr;
   // plan tables
   int32_t *f_m = nullptr, *f_p = nullptr, *f_parent = nullptr;
   int64_t *f_off = nullptr, *f_piv = nullptr, *f_soff = nullptr, *f_start = nullptr, *f_y = nullptr;
@@ -1857,6 +1859,9 @@ struct DeviceState {
   std::vector<std::array<int, 6>> sol_lvl;     // per level: fwd (item0, n, tiles), bwd (item0, n, tiles)
   int sol_r = 0;
   void *Y2 = nullptr;
+  cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;  // captured substitution sweeps
+  int g_r = 0;
+  int64_t g_launches[2] = {0, 0};
   int2 *swp = nullptr;           // per level position: interchanges of the current panel (NB each)
   std::vector<int> level_maxp;   // largest pivot block per level
   int32_t *nsplit = nullptr;     // per level position: row splits of k_bwd_gemm
@@ -1904,6 +1909,14 @@ static int dev_init(Ctx &c) {
   c.dev = d;
   d->precision = c.opt.precision;
   d->stream = (cudaStream_t)c.opt.stream;
+  if (!d->stream) {
+    // CUDA graphs cannot be captured on the legacy NULL stream: work on an own
+    // non-blocking stream, ordered after the caller's legacy-stream work at
+    // every entry point (enter()) and synchronised before returning
+    CUDA_TRY(cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&d->legacy_ev, cudaEventDisableTiming));
+    d->own_stream = true;
+  }
   const int64_t nsn = (int64_t)P.sn_start.size();
   std::vector<int32_t> m(nsn), pp(nsn), par(nsn);
   std::vector<int64_t> soff(nsn);
@@ -2239,8 +2252,20 @@ static int factor_t(Ctx &c) {
   return D3M_OK;
 }
 
+// Order the library stream after the caller's legacy-stream work.
+static int enter(Ctx &c) {
+  DeviceState *d = c.dev;
+  if (d->own_stream) {
+    CUDA_TRY(cudaEventRecord(d->legacy_ev, 0));
+    CUDA_TRY(cudaStreamWaitEvent(d->stream, d->legacy_ev, 0));
+  }
+  return D3M_OK;
+}
+
 int dev_factor(Ctx &c) {
   int rc = dev_init(c);
+  if (rc) return rc;
+  rc = enter(c);
   if (rc) return rc;
   rc = c.opt.precision == D3M_FP64 ? factor_t<double>(c) : factor_t<float>(c);
   c.factored = rc == D3M_OK;
@@ -2263,6 +2288,12 @@ static int ensure_rhs(Ctx &c, int r) {
     if (e == cudaSuccess) d->allocs.push_back(*p);
     return e;
   };
+  for (cudaGraphExec_t *g : {&d->g_fwd, &d->g_bwd})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  d->g_r = 0;
   CUDA_TRY(A(&d->bM, P.n_m * r * esz));
   CUDA_TRY(A(&d->zM, P.n_m * r * esz));
   CUDA_TRY(A(&d->xM, P.n_m * r * esz));
@@ -2324,9 +2355,10 @@ static int solve_items(Ctx &c, int r) {
   return D3M_OK;
 }
 
-// One pass of the factored operator: xM = M^{-1} bM (in the factor precision)
+// One pass of the factored operator: xM = M^{-1} bM (in the factor precision).
+// dir: 1 forward sweep only, 2 backward sweep only, 3 both (eager).
 template <typename T>
-static int64_t apply_inverse(Ctx &c, int r) {
+static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
   const Plan &P = c.plan;
   DeviceState *d = c.dev;
   cudaStream_t s = d->stream;
@@ -2338,6 +2370,7 @@ static int64_t apply_inverse(Ctx &c, int r) {
   const bool use_inv = sizeof(T) == 4;  // L11^{-1} exists for the mixed factors only
   constexpr int RC = 8;
   int64_t nl = 0;
+  if (dir & 1) {
   PROF_BEGIN(PC_FWD);
   for (int l = 0; l < P.n_levels; ++l) {
     const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
@@ -2373,6 +2406,8 @@ static int64_t apply_inverse(Ctx &c, int r) {
     }
   }
   PROF_END(PC_FWD);
+  }
+  if (dir & 2) {
   PROF_BEGIN(PC_BWD);
   for (int l = P.n_levels - 1; l >= 0; --l) {
     const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
@@ -2399,7 +2434,59 @@ static int64_t apply_inverse(Ctx &c, int r) {
     }
   }
   PROF_END(PC_BWD);
+  }
   return nl;
+}
+
+// The two sweeps of apply_inverse captured as CUDA graphs for r right-hand
+// sides (rebuilt when r or the solve buffers change); each replay is timed
+// with events on the stream when profiling.
+template <typename T>
+static int graph_sweeps(Ctx &c, int r) {
+  DeviceState *d = c.dev;
+  if (d->g_r == r && d->g_fwd && d->g_bwd) return D3M_OK;
+  for (cudaGraphExec_t *g : {&d->g_fwd, &d->g_bwd})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  const bool prof = d->prof.on;
+  d->prof.on = false;  // no event nodes inside the graphs
+  for (int dir = 1; dir <= 2; ++dir) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      d->g_launches[dir - 1] = apply_inverse<T>(c, r, dir);
+      e = cudaStreamEndCapture(d->stream, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(dir == 1 ? &d->g_fwd : &d->g_bwd, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      d->prof.on = prof;
+      c.err = std::string("CUDA graph capture of the substitution failed: ") + cudaGetErrorString(e);
+      return D3M_ECUDA;
+    }
+  }
+  d->prof.on = prof;
+  d->g_r = r;
+  return D3M_OK;
+}
+
+template <typename T>
+static int64_t run_sweeps(Ctx &c, int r) {
+  DeviceState *d = c.dev;
+  cudaStream_t s = d->stream;
+  {
+    PROF_BEGIN(PC_FWD);
+    cudaGraphLaunch(d->g_fwd, s);
+    PROF_END(PC_FWD);
+  }
+  {
+    PROF_BEGIN(PC_BWD);
+    cudaGraphLaunch(d->g_bwd, s);
+    PROF_END(PC_BWD);
+  }
+  return d->g_launches[0] + d->g_launches[1];
 }
 
 static unsigned grid1(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
@@ -2428,7 +2515,11 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   int napply = 1;
   CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
   k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->fe, d->owner, (cx<T> *)d->bM, n, r);
-  nl += apply_inverse<T>(c, r);
+  {
+    int grc = graph_sweeps<T>(c, r);
+    if (grc) return grc;
+  }
+  nl += run_sweeps<T>(c, r);
   k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 0);
   if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 0);
   std::vector<double> nh(2 * r);
@@ -2456,7 +2547,7 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
     // correction: solve with the residual, accumulate in fp64
     CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
     k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->re, d->owner, (cx<T> *)d->bM, n, r);
-    nl += apply_inverse<T>(c, r) + 3;
+    nl += run_sweeps<T>(c, r) + 3;
     ++napply;
     k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 1);
     if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 1);
@@ -2504,6 +2595,8 @@ int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, in
   if (rc) return rc;
   rc = solve_items(c, nrhs);
   if (rc) return rc;
+  rc = enter(c);
+  if (rc) return rc;
   rc = c.opt.precision == D3M_FP64 ? solve_t<double>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs, adjoint)
                                    : solve_t<float>(c, rhs, ldb, x, ldx, nrhs, info, host_ptrs, adjoint);
   // keep the multipliers for d3m_structure(D3M_LAMBDA)
@@ -2528,6 +2621,8 @@ int dev_solve(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, in
 int dev_grad_eps(Ctx &c, const double *x, int64_t ldx, const double *y, int64_t ldy, int nrhs, double *grad) {
   int rc = dev_init(c);
   if (rc) return rc;
+  rc = enter(c);
+  if (rc) return rc;
   const Plan &P = c.plan;
   ElemMass Me;
   double S[12][12];
@@ -2543,6 +2638,13 @@ int dev_grad_eps(Ctx &c, const double *x, int64_t ldx, const double *y, int64_t 
 
 void dev_free(Ctx &c) {
   if (!c.dev) return;
+  for (cudaGraphExec_t g : {c.dev->g_fwd, c.dev->g_bwd})
+    if (g) cudaGraphExecDestroy(g);
+  if (c.dev->own_stream) {
+    cudaStreamSynchronize(c.dev->stream);
+    cudaStreamDestroy(c.dev->stream);
+    cudaEventDestroy(c.dev->legacy_ev);
+  }
   for (void *p : c.dev->allocs) cudaFree(p);
   delete c.dev;
   c.dev = nullptr;
