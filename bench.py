@@ -378,6 +378,10 @@ def main():
                 "solve_ms": round(r["solve_ms"], 3), "refine_steps": r["iters"],
                 "max_resid": r["max_resid"], "ms_per_step": round(r["step_ms"], 3),
                 "kernel_ms": {k: round(v, 3) for k, v in r["prof"].items() if k.startswith("ms_")},
+                "schedule": {"levels": r["stats"]["n_levels"],
+                             "tcgen05_update_levels": r["stats"]["tuned_levels_tc"],
+                             "doubled_cluster_levels": r["stats"]["tuned_levels_cs2"],
+                             "tuning_ms": round(r["stats"]["ms_tuning"], 1)},
                 "roofline": _roofline(r["prof"], alu, _load_traffic(traffic_key))}
 
     if rank != 0:

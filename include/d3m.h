@@ -96,6 +96,17 @@ typedef struct {
   int32_t panel_kernel; /* 0: thread-block-cluster panels where the front fits the
                            cluster's shared memory (default); 1: always the
                            single-CTA global-memory panel (same arithmetic) */
+  int32_t update_kernel;/* MIXED trailing/Schur updates: 0 = per level, the faster of
+                           the two below as measured by the autotuner (default);
+                           1 = fp32 FMA; 2 = tcgen05 tensor cores with 3xTF32
+                           split products */
+  int32_t autotune;     /* 0 = tune on the first d3m_factor (default): the update
+                           kernel and the panel cluster size of every tree level
+                           are timed with CUDA events over two trial
+                           factorisations and the faster kept; 1 = off (fixed
+                           defaults: FMA updates, smallest fitting cluster) */
+  const char *autotune_cache; /* optional file: read the tuned schedule from it when
+                           it matches this problem, write it after tuning; NULL = none */
 } d3m_options;
 
 /* Per-solve report: per column relative residual (Numerical Results
@@ -125,6 +136,9 @@ typedef struct {
   double ms_fwd, ms_bwd, ms_residual;             /* last solve, all refinement steps */
   double solve_flops;     /* real flops of the last solve's substitutions */
   double ms_inverse;      /* factor: building L11^{-1} of every front (profile=1) */
+  int64_t tuned_levels_tc;/* levels whose updates the autotuner put on tensor cores */
+  int64_t tuned_levels_cs2; /* levels whose panels run with the doubled cluster size */
+  double ms_tuning;       /* wall time of the trial factorisations */
 } d3m_stats;
 
 /*

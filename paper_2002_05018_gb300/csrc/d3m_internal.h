@@ -72,6 +72,7 @@ struct Plan {
 struct Ctx {
   Plan plan;
   d3m_options opt{};
+  std::string cache_path;  // copy of opt.autotune_cache
   std::string err;
   DeviceState *dev = nullptr;
   d3m_stats stats{};

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1079,6 +1080,236 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ------------------------------------------------------------ tensor-core trailing update
+// The complex64 trailing/Schur update of the mixed path on the 5th-generation
+// tensor cores: C[i, c] -= sum_t L[i, k0+t] W[c, t] per 128 x 64 tile of the
+// lower trailing part, K = kb <= 32 complex.  Split products (3xTF32): every
+// fp32 operand x = hi + lo with hi, lo in tf32, and X Y^T ~ Xhi Yhi^T + Xhi Ylo^T
+// + Xlo Yhi^T (fp32 accumulation), so the result keeps fp32 accuracy.  Complex
+// arithmetic as four real products:
+//   Re += Lr Wr^T - Li Wi^T,   Im += Lr Wi^T + Li Wr^T
+// (the minus through the A-negate bit of the instruction descriptor).  The
+// 8 operand planes (Lr, Li, Wr, Wi in hi/lo) are staged in shared memory in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
+// LBO = 128 B between k-neighbours, SBO = 1024 B between 8-row groups); one
+// thread issues tcgen05.mma (M = 128, N = 64, K = 8) into two TMEM
+// accumulators (Re: columns 0-63, Im: 64-127), commits to an mbarrier, and the
+// four warps read their 32 TMEM lanes back with tcgen05.ld for the epilogue.
+// The mbarrier wait is bounded: on expiry the tile is skipped and an error
+// flag is raised (the factorisation then reports D3M_ETIMEOUT).
+constexpr int TCM = 128, TCN = 64, TCK = 32;
+constexpr uint32_t TC_LBO = 128, TC_SBO = 1024;
+constexpr int TC_PLANE_A = TCM * TCK * 4;   // bytes of one A plane (16 KB)
+constexpr int TC_PLANE_B = TCN * TCK * 4;   // bytes of one B plane (8 KB)
+constexpr int TC_SMEM = 4 * TC_PLANE_A + 4 * TC_PLANE_B + 64;  // + mbarrier, TMEM address
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// byte offset of element (row, k) of a K-major no-swizzle operand plane
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+  return (uint32_t)((row >> 3) * TC_SBO + (k >> 2) * TC_LBO + (row & 7) * 16 + (k & 3) * 4);
+}
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// instruction descriptor: D f32, A/B tf32, K-major, N = 64, M = 128
+__device__ __forceinline__ uint32_t tc_idesc(int negA) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negA << 13) | ((uint32_t)(TCN >> 3) << 17) |
+         ((uint32_t)(TCM >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_update_tc(const int32_t *__restrict__ lvl, FrontTab ft, const int64_t *__restrict__ wofs,
+                cx<T> *__restrict__ arena, const cx<T> *__restrict__ Wbuf, const int32_t *__restrict__ st_k0,
+                const int32_t *__restrict__ st_kb, int32_t *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const int f = lvl[blockIdx.y];
+  const int kb = st_kb[f];
+  if (kb == 0) return;
+  const int c0 = st_k0[f];
+  const int k0 = c0 - kb;
+  const int m = ft.m[f];
+  // tiles: row blocks of 128 from R0, column blocks of 64 from C0, lower part
+  const int R0 = (c0 / TCM) * TCM, C0 = (c0 / TCN) * TCN;
+  const int nI = (m - R0 + TCM - 1) / TCM, nJmax = (m - C0 + TCN - 1) / TCN;
+  int t = blockIdx.x, I = 0, J = -1;
+  for (int ii = 0; ii < nI; ++ii) {
+    int rs = R0 + ii * TCM;
+    int nj = min(nJmax, (rs + TCM - C0 + TCN - 1) / TCN);
+    if (t < nj) {
+      I = ii;
+      J = t;
+      break;
+    }
+    t -= nj;
+  }
+  if (J < 0) return;  // uniform per CTA
+  const int rs = R0 + I * TCM, cs = C0 + J * TCN;
+  cx<T> *F = arena + ft.off[f];
+  const cx<T> *W = Wbuf + wofs[blockIdx.y];
+  const int64_t ld = m;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char *pA = tsm;                      // Lr_hi, Lr_lo, Li_hi, Li_lo
+  unsigned char *pB = tsm + 4 * TC_PLANE_A;     // Wr_hi, Wr_lo, Wi_hi, Wi_lo
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + 4 * TC_PLANE_A + 4 * TC_PLANE_B);
+  uint32_t *taddr_s = reinterpret_cast<uint32_t *>(mbar + 1);
+  // TMEM: 128 columns (two 64-column accumulators), one warp allocates
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(taddr_s)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // operands: thread = row of L (128 rows); W rows split over thread pairs
+  {
+    const int i = rs + tid;
+    for (int kk = 0; kk < TCK; ++kk) {
+      float re = 0.f, im = 0.f;
+      if (kk < kb && i < m) {
+        cx<T> v = F[i + (int64_t)(k0 + kk) * ld];
+        re = (float)v.re;
+        im = (float)v.im;
+      }
+      uint32_t rh = tf32_rna(re), ih = tf32_rna(im);
+      uint32_t rl = tf32_rna(re - __uint_as_float(rh)), il = tf32_rna(im - __uint_as_float(ih));
+      uint32_t o = tc_off(tid, kk);
+      *reinterpret_cast<uint32_t *>(pA + 0 * TC_PLANE_A + o) = rh;
+      *reinterpret_cast<uint32_t *>(pA + 1 * TC_PLANE_A + o) = rl;
+      *reinterpret_cast<uint32_t *>(pA + 2 * TC_PLANE_A + o) = ih;
+      *reinterpret_cast<uint32_t *>(pA + 3 * TC_PLANE_A + o) = il;
+    }
+    const int wr = tid & 63, half = tid >> 6;
+    const int c = cs + wr;
+    for (int kk = half * 16; kk < half * 16 + 16; ++kk) {
+      float re = 0.f, im = 0.f;
+      if (kk < kb && c < m) {
+        cx<T> v = W[c + (int64_t)kk * ld];
+        re = (float)v.re;
+        im = (float)v.im;
+      }
+      uint32_t rh = tf32_rna(re), ih = tf32_rna(im);
+      uint32_t rl = tf32_rna(re - __uint_as_float(rh)), il = tf32_rna(im - __uint_as_float(ih));
+      uint32_t o = tc_off(wr, kk);
+      *reinterpret_cast<uint32_t *>(pB + 0 * TC_PLANE_B + o) = rh;
+      *reinterpret_cast<uint32_t *>(pB + 1 * TC_PLANE_B + o) = rl;
+      *reinterpret_cast<uint32_t *>(pB + 2 * TC_PLANE_B + o) = ih;
+      *reinterpret_cast<uint32_t *>(pB + 3 * TC_PLANE_B + o) = il;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *taddr_s;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(pA), b0 = smem_u32(pB);
+    const uint32_t id_pos = tc_idesc(0), id_neg = tc_idesc(1);
+    const uint32_t dre = tmem, dim = tmem + TCN;
+    for (int ks = 0; ks < TCK / 8; ++ks) {
+      const uint32_t ko = (uint32_t)ks * 2 * TC_LBO;  // 8 tf32 = two core matrices along k
+      const uint64_t Lrh = tc_desc(a0 + 0 * TC_PLANE_A + ko), Lrl = tc_desc(a0 + 1 * TC_PLANE_A + ko);
+      const uint64_t Lih = tc_desc(a0 + 2 * TC_PLANE_A + ko), Lil = tc_desc(a0 + 3 * TC_PLANE_A + ko);
+      const uint64_t Wrh = tc_desc(b0 + 0 * TC_PLANE_B + ko), Wrl = tc_desc(b0 + 1 * TC_PLANE_B + ko);
+      const uint64_t Wih = tc_desc(b0 + 2 * TC_PLANE_B + ko), Wil = tc_desc(b0 + 3 * TC_PLANE_B + ko);
+      const uint32_t first = ks == 0 ? 0u : 1u;
+      tc_mma(dre, Lrh, Wrh, id_pos, first);
+      tc_mma(dre, Lrh, Wrl, id_pos, 1u);
+      tc_mma(dre, Lrl, Wrh, id_pos, 1u);
+      tc_mma(dre, Lih, Wih, id_neg, 1u);
+      tc_mma(dre, Lih, Wil, id_neg, 1u);
+      tc_mma(dre, Lil, Wih, id_neg, 1u);
+      tc_mma(dim, Lrh, Wih, id_pos, first);
+      tc_mma(dim, Lrh, Wil, id_pos, 1u);
+      tc_mma(dim, Lrl, Wih, id_pos, 1u);
+      tc_mma(dim, Lih, Wrh, id_pos, 1u);
+      tc_mma(dim, Lih, Wrl, id_pos, 1u);
+      tc_mma(dim, Lil, Wrh, id_pos, 1u);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+  }
+  // bounded wait for the MMAs (phase 0 of the mbarrier)
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar))
+        : "memory");
+  }
+  const int ok = __syncthreads_and(done);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = rs + warp * 32 + (tid & 31);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    for (int cc = 0; cc < TCN; cc += 16) {
+      uint32_t vr[16], vi[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
+            "=r"(vr[7]), "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]),
+            "=r"(vr[14]), "=r"(vr[15])
+          : "r"(tmem + lane_base + (uint32_t)cc));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
+            "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]),
+            "=r"(vi[14]), "=r"(vi[15])
+          : "r"(tmem + lane_base + (uint32_t)(TCN + cc)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < m) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int col = cs + cc + q;
+          if (col < c0 || col > row) continue;
+          cx<T> *dst = F + row + (int64_t)col * ld;
+          cx<T> v = *dst;
+          v.re -= (T)__uint_as_float(vr[q]);
+          v.im -= (T)__uint_as_float(vi[q]);
+          *dst = v;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
+static cudaError_t tc_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_update_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  done = e == cudaSuccess;
+  return e;
+}
+template <typename T>
+static void launch_update_tc(dim3 g, cudaStream_t s, const int32_t *lvl, FrontTab ft, const int64_t *wofs,
+                             cx<T> *arena, const cx<T> *W, const int32_t *k0, const int32_t *kb, int32_t *err) {
+  if constexpr (sizeof(T) == 4) k_update_tc<T><<<g, 128, TC_SMEM, s>>>(lvl, ft, wofs, arena, W, k0, kb, err);
+}
+
 // ------------------------------------------------------------ solve kernels
 // Vectors in M space and front-local vectors are row-major (RHS fastest).
 template <typename T>
@@ -1763,6 +1994,8 @@ struct Profiler {
   cudaStream_t s = nullptr;
   std::vector<cudaEvent_t> pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  std::vector<int> mark_level;
+  int cur_level = -1;
   size_t used = 0;
   cudaEvent_t get() {
     if (used == pool.size()) {
@@ -1783,10 +2016,23 @@ struct Profiler {
     cudaEvent_t e1 = get();
     cudaEventRecord(e1, s);
     marks.push_back({cls, {e0, e1}});
+    mark_level.push_back(cur_level);
   }
   void reset() {
     marks.clear();
+    mark_level.clear();
     used = 0;
+  }
+  // per-level sums of one class (after the stream has been synchronised)
+  std::vector<double> per_level(int cls, int nlev) {
+    std::vector<double> v(nlev, 0.0);
+    for (size_t q = 0; q < marks.size(); ++q) {
+      if (marks[q].first != cls || mark_level[q] < 0) continue;
+      float t = 0;
+      cudaEventElapsedTime(&t, marks[q].second.first, marks[q].second.second);
+      v[mark_level[q]] += t;
+    }
+    return v;
   }
   void collect(double ms[PC_N]) {
     for (int q = 0; q < PC_N; ++q) ms[q] = 0;
@@ -1863,6 +2109,13 @@ struct DeviceState {
   int g_r = 0;
   int64_t g_launches[2] = {0, 0};
   int2 *swp = nullptr;           // per level position: interchanges of the current panel (NB each)
+  int32_t *tc_err = nullptr;     // set by k_update_tc when a bounded wait expires
+  std::vector<uint8_t> lvl_tc;   // per level: tensor-core updates (mixed)
+  std::vector<int> lvl_cs;       // per level: panel cluster size (0 = global panel)
+  bool tuned = false;
+  bool tune_out = false;                       // fill tune_panel / tune_update on the next factor
+  std::vector<double> tune_panel, tune_update;
+  std::vector<std::vector<int>> tc_grid;  // per level, per step: 128x64 tiles (upper bound)
   std::vector<int> level_maxp;   // largest pivot block per level
   int32_t *nsplit = nullptr;     // per level position: row splits of k_bwd_gemm
   int64_t *part_off = nullptr;   // per level position: partial-buffer offset (units of r)
@@ -2084,10 +2337,30 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(dalloc(d, &d->st_minpiv, nsn));
   CUDA_TRY(dalloc(d, &d->flop_cnt, 2));
   CUDA_TRY(dalloc(d, &d->swp, (size_t)nsn * NB));
+  CUDA_TRY(dalloc(d, &d->tc_err, 1));
+  d->tc_grid.assign(P.n_levels, {});
+  for (int l = 0; l < P.n_levels; ++l)
+    for (int stp = 0; stp < d->level_steps[l]; ++stp) {
+      int g = 0;
+      for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+        int s = P.level_fronts[i];
+        int cmin = std::min<int>(pp[s], (stp + 1) * (NB - 1));
+        int R0 = (cmin / TCM) * TCM, C0 = (cmin / TCN) * TCN;
+        int nI = (m[s] - R0 + TCM - 1) / TCM, nJ = (m[s] - C0 + TCN - 1) / TCN, t = 0;
+        for (int ii = 0; ii < nI; ++ii) t += std::min(nJ, (R0 + ii * TCM + TCM - C0 + TCN - 1) / TCN);
+        g = std::max(g, t);
+      }
+      d->tc_grid[l].push_back(std::max(g, 1));
+    }
   d->level_maxp.assign(P.n_levels, 0);
   for (int l = 0; l < P.n_levels; ++l)
     for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i)
       d->level_maxp[l] = std::max(d->level_maxp[l], pp[P.level_fronts[i]]);
+  d->lvl_tc.assign(P.n_levels, 0);
+  d->lvl_cs.assign(P.n_levels, 0);
+  for (int l = 0; l < P.n_levels; ++l)
+    d->lvl_cs[l] = panel_cluster_size(d->level_maxp[l], c.opt.precision == D3M_FP64 ? sizeof(cx<double>)
+                                                                                      : sizeof(cx<float>));
   d->prof.on = c.opt.profile != 0;
   d->prof.s = d->stream;
   d->solve_flops_per_rhs = 0;
@@ -2138,6 +2411,8 @@ static int factor_t(Ctx &c) {
   CUDA_TRY(cudaMemsetAsync(d->st_kb, 0, nsn * sizeof(int32_t), s));
   CUDA_TRY(cudaMemsetAsync(d->st_info, 0, nsn * sizeof(int32_t), s));
   CUDA_TRY(cudaMemsetAsync(d->flop_cnt, 0, 2 * sizeof(double), s));
+  CUDA_TRY(cudaMemsetAsync(d->tc_err, 0, sizeof(int32_t), s));
+  if (sizeof(T) == 4) CUDA_TRY(tc_attrs());
   d->prof.reset();
   int64_t nl = 0;
   k_fill_double<<<(unsigned)((nsn + 255) / 256), 256, 0, s>>>(d->st_minpiv, nsn, 1e300);
@@ -2146,6 +2421,8 @@ static int factor_t(Ctx &c) {
   for (int l = 0; l < P.n_levels; ++l) {
     const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
     const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
+    d->prof.cur_level = l;
+    const bool use_tc = sizeof(T) == 4 && (c.opt.update_kernel == 2 || (c.opt.update_kernel == 0 && d->lvl_tc[l]));
     // zero the level's fronts (contiguous) and assemble the entries of M
     int64_t first = P.front_off[P.level_fronts[P.level_ptr[l]]];
     int last_s = P.level_fronts[P.level_ptr[l + 1] - 1];
@@ -2173,7 +2450,7 @@ static int factor_t(Ctx &c) {
     for (int stp = 0; stp < d->level_steps[l]; ++stp) {
       {
         PROF_BEGIN(PC_PANEL);
-        int cs = c.opt.panel_kernel == 1 ? 0 : panel_cluster_size(d->level_maxp[l], sizeof(cx<T>));
+        int cs = c.opt.panel_kernel == 1 ? 0 : d->lvl_cs[l];
         CUDA_TRY(launch_panel<T>(cs, d->level_maxp[l], d->level_maxm[l], nf, lvl, ft, wofs, arena, W, d->perm,
                                  d->dinv_d, d->dinv_o, d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv,
                                  d->flop_cnt, d->swp + (int64_t)P.level_ptr[l] * NB, s));
@@ -2181,8 +2458,13 @@ static int factor_t(Ctx &c) {
       }
       {
         PROF_BEGIN(PC_UPDATE);
-        dim3 g(d->update_grid[l][stp], nf);
-        k_update<T><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, d->st_k0, d->st_kb);
+        if (use_tc) {
+          dim3 g(d->tc_grid[l][stp], nf);
+          launch_update_tc<T>(g, s, lvl, ft, wofs, arena, W, d->st_k0, d->st_kb, d->tc_err);
+        } else {
+          dim3 g(d->update_grid[l][stp], nf);
+          k_update<T><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, d->st_k0, d->st_kb);
+        }
         PROF_END(PC_UPDATE);
       }
       nl += 2;
@@ -2212,6 +2494,7 @@ static int factor_t(Ctx &c) {
       PROF_END(PC_INV);
     }
   }
+  d->prof.cur_level = -1;
   k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
   ++nl;
   c.stats.launches_factor = nl + d->inv_launches;
@@ -2231,9 +2514,19 @@ static int factor_t(Ctx &c) {
   c.stats.min_pivot_ratio = mn;
   double fc[2];
   CUDA_TRY(cudaMemcpy(fc, d->flop_cnt, sizeof fc, cudaMemcpyDeviceToHost));
+  int32_t tce = 0;
+  CUDA_TRY(cudaMemcpy(&tce, d->tc_err, sizeof tce, cudaMemcpyDeviceToHost));
+  if (tce) {
+    c.err = "d3m_factor: a tensor-core update tile timed out waiting for its MMAs";
+    return D3M_ETIMEOUT;
+  }
   c.stats.flops_update = fc[0];
   c.stats.flops_panel = fc[1];
   if (d->prof.on) {
+    if (d->tune_out) {
+      d->tune_panel = d->prof.per_level(PC_PANEL, P.n_levels);
+      d->tune_update = d->prof.per_level(PC_UPDATE, P.n_levels);
+    }
     double ms[PC_N];
     d->prof.collect(ms);
     c.stats.ms_assemble = ms[PC_ASSEMBLE];
@@ -2262,12 +2555,122 @@ static int enter(Ctx &c) {
   return D3M_OK;
 }
 
+// ---- autotuner: per tree level, the trailing-update kernel (mixed: fp32 FMA
+// or tcgen05) and the panel cluster size (smallest that fits, or twice that),
+// chosen by timing two trial factorisations with CUDA events per level.
+static std::string tune_signature(const Ctx &c) {
+  const Plan &P = c.plan;
+  char buf[256];
+  snprintf(buf, sizeof buf, "d3m-autotune-v1 nm=%lld fronts=%lld levels=%d prec=%d arena=%lld", (long long)P.n_m,
+           (long long)P.sn_start.size(), P.n_levels, c.opt.precision, (long long)P.arena_elems);
+  return buf;
+}
+static bool tune_load(Ctx &c) {
+  if (c.cache_path.empty()) return false;
+  FILE *fp = fopen(c.cache_path.c_str(), "r");
+  if (!fp) return false;
+  char line[512];
+  bool ok = fgets(line, sizeof line, fp) != nullptr;
+  std::string sig = tune_signature(c);
+  ok = ok && std::string(line).substr(0, sig.size()) == sig;
+  DeviceState *d = c.dev;
+  std::vector<uint8_t> tc(c.plan.n_levels, 0);
+  std::vector<int> cs(c.plan.n_levels, 0);
+  for (int l = 0; ok && l < c.plan.n_levels; ++l) {
+    int ll, a, b;
+    ok = fscanf(fp, "%d %d %d", &ll, &a, &b) == 3 && ll == l && b >= 0 && b <= 16;
+    if (ok) {
+      tc[l] = (uint8_t)(a != 0);
+      cs[l] = b;
+    }
+  }
+  fclose(fp);
+  if (!ok) return false;
+  // a cached cluster size must still fit this level
+  for (int l = 0; l < c.plan.n_levels; ++l)
+    if (cs[l] != 0 && cs[l] < d->lvl_cs[l]) return false;
+  int64_t ncs2 = 0, ntc = 0;
+  for (int l = 0; l < c.plan.n_levels; ++l) {
+    ntc += tc[l];
+    ncs2 += cs[l] != d->lvl_cs[l];
+  }
+  d->lvl_tc = tc;
+  d->lvl_cs = cs;
+  c.stats.tuned_levels_tc = ntc;
+  c.stats.tuned_levels_cs2 = ncs2;
+  c.stats.ms_tuning = 0.0;
+  return true;
+}
+static void tune_save(const Ctx &c) {
+  if (c.cache_path.empty()) return;
+  FILE *fp = fopen(c.cache_path.c_str(), "w");
+  if (!fp) return;
+  fprintf(fp, "%s\n", tune_signature(c).c_str());
+  for (int l = 0; l < c.plan.n_levels; ++l) fprintf(fp, "%d %d %d\n", l, (int)c.dev->lvl_tc[l], c.dev->lvl_cs[l]);
+  fclose(fp);
+}
+
+static int factor_any(Ctx &c) { return c.opt.precision == D3M_FP64 ? factor_t<double>(c) : factor_t<float>(c); }
+
+static int autotune(Ctx &c) {
+  DeviceState *d = c.dev;
+  const int nlev = c.plan.n_levels;
+  if (tune_load(c)) {
+    d->tuned = true;
+    return D3M_OK;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  const bool prof = d->prof.on;
+  const int uk = c.opt.update_kernel;
+  d->prof.on = true;
+  d->tune_out = true;
+  // trial A: fp32-FMA updates, smallest cluster
+  std::vector<int> csA = d->lvl_cs, csB(nlev);
+  // (clusters stay within the portable size 8)
+  for (int l = 0; l < nlev; ++l) csB[l] = csA[l] > 0 && csA[l] <= 4 ? csA[l] * 2 : csA[l];
+  c.opt.update_kernel = 1;
+  int rc = factor_any(c);
+  std::vector<double> pA = d->tune_panel, uA = d->tune_update;
+  // trial B: tensor-core updates (mixed), doubled cluster
+  if (rc == D3M_OK) {
+    c.opt.update_kernel = 2;
+    d->lvl_cs = csB;
+    rc = factor_any(c);
+  }
+  std::vector<double> pB = d->tune_panel, uB = d->tune_update;
+  c.opt.update_kernel = uk;
+  d->prof.on = prof;
+  d->tune_out = false;
+  if (rc != D3M_OK) {
+    d->lvl_cs = csA;
+    return rc;
+  }
+  int64_t ntc = 0, ncs2 = 0;
+  for (int l = 0; l < nlev; ++l) {
+    d->lvl_tc[l] = c.opt.precision == D3M_MIXED && uB[l] < uA[l] ? 1 : 0;
+    d->lvl_cs[l] = pB[l] < pA[l] ? csB[l] : csA[l];
+    ntc += d->lvl_tc[l];
+    ncs2 += d->lvl_cs[l] != csA[l];
+  }
+  c.stats.tuned_levels_tc = ntc;
+  c.stats.tuned_levels_cs2 = ncs2;
+  c.stats.ms_tuning =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  d->tuned = true;
+  tune_save(c);
+  return D3M_OK;
+}
+
 int dev_factor(Ctx &c) {
   int rc = dev_init(c);
   if (rc) return rc;
   rc = enter(c);
   if (rc) return rc;
-  rc = c.opt.precision == D3M_FP64 ? factor_t<double>(c) : factor_t<float>(c);
+  if (!c.dev->tuned && c.opt.autotune == 0 && c.opt.panel_kernel != 1) {
+    rc = autotune(c);
+    if (rc) return rc;
+  }
+  rc = factor_any(c);
   c.factored = rc == D3M_OK;
   return rc;
 }

