@@ -235,8 +235,14 @@ enum d3m_structure_kind {
   D3M_LAMBDA = 7,      /* double [n_lm][nrhs][2]: multipliers of the last solve,
                           column-major complex */
   D3M_STATS = 8,       /* d3m_stats */
-  D3M_M_ENTRIES = 9    /* double [nnz][4]: (row, col, re, im) of the lower triangle of
+  D3M_M_ENTRIES = 9,   /* double [nnz][4]: (row, col, re, im) of the lower triangle of
                           M = [[A, D], [D^T, 0]] in M order, as assembled */
+  D3M_LEVELS = 10      /* double [n_levels][8] per level of the assembly tree (leaves
+                          first): fronts, largest pivot block, largest front,
+                          algorithmic real flops, then from the last factorisation
+                          run with d3m_options.profile = 1 (else 0): panel ms,
+                          update ms, 1 if the tcgen05 update ran, panel cluster
+                          size (0 = single-CTA panel) */
 };
 int d3m_structure(d3m_ctx *ctx, int32_t which, void *buf, size_t *bytes);
 

@@ -76,6 +76,8 @@ struct Ctx {
   std::string err;
   DeviceState *dev = nullptr;
   d3m_stats stats{};
+  std::vector<double> lvl_ms_panel, lvl_ms_update;  // last profiled factorisation, per level
+  std::vector<int> lvl_tc, lvl_cs;                   // schedule of the last factorisation
   std::vector<cplx> lambda_host;  // last solve's multipliers, column-major n_lm x nrhs
   int32_t lambda_nrhs = 0;
   bool factored = false;

@@ -450,25 +450,156 @@ __global__ void __launch_bounds__(PANEL_THREADS)
 
 // ------------------------------------------------------------ cluster panel kernel
 // The same restricted Bunch-Kaufman panel as k_panel, run by a thread-block
-// cluster of CS CTAs per front with the panel's L rows resident in the
-// cluster's distributed shared memory.  The rows [k0, m) of the front are
-// split into CS contiguous slot ranges; row interchanges only permute the
-// replicated logical-row <-> slot tables (data stays in its slot), while the
-// global front keeps its rows in logical order (previous columns, the
-// trailing part and the panel's own columns are swapped there as before).
+// cluster of CS CTAs per front on the pivot rows [k0, p) (the update rows are
+// k_l21's), with the panel's L rows resident in the cluster's distributed
+// shared memory.  The rows are split into CS contiguous slot ranges; a row
+// interchange only permutes the replicated logical-row <-> slot tables (data
+// stays in its slot) and moves the not yet factored column in the global front.
 // Per column: every CTA updates its slots of the column (original column from
 // global, L from its shared memory, the pivot row of L from the owner CTA via
-// DSMEM), posts its local pivot-search result in a mailbox, and after one
-// cluster barrier every CTA reads all mailboxes and takes the same decision.
+// DSMEM) and reduces its local pivot search; with CS > 1 it posts the result
+// in a mailbox and, after one cluster barrier, every thread reads all
+// mailboxes.  Every thread then takes the same pivot decision (fp32 path:
+// tests in fp32 with an exact fp64 re-evaluation when the two sides are
+// within rounding; fp64 path: one thread, published through shared memory,
+// because an fp64 instruction issued by all 512 threads costs hundreds of
+// cycles on GB300).  The panel's L and D columns, W = L D and the row
+// interchanges of the earlier panels' columns are written once, after the
+// last column, in the final row order.
 namespace cg = cooperative_groups;
 
-struct PanelBox {
-  double cmax;   // local max |w_i| over candidate rows (factor precision, widened)
-  int cidx;      // its logical row
-  int has;       // 1 if this CTA owns the queried row(s)
-  double2 v0, v1, v2;  // owner-published values (see use)
-  double2 vmax;  // the winning element itself (exact fp64 magnitude for the tests)
+// inverse of a pivot in the factor precision (scales the panel's L columns);
+// fp32 scales against overflow, fp64 uses the Newton reciprocal below
+__device__ __forceinline__ cx<float> cinv_t(cx<float> a) {
+  float s = fmaxf(fabsf(a.re), fabsf(a.im));
+  if (s == 0.0f) return mk<float>(0, 0);
+  float ar = a.re / s, ai = a.im / s;
+  float r = 1.0f / (s * (ar * ar + ai * ai));
+  return mk<float>(ar * r, -ai * r);
+}
+__device__ __forceinline__ cx<double> cinv_t(cx<double> a) {
+  if (a.re == 0.0 && a.im == 0.0) return mk<double>(0, 0);
+  double2 z = zinv_nr(make_double2(a.re, a.im));
+  return mk<double>(z.x, z.y);
+}
+__device__ __forceinline__ double cabs1_d(cx<float> a) { return fabs((double)a.re) + fabs((double)a.im); }
+__device__ __forceinline__ double cabs1_d(cx<double> a) { return fabs(a.re) + fabs(a.im); }
+
+// lhs < rhs for magnitudes evaluated in T; for T = float the comparison is
+// re-evaluated in fp64 from the exact operands when the two sides agree to
+// within 2^-20 (the rounding of their fp32 evaluation is below 2^-21), so the
+// outcome is the exact fp64 test's
+template <typename T, typename Exact>
+__device__ __forceinline__ bool bk_less(T lhs, T rhs, Exact exact) {
+  if (sizeof(T) == 8) return lhs < rhs;
+  const T g = (T)9.5367431640625e-07;
+  if (lhs < rhs * ((T)1 - g)) return true;
+  if (lhs > rhs * ((T)1 + g)) return false;
+  return exact();
+}
+
+// warp arg-max, the result broadcast from lane 0 (uniform even for NaN input)
+template <typename T>
+__device__ __forceinline__ ArgMaxT<T> warp_argmaxT(ArgMaxT<T> x) {
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMaxT<T> y;
+    y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+    y.i = __shfl_down_sync(0xffffffffu, x.i, o);
+    x = amaxT(x, y);
+  }
+  x.v = __shfl_sync(0xffffffffu, x.v, 0);
+  x.i = __shfl_sync(0xffffffffu, x.i, 0);
+  return x;
+}
+// Block arg-max with one barrier: the warp results go to half `par` of sh
+// (2 x 32 entries) and every warp reduces them itself.  Consecutive calls use
+// alternate halves, so a half is rewritten only after the barrier of the call
+// in between has been passed by every thread.
+template <typename T>
+__device__ __forceinline__ ArgMaxT<T> block_argmax1(ArgMaxT<T> x, ArgMaxT<T> *sh, int &par) {
+  x = warp_argmaxT(x);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  ArgMaxT<T> *h = sh + 32 * par;
+  if (l == 0) h[w] = x;
+  __syncthreads();
+  x = l < (int)(blockDim.x >> 5) ? h[l] : ArgMaxT<T>{(T)-1, 0x7fffffff};
+  par ^= 1;
+  return warp_argmaxT(x);
+}
+
+// the pivot decision of one column
+template <typename T>
+struct PivotDec {
+  int imax, kstep, kp;
+  int need2, singular, use_r;
+  T colmax, absakk;
+  cx<T> akk, vmax;
+  cx<T> d11, d21, d22;  // D block in the factor precision
+  cx<T> a11, a21, a22;  // its inverse in the factor precision
 };
+// what one CTA posts for the others (CS > 1)
+template <typename T>
+struct PanelBox {
+  T cmax;           // local max |w_i| over candidate rows
+  int cidx;         // its logical row
+  int has;          // 1 if this CTA owns the queried row
+  cx<T> vmax;       // the local winner itself
+  cx<T> v1, v2;     // owner-published values (w at row k / at row imax)
+};
+
+// first half of the decision: column maximum and the 1x1 test on a_kk
+template <typename T>
+__device__ __forceinline__ void bk_decide1(PivotDec<T> &d, int k, int p, int cidx, cx<T> akk, cx<T> vmax) {
+  d.akk = akk;
+  d.vmax = vmax;
+  d.imax = cidx;
+  d.colmax = cabs1T(vmax);
+  if (!(cidx < p)) {
+    d.colmax = (T)0;
+    d.vmax = mk<T>(0, 0);
+    d.imax = k;
+  }
+  d.absakk = cabs1T(akk);
+  d.singular = d.absakk == (T)0 && d.colmax == (T)0;
+  const cx<T> va = d.akk, vm = d.vmax;
+  d.need2 = !d.singular &&
+            bk_less(d.absakk, (T)BK_ALPHA * d.colmax, [&] { return cabs1_d(va) < BK_ALPHA * cabs1_d(vm); });
+}
+// record the chosen block and its inverse in the factor precision
+template <typename T>
+__device__ __forceinline__ void bk_finish(PivotDec<T> &d, int kstep, int kp, int use_r, cx<T> d11, cx<T> d21,
+                                          cx<T> d22) {
+  d.kstep = kstep;
+  d.kp = kp;
+  d.use_r = use_r;
+  d.d11 = d11;
+  d.d21 = d21;
+  d.d22 = d22;
+  if (kstep == 1) {
+    d.a11 = cinv_t(d11);
+  } else {
+    const cx<T> idet = cinv_t(cfms(cmul(d11, d22), d21, d21));
+    d.a11 = cmul(d22, idet);
+    d.a22 = cmul(d11, idet);
+    const cx<T> n = cmul(d21, idet);
+    d.a21 = mk<T>(-n.re, -n.im);
+  }
+}
+// second half: the tests on the row maximum of column imax
+template <typename T>
+__device__ __forceinline__ void bk_decide2(PivotDec<T> &d, int k, T rowmax, cx<T> rwin, cx<T> wki, cx<T> wri) {
+  const cx<T> va = d.akk, vm = d.vmax;
+  const double cm = cabs1_d(vm);
+  if (!bk_less(d.absakk * rowmax, (T)BK_ALPHA * d.colmax * d.colmax,
+               [&] { return cabs1_d(va) * cabs1_d(rwin) < BK_ALPHA * cm * cm; })) {
+    bk_finish(d, 1, k, 0, d.akk, mk<T>(0, 0), mk<T>(0, 0));
+  } else if (!bk_less(cabs1T(wri), (T)BK_ALPHA * rowmax,
+                      [&] { return cabs1_d(wri) < BK_ALPHA * cabs1_d(rwin); })) {
+    bk_finish(d, 1, d.imax, 1, wri, mk<T>(0, 0), mk<T>(0, 0));
+  } else {
+    bk_finish(d, 2, d.imax, 0, d.akk, wki, wri);
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(512)
@@ -478,6 +609,8 @@ __global__ void __launch_bounds__(512)
                int32_t *__restrict__ st_k0, int32_t *__restrict__ st_kb, int32_t *__restrict__ st_info,
                double *__restrict__ st_minpiv, double *__restrict__ flop_cnt, int2 *__restrict__ swp, int rcap,
                int mcap) {
+  // fp32: every thread takes the decisions; fp64: one thread, then a barrier
+  constexpr bool ONE = sizeof(T) == 8;
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -508,31 +641,20 @@ __global__ void __launch_bounds__(512)
   cx<T> *wr = wk + rcap;                                  // [rcap]
   int *spos = reinterpret_cast<int *>(wr + rcap);         // [rcap] logical row of each own slot
   int *p2s = spos + rcap;                                 // [mcap] logical row - k0 -> global slot
-  __shared__ PanelBox box[2];
+  __shared__ PanelBox<T> box[2];
   __shared__ cx<T> wrow[NB], wrow2[NB];
   __shared__ cx<T> Dd[NB], Do[NB];    // D of the panel's pivots: diag / 2x2 coupling
-  __shared__ double2 s_inv[3];         // fp64 inverse of the current pivot block (one thread)
+  __shared__ PivotDec<T> pd;          // fp64 path: the decision of thread 0
   __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
-  __shared__ ArgMaxT<T> red[32];
-  __shared__ double s_minpiv, s_cmac, bc_cmax;
-  __shared__ int bc_imax;
-  __shared__ double2 bc_v0, bc_v1;
+  __shared__ ArgMaxT<T> red[64];
+  __shared__ int s_nmv;
+  __shared__ int2 s_mv[2 * NB];       // rows moved by the panel: (destination, source)
   for (int q = tid; q < nr; q += nth) p2s[q] = q;  // slot q holds row k0 + q initially
   if (rank == 0 && tid < NB) swp[(int64_t)fi * NB + tid] = make_int2(-1, -1);
   for (int q = tid; q < ns; q += nth) spos[q] = k0 + s_lo + q;
-  if (tid == 0) {
-    s_minpiv = 1e300;
-    s_cmac = 0.0;
-  }
+  if (tid == 0) s_nmv = 0;
   __syncthreads();
   if (CS > 1) cl.sync();
-  // original data of the column being processed, for the first two own slots,
-  // prefetched during the previous column's scale phase
-  cx<T> pre[2] = {mk<T>(0, 0), mk<T>(0, 0)};
-  {
-    int qi = 0;
-    for (int q = tid; q < ns && qi < 2; q += nth, ++qi) pre[qi] = F[spos[q] + (int64_t)k0 * ld];
-  }
   // a cluster of one synchronises like a plain block
   auto csync = [&]() {
     if (CS == 1)
@@ -540,12 +662,19 @@ __global__ void __launch_bounds__(512)
     else
       cl.sync();
   };
-  int k = k0, j = 0;
+  // original data of the column being processed for the first two own slots
+  // (q = tid, tid + nth), loaded during the previous column's scale phase
+  cx<T> pre0 = mk<T>(0, 0), pre1 = mk<T>(0, 0);
+  if (tid < ns) pre0 = F[spos[tid] + (int64_t)k0 * ld];
+  if (tid + nth < ns) pre1 = F[spos[tid + nth] + (int64_t)k0 * ld];
+  int k = k0, j = 0, par = 0;
+  long long cmac = 0;        // complex MACs of the column updates (thread 0)
+  float minpiv = 3.0e38f;    // smallest |d| / colmax of the 1x1 pivots (thread 0)
   // W row of logical row `row` for the panel columns 0..j-1: L[row, :] D
   auto load_wrow = [&](int row, cx<T> *dst) {
     int g = p2s[row - k0];
     int o = g / R, sl = g - o * R;
-    const cx<T> *Lr = cl.map_shared_rank(Ls, o) + (size_t)sl * LSTR;
+    const cx<T> *Lr = (CS == 1 ? Ls : cl.map_shared_rank(Ls, o)) + (size_t)sl * LSTR;
     if (tid < NB) {
       cx<T> v = mk<T>(0, 0);
       if (tid < j) {
@@ -562,77 +691,73 @@ __global__ void __launch_bounds__(512)
       dst[tid] = v;
     }
   };
+  // value of own-CTA slot array a at logical row `row` (CS == 1: any row)
+  auto own_at = [&](const cx<T> *a, int row) { return a[p2s[row - k0] - rank * R]; };
   while (k < p && j < NB - 1) {
     // ---- (1) updated column k for own slots, local pivot search
     load_wrow(k, wrow);
     __syncthreads();
     ArgMaxT<T> loc{(T)-1, 0x7fffffff};
-    {
-      int qi = 0;
-      for (int q = tid; q < ns; q += nth, ++qi) {
-        int i = spos[q];
-        if (i < k) continue;
-        cx<T> acc = qi < 2 ? pre[qi] : F[i + (int64_t)k * ld];
-        const cx<T> *Lq = Ls + (size_t)q * LSTR;
+    for (int q = tid, qi = 0; q < ns; q += nth, ++qi) {
+      int i = spos[q];
+      if (i < k) continue;
+      cx<T> acc = qi == 0 ? pre0 : qi == 1 ? pre1 : F[i + (int64_t)k * ld];
+      const cx<T> *Lq = Ls + (size_t)q * LSTR;
 #pragma unroll 8
-        for (int t = 0; t < NB - 1; ++t)
-          if (t < j) acc = cfms(acc, Lq[t], wrow[t]);
-        wk[q] = acc;
-        if (i > k && i < p) loc = amaxT(loc, ArgMaxT<T>{cabs1T(acc), i});
-      }
+      for (int t = 0; t < NB - 1; ++t)
+        if (t < j) acc = cfms(acc, Lq[t], wrow[t]);
+      wk[q] = acc;
+      if (i > k && i < p) loc = amaxT(loc, ArgMaxT<T>{cabs1T(acc), i});
     }
-    ArgMaxT<T> cm = block_argmaxT(loc, red);
-    {
-      int g = p2s[k - k0];
-      int o = g / R;
+    cmac += (long long)(p - k) * (j + 1);
+    ArgMaxT<T> cm = block_argmax1(loc, red, par);
+    cx<T> akk, vmax;
+    if (CS == 1) {
+      akk = own_at(wk, k);
+      vmax = cm.i < p ? own_at(wk, cm.i) : mk<T>(0, 0);
+    } else {
+      const int gk = p2s[k - k0];
       if (tid == 0) {
-        box[0].cmax = (double)cm.v;
+        box[0].cmax = cm.v;
         box[0].cidx = cm.i;
-        box[0].has = o == rank;
-        box[0].v0 = o == rank ? to_d(wk[g - o * R]) : make_double2(0, 0);
-        box[0].vmax = make_double2(0, 0);
-        if (cm.i < p) box[0].vmax = to_d(wk[p2s[cm.i - k0] - rank * R]);
+        box[0].has = gk / R == rank;
+        box[0].v1 = gk / R == rank ? wk[gk - rank * R] : mk<T>(0, 0);
+        box[0].vmax = cm.i < p ? own_at(wk, cm.i) : mk<T>(0, 0);
       }
-    }
-    if (tid == 0) s_cmac += (double)(p - k) * (j + 1);
-    csync();  // #1
-    if (tid == 0) {
-      double cmx = -1.0;
-      int imx = 0x7fffffff;
-      double2 a = make_double2(0, 0), vm = make_double2(0, 0);
+      cl.sync();  // #1
+      ArgMaxT<T> best{(T)-1, 0x7fffffff};
+      vmax = mk<T>(0, 0);
+      akk = mk<T>(0, 0);
       for (int c = 0; c < CS; ++c) {
-        const PanelBox *b = cl.map_shared_rank(&box[0], c);
-        if (b->cmax > cmx || (b->cmax == cmx && b->cidx < imx)) {
-          cmx = b->cmax;
-          imx = b->cidx;
-          vm = b->vmax;
+        const PanelBox<T> *b = cl.map_shared_rank(&box[0], c);
+        const T v = b->cmax;
+        const int i = b->cidx;
+        if (v > best.v || (v == best.v && i < best.i)) {
+          best = ArgMaxT<T>{v, i};
+          vmax = b->vmax;
         }
-        if (b->has) a = b->v0;
+        if (b->has) akk = b->v1;
       }
-      bc_cmax = fabs(vm.x) + fabs(vm.y);  // exact fp64 magnitude of the winner
-      bc_imax = imx;
-      bc_v0 = a;
+      cm = best;
     }
-    __syncthreads();
-    double colmax = bc_cmax;
-    int imax = bc_imax;
-    double2 akk = bc_v0;
-    if (!(imax < p)) {
-      colmax = 0.0;
-      imax = k;
+    PivotDec<T> d;
+    if (ONE) {
+      if (tid == 0) {
+        bk_decide1(pd, k, p, cm.i, akk, vmax);
+        if (!pd.need2) bk_finish(pd, 1, k, 0, akk, mk<T>(0, 0), mk<T>(0, 0));
+      }
+      __syncthreads();
+      d = pd;
+    } else {
+      bk_decide1(d, k, p, cm.i, akk, vmax);
+      if (!d.need2) bk_finish(d, 1, k, 0, akk, mk<T>(0, 0), mk<T>(0, 0));
     }
-    const double absakk = fabs(akk.x) + fabs(akk.y);
-    int kstep = 1, kp = k;
-    bool use_r = false;
-    bool singular = fmax(absakk, colmax) == 0.0;
-    double2 d11 = akk, d21 = make_double2(0, 0), d22 = make_double2(0, 0);
-    if (!singular && absakk < BK_ALPHA * colmax) {
+    if (d.need2) {
+      const int imax = d.imax;
       // ---- (2) updated column imax for own slots
       load_wrow(imax, wrow2);
       __syncthreads();
       ArgMaxT<T> rl{(T)-1, 0x7fffffff};
-      int gi = p2s[imax - k0];
-      int oi = gi / R;
       for (int q = tid; q < ns; q += nth) {
         int i = spos[q];
         if (i < k) continue;
@@ -644,68 +769,66 @@ __global__ void __launch_bounds__(512)
         wr[q] = acc;
         if (i != imax && i < p) rl = amaxT(rl, ArgMaxT<T>{cabs1T(acc), i});
       }
-      ArgMaxT<T> rm = block_argmaxT(rl, red);
-      if (tid == 0) {
-        box[1].cidx = rm.i;
-        box[1].cmax = -1.0;
-        if (rm.i < p) {  // exact fp64 magnitude of the local winner
-          double2 v = to_d(wr[p2s[rm.i - k0] - rank * R]);
-          box[1].cmax = fabs(v.x) + fabs(v.y);
+      cmac += (long long)(p - k) * j;
+      ArgMaxT<T> rm = block_argmax1(rl, red, par);
+      cx<T> rwin, wki, wri;
+      T rowmax;
+      if (CS == 1) {
+        rowmax = rm.i < p ? rm.v : (T)0;
+        rwin = rm.i < p ? own_at(wr, rm.i) : mk<T>(0, 0);
+        wki = own_at(wk, imax);
+        wri = own_at(wr, imax);
+      } else {
+        const int gi = p2s[imax - k0];
+        if (tid == 0) {
+          box[1].cmax = rm.i < p ? rm.v : (T)-1;
+          box[1].cidx = rm.i;
+          box[1].vmax = rm.i < p ? own_at(wr, rm.i) : mk<T>(0, 0);
+          box[1].has = gi / R == rank;
+          box[1].v1 = gi / R == rank ? wk[gi - rank * R] : mk<T>(0, 0);  // w_k at row imax
+          box[1].v2 = gi / R == rank ? wr[gi - rank * R] : mk<T>(0, 0);  // w_r at row imax
         }
-        box[1].has = oi == rank;
-        box[1].v1 = oi == rank ? to_d(wk[gi - oi * R]) : make_double2(0, 0);  // w_k at row imax
-        box[1].v2 = oi == rank ? to_d(wr[gi - oi * R]) : make_double2(0, 0);  // w_r at row imax
-        s_cmac += (double)(p - k) * j;
-      }
-      csync();  // #2
-      if (tid == 0) {
-        double rmx = 0.0;
-        double2 a = make_double2(0, 0), b2 = make_double2(0, 0);
+        cl.sync();  // #2
+        rowmax = (T)0;
+        double rex = 0.0;  // exact magnitude of the largest winner
+        rwin = mk<T>(0, 0);
+        wki = wri = mk<T>(0, 0);
         for (int c = 0; c < CS; ++c) {
-          const PanelBox *b = cl.map_shared_rank(&box[1], c);
-          if (b->cmax > rmx) rmx = b->cmax;
+          const PanelBox<T> *b = cl.map_shared_rank(&box[1], c);
+          if (b->cmax > rowmax) rowmax = b->cmax;
+          if (b->cmax >= (T)0 && cabs1_d(b->vmax) > rex) {
+            rex = cabs1_d(b->vmax);
+            rwin = b->vmax;
+          }
           if (b->has) {
-            a = b->v1;
-            b2 = b->v2;
+            wki = b->v1;
+            wri = b->v2;
           }
         }
-        bc_cmax = rmx;
-        bc_v0 = a;
-        bc_v1 = b2;
       }
-      __syncthreads();
-      double rowmax = bc_cmax;
-      double2 wki = bc_v0, wri = bc_v1;
-      if (absakk * rowmax >= BK_ALPHA * colmax * colmax) {
-        kp = k;
-      } else if (fabs(wri.x) + fabs(wri.y) >= BK_ALPHA * rowmax) {
-        kp = imax;
-        use_r = true;
-        d11 = wri;
+      if (ONE) {
+        if (tid == 0) bk_decide2(pd, k, rowmax, rwin, wki, wri);
+        __syncthreads();
+        d = pd;
       } else {
-        kp = imax;
-        kstep = 2;
-        d21 = wki;
-        d22 = wri;
+        bk_decide2(d, k, rowmax, rwin, wki, wri);
       }
     }
+    const int kstep = d.kstep, kp = d.kp;
     const int kk = k + kstep - 1;
+    if (tid == 0) {
+      if (d.singular && rank == 0 && st_info[f] == 0) st_info[f] = k + 1;
+      if (kstep == 1 && d.colmax > (T)0) minpiv = fminf(minpiv, (float)cabs1_d(d.d11) / (float)d.colmax);
+    }
     if (kp != kk) {
-      // ---- interchange kk <-> kp in the global front (logical order) and in the tables
-      // (a) the non-updated column kk moves to position kp; each thread handles the
-      //     rows of its own slots so that its later writes to those rows stay ordered
+      // ---- interchange kk <-> kp: the not yet factored column kk moves to
+      // position kp in the global front; each thread handles the rows of its
+      // own slots so that its later accesses to those rows stay ordered
       for (int q = tid; q < ns; q += nth) {
         int i = spos[q];
         if (i > kk && i < kp) F[kp + (int64_t)i * ld] = F[i + (int64_t)kk * ld];
         else if (i > kp) F[i + (int64_t)kp * ld] = F[i + (int64_t)kk * ld];
         else if (i == kk) F[kp + (int64_t)kp * ld] = F[kk + (int64_t)kk * ld];
-      }
-      // (b) rows kk and kp of the factored columns [0, k) (column k itself is
-      //     rewritten below), split over the cluster
-      for (int c = rank * nth + tid; c < k; c += CS * nth) {
-        cx<T> a = F[kk + (int64_t)c * ld], b = F[kp + (int64_t)c * ld];
-        F[kk + (int64_t)c * ld] = b;
-        F[kp + (int64_t)c * ld] = a;
       }
       if (rank == 0 && tid == 0) {
         int32_t a = pv[kk];
@@ -713,61 +836,34 @@ __global__ void __launch_bounds__(512)
         pv[kp] = a;
         swp[(int64_t)fi * NB + j] = make_int2(kk, kp);  // replayed on the update rows by k_l21
       }
-      csync();  // copies done before the tables change and column k is rewritten
+      csync();  // the moves have read their sources; every thread has read p2s
+      for (int q = tid; q < ns; q += nth) {
+        if (spos[q] == kk) spos[q] = kp;
+        else if (spos[q] == kp) spos[q] = kk;
+      }
       if (tid == 0) {
-        int ga = p2s[kk - k0], gb = p2s[kp - k0];
-        p2s[kk - k0] = gb;
+        int ga = p2s[kk - k0];
+        p2s[kk - k0] = p2s[kp - k0];
         p2s[kp - k0] = ga;
-        if (ga / R == rank) spos[ga - rank * R] = kp;
-        if (gb / R == rank) spos[gb - rank * R] = kk;
-      }
-      __syncthreads();
-    }
-    // ---- scale: L columns for own slots (logical order after the interchange)
-    if (singular) {
-      if (rank == 0 && tid == 0 && st_info[f] == 0) st_info[f] = k + 1;
-    }
-    if (tid == 0) {  // fp64 inverse of the pivot block, computed once
-      if (kstep == 1) {
-        s_inv[0] = (d11.x == 0.0 && d11.y == 0.0) ? make_double2(0, 0) : zinv_nr(d11);
-      } else {
-        double2 det = zmul(d11, d22), d2 = zmul(d21, d21);
-        det.x -= d2.x;
-        det.y -= d2.y;
-        double2 idet = zinv_nr(det);
-        s_inv[0] = zmul(d22, idet);
-        s_inv[2] = zmul(d11, idet);
-        double2 t21 = zmul(d21, idet);
-        s_inv[1] = make_double2(-t21.x, -t21.y);
       }
     }
-    __syncthreads();
+    // ---- scale: L columns of own slots (in shared memory; written to the
+    // front after the last column)
     if (kstep == 1) {
-      const double2 di = s_inv[0];
-      cx<T> dinv = from_d<T>(di);
-      const cx<T> *src = use_r ? wr : wk;
+      const cx<T> dinv = d.a11;
+      const cx<T> *src = d.use_r ? wr : wk;
       for (int q = tid; q < ns; q += nth) {
         int i = spos[q];
         if (i < k) continue;
-        cx<T> l = i == k ? mk<T>(1, 0) : cmul(src[q], dinv);
-        Ls[(size_t)q * LSTR + j] = l;
-        if (i > k) F[i + (int64_t)k * ld] = l;
-        else F[k + (int64_t)k * ld] = from_d<T>(d11);
+        Ls[(size_t)q * LSTR + j] = i == k ? mk<T>(1, 0) : cmul(src[q], dinv);
       }
       if (tid == 0) {
-        Dd[j] = from_d<T>(d11);
+        Dd[j] = d.d11;
         Do[j] = mk<T>(0, 0);
         Dz[j] = 1;
-        if (colmax > 0) s_minpiv = fmin(s_minpiv, (double)((float)(fabs(d11.x) + fabs(d11.y)) / (float)colmax));
-      }
-      if (rank == 0 && tid == 0) {
-        dd[k] = di;
-        dof[k] = make_double2(0, 0);
-        ps[k] = 1;
       }
     } else {
-      const double2 i11 = s_inv[0], i21 = s_inv[1], i22 = s_inv[2];
-      cx<T> a11 = from_d<T>(i11), a21 = from_d<T>(i21), a22 = from_d<T>(i22);
+      const cx<T> a11 = d.a11, a21 = d.a21, a22 = d.a22;
       for (int q = tid; q < ns; q += nth) {
         int i = spos[q];
         if (i < k) continue;
@@ -775,55 +871,70 @@ __global__ void __launch_bounds__(512)
         if (i == k) {
           l1 = mk<T>(1, 0);
           l2 = mk<T>(0, 0);
-          F[k + (int64_t)k * ld] = from_d<T>(d11);
         } else if (i == k + 1) {
           l1 = mk<T>(0, 0);
           l2 = mk<T>(1, 0);
-          F[k + 1 + (int64_t)k * ld] = mk<T>(0, 0);
-          F[k + 1 + (int64_t)(k + 1) * ld] = from_d<T>(d22);
         } else {
           cx<T> w1 = wk[q], w2 = wr[q];
           l1 = cfma(cmul(w1, a11), w2, a21);
           l2 = cfma(cmul(w1, a21), w2, a22);
-          F[i + (int64_t)k * ld] = l1;
-          F[i + (int64_t)(k + 1) * ld] = l2;
         }
         Ls[(size_t)q * LSTR + j] = l1;
         Ls[(size_t)q * LSTR + j + 1] = l2;
       }
       if (tid == 0) {
-        Dd[j] = from_d<T>(d11);
-        Dd[j + 1] = from_d<T>(d22);
-        Do[j] = from_d<T>(d21);
-        Do[j + 1] = from_d<T>(d21);
+        Dd[j] = d.d11;
+        Dd[j + 1] = d.d22;
+        Do[j] = d.d21;
+        Do[j + 1] = d.d21;
         Dz[j] = 2;
         Dz[j + 1] = -2;
       }
-      if (rank == 0 && tid == 0) {
-        dd[k] = i11;
-        dd[k + 1] = i22;
-        dof[k] = i21;
-        dof[k + 1] = i21;
-        ps[k] = 2;
-        ps[k + 1] = -2;
-      }
     }
-    if (k + kstep < p) {  // prefetch the next column (this step's interchanges are done)
-      int qi = 0;
-      for (int q = tid; q < ns && qi < 2; q += nth, ++qi) {
-        int i = spos[q];
-        if (i >= k + kstep) pre[qi] = F[i + (int64_t)(k + kstep) * ld];
-      }
+    if (k + kstep < p) {  // load the next column (this step's interchange is done)
+      const int kn = k + kstep;
+      if (tid < ns && spos[tid] >= kn) pre0 = F[spos[tid] + (int64_t)kn * ld];
+      if (tid + nth < ns && spos[tid + nth] >= kn) pre1 = F[spos[tid + nth] + (int64_t)kn * ld];
     }
-    csync();  // #3: L rows, tables and the global front are consistent for the next column
+    csync();  // #3: L rows, D and the tables are consistent for the next column
     k += kstep;
     j += kstep;
   }
-  // ---- W = L D for the rows below the panel (trailing update input)
+  // ---- fp64 D^{-1} of the panel's pivots (one thread per pivot)
+  if (rank == 0 && tid < j) {
+    const int t = tid, z = Dz[t];
+    if (z == 1) {
+      const double2 d11 = to_d(Dd[t]);
+      dd[k0 + t] = (d11.x == 0.0 && d11.y == 0.0) ? make_double2(0, 0) : zinv_nr(d11);
+      dof[k0 + t] = make_double2(0, 0);
+      ps[k0 + t] = 1;
+    } else if (z == 2) {
+      const double2 d11 = to_d(Dd[t]), d22 = to_d(Dd[t + 1]), d21 = to_d(Do[t]);
+      double2 det = zmul(d11, d22), d2 = zmul(d21, d21);
+      det.x -= d2.x;
+      det.y -= d2.y;
+      const double2 idet = zinv_nr(det), t21 = zmul(d21, idet);
+      dd[k0 + t] = zmul(d22, idet);
+      dd[k0 + t + 1] = zmul(d11, idet);
+      dof[k0 + t] = make_double2(-t21.x, -t21.y);
+      dof[k0 + t + 1] = make_double2(-t21.x, -t21.y);
+      ps[k0 + t] = 2;
+      ps[k0 + t + 1] = -2;
+    }
+  }
+  // ---- the panel's columns in the final row order: L below the diagonal,
+  // D on it (the coupling entry L(k+1, k) of a 2x2 pair is stored as 0, so
+  // every consumer may read the pivot columns as a plain unit-lower L), and
+  // W = L D for the rows below the panel (trailing update input)
   for (int q = tid; q < ns; q += nth) {
-    int i = spos[q];
-    if (i < k) continue;
+    const int i = spos[q];
     const cx<T> *Lq = Ls + (size_t)q * LSTR;
+    for (int t = 0; t < j; ++t) {
+      const int c = k0 + t;
+      if (c < i) F[i + (int64_t)c * ld] = Lq[t];
+      else if (c == i) F[i + (int64_t)c * ld] = Dd[t];
+    }
+    if (i < k) continue;
     for (int t = 0; t < j; ++t) {
       cx<T> l = Lq[t], acc;
       if (Dz[t] == 1) {
@@ -836,6 +947,33 @@ __global__ void __launch_bounds__(512)
       W[i + (int64_t)t * ld] = acc;
     }
   }
+  // ---- the panel's row interchanges on the earlier panels' columns [0, k0):
+  // logical row r now holds what row k0 + p2s[r - k0] held
+  for (int q = tid; q < nr; q += nth)
+    if (p2s[q] != q) {
+      int a = atomicAdd(&s_nmv, 1);
+      s_mv[a] = make_int2(k0 + q, k0 + p2s[q]);
+    }
+  __syncthreads();  // Ls is free from here on: staging buffer for the moves
+  const int nmv = s_nmv;
+  if (nmv > 0 && k0 > 0) {
+    const int cap = rcap * LSTR;
+    const int cpc = cap / nmv;  // columns per chunk (nmv <= min(2 NB, nr) <= LSTR rcap)
+    const int ncol = (k0 + CS - 1) / CS, c_lo = rank * ncol, c_hi = min(k0, c_lo + ncol);
+    for (int cb = c_lo; cb < c_hi; cb += cpc) {
+      const int nc = min(cpc, c_hi - cb), ne = nc * nmv;
+      for (int e = tid; e < ne; e += nth) {
+        const int2 mv = s_mv[e % nmv];
+        Ls[e] = F[mv.y + (int64_t)(cb + e / nmv) * ld];
+      }
+      __syncthreads();
+      for (int e = tid; e < ne; e += nth) {
+        const int2 mv = s_mv[e % nmv];
+        F[mv.x + (int64_t)(cb + e / nmv) * ld] = Ls[e];
+      }
+      __syncthreads();
+    }
+  }
   if (rank == 0 && tid == 0) {
     st_k0[f] = k;
     st_kb[f] = j;
@@ -844,10 +982,11 @@ __global__ void __launch_bounds__(512)
     if (flop_cnt && rank == 0) {
       const double n = (double)(m - k);
       atomicAdd(flop_cnt, 8.0 * j * n * (n + 1.0) * 0.5);
-      atomicAdd(flop_cnt + 1, 8.0 * s_cmac);
+      atomicAdd(flop_cnt + 1, 8.0 * (double)cmac);
     }
-    if (s_minpiv < 1e300) atomicMin(reinterpret_cast<unsigned long long *>(st_minpiv + f),
-                                    (unsigned long long)__double_as_longlong(s_minpiv));
+    if (minpiv < 3.0e38f)
+      atomicMin(reinterpret_cast<unsigned long long *>(st_minpiv + f),
+                (unsigned long long)__double_as_longlong((double)minpiv));
   }
   csync();  // no CTA leaves while others may still read its shared memory
 }
@@ -1032,50 +1171,57 @@ __global__ void __launch_bounds__(256)
   cx<T> *F = arena + ft.off[f];
   const cx<T> *W = Wbuf + wofs[blockIdx.y];
   const int64_t ld = m;
-  __shared__ cx<T> Ls[UK][UT + 1];
-  __shared__ cx<T> Ws[UK][UT + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  cx<T> acc[4][4];
+  // K chunk: the whole panel (32 KB of shared memory) in fp32, half of it in fp64
+  constexpr int KC = sizeof(T) == 4 ? NB : UK;
+  __shared__ cx<T> Ls[KC][UT];
+  __shared__ cx<T> Ws[KC][UT];
+  // the fast thread index runs along the rows (column-major front), so every
+  // warp access to the C tile covers two 128-byte column segments
+  const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
+  // C tile first: its loads are in flight while L and W are staged
+  cx<T> cv[4][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a) {
+    const int i = r0 + tr + 16 * a;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = mk<T>(0, 0);
-  for (int t0 = 0; t0 < kb; t0 += UK) {
-    for (int e = threadIdx.x; e < UK * UT; e += 256) {
-      int r = e % UT, tt = e / UT;
-      int gi = r0 + r, gc = cc0 + r;
-      bool ok = tt + t0 < kb;
+    for (int b = 0; b < 4; ++b) {
+      const int cidx = cc0 + tc + 16 * b;
+      cv[a][b] = (i < m && cidx >= c0 && cidx <= i) ? F[i + (int64_t)cidx * ld] : mk<T>(0, 0);
+    }
+  }
+  for (int t0 = 0; t0 < kb; t0 += KC) {
+    if (t0 > 0) __syncthreads();
+    for (int e = threadIdx.x; e < KC * UT; e += 256) {
+      const int r = e % UT, tt = e / UT;
+      const int gi = r0 + r, gc = cc0 + r;
+      const bool ok = t0 + tt < kb;
       Ls[tt][r] = (ok && gi < m) ? F[gi + (int64_t)(k0 + t0 + tt) * ld] : mk<T>(0, 0);
       Ws[tt][r] = (ok && gc < m) ? W[gc + (int64_t)(t0 + tt) * ld] : mk<T>(0, 0);
     }
     __syncthreads();
+    const int nt = min(KC, kb - t0);
 #pragma unroll 4
-    for (int tt = 0; tt < UK; ++tt) {
+    for (int tt = 0; tt < nt; ++tt) {
       cx<T> lv[4], wv[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) lv[a] = Ls[tt][ty + 16 * a];
+      for (int a = 0; a < 4; ++a) lv[a] = Ls[tt][tr + 16 * a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) wv[b] = Ws[tt][tx + 16 * b];
+      for (int b = 0; b < 4; ++b) wv[b] = Ws[tt][tc + 16 * b];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = cfma(acc[a][b], lv[a], wv[b]);
+        for (int b = 0; b < 4; ++b) cv[a][b] = cfms(cv[a][b], lv[a], wv[b]);
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    int i = r0 + ty + 16 * a;
+    const int i = r0 + tr + 16 * a;
     if (i >= m) continue;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      int cidx = cc0 + tx + 16 * b;
+      const int cidx = cc0 + tc + 16 * b;
       if (cidx < c0 || cidx > i) continue;
-      cx<T> *dst = F + i + (int64_t)cidx * ld;
-      cx<T> v = *dst;
-      v.re -= acc[a][b].re;
-      v.im -= acc[a][b].im;
-      *dst = v;
+      F[i + (int64_t)cidx * ld] = cv[a][b];
     }
   }
 }
@@ -1538,131 +1684,9 @@ __global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ l
   }
 }
 
-// Forward update of a front's update rows: Y[p+i, c] -= sum_k L21[i, k] y[k, c]
-// (all fronts of a level; 64 rows x 32 RHS per CTA, k in chunks of 16).
-constexpr int GR = 64, GC = 32, GK = 16;
-template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_gemm(const int32_t *__restrict__ lvl, FrontTab ft,
-                                                  const cx<T> *__restrict__ arena, cx<T> *__restrict__ Y,
-                                                  const cx<T> *__restrict__ Ysrc, int r) {
-  const int f = lvl[blockIdx.y];
-  const int m = ft.m[f], p = ft.p[f];
-  const int nrt = (m - p + GR - 1) / GR, nct = (r + GC - 1) / GC;
-  if ((int)blockIdx.x >= nrt * nct) return;
-  const int rt = blockIdx.x % nrt, ct = blockIdx.x / nrt;
-  const int i0 = p + rt * GR, c0 = ct * GC;
-  const cx<T> *F = arena + ft.off[f];
-  const int64_t ld = m;
-  cx<T> *Yf = Y + ft.yoff[f] * r;
-  __shared__ cx<T> Ls[GK][GR + 1];
-  __shared__ cx<T> Ys[GK][GC + 1];
-  const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
-  cx<T> acc[4][2];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = mk<T>(0, 0);
-  for (int k0 = 0; k0 < p; k0 += GK) {
-    for (int e = threadIdx.x; e < GK * GR; e += 256) {
-      int rr = e % GR, kk = e / GR;
-      int i = i0 + rr, k = k0 + kk;
-      Ls[kk][rr] = (i < m && k < p) ? F[i + (int64_t)k * ld] : mk<T>(0, 0);
-    }
-    for (int e = threadIdx.x; e < GK * GC; e += 256) {
-      int cc = e % GC, kk = e / GC;
-      int k = k0 + kk, c = c0 + cc;
-      Ys[kk][cc] = (k < p && c < r) ? Ysrc[ft.yoff[f] * r + (int64_t)k * r + c] : mk<T>(0, 0);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < GK; ++kk) {
-      cx<T> y0 = Ys[kk][tc], y1 = Ys[kk][tc + 16];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        cx<T> l = Ls[kk][tr + 16 * a];
-        acc[a][0] = cfma(acc[a][0], l, y0);
-        acc[a][1] = cfma(acc[a][1], l, y1);
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int i = i0 + tr + 16 * a;
-    if (i >= m) continue;
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int c = c0 + tc + 16 * b;
-      if (c >= r) continue;
-      cx<T> *d = Yf + (int64_t)i * r + c;
-      cx<T> v = *d;
-      v.re -= acc[a][b].re;
-      v.im -= acc[a][b].im;
-      *d = v;
-    }
-  }
-}
-
-// Backward update, split over the update rows: part[q][k][c] = sum over rows i
-// of split q of L21[i, k] x[struct_i, c] (BSPLIT rows per split), for every
-// pivot k of the fronts of a level; k_bwd_solve subtracts the partials.
+// Backward update rows are split into blocks of BSPLIT rows; each block's
+// partial sums L21^T x (per pivot) are added up by k_bwd_solve / k_bwd_w.
 constexpr int BSPLIT = 512;
-template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_gemm(const int32_t *__restrict__ lvl, FrontTab ft,
-                                                  const cx<T> *__restrict__ arena, const int64_t *__restrict__ sidx,
-                                                  const cx<T> *__restrict__ xM, const int64_t *__restrict__ part_off,
-                                                  cx<T> *__restrict__ part, int r) {
-  const int f = lvl[blockIdx.y];
-  const int m = ft.m[f], p = ft.p[f];
-  const int nrt = (p + GR - 1) / GR, nct = (r + GC - 1) / GC;
-  const int S = (m - p + BSPLIT - 1) / BSPLIT;
-  if ((int)blockIdx.x >= nrt * nct * S) return;
-  const int rt = blockIdx.x % nrt, ct = (blockIdx.x / nrt) % nct, q = blockIdx.x / (nrt * nct);
-  const int k0 = rt * GR, c0 = ct * GC;
-  const int ib = p + q * BSPLIT, ie = min(m, ib + BSPLIT);
-  const cx<T> *F = arena + ft.off[f];
-  const int64_t ld = m;
-  const int64_t *rows = sidx + ft.soff[f];
-  cx<T> *pt = part + part_off[blockIdx.y] * r + (int64_t)q * p * r;
-  __shared__ cx<T> Ls[GK][GR + 1];  // [i][k]
-  __shared__ cx<T> Xs[GK][GC + 1];  // [i][c]
-  const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
-  cx<T> acc[4][2];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = mk<T>(0, 0);
-  for (int i0 = ib; i0 < ie; i0 += GK) {
-    for (int e = threadIdx.x; e < GK * GR; e += 256) {
-      int ii = e % GK, kk = e / GK;
-      int i = i0 + ii, k = k0 + kk;
-      Ls[ii][kk] = (i < ie && k < p) ? F[i + (int64_t)k * ld] : mk<T>(0, 0);
-    }
-    for (int e = threadIdx.x; e < GK * GC; e += 256) {
-      int cc = e % GC, ii = e / GC;
-      int i = i0 + ii, c = c0 + cc;
-      Xs[ii][cc] = (i < ie && c < r) ? xM[rows[i - p] * r + c] : mk<T>(0, 0);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int ii = 0; ii < GK; ++ii) {
-      cx<T> x0 = Xs[ii][tc], x1 = Xs[ii][tc + 16];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        cx<T> l = Ls[ii][tr + 16 * a];
-        acc[a][0] = cfma(acc[a][0], l, x0);
-        acc[a][1] = cfma(acc[a][1], l, x1);
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int k = k0 + tr + 16 * a;
-    if (k >= p) continue;
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int c = c0 + tc + 16 * b;
-      if (c < r) pt[(int64_t)k * r + c] = acc[a][b];
-    }
-  }
-}
 
 // ------------------------------------------------------------ batched tile GEMM
 // C = alpha op(A) B (+ C), over a list of items of all fronts of a level.
@@ -1754,6 +1778,155 @@ __global__ void __launch_bounds__(256) k_tgemm(const GemmItem *__restrict__ item
       *d = v;
     }
   }
+}
+
+// ------------------------------------------------------------ batched complex GEMM of the solve
+// C = alpha op(A) B (+ C) over a list of items (all fronts of a level), one
+// CTA per BM x 64 output tile (BM = 32, 64 or 128, chosen per launch: small
+// tiles for the levels with few fronts): 256 threads with (BM/16) x 4 complex
+// accumulators each, K in chunks of 16 staged through shared memory, the next
+// chunk loaded into registers while the current one is multiplied.  Operands
+// are addressed by (row stride, column stride) into one of six buffers; B's
+// rows may be gathered through an index list (gath >= 0).  The fast thread
+// index runs along A's and C's contiguous dimension, so loads and stores
+// coalesce for column- and row-major operands alike.  Triangular operands
+// (stored with explicit zeros) bound the k range of a tile: mode 1 A lower
+// (k <= i), 2 B lower (k >= j), 3 A upper (k >= i).
+struct CgItem {
+  int64_t a, b, c, gath;
+  int32_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
+  int32_t M, N, K, mode, abuf, bbuf, cbuf, beta;
+  float alpha;
+  int32_t tile0;
+};
+template <typename T>
+struct CgBufs {
+  cx<T> *p[6];
+};
+constexpr int CG_BN = 64, CG_KC = 16;
+template <typename T, int BM>
+__global__ void __launch_bounds__(256) k_cgemm(const CgItem *__restrict__ items, int nitems, int ntiles,
+                                               CgBufs<T> bufs, const int64_t *__restrict__ gidx) {
+  constexpr int BN = CG_BN, KC = CG_KC, RA = BM / 16, RB = BN / 16;
+  constexpr int LA = BM * KC / 256, LB = BN * KC / 256;  // staged elements per thread
+  const int t = blockIdx.x;
+  if (t >= ntiles) return;
+  int lo = 0, hi = nitems - 1;  // last item with tile0 <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].tile0 <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const CgItem it = items[lo];
+  const cx<T> *A = bufs.p[it.abuf] + it.a;
+  const cx<T> *B = bufs.p[it.bbuf] + it.b;
+  cx<T> *C = bufs.p[it.cbuf] + it.c;
+  const int64_t *G = it.gath >= 0 ? gidx + it.gath : nullptr;
+  const int ntm = (it.M + BM - 1) / BM;
+  const int ti = t - it.tile0, tm = ti % ntm, tn = ti / ntm;
+  const int i0 = tm * BM, j0 = tn * BN;
+  int klo = 0, khi = it.K;
+  if (it.mode == 1) khi = min(it.K, i0 + BM);
+  if (it.mode == 2) klo = j0;
+  if (it.mode == 3) klo = i0;
+  __shared__ cx<T> As[KC][BM + 1];
+  __shared__ cx<T> Bs[KC][BN + 1];
+  // thread -> (row, column) of its outputs: rows fast for column-major C
+  const bool cfast = it.c_rs == 1;
+  const int tr = cfast ? (threadIdx.x & 15) : (threadIdx.x >> 4);
+  const int tc = cfast ? (threadIdx.x >> 4) : (threadIdx.x & 15);
+  // staging maps: the fast index along each operand's contiguous dimension
+  const bool afast = it.a_rs == 1, bfast = it.b_cs == 1;
+  cx<T> ra[LA], rb[LB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int x = afast ? e % BM : e / KC, kk = afast ? e / BM : e % KC;
+      const int i = i0 + x, k = k0 + kk;
+      ra[u] = (i < it.M && k < khi) ? A[(int64_t)i * it.a_rs + (int64_t)k * it.a_cs] : mk<T>(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int x = bfast ? e % BN : e / KC, kk = bfast ? e / BN : e % KC;
+      const int j = j0 + x, k = k0 + kk;
+      cx<T> v = mk<T>(0, 0);
+      if (j < it.N && k < khi) {
+        const int64_t kr = G ? G[k] : (int64_t)k;
+        v = B[kr * it.b_rs + (int64_t)j * it.b_cs];
+      }
+      rb[u] = v;
+    }
+  };
+  auto stage = [&]() {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int x = afast ? e % BM : e / KC, kk = afast ? e / BM : e % KC;
+      As[kk][x] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int x = bfast ? e % BN : e / KC, kk = bfast ? e / BN : e % KC;
+      Bs[kk][x] = rb[u];
+    }
+  };
+  cx<T> acc[RA][RB];
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < RB; ++b) acc[a][b] = mk<T>(0, 0);
+  if (klo < khi) load(klo);
+  for (int k0 = klo; k0 < khi; k0 += KC) {
+    __syncthreads();  // the previous chunk has been read
+    stage();
+    __syncthreads();
+    if (k0 + KC < khi) load(k0 + KC);  // in flight during the multiply
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      cx<T> av[RA], bv[RB];
+#pragma unroll
+      for (int a = 0; a < RA; ++a) av[a] = As[kk][tr + 16 * a];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) bv[b] = Bs[kk][tc + 16 * b];
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[a][b] = cfma(acc[a][b], av[a], bv[b]);
+    }
+  }
+  const T al = (T)it.alpha;
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int i = i0 + tr + 16 * a;
+    if (i >= it.M) continue;
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      const int j = j0 + tc + 16 * b;
+      if (j >= it.N) continue;
+      cx<T> *d = C + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
+      cx<T> v = mk<T>(al * acc[a][b].re, al * acc[a][b].im);
+      if (it.beta) {
+        const cx<T> o = *d;
+        v.re += o.re;
+        v.im += o.im;
+      }
+      *d = v;
+    }
+  }
+}
+
+template <typename T>
+static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, const CgBufs<T> &bufs,
+                         const int64_t *gidx, cudaStream_t s) {
+  if (bm == 32)
+    k_cgemm<T, 32><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
+  else if (bm == 64 || sizeof(T) == 8)
+    k_cgemm<T, 64><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
+  else
+    k_cgemm<T, (sizeof(T) == 4 ? 128 : 64)><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
 }
 
 // Inverse of each 32x32 unit-lower diagonal block of L11 (2x2 couplings are
@@ -1959,28 +2132,56 @@ __device__ __forceinline__ void atomic_max_pos(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// r = f - A x (fp64), per-column max |r| and max |f|; one warp per row
-__global__ void k_residual(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                           const double2 *__restrict__ val, const double2 *__restrict__ x,
-                           const double2 *__restrict__ f, double2 *__restrict__ res, int r,
-                           double *__restrict__ rnorm, double *__restrict__ fnorm) {
-  int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  int64_t a = ptr[row], b = ptr[row + 1];
-  for (int c = lane; c < r; c += 32) {
-    double2 acc = f[row * r + c];
-    double fm = fabs(acc.x) > 0 || fabs(acc.y) > 0 ? sqrt(acc.x * acc.x + acc.y * acc.y) : 0.0;
-    for (int64_t q = a; q < b; ++q) {
-      double2 av = val[q];
-      double2 xv = x[(int64_t)col[q] * r + c];
-      acc.x -= av.x * xv.x - av.y * xv.y;
-      acc.y -= av.x * xv.y + av.y * xv.x;
+// r = f - A x (fp64) with per-column max |r|^2 (and max |f|^2 when fnorm is
+// given); one warp per row, lanes over the right-hand sides, a bounded grid of
+// CTAs looping over the rows.  The maxima are reduced per CTA in shared memory
+// (2 r doubles of dynamic shared memory when smem_max != 0) and leave with
+// one atomic per column and CTA.
+__global__ void __launch_bounds__(256)
+    k_residual(int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+               const double *__restrict__ vre, const int64_t *__restrict__ iptr, const int32_t *__restrict__ icol,
+               const double *__restrict__ vim, const double2 *__restrict__ x, const double2 *__restrict__ f,
+               double2 *__restrict__ res, int r, double *__restrict__ rnorm, double *__restrict__ fnorm,
+               int smem_max) {
+  extern __shared__ double s_nrm[];  // [2][r]
+  if (smem_max)
+    for (int c = threadIdx.x; c < 2 * r; c += blockDim.x) s_nrm[c] = 0.0;
+  __syncthreads();
+  double *rmax = smem_max ? s_nrm : rnorm;
+  double *fmax_ = smem_max ? s_nrm + r : fnorm;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += nw) {
+    const int64_t a = ptr[row], b = ptr[row + 1];
+    if (a == b) {  // removed (PEC) edge: no equation, r = f
+      for (int c = lane; c < r; c += 32) res[row * r + c] = f[row * r + c];
+      continue;
     }
-    res[row * r + c] = acc;
-    if (a < b) {
-      atomic_max_pos(rnorm + c, sqrt(acc.x * acc.x + acc.y * acc.y));
-      atomic_max_pos(fnorm + c, fm);
+    for (int c = lane; c < r; c += 32) {
+      const double2 fv = f[row * r + c];
+      double2 acc = fv;
+      for (int64_t q = a; q < b; ++q) {  // real part
+        const double av = vre[q];
+        const double2 xv = x[(int64_t)col[q] * r + c];
+        acc.x -= av * xv.x;
+        acc.y -= av * xv.y;
+      }
+      for (int64_t q = iptr[row]; q < iptr[row + 1]; ++q) {  // j * imaginary part
+        const double av = vim[q];
+        const double2 xv = x[(int64_t)icol[q] * r + c];
+        acc.x += av * xv.y;
+        acc.y -= av * xv.x;
+      }
+      res[row * r + c] = acc;
+      atomic_max_pos(rmax + c, acc.x * acc.x + acc.y * acc.y);
+      if (fnorm) atomic_max_pos(fmax_ + c, fv.x * fv.x + fv.y * fv.y);
+    }
+  }
+  if (smem_max) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < r; c += blockDim.x) {
+      if (s_nrm[c] > 0.0) atomic_max_pos(rnorm + c, s_nrm[c]);
+      if (fnorm && s_nrm[r + c] > 0.0) atomic_max_pos(fnorm + c, s_nrm[r + c]);
     }
   }
 }
@@ -2078,9 +2279,12 @@ struct DeviceState {
   double *st_minpiv = nullptr;
   void *W = nullptr;
   // operator for residuals
-  int64_t *csr_ptr = nullptr;
-  int32_t *csr_col = nullptr;
-  double2 *csr_val = nullptr;
+  int64_t *csr_ptr = nullptr;  // A = Ar + j Ai: Ar on the full pattern,
+  int32_t *csr_col = nullptr;  // Ai (absorbing faces, lossy cells) on its own
+  double *csr_re = nullptr;
+  int64_t *csi_ptr = nullptr;
+  int32_t *csi_col = nullptr;
+  double *csi_val = nullptr;
   uint8_t *pec = nullptr;
   // solve buffers (capacity in RHS)
   int cap = 0;
@@ -2093,7 +2297,6 @@ struct DeviceState {
   std::vector<std::vector<int>> update_grid;  // per level, per step: grid.x upper bound
   std::vector<int> ea_grid;                   // per pass: grid.x (tiles) upper bound
   std::vector<int> level_maxm, pass_maxn;
-  std::vector<int> level_gemm_upd, level_gemm_piv;  // solve GEMM grid.x / (RHS tiles), max over the level
   // explicit L11^{-1} of every front (p x p column-major), built after each level
   void *linv = nullptr;
   int64_t *linv_off = nullptr;                 // per level position
@@ -2101,8 +2304,10 @@ struct DeviceState {
   void *tmp_inv = nullptr;                     // doubling-stage temporaries
   GemmItem *inv_items = nullptr;               // all factor-time doubling items
   std::vector<std::vector<std::array<int, 4>>> inv_stage;  // per level: (item0, nitems, ntiles, unused)
-  GemmItem *sol_items = nullptr;               // solve items for sol_r RHS (fwd then bwd per level)
-  std::vector<std::array<int, 6>> sol_lvl;     // per level: fwd (item0, n, tiles), bwd (item0, n, tiles)
+  CgItem *sol_items = nullptr;                 // solve GEMM items for sol_r RHS
+  // per level, (item0, nitems, ntiles) of: forward L11^{-1}, forward L21,
+  // backward L21^T (split partials), backward L11^{-T}
+  std::vector<std::array<int, 16>> sol_lvl;  // (item0, nitems, ntiles, row tile) per kind
   int sol_r = 0;
   void *Y2 = nullptr;
   cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;  // captured substitution sweeps
@@ -2113,11 +2318,11 @@ struct DeviceState {
   std::vector<uint8_t> lvl_tc;   // per level: tensor-core updates (mixed)
   std::vector<int> lvl_cs;       // per level: panel cluster size (0 = global panel)
   bool tuned = false;
-  bool tune_out = false;                       // fill tune_panel / tune_update on the next factor
-  std::vector<double> tune_panel, tune_update;
+  std::vector<double> tune_panel, tune_update;  // per-level ms of the last profiled factor
   std::vector<std::vector<int>> tc_grid;  // per level, per step: 128x64 tiles (upper bound)
   std::vector<int> level_maxp;   // largest pivot block per level
-  int32_t *nsplit = nullptr;     // per level position: row splits of k_bwd_gemm
+  int32_t *nsplit = nullptr;     // per level position: row splits of the backward partials
+  std::vector<int64_t> part_off_h;  // per level position: first partial row
   int64_t *part_off = nullptr;   // per level position: partial-buffer offset (units of r)
   int64_t part_rows = 0;         // max over levels of sum(nsplit * p)
   void *part = nullptr;
@@ -2197,9 +2402,29 @@ static int dev_init(Ctx &c) {
     std::vector<double2> v(P.ent_val.size());
     for (size_t i = 0; i < v.size(); ++i) v[i] = make_double2(P.ent_val[i].real(), P.ent_val[i].imag());
     CUDA_TRY(upload(d, &d->ent_val, v));
-    std::vector<double2> cv(P.csr_val.size());
-    for (size_t i = 0; i < cv.size(); ++i) cv[i] = make_double2(P.csr_val[i].real(), P.csr_val[i].imag());
-    CUDA_TRY(upload(d, &d->csr_val, cv));
+    // the residual's operator as Ar + j Ai: most entries are real, so the
+    // fp64 product costs two multiply-adds per entry instead of four
+    std::vector<double> re(P.csr_val.size()), iv;
+    std::vector<int64_t> ip(P.csr_ptr.size(), 0);
+    std::vector<int32_t> ic;
+    for (int64_t r = 0; r + 1 < (int64_t)P.csr_ptr.size(); ++r) {
+      for (int64_t q = P.csr_ptr[r]; q < P.csr_ptr[r + 1]; ++q) {
+        re[q] = P.csr_val[q].real();
+        if (P.csr_val[q].imag() != 0.0) {
+          ic.push_back(P.csr_col[q]);
+          iv.push_back(P.csr_val[q].imag());
+        }
+      }
+      ip[r + 1] = (int64_t)ic.size();
+    }
+    if (ic.empty()) {  // keep the device arrays non-null
+      ic.push_back(0);
+      iv.push_back(0.0);
+    }
+    CUDA_TRY(upload(d, &d->csr_re, re));
+    CUDA_TRY(upload(d, &d->csi_ptr, ip));
+    CUDA_TRY(upload(d, &d->csi_col, ic));
+    CUDA_TRY(upload(d, &d->csi_val, iv));
   }
   CUDA_TRY(upload(d, &d->csr_ptr, P.csr_ptr));
   CUDA_TRY(upload(d, &d->csr_col, P.csr_col));
@@ -2211,20 +2436,16 @@ static int dev_init(Ctx &c) {
   d->update_grid.assign(P.n_levels, {});
   d->level_maxm.assign(P.n_levels, 0);
   std::vector<int32_t> nsplit_h(nsn, 0);
-  std::vector<int64_t> part_off_h(nsn, 0);
+  d->part_off_h.assign(nsn, 0);
   d->part_rows = 0;
-  d->level_gemm_upd.assign(P.n_levels, 0);
-  d->level_gemm_piv.assign(P.n_levels, 0);
   for (int l = 0; l < P.n_levels; ++l) {
     int64_t prow = 0;
     for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
       int s = P.level_fronts[i];
       int S = (m[s] - pp[s] + BSPLIT - 1) / BSPLIT;
       nsplit_h[i] = S;
-      part_off_h[i] = prow;
+      d->part_off_h[i] = prow;
       prow += (int64_t)S * pp[s];
-      d->level_gemm_upd[l] = std::max(d->level_gemm_upd[l], (m[s] - pp[s] + GR - 1) / GR);
-      d->level_gemm_piv[l] = std::max(d->level_gemm_piv[l], S * ((pp[s] + GR - 1) / GR));
     }
     d->part_rows = std::max(d->part_rows, prow);
     int64_t w = 0;
@@ -2320,7 +2541,7 @@ static int dev_init(Ctx &c) {
     CUDA_TRY(upload(d, &d->linv_off, d->linv_off_h));
   }
   CUDA_TRY(upload(d, &d->nsplit, nsplit_h));
-  CUDA_TRY(upload(d, &d->part_off, part_off_h));
+  CUDA_TRY(upload(d, &d->part_off, d->part_off_h));
   const size_t esz = c.opt.precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
   CUDA_TRY(cudaMalloc(&d->W, std::max<int64_t>(wmax, 1) * esz));
   d->allocs.push_back(d->W);
@@ -2522,11 +2743,16 @@ static int factor_t(Ctx &c) {
   }
   c.stats.flops_update = fc[0];
   c.stats.flops_panel = fc[1];
+  c.lvl_cs = d->lvl_cs;
+  c.lvl_tc.assign(P.n_levels, 0);
+  for (int l = 0; l < P.n_levels; ++l)
+    c.lvl_tc[l] = sizeof(T) == 4 && (c.opt.update_kernel == 2 || (c.opt.update_kernel == 0 && d->lvl_tc[l]));
+  if (c.opt.panel_kernel == 1) c.lvl_cs.assign(P.n_levels, 0);
   if (d->prof.on) {
-    if (d->tune_out) {
-      d->tune_panel = d->prof.per_level(PC_PANEL, P.n_levels);
-      d->tune_update = d->prof.per_level(PC_UPDATE, P.n_levels);
-    }
+    d->tune_panel = d->prof.per_level(PC_PANEL, P.n_levels);
+    d->tune_update = d->prof.per_level(PC_UPDATE, P.n_levels);
+    c.lvl_ms_panel = d->tune_panel;
+    c.lvl_ms_update = d->tune_update;
     double ms[PC_N];
     d->prof.collect(ms);
     c.stats.ms_assemble = ms[PC_ASSEMBLE];
@@ -2623,7 +2849,6 @@ static int autotune(Ctx &c) {
   const bool prof = d->prof.on;
   const int uk = c.opt.update_kernel;
   d->prof.on = true;
-  d->tune_out = true;
   // trial A: fp32-FMA updates, smallest cluster
   std::vector<int> csA = d->lvl_cs, csB(nlev);
   // (clusters stay within the portable size 8)
@@ -2640,7 +2865,6 @@ static int autotune(Ctx &c) {
   std::vector<double> pB = d->tune_panel, uB = d->tune_update;
   c.opt.update_kernel = uk;
   d->prof.on = prof;
-  d->tune_out = false;
   if (rc != D3M_OK) {
     d->lvl_cs = csA;
     return rc;
@@ -2713,39 +2937,104 @@ static int ensure_rhs(Ctx &c, int r) {
   return D3M_OK;
 }
 
-// Work lists of the solve GEMMs for r right-hand sides: per level, the
-// forward items Y2[0:p] = L11^{-1} Y[0:p] and the backward items
-// Y2[0:p] = L11^{-T} Y[0:p] (buffers: 1 = L^{-1}, 2 = Y, 3 = Y2).
+// Work lists of the solve GEMMs for r right-hand sides, per level:
+//   forward   Y2[0:p] = L11^{-1} Y[0:p]                       (mixed factors)
+//             Y[p:m] -= L21 y[0:p]   (y = Y2 mixed, Y fp64)
+//   backward  part[q] = L21[split q]^T x[struct rows of split q]
+//             Y2[0:p] = L11^{-T} Y[0:p]                       (mixed factors)
+// Buffers: 0 arena, 1 L^{-1}, 2 Y, 3 Y2, 4 xM, 5 partials; B rows of the
+// backward items are gathered through the fronts' update-row lists.
 static int solve_items(Ctx &c, int r) {
   DeviceState *d = c.dev;
   if (d->sol_r == r && d->sol_items) return D3M_OK;
   const Plan &P = c.plan;
-  std::vector<GemmItem> items;
+  const bool mixed = c.opt.precision == D3M_MIXED;
+  std::vector<CgItem> items;
   d->sol_lvl.assign(P.n_levels, {});
+  int BM = 128;
+  auto tiles_of = [&](const CgItem &g) { return ((g.M + BM - 1) / BM) * ((g.N + CG_BN - 1) / CG_BN); };
   for (int l = 0; l < P.n_levels; ++l) {
-    for (int dir = 0; dir < 2; ++dir) {
+    for (int kind = 0; kind < 4; ++kind) {
+      // row tile of this launch: the fewest (efficiency-weighted) rows per SM
+      // over the waves of CTAs (1 resident CTA per SM for 128-row tiles, 2 for
+      // the smaller ones, by their register use)
+      int best = 64;
+      double bcost = 1e300;
+      for (int bm : {32, 64, 128}) {
+        if (bm == 128 && !mixed) continue;
+        BM = bm;
+        int64_t t = 0;
+        for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+          const int f = P.level_fronts[i];
+          const int pf = (int)(P.sn_end[f] - P.sn_start[f]);
+          const int mf = pf + (int)(P.struct_ptr[f + 1] - P.struct_ptr[f]);
+          const int M = kind == 1 ? mf - pf : pf;
+          const int S = kind == 2 ? (mf - pf + BSPLIT - 1) / BSPLIT : 1;
+          t += (int64_t)S * ((M + bm - 1) / bm) * ((r + CG_BN - 1) / CG_BN);
+        }
+        const int occ = bm == 128 ? 1 : 2;
+        const double eff = bm == 128 ? 1.0 : bm == 64 ? 0.85 : 0.6;
+        const double cost = (double)((t + 152 * occ - 1) / (152 * occ)) * bm / eff;
+        if (cost < bcost) {
+          bcost = cost;
+          best = bm;
+        }
+      }
+      BM = best;
       int first = (int)items.size(), tiles = 0;
       for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
-        int f = P.level_fronts[i];
-        int pf = (int)(P.sn_end[f] - P.sn_start[f]);
-        GemmItem g{};
-        g.a = d->linv_off_h[i];
-        if (dir == 0) {
-          g.a_rs = 1; g.a_cs = pf; g.mode = 1;
-        } else {
-          g.a_rs = pf; g.a_cs = 1; g.mode = 3;
+        const int f = P.level_fronts[i];
+        const int pf = (int)(P.sn_end[f] - P.sn_start[f]);
+        const int mf = pf + (int)(P.struct_ptr[f + 1] - P.struct_ptr[f]);
+        CgItem g{};
+        g.gath = -1;
+        g.N = r;
+        if (kind == 0 || kind == 3) {  // L11^{-1} (lower) or its transpose (upper)
+          if (!mixed) continue;
+          g.a = d->linv_off_h[i];
+          if (kind == 0) {
+            g.a_rs = 1; g.a_cs = pf; g.mode = 1;
+          } else {
+            g.a_rs = pf; g.a_cs = 1; g.mode = 3;
+          }
+          g.b = P.y_off[f] * r; g.b_rs = r; g.b_cs = 1;
+          g.c = P.y_off[f] * r; g.c_rs = r; g.c_cs = 1;
+          g.M = pf; g.K = pf;
+          g.abuf = 1; g.bbuf = 2; g.cbuf = 3; g.beta = 0; g.alpha = 1.f;
+          g.tile0 = tiles;
+          tiles += tiles_of(g);
+          items.push_back(g);
+        } else if (kind == 1) {  // Y[p:m] -= L21 y[0:p]
+          if (mf == pf || pf == 0) continue;
+          g.a = P.front_off[f] + pf; g.a_rs = 1; g.a_cs = mf;
+          g.b = P.y_off[f] * r; g.b_rs = r; g.b_cs = 1;
+          g.c = (P.y_off[f] + pf) * r; g.c_rs = r; g.c_cs = 1;
+          g.M = mf - pf; g.K = pf;
+          g.abuf = 0; g.bbuf = mixed ? 3 : 2; g.cbuf = 2; g.beta = 1; g.alpha = -1.f;
+          g.tile0 = tiles;
+          tiles += tiles_of(g);
+          items.push_back(g);
+        } else {  // partials of L21^T x over row splits
+          if (mf == pf || pf == 0) continue;
+          const int S = (mf - pf + BSPLIT - 1) / BSPLIT;
+          for (int q = 0; q < S; ++q) {
+            CgItem h = g;
+            const int rb = q * BSPLIT;
+            h.a = P.front_off[f] + pf + rb; h.a_rs = mf; h.a_cs = 1;
+            h.b = 0; h.b_rs = r; h.b_cs = 1; h.gath = P.struct_ptr[f] + rb;
+            h.c = (d->part_off_h[i] + (int64_t)q * pf) * r; h.c_rs = r; h.c_cs = 1;
+            h.M = pf; h.K = std::min(BSPLIT, mf - pf - rb);
+            h.abuf = 0; h.bbuf = 4; h.cbuf = 5; h.beta = 0; h.alpha = 1.f;
+            h.tile0 = tiles;
+            tiles += tiles_of(h);
+            items.push_back(h);
+          }
         }
-        g.b = P.y_off[f] * r; g.b_rs = r; g.b_cs = 1;
-        g.c = P.y_off[f] * r; g.c_rs = r; g.c_cs = 1;
-        g.M = pf; g.N = r; g.K = pf;
-        g.abuf = 1; g.bbuf = 2; g.cbuf = 3; g.beta = 0; g.alpha = 1.f;
-        g.tile0 = tiles;
-        tiles += ((pf + TG - 1) / TG) * ((r + TG - 1) / TG);
-        items.push_back(g);
       }
-      d->sol_lvl[l][3 * dir + 0] = first;
-      d->sol_lvl[l][3 * dir + 1] = (int)items.size() - first;
-      d->sol_lvl[l][3 * dir + 2] = tiles;
+      d->sol_lvl[l][4 * kind + 0] = first;
+      d->sol_lvl[l][4 * kind + 1] = (int)items.size() - first;
+      d->sol_lvl[l][4 * kind + 2] = tiles;
+      d->sol_lvl[l][4 * kind + 3] = BM;
     }
   }
   if (d->sol_items) {
@@ -2753,6 +3042,7 @@ static int solve_items(Ctx &c, int r) {
     d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), (void *)d->sol_items), d->allocs.end());
     d->sol_items = nullptr;
   }
+  if (items.empty()) items.push_back(CgItem{});
   CUDA_TRY(upload(d, &d->sol_items, items));
   d->sol_r = r;
   return D3M_OK;
@@ -2772,6 +3062,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
   cx<T> *Li = (cx<T> *)d->linv;
   const bool use_inv = sizeof(T) == 4;  // L11^{-1} exists for the mixed factors only
   constexpr int RC = 8;
+  const CgBufs<T> bufs{{arena, Li, Y, Y2, (cx<T> *)d->xM, (cx<T> *)d->part}};
   int64_t nl = 0;
   if (dir & 1) {
   PROF_BEGIN(PC_FWD);
@@ -2789,22 +3080,18 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
       k_fwd_ea<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, d->iperm, Y, r);
       ++nl;
     }
-    const cx<T> *ysrc;
+    const auto &sl = d->sol_lvl[l];
     if (use_inv) {
-      const auto &sl = d->sol_lvl[l];
-      k_tgemm<T><<<sl[2], 256, 0, s>>>(d->sol_items + sl[0], sl[1], sl[2], arena, Li, Y, Y2);
+      launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s);
       dim3 gdv((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
-      ysrc = Y2;
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
       k_fwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->dinv_d, d->dinv_o, d->psize, Y, (cx<T> *)d->zM, r);
-      ysrc = Y;
     }
     nl += 2;
-    if (d->level_gemm_upd[l] > 0) {
-      dim3 gg(d->level_gemm_upd[l] * ((r + GC - 1) / GC), nf);
-      k_fwd_gemm<T><<<gg, 256, 0, s>>>(lvl, ft, arena, Y, ysrc, r);
+    if (sl[5] > 0) {
+      launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s);
       ++nl;
     }
   }
@@ -2817,16 +3104,15 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
     const int32_t *ns = d->nsplit + P.level_ptr[l];
     const int64_t *po = d->part_off + P.level_ptr[l];
-    if (d->level_gemm_piv[l] > 0) {
-      dim3 gb(d->level_gemm_piv[l] * ((r + GC - 1) / GC), nf);
-      k_bwd_gemm<T><<<gb, 256, 0, s>>>(lvl, ft, arena, d->sidx, (const cx<T> *)d->xM, po, (cx<T> *)d->part, r);
+    const auto &sl = d->sol_lvl[l];
+    if (sl[9] > 0) {
+      launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s);
       ++nl;
     }
     if (use_inv) {
       dim3 gw((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
-      const auto &sl = d->sol_lvl[l];
-      k_tgemm<T><<<sl[5], 256, 0, s>>>(d->sol_items + sl[3], sl[4], sl[5], arena, Li, Y, Y2);
+      launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s);
       k_bwd_out<T><<<gw, 256, 0, s>>>(lvl, ft, d->perm, Y2, (cx<T> *)d->xM, r);
       nl += 3;
     } else {
@@ -2930,19 +3216,25 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   double maxres = 0;
   const bool refine = d->precision == D3M_MIXED;
   for (;;) {
-    CUDA_TRY(cudaMemsetAsync(d->norms, 0, 2 * r * sizeof(double), s));
+    // max |r|^2 per column each time, max |f|^2 on the first pass only
+    const bool first = iters == 0;
+    CUDA_TRY(cudaMemsetAsync(d->norms, 0, (first ? 2 : 1) * r * sizeof(double), s));
     {
       PROF_BEGIN(PC_RESID);
-      k_residual<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(n, d->csr_ptr, d->csr_col, d->csr_val, d->xe,
-                                                                   d->fe, d->re, r, d->norms, d->norms + r);
+      const int smem_max = r <= 2048;
+      const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 8));
+      k_residual<<<grid, 256, smem_max ? 2 * r * sizeof(double) : 0, s>>>(
+          n, d->csr_ptr, d->csr_col, d->csr_re, d->csi_ptr, d->csi_col, d->csi_val, d->xe, d->fe, d->re, r, d->norms, first ? d->norms + r : nullptr,
+          smem_max);
       PROF_END(PC_RESID);
     }
     ++nl;
-    CUDA_TRY(cudaMemcpyAsync(nh.data(), d->norms, 2 * r * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(nh.data(), d->norms, (first ? 2 : 1) * r * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     maxres = 0;
     for (int q = 0; q < r; ++q) {
-      double rr = nh[r + q] > 0 ? nh[q] / nh[r + q] : nh[q];
+      const double rn = std::sqrt(nh[q]), fn = std::sqrt(nh[r + q]);
+      double rr = fn > 0 ? rn / fn : rn;
       if (info && info->resid) info->resid[q] = rr;
       maxres = std::max(maxres, rr);
     }

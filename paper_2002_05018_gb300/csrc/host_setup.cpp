@@ -960,6 +960,27 @@ extern "C" int d3m_structure(d3m_ctx *h, int32_t which, void *buf, size_t *bytes
       }
       return put(buf, bytes, d);
     }
+    case D3M_LEVELS: {
+      const d3m::Ctx &c = h->c;
+      std::vector<double> d((size_t)p.n_levels * 8, 0.0);
+      for (int l = 0; l < p.n_levels; ++l) {
+        double *o = d.data() + (size_t)l * 8;
+        for (int i = p.level_ptr[l]; i < p.level_ptr[l + 1]; ++i) {
+          int32_t f = p.level_fronts[i];
+          int64_t pp = p.sn_end[f] - p.sn_start[f];
+          int64_t m = pp + p.struct_ptr[f + 1] - p.struct_ptr[f];
+          o[0] += 1;
+          o[1] = std::max(o[1], (double)pp);
+          o[2] = std::max(o[2], (double)m);
+          for (int64_t kk = 0; kk < pp; ++kk) o[3] += 4.0 * double(m - kk - 1) * double(m - kk);
+        }
+        if ((size_t)l < c.lvl_ms_panel.size()) o[4] = c.lvl_ms_panel[l];
+        if ((size_t)l < c.lvl_ms_update.size()) o[5] = c.lvl_ms_update[l];
+        if ((size_t)l < c.lvl_tc.size()) o[6] = c.lvl_tc[l];
+        if ((size_t)l < c.lvl_cs.size()) o[7] = c.lvl_cs[l];
+      }
+      return put(buf, bytes, d);
+    }
     case D3M_STATS: {
       std::vector<d3m_stats> s(1, h->c.stats);
       return put(buf, bytes, s);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libd3m.so")
 
 D3M_OK, D3M_EINVAL, D3M_ENOMEM, D3M_ESINGULAR, D3M_ENOCONV, D3M_ETIMEOUT, D3M_ECUDA, D3M_ESTATE = range(8)
 FP64, MIXED = 0, 1
-SN_RANGE, SN_PARENT, SN_KIND, SN_STRUCT, M_MAP, LM, BLOCKS, LAMBDA, STATS, M_ENTRIES = range(10)
+SN_RANGE, SN_PARENT, SN_KIND, SN_STRUCT, M_MAP, LM, BLOCKS, LAMBDA, STATS, M_ENTRIES, LEVELS = range(11)
 
 _SYMBOLS = ["d3m_setup", "d3m_factor", "d3m_solve", "d3m_solve_host", "d3m_rhs_planewave",
             "d3m_structure", "d3m_dense_ldlt", "d3m_dense_ldlt_noalloc", "d3m_export_front", "d3m_stats_get",
@@ -237,7 +237,7 @@ class Solver:
     def structure(self, which):
         n = ctypes.c_size_t(0)
         self._check(self.lib.d3m_structure(self.h, which, None, ctypes.byref(n)))
-        dt = np.float64 if which in (LAMBDA, M_ENTRIES) else np.int64
+        dt = np.float64 if which in (LAMBDA, M_ENTRIES, LEVELS) else np.int64
         buf = np.zeros(max(n.value // 8, 1), dt)
         self._check(self.lib.d3m_structure(self.h, which, buf.ctypes.data, ctypes.byref(n)))
         buf = buf[: n.value // 8]
@@ -249,6 +249,8 @@ class Solver:
             return buf.view(np.complex128)
         if which == M_ENTRIES:
             return buf.reshape(-1, 4)
+        if which == LEVELS:
+            return buf.reshape(-1, 8)
         return buf
 
     def lam(self, nrhs):

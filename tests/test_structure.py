@@ -76,3 +76,32 @@ def test_rhs_planewave_matches_oracle():
     f = s.rhs_planewave(w.khat_pol6())
     fo = fem.rhs_planewave(w)
     assert np.abs(f - fo).max() < 1e-13 * np.abs(fo).max()
+
+
+def test_level_table_matches_tree_heights():
+    """D3M_LEVELS: fronts grouped by height in the supernodal elimination tree
+    (leaves 0, a parent one above its highest child), computed here from the
+    oracle's plan; per-level flops add up to the factorisation's total."""
+    w = W.make(1)
+    dec = decomp.decompose(w)
+    plan = ordering.build_plan(dec, leaf_max=64)
+    r, c = ordering.saddle_pattern(dec, plan)
+    ordering.symbolic(plan, r, c)
+    n = len(plan.sn_start)
+    h = np.zeros(n, np.int64)
+    for q in range(n):  # children precede parents in elimination order
+        if plan.parent[q] >= 0:
+            h[plan.parent[q]] = max(h[plan.parent[q]], h[q] + 1)
+    s = d3m.Solver.from_workload(w, leaf_max=64)
+    lv = s.structure(d3m.LEVELS)
+    assert lv.shape == (h.max() + 1, 8)
+    pp = np.asarray(plan.sn_end) - np.asarray(plan.sn_start)
+    mm = pp + np.array([len(plan.struct[q]) for q in range(n)])
+    for L in range(h.max() + 1):
+        sel = h == L
+        assert lv[L, 0] == sel.sum() and lv[L, 1] == pp[sel].max() and lv[L, 2] == mm[sel].max()
+    st = s.stats()
+    total = st["flops_interior"] + st["flops_domain"] + st["flops_k"]
+    assert abs(lv[:, 3].sum() - total) <= 1e-9 * total
+    assert np.all(lv[:, 4:] == 0)  # nothing factored yet
+    s.close()
