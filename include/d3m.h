@@ -107,6 +107,14 @@ typedef struct {
                            defaults: FMA updates, smallest fitting cluster) */
   const char *autotune_cache; /* optional file: read the tuned schedule from it when
                            it matches this problem, write it after tuning; NULL = none */
+  int32_t lookahead;    /* 0 = off (default): every trailing update completes
+                           before the next panel; 1 = overlap: the
+                           Schur-complement part of each update runs on a second,
+                           low-priority stream while the next panels of the front
+                           proceed (they only touch its pivot block).  Both give
+                           bitwise identical factors; on GB300 the overlap is
+                           slower, since a full-grid update leaves no SM room for
+                           the panel's CTAs. */
 } d3m_options;
 
 /* Per-solve report: per column relative residual (Numerical Results

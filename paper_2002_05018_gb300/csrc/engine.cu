@@ -256,13 +256,16 @@ __global__ void __launch_bounds__(PANEL_THREADS)
             cx<T> *__restrict__ arena, cx<T> *__restrict__ Wbuf, int32_t *__restrict__ perm,
             double2 *__restrict__ dinv_d, double2 *__restrict__ dinv_o, int8_t *__restrict__ psize,
             int32_t *__restrict__ st_k0, int32_t *__restrict__ st_kb, int32_t *__restrict__ st_info,
-            double *__restrict__ st_minpiv, double *__restrict__ flop_cnt) {
+            double *__restrict__ st_minpiv, double *__restrict__ flop_cnt, int2 *__restrict__ snap) {
   const int f = lvl[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f];
   const int k0 = st_k0[f];
   const int tid = threadIdx.x, nth = blockDim.x;
   if (k0 >= p) {
-    if (tid == 0) st_kb[f] = 0;
+    if (tid == 0) {
+      st_kb[f] = 0;
+      snap[blockIdx.x] = make_int2(k0, 0);
+    }
     return;
   }
   cx<T> *F = arena + ft.off[f];
@@ -439,6 +442,7 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   if (tid == 0) {
     st_k0[f] = k;
     st_kb[f] = j;
+    snap[blockIdx.x] = make_int2(k, j);
     if (s_minpiv < st_minpiv[f]) st_minpiv[f] = s_minpiv;
     if (flop_cnt) {
       const double n = (double)(m - k);
@@ -608,7 +612,7 @@ __global__ void __launch_bounds__(512)
                double2 *__restrict__ dinv_d, double2 *__restrict__ dinv_o, int8_t *__restrict__ psize,
                int32_t *__restrict__ st_k0, int32_t *__restrict__ st_kb, int32_t *__restrict__ st_info,
                double *__restrict__ st_minpiv, double *__restrict__ flop_cnt, int2 *__restrict__ swp, int rcap,
-               int mcap) {
+               int mcap, int2 *__restrict__ snap) {
   // fp32: every thread takes the decisions; fp64: one thread, then a barrier
   constexpr bool ONE = sizeof(T) == 8;
   cg::cluster_group cl = cg::this_cluster();
@@ -620,7 +624,10 @@ __global__ void __launch_bounds__(512)
   const int k0 = st_k0[f];
   const int tid = threadIdx.x, nth = blockDim.x;
   if (k0 >= p) {  // uniform over the cluster
-    if (rank == 0 && tid == 0) st_kb[f] = 0;
+    if (rank == 0 && tid == 0) {
+      st_kb[f] = 0;
+      snap[fi] = make_int2(k0, 0);
+    }
     return;
   }
   cx<T> *F = arena + ft.off[f];
@@ -647,12 +654,12 @@ __global__ void __launch_bounds__(512)
   __shared__ PivotDec<T> pd;          // fp64 path: the decision of thread 0
   __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
   __shared__ ArgMaxT<T> red[64];
-  __shared__ int s_nmv;
+  __shared__ int s_nmv, s_nout;
   __shared__ int2 s_mv[2 * NB];       // rows moved by the panel: (destination, source)
   for (int q = tid; q < nr; q += nth) p2s[q] = q;  // slot q holds row k0 + q initially
-  if (rank == 0 && tid < NB) swp[(int64_t)fi * NB + tid] = make_int2(-1, -1);
+  if (rank == 0 && tid < 2 * NB) swp[(int64_t)fi * 2 * NB + tid] = make_int2(-1, -1);
   for (int q = tid; q < ns; q += nth) spos[q] = k0 + s_lo + q;
-  if (tid == 0) s_nmv = 0;
+  if (tid == 0) s_nmv = s_nout = 0;
   __syncthreads();
   if (CS > 1) cl.sync();
   // a cluster of one synchronises like a plain block
@@ -834,7 +841,6 @@ __global__ void __launch_bounds__(512)
         int32_t a = pv[kk];
         pv[kk] = pv[kp];
         pv[kp] = a;
-        swp[(int64_t)fi * NB + j] = make_int2(kk, kp);  // replayed on the update rows by k_l21
       }
       csync();  // the moves have read their sources; every thread has read p2s
       for (int q = tid; q < ns; q += nth) {
@@ -956,6 +962,14 @@ __global__ void __launch_bounds__(512)
     }
   __syncthreads();  // Ls is free from here on: staging buffer for the moves
   const int nmv = s_nmv;
+  // the panel's column permutation for k_l21 (update rows): per panel column
+  // its source column, then the moves (destination, source) of the columns
+  // right of the panel
+  if (rank == 0) {
+    int2 *rec = swp + (int64_t)fi * 2 * NB;
+    if (tid < j) rec[tid] = make_int2(k0 + p2s[tid], 0);
+    if (tid < nmv && s_mv[tid].x >= k0 + j) rec[NB + atomicAdd(&s_nout, 1)] = s_mv[tid];
+  }
   if (nmv > 0 && k0 > 0) {
     const int cap = rcap * LSTR;
     const int cpc = cap / nmv;  // columns per chunk (nmv <= min(2 NB, nr) <= LSTR rcap)
@@ -977,6 +991,7 @@ __global__ void __launch_bounds__(512)
   if (rank == 0 && tid == 0) {
     st_k0[f] = k;
     st_kb[f] = j;
+    snap[fi] = make_int2(k, j);  // this step's (k0 + kb, kb) for the trailing updates
   }
   if (tid == 0) {
     if (flop_cnt && rank == 0) {
@@ -996,7 +1011,9 @@ static size_t panel_cl_smem(int rcap, int mcap, size_t esz) {
 }
 
 // Update rows of the panel's columns (rows p..m-1), Algorithm 1's triangular
-// solve: replay the panel's interchanges on the row, then w = a L11^{-T}
+// solve: apply the panel's column permutation to the row (the panel columns
+// gathered from their source columns, the moved columns right of the panel
+// rewritten; all loads before any store), then w = a L11^{-T}
 // (forward substitution with the panel's unit-lower block), L21 = w D^{-1};
 // L21 goes to the front, w (= L21 D) to the workspace for the trailing update.
 // One thread per update row, all fronts of the level.
@@ -1021,14 +1038,20 @@ __global__ void __launch_bounds__(128) k_l21(const int32_t *__restrict__ lvl, Fr
   __shared__ cx<T> L11[NB][NB + 1];
   __shared__ cx<T> Di[NB], Do[NB];
   __shared__ int Dz[NB];
-  __shared__ int2 sw[NB];
+  __shared__ int s_src[NB];   // source column of panel column t
+  __shared__ int2 s_out[NB];  // moves right of the panel: (destination, source)
+  __shared__ int s_nout;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     int a = e % NB, b = e / NB;
     L11[a][b] = (a < kb && b < a) ? F[k0 + a + (int64_t)(k0 + b) * ld] : mk<T>(0, 0);
   }
   if (threadIdx.x < NB) {
     int t = threadIdx.x;
-    sw[t] = t < kb ? swp[(int64_t)fi * NB + t] : make_int2(-1, -1);
+    const int2 *rec = swp + (int64_t)fi * 2 * NB;
+    s_src[t] = t < kb ? rec[t].x : k0 + t;
+    s_out[t] = rec[NB + t];
+    const unsigned ball = __ballot_sync(0xffffffffu, rec[NB + t].x >= 0);
+    if (t == 0) s_nout = __popc(ball);
     if (t < kb) {
       Di[t] = from_d<T>(dinv_d[ft.piv[f] + k0 + t]);
       Do[t] = from_d<T>(dinv_o[ft.piv[f] + k0 + t]);
@@ -1038,19 +1061,22 @@ __global__ void __launch_bounds__(128) k_l21(const int32_t *__restrict__ lvl, Fr
   __syncthreads();
   // 2x2 couplings inside L11 are zero by construction (stored as 0)
   if (r < m) {
-    // replay the panel's interchanges on this row (columns kk <-> kp, in order;
-    // the thread owns the row, so plain loads/stores keep the order)
-    for (int t = 0; t < kb; ++t) {
-      int2 q = sw[t];
-      if (q.x < 0) continue;
-      cx<T> *fa = F + r + (int64_t)q.x * ld, *fb = F + r + (int64_t)q.y * ld;
-      cx<T> va = *fa, vb = *fb;
-      *fa = vb;
-      *fb = va;
-    }
+    // the panel's column permutation on this row (the thread owns the row):
+    // the panel columns gathered from their sources, then the columns right
+    // of the panel, whose sources are panel columns that no move rewrites
+    const int nout = s_nout;
     cx<T> a[NB];
 #pragma unroll
-    for (int t = 0; t < NB; ++t) a[t] = t < kb ? F[r + (int64_t)(k0 + t) * ld] : mk<T>(0, 0);
+    for (int t = 0; t < NB; ++t) a[t] = t < kb ? F[r + (int64_t)s_src[t] * ld] : mk<T>(0, 0);
+    for (int u0 = 0; u0 < nout; u0 += 8) {
+      cx<T> o[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u0 + u < nout) o[u] = F[r + (int64_t)s_out[u0 + u].y * ld];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u0 + u < nout) F[r + (int64_t)s_out[u0 + u].x * ld] = o[u];
+    }
     // forward substitution: w[t] = a[t] - sum_{u<t} L11[t][u] w[u]
 #pragma unroll
     for (int t = 1; t < NB; ++t) {
@@ -1114,9 +1140,10 @@ template <typename T>
 static cudaError_t launch_panel(int cs, int pmax, int mmax, int nf, const int32_t *lvl, FrontTab ft,
                                 const int64_t *wofs, cx<T> *arena, cx<T> *W, int32_t *perm, double2 *dd,
                                 double2 *dof, int8_t *ps, int32_t *k0, int32_t *kb, int32_t *info, double *minpiv,
-                                double *flops, int2 *swp, cudaStream_t s) {
+                                double *flops, int2 *swp, int2 *snap, cudaStream_t s) {
   if (cs <= 0) {
-    k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv, flops);
+    k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv, flops,
+                                            snap);
     return cudaGetLastError();
   }
   cudaError_t e = panel_attrs<T>();
@@ -1136,7 +1163,7 @@ static cudaError_t launch_panel(int cs, int pmax, int mmax, int nf, const int32_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, k_panel_cl<T>, lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv,
-                         flops, swp, rcap, mcap);
+                         flops, swp, rcap, mcap, snap);
   if (e != cudaSuccess) return e;
   if (mmax > 0) {
     dim3 g((unsigned)std::max(1, (mmax + 127) / 128), (unsigned)nf);
@@ -1151,23 +1178,30 @@ static cudaError_t launch_panel(int cs, int pmax, int mmax, int nf, const int32_
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_update(const int32_t *__restrict__ lvl, FrontTab ft, const int64_t *__restrict__ wofs,
-             cx<T> *__restrict__ arena, const cx<T> *__restrict__ Wbuf,
-             const int32_t *__restrict__ st_k0, const int32_t *__restrict__ st_kb) {
+             cx<T> *__restrict__ arena, const cx<T> *__restrict__ Wbuf, const int2 *__restrict__ snap,
+             int mode) {
   const int f = lvl[blockIdx.y];
-  const int kb = st_kb[f];
+  const int2 sk = snap[blockIdx.y];
+  const int kb = sk.y;
   if (kb == 0) return;
-  const int c0 = st_k0[f];
+  const int c0 = sk.x;
   const int k0 = c0 - kb;
-  const int m = ft.m[f];
+  const int m = ft.m[f], p = ft.p[f];
+  // column window: mode 0 every trailing column, 1 those of the pivot block
+  // (< p), 2 those of the Schur complement (>= p)
+  const int clo = mode == 2 ? max(c0, p) : c0, chi = mode == 1 ? p : m;
   const int I0 = c0 / UT;
   const int nt = (m + UT - 1) / UT - I0;
-  const int t = blockIdx.x;
-  if (nt <= 0 || t >= nt * (nt + 1) / 2) return;
+  const int ntl = nt > 0 ? nt * (nt + 1) / 2 : 0;
+  // tiles of the trailing lower triangle, grid-strided (a launch may use
+  // fewer CTAs than tiles, leaving room on every SM for other kernels)
+  for (int t = blockIdx.x; t < ntl; t += gridDim.x) {
   int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while (ii * (ii + 1) / 2 > t) --ii;
   while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
   const int jj = t - ii * (ii + 1) / 2;
   const int r0 = (I0 + ii) * UT, cc0 = (I0 + jj) * UT;
+  if (cc0 + UT <= clo || cc0 >= chi) continue;  // uniform per CTA
   cx<T> *F = arena + ft.off[f];
   const cx<T> *W = Wbuf + wofs[blockIdx.y];
   const int64_t ld = m;
@@ -1186,7 +1220,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int cidx = cc0 + tc + 16 * b;
-      cv[a][b] = (i < m && cidx >= c0 && cidx <= i) ? F[i + (int64_t)cidx * ld] : mk<T>(0, 0);
+      cv[a][b] = (i < m && cidx >= clo && cidx < chi && cidx <= i) ? F[i + (int64_t)cidx * ld] : mk<T>(0, 0);
     }
   }
   for (int t0 = 0; t0 < kb; t0 += KC) {
@@ -1220,9 +1254,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int cidx = cc0 + tc + 16 * b;
-      if (cidx < c0 || cidx > i) continue;
+      if (cidx < clo || cidx >= chi || cidx > i) continue;
       F[i + (int64_t)cidx * ld] = cv[a][b];
     }
+  }
+  __syncthreads();  // the shared tiles are restaged for the next tile
   }
 }
 
@@ -1281,15 +1317,17 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, 
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_update_tc(const int32_t *__restrict__ lvl, FrontTab ft, const int64_t *__restrict__ wofs,
-                cx<T> *__restrict__ arena, const cx<T> *__restrict__ Wbuf, const int32_t *__restrict__ st_k0,
-                const int32_t *__restrict__ st_kb, int32_t *__restrict__ err) {
+                cx<T> *__restrict__ arena, const cx<T> *__restrict__ Wbuf, const int2 *__restrict__ snap, int mode,
+                int32_t *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const int f = lvl[blockIdx.y];
-  const int kb = st_kb[f];
+  const int2 sk = snap[blockIdx.y];
+  const int kb = sk.y;
   if (kb == 0) return;
-  const int c0 = st_k0[f];
+  const int c0 = sk.x;
   const int k0 = c0 - kb;
-  const int m = ft.m[f];
+  const int m = ft.m[f], p = ft.p[f];
+  const int clo = mode == 2 ? max(c0, p) : c0, chi = mode == 1 ? p : m;  // column window as in k_update
   // tiles: row blocks of 128 from R0, column blocks of 64 from C0, lower part
   const int R0 = (c0 / TCM) * TCM, C0 = (c0 / TCN) * TCN;
   const int nI = (m - R0 + TCM - 1) / TCM, nJmax = (m - C0 + TCN - 1) / TCN;
@@ -1306,6 +1344,7 @@ __global__ void __launch_bounds__(128)
   }
   if (J < 0) return;  // uniform per CTA
   const int rs = R0 + I * TCM, cs = C0 + J * TCN;
+  if (cs + TCN <= clo || cs >= chi) return;  // uniform per CTA, before any TMEM allocation
   cx<T> *F = arena + ft.off[f];
   const cx<T> *W = Wbuf + wofs[blockIdx.y];
   const int64_t ld = m;
@@ -1426,7 +1465,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int col = cs + cc + q;
-          if (col < c0 || col > row) continue;
+          if (col < clo || col >= chi || col > row) continue;
           cx<T> *dst = F + row + (int64_t)col * ld;
           cx<T> v = *dst;
           v.re -= (T)__uint_as_float(vr[q]);
@@ -1452,8 +1491,8 @@ static cudaError_t tc_attrs() {
 }
 template <typename T>
 static void launch_update_tc(dim3 g, cudaStream_t s, const int32_t *lvl, FrontTab ft, const int64_t *wofs,
-                             cx<T> *arena, const cx<T> *W, const int32_t *k0, const int32_t *kb, int32_t *err) {
-  if constexpr (sizeof(T) == 4) k_update_tc<T><<<g, 128, TC_SMEM, s>>>(lvl, ft, wofs, arena, W, k0, kb, err);
+                             cx<T> *arena, const cx<T> *W, const int2 *snap, int mode, int32_t *err) {
+  if constexpr (sizeof(T) == 4) k_update_tc<T><<<g, 128, TC_SMEM, s>>>(lvl, ft, wofs, arena, W, snap, mode, err);
 }
 
 // ------------------------------------------------------------ solve kernels
@@ -1688,99 +1727,7 @@ __global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ l
 // partial sums L21^T x (per pivot) are added up by k_bwd_solve / k_bwd_w.
 constexpr int BSPLIT = 512;
 
-// ------------------------------------------------------------ batched tile GEMM
-// C = alpha op(A) B (+ C), over a list of items of all fronts of a level.
-// Operands are addressed by (row stride, column stride) into one of four
-// buffers, so column-major fronts, row-major RHS blocks and transposed views
-// all fit.  Triangular operands (stored with explicit zeros) bound the k
-// range per output tile: mode 1 A lower (k <= i), 2 B lower (k >= j), 3 A
-// upper (k >= i).
-struct GemmItem {
-  int64_t a, b, c;
-  int32_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
-  int32_t M, N, K, mode, abuf, bbuf, cbuf, beta;
-  float alpha;
-  int32_t tile0;
-};
-constexpr int TG = 64, TGK = 16;
-template <typename T>
-__global__ void __launch_bounds__(256) k_tgemm(const GemmItem *__restrict__ items, int nitems, int ntiles,
-                                               cx<T> *b0, cx<T> *b1, cx<T> *b2, cx<T> *b3) {
-  const int t = blockIdx.x;
-  if (t >= ntiles) return;
-  int lo = 0, hi = nitems - 1;  // last item with tile0 <= t
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (items[mid].tile0 <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  const GemmItem it = items[lo];
-  cx<T> *bufs[4] = {b0, b1, b2, b3};
-  const cx<T> *A = bufs[it.abuf] + it.a;
-  const cx<T> *B = bufs[it.bbuf] + it.b;
-  cx<T> *C = bufs[it.cbuf] + it.c;
-  const int ntm = (it.M + TG - 1) / TG;
-  const int ti = t - it.tile0, tm = ti % ntm, tn = ti / ntm;
-  const int i0 = tm * TG, j0 = tn * TG;
-  int klo = 0, khi = it.K;
-  if (it.mode == 1) khi = min(it.K, i0 + TG);
-  if (it.mode == 2) klo = j0;
-  if (it.mode == 3) klo = i0;
-  __shared__ cx<T> As[TGK][TG + 1];
-  __shared__ cx<T> Bs[TGK][TG + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  cx<T> acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = mk<T>(0, 0);
-  for (int k0 = klo; k0 < khi; k0 += TGK) {
-    for (int e = threadIdx.x; e < TGK * TG; e += 256) {
-      int x = e % TG, kk = e / TG;
-      int i = i0 + x, k = k0 + kk;
-      As[kk][x] = (i < it.M && k < khi) ? A[(int64_t)i * it.a_rs + (int64_t)k * it.a_cs] : mk<T>(0, 0);
-    }
-    for (int e = threadIdx.x; e < TGK * TG; e += 256) {
-      int x = e % TG, kk = e / TG;
-      int j = j0 + x, k = k0 + kk;
-      Bs[kk][x] = (j < it.N && k < khi) ? B[(int64_t)k * it.b_rs + (int64_t)j * it.b_cs] : mk<T>(0, 0);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < TGK; ++kk) {
-      cx<T> av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = cfma(acc[a][b], av[a], bv[b]);
-    }
-    __syncthreads();
-  }
-  const T al = (T)it.alpha;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int i = i0 + ty + 16 * a;
-    if (i >= it.M) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int j = j0 + tx + 16 * b;
-      if (j >= it.N) continue;
-      cx<T> *d = C + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
-      cx<T> v = mk<T>(al * acc[a][b].re, al * acc[a][b].im);
-      if (it.beta) {
-        v.re += d->re;
-        v.im += d->im;
-      }
-      *d = v;
-    }
-  }
-}
-
-// ------------------------------------------------------------ batched complex GEMM of the solve
+// ------------------------------------------------------------ batched complex GEMM
 // C = alpha op(A) B (+ C) over a list of items (all fronts of a level), one
 // CTA per BM x 64 output tile (BM = 32, 64 or 128, chosen per launch: small
 // tiles for the levels with few fronts): 256 threads with (BM/16) x 4 complex
@@ -2206,16 +2153,16 @@ struct Profiler {
     }
     return pool[used++];
   }
-  void begin(int cls, cudaEvent_t &e0) {
+  void begin(int cls, cudaEvent_t &e0, cudaStream_t st = nullptr) {
     if (!on) return;
     e0 = get();
-    cudaEventRecord(e0, s);
+    cudaEventRecord(e0, st ? st : s);
     (void)cls;
   }
-  void end(int cls, cudaEvent_t e0) {
+  void end(int cls, cudaEvent_t e0, cudaStream_t st = nullptr) {
     if (!on) return;
     cudaEvent_t e1 = get();
-    cudaEventRecord(e1, s);
+    cudaEventRecord(e1, st ? st : s);
     marks.push_back({cls, {e0, e1}});
     mark_level.push_back(cur_level);
   }
@@ -2252,6 +2199,10 @@ struct Profiler {
   cudaEvent_t pe_##cls{}; \
   d->prof.begin(cls, pe_##cls)
 #define PROF_END(cls) d->prof.end(cls, pe_##cls)
+#define PROF_BEGIN_ON(cls, st) \
+  cudaEvent_t pb_##cls{};      \
+  d->prof.begin(cls, pb_##cls, st)
+#define PROF_END_ON(cls, st) d->prof.end(cls, pb_##cls, st)
 
 // ------------------------------------------------------------ device state
 struct DeviceState {
@@ -2264,6 +2215,14 @@ struct DeviceState {
   cudaStream_t stream = nullptr;
   bool own_stream = false;       // created here when the caller passed the legacy NULL stream
   cudaEvent_t legacy_ev = nullptr;
+  // look-ahead: the Schur-complement part of each trailing update runs on a
+  // second, low-priority stream while the next panels proceed on the first;
+  // W and the per-step (k0 + kb, kb) snapshots rotate through three slots
+  cudaStream_t stream_b = nullptr;
+  cudaEvent_t ev_step[3] = {}, ev_schur[3] = {}, ev_b = nullptr;
+  int2 *snap = nullptr;          // [3][level position]
+  int64_t wslot = 0;             // elements per W slot
+  bool lookahead_off = false;    // set while the autotuner times the kernels
   // plan tables
   int32_t *f_m = nullptr, *f_p = nullptr, *f_parent = nullptr;
   int64_t *f_off = nullptr, *f_piv = nullptr, *f_soff = nullptr, *f_start = nullptr, *f_y = nullptr;
@@ -2302,8 +2261,8 @@ struct DeviceState {
   int64_t *linv_off = nullptr;                 // per level position
   std::vector<int64_t> linv_off_h;
   void *tmp_inv = nullptr;                     // doubling-stage temporaries
-  GemmItem *inv_items = nullptr;               // all factor-time doubling items
-  std::vector<std::vector<std::array<int, 4>>> inv_stage;  // per level: (item0, nitems, ntiles, unused)
+  CgItem *inv_items = nullptr;                 // all factor-time doubling items
+  std::vector<std::vector<std::array<int, 4>>> inv_stage;  // per level: (item0, nitems, ntiles, row tile)
   CgItem *sol_items = nullptr;                 // solve GEMM items for sol_r RHS
   // per level, (item0, nitems, ntiles) of: forward L11^{-1}, forward L21,
   // backward L21^T (split partials), backward L11^{-T}
@@ -2313,7 +2272,7 @@ struct DeviceState {
   cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;  // captured substitution sweeps
   int g_r = 0;
   int64_t g_launches[2] = {0, 0};
-  int2 *swp = nullptr;           // per level position: interchanges of the current panel (NB each)
+  int2 *swp = nullptr;           // per level position: the current panel's column permutation (2 NB each)
   int32_t *tc_err = nullptr;     // set by k_update_tc when a bounded wait expires
   std::vector<uint8_t> lvl_tc;   // per level: tensor-core updates (mixed)
   std::vector<int> lvl_cs;       // per level: panel cluster size (0 = global panel)
@@ -2360,6 +2319,33 @@ static FrontTab tab(const DeviceState *d) {
   return t;
 }
 
+// Row tile (32, 64 or 128) of one batched k_cgemm launch over `items`: the
+// fewest efficiency-weighted rows per SM over the waves of CTAs (1 resident
+// CTA per SM for 128-row tiles, 2 for the smaller ones); assigns the items'
+// first tiles and returns (tiles, row tile).
+static std::pair<int, int> cg_assign(std::vector<CgItem> &items, bool allow128) {
+  int best = 64;
+  double bcost = 1e300;
+  for (int bm : {32, 64, 128}) {
+    if (bm == 128 && !allow128) continue;
+    int64_t t = 0;
+    for (const CgItem &g : items) t += (int64_t)((g.M + bm - 1) / bm) * ((g.N + CG_BN - 1) / CG_BN);
+    const int occ = bm == 128 ? 1 : 2;
+    const double eff = bm == 128 ? 1.0 : bm == 64 ? 0.85 : 0.6;
+    const double cost = (double)((t + 152 * occ - 1) / (152 * occ)) * bm / eff;
+    if (cost < bcost) {
+      bcost = cost;
+      best = bm;
+    }
+  }
+  int tiles = 0;
+  for (CgItem &g : items) {
+    g.tile0 = tiles;
+    tiles += ((g.M + best - 1) / best) * ((g.N + CG_BN - 1) / CG_BN);
+  }
+  return {tiles, best};
+}
+
 static int dev_init(Ctx &c) {
   if (c.dev) return D3M_OK;
   const Plan &P = c.plan;
@@ -2367,14 +2353,22 @@ static int dev_init(Ctx &c) {
   c.dev = d;
   d->precision = c.opt.precision;
   d->stream = (cudaStream_t)c.opt.stream;
+  int prio_lo = 0, prio_hi = 0;
+  CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
   if (!d->stream) {
     // CUDA graphs cannot be captured on the legacy NULL stream: work on an own
     // non-blocking stream, ordered after the caller's legacy-stream work at
     // every entry point (enter()) and synchronised before returning
-    CUDA_TRY(cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithPriority(&d->stream, cudaStreamNonBlocking, prio_hi));
     CUDA_TRY(cudaEventCreateWithFlags(&d->legacy_ev, cudaEventDisableTiming));
     d->own_stream = true;
   }
+  CUDA_TRY(cudaStreamCreateWithPriority(&d->stream_b, cudaStreamNonBlocking, prio_lo));
+  for (int q = 0; q < 3; ++q) {
+    CUDA_TRY(cudaEventCreateWithFlags(&d->ev_step[q], cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&d->ev_schur[q], cudaEventDisableTiming));
+  }
+  CUDA_TRY(cudaEventCreateWithFlags(&d->ev_b, cudaEventDisableTiming));
   const int64_t nsn = (int64_t)P.sn_start.size();
   std::vector<int32_t> m(nsn), pp(nsn), par(nsn);
   std::vector<int64_t> soff(nsn);
@@ -2476,7 +2470,7 @@ static int dev_init(Ctx &c) {
     // L11^{-1} storage (level-major) and the factor-time doubling stages:
     // for blocks A = [i0, i0+s), C = [i0+s, i0+2s) of the pivot range,
     //   T1 = L[C, A] A^{-1}  (mode 2),   L^{-1}[C, A] = -C^{-1} T1  (mode 1)
-    std::vector<GemmItem> items;
+    std::vector<CgItem> items;
     d->linv_off_h.assign(nsn, 0);
     int64_t lo = 0, tmax = 0;
     for (int i = 0; i < (int)nsn; ++i) {
@@ -2484,21 +2478,22 @@ static int dev_init(Ctx &c) {
       d->linv_off_h[i] = lo;
       lo += (int64_t)pp[s] * pp[s];
     }
+    const bool mixed = c.opt.precision == D3M_MIXED;
     d->inv_stage.assign(P.n_levels, {});
     for (int l = 0; l < P.n_levels; ++l) {
       int pmax = 0;
       for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) pmax = std::max(pmax, pp[P.level_fronts[i]]);
       for (int sz = 32; sz < pmax; sz *= 2) {
-        std::vector<GemmItem> g1, g2;
+        std::vector<CgItem> g1, g2;
         int64_t toff = 0;
-        int t1 = 0, t2 = 0;
         for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
           int f = P.level_fronts[i];
           int pf = pp[f], mf = m[f];
           int64_t lf = d->linv_off_h[i];
           for (int i0 = 0; i0 + sz < pf; i0 += 2 * sz) {
             int cs = std::min(sz, pf - i0 - sz);
-            GemmItem a{};
+            CgItem a{};
+            a.gath = -1;
             a.a = P.front_off[f] + (i0 + sz) + (int64_t)i0 * mf;  // L[C, A]
             a.a_rs = 1; a.a_cs = mf;
             a.b = lf + i0 + (int64_t)i0 * pf;                      // A^{-1}
@@ -2507,10 +2502,9 @@ static int dev_init(Ctx &c) {
             a.c_rs = 1; a.c_cs = cs;
             a.M = cs; a.N = sz; a.K = sz; a.mode = 2;
             a.abuf = 0; a.bbuf = 1; a.cbuf = 2; a.beta = 0; a.alpha = 1.f;
-            a.tile0 = t1;
-            t1 += ((cs + TG - 1) / TG) * ((sz + TG - 1) / TG);
             g1.push_back(a);
-            GemmItem b{};
+            CgItem b{};
+            b.gath = -1;
             b.a = lf + (i0 + sz) + (int64_t)(i0 + sz) * pf;      // C^{-1}
             b.a_rs = 1; b.a_cs = pf;
             b.b = toff; b.b_rs = 1; b.b_cs = cs;                   // T1
@@ -2518,17 +2512,16 @@ static int dev_init(Ctx &c) {
             b.c_rs = 1; b.c_cs = pf;
             b.M = cs; b.N = sz; b.K = cs; b.mode = 1;
             b.abuf = 1; b.bbuf = 2; b.cbuf = 1; b.beta = 0; b.alpha = -1.f;
-            b.tile0 = t2;
-            t2 += ((cs + TG - 1) / TG) * ((sz + TG - 1) / TG);
             g2.push_back(b);
             toff += (int64_t)cs * sz;
           }
         }
         tmax = std::max(tmax, toff);
         if (g1.empty()) continue;
-        d->inv_stage[l].push_back({(int)items.size(), (int)g1.size(), t1, 0});
+        auto t1 = cg_assign(g1, mixed), t2 = cg_assign(g2, mixed);
+        d->inv_stage[l].push_back({(int)items.size(), (int)g1.size(), t1.first, t1.second});
         items.insert(items.end(), g1.begin(), g1.end());
-        d->inv_stage[l].push_back({(int)items.size(), (int)g2.size(), t2, 0});
+        d->inv_stage[l].push_back({(int)items.size(), (int)g2.size(), t2.first, t2.second});
         items.insert(items.end(), g2.begin(), g2.end());
       }
     }
@@ -2543,7 +2536,9 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(upload(d, &d->nsplit, nsplit_h));
   CUDA_TRY(upload(d, &d->part_off, d->part_off_h));
   const size_t esz = c.opt.precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
-  CUDA_TRY(cudaMalloc(&d->W, std::max<int64_t>(wmax, 1) * esz));
+  d->wslot = std::max<int64_t>(wmax, 1);
+  CUDA_TRY(cudaMalloc(&d->W, 3 * d->wslot * esz));
+  CUDA_TRY(dalloc(d, &d->snap, (size_t)3 * nsn));
   d->allocs.push_back(d->W);
   CUDA_TRY(cudaMalloc(&d->arena, std::max<int64_t>(P.arena_elems, 1) * esz));
   d->allocs.push_back(d->arena);
@@ -2557,7 +2552,7 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(dalloc(d, &d->st_info, nsn));
   CUDA_TRY(dalloc(d, &d->st_minpiv, nsn));
   CUDA_TRY(dalloc(d, &d->flop_cnt, 2));
-  CUDA_TRY(dalloc(d, &d->swp, (size_t)nsn * NB));
+  CUDA_TRY(dalloc(d, &d->swp, (size_t)nsn * 2 * NB));
   CUDA_TRY(dalloc(d, &d->tc_err, 1));
   d->tc_grid.assign(P.n_levels, {});
   for (int l = 0; l < P.n_levels; ++l)
@@ -2635,6 +2630,11 @@ static int factor_t(Ctx &c) {
   CUDA_TRY(cudaMemsetAsync(d->tc_err, 0, sizeof(int32_t), s));
   if (sizeof(T) == 4) CUDA_TRY(tc_attrs());
   d->prof.reset();
+  const bool la = c.opt.lookahead == 1 && !d->lookahead_off;
+  if (la) {  // stream_b starts after everything issued so far on the factor stream
+    CUDA_TRY(cudaEventRecord(d->ev_b, s));
+    CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_b, 0));
+  }
   int64_t nl = 0;
   k_fill_double<<<(unsigned)((nsn + 255) / 256), 256, 0, s>>>(d->st_minpiv, nsn, 1e300);
   k_init_perm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm);
@@ -2668,27 +2668,61 @@ static int factor_t(Ctx &c) {
       PROF_END(PC_ASSEMBLE);
     }
     const int64_t *wofs = d->wofs + P.level_ptr[l];
+    // trailing update of one step: mode 0 all trailing columns, 1 the pivot
+    // block's, 2 the Schur complement's (on stream st)
+    auto update = [&](int stp, const cx<T> *Ws, const int2 *sn, int mode, cudaStream_t st) {
+      if (use_tc) {
+        dim3 g(d->tc_grid[l][stp], nf);
+        launch_update_tc<T>(g, st, lvl, ft, wofs, arena, Ws, sn, mode, d->tc_err);
+      } else {
+        dim3 g(d->update_grid[l][stp], nf);
+        k_update<T><<<g, 256, 0, st>>>(lvl, ft, wofs, arena, Ws, sn, mode);
+      }
+    };
     for (int stp = 0; stp < d->level_steps[l]; ++stp) {
+      // Look-ahead: the panels of a front read and write only its pivot
+      // block (columns < p), so the Schur-complement part of step stp's
+      // update (columns >= p) runs on stream_b while step stp + 1 proceeds
+      // here.  Slot stp % 3 of W and of the snapshots is rewritten by the
+      // panel of step stp + 3, which first waits for that update.
+      const int slot = stp % 3;
+      cx<T> *Ws = W + (la ? slot * d->wslot : 0);
+      int2 *sn = d->snap + (la ? slot * nsn : 0) + P.level_ptr[l];
+      if (la && stp >= 3) CUDA_TRY(cudaStreamWaitEvent(s, d->ev_schur[slot], 0));
       {
         PROF_BEGIN(PC_PANEL);
         int cs = c.opt.panel_kernel == 1 ? 0 : d->lvl_cs[l];
-        CUDA_TRY(launch_panel<T>(cs, d->level_maxp[l], d->level_maxm[l], nf, lvl, ft, wofs, arena, W, d->perm,
+        CUDA_TRY(launch_panel<T>(cs, d->level_maxp[l], d->level_maxm[l], nf, lvl, ft, wofs, arena, Ws, d->perm,
                                  d->dinv_d, d->dinv_o, d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv,
-                                 d->flop_cnt, d->swp + (int64_t)P.level_ptr[l] * NB, s));
+                                 d->flop_cnt, d->swp + (int64_t)P.level_ptr[l] * 2 * NB, sn, s));
         PROF_END(PC_PANEL);
       }
+      if (!la) {
+        PROF_BEGIN(PC_UPDATE);
+        update(stp, Ws, sn, 0, s);
+        PROF_END(PC_UPDATE);
+        nl += 2;
+        continue;
+      }
+      CUDA_TRY(cudaEventRecord(d->ev_step[slot], s));
       {
         PROF_BEGIN(PC_UPDATE);
-        if (use_tc) {
-          dim3 g(d->tc_grid[l][stp], nf);
-          launch_update_tc<T>(g, s, lvl, ft, wofs, arena, W, d->st_k0, d->st_kb, d->tc_err);
-        } else {
-          dim3 g(d->update_grid[l][stp], nf);
-          k_update<T><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, d->st_k0, d->st_kb);
-        }
+        update(stp, Ws, sn, 1, s);
         PROF_END(PC_UPDATE);
       }
-      nl += 2;
+      CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_step[slot], 0));
+      {
+        PROF_BEGIN_ON(PC_UPDATE, d->stream_b);
+        update(stp, Ws, sn, 2, d->stream_b);
+        PROF_END_ON(PC_UPDATE, d->stream_b);
+      }
+      CUDA_TRY(cudaEventRecord(d->ev_schur[slot], d->stream_b));
+      nl += 3;
+    }
+    // the next level's extend-add reads these Schur complements
+    if (la) {
+      CUDA_TRY(cudaEventRecord(d->ev_b, d->stream_b));
+      CUDA_TRY(cudaStreamWaitEvent(s, d->ev_b, 0));
     }
     // L11^{-1} of the level's fronts (mixed precision only: it turns every
     // substitution into tile GEMMs; the fp64 path keeps the triangular-solve
@@ -2707,9 +2741,9 @@ static int factor_t(Ctx &c) {
       dim3 gd((unsigned)((d->level_maxp[l] + 31) / 32), nf);
       k_trinv_diag<T><<<gd, 32, 0, s>>>(lvl, ft, arena, d->linv_off + P.level_ptr[l], Li);
       ++nl;
+      const CgBufs<T> ib{{arena, Li, (cx<T> *)d->tmp_inv, nullptr, nullptr, nullptr}};
       for (auto &st : d->inv_stage[l]) {
-        k_tgemm<T><<<st[2], 256, 0, s>>>(d->inv_items + st[0], st[1], st[2], arena, Li, (cx<T> *)d->tmp_inv,
-                                         nullptr);
+        launch_cgemm<T>(st[3], st[2], d->inv_items + st[0], st[1], ib, nullptr, s);
         ++nl;
       }
       PROF_END(PC_INV);
@@ -2849,6 +2883,7 @@ static int autotune(Ctx &c) {
   const bool prof = d->prof.on;
   const int uk = c.opt.update_kernel;
   d->prof.on = true;
+  d->lookahead_off = true;  // per-kernel times without the overlap
   // trial A: fp32-FMA updates, smallest cluster
   std::vector<int> csA = d->lvl_cs, csB(nlev);
   // (clusters stay within the portable size 8)
@@ -2865,6 +2900,7 @@ static int autotune(Ctx &c) {
   std::vector<double> pB = d->tune_panel, uB = d->tune_update;
   c.opt.update_kernel = uk;
   d->prof.on = prof;
+  d->lookahead_off = false;
   if (rc != D3M_OK) {
     d->lvl_cs = csA;
     return rc;
@@ -3335,6 +3371,15 @@ void dev_free(Ctx &c) {
   if (!c.dev) return;
   for (cudaGraphExec_t g : {c.dev->g_fwd, c.dev->g_bwd})
     if (g) cudaGraphExecDestroy(g);
+  if (c.dev->stream_b) {
+    cudaStreamSynchronize(c.dev->stream_b);
+    cudaStreamDestroy(c.dev->stream_b);
+    for (int q = 0; q < 3; ++q) {
+      cudaEventDestroy(c.dev->ev_step[q]);
+      cudaEventDestroy(c.dev->ev_schur[q]);
+    }
+    cudaEventDestroy(c.dev->ev_b);
+  }
   if (c.dev->own_stream) {
     cudaStreamSynchronize(c.dev->stream);
     cudaStreamDestroy(c.dev->stream);
@@ -3396,7 +3441,9 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
   DTRY(dalloc(&tmp, &k0, batch));
   DTRY(dalloc(&tmp, &kb, batch));
   DTRY(dalloc(&tmp, &mp, batch));
-  DTRY(dalloc(&tmp, &swp, (size_t)batch * NB));
+  DTRY(dalloc(&tmp, &swp, (size_t)batch * 2 * NB));
+  int2 *snap = nullptr;
+  DTRY(dalloc(&tmp, &snap, batch));
   DTRY(cudaMemsetAsync(k0, 0, batch * sizeof(int32_t), s));
   DTRY(cudaMemsetAsync(kb, 0, batch * sizeof(int32_t), s));
   DTRY(cudaMemsetAsync(info, 0, batch * sizeof(int32_t), s));
@@ -3408,11 +3455,11 @@ int dense_ldlt(int m, int p, int batch, double *A, int32_t *perm, double *dinv, 
   for (int stp = 0; stp < steps; ++stp) {
     int cs = panel_kernel == 1 ? 0 : panel_cluster_size(p, sizeof(cx<double>));
     DTRY(launch_panel<double>(cs, p, m, batch, tmp.lvl_fronts, ft, tmp.wofs, arena, W, pv, dd, dof, ps, k0, kb, info,
-                              mp, nullptr, swp, s));
+                              mp, nullptr, swp, snap, s));
     int cmin = std::min(p, (stp + 1) * (NB - 1));
     int nt = (m + UT - 1) / UT - cmin / UT;
     dim3 g(std::max(1, nt * (nt + 1) / 2), batch);
-    k_update<double><<<g, 256, 0, s>>>(tmp.lvl_fronts, ft, tmp.wofs, arena, W, k0, kb);
+    k_update<double><<<g, 256, 0, s>>>(tmp.lvl_fronts, ft, tmp.wofs, arena, W, snap, 0);
   }
   DTRY(cudaGetLastError());
   DTRY(cudaStreamSynchronize(s));
@@ -3453,7 +3500,7 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
 struct NoallocLayout {
-  size_t f_m, f_p, f_parent, lvl, f_off, f_piv, f_zero, wofs, W, pv, dd, dof, k0, kb, mp, ps, swp, total;
+  size_t f_m, f_p, f_parent, lvl, f_off, f_piv, f_zero, wofs, W, pv, dd, dof, k0, kb, mp, ps, swp, snap, total;
 };
 static NoallocLayout noalloc_layout(int m, int p, int batch) {
   NoallocLayout L{};
@@ -3480,7 +3527,8 @@ static NoallocLayout noalloc_layout(int m, int p, int batch) {
   L.kb = take(4 * b);
   L.mp = take(8 * b);
   L.ps = take(b * pp);
-  L.swp = take(8 * b * NB);
+  L.swp = take(8 * b * 2 * NB);
+  L.snap = take(8 * b);
   L.total = o;
   return L;
 }
@@ -3566,14 +3614,15 @@ static int dense_ldlt_noalloc(int m, int p, int batch, double *A, int32_t *perm,
   const int cs = panel_cluster_size(p, sizeof(cx<double>));
   cx<double> *arena = reinterpret_cast<cx<double> *>(A);
   int2 *swp = reinterpret_cast<int2 *>(base + Lo.swp);
+  int2 *snap = reinterpret_cast<int2 *>(base + Lo.snap);
   for (int stp = 0; stp < steps; ++stp) {
     if (launch_panel<double>(cs, p, m, batch, lvl, ft, wofs, arena, W, pv, dd, dof, ps, k0, kb, info, mp, nullptr,
-                             swp, s) != cudaSuccess)
+                             swp, snap, s) != cudaSuccess)
       return D3M_ECUDA;
     int cmin = std::min(p, (stp + 1) * (NB - 1));
     int nt = (m + UT - 1) / UT - cmin / UT;
     dim3 g(std::max(1, nt * (nt + 1) / 2), batch);
-    k_update<double><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, k0, kb);
+    k_update<double><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, snap, 0);
   }
   k_noalloc_out<<<(unsigned)std::min<int64_t>(((int64_t)batch * m + 255) / 256, 4096), 256, 0, s>>>(
       m, p, batch, pv, dd, dof, ps, perm, dinv);

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32), ("panel_kernel", ctypes.c_int32),
                 ("update_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("autotune_cache", ctypes.c_char_p)]
+                ("autotune_cache", ctypes.c_char_p), ("lookahead", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -135,7 +135,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
-                 update_kernel=0, autotune=0, autotune_cache=None):
+                 update_kernel=0, autotune=0, autotune_cache=None, lookahead=0):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -150,7 +150,7 @@ class Solver:
         self.stream = stream
         self._cache = None if autotune_cache is None else str(autotune_cache).encode()
         opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile),
-                      int(panel_kernel), int(update_kernel), int(autotune), self._cache)
+                      int(panel_kernel), int(update_kernel), int(autotune), self._cache, int(lookahead))
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))

@@ -290,3 +290,32 @@ def test_autotuner_choices_and_cache(tmp_path):
     assert cache.read_text().splitlines()[0] == lines[0]
     for s in (a, ref, c2, c3):
         s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,uk", [(d3m.MIXED, 1), (d3m.MIXED, 2), (d3m.FP64, 1)])
+def test_lookahead_bitwise_identical(prec, uk):
+    """The overlapped schedule (Schur-complement updates on a second stream)
+    partitions every step's trailing update by columns and keeps the step
+    order per entry, so its factors equal the sequential schedule's bit for
+    bit."""
+    _need_gpu()
+    w = W.make(1)
+    sv = []
+    for la in (1, 0):
+        s = d3m.Solver.from_workload(w, precision=prec, update_kernel=uk, autotune=1, lookahead=la)
+        s.factor()
+        sv.append(s)
+    n = len(sv[0].structure(d3m.SN_RANGE))
+    for q in range(n):
+        Fa, pa, da = sv[0].export_front(q)
+        Fb, pb, db = sv[1].export_front(q)
+        assert np.array_equal(pa, pb) and np.array_equal(da, db), q
+        assert np.array_equal(Fa, Fb), q
+    f = fem.rhs_planewave(w)
+    b = torch.tensor(f.T.copy(), device="cuda").t()
+    xa, _ = sv[0].solve(b)
+    xb, _ = sv[1].solve(b)
+    assert torch.equal(xa, xb)
+    for s in sv:
+        s.close()
