@@ -107,14 +107,13 @@ typedef struct {
                            defaults: FMA updates, smallest fitting cluster) */
   const char *autotune_cache; /* optional file: read the tuned schedule from it when
                            it matches this problem, write it after tuning; NULL = none */
-  int32_t lookahead;    /* 0 = off (default): every trailing update completes
-                           before the next panel; 1 = overlap: the
-                           Schur-complement part of each update runs on a second,
-                           low-priority stream while the next panels of the front
-                           proceed (they only touch its pivot block).  Both give
-                           bitwise identical factors; on GB300 the overlap is
-                           slower, since a full-grid update leaves no SM room for
-                           the panel's CTAs. */
+  int32_t lookahead;    /* 0 = overlap (default): the Schur-complement part of each
+                           trailing update runs on a second stream, launched with
+                           the least urgent priority, while the next panels of the
+                           front (which touch only its pivot block) proceed with
+                           the most urgent one; 1 = off, every update completes
+                           before the next panel.  Both give bitwise identical
+                           factors. */
 } d3m_options;
 
 /* Per-solve report: per column relative residual (Numerical Results
@@ -313,6 +312,13 @@ int d3m_dense_ldlt_noalloc(int32_t m, int32_t p, int32_t batch, double *A, int32
                            int32_t *info, void *stream);
 
 int d3m_stats_get(d3m_ctx *ctx, d3m_stats *out);
+
+/* Turn the per-kernel-class CUDA-event timing (d3m_options.profile) on (1)
+ * or off (0) for the following calls.  Unprofiled factorisations replay the
+ * launch sequence captured into a CUDA graph at their first call; profiled
+ * ones launch eagerly with events around every kernel group, which costs host
+ * time.  D3M_EINVAL for a NULL context. */
+int d3m_set_profile(d3m_ctx *ctx, int32_t on);
 const char *d3m_last_error(const d3m_ctx *ctx);
 void d3m_free(d3m_ctx *ctx);
 

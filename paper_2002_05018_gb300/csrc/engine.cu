@@ -669,11 +669,15 @@ __global__ void __launch_bounds__(512)
     else
       cl.sync();
   };
-  // original data of the column being processed for the first two own slots
-  // (q = tid, tid + nth), loaded during the previous column's scale phase
-  cx<T> pre0 = mk<T>(0, 0), pre1 = mk<T>(0, 0);
-  if (tid < ns) pre0 = F[spos[tid] + (int64_t)k0 * ld];
-  if (tid + nth < ns) pre1 = F[spos[tid + nth] + (int64_t)k0 * ld];
+  // Original (not yet updated) data of the column being processed (cur) and
+  // of the next column (nx, loaded at the start of the current column), for
+  // the own slots q = tid and tid + nth (a CTA owns at most 2 nth slots).
+  // An interchange moves data with the slots, so nx stays valid for the next
+  // column except for one entry, passed through fixv (see below).
+  cx<T> cur0 = mk<T>(0, 0), cur1 = mk<T>(0, 0), nx0 = mk<T>(0, 0), nx1 = mk<T>(0, 0);
+  if (tid < ns) cur0 = F[spos[tid] + (int64_t)k0 * ld];
+  if (tid + nth < ns) cur1 = F[spos[tid + nth] + (int64_t)k0 * ld];
+  __shared__ cx<T> fixv;
   int k = k0, j = 0, par = 0;
   long long cmac = 0;        // complex MACs of the column updates (thread 0)
   float minpiv = 3.0e38f;    // smallest |d| / colmax of the 1x1 pivots (thread 0)
@@ -701,6 +705,10 @@ __global__ void __launch_bounds__(512)
   // value of own-CTA slot array a at logical row `row` (CS == 1: any row)
   auto own_at = [&](const cx<T> *a, int row) { return a[p2s[row - k0] - rank * R]; };
   while (k < p && j < NB - 1) {
+    if (k + 1 < p) {  // the next column, in flight during this one
+      if (tid < ns && spos[tid] >= k + 1) nx0 = F[spos[tid] + (int64_t)(k + 1) * ld];
+      if (tid + nth < ns && spos[tid + nth] >= k + 1) nx1 = F[spos[tid + nth] + (int64_t)(k + 1) * ld];
+    }
     // ---- (1) updated column k for own slots, local pivot search
     load_wrow(k, wrow);
     __syncthreads();
@@ -708,7 +716,7 @@ __global__ void __launch_bounds__(512)
     for (int q = tid, qi = 0; q < ns; q += nth, ++qi) {
       int i = spos[q];
       if (i < k) continue;
-      cx<T> acc = qi == 0 ? pre0 : qi == 1 ? pre1 : F[i + (int64_t)k * ld];
+      cx<T> acc = qi == 0 ? cur0 : cur1;
       const cx<T> *Lq = Ls + (size_t)q * LSTR;
 #pragma unroll 8
       for (int t = 0; t < NB - 1; ++t)
@@ -828,14 +836,18 @@ __global__ void __launch_bounds__(512)
       if (kstep == 1 && d.colmax > (T)0) minpiv = fminf(minpiv, (float)cabs1_d(d.d11) / (float)d.colmax);
     }
     if (kp != kk) {
-      // ---- interchange kk <-> kp: the not yet factored column kk moves to
-      // position kp in the global front; each thread handles the rows of its
-      // own slots so that its later accesses to those rows stay ordered
-      for (int q = tid; q < ns; q += nth) {
-        int i = spos[q];
-        if (i > kk && i < kp) F[kp + (int64_t)i * ld] = F[i + (int64_t)kk * ld];
-        else if (i > kp) F[i + (int64_t)kp * ld] = F[i + (int64_t)kk * ld];
-        else if (i == kk) F[kp + (int64_t)kp * ld] = F[kk + (int64_t)kk * ld];
+      // ---- interchange kk <-> kp: the not yet factored column kk (original
+      // data: cur for kk = k, nx for kk = k + 1) moves to position kp in the
+      // global front; each thread writes the rows of its own slots
+      for (int q = tid, qi = 0; q < ns; q += nth, ++qi) {
+        const int i = spos[q];
+        const cx<T> v = kstep == 1 ? (qi == 0 ? cur0 : cur1) : (qi == 0 ? nx0 : nx1);
+        if (i > kk && i < kp) F[kp + (int64_t)i * ld] = v;
+        else if (i > kp) F[i + (int64_t)kp * ld] = v;
+        else if (i == kk) F[kp + (int64_t)kp * ld] = v;
+        // after a 1x1 interchange with kp > k + 1 the slot now at row kp needs
+        // A[kp, k+1] = A[k+1, k] (original), held by the slot of row k + 1
+        if (kstep == 1 && kp > k + 1 && i == k + 1) fixv = qi == 0 ? cur0 : cur1;
       }
       if (rank == 0 && tid == 0) {
         int32_t a = pv[kk];
@@ -851,6 +863,28 @@ __global__ void __launch_bounds__(512)
         int ga = p2s[kk - k0];
         p2s[kk - k0] = p2s[kp - k0];
         p2s[kp - k0] = ga;
+      }
+    }
+    // ---- original data of the next column for the own slots
+    if (kstep == 1 && k + 1 < p) {
+      if (kp == k + 1) {  // the next column is the old column k
+        nx0 = cur0;
+        nx1 = cur1;
+      } else if (kp != kk) {
+        const int g1 = p2s[k + 1 - k0];  // row k + 1 did not move
+        const cx<T> fv = CS == 1 ? fixv : *cl.map_shared_rank(&fixv, g1 / R);
+        if (tid < ns && spos[tid] == kp) nx0 = fv;
+        if (tid + nth < ns && spos[tid + nth] == kp) nx1 = fv;
+      }
+      cur0 = nx0;
+      cur1 = nx1;
+    } else if (kstep == 2 && k + 2 < p) {
+      if (kp == k + 2) {  // the next column is the old column k + 1
+        cur0 = nx0;
+        cur1 = nx1;
+      } else {  // loaded after the interchange (which may have written row kp of it)
+        if (tid < ns && spos[tid] >= k + 2) cur0 = F[spos[tid] + (int64_t)(k + 2) * ld];
+        if (tid + nth < ns && spos[tid + nth] >= k + 2) cur1 = F[spos[tid + nth] + (int64_t)(k + 2) * ld];
       }
     }
     // ---- scale: L columns of own slots (in shared memory; written to the
@@ -896,11 +930,6 @@ __global__ void __launch_bounds__(512)
         Dz[j] = 2;
         Dz[j + 1] = -2;
       }
-    }
-    if (k + kstep < p) {  // load the next column (this step's interchange is done)
-      const int kn = k + kstep;
-      if (tid < ns && spos[tid] >= kn) pre0 = F[spos[tid] + (int64_t)kn * ld];
-      if (tid + nth < ns && spos[tid + nth] >= kn) pre1 = F[spos[tid + nth] + (int64_t)kn * ld];
     }
     csync();  // #3: L rows, D and the tables are consistent for the next column
     k += kstep;
@@ -1120,6 +1149,25 @@ static int panel_cluster_size(int mmax, size_t esz) {
   return 0;
 }
 
+// Kernel launch with an optional scheduling priority (lower = more urgent, as
+// for streams; 0 = the stream's own).  The attribute travels with the launch
+// into a captured graph's kernel node, where stream priorities do not.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_prio(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, int prio,
+                               Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = prio;
+  cfg.attrs = at;
+  cfg.numAttrs = prio != 0 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <typename T>
 static cudaError_t panel_attrs() {
   static bool done = false;
@@ -1140,35 +1188,37 @@ template <typename T>
 static cudaError_t launch_panel(int cs, int pmax, int mmax, int nf, const int32_t *lvl, FrontTab ft,
                                 const int64_t *wofs, cx<T> *arena, cx<T> *W, int32_t *perm, double2 *dd,
                                 double2 *dof, int8_t *ps, int32_t *k0, int32_t *kb, int32_t *info, double *minpiv,
-                                double *flops, int2 *swp, int2 *snap, cudaStream_t s) {
-  if (cs <= 0) {
-    k_panel<T><<<nf, PANEL_THREADS, 0, s>>>(lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv, flops,
-                                            snap);
-    return cudaGetLastError();
-  }
+                                double *flops, int2 *swp, int2 *snap, cudaStream_t s, int prio = 0) {
+  if (cs <= 0)
+    return launch_prio(k_panel<T>, dim3(nf), dim3(PANEL_THREADS), 0, s, prio, lvl, ft, wofs, arena, W, perm, dd, dof,
+                       ps, k0, kb, info, minpiv, flops, snap);
   cudaError_t e = panel_attrs<T>();
   if (e != cudaSuccess) return e;
   int rcap = (pmax + cs - 1) / cs;
+  if (rcap > 2 * 512) return cudaErrorInvalidValue;  // k_panel_cl keeps two slots per thread
   const int mcap = pmax;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nf * cs));
   cfg.blockDim = dim3(512);
   cfg.dynamicSmemBytes = panel_cl_smem(rcap, mcap, sizeof(cx<T>));
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributePriority;
+  attr[1].val.priority = prio;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = prio != 0 ? 2 : 1;
   e = cudaLaunchKernelEx(&cfg, k_panel_cl<T>, lvl, ft, wofs, arena, W, perm, dd, dof, ps, k0, kb, info, minpiv,
                          flops, swp, rcap, mcap, snap);
   if (e != cudaSuccess) return e;
   if (mmax > 0) {
     dim3 g((unsigned)std::max(1, (mmax + 127) / 128), (unsigned)nf);
-    k_l21<T><<<g, 128, 0, s>>>(lvl, ft, wofs, arena, W, dd, dof, ps, k0, kb, swp, flops);
-    e = cudaGetLastError();
+    e = launch_prio(k_l21<T>, g, dim3(128), 0, s, prio, lvl, ft, wofs, arena, W, (const double2 *)dd,
+                    (const double2 *)dof, (const int8_t *)ps, (const int32_t *)k0, (const int32_t *)kb,
+                    (const int2 *)swp, flops);
   }
   return e;
 }
@@ -1491,8 +1541,9 @@ static cudaError_t tc_attrs() {
 }
 template <typename T>
 static void launch_update_tc(dim3 g, cudaStream_t s, const int32_t *lvl, FrontTab ft, const int64_t *wofs,
-                             cx<T> *arena, const cx<T> *W, const int2 *snap, int mode, int32_t *err) {
-  if constexpr (sizeof(T) == 4) k_update_tc<T><<<g, 128, TC_SMEM, s>>>(lvl, ft, wofs, arena, W, snap, mode, err);
+                             cx<T> *arena, const cx<T> *W, const int2 *snap, int mode, int32_t *err, int prio = 0) {
+  if constexpr (sizeof(T) == 4)
+    launch_prio(k_update_tc<T>, g, dim3(128), TC_SMEM, s, prio, lvl, ft, wofs, arena, W, snap, mode, err);
 }
 
 // ------------------------------------------------------------ solve kernels
@@ -2223,6 +2274,7 @@ struct DeviceState {
   int2 *snap = nullptr;          // [3][level position]
   int64_t wslot = 0;             // elements per W slot
   bool lookahead_off = false;    // set while the autotuner times the kernels
+  int prio_lo = 0, prio_hi = 0;  // least / most urgent scheduling priority
   // plan tables
   int32_t *f_m = nullptr, *f_p = nullptr, *f_parent = nullptr;
   int64_t *f_off = nullptr, *f_piv = nullptr, *f_soff = nullptr, *f_start = nullptr, *f_y = nullptr;
@@ -2270,6 +2322,8 @@ struct DeviceState {
   int sol_r = 0;
   void *Y2 = nullptr;
   cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;  // captured substitution sweeps
+  cudaGraphExec_t g_factor = nullptr;                // captured factorisation (unprofiled calls)
+  int64_t g_factor_launches = 0;
   int g_r = 0;
   int64_t g_launches[2] = {0, 0};
   int2 *swp = nullptr;           // per level position: the current panel's column permutation (2 NB each)
@@ -2355,6 +2409,8 @@ static int dev_init(Ctx &c) {
   d->stream = (cudaStream_t)c.opt.stream;
   int prio_lo = 0, prio_hi = 0;
   CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  d->prio_lo = prio_lo;
+  d->prio_hi = prio_hi;
   if (!d->stream) {
     // CUDA graphs cannot be captured on the legacy NULL stream: work on an own
     // non-blocking stream, ordered after the caller's legacy-stream work at
@@ -2623,135 +2679,175 @@ static int factor_t(Ctx &c) {
   cx<T> *arena = (cx<T> *)d->arena;
   cx<T> *W = (cx<T> *)d->W;
   FrontTab ft = tab(d);
-  CUDA_TRY(cudaMemsetAsync(d->st_k0, 0, nsn * sizeof(int32_t), s));
-  CUDA_TRY(cudaMemsetAsync(d->st_kb, 0, nsn * sizeof(int32_t), s));
-  CUDA_TRY(cudaMemsetAsync(d->st_info, 0, nsn * sizeof(int32_t), s));
-  CUDA_TRY(cudaMemsetAsync(d->flop_cnt, 0, 2 * sizeof(double), s));
-  CUDA_TRY(cudaMemsetAsync(d->tc_err, 0, sizeof(int32_t), s));
   if (sizeof(T) == 4) CUDA_TRY(tc_attrs());
-  d->prof.reset();
-  const bool la = c.opt.lookahead == 1 && !d->lookahead_off;
-  if (la) {  // stream_b starts after everything issued so far on the factor stream
-    CUDA_TRY(cudaEventRecord(d->ev_b, s));
-    CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_b, 0));
-  }
+  CUDA_TRY(panel_attrs<T>());
+  // Without profiling the launch sequence (fixed once the schedule is tuned)
+  // is captured into a CUDA graph at the first call and replayed after.
+  const bool use_graph = !d->prof.on;
   int64_t nl = 0;
-  k_fill_double<<<(unsigned)((nsn + 255) / 256), 256, 0, s>>>(d->st_minpiv, nsn, 1e300);
-  k_init_perm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm);
-  nl += 2;
-  for (int l = 0; l < P.n_levels; ++l) {
-    const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
-    const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
-    d->prof.cur_level = l;
-    const bool use_tc = sizeof(T) == 4 && (c.opt.update_kernel == 2 || (c.opt.update_kernel == 0 && d->lvl_tc[l]));
-    // zero the level's fronts (contiguous) and assemble the entries of M
-    int64_t first = P.front_off[P.level_fronts[P.level_ptr[l]]];
-    int last_s = P.level_fronts[P.level_ptr[l + 1] - 1];
-    int64_t mlast = (P.sn_end[last_s] - P.sn_start[last_s]) + (P.struct_ptr[last_s + 1] - P.struct_ptr[last_s]);
-    int64_t end = P.front_off[last_s] + mlast * mlast;
-    {
-      PROF_BEGIN(PC_ASSEMBLE);
-      CUDA_TRY(cudaMemsetAsync(arena + first, 0, (end - first) * sizeof(cx<T>), s));
-      int64_t ne = P.ent_ptr[l + 1] - P.ent_ptr[l];
-      if (ne > 0) {
-        k_assemble<T><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(ne, d->ent_off + P.ent_ptr[l],
-                                                                    d->ent_val + P.ent_ptr[l], arena);
-        ++nl;
-      }
-      for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
-        int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
-        if (nk == 0) continue;
-        dim3 g(d->ea_grid[q], nk);
-        k_extend_add<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, arena);
-        ++nl;
-      }
-      PROF_END(PC_ASSEMBLE);
+  auto enqueue = [&]() -> int {
+    CUDA_TRY(cudaMemsetAsync(d->st_k0, 0, nsn * sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(d->st_kb, 0, nsn * sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(d->st_info, 0, nsn * sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(d->flop_cnt, 0, 2 * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(d->tc_err, 0, sizeof(int32_t), s));
+    d->prof.reset();
+    // (profiled runs are sequential, so that every kernel class's events time
+  // that class alone)
+  const bool la = c.opt.lookahead == 0 && !d->lookahead_off && !d->prof.on;
+    if (la) {  // stream_b starts after everything issued so far on the factor stream
+      CUDA_TRY(cudaEventRecord(d->ev_b, s));
+      CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_b, 0));
     }
-    const int64_t *wofs = d->wofs + P.level_ptr[l];
-    // trailing update of one step: mode 0 all trailing columns, 1 the pivot
-    // block's, 2 the Schur complement's (on stream st)
-    auto update = [&](int stp, const cx<T> *Ws, const int2 *sn, int mode, cudaStream_t st) {
-      if (use_tc) {
-        dim3 g(d->tc_grid[l][stp], nf);
-        launch_update_tc<T>(g, st, lvl, ft, wofs, arena, Ws, sn, mode, d->tc_err);
-      } else {
-        dim3 g(d->update_grid[l][stp], nf);
-        k_update<T><<<g, 256, 0, st>>>(lvl, ft, wofs, arena, Ws, sn, mode);
-      }
-    };
-    for (int stp = 0; stp < d->level_steps[l]; ++stp) {
-      // Look-ahead: the panels of a front read and write only its pivot
-      // block (columns < p), so the Schur-complement part of step stp's
-      // update (columns >= p) runs on stream_b while step stp + 1 proceeds
-      // here.  Slot stp % 3 of W and of the snapshots is rewritten by the
-      // panel of step stp + 3, which first waits for that update.
-      const int slot = stp % 3;
-      cx<T> *Ws = W + (la ? slot * d->wslot : 0);
-      int2 *sn = d->snap + (la ? slot * nsn : 0) + P.level_ptr[l];
-      if (la && stp >= 3) CUDA_TRY(cudaStreamWaitEvent(s, d->ev_schur[slot], 0));
+    k_fill_double<<<(unsigned)((nsn + 255) / 256), 256, 0, s>>>(d->st_minpiv, nsn, 1e300);
+    k_init_perm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm);
+    nl += 2;
+    for (int l = 0; l < P.n_levels; ++l) {
+      const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
+      const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
+      d->prof.cur_level = l;
+      const bool use_tc = sizeof(T) == 4 && (c.opt.update_kernel == 2 || (c.opt.update_kernel == 0 && d->lvl_tc[l]));
+      // zero the level's fronts (contiguous) and assemble the entries of M
+      int64_t first = P.front_off[P.level_fronts[P.level_ptr[l]]];
+      int last_s = P.level_fronts[P.level_ptr[l + 1] - 1];
+      int64_t mlast = (P.sn_end[last_s] - P.sn_start[last_s]) + (P.struct_ptr[last_s + 1] - P.struct_ptr[last_s]);
+      int64_t end = P.front_off[last_s] + mlast * mlast;
       {
-        PROF_BEGIN(PC_PANEL);
-        int cs = c.opt.panel_kernel == 1 ? 0 : d->lvl_cs[l];
-        CUDA_TRY(launch_panel<T>(cs, d->level_maxp[l], d->level_maxm[l], nf, lvl, ft, wofs, arena, Ws, d->perm,
-                                 d->dinv_d, d->dinv_o, d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv,
-                                 d->flop_cnt, d->swp + (int64_t)P.level_ptr[l] * 2 * NB, sn, s));
-        PROF_END(PC_PANEL);
+        PROF_BEGIN(PC_ASSEMBLE);
+        CUDA_TRY(cudaMemsetAsync(arena + first, 0, (end - first) * sizeof(cx<T>), s));
+        int64_t ne = P.ent_ptr[l + 1] - P.ent_ptr[l];
+        if (ne > 0) {
+          k_assemble<T><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(ne, d->ent_off + P.ent_ptr[l],
+                                                                      d->ent_val + P.ent_ptr[l], arena);
+          ++nl;
+        }
+        for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
+          int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
+          if (nk == 0) continue;
+          dim3 g(d->ea_grid[q], nk);
+          k_extend_add<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, arena);
+          ++nl;
+        }
+        PROF_END(PC_ASSEMBLE);
       }
-      if (!la) {
-        PROF_BEGIN(PC_UPDATE);
-        update(stp, Ws, sn, 0, s);
-        PROF_END(PC_UPDATE);
-        nl += 2;
-        continue;
+      const int64_t *wofs = d->wofs + P.level_ptr[l];
+      // trailing update of one step: mode 0 all trailing columns, 1 the pivot
+      // block's, 2 the Schur complement's (on stream st)
+      // (priorities under look-ahead: the panel chain urgent, the overlapped
+      // Schur part least urgent)
+      auto update = [&](int stp, const cx<T> *Ws, const int2 *sn, int mode, cudaStream_t st) {
+        const int prio = !la ? 0 : mode == 2 ? d->prio_lo : d->prio_hi;
+        if (use_tc) {
+          dim3 g(d->tc_grid[l][stp], nf);
+          launch_update_tc<T>(g, st, lvl, ft, wofs, arena, Ws, sn, mode, d->tc_err, prio);
+        } else {
+          dim3 g(d->update_grid[l][stp], nf);
+          launch_prio(k_update<T>, g, dim3(256), 0, st, prio, lvl, ft, wofs, arena, (const cx<T> *)Ws, sn, mode);
+        }
+      };
+      for (int stp = 0; stp < d->level_steps[l]; ++stp) {
+        // Look-ahead: the panels of a front read and write only its pivot
+        // block (columns < p), so the Schur-complement part of step stp's
+        // update (columns >= p) runs on stream_b while step stp + 1 proceeds
+        // here.  Slot stp % 3 of W and of the snapshots is rewritten by the
+        // panel of step stp + 3, which first waits for that update.
+        const int slot = stp % 3;
+        cx<T> *Ws = W + (la ? slot * d->wslot : 0);
+        int2 *sn = d->snap + (la ? slot * nsn : 0) + P.level_ptr[l];
+        if (la && stp >= 3) CUDA_TRY(cudaStreamWaitEvent(s, d->ev_schur[slot], 0));
+        {
+          PROF_BEGIN(PC_PANEL);
+          int cs = c.opt.panel_kernel == 1 ? 0 : d->lvl_cs[l];
+          CUDA_TRY(launch_panel<T>(cs, d->level_maxp[l], d->level_maxm[l], nf, lvl, ft, wofs, arena, Ws, d->perm,
+                                   d->dinv_d, d->dinv_o, d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv,
+                                   d->flop_cnt, d->swp + (int64_t)P.level_ptr[l] * 2 * NB, sn, s,
+                                   la ? d->prio_hi : 0));
+          PROF_END(PC_PANEL);
+        }
+        if (!la) {
+          PROF_BEGIN(PC_UPDATE);
+          update(stp, Ws, sn, 0, s);
+          PROF_END(PC_UPDATE);
+          nl += 2;
+          continue;
+        }
+        CUDA_TRY(cudaEventRecord(d->ev_step[slot], s));
+        {
+          PROF_BEGIN(PC_UPDATE);
+          update(stp, Ws, sn, 1, s);
+          PROF_END(PC_UPDATE);
+        }
+        CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_step[slot], 0));
+        {
+          PROF_BEGIN_ON(PC_UPDATE, d->stream_b);
+          update(stp, Ws, sn, 2, d->stream_b);
+          PROF_END_ON(PC_UPDATE, d->stream_b);
+        }
+        CUDA_TRY(cudaEventRecord(d->ev_schur[slot], d->stream_b));
+        nl += 3;
       }
-      CUDA_TRY(cudaEventRecord(d->ev_step[slot], s));
-      {
-        PROF_BEGIN(PC_UPDATE);
-        update(stp, Ws, sn, 1, s);
-        PROF_END(PC_UPDATE);
+      // the next level's extend-add reads these Schur complements
+      if (la) {
+        CUDA_TRY(cudaEventRecord(d->ev_b, d->stream_b));
+        CUDA_TRY(cudaStreamWaitEvent(s, d->ev_b, 0));
       }
-      CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_step[slot], 0));
-      {
-        PROF_BEGIN_ON(PC_UPDATE, d->stream_b);
-        update(stp, Ws, sn, 2, d->stream_b);
-        PROF_END_ON(PC_UPDATE, d->stream_b);
-      }
-      CUDA_TRY(cudaEventRecord(d->ev_schur[slot], d->stream_b));
-      nl += 3;
-    }
-    // the next level's extend-add reads these Schur complements
-    if (la) {
-      CUDA_TRY(cudaEventRecord(d->ev_b, d->stream_b));
-      CUDA_TRY(cudaStreamWaitEvent(s, d->ev_b, 0));
-    }
-    // L11^{-1} of the level's fronts (mixed precision only: it turns every
-    // substitution into tile GEMMs; the fp64 path keeps the triangular-solve
-    // kernels, since on the fp64 pipe the extra p^3/6 flops cost more than
-    // the sequential blocks): diagonal 32-blocks, then doubling stages
-    if (sizeof(T) == 4) {
-      PROF_BEGIN(PC_INV);
-      cx<T> *Li = (cx<T> *)d->linv;
-      int lf = P.level_fronts[P.level_ptr[l]];
-      int ll = P.level_fronts[P.level_ptr[l + 1] - 1];
-      int64_t a0 = d->linv_off_h[P.level_ptr[l]];
-      int64_t pl = P.sn_end[ll] - P.sn_start[ll];
-      int64_t a1 = d->linv_off_h[P.level_ptr[l + 1] - 1] + pl * pl;
-      (void)lf;
-      CUDA_TRY(cudaMemsetAsync(Li + a0, 0, (a1 - a0) * sizeof(cx<T>), s));
-      dim3 gd((unsigned)((d->level_maxp[l] + 31) / 32), nf);
-      k_trinv_diag<T><<<gd, 32, 0, s>>>(lvl, ft, arena, d->linv_off + P.level_ptr[l], Li);
-      ++nl;
-      const CgBufs<T> ib{{arena, Li, (cx<T> *)d->tmp_inv, nullptr, nullptr, nullptr}};
-      for (auto &st : d->inv_stage[l]) {
-        launch_cgemm<T>(st[3], st[2], d->inv_items + st[0], st[1], ib, nullptr, s);
+      // L11^{-1} of the level's fronts (mixed precision only: it turns every
+      // substitution into tile GEMMs; the fp64 path keeps the triangular-solve
+      // kernels, since on the fp64 pipe the extra p^3/6 flops cost more than
+      // the sequential blocks): diagonal 32-blocks, then doubling stages
+      if (sizeof(T) == 4) {
+        PROF_BEGIN(PC_INV);
+        cx<T> *Li = (cx<T> *)d->linv;
+        int lf = P.level_fronts[P.level_ptr[l]];
+        int ll = P.level_fronts[P.level_ptr[l + 1] - 1];
+        int64_t a0 = d->linv_off_h[P.level_ptr[l]];
+        int64_t pl = P.sn_end[ll] - P.sn_start[ll];
+        int64_t a1 = d->linv_off_h[P.level_ptr[l + 1] - 1] + pl * pl;
+        (void)lf;
+        CUDA_TRY(cudaMemsetAsync(Li + a0, 0, (a1 - a0) * sizeof(cx<T>), s));
+        dim3 gd((unsigned)((d->level_maxp[l] + 31) / 32), nf);
+        k_trinv_diag<T><<<gd, 32, 0, s>>>(lvl, ft, arena, d->linv_off + P.level_ptr[l], Li);
         ++nl;
+        const CgBufs<T> ib{{arena, Li, (cx<T> *)d->tmp_inv, nullptr, nullptr, nullptr}};
+        for (auto &st : d->inv_stage[l]) {
+          launch_cgemm<T>(st[3], st[2], d->inv_items + st[0], st[1], ib, nullptr, s);
+          ++nl;
+        }
+        PROF_END(PC_INV);
       }
-      PROF_END(PC_INV);
     }
+    d->prof.cur_level = -1;
+    k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
+    ++nl;
+  return D3M_OK;
+  };
+  if (use_graph && d->g_factor) {
+    CUDA_TRY(cudaGraphLaunch(d->g_factor, s));
+    nl = d->g_factor_launches;
+  } else if (use_graph) {
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc != D3M_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e == cudaSuccess) {
+      // node priorities (look-ahead) apply only with this flag
+      const cudaError_t ei =
+          cudaGraphInstantiateWithFlags(&d->g_factor, g, cudaGraphInstantiateFlagUseNodePriority);
+      cudaGraphDestroy(g);
+      CUDA_TRY(ei);
+    } else {
+      CUDA_TRY(e);
+    }
+    d->g_factor_launches = nl;
+    CUDA_TRY(cudaGraphLaunch(d->g_factor, s));
+  } else {
+    const int rc = enqueue();
+    if (rc != D3M_OK) return rc;
   }
-  d->prof.cur_level = -1;
-  k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
-  ++nl;
   c.stats.launches_factor = nl + d->inv_launches;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -3369,7 +3465,7 @@ int dev_grad_eps(Ctx &c, const double *x, int64_t ldx, const double *y, int64_t 
 
 void dev_free(Ctx &c) {
   if (!c.dev) return;
-  for (cudaGraphExec_t g : {c.dev->g_fwd, c.dev->g_bwd})
+  for (cudaGraphExec_t g : {c.dev->g_fwd, c.dev->g_bwd, c.dev->g_factor})
     if (g) cudaGraphExecDestroy(g);
   if (c.dev->stream_b) {
     cudaStreamSynchronize(c.dev->stream_b);
@@ -3638,6 +3734,13 @@ extern "C" int d3m_dense_ldlt_noalloc(int32_t m, int32_t p, int32_t batch, doubl
                                       int32_t *info, void *stream) {
   if (m <= 0 || p < 0 || p > m || batch <= 0 || !A || !perm || !dinv || !info) return D3M_EINVAL;
   return d3m::dense_ldlt_noalloc(m, p, batch, A, perm, dinv, info, stream);
+}
+
+extern "C" int d3m_set_profile(d3m_ctx *h, int32_t on) {
+  if (!h) return D3M_EINVAL;
+  h->c.opt.profile = on != 0;
+  if (h->c.dev) h->c.dev->prof.on = on != 0;
+  return D3M_OK;
 }
 
 extern "C" int d3m_factor(d3m_ctx *h) {

@@ -21,7 +21,7 @@ SN_RANGE, SN_PARENT, SN_KIND, SN_STRUCT, M_MAP, LM, BLOCKS, LAMBDA, STATS, M_ENT
 
 _SYMBOLS = ["d3m_setup", "d3m_factor", "d3m_solve", "d3m_solve_host", "d3m_rhs_planewave",
             "d3m_structure", "d3m_dense_ldlt", "d3m_dense_ldlt_noalloc", "d3m_export_front", "d3m_stats_get",
-            "d3m_last_error", "d3m_free", "d3m_solve_adjoint", "d3m_grad_eps"]
+            "d3m_last_error", "d3m_free", "d3m_solve_adjoint", "d3m_grad_eps", "d3m_set_profile"]
 
 
 class Mesh(ctypes.Structure):
@@ -98,6 +98,7 @@ def load():
     lib.d3m_dense_ldlt.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32]
     lib.d3m_dense_ldlt_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P]
     lib.d3m_stats_get.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.d3m_set_profile.argtypes = [P, ctypes.c_int32]
     lib.d3m_export_front.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32), P, P, P]
     lib.d3m_last_error.argtypes = [P]
@@ -267,6 +268,10 @@ class Solver:
         self._check(self.lib.d3m_export_front(self.h, q, None, None, F.ctypes.data, perm.ctypes.data,
                                               dinv.ctypes.data))
         return F.T.copy(), perm[: p.value], dinv[: p.value]
+
+    def set_profile(self, on):
+        """Per-kernel-class event timing on/off for the following calls."""
+        self._check(self.lib.d3m_set_profile(self.h, int(bool(on))))
 
     def stats(self):
         s = Stats()

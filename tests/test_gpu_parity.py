@@ -302,7 +302,7 @@ def test_lookahead_bitwise_identical(prec, uk):
     _need_gpu()
     w = W.make(1)
     sv = []
-    for la in (1, 0):
+    for la in (0, 1):
         s = d3m.Solver.from_workload(w, precision=prec, update_kernel=uk, autotune=1, lookahead=la)
         s.factor()
         sv.append(s)
@@ -319,3 +319,27 @@ def test_lookahead_bitwise_identical(prec, uk):
     assert torch.equal(xa, xb)
     for s in sv:
         s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [d3m.MIXED, d3m.FP64])
+def test_factor_graph_replay_bitwise(prec):
+    """Unprofiled factorisations replay the launch sequence captured at their
+    first call; the replay, the capture run and an eager profiled run give
+    the same factors bit for bit."""
+    _need_gpu()
+    w = W.make(1)
+    s = d3m.Solver.from_workload(w, precision=prec, autotune=1)
+    n = len(s.structure(d3m.SN_RANGE))
+    fronts = []
+    for prof in (True, False, False):  # eager, capture + launch, replay
+        s.set_profile(prof)
+        s.factor()
+        fronts.append([s.export_front(q) for q in range(0, n, max(1, n // 60))])
+    for other in fronts[1:]:
+        for (Fa, pa, da), (Fb, pb, db) in zip(fronts[0], other):
+            assert np.array_equal(pa, pb) and np.array_equal(da, db) and np.array_equal(Fa, Fb)
+    f = fem.rhs_planewave(w)
+    x, info = s.solve(torch.tensor(f.T.copy(), device="cuda").t())
+    assert info["max_resid"] < 1e-10
+    s.close()
