@@ -1776,7 +1776,7 @@ __global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ l
 
 // Backward update rows are split into blocks of BSPLIT rows; each block's
 // partial sums L21^T x (per pivot) are added up by k_bwd_solve / k_bwd_w.
-constexpr int BSPLIT = 512;
+constexpr int BSPLIT = 256;
 
 // ------------------------------------------------------------ batched complex GEMM
 // C = alpha op(A) B (+ C) over a list of items (all fronts of a level), one
@@ -1801,11 +1801,17 @@ template <typename T>
 struct CgBufs {
   cx<T> *p[6];
 };
-constexpr int CG_BN = 64, CG_KC = 16;
+constexpr int CG_BN = 64;
+// K chunk: 48 for the small fp32 tiles (the launches of the levels with few
+// fronts are latency bound, so each round trip carries more of K), else 16
 template <typename T, int BM>
-__global__ void __launch_bounds__(256) k_cgemm(const CgItem *__restrict__ items, int nitems, int ntiles,
+__host__ __device__ constexpr int cg_kc() {
+  return sizeof(T) == 4 && BM == 32 ? 48 : 16;
+}
+template <typename T, int BM>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_cgemm(const CgItem *__restrict__ items, int nitems, int ntiles,
                                                CgBufs<T> bufs, const int64_t *__restrict__ gidx) {
-  constexpr int BN = CG_BN, KC = CG_KC, RA = BM / 16, RB = BN / 16;
+  constexpr int BN = CG_BN, KC = cg_kc<T, BM>(), RA = BM / 16, RB = BN / 16;
   constexpr int LA = BM * KC / 256, LB = BN * KC / 256;  // staged elements per thread
   const int t = blockIdx.x;
   if (t >= ntiles) return;
