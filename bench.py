@@ -132,13 +132,14 @@ def _sum_over_ranks(ws, v):
     return float(t.item())
 
 
-def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=False, dev_index=0):
+def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=False, dev_index=0, cache=None):
     """Times `steps` steps (factor + solve) of one precision, then runs the same
     steps again with the library's per-kernel-class CUDA events on (eager
     launches) for the kernel breakdown and the roofline.  Returns a dict."""
     import torch
     from paper_2002_05018_gb300 import d3m
-    s = d3m.Solver.from_workload(w, precision=prec, stream=stream, profile=False)
+    s = d3m.Solver.from_workload(w, precision=prec, stream=stream, profile=False,
+                                 autotune_cache=None if cache is None else f"{cache}.{'mixed' if prec else 'fp64'}")
     st0 = s.stats()
     factor_flops = st0["flops_interior"] + st0["flops_domain"] + st0["flops_k"]
     r = rhs_dev.shape[1]
@@ -320,6 +321,9 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--autotune-cache", default=None,
+                    help="file prefix for the tuned factor schedules (read when they match, else written); "
+                         "lets a profiler run reuse the schedule of a plain run")
     args = ap.parse_args()
     ws, rank, local = _dist()
     from paper_2002_05018_gb300 import workloads as W
@@ -372,14 +376,14 @@ def main():
     torch.cuda.synchronize()
 
     mixed = run_precision(w, d3m.MIXED, args.steps, args.warmup, ws, stream, rhs_dev, sample_clocks=(rank == 0),
-                          dev_index=dev)
+                          dev_index=dev, cache=args.autotune_cache)
     e2e_ms, h2d, d2h = e2e_mixed(mixed["solver"], w, f_host, args.steps, args.warmup, ws, stream)
     mixed["solver"].close()
     del mixed["solver"], mixed["x"]
     torch.cuda.empty_cache()
     fp64 = None
     if not args.no_fp64:
-        fp64 = run_precision(w, d3m.FP64, args.steps, args.warmup, ws, stream, rhs_dev)
+        fp64 = run_precision(w, d3m.FP64, args.steps, args.warmup, ws, stream, rhs_dev, cache=args.autotune_cache)
         fp64["solver"].close()
         del fp64["solver"], fp64["x"]
         torch.cuda.empty_cache()
