@@ -112,24 +112,26 @@ def _barrier(ws):
         dist.barrier()
 
 
-def _max_over_ranks(ws, v):
+def _reduce(ws, v, op):
+    """All-reduce of one float over the ranks (NCCL on the GPU, gloo on CPU)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _max_over_ranks(ws, v):
+    import torch.distributed as dist
+    return v if ws == 1 else _reduce(ws, v, dist.ReduceOp.MAX)
 
 
 def _sum_over_ranks(ws, v):
-    if ws == 1:
-        return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return v if ws == 1 else _reduce(ws, v, dist.ReduceOp.SUM)
 
 
 def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=False, dev_index=0, cache=None):
