@@ -718,9 +718,8 @@ __global__ void __launch_bounds__(512)
       if (i < k) continue;
       cx<T> acc = qi == 0 ? cur0 : cur1;
       const cx<T> *Lq = Ls + (size_t)q * LSTR;
-#pragma unroll 8
-      for (int t = 0; t < NB - 1; ++t)
-        if (t < j) acc = cfms(acc, Lq[t], wrow[t]);
+#pragma unroll 4
+      for (int t = 0; t < j; ++t) acc = cfms(acc, Lq[t], wrow[t]);  // j terms (not NB predicated)
       wk[q] = acc;
       if (i > k && i < p) loc = amaxT(loc, ArgMaxT<T>{cabs1T(acc), i});
     }
@@ -778,9 +777,8 @@ __global__ void __launch_bounds__(512)
         if (i < k) continue;
         cx<T> acc = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
         const cx<T> *Lq = Ls + (size_t)q * LSTR;
-#pragma unroll 8
-        for (int t = 0; t < NB - 1; ++t)
-          if (t < j) acc = cfms(acc, Lq[t], wrow2[t]);
+#pragma unroll 4
+        for (int t = 0; t < j; ++t) acc = cfms(acc, Lq[t], wrow2[t]);
         wr[q] = acc;
         if (i != imax && i < p) rl = amaxT(rl, ArgMaxT<T>{cabs1T(acc), i});
       }
@@ -848,11 +846,6 @@ __global__ void __launch_bounds__(512)
         // after a 1x1 interchange with kp > k + 1 the slot now at row kp needs
         // A[kp, k+1] = A[k+1, k] (original), held by the slot of row k + 1
         if (kstep == 1 && kp > k + 1 && i == k + 1) fixv = qi == 0 ? cur0 : cur1;
-      }
-      if (rank == 0 && tid == 0) {
-        int32_t a = pv[kk];
-        pv[kk] = pv[kp];
-        pv[kp] = a;
       }
       csync();  // the moves have read their sources; every thread has read p2s
       for (int q = tid; q < ns; q += nth) {
@@ -991,6 +984,16 @@ __global__ void __launch_bounds__(512)
     }
   __syncthreads();  // Ls is free from here on: staging buffer for the moves
   const int nmv = s_nmv;
+  // the panel's interchanges on the pivot order (rank 0): position r now holds
+  // what position k0 + p2s[r - k0] held (staged, since the gather is in place)
+  if (rank == 0 && nmv > 0) {
+    int32_t *pvs = reinterpret_cast<int32_t *>(Ls);  // nr ints fit: 4 nr <= 8 LSTR rcap
+    for (int q = tid; q < nr; q += nth) pvs[q] = pv[k0 + p2s[q]];
+    __syncthreads();
+    for (int q = tid; q < nr; q += nth)
+      if (p2s[q] != q) pv[k0 + q] = pvs[q];
+    __syncthreads();
+  }
   // the panel's column permutation for k_l21 (update rows): per panel column
   // its source column, then the moves (destination, source) of the columns
   // right of the panel
