@@ -181,33 +181,6 @@ template <typename T>
 __device__ __forceinline__ T cabs1T(cx<T> a) {
   return fabs(a.re) + fabs(a.im);
 }
-template <typename T>
-__device__ ArgMaxT<T> block_argmaxT(ArgMaxT<T> x, ArgMaxT<T> *sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    ArgMaxT<T> y;
-    y.v = __shfl_down_sync(0xffffffffu, x.v, o);
-    y.i = __shfl_down_sync(0xffffffffu, x.i, o);
-    x = amaxT(x, y);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    x = l < (int)(blockDim.x >> 5) ? sh[l] : ArgMaxT<T>{(T)-1, 0x7fffffff};
-    for (int o = 16; o > 0; o >>= 1) {
-      ArgMaxT<T> y;
-      y.v = __shfl_down_sync(0xffffffffu, x.v, o);
-      y.i = __shfl_down_sync(0xffffffffu, x.i, o);
-      x = amaxT(x, y);
-    }
-    if (l == 0) sh[0] = x;
-  }
-  __syncthreads();
-  ArgMaxT<T> r = sh[0];
-  __syncthreads();
-  return r;
-}
 struct ArgMax {
   double v;
   int i;
