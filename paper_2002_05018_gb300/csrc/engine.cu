@@ -2253,6 +2253,10 @@ struct DeviceState {
   // W and the per-step (k0 + kb, kb) snapshots rotate through three slots
   cudaStream_t stream_b = nullptr;
   cudaEvent_t ev_step[3] = {}, ev_schur[3] = {}, ev_b = nullptr;
+  // the mixed path's L11^{-1} of a finished level runs on a third stream while
+  // the next level proceeds (it reads only the level's pivot blocks)
+  cudaStream_t stream_c = nullptr;
+  cudaEvent_t ev_lvl = nullptr, ev_c = nullptr;
   int2 *snap = nullptr;          // [3][level position]
   int64_t wslot = 0;             // elements per W slot
   bool lookahead_off = false;    // set while the autotuner times the kernels
@@ -2407,6 +2411,9 @@ static int dev_init(Ctx &c) {
     CUDA_TRY(cudaEventCreateWithFlags(&d->ev_schur[q], cudaEventDisableTiming));
   }
   CUDA_TRY(cudaEventCreateWithFlags(&d->ev_b, cudaEventDisableTiming));
+  CUDA_TRY(cudaStreamCreateWithPriority(&d->stream_c, cudaStreamNonBlocking, prio_lo));
+  CUDA_TRY(cudaEventCreateWithFlags(&d->ev_lvl, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&d->ev_c, cudaEventDisableTiming));
   const int64_t nsn = (int64_t)P.sn_start.size();
   std::vector<int32_t> m(nsn), pp(nsn), par(nsn);
   std::vector<int64_t> soff(nsn);
@@ -2778,6 +2785,13 @@ static int factor_t(Ctx &c) {
       // kernels, since on the fp64 pipe the extra p^3/6 flops cost more than
       // the sequential blocks): diagonal 32-blocks, then doubling stages
       if (sizeof(T) == 4) {
+        // under look-ahead on stream_c, after everything of this level
+        cudaStream_t si = s;
+        if (la) {
+          si = d->stream_c;
+          CUDA_TRY(cudaEventRecord(d->ev_lvl, s));
+          CUDA_TRY(cudaStreamWaitEvent(si, d->ev_lvl, 0));
+        }
         PROF_BEGIN(PC_INV);
         cx<T> *Li = (cx<T> *)d->linv;
         int lf = P.level_fronts[P.level_ptr[l]];
@@ -2786,17 +2800,21 @@ static int factor_t(Ctx &c) {
         int64_t pl = P.sn_end[ll] - P.sn_start[ll];
         int64_t a1 = d->linv_off_h[P.level_ptr[l + 1] - 1] + pl * pl;
         (void)lf;
-        CUDA_TRY(cudaMemsetAsync(Li + a0, 0, (a1 - a0) * sizeof(cx<T>), s));
+        CUDA_TRY(cudaMemsetAsync(Li + a0, 0, (a1 - a0) * sizeof(cx<T>), si));
         dim3 gd((unsigned)((d->level_maxp[l] + 31) / 32), nf);
-        k_trinv_diag<T><<<gd, 32, 0, s>>>(lvl, ft, arena, d->linv_off + P.level_ptr[l], Li);
+        k_trinv_diag<T><<<gd, 32, 0, si>>>(lvl, ft, arena, d->linv_off + P.level_ptr[l], Li);
         ++nl;
         const CgBufs<T> ib{{arena, Li, (cx<T> *)d->tmp_inv, nullptr, nullptr, nullptr}};
         for (auto &st : d->inv_stage[l]) {
-          launch_cgemm<T>(st[3], st[2], d->inv_items + st[0], st[1], ib, nullptr, s);
+          launch_cgemm<T>(st[3], st[2], d->inv_items + st[0], st[1], ib, nullptr, si);
           ++nl;
         }
         PROF_END(PC_INV);
       }
+    }
+    if (la && sizeof(T) == 4) {  // join the inverses before the factor completes
+      CUDA_TRY(cudaEventRecord(d->ev_c, d->stream_c));
+      CUDA_TRY(cudaStreamWaitEvent(s, d->ev_c, 0));
     }
     d->prof.cur_level = -1;
     k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
@@ -3457,6 +3475,12 @@ void dev_free(Ctx &c) {
       cudaEventDestroy(c.dev->ev_schur[q]);
     }
     cudaEventDestroy(c.dev->ev_b);
+  }
+  if (c.dev->stream_c) {
+    cudaStreamSynchronize(c.dev->stream_c);
+    cudaStreamDestroy(c.dev->stream_c);
+    cudaEventDestroy(c.dev->ev_lvl);
+    cudaEventDestroy(c.dev->ev_c);
   }
   if (c.dev->own_stream) {
     cudaStreamSynchronize(c.dev->stream);
