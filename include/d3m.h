@@ -115,6 +115,8 @@ typedef struct {
                            before the next panel.  Both give bitwise identical
                            factors. */
 } d3m_options;
+/* d3m_setup returns D3M_EINVAL (and the context, for d3m_last_error) when an
+ * option lies outside the values listed above. */
 
 /* Per-solve report: per column relative residual (Numerical Results
  * section's ||A x - f||_inf / ||f||_inf) and refinement steps taken. */

@@ -850,6 +850,17 @@ extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double 
     *out = h;
     return D3M_EINVAL;
   }
+  const char *bad = nullptr;
+  if (c.opt.leaf_max < 0) bad = "leaf_max < 0";
+  else if (c.opt.panel_kernel != 0 && c.opt.panel_kernel != 1) bad = "panel_kernel not 0 or 1";
+  else if (c.opt.update_kernel < 0 || c.opt.update_kernel > 2) bad = "update_kernel not 0, 1 or 2";
+  else if (c.opt.autotune != 0 && c.opt.autotune != 1) bad = "autotune not 0 or 1";
+  else if (c.opt.lookahead != 0 && c.opt.lookahead != 1) bad = "lookahead not 0 or 1";
+  if (bad) {
+    c.err = std::string("d3m_setup: ") + bad;
+    *out = h;
+    return D3M_EINVAL;
+  }
   int rc;
   try {
     rc = d3m::build_plan(c, mesh, mat, k, part);

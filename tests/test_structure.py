@@ -105,3 +105,14 @@ def test_level_table_matches_tree_heights():
     assert abs(lv[:, 3].sum() - total) <= 1e-9 * total
     assert np.all(lv[:, 4:] == 0)  # nothing factored yet
     s.close()
+
+
+@pytest.mark.parametrize("kw", [dict(update_kernel=3), dict(panel_kernel=2), dict(autotune=-1),
+                                dict(lookahead=2), dict(leaf_max=-5)])
+def test_setup_rejects_bad_options(kw):
+    """Option values outside their documented sets are refused at set-up."""
+    w = W.make(1)
+    with pytest.raises(d3m.D3MError) as ei:
+        d3m.Solver.from_workload(w, **kw)
+    assert ei.value.code == d3m.D3M_EINVAL
+    assert "d3m_setup" in str(ei.value)
