@@ -1608,7 +1608,7 @@ __global__ void __launch_bounds__(256) k_fwd_solve(const int32_t *__restrict__ l
       int a = e / RC, cc = e % RC;
       if (cc < nc) Yf[(int64_t)(kb0 + a) * r + c0 + cc] = ys[a][cc];
     }
-    // pivot rows below the block (the update rows are done by k_fwd_gemm)
+    // pivot rows below the block (the update rows are done by the L21 GEMM, k_cgemm)
     for (int i = kb0 + nbk + tid; i < p; i += 256) {
       cx<T> acc[RC];
 #pragma unroll
@@ -1658,7 +1658,7 @@ __global__ void __launch_bounds__(256) k_fwd_solve(const int32_t *__restrict__ l
 
 // Backward substitution with L11^T on the pivot rows, right-looking: start
 // from w = z - sum_s part_s (the split partial products L21^T x_upd of
-// k_bwd_gemm), then for each 32-block from the last: solve the diagonal
+// the L21^T GEMM, k_cgemm), then for each 32-block from the last: solve the diagonal
 // block, publish x, and subtract L[blk, k]^T x_blk from every earlier pivot
 // row k.  x is written to xM at the original (un-permuted) positions.
 template <typename T, int RC>
