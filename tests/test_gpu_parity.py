@@ -222,6 +222,28 @@ def test_config2_full_size_residual(precision):
     assert info["max_resid"] < 1e-10
 
 
+def test_config4_pec_plate_full_size_residual():
+    """Full-size 48x48x24 workload with a PEC plate on the mid-z node layer
+    (8 plane waves), mixed precision with refinement: residual of the
+    oracle's own assembled operator on the free edges, zero field on the
+    removed (PEC) edges."""
+    _need_gpu()
+    w = W.make(4)
+    s = d3m.Solver.from_workload(w, precision=d3m.MIXED)
+    s.factor()
+    f = s.rhs_planewave(w.khat_pol6())
+    cols = [0, 7]
+    fo = fem.rhs_planewave(w, which=cols)
+    assert np.abs(f[:, cols] - fo).max() < 1e-12 * np.abs(fo).max()
+    x, info = s.solve(torch.tensor(f.T.copy(), device="cuda").t())
+    x = x.cpu().numpy()
+    assert info["max_resid"] < 1e-10
+    assert fem.rel_residual(w, x[:, cols], fo).max() < 1e-10
+    pec = np.flatnonzero(w.pec_edge)
+    assert pec.size > 0 and np.all(x[pec] == 0)
+    s.close()
+
+
 @pytest.mark.parametrize("wk", [1, 3])
 def test_tensor_core_update_matches_fp32_fma(wk):
     """The tcgen05 3xTF32 trailing update against the fp32-FMA update: every
