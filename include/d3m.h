@@ -29,7 +29,9 @@
  *    from d3m_last_error(ctx).  No call aborts the process or traps the GPU;
  *    device-side waits are bounded and report D3M_ETIMEOUT.
  *  - all device work is ordered on d3m_options.stream (a cudaStream_t, NULL =
- *    the legacy default stream); calls return after the work is complete.
+ *    the legacy default stream); the library's internal streams (look-ahead,
+ *    overlapped inverses) fork from and join back into it, and calls return
+ *    after the work is complete.
  */
 #ifndef D3M_H
 #define D3M_H
@@ -54,9 +56,12 @@ enum d3m_status {
 
 enum d3m_precision {
   D3M_FP64 = 0,       /* factors and substitutions in complex128 */
-  D3M_MIXED = 1       /* factors in complex64 (pivot choice and 1x1/2x2
-                         inverses in fp64), fp64 residuals and iterative
-                         refinement against the fp64 sparse operator */
+  D3M_MIXED = 1       /* factors in complex64; the pivot tests decide as fp64
+                         tests on the complex64 values (fp32 comparisons,
+                         re-evaluated in fp64 when within 2^-20 of a tie); the
+                         1x1/2x2 pivot inverses kept for the substitution in
+                         fp64; fp64 residuals and iterative refinement against
+                         the fp64 sparse operator */
 };
 
 typedef struct d3m_ctx d3m_ctx;
@@ -172,7 +177,12 @@ int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double k,
  * tree, the front assembly (extend-add), restricted Bunch-Kaufman panels and
  * trailing updates of every front: subdomain interiors, interface fronts whose
  * contribution blocks are -K_D^(i), and the fronts of K.  D3M_ESINGULAR if a
- * pivot column is exactly zero.
+ * pivot column is exactly zero.  The first call also tunes the per-level
+ * schedule (d3m_options.autotune) with two timed trial factorisations; an
+ * unprofiled call captures its launch sequence into a CUDA graph that later
+ * unprofiled calls replay (the same arithmetic, bit for bit).  Call it again
+ * after the materials change (a new d3m_setup) or to refactor the same
+ * operator.
  */
 int d3m_factor(d3m_ctx *ctx);
 
