@@ -19,6 +19,9 @@ Modules
   d3m       the seven main steps: domain matrices K_D, assembly of K,
             Algorithm 1 block LDL^T, substitution, recovery of E
   adjoint   gradient of J = sum |x_probe|^2 w.r.t. per-cell eps_r
+  gmres_ir  plain and GMRES-based iterative refinement with a low-precision
+            factorisation (the mixed path's refinement step and its
+            GMRES-IR variant)
 
 Parity status per function is stated in each module header.
 """
