@@ -412,8 +412,9 @@ def main():
                              "tcgen05_update_levels": r["stats"]["tuned_levels_tc"],
                              "doubled_cluster_levels": r["stats"]["tuned_levels_cs2"],
                              "tuning_ms": round(r["stats"]["ms_tuning"], 1)},
-                "roofline": _roofline(r["prof"], alu, dom, _load_traffic(f"{dom}<{prec_tag}>")),
-                "roofline_" + other: _roofline(r["prof"], alu, other, _load_traffic(f"{other}<{prec_tag}>")),
+                "roofline": _roofline(r["prof"], alu, dom, _load_traffic(f"config{args.config}:{dom}<{prec_tag}>")),
+                "roofline_" + other: _roofline(r["prof"], alu, other,
+                                               _load_traffic(f"config{args.config}:{other}<{prec_tag}>")),
                 "kernel_timing": "per-kernel-class CUDA events in a second, profiled run of the same steps "
                                  "(the timed steps replay the captured factor graph without events)"}
 
