@@ -314,6 +314,29 @@ def _load_traffic(name):
     return None
 
 
+def precision_summary(r, alu, prec_tag, config, nrhs):
+    """The per-precision sub-object of the JSON line from one run_precision
+    result: step/factor/solve figures, the profiled kernel split, the tuned
+    schedule, and rooflines for the kernel class with the most time
+    ("roofline") and for the other class."""
+    dom = "panel" if r["prof"]["ms_panel"] >= r["prof"]["ms_update"] else "update"
+    other = "update" if dom == "panel" else "panel"
+    return {"factor_gflops": round(r["factor_flops"] / (r["factor_ms"] * 1e-3) / 1e9, 2),
+            "factor_ms": round(r["factor_ms"], 3),
+            "solve_rhs_per_s": round(nrhs / (r["solve_ms"] * 1e-3), 1),
+            "solve_ms": round(r["solve_ms"], 3), "refine_steps": r["iters"],
+            "max_resid": r["max_resid"], "ms_per_step": round(r["step_ms"], 3),
+            "kernel_ms": {k: round(v, 3) for k, v in r["prof"].items() if k.startswith("ms_")},
+            "schedule": {"levels": r["stats"]["n_levels"],
+                         "tcgen05_update_levels": r["stats"]["tuned_levels_tc"],
+                         "doubled_cluster_levels": r["stats"]["tuned_levels_cs2"],
+                         "tuning_ms": round(r["stats"]["ms_tuning"], 1)},
+            "roofline": _roofline(r["prof"], alu, dom, _load_traffic(f"config{config}:{dom}<{prec_tag}>")),
+            "roofline_" + other: _roofline(r["prof"], alu, other, _load_traffic(f"config{config}:{other}<{prec_tag}>")),
+            "kernel_timing": "per-kernel-class CUDA events in a second, profiled run of the same steps "
+                             "(the timed steps replay the captured factor graph without events)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,23 +423,7 @@ def main():
     alu64 = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_GHZ / 1e3
 
     def summary(r, alu, prec_tag):
-        dom = "panel" if r["prof"]["ms_panel"] >= r["prof"]["ms_update"] else "update"
-        other = "update" if dom == "panel" else "panel"
-        return {"factor_gflops": round(r["factor_flops"] / (r["factor_ms"] * 1e-3) / 1e9, 2),
-                "factor_ms": round(r["factor_ms"], 3),
-                "solve_rhs_per_s": round(w.nrhs / (r["solve_ms"] * 1e-3), 1),
-                "solve_ms": round(r["solve_ms"], 3), "refine_steps": r["iters"],
-                "max_resid": r["max_resid"], "ms_per_step": round(r["step_ms"], 3),
-                "kernel_ms": {k: round(v, 3) for k, v in r["prof"].items() if k.startswith("ms_")},
-                "schedule": {"levels": r["stats"]["n_levels"],
-                             "tcgen05_update_levels": r["stats"]["tuned_levels_tc"],
-                             "doubled_cluster_levels": r["stats"]["tuned_levels_cs2"],
-                             "tuning_ms": round(r["stats"]["ms_tuning"], 1)},
-                "roofline": _roofline(r["prof"], alu, dom, _load_traffic(f"config{args.config}:{dom}<{prec_tag}>")),
-                "roofline_" + other: _roofline(r["prof"], alu, other,
-                                               _load_traffic(f"config{args.config}:{other}<{prec_tag}>")),
-                "kernel_timing": "per-kernel-class CUDA events in a second, profiled run of the same steps "
-                                 "(the timed steps replay the captured factor graph without events)"}
+        return precision_summary(r, alu, prec_tag, args.config, w.nrhs)
 
     if rank != 0:
         if ws > 1:

@@ -41,3 +41,35 @@ def test_set_profile_argument_checks():
     s.set_profile(True)
     s.set_profile(False)
     s.close()
+
+
+def _fake_run(ms_panel, ms_update):
+    prof = {"ms_update": ms_update, "ms_panel": ms_panel, "ms_assemble": 1.0, "ms_inverse": 2.0, "ms_fwd": 3.0,
+            "ms_bwd": 4.0, "ms_residual": 0.5, "flops_update": 4.0e11, "flops_panel": 1.0e10}
+    stats = {"n_levels": 28, "tuned_levels_tc": 0, "tuned_levels_cs2": 3, "ms_tuning": 200.0}
+    return dict(factor_flops=6.8e11, factor_ms=70.0, solve_ms=45.0, iters=3, max_resid=3e-11, step_ms=115.0,
+                prof=prof, stats=stats)
+
+
+def test_precision_summary_roofline_keys():
+    sys.path.insert(0, ROOT)
+    import bench
+    for ms_panel, ms_update, dom in ((40.0, 30.0, "panel"), (20.0, 30.0, "update")):
+        sub = bench.precision_summary(_fake_run(ms_panel, ms_update), 80.55, "float", 2, 64)
+        other = "update" if dom == "panel" else "panel"
+        roof, roof2 = sub["roofline"], sub["roofline_" + other]
+        for r in (roof, roof2):
+            for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+                assert k in r
+            assert r["unit"] == "TFLOP/s" and r["peak"] == 80.55
+            assert abs(r["frac"] - r["achieved"] / 80.55) < 1e-3
+        ms, fl = (ms_panel, 1.0e10) if dom == "panel" else (ms_update, 4.0e11)
+        assert abs(roof["achieved"] - fl / (ms * 1e-3) / 1e12) < 1e-3
+        assert roof["ms_per_step"] == ms
+        # traffic data exist for workload 2's update class only
+        assert (roof["traffic"] is not None) == (dom == "update")
+        assert sub["solve_rhs_per_s"] == round(64 / 45e-3, 1)
+        assert sub["schedule"]["doubled_cluster_levels"] == 3
+    # another workload never picks up workload 2's traffic figure
+    sub5 = bench.precision_summary(_fake_run(20.0, 30.0), 80.55, "float", 5, 128)
+    assert sub5["roofline"]["traffic"] is None
