@@ -189,3 +189,35 @@ def symbolic(plan, rows, cols):
     plan.parent = parent
     plan.struct = structs
     return plan
+
+
+def symbolic_merge(plan, rows, cols):
+    """The same supernodal structure as symbolic(), for matrices too large
+    for its n x n bitset: struct(s) = the neighbours of the rows of s in M,
+    together with the structures of the children of s in the supernodal tree,
+    keeping only indices past the last row of s; parent(s) = the supernode
+    holding min struct(s).  (Eliminating a supernode makes its structure a
+    clique; whatever of that clique lies past its parent is also in the
+    parent's structure, so a supernode only has to merge its children's.)
+    Pinned against the elimination game (tests/test_oracle_ordering.py)."""
+    n = plan.n
+    off = rows != cols
+    r, c = np.asarray(rows)[off], np.asarray(cols)[off]
+    o = np.argsort(r, kind="stable")
+    r, c = r[o], c[o]
+    ptr = np.searchsorted(r, np.arange(n + 1))
+    sn_of = np.repeat(np.arange(len(plan.sn_start)), plan.sn_end - plan.sn_start)
+    nsn = len(plan.sn_start)
+    parent = -np.ones(nsn, np.int64)
+    structs = [None] * nsn
+    kids = [[] for _ in range(nsn)]
+    for s, (a, b) in enumerate(zip(plan.sn_start, plan.sn_end)):
+        u = np.unique(np.concatenate([c[ptr[a]:ptr[b]]] + [structs[k] for k in kids[s]]))
+        st = u[u >= b].astype(np.int64)
+        structs[s] = st
+        if len(st):
+            parent[s] = sn_of[st[0]]
+            kids[parent[s]].append(s)
+    plan.parent = parent
+    plan.struct = structs
+    return plan

@@ -75,3 +75,68 @@ def test_singular_detected():
     F[2, 2] = F[3, 3] = 1.0
     with pytest.raises(bk.SingularPivot):
         bk.ldlt_restricted(F, 2)
+
+
+def _scipy_pattern(F):
+    """(perm, block sizes by first position, D) of LAPACK's complex-symmetric
+    Bunch-Kaufman LDL^T (scipy.linalg.ldl, hermitian=False, lower): the same
+    magnitude |Re| + |Im|, the same alpha and lowest-index ties."""
+    lu, d, perm = scipy.linalg.ldl(F, lower=True, hermitian=False)
+    n = F.shape[0]
+    sizes = {}
+    k = 0
+    while k < n:
+        if k + 1 < n and d[k + 1, k] != 0:
+            sizes[k] = 2
+            k += 2
+        else:
+            sizes[k] = 1
+            k += 1
+    return perm, sizes, d, lu
+
+
+@pytest.mark.parametrize("n,seed,scale", [(12, 0, 1.0), (24, 1, 0.3), (40, 2, 0.1), (48, 3, 0.0),
+                                          (60, 4, 0.05), (33, 5, 2.0)])
+def test_pivot_sequence_matches_lapack(n, seed, scale):
+    """Pivot sequence (1x1 / 2x2 pattern and the permutation) and D of the
+    full (p = n) factorisation against LAPACK's Bunch-Kaufman on random complex
+    symmetric matrices.  Below LAPACK's block size (64) it runs the unblocked
+    algorithm, the same right-looking order of updates; Gaussian entries keep
+    every decision far from a tie for these seeds."""
+    rng = np.random.default_rng(100 + seed)
+    F = _sym(n, rng, scale)
+    perm, L, dbl, C, steps = bk.ldlt_restricted(F)
+    sp_perm, sizes, d, lu = _scipy_pattern(F)
+    assert {k: s for k, s in steps} == sizes
+    assert np.array_equal(perm, sp_perm)
+    D = bk.d_matrix(dbl, n)
+    assert np.abs(D - d).max() < 1e-11 * np.abs(d).max()
+    assert np.abs(L - lu[sp_perm]).max() < 1e-10 * max(1.0, np.abs(L).max())
+    if scale < 0.2:
+        assert any(s == 2 for _, s in steps)     # small diagonals force 2x2 pivots
+
+
+def test_one_by_one_after_row_test():
+    """|a_kk| < alpha*omega_1 but |a_kk|*omega_r >= alpha*omega_1^2: a 1x1
+    pivot at k with no interchange (the middle Bunch-Kaufman test).  Without
+    that test the step would become the 2x2 pivot (|a_rr| < alpha*omega_r)."""
+    F = np.array([[0.5, 1.0, 0.0], [1.0, 0.1, 2.0], [0.0, 2.0, 1.0]], complex)
+    # omega_1 = 1 (row 1), omega_r = 2; 0.5 < 0.64 * 1, 0.5 * 2 >= 0.64 * 1
+    PF, R, perm, steps = _reconstruct(F, 3)
+    assert steps[0] == (0, 1) and perm[0] == 0
+    assert np.abs(PF - R).max() < 1e-14
+    sp_perm, sizes, _, _ = _scipy_pattern(F)
+    assert sizes[0] == 1 and sp_perm[0] == 0
+
+
+def test_two_by_two_when_all_tests_fail():
+    """|a_kk| small, |a_kk|*omega_r < alpha*omega_1^2 and |a_rr| < alpha*omega_r:
+    a 2x2 pivot on (k, r) with r moved next to k."""
+    F = np.array([[0.01, 0.2, 1.0], [0.2, 3.0, 0.1], [1.0, 0.1, 0.02]], complex)
+    # omega_1 = 1 at r = 2; omega_r = 1 (row 0 of column 2); 0.01 * 1 < 0.64;
+    # |a_22| = 0.02 < 0.64 * 1  ->  2x2 on (0, 2)
+    PF, R, perm, steps = _reconstruct(F, 3)
+    assert steps[0] == (0, 2) and list(perm[:2]) == [0, 2]
+    assert np.abs(PF - R).max() < 1e-14
+    sp_perm, sizes, _, _ = _scipy_pattern(F)
+    assert sizes[0] == 2 and list(sp_perm[:2]) == [0, 2]

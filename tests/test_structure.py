@@ -14,7 +14,15 @@ CASES = [
     ("tiny-2x2x2", lambda: W.tiny(4, 4, 4, 2, 2, 2, seed=1), 16),
     ("tiny-jitter", lambda: W.tiny(9, 7, 5, 3, 2, 2, seed=4, jitter=True), 24),
     ("tiny-pec", lambda: _pec_case(), 32),
+    # full-size workloads: jittered uneven 4x4x2 cuts (32^3 sphere; 48x48x24
+    # PEC plate) and the 2x2x2 per-cell-eps workload; their M is too large for
+    # the n x n bitset of the elimination game, so the oracle's children-merge
+    # form (pinned against the game in test_oracle_ordering.py) is used
+    ("config2", lambda: W.make(2), 64),
+    ("config3", lambda: W.make(3), 64),
+    ("config4", lambda: W.make(4), 64),
 ]
+LARGE = {"config2", "config3", "config4"}
 
 
 def _pec_case():
@@ -29,7 +37,7 @@ def test_structure_bit_exact(name, make, leaf):
     dec = decomp.decompose(w)
     plan = ordering.build_plan(dec, leaf_max=leaf)
     r, c = ordering.saddle_pattern(dec, plan)
-    ordering.symbolic(plan, r, c)
+    (ordering.symbolic_merge if name in LARGE else ordering.symbolic)(plan, r, c)
     s = d3m.Solver.from_workload(w, leaf_max=leaf)
     rng = s.structure(d3m.SN_RANGE)
     assert np.array_equal(rng[:, 0], plan.sn_start) and np.array_equal(rng[:, 1], plan.sn_end)
