@@ -230,60 +230,113 @@ def e2e_mixed(s, w, f_host, steps, warmup, ws, stream):
     return statistics.mean(ms), rhs.numel() * 16, xh.numel() * 16
 
 
-_CPU_CTX = {}
+# ------------------------------------------------------------ CPU oracle baseline
+def front_arena_bytes(rng, st):
+    """8 sum m^2 (complex64 fronts) from the exported supernode ranges and
+    update-row offsets."""
+    import numpy as np
+    n = len(rng)
+    m = (rng[:, 1] - rng[:, 0]) + np.diff(st[: n + 1])
+    return int(8 * (m.astype(np.int64) ** 2).sum())
 
 
-def _cpu_context(w):
-    """Oracle decomposition plus the library's per-front algorithmic flops."""
-    key = (w.name, w.seed)
-    if key not in _CPU_CTX:
+def oracle_front_flops(dec):
+    """The metric's algorithmic flop count per front, from the oracle's own
+    ordering and supernodal symbolic factorisation (no library involved):
+    eliminating p pivots of a front of order m costs sum_{k<p} (m-k)(m-k-1)/2
+    complex MACs = C(m+1, 3) - C(m-p+1, 3), 8 real flops each.  Returns
+    (kind, owner, flops) per front (kind 0 interior, 1 interface dofs, 2 K)
+    and the complex64 front storage 8 sum m^2 in bytes."""
+    import numpy as np
+    from oracle import ordering
+    plan = ordering.build_plan(dec)
+    r, c = ordering.saddle_pattern(dec, plan)
+    ordering.symbolic_merge(plan, r, c)
+    p = (plan.sn_end - plan.sn_start).astype(float)
+    m = p + np.array([len(st) for st in plan.struct], float)
+    c3 = lambda n: n * (n - 1.0) * (n - 2.0) / 6.0
+    return plan.sn_kind, plan.sn_owner, 8.0 * (c3(m + 1.0) - c3(m - p + 1.0)), int(8 * (m.astype(np.int64) ** 2).sum())
+
+
+def _kd_columns(args):
+    """Worker (spawned process): the oracle's main step 1 on a slice of the
+    multiplier columns of one subdomain."""
+    from oracle import d3m as od3m
+    A, Dc, which = args
+    KD = od3m.domain_matrix(A, Dc, which=which)
+    return float(abs(KD).max()) if KD.size else 0.0
+
+
+class OracleStep1:
+    """Bounded CPU sample of the oracle's D^3M path: its main step 1 (dense
+    domain matrix K_D of a subdomain by SciPy sparse LU, the dominant cost of
+    the oracle's factorisation) for one subdomain at a time, its multiplier
+    columns split over a pool of spawned worker processes (one per host core).
+    Each subdomain is credited with the algorithmic flops of its fronts
+    (interior + interface dofs) from the oracle's own symbolic factorisation."""
+
+    def __init__(self, w, workers=None):
+        import multiprocessing as mp
         import numpy as np
         from oracle import decomp
-        from paper_2002_05018_gb300 import d3m
-        dec = decomp.decompose(w)
-        s = d3m.Solver.from_workload(w)
-        rng = s.structure(d3m.SN_RANGE)
-        kind = s.structure(d3m.SN_KIND)
-        st = s.structure(d3m.SN_STRUCT)
-        s.close()
-        n = len(rng)
-        p = (rng[:, 1] - rng[:, 0]).astype(float)
-        m = p + np.diff(st[: n + 1])
-        # exact count used by the library: sum_{k<p} (m-k-1)(m-k)/2 complex MACs, 8 flops each
-        fl = np.array([8.0 * sum(0.5 * (mm - kk - 1) * (mm - kk) for kk in range(int(pp)))
-                       for mm, pp in zip(m, p)])
-        _CPU_CTX[key] = (dec, kind, fl)
-    return _CPU_CTX[key]
+        self.w = w
+        self.dec = decomp.decompose(w)
+        kind, owner, fl, self.arena_bytes = oracle_front_flops(self.dec)
+        self.flops = [float(fl[(kind <= 1) & (owner == q)].sum()) for q in range(len(self.dec.subs))]
+        self.workers = workers or os.cpu_count() or 1
+        # one BLAS thread per worker process (the workers already use every core)
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.workers)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        A0 = self.dec.subs[0].A
+        self.pool.map(_kd_columns, [(A0, np.zeros((A0.shape[0], 1)), None)] * self.workers)  # warm the workers
 
-
-def cpu_baseline_sample(w, budget_s=20.0, subs=None):
-    """The oracle's main step 1 (domain matrices K_D via sparse LU of A_i) on a
-    bounded number of subdomains of the same workload; rate in GFLOP/s using
-    the library's algorithmic flop count of those subdomains' fronts."""
-    import numpy as np
-    from oracle import decomp
-    dec, kind, fl = _cpu_context(w)
-    order = subs if subs is not None else list(range(len(dec.subs)))
-    done, flops, t0 = [], 0.0, time.perf_counter()
-    for q in order:
-        sd = dec.subs[q]
-        import scipy.sparse.linalg as spla
-        D = decomp.D_matrix(dec, sd).tocsc()
+    def run(self, q):
+        """Step 1 of subdomain q; returns (seconds, flops)."""
+        import numpy as np
+        from oracle import decomp
+        sd = self.dec.subs[q]
+        t0 = time.perf_counter()
+        D = decomp.D_matrix(self.dec, sd).tocsc()
         cols = np.flatnonzero(np.diff(D.indptr))
-        Dc = D[:, cols].toarray().astype(np.complex128)
-        lu = spla.splu(sd.A.tocsc())
-        KD = Dc.T @ lu.solve(Dc)
-        del KD
-        done.append(q)
-        sel = (kind[:, 1] == q) & (kind[:, 0] <= 1)
-        flops += fl[sel].sum()
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return flops / dt / 1e9, dict(cores=os.cpu_count(), sample=(
-        f"oracle main step 1 (SciPy sparse LU of A_i, K_D = D_i^T A_i^-1 D_i) on {len(done)} of "
-        f"{len(dec.subs)} subdomains of {w.name}; flops = the library's algorithmic count of those "
-        f"subdomains' fronts; {dt:.1f} s"), seconds=dt)
+        Dc = D[:, cols].toarray()
+        chunks = [c for c in np.array_split(np.arange(Dc.shape[1]), self.workers) if len(c)]
+        self.pool.map(_kd_columns, [(sd.A, Dc, c) for c in chunks])
+        return time.perf_counter() - t0, self.flops[q]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline_sample(w, budget_s=20.0):
+    """The oracle sample (OracleStep1) over subdomains 0, 1, ... until
+    budget_s seconds have passed; rate in GFLOP/s of the metric's count."""
+    o = OracleStep1(w)
+    done, secs, flops = 0, 0.0, 0.0
+    try:
+        for q in range(len(o.dec.subs)):
+            t, f = o.run(q)
+            secs += t
+            flops += f
+            done += 1
+            if secs > budget_s:
+                break
+    finally:
+        o.close()
+    return flops / secs / 1e9, dict(cores=o.workers, seconds=secs, sample=(
+        f"oracle main step 1 (K_D = D_i^T A_i^-1 D_i by SciPy sparse LU) on {done} of {len(o.dec.subs)} "
+        f"subdomains of {w.name}, multiplier columns split over {o.workers} spawned processes; flops = the "
+        f"metric's algorithmic count of those subdomains' fronts from the oracle's own symbolic "
+        f"factorisation; {secs:.1f} s"))
 
 
 _ROOF_KERNELS = {
@@ -337,6 +390,20 @@ def precision_summary(r, alu, prec_tag, config, nrhs):
                              "(the timed steps replay the captured factor graph without events)"}
 
 
+def bench_config(w, config, arena_bytes):
+    """The `config` object of the JSON line (the same for both arms);
+    arena_bytes = 8 sum m^2 over the fronts (complex64 front storage)."""
+    return {"workload": (f"config{config}: {w.nx}x{w.ny}x{w.nz} bricks ({w.n_edges} edges), "
+                         f"{w.lx:g}x{w.ly:g}x{w.lz:g} wavelengths, {'x'.join(map(str, w.partition))} subdomains "
+                         f"(cuts {[int(v) for v in w.cx]}/{[int(v) for v in w.cy]}/{[int(v) for v in w.cz]}), "
+                         f"{w.nrhs} plane waves"),
+            "nrhs": w.nrhs, "precision": "mixed+refine (headline)",
+            "l2": ("every step refactors the whole front arena (%.2f GB in complex64; L2 is 0.13 GB)"
+                   % (arena_bytes / 1e9)),
+            "step": f"d3m_factor + d3m_solve({w.nrhs} RHS) incl. refinement to resid<=1e-10",
+            "value_def": "algorithmic flops (factor + one substitution pass) / step time"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,33 +420,37 @@ def main():
     ws, rank, local = _dist()
     from paper_2002_05018_gb300 import workloads as W
     w = W.make(args.config)
-    workload = (f"config{args.config}: {w.nx}x{w.ny}x{w.nz} bricks ({w.n_edges} edges), "
-                f"{w.lx:g}x{w.ly:g}x{w.lz:g} wavelengths, {'x'.join(map(str, w.partition))} subdomains "
-                f"(cuts {[int(v) for v in w.cx]}/{[int(v) for v in w.cy]}/{[int(v) for v in w.cz]}), {w.nrhs} plane waves")
     if args.impl == "reference":
+        # the reference arm is the CPU oracle (no GPU, no library): rank 0 only
         if rank != 0:
             return
-        rates = []
         t0 = time.perf_counter()
-        budget = max(5.0, 120.0 / max(1, args.steps + args.warmup))
-        nsub = len(w.cx) - 1
-        nsubs = (len(w.cx) - 1) * (len(w.cy) - 1) * (len(w.cz) - 1)
-        for i in range(args.warmup + args.steps):
-            rate, meta = cpu_baseline_sample(w, budget_s=budget, subs=[i % nsubs])
-            if i >= args.warmup:
-                rates.append((rate, meta))
-        v = statistics.mean(r for r, _ in rates)
-        wall = time.perf_counter() - t0
+        o = OracleStep1(w)
+        samples = []
+        nsub = len(o.dec.subs)
+        try:
+            for i in range(args.warmup + args.steps):
+                t, f = o.run(i % nsub)
+                if i >= args.warmup:
+                    samples.append((t, f, i % nsub))
+        finally:
+            o.close()
+        secs = sum(t for t, _, _ in samples)
+        v = sum(f for _, f, _ in samples) / secs / 1e9
+        sample = (f"per step: oracle main step 1 (K_D = D_i^T A_i^-1 D_i by SciPy sparse LU) of one subdomain "
+                  f"of {w.name} (round robin), multiplier columns split over {o.workers} spawned processes; "
+                  f"flops = the metric's algorithmic count of that subdomain's fronts from the oracle's own "
+                  f"symbolic factorisation; {len(samples)} steps, {secs:.1f} s")
         line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "GFLOP/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": round(1000 * statistics.mean(m["seconds"] for _, m in rates), 1),
+                "ms_per_step": round(1000 * secs / max(1, len(samples)), 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-                "data": "synthetic", "config": {"workload": workload, "sample": "one subdomain per step"},
-                "cpu_baseline": {"value": round(v, 3), "unit": "GFLOP/s", "cores": os.cpu_count(),
-                                 "kind": "oracle", "sample": rates[-1][1]["sample"]},
+                "data": "synthetic", "config": bench_config(w, args.config, o.arena_bytes),
+                "cpu_baseline": {"value": round(v, 3), "unit": "GFLOP/s", "cores": o.workers,
+                                 "kind": "oracle", "sample": sample},
                 "e2e": {"value": round(v, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0},
-                "wall_s": round(wall, 1)}
+                "wall_s": round(time.perf_counter() - t0, 1)}
         print(json.dumps(line))
         return
 
@@ -395,6 +466,7 @@ def main():
     # RHS on the host once (d3m_rhs_planewave), then resident on the device
     probe = d3m.Solver.from_workload(w)
     f_host = probe.rhs_planewave(w.khat_pol6())
+    arena_c64 = front_arena_bytes(probe.structure(d3m.SN_RANGE), probe.structure(d3m.SN_STRUCT))
     probe.close()
     with torch.cuda.stream(stream):
         rhs_dev = torch.tensor(f_host.T.copy(), device="cuda").t()
@@ -441,10 +513,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 factors + c128 residual/refinement (mixed); c128 (fp64 leg)",
         "data": "synthetic",
-        "config": {"workload": workload, "nrhs": w.nrhs, "precision": "mixed+refine (headline)",
-                   "l2": "inputs larger than L2 (factor arena %.1f GB)" % (mixed["stats"]["arena_bytes"] / 1e9),
-                   "step": "d3m_factor + d3m_solve(64 RHS) incl. refinement to resid<=1e-10",
-                   "value_def": "algorithmic flops (factor + one substitution pass) / step time"},
+        "config": bench_config(w, args.config, arena_c64),
         "roofline": mix["roofline"],
         "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -31,6 +31,16 @@ import scipy.sparse.linalg as spla
 from . import bk, decomp, fem, ordering
 
 
+def domain_matrix(A, Dc, which=None, lu=None):
+    """Step 1 for one subdomain: K_D = D_i^T A_i^{-1} D_i with D_i restricted
+    to its nonzero columns (Dc, dense); with `which`, only those columns of
+    K_D (A_i^{-1} applied to those columns of Dc).  A_i^{-1} by SciPy sparse
+    LU (given in `lu`, or computed here)."""
+    lu = spla.splu(A.tocsc()) if lu is None else lu
+    B = Dc if which is None else Dc[:, which]
+    return Dc.T @ lu.solve(np.asarray(B, np.complex128))
+
+
 def domain_matrices(w, dec, dense=False):
     """Step 1: {subdomain: (multiplier ids, K_D)} and the LU objects."""
     out, lus = {}, {}
@@ -39,12 +49,12 @@ def domain_matrices(w, dec, dense=False):
         cols = np.flatnonzero(np.diff(D.indptr))
         Dc = D[:, cols].toarray()
         if dense:
-            X = np.linalg.inv(sd.A.toarray()) @ Dc
+            KD = Dc.T @ (np.linalg.inv(sd.A.toarray()) @ Dc)
         else:
             lu = spla.splu(sd.A.tocsc())
             lus[sd.index] = lu
-            X = lu.solve(Dc.astype(np.complex128))
-        out[sd.index] = (cols, Dc.T @ X)
+            KD = domain_matrix(sd.A, Dc, lu=lu)
+        out[sd.index] = (cols, KD)
     return out, lus
 
 

@@ -15,12 +15,25 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "1",
-                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    """The reference arm (the CPU oracle) prints the contract's line with the
+    same config as the GPU arm, and never loads the product library."""
+    code = ("import runpy, sys; sys.argv = ['bench.py', '--impl', 'reference', '--config', '1', '--steps', '1', "
+            "'--warmup', '3']; runpy.run_path('bench.py', run_name='__main__'); "
+            "print('LIBD3M_LOADED', any('libd3m' in ln for ln in open('/proc/self/maps')))")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
+    assert "LIBD3M_LOADED False" in out.stdout
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2002_05018_gb300 import workloads as W
+    w = W.make(1)
+    sv = d3m.Solver.from_workload(w)   # host-only set-up: the exported structure gives the same arena
+    arena = bench.front_arena_bytes(sv.structure(d3m.SN_RANGE), sv.structure(d3m.SN_STRUCT))
+    sv.close()
+    assert d["config"] == bench.bench_config(w, 1, arena)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
         assert k in d, k
