@@ -202,41 +202,68 @@ def test_config3_fp64():
     assert np.abs(x - xg).max() < 1e-10 * np.abs(xg).max()
 
 
+def _golden(cfg):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"x_samples_config{cfg}.npz")
+    if not os.path.exists(path):
+        pytest.fail(f"{path} is missing: run tests/golden/make_full_size_samples.py {cfg}")
+    return dict(np.load(path))
+
+
+def _check_against_golden(w, g, x, f, tol):
+    """Element-wise check of x at the stored sample rows against the oracle's
+    solution (relative to the oracle column's max |x|), after checking that
+    the library's RHS equals the oracle's at those rows."""
+    cols, rows = g["columns"], g["rows"]
+    assert np.abs(f[np.ix_(rows, cols)] - g["f"]).max() < 1e-12 * g["fmax"].max()
+    err = np.abs(x[np.ix_(rows, cols)] - g["x"]) / g["xmax"][None, :]
+    assert err.max() < tol, err.max()
+
+
 @pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
-def test_config2_full_size_residual(precision):
-    """Full-size 32^3 / 64-RHS workload in the bench configuration; checked
-    through the residual of the oracle's own assembled operator."""
+def test_config2_full_size(precision):
+    """Full-size 32^3 / 64-RHS workload in the bench configuration (the launch
+    configuration bench.py times, default schedule): x element by element at
+    2048 sampled rows of 8 of the 64 columns against the oracle's solution
+    (tests/golden, written by the oracle alone), and the residual of the
+    oracle's own assembled operator on 3 columns."""
     _need_gpu()
     w = W.make(2)
+    g = _golden(2)
     s = d3m.Solver.from_workload(w, precision=precision)
     s.factor()
     f = s.rhs_planewave(w.khat_pol6())
-    cols = [0, 17, 63]
-    fo = fem.rhs_planewave(w, which=cols)
-    assert np.abs(f[:, cols] - fo).max() < 1e-12 * np.abs(fo).max()
     rhs = torch.tensor(f.T.copy(), device="cuda").t()
     x, info = s.solve(rhs)
     x = x.cpu().numpy()
+    _check_against_golden(w, g, x, f, 1e-10 if precision == d3m.FP64 else 1e-8)
+    cols = [0, 17, 63]
+    fo = fem.rhs_planewave(w, which=cols)
+    assert np.abs(f[:, cols] - fo).max() < 1e-12 * np.abs(fo).max()
     res = fem.rel_residual(w, x[:, cols], fo)
     assert res.max() < 1e-10
     assert info["max_resid"] < 1e-10
+    s.close()
 
 
-def test_config4_pec_plate_full_size_residual():
+def test_config4_pec_plate_full_size():
     """Full-size 48x48x24 workload with a PEC plate on the mid-z node layer
-    (8 plane waves), mixed precision with refinement: residual of the
-    oracle's own assembled operator on the free edges, zero field on the
-    removed (PEC) edges."""
+    (8 plane waves), mixed precision with refinement: x element by element at
+    2048 sampled rows of 4 of the 8 columns against the oracle's solution, the
+    residual of the oracle's own assembled operator on the free edges, zero
+    field on the removed (PEC) edges."""
     _need_gpu()
     w = W.make(4)
+    g = _golden(4)
     s = d3m.Solver.from_workload(w, precision=d3m.MIXED)
     s.factor()
     f = s.rhs_planewave(w.khat_pol6())
+    x, info = s.solve(torch.tensor(f.T.copy(), device="cuda").t())
+    x = x.cpu().numpy()
+    _check_against_golden(w, g, x, f, 1e-8)
     cols = [0, 7]
     fo = fem.rhs_planewave(w, which=cols)
     assert np.abs(f[:, cols] - fo).max() < 1e-12 * np.abs(fo).max()
-    x, info = s.solve(torch.tensor(f.T.copy(), device="cuda").t())
-    x = x.cpu().numpy()
     assert info["max_resid"] < 1e-10
     assert fem.rel_residual(w, x[:, cols], fo).max() < 1e-10
     pec = np.flatnonzero(w.pec_edge)
@@ -244,10 +271,54 @@ def test_config4_pec_plate_full_size_residual():
     s.close()
 
 
+def test_config3_mixed():
+    """The 20^3 per-cell-eps workload in mixed precision with refinement
+    against the oracle's global solve (16 RHS would be the adjoint probes; one
+    plane wave here)."""
+    _need_gpu()
+    w = W.make(3)
+    s, x, info, f = _solve_case(w, d3m.MIXED)
+    xg = fem.solve_global(w, f)
+    assert np.abs(x - xg).max() < 1e-8 * np.abs(xg).max()
+    assert info["max_resid"] < 1e-10
+    s.close()
+
+
+def test_config5_full_size_mixed():
+    """The 64^3 workload (811k edges, 4x4x4 jittered subdomains, 128 plane
+    waves in one batch), mixed precision with refinement: every column meets
+    the residual criterion by the library's count, and 2 columns are checked
+    with the oracle's own assembled operator and plane-wave RHS (the oracle's
+    direct solvers cannot factor this size in a test's time, so x itself is
+    not compared).  Peak device memory stays under 180 GB."""
+    _need_gpu()
+    w = W.make(5)
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    s = d3m.Solver.from_workload(w, precision=d3m.MIXED)
+    s.factor()
+    f = s.rhs_planewave(w.khat_pol6())
+    rhs = torch.tensor(f.T.copy(), device="cuda").t()
+    x, info = s.solve(rhs)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 < 180e9
+    assert info["max_resid"] < 1e-10 and len(info["resid"]) == 128
+    cols = [0, 127]
+    xs = x[:, cols].cpu().numpy()
+    del x, rhs
+    s.close()
+    fo = fem.rhs_planewave(w, which=cols)
+    assert np.abs(f[:, cols] - fo).max() < 1e-12 * np.abs(fo).max()
+    assert fem.rel_residual(w, xs, fo).max() < 1e-10
+
+
 @pytest.mark.parametrize("wk", [1, 3])
 def test_tensor_core_update_matches_fp32_fma(wk):
-    """The tcgen05 3xTF32 trailing update against the fp32-FMA update: every
-    front of a mixed factorisation agrees to fp32 rounding, and both solve."""
+    """The deferred tcgen05 products (BF16x3 split operands, update rows through
+    the explicit L11^{-1}) against the right-looking fp32-FMA updates: the
+    fronts of the two mixed factorisations agree to fp32 rounding amplified
+    by the fronts' conditioning (5e-4 relative), and both solve."""
     _need_gpu()
     w = W.make(wk)
     solvers = []
@@ -264,7 +335,7 @@ def test_tensor_core_update_matches_fp32_fma(wk):
             continue  # a near-tie pivot may differ; the solve check below covers it
         La, Lb = np.tril(Fa), np.tril(Fb)
         worst = max(worst, np.abs(La - Lb).max() / max(np.abs(Lb).max(), 1e-30))
-    assert worst < 1e-4
+    assert worst < 5e-4
     f = fem.rhs_planewave(w)
     x, info = solvers[0].solve(torch.tensor(f.T.copy(), device="cuda").t())
     assert info["max_resid"] < 1e-10
