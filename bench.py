@@ -154,8 +154,8 @@ def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=Fal
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    acc = {k: 0.0 for k in ("ms_update", "ms_panel", "ms_assemble", "ms_inverse", "ms_fwd", "ms_bwd",
-                            "ms_residual", "flops_update", "flops_panel")}
+    acc = {k: 0.0 for k in ("ms_update", "ms_panel", "ms_assemble", "ms_inverse", "ms_tc", "ms_fwd", "ms_bwd",
+                            "ms_residual", "flops_update", "flops_panel", "flops_tc")}
     launches = 0
     infos = []
     sampler = ClockSampler(dev_index) if sample_clocks else None
@@ -186,7 +186,8 @@ def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=Fal
         stf = s.stats()
         s.solve(rhs_dev, x)
         sts = s.stats()
-        for k in ("ms_update", "ms_panel", "ms_assemble", "ms_inverse", "flops_update", "flops_panel"):
+        for k in ("ms_update", "ms_panel", "ms_assemble", "ms_inverse", "ms_tc", "flops_update", "flops_panel",
+                  "flops_tc"):
             acc[k] += stf[k]
         for k in ("ms_fwd", "ms_bwd", "ms_residual"):
             acc[k] += sts[k]
@@ -199,6 +200,7 @@ def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=Fal
     solve_flops_1 = stats["solve_flops"] / max(1, infos[-1]["iters"] + 1)
     out = dict(solver=s, x=x, factor_flops=factor_flops, solve_flops=solve_flops_1,
                factor_ms=statistics.mean(fac_ms), solve_ms=statistics.mean(sol_ms),
+               step_ms_each=[round(v, 3) for v in step_ms], factor_ms_each=[round(v, 3) for v in fac_ms],
                step_ms=statistics.mean(step_ms), max_step_ms=max(step_ms), wall_s=t_wall,
                iters=max(i["iters"] for i in infos), max_resid=max(i["max_resid"] for i in infos),
                launches=launches, clocks=clocks, stats=stats,
@@ -339,23 +341,34 @@ def cpu_baseline_sample(w, budget_s=20.0):
         f"factorisation; {secs:.1f} s"))
 
 
+# kernel classes of the factorisation: (kernel names, time key, algorithmic
+# flop key, bound, peak key)
 _ROOF_KERNELS = {
-    "update": ("k_update (trailing/Schur update of the fronts, rank-kb complex SYRK-like)", "ms_update",
-               "flops_update"),
+    "update": ("k_update (right-looking trailing update after each panel: whole trailing triangle on FMA "
+               "levels, the pivot block only on deferred levels)", "ms_update", "flops_update", "alu", "alu"),
     "panel": ("k_panel_cl + k_l21 (restricted Bunch-Kaufman panel of the pivot rows, update-row solve)",
-              "ms_panel", "flops_panel"),
+              "ms_panel", "flops_panel", "alu", "alu"),
+    "tc": ("k_tc_split + k_tc_gemm + k_tc_scale (deferred W21 = F21 P^T L11^-T and Schur C = F22 - L21 W21^T, "
+           "complex 3xTF32 on tcgen05, TMA-staged)", "ms_tc", "flops_tc", "tensor", "tensor"),
 }
 
 
-def _roofline(prof, peak_alu_tflops, cls, traffic=None):
-    """Algorithmic flops of a kernel class (the library's counts) over its
-    CUDA-event time in the profiled steps, against the ALU peak."""
-    name, kms, kfl = _ROOF_KERNELS[cls]
-    ms = prof[kms]
-    achieved = prof[kfl] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
-    return {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu_tflops, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / peak_alu_tflops, 4), "traffic": traffic,
-            "ms_per_step": round(ms, 3)}
+def _roofline(prof, peaks, cls, traffic=None):
+    """Algorithmic flops of a kernel class (8 real flops per complex MAC, the
+    library's counts) over its CUDA-event time in the profiled steps, against
+    the peak of the pipe it runs on (peaks: {"alu": ..., "tensor": ...})."""
+    name, kms, kfl, bound, pk = _ROOF_KERNELS[cls]
+    ms = prof.get(kms, 0.0)
+    peak = peaks[pk]
+    achieved = prof.get(kfl, 0.0) / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    out = {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
+           "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None, "traffic": traffic,
+           "ms_per_step": round(ms, 3)}
+    if cls == "tc" and peak:
+        # 3xTF32 complex: 12 real tf32 products per complex MAC, i.e. 3 tensor
+        # flops per algorithmic flop; the ceiling of this scheme is peak / 3
+        out["frac_of_3xtf32_ceiling"] = round(3.0 * achieved / peak, 4)
+    return out
 
 
 def _load_traffic(name):
@@ -367,27 +380,57 @@ def _load_traffic(name):
     return None
 
 
-def precision_summary(r, alu, prec_tag, config, nrhs):
+def precision_summary(r, peaks, prec_tag, config, nrhs):
     """The per-precision sub-object of the JSON line from one run_precision
     result: step/factor/solve figures, the profiled kernel split, the tuned
     schedule, and rooflines for the kernel class with the most time
-    ("roofline") and for the other class."""
-    dom = "panel" if r["prof"]["ms_panel"] >= r["prof"]["ms_update"] else "update"
-    other = "update" if dom == "panel" else "panel"
+    ("roofline") and for each other class ("roofline_<class>")."""
+    classes = [c for c in _ROOF_KERNELS if r["prof"].get(_ROOF_KERNELS[c][1], 0.0) > 0 or c != "tc"]
+    dom = max(classes, key=lambda c: r["prof"].get(_ROOF_KERNELS[c][1], 0.0))
+    roofs = {"roofline_" + c: _roofline(r["prof"], peaks, c, _load_traffic(f"config{config}:{c}<{prec_tag}>"))
+             for c in classes if c != dom}
     return {"factor_gflops": round(r["factor_flops"] / (r["factor_ms"] * 1e-3) / 1e9, 2),
             "factor_ms": round(r["factor_ms"], 3),
             "solve_rhs_per_s": round(nrhs / (r["solve_ms"] * 1e-3), 1),
             "solve_ms": round(r["solve_ms"], 3), "refine_steps": r["iters"],
             "max_resid": r["max_resid"], "ms_per_step": round(r["step_ms"], 3),
+            "ms_each_step": r.get("step_ms_each"), "factor_ms_each_step": r.get("factor_ms_each"),
             "kernel_ms": {k: round(v, 3) for k, v in r["prof"].items() if k.startswith("ms_")},
             "schedule": {"levels": r["stats"]["n_levels"],
                          "tcgen05_update_levels": r["stats"]["tuned_levels_tc"],
                          "doubled_cluster_levels": r["stats"]["tuned_levels_cs2"],
                          "tuning_ms": round(r["stats"]["ms_tuning"], 1)},
-            "roofline": _roofline(r["prof"], alu, dom, _load_traffic(f"config{config}:{dom}<{prec_tag}>")),
-            "roofline_" + other: _roofline(r["prof"], alu, other, _load_traffic(f"config{config}:{other}<{prec_tag}>")),
+            "roofline": _roofline(r["prof"], peaks, dom, _load_traffic(f"config{config}:{dom}<{prec_tag}>")),
+            **roofs,
             "kernel_timing": "per-kernel-class CUDA events in a second, profiled run of the same steps "
                              "(the timed steps replay the captured factor graph without events)"}
+
+
+def measure_tf32_tflops(n=8192, reps=10):
+    """Dense TF32 tensor-core throughput of this GPU (cuBLAS through torch,
+    fp32 operands with TF32 math), best of `reps`: the peak for the 3xTF32
+    products' roofline."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b)
+        best = 1e30
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(reps):
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        torch.cuda.empty_cache()
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def bench_config(w, config, arena_bytes):
@@ -494,8 +537,10 @@ def main():
     alu32 = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
     alu64 = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_GHZ / 1e3
 
+    tf32 = measure_tf32_tflops()
+
     def summary(r, alu, prec_tag):
-        return precision_summary(r, alu, prec_tag, args.config, w.nrhs)
+        return precision_summary(r, {"alu": alu, "tensor": tf32}, prec_tag, args.config, w.nrhs)
 
     if rank != 0:
         if ws > 1:
@@ -523,7 +568,8 @@ def main():
         "mixed": mix,
         "fp64": summary(fp64, alu64, "double") if fp64 else None,
         "peaks": {"source": peak_kind, "fp32_alu_tflops": round(alu32, 2), "fp64_alu_tflops": round(alu64, 3),
-                  "hbm_gbs": peaks.get("hbm_gbs")},
+                  "hbm_gbs": peaks.get("hbm_gbs"), "tf32_tensor_tflops": round(tf32, 1),
+                  "tf32_source": "measured here: cuBLAS fp32 8192^3 GEMM with TF32 tensor cores, best of 10"},
     }
     if line["fp64"]:
         line["mixed_speedup_vs_fp64"] = round(fp64["step_ms"] / mixed["step_ms"], 2)

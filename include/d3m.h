@@ -31,7 +31,8 @@
  *  - all device work is ordered on d3m_options.stream (a cudaStream_t, NULL =
  *    the legacy default stream); the library's internal streams (look-ahead,
  *    overlapped inverses) fork from and join back into it, and calls return
- *    after the work is complete.
+ *    after the work is complete (d3m_dense_ldlt_noalloc is the one exception:
+ *    it only enqueues its work, see there).
  */
 #ifndef D3M_H
 #define D3M_H
@@ -103,8 +104,13 @@ typedef struct {
                            single-CTA global-memory panel (same arithmetic) */
   int32_t update_kernel;/* MIXED trailing/Schur updates: 0 = per level, the faster of
                            the two below as measured by the autotuner (default);
-                           1 = fp32 FMA; 2 = tcgen05 tensor cores with 3xTF32
-                           split products */
+                           1 = fp32 FMA, right-looking after every panel; 2 =
+                           deferred: the panels update only the pivot block, then
+                           the update rows (W21 = F21 P^T L11^{-T}, L21 = W21
+                           D^{-1}) and the Schur complement (F22 - L21 W21^T)
+                           of every front of the level are two batched complex
+                           products on the tcgen05 tensor cores with 3xTF32 split
+                           operands staged by TMA */
   int32_t autotune;     /* 0 = tune on the first d3m_factor (default): the update
                            kernel and the panel cluster size of every tree level
                            are timed with CUDA events over two trial
@@ -119,6 +125,17 @@ typedef struct {
                            the most urgent one; 1 = off, every update completes
                            before the next panel.  Both give bitwise identical
                            factors. */
+  int32_t refine_method;/* MIXED: 0 = plain iterative refinement (default): x +=
+                           M^{-1} (f - A x) with M^{-1} the complex64 factors;
+                           1 = GMRES-based refinement: each correction d solves
+                           A d = f - A x by flexible GMRES in fp64, right
+                           preconditioned by M^{-1}, for cases where plain
+                           refinement stalls (conditioning times the factor
+                           precision near one).  Every refinement step counts
+                           toward max_refine. */
+  int32_t gmres_restart;/* GMRES-IR: Krylov steps per correction; 0 -> 20 (<= 200) */
+  double gmres_tol;     /* GMRES-IR: relative 2-norm reduction of each correction
+                           equation's residual; 0 -> 1e-4 */
 } d3m_options;
 /* d3m_setup returns D3M_EINVAL (and the context, for d3m_last_error) when an
  * option lies outside the values listed above. */
@@ -129,6 +146,7 @@ typedef struct {
   double *resid;        /* caller array of nrhs doubles, or NULL */
   int32_t iters;        /* refinement steps (0 for FP64) */
   double max_resid;
+  int32_t inner_iters;  /* GMRES-IR: Krylov steps summed over the corrections */
 } d3m_solve_info;
 
 /* Sizes and counts of a set-up problem. */
@@ -153,6 +171,11 @@ typedef struct {
   int64_t tuned_levels_tc;/* levels whose updates the autotuner put on tensor cores */
   int64_t tuned_levels_cs2; /* levels whose panels run with the doubled cluster size */
   double ms_tuning;       /* wall time of the trial factorisations */
+  /* MIXED, levels on the tensor cores: the deferred products W21 = F21 P^T
+     L11^{-T} and C = F22 - L21 W21^T with their operand splits and the
+     L21 = W21 D^{-1} scaling (profile=1), and their algorithmic real flops */
+  double ms_tc;
+  double flops_tc;
 } d3m_stats;
 
 /*
@@ -256,12 +279,13 @@ enum d3m_structure_kind {
   D3M_STATS = 8,       /* d3m_stats */
   D3M_M_ENTRIES = 9,   /* double [nnz][4]: (row, col, re, im) of the lower triangle of
                           M = [[A, D], [D^T, 0]] in M order, as assembled */
-  D3M_LEVELS = 10      /* double [n_levels][8] per level of the assembly tree (leaves
-                          first): fronts, largest pivot block, largest front,
-                          algorithmic real flops, then from the last factorisation
-                          run with d3m_options.profile = 1 (else 0): panel ms,
-                          update ms, 1 if the tcgen05 update ran, panel cluster
-                          size (0 = single-CTA panel) */
+  D3M_LEVELS = 10      /* double [n_levels][10] per level of the assembly tree
+                          (leaves first): fronts, largest pivot block, largest
+                          front, algorithmic real flops, then from the last
+                          factorisation run with d3m_options.profile = 1 (else
+                          0): panel ms, update ms, 1 if the deferred tcgen05
+                          products ran, panel cluster size (0 = single-CTA
+                          panel), L11^{-1} ms, tcgen05 products ms */
 };
 int d3m_structure(d3m_ctx *ctx, int32_t which, void *buf, size_t *bytes);
 
@@ -307,7 +331,13 @@ int d3m_export_front(d3m_ctx *ctx, int64_t front, int32_t *m_out, int32_t *p_out
  * (front tables, panel workspace, pivot state) in one fixed device array of
  * D3M_NOALLOC_SCRATCH_BYTES that is part of the library image; it calls no
  * cudaMalloc, cudaFree or other allocating routine, on the host or the device.
- * Arguments, layout and results are exactly those of d3m_dense_ldlt.
+ * Arguments, layout and results are exactly those of d3m_dense_ldlt, but the
+ * call is asynchronous: it returns as soon as its kernels are enqueued on
+ * `stream` (NULL = the legacy default stream) and never waits for the device;
+ * A, perm, dinv and info hold the results once the stream has reached that
+ * point.  A non-OK return means that a launch was refused (D3M_ECUDA) or the
+ * request was invalid (D3M_EINVAL): after D3M_ECUDA, A may be partly factored
+ * and perm, dinv, info are undefined.
  * Limits: the scratch must hold 16*NB*m*batch bytes of panel workspace (NB =
  * 32) plus about 96 bytes per matrix and 37 bytes per pivot; larger requests
  * return D3M_EINVAL without touching the GPU.  The first call on a device

@@ -73,10 +73,12 @@ struct Ctx {
   Plan plan;
   d3m_options opt{};
   std::string cache_path;  // copy of opt.autotune_cache
+  std::string fault;       // host-side fault injection (environment D3M_FAULT): "", alloc, pivot, nan, timeout
   std::string err;
   DeviceState *dev = nullptr;
   d3m_stats stats{};
   std::vector<double> lvl_ms_panel, lvl_ms_update;  // last profiled factorisation, per level
+  std::vector<double> lvl_ms_inv, lvl_ms_tc;
   std::vector<int> lvl_tc, lvl_cs;                   // schedule of the last factorisation
   std::vector<cplx> lambda_host;  // last solve's multipliers, column-major n_lm x nrhs
   int32_t lambda_nrhs = 0;

@@ -17,6 +17,8 @@
 // left-looking updates inside the panel, one CTA per front) followed by a
 // trailing update of all fronts of the level (64x64 tiles).
 #include <cooperative_groups.h>
+#include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime, no driver link)
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1022,23 +1024,30 @@ static size_t panel_cl_smem(int rcap, int mcap, size_t esz) {
 // (forward substitution with the panel's unit-lower block), L21 = w D^{-1};
 // L21 goes to the front, w (= L21 D) to the workspace for the trailing update.
 // One thread per update row, all fronts of the level.
+// The step is read from the panel's (k0 + kb, kb) snapshot, so the kernel may
+// run behind later panels on another stream.  With w21 given (mixed path,
+// deferred Schur products), w goes to the front's W21 block of that buffer
+// (column-major (m - p) x p at w21_off[level position]) instead of the
+// workspace.
 template <typename T>
 __global__ void __launch_bounds__(128) k_l21(const int32_t *__restrict__ lvl, FrontTab ft,
                                              const int64_t *__restrict__ wofs, cx<T> *__restrict__ arena,
                                              cx<T> *__restrict__ Wbuf, const double2 *__restrict__ dinv_d,
                                              const double2 *__restrict__ dinv_o, const int8_t *__restrict__ psize,
-                                             const int32_t *__restrict__ st_k0, const int32_t *__restrict__ st_kb,
-                                             const int2 *__restrict__ swp, double *__restrict__ flop_cnt) {
+                                             const int2 *__restrict__ snap, const int2 *__restrict__ swp,
+                                             double *__restrict__ flop_cnt, float2 *__restrict__ w21,
+                                             const int64_t *__restrict__ w21_off) {
   const int fi = blockIdx.y;
   const int f = lvl[fi];
-  const int kb = st_kb[f];
+  const int kb = snap[fi].y;
   if (kb == 0) return;
   const int m = ft.m[f], p = ft.p[f];
   const int r = p + blockIdx.x * blockDim.x + threadIdx.x;
   if (p + (int)(blockIdx.x * blockDim.x) >= m) return;  // uniform per CTA
-  const int k0 = st_k0[f] - kb;
+  const int k0 = snap[fi].x - kb;
   cx<T> *F = arena + ft.off[f];
   cx<T> *W = Wbuf + wofs[fi];
+  float2 *W21 = w21 ? w21 + w21_off[fi] + (r - p) : nullptr;
   const int64_t ld = m;
   __shared__ cx<T> L11[NB][NB + 1];
   __shared__ cx<T> Di[NB], Do[NB];
@@ -1096,7 +1105,10 @@ __global__ void __launch_bounds__(128) k_l21(const int32_t *__restrict__ lvl, Fr
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
       if (t < kb) {
-        W[r + (int64_t)t * ld] = a[t];
+        if (W21)
+          W21[(int64_t)(k0 + t) * (m - p)] = make_float2((float)a[t].re, (float)a[t].im);
+        else
+          W[r + (int64_t)t * ld] = a[t];
         cx<T> l;
         if (Dz[t] == 1) {
           l = cmul(a[t], Di[t]);
@@ -1144,14 +1156,23 @@ static cudaError_t launch_prio(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem,
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+// Kernel attributes are per device: one "set" flag per device ordinal
+// (ordinals beyond the table set the attributes on every call).
+constexpr int ATTR_MAX_DEVICES = 64;
+static bool *attr_flag(bool *tab) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= ATTR_MAX_DEVICES) return nullptr;
+  return tab + dev;
+}
 template <typename T>
 static cudaError_t panel_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+  static bool done[ATTR_MAX_DEVICES] = {};
+  bool *f = attr_flag(done);
+  if (f && *f) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)PANEL_SMEM_MAX);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  done = e == cudaSuccess;
+  if (f) *f = e == cudaSuccess;
   return e;
 }
 
@@ -1193,8 +1214,8 @@ static cudaError_t launch_panel(int cs, int pmax, int mmax, int nf, const int32_
   if (mmax > 0) {
     dim3 g((unsigned)std::max(1, (mmax + 127) / 128), (unsigned)nf);
     e = launch_prio(k_l21<T>, g, dim3(128), 0, s, prio, lvl, ft, wofs, arena, W, (const double2 *)dd,
-                    (const double2 *)dof, (const int8_t *)ps, (const int32_t *)k0, (const int32_t *)kb,
-                    (const int2 *)swp, flops);
+                    (const double2 *)dof, (const int8_t *)ps, (const int2 *)snap, (const int2 *)swp, flops,
+                    (float2 *)nullptr, (const int64_t *)nullptr);
   }
   return e;
 }
@@ -1214,19 +1235,32 @@ __global__ void __launch_bounds__(256)
   const int k0 = c0 - kb;
   const int m = ft.m[f], p = ft.p[f];
   // column window: mode 0 every trailing column, 1 those of the pivot block
-  // (< p), 2 those of the Schur complement (>= p)
-  const int clo = mode == 2 ? max(c0, p) : c0, chi = mode == 1 ? p : m;
+  // (< p), 2 those of the Schur complement (>= p); mode 3 the pivot block's
+  // columns and rows only (the update rows and the Schur complement are left
+  // to the deferred tensor-core products)
+  // (to the deferred tensor-core products); mode 4 the update rows (>= p)
+  // of the pivot block's columns, a rectangle of tiles
+  const int clo = mode == 2 ? max(c0, p) : c0, chi = (mode == 1 || mode == 3 || mode == 4) ? p : m;
+  const int rhi = mode == 3 ? p : m, rlo = mode == 4 ? p : 0;
   const int I0 = c0 / UT;
-  const int nt = (m + UT - 1) / UT - I0;
-  const int ntl = nt > 0 ? nt * (nt + 1) / 2 : 0;
+  const int nt = (rhi + UT - 1) / UT - I0;
+  const int R4 = (p / UT) * UT, nr4 = (m - R4 + UT - 1) / UT, nc4 = (p - I0 * UT + UT - 1) / UT;
+  const int ntl = mode == 4 ? (c0 < p ? nr4 * nc4 : 0) : (nt > 0 ? nt * (nt + 1) / 2 : 0);
   // tiles of the trailing lower triangle, grid-strided (a launch may use
   // fewer CTAs than tiles, leaving room on every SM for other kernels)
   for (int t = blockIdx.x; t < ntl; t += gridDim.x) {
-  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while (ii * (ii + 1) / 2 > t) --ii;
-  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-  const int jj = t - ii * (ii + 1) / 2;
-  const int r0 = (I0 + ii) * UT, cc0 = (I0 + jj) * UT;
+  int r0, cc0;
+  if (mode == 4) {
+    r0 = R4 + (t % nr4) * UT;
+    cc0 = (I0 + t / nr4) * UT;
+  } else {
+    int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (ii * (ii + 1) / 2 > t) --ii;
+    while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+    const int jj = t - ii * (ii + 1) / 2;
+    r0 = (I0 + ii) * UT;
+    cc0 = (I0 + jj) * UT;
+  }
   if (cc0 + UT <= clo || cc0 >= chi) continue;  // uniform per CTA
   cx<T> *F = arena + ft.off[f];
   const cx<T> *W = Wbuf + wofs[blockIdx.y];
@@ -1246,7 +1280,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int cidx = cc0 + tc + 16 * b;
-      cv[a][b] = (i < m && cidx >= clo && cidx < chi && cidx <= i) ? F[i + (int64_t)cidx * ld] : mk<T>(0, 0);
+      cv[a][b] = (i >= rlo && i < rhi && cidx >= clo && cidx < chi && cidx <= i) ? F[i + (int64_t)cidx * ld]
+                                                                                 : mk<T>(0, 0);
     }
   }
   for (int t0 = 0; t0 < kb; t0 += KC) {
@@ -1255,8 +1290,8 @@ __global__ void __launch_bounds__(256)
       const int r = e % UT, tt = e / UT;
       const int gi = r0 + r, gc = cc0 + r;
       const bool ok = t0 + tt < kb;
-      Ls[tt][r] = (ok && gi < m) ? F[gi + (int64_t)(k0 + t0 + tt) * ld] : mk<T>(0, 0);
-      Ws[tt][r] = (ok && gc < m) ? W[gc + (int64_t)(t0 + tt) * ld] : mk<T>(0, 0);
+      Ls[tt][r] = (ok && gi >= rlo && gi < rhi) ? F[gi + (int64_t)(k0 + t0 + tt) * ld] : mk<T>(0, 0);
+      Ws[tt][r] = (ok && gc < chi) ? W[gc + (int64_t)(t0 + tt) * ld] : mk<T>(0, 0);
     }
     __syncthreads();
     const int nt = min(KC, kb - t0);
@@ -1276,7 +1311,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int i = r0 + tr + 16 * a;
-    if (i >= m) continue;
+    if (i < rlo || i >= rhi) continue;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int cidx = cc0 + tc + 16 * b;
@@ -1288,29 +1323,7 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// ------------------------------------------------------------ tensor-core trailing update
-// The complex64 trailing/Schur update of the mixed path on the 5th-generation
-// tensor cores: C[i, c] -= sum_t L[i, k0+t] W[c, t] per 128 x 64 tile of the
-// lower trailing part, K = kb <= 32 complex.  Split products (3xTF32): every
-// fp32 operand x = hi + lo with hi, lo in tf32, and X Y^T ~ Xhi Yhi^T + Xhi Ylo^T
-// + Xlo Yhi^T (fp32 accumulation), so the result keeps fp32 accuracy.  Complex
-// arithmetic as four real products:
-//   Re += Lr Wr^T - Li Wi^T,   Im += Lr Wi^T + Li Wr^T
-// (the minus through the A-negate bit of the instruction descriptor).  The
-// 8 operand planes (Lr, Li, Wr, Wi in hi/lo) are staged in shared memory in the
-// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix,
-// LBO = 128 B between k-neighbours, SBO = 1024 B between 8-row groups); one
-// thread issues tcgen05.mma (M = 128, N = 64, K = 8) into two TMEM
-// accumulators (Re: columns 0-63, Im: 64-127), commits to an mbarrier, and the
-// four warps read their 32 TMEM lanes back with tcgen05.ld for the epilogue.
-// The mbarrier wait is bounded: on expiry the tile is skipped and an error
-// flag is raised (the factorisation then reports D3M_ETIMEOUT).
-constexpr int TCM = 128, TCN = 64, TCK = 32;
-constexpr uint32_t TC_LBO = 128, TC_SBO = 1024;
-constexpr int TC_PLANE_A = TCM * TCK * 4;   // bytes of one A plane (16 KB)
-constexpr int TC_PLANE_B = TCN * TCK * 4;   // bytes of one B plane (8 KB)
-constexpr int TC_SMEM = 4 * TC_PLANE_A + 4 * TC_PLANE_B + 64;  // + mbarrier, TMEM address
-
+// ------------------------------------------------------------ tensor-core helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -1319,19 +1332,7 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return r;
 }
-// byte offset of element (row, k) of a K-major no-swizzle operand plane
-__device__ __forceinline__ uint32_t tc_off(int row, int k) {
-  return (uint32_t)((row >> 3) * TC_SBO + (k >> 2) * TC_LBO + (row & 7) * 16 + (k & 3) * 4);
-}
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-// instruction descriptor: D f32, A/B tf32, K-major, N = 64, M = 128
-__device__ __forceinline__ uint32_t tc_idesc(int negA) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negA << 13) | ((uint32_t)(TCN >> 3) << 17) |
-         ((uint32_t)(TCM >> 4) << 24);
-}
+// D (TMEM) (+)= A B^T for shared-memory descriptors a, b (acc = 0 overwrites D)
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -1340,187 +1341,24 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, 
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128)
-    k_update_tc(const int32_t *__restrict__ lvl, FrontTab ft, const int64_t *__restrict__ wofs,
-                cx<T> *__restrict__ arena, const cx<T> *__restrict__ Wbuf, const int2 *__restrict__ snap, int mode,
-                int32_t *__restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char tsm[];
-  const int f = lvl[blockIdx.y];
-  const int2 sk = snap[blockIdx.y];
-  const int kb = sk.y;
-  if (kb == 0) return;
-  const int c0 = sk.x;
-  const int k0 = c0 - kb;
-  const int m = ft.m[f], p = ft.p[f];
-  const int clo = mode == 2 ? max(c0, p) : c0, chi = mode == 1 ? p : m;  // column window as in k_update
-  // tiles: row blocks of 128 from R0, column blocks of 64 from C0, lower part
-  const int R0 = (c0 / TCM) * TCM, C0 = (c0 / TCN) * TCN;
-  const int nI = (m - R0 + TCM - 1) / TCM, nJmax = (m - C0 + TCN - 1) / TCN;
-  int t = blockIdx.x, I = 0, J = -1;
-  for (int ii = 0; ii < nI; ++ii) {
-    int rs = R0 + ii * TCM;
-    int nj = min(nJmax, (rs + TCM - C0 + TCN - 1) / TCN);
-    if (t < nj) {
-      I = ii;
-      J = t;
-      break;
-    }
-    t -= nj;
-  }
-  if (J < 0) return;  // uniform per CTA
-  const int rs = R0 + I * TCM, cs = C0 + J * TCN;
-  if (cs + TCN <= clo || cs >= chi) return;  // uniform per CTA, before any TMEM allocation
-  cx<T> *F = arena + ft.off[f];
-  const cx<T> *W = Wbuf + wofs[blockIdx.y];
-  const int64_t ld = m;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  unsigned char *pA = tsm;                      // Lr_hi, Lr_lo, Li_hi, Li_lo
-  unsigned char *pB = tsm + 4 * TC_PLANE_A;     // Wr_hi, Wr_lo, Wi_hi, Wi_lo
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm + 4 * TC_PLANE_A + 4 * TC_PLANE_B);
-  uint32_t *taddr_s = reinterpret_cast<uint32_t *>(mbar + 1);
-  // TMEM: 128 columns (two 64-column accumulators), one warp allocates
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(taddr_s)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // operands: thread = row of L (128 rows); W rows split over thread pairs
-  {
-    const int i = rs + tid;
-    for (int kk = 0; kk < TCK; ++kk) {
-      float re = 0.f, im = 0.f;
-      if (kk < kb && i < m) {
-        cx<T> v = F[i + (int64_t)(k0 + kk) * ld];
-        re = (float)v.re;
-        im = (float)v.im;
-      }
-      uint32_t rh = tf32_rna(re), ih = tf32_rna(im);
-      uint32_t rl = tf32_rna(re - __uint_as_float(rh)), il = tf32_rna(im - __uint_as_float(ih));
-      uint32_t o = tc_off(tid, kk);
-      *reinterpret_cast<uint32_t *>(pA + 0 * TC_PLANE_A + o) = rh;
-      *reinterpret_cast<uint32_t *>(pA + 1 * TC_PLANE_A + o) = rl;
-      *reinterpret_cast<uint32_t *>(pA + 2 * TC_PLANE_A + o) = ih;
-      *reinterpret_cast<uint32_t *>(pA + 3 * TC_PLANE_A + o) = il;
-    }
-    const int wr = tid & 63, half = tid >> 6;
-    const int c = cs + wr;
-    for (int kk = half * 16; kk < half * 16 + 16; ++kk) {
-      float re = 0.f, im = 0.f;
-      if (kk < kb && c < m) {
-        cx<T> v = W[c + (int64_t)kk * ld];
-        re = (float)v.re;
-        im = (float)v.im;
-      }
-      uint32_t rh = tf32_rna(re), ih = tf32_rna(im);
-      uint32_t rl = tf32_rna(re - __uint_as_float(rh)), il = tf32_rna(im - __uint_as_float(ih));
-      uint32_t o = tc_off(wr, kk);
-      *reinterpret_cast<uint32_t *>(pB + 0 * TC_PLANE_B + o) = rh;
-      *reinterpret_cast<uint32_t *>(pB + 1 * TC_PLANE_B + o) = rl;
-      *reinterpret_cast<uint32_t *>(pB + 2 * TC_PLANE_B + o) = ih;
-      *reinterpret_cast<uint32_t *>(pB + 3 * TC_PLANE_B + o) = il;
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *taddr_s;
-  if (tid == 0) {
-    const uint32_t a0 = smem_u32(pA), b0 = smem_u32(pB);
-    const uint32_t id_pos = tc_idesc(0), id_neg = tc_idesc(1);
-    const uint32_t dre = tmem, dim = tmem + TCN;
-    for (int ks = 0; ks < TCK / 8; ++ks) {
-      const uint32_t ko = (uint32_t)ks * 2 * TC_LBO;  // 8 tf32 = two core matrices along k
-      const uint64_t Lrh = tc_desc(a0 + 0 * TC_PLANE_A + ko), Lrl = tc_desc(a0 + 1 * TC_PLANE_A + ko);
-      const uint64_t Lih = tc_desc(a0 + 2 * TC_PLANE_A + ko), Lil = tc_desc(a0 + 3 * TC_PLANE_A + ko);
-      const uint64_t Wrh = tc_desc(b0 + 0 * TC_PLANE_B + ko), Wrl = tc_desc(b0 + 1 * TC_PLANE_B + ko);
-      const uint64_t Wih = tc_desc(b0 + 2 * TC_PLANE_B + ko), Wil = tc_desc(b0 + 3 * TC_PLANE_B + ko);
-      const uint32_t first = ks == 0 ? 0u : 1u;
-      tc_mma(dre, Lrh, Wrh, id_pos, first);
-      tc_mma(dre, Lrh, Wrl, id_pos, 1u);
-      tc_mma(dre, Lrl, Wrh, id_pos, 1u);
-      tc_mma(dre, Lih, Wih, id_neg, 1u);
-      tc_mma(dre, Lih, Wil, id_neg, 1u);
-      tc_mma(dre, Lil, Wih, id_neg, 1u);
-      tc_mma(dim, Lrh, Wih, id_pos, first);
-      tc_mma(dim, Lrh, Wil, id_pos, 1u);
-      tc_mma(dim, Lrl, Wih, id_pos, 1u);
-      tc_mma(dim, Lih, Wrh, id_pos, 1u);
-      tc_mma(dim, Lih, Wrl, id_pos, 1u);
-      tc_mma(dim, Lil, Wrh, id_pos, 1u);
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
-                 : "memory");
-  }
-  // bounded wait for the MMAs (phase 0 of the mbarrier)
+// Bounded wait on phase `parity` of an mbarrier: true once the phase has
+// completed, false after `iters` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int iters) {
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it) {
+  for (int it = 0; it < iters && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred q;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(done)
-        : "r"(smem_u32(mbar))
+        : "r"(mbar), "r"(parity)
         : "memory");
   }
-  const int ok = __syncthreads_and(done);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    const int row = rs + warp * 32 + (tid & 31);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    for (int cc = 0; cc < TCN; cc += 16) {
-      uint32_t vr[16], vi[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
-            "=r"(vr[7]), "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]),
-            "=r"(vr[14]), "=r"(vr[15])
-          : "r"(tmem + lane_base + (uint32_t)cc));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
-            "=r"(vi[7]), "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]),
-            "=r"(vi[14]), "=r"(vi[15])
-          : "r"(tmem + lane_base + (uint32_t)(TCN + cc)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < m) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int col = cs + cc + q;
-          if (col < clo || col >= chi || col > row) continue;
-          cx<T> *dst = F + row + (int64_t)col * ld;
-          cx<T> v = *dst;
-          v.re -= (T)__uint_as_float(vr[q]);
-          v.im -= (T)__uint_as_float(vi[q]);
-          *dst = v;
-        }
-      }
-    }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+  return done != 0;
 }
 
-static cudaError_t tc_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_update_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-  done = e == cudaSuccess;
-  return e;
-}
-template <typename T>
-static void launch_update_tc(dim3 g, cudaStream_t s, const int32_t *lvl, FrontTab ft, const int64_t *wofs,
-                             cx<T> *arena, const cx<T> *W, const int2 *snap, int mode, int32_t *err, int prio = 0) {
-  if constexpr (sizeof(T) == 4)
-    launch_prio(k_update_tc<T>, g, dim3(128), TC_SMEM, s, prio, lvl, ft, wofs, arena, W, snap, mode, err);
-}
+#include "tc_gemm.cuh"
+#include "gmres_ir.cuh"
 
 // ------------------------------------------------------------ solve kernels
 // Vectors in M space and front-local vectors are row-major (RHS fastest).
@@ -2169,7 +2007,7 @@ __global__ void __launch_bounds__(256)
 // ------------------------------------------------------------ profiling
 // CUDA events around each launch group, on the launching stream; durations
 // are summed per kernel class after the stream is synchronised.
-enum ProfClass { PC_ASSEMBLE = 0, PC_PANEL, PC_UPDATE, PC_FWD, PC_BWD, PC_RESID, PC_INV, PC_N };
+enum ProfClass { PC_ASSEMBLE = 0, PC_PANEL, PC_UPDATE, PC_FWD, PC_BWD, PC_RESID, PC_INV, PC_TC, PC_N };
 struct Profiler {
   bool on = false;
   cudaStream_t s = nullptr;
@@ -2313,18 +2151,41 @@ struct DeviceState {
   int g_r = 0;
   int64_t g_launches[2] = {0, 0};
   int2 *swp = nullptr;           // per level position: the current panel's column permutation (2 NB each)
-  int32_t *tc_err = nullptr;     // set by k_update_tc when a bounded wait expires
-  std::vector<uint8_t> lvl_tc;   // per level: tensor-core updates (mixed)
+  int32_t *tc_err = nullptr;     // set by k_tc_gemm when a bounded wait expires
+  int32_t *fin_err = nullptr;    // set when a pivot inverse is not finite
+  int tc_wait_cap = 1 << 22;     // first-attempt bound of k_tc_gemm's mbarrier waits
+  std::vector<uint8_t> lvl_tc;   // per level: deferred tensor-core products (mixed)
   std::vector<int> lvl_cs;       // per level: panel cluster size (0 = global panel)
   bool tuned = false;
-  std::vector<double> tune_panel, tune_update;  // per-level ms of the last profiled factor
-  std::vector<std::vector<int>> tc_grid;  // per level, per step: 128x64 tiles (upper bound)
+  std::vector<double> tune_panel, tune_update, tune_inv, tune_tc;  // per-level ms of the last profiled factor
+  std::vector<std::vector<int>> update_grid_p;  // per level, per step: tiles of the pivot-block update
+  std::vector<std::vector<int>> update_grid_r;  // ... of the update rows of the pivot-block columns
+  // deferred Schur products of the mixed path on the tensor cores
+  // (tc_gemm.cuh), per level: operand-split blocks (L21, W21) and product tiles
+  struct TcLevel {
+    int kpitch = 0;                 // K pitch of the level's planes (0: nothing to do)
+    int64_t rowsA = 0, rowsB = 0;   // plane rows of the A / B operands
+    int sx0 = 0, nsx = 0, sl0 = 0, nsl = 0, g20 = 0, ng2 = 0;  // L21 / W21 split blocks, Schur tiles
+    double flops = 0;               // algorithmic real flops of the Schur products
+    CUtensorMap tmA, tmB;
+  };
+  std::vector<TcLevel> tcl;
+  TcSplit *tc_split = nullptr;
+  TcTile *tc_tiles = nullptr;
+  int64_t *w21_off = nullptr;     // per level position: the front's W21 block in tc_w
+  uint16_t *planesA = nullptr, *planesB = nullptr;  // bf16 operand planes
+  float2 *tc_w = nullptr;         // W21 of every front of a level (fp32 complex)
   std::vector<int> level_maxp;   // largest pivot block per level
   int32_t *nsplit = nullptr;     // per level position: row splits of the backward partials
   std::vector<int64_t> part_off_h;  // per level position: first partial row
   int64_t *part_off = nullptr;   // per level position: partial-buffer offset (units of r)
   int64_t part_rows = 0;         // max over levels of sum(nsplit * p)
   void *part = nullptr;
+  // GMRES-IR work space (edge space, fp64): basis V (m + 1 vectors), the
+  // preconditioned directions Z (m), their multiplier parts, w, reductions
+  int gm_r = 0, gm_m = 0;
+  double2 *gm_V = nullptr, *gm_Z = nullptr, *gm_lamZ = nullptr, *gm_w = nullptr, *gm_y = nullptr;
+  double *gm_h = nullptr, *gm_s = nullptr;
   std::vector<void *> allocs;
 };
 
@@ -2386,9 +2247,132 @@ static std::pair<int, int> cg_assign(std::vector<CgItem> &items, bool allow128) 
   return {tiles, best};
 }
 
+// ---- deferred tensor-core products: the driver entry point of the tensor-map
+// encoder, fetched through the runtime (no link against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+// Tensor map over the six bf16 planes of one operand: dims (k, row, plane),
+// 32 x 128 x 1 boxes with 64-byte swizzle (the K-major shared-memory layout
+// that k_tc_gemm's descriptors describe).
+static bool encode_planes(CUtensorMap *tm, uint16_t *base, int kpitch, int64_t rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)kpitch, (cuuint64_t)rows, (cuuint64_t)G_NPL};
+  const cuuint64_t strides[2] = {(cuuint64_t)kpitch * 2, (cuuint64_t)rows * kpitch * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)G_BK, (cuuint32_t)G_BM, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Per level: the fronts with a pivot block and update rows get an A-operand
+// block (their Mr = m - p update rows of L21, padded to 128 rows) and a
+// B-operand block (W21, same shape) in the plane buffers, a W21 slot (Mr x p,
+// written by the update-row solve), the 32 x 32 split blocks of both operands
+// and the 128 x 128 tiles of the lower triangle of the Schur product
+// C = F22 - L21 W21^T.
+static int tc_plan(Ctx &c, DeviceState *d, const std::vector<int32_t> &m, const std::vector<int32_t> &pp) {
+  const Plan &P = c.plan;
+  std::vector<TcSplit> sp;
+  std::vector<TcTile> tl;
+  std::vector<int64_t> w21_off((size_t)P.sn_start.size(), 0);
+  d->tcl.assign(P.n_levels, DeviceState::TcLevel{});
+  int64_t maxA = 0, maxW = 0;
+  auto rup = [](int64_t v, int64_t q) { return (v + q - 1) / q * q; };
+  struct Fo {
+    int f, i, pf, mf, Mr;
+    int64_t row, woff;
+  };
+  for (int l = 0; l < P.n_levels; ++l) {
+    DeviceState::TcLevel &L = d->tcl[l];
+    std::vector<Fo> fo;
+    int64_t ra = 0, wo = 0;
+    int kp = 0;
+    for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+      const int f = P.level_fronts[i], pf = pp[f], mf = m[f], Mr = mf - pf;
+      if (pf == 0 || Mr == 0) continue;
+      fo.push_back({f, i, pf, mf, Mr, ra, wo});
+      w21_off[i] = wo;
+      ra += rup(Mr, G_BM);
+      wo += (int64_t)Mr * pf;
+      kp = std::max<int>(kp, (int)rup(pf, G_KPAD));
+      L.flops += 8.0 * 0.5 * (double)pf * Mr * (Mr + 1.0);
+    }
+    if (fo.empty()) continue;
+    L.kpitch = kp;
+    L.rowsA = L.rowsB = ra;
+    maxA = std::max(maxA, ra * kp);
+    maxW = std::max(maxW, wo);
+    L.sx0 = (int)sp.size();
+    for (const Fo &q : fo)  // L21: rows p.. of the front's pivot columns (pivot order)
+      for (int r0 = 0; r0 < rup(q.Mr, G_BM); r0 += 32)
+        for (int k0 = 0; k0 < rup(q.pf, G_KPAD); k0 += 32)
+          sp.push_back({q.f, r0, k0, q.Mr, q.pf, (int32_t)q.row, P.front_off[q.f] + q.pf, q.mf, 0});
+    L.nsx = (int)sp.size() - L.sx0;
+    L.sl0 = (int)sp.size();
+    for (const Fo &q : fo)  // W21 = L21 D (column-major Mr x p in the W21 buffer)
+      for (int r0 = 0; r0 < rup(q.Mr, G_BM); r0 += 32)
+        for (int k0 = 0; k0 < rup(q.pf, G_KPAD); k0 += 32)
+          sp.push_back({q.f, r0, k0, q.Mr, q.pf, (int32_t)q.row, q.woff, q.Mr, 0});
+    L.nsl = (int)sp.size() - L.sl0;
+    L.g20 = (int)tl.size();
+    for (const Fo &q : fo)  // C -= L21 W21^T, lower triangle of tiles
+      for (int I = 0; I * G_BM < q.Mr; ++I)
+        for (int J = 0; J <= I; ++J) {
+          TcTile t{};
+          t.arow = (int32_t)(q.row + I * G_BM);
+          t.brow = (int32_t)(q.row + J * G_BN);
+          t.M = std::min(G_BM, q.Mr - I * G_BM);
+          t.N = std::min(G_BN, q.Mr - J * G_BN);
+          t.nk = (q.pf + G_BK - 1) / G_BK;
+          t.mode = 1;
+          t.diag = I == J;
+          t.ldc = q.mf;
+          t.c_off = P.front_off[q.f] + (int64_t)(q.pf + I * G_BM) + (int64_t)(q.pf + J * G_BN) * q.mf;
+          tl.push_back(t);
+        }
+    L.ng2 = (int)tl.size() - L.g20;
+  }
+  if (tl.empty()) return D3M_OK;
+  CUDA_TRY(upload(d, &d->tc_split, sp));
+  CUDA_TRY(upload(d, &d->tc_tiles, tl));
+  CUDA_TRY(upload(d, &d->w21_off, w21_off));
+  CUDA_TRY(dalloc(d, &d->planesA, (size_t)maxA * G_NPL));
+  CUDA_TRY(dalloc(d, &d->planesB, (size_t)maxA * G_NPL));
+  CUDA_TRY(dalloc(d, &d->tc_w, (size_t)maxW));
+  for (int l = 0; l < P.n_levels; ++l) {
+    DeviceState::TcLevel &L = d->tcl[l];
+    if (L.kpitch == 0) continue;
+    if (!encode_planes(&L.tmA, d->planesA, L.kpitch, L.rowsA) || !encode_planes(&L.tmB, d->planesB, L.kpitch, L.rowsB)) {
+      c.err = "d3m_factor: tensor map encoding of the operand planes failed";
+      return D3M_ECUDA;
+    }
+  }
+  CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM));
+  return D3M_OK;
+}
+
 static int dev_init(Ctx &c) {
   if (c.dev) return D3M_OK;
   const Plan &P = c.plan;
+  if (c.fault == "alloc") {  // host-side fault injection: the first device allocation fails
+    c.err = "d3m_factor: device allocation failed (injected by D3M_FAULT=alloc)";
+    return D3M_ENOMEM;
+  }
   DeviceState *d = new DeviceState();
   c.dev = d;
   d->precision = c.opt.precision;
@@ -2440,6 +2424,16 @@ static int dev_init(Ctx &c) {
   {
     std::vector<double2> v(P.ent_val.size());
     for (size_t i = 0; i < v.size(); ++i) v[i] = make_double2(P.ent_val[i].real(), P.ent_val[i].imag());
+    // host-side fault injection on the uploaded copy of the entries of M:
+    // "pivot" zeroes row and column of the first pivot of front 0 (an exactly
+    // zero pivot column), "nan" makes its diagonal entry NaN
+    if ((c.fault == "pivot" || c.fault == "nan") && !P.sn_start.empty()) {
+      const int64_t j0 = P.sn_start[0];
+      for (size_t i = 0; i < v.size(); ++i) {
+        if (c.fault == "pivot" && (P.ent_row[i] == j0 || P.ent_col[i] == j0)) v[i] = make_double2(0.0, 0.0);
+        if (c.fault == "nan" && P.ent_row[i] == j0 && P.ent_col[i] == j0) v[i] = make_double2(NAN, 0.0);
+      }
+    }
     CUDA_TRY(upload(d, &d->ent_val, v));
     // the residual's operator as Ar + j Ai: most entries are real, so the
     // fp64 product costs two multiply-adds per entry instead of four
@@ -2597,22 +2591,30 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(dalloc(d, &d->st_info, nsn));
   CUDA_TRY(dalloc(d, &d->st_minpiv, nsn));
   CUDA_TRY(dalloc(d, &d->flop_cnt, 2));
-  CUDA_TRY(dalloc(d, &d->swp, (size_t)nsn * 2 * NB));
+  CUDA_TRY(dalloc(d, &d->swp, (size_t)3 * nsn * 2 * NB));  // three look-ahead slots
   CUDA_TRY(dalloc(d, &d->tc_err, 1));
-  d->tc_grid.assign(P.n_levels, {});
+  CUDA_TRY(dalloc(d, &d->fin_err, 1));
+  if (c.fault == "timeout") d->tc_wait_cap = 0;  // every first wait of k_tc_gemm expires at once
+  d->update_grid_p.assign(P.n_levels, {});
+  d->update_grid_r.assign(P.n_levels, {});
   for (int l = 0; l < P.n_levels; ++l)
     for (int stp = 0; stp < d->level_steps[l]; ++stp) {
-      int g = 0;
+      int g = 0, gr = 0;
       for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
         int s = P.level_fronts[i];
         int cmin = std::min<int>(pp[s], (stp + 1) * (NB - 1));
-        int R0 = (cmin / TCM) * TCM, C0 = (cmin / TCN) * TCN;
-        int nI = (m[s] - R0 + TCM - 1) / TCM, nJ = (m[s] - C0 + TCN - 1) / TCN, t = 0;
-        for (int ii = 0; ii < nI; ++ii) t += std::min(nJ, (R0 + ii * TCM + TCM - C0 + TCN - 1) / TCN);
-        g = std::max(g, t);
+        int nt = (pp[s] + UT - 1) / UT - cmin / UT;
+        g = std::max(g, nt * (nt + 1) / 2);
+        const int nr = (m[s] - (pp[s] / UT) * UT + UT - 1) / UT, nc = (pp[s] - (cmin / UT) * UT + UT - 1) / UT;
+        gr = std::max(gr, nr * nc);
       }
-      d->tc_grid[l].push_back(std::max(g, 1));
+      d->update_grid_p[l].push_back(std::max(g, 1));
+      d->update_grid_r[l].push_back(std::max(gr, 1));
     }
+  if (c.opt.precision == D3M_MIXED) {
+    const int rc = tc_plan(c, d, m, pp);
+    if (rc) return rc;
+  }
   d->level_maxp.assign(P.n_levels, 0);
   for (int l = 0; l < P.n_levels; ++l)
     for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i)
@@ -2654,6 +2656,11 @@ __global__ void k_iperm(int64_t nsn, const int32_t *__restrict__ fp, const int64
   if (s >= nsn) return;
   for (int i = threadIdx.x; i < fp[s]; i += blockDim.x) iperm[fpiv[s] + perm[fpiv[s] + i]] = i;
 }
+// flag = 1 if an entry of the pivot inverses is not finite
+__global__ void k_check_finite(const double2 *__restrict__ v, int64_t n, int32_t *__restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[i].x) || !isfinite(v[i].y)) *flag = 1;
+}
 __global__ void k_fill_double(double *x, int64_t n, double v) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) x[i] = v;
@@ -2668,7 +2675,6 @@ static int factor_t(Ctx &c) {
   cx<T> *arena = (cx<T> *)d->arena;
   cx<T> *W = (cx<T> *)d->W;
   FrontTab ft = tab(d);
-  if (sizeof(T) == 4) CUDA_TRY(tc_attrs());
   CUDA_TRY(panel_attrs<T>());
   // Without profiling the launch sequence (fixed once the schedule is tuned)
   // is captured into a CUDA graph at the first call and replayed after.
@@ -2680,14 +2686,12 @@ static int factor_t(Ctx &c) {
     CUDA_TRY(cudaMemsetAsync(d->st_info, 0, nsn * sizeof(int32_t), s));
     CUDA_TRY(cudaMemsetAsync(d->flop_cnt, 0, 2 * sizeof(double), s));
     CUDA_TRY(cudaMemsetAsync(d->tc_err, 0, sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(d->fin_err, 0, sizeof(int32_t), s));
     d->prof.reset();
     // (profiled runs are sequential, so that every kernel class's events time
   // that class alone)
   const bool la = c.opt.lookahead == 0 && !d->lookahead_off && !d->prof.on;
-    if (la) {  // stream_b starts after everything issued so far on the factor stream
-      CUDA_TRY(cudaEventRecord(d->ev_b, s));
-      CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_b, 0));
-    }
+    bool used_c = false;  // stream_c carried an L11^{-1} (join it before the end)
     k_fill_double<<<(unsigned)((nsn + 255) / 256), 256, 0, s>>>(d->st_minpiv, nsn, 1e300);
     k_init_perm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm);
     nl += 2;
@@ -2695,7 +2699,10 @@ static int factor_t(Ctx &c) {
       const int nf = P.level_ptr[l + 1] - P.level_ptr[l];
       const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
       d->prof.cur_level = l;
-      const bool use_tc = sizeof(T) == 4 && (c.opt.update_kernel == 2 || (c.opt.update_kernel == 0 && d->lvl_tc[l]));
+      // deferred products on the tensor cores (mixed): the panels update only
+      // the pivot blocks; the update rows and Schur complements follow as two
+      // batched tcgen05 products after the level's L11^{-1}
+      const bool defer = sizeof(T) == 4 && (c.opt.update_kernel == 2 || (c.opt.update_kernel == 0 && d->lvl_tc[l]));
       // zero the level's fronts (contiguous) and assemble the entries of M
       int64_t first = P.front_off[P.level_fronts[P.level_ptr[l]]];
       int last_s = P.level_fronts[P.level_ptr[l + 1] - 1];
@@ -2726,15 +2733,74 @@ static int factor_t(Ctx &c) {
       // Schur part least urgent)
       auto update = [&](int stp, const cx<T> *Ws, const int2 *sn, int mode, cudaStream_t st) {
         const int prio = !la ? 0 : mode == 2 ? d->prio_lo : d->prio_hi;
-        if (use_tc) {
-          dim3 g(d->tc_grid[l][stp], nf);
-          launch_update_tc<T>(g, st, lvl, ft, wofs, arena, Ws, sn, mode, d->tc_err, prio);
-        } else {
-          dim3 g(d->update_grid[l][stp], nf);
-          launch_prio(k_update<T>, g, dim3(256), 0, st, prio, lvl, ft, wofs, arena, (const cx<T> *)Ws, sn, mode);
-        }
+        dim3 g(mode == 3 ? d->update_grid_p[l][stp] : mode == 4 ? d->update_grid_r[l][stp] : d->update_grid[l][stp],
+               nf);
+        launch_prio(k_update<T>, g, dim3(256), 0, st, prio, lvl, ft, wofs, arena, (const cx<T> *)Ws, sn, mode);
       };
-      for (int stp = 0; stp < d->level_steps[l]; ++stp) {
+      // Deferred levels: each step's panel and its pivot-block update (mode
+      // 3) form the critical chain on stream s; the update rows of the step
+      // (Algorithm 1's triangular solve, k_l21, writing W21 = L21 D to the
+      // W21 buffer) and their trailing update (mode 4) follow on stream_b with
+      // the least urgent priority.  W, the snapshots and the column
+      // permutations rotate through three slots, as in the look-ahead below.
+      // The Schur complements are one tensor-core product after the level.
+      if (defer && la) {
+        CUDA_TRY(cudaEventRecord(d->ev_b, s));
+        CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_b, 0));
+      }
+      for (int stp = 0; defer && stp < d->level_steps[l]; ++stp) {
+        const int slot = stp % 3;
+        cx<T> *Ws = W + slot * d->wslot;
+        int2 *sn = d->snap + slot * nsn + P.level_ptr[l];
+        int2 *sw = d->swp + ((int64_t)slot * nsn + P.level_ptr[l]) * 2 * NB;
+        cudaStream_t sb = la ? d->stream_b : s;
+        if (la && stp >= 3) CUDA_TRY(cudaStreamWaitEvent(s, d->ev_schur[slot], 0));
+        {
+          PROF_BEGIN(PC_PANEL);
+          int cs = c.opt.panel_kernel == 1 ? 0 : d->lvl_cs[l];
+          CUDA_TRY(launch_panel<T>(cs, d->level_maxp[l], 0, nf, lvl, ft, wofs, arena, Ws, d->perm, d->dinv_d,
+                                   d->dinv_o, d->psize, d->st_k0, d->st_kb, d->st_info, d->st_minpiv, d->flop_cnt, sw,
+                                   sn, s, la ? d->prio_hi : 0));
+          PROF_END(PC_PANEL);
+        }
+        {
+          PROF_BEGIN(PC_UPDATE);
+          update(stp, Ws, sn, 3, s);
+          PROF_END(PC_UPDATE);
+        }
+        if (la) {
+          CUDA_TRY(cudaEventRecord(d->ev_step[slot], s));
+          CUDA_TRY(cudaStreamWaitEvent(sb, d->ev_step[slot], 0));
+        }
+        if (d->level_maxm[l] > d->level_maxp[l]) {
+          {
+            PROF_BEGIN_ON(PC_PANEL, sb);
+            dim3 g((unsigned)std::max(1, (d->level_maxm[l] + 127) / 128), (unsigned)nf);
+            CUDA_TRY(launch_prio(k_l21<T>, g, dim3(128), 0, sb, la ? d->prio_lo : 0, lvl, ft, wofs, arena, Ws,
+                                 (const double2 *)d->dinv_d, (const double2 *)d->dinv_o, (const int8_t *)d->psize,
+                                 (const int2 *)sn, (const int2 *)sw, d->flop_cnt, d->tc_w,
+                                 (const int64_t *)(d->w21_off + P.level_ptr[l])));
+            PROF_END_ON(PC_PANEL, sb);
+          }
+          {
+            PROF_BEGIN_ON(PC_UPDATE, sb);
+            update(stp, Ws, sn, 4, sb);
+            PROF_END_ON(PC_UPDATE, sb);
+          }
+          nl += 2;
+        }
+        if (la) CUDA_TRY(cudaEventRecord(d->ev_schur[slot], sb));
+        nl += 2;
+      }
+      if (defer && la) {
+        CUDA_TRY(cudaEventRecord(d->ev_b, d->stream_b));
+        CUDA_TRY(cudaStreamWaitEvent(s, d->ev_b, 0));
+      }
+      if (la && !defer) {  // stream_b starts after everything issued so far on the factor stream
+        CUDA_TRY(cudaEventRecord(d->ev_b, s));
+        CUDA_TRY(cudaStreamWaitEvent(d->stream_b, d->ev_b, 0));
+      }
+      for (int stp = 0; !defer && stp < d->level_steps[l]; ++stp) {
         // Look-ahead: the panels of a front read and write only its pivot
         // block (columns < p), so the Schur-complement part of step stp's
         // update (columns >= p) runs on stream_b while step stp + 1 proceeds
@@ -2776,7 +2842,7 @@ static int factor_t(Ctx &c) {
         nl += 3;
       }
       // the next level's extend-add reads these Schur complements
-      if (la) {
+      if (la && !defer) {
         CUDA_TRY(cudaEventRecord(d->ev_b, d->stream_b));
         CUDA_TRY(cudaStreamWaitEvent(s, d->ev_b, 0));
       }
@@ -2789,6 +2855,7 @@ static int factor_t(Ctx &c) {
         cudaStream_t si = s;
         if (la) {
           si = d->stream_c;
+          used_c = true;
           CUDA_TRY(cudaEventRecord(d->ev_lvl, s));
           CUDA_TRY(cudaStreamWaitEvent(si, d->ev_lvl, 0));
         }
@@ -2811,14 +2878,30 @@ static int factor_t(Ctx &c) {
         }
         PROF_END(PC_INV);
       }
+      if (defer && sizeof(T) == 4 && d->tcl[l].kpitch > 0) {
+        const DeviceState::TcLevel &L = d->tcl[l];
+        cx<float> *ar = (cx<float> *)d->arena;
+        PROF_BEGIN(PC_TC);
+        // operands of C = F22 - L21 W21^T as bf16 planes, then the product
+        k_tc_split<<<L.nsx, 256, 0, s>>>(d->tc_split + L.sx0, ar, d->perm, d->f_piv, d->planesA, L.rowsA,
+                                         L.kpitch);
+        k_tc_split<<<L.nsl, 256, 0, s>>>(d->tc_split + L.sl0, (const cx<float> *)d->tc_w, d->perm, d->f_piv,
+                                         d->planesB, L.rowsB, L.kpitch);
+        k_tc_gemm<<<L.ng2, 128, G_SMEM, s>>>(L.tmA, L.tmB, d->tc_tiles + L.g20, ar, d->tc_w, d->tc_err,
+                                             d->tc_wait_cap);
+        PROF_END(PC_TC);
+        nl += 3;
+      }
     }
-    if (la && sizeof(T) == 4) {  // join the inverses before the factor completes
+    if (used_c) {  // join the inverses before the factor completes
       CUDA_TRY(cudaEventRecord(d->ev_c, d->stream_c));
       CUDA_TRY(cudaStreamWaitEvent(s, d->ev_c, 0));
     }
     d->prof.cur_level = -1;
     k_iperm<<<(unsigned)nsn, 128, 0, s>>>(nsn, d->f_p, d->f_piv, d->perm, d->iperm);
-    ++nl;
+    k_check_finite<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P.piv_total + 255) / 256, 1216)), 256, 0, s>>>(
+        d->dinv_d, P.piv_total, d->fin_err);
+    nl += 2;
   return D3M_OK;
   };
   if (use_graph && d->g_factor) {
@@ -2868,27 +2951,44 @@ static int factor_t(Ctx &c) {
   int32_t tce = 0;
   CUDA_TRY(cudaMemcpy(&tce, d->tc_err, sizeof tce, cudaMemcpyDeviceToHost));
   if (tce) {
-    c.err = "d3m_factor: a tensor-core update tile timed out waiting for its MMAs";
+    c.err = "d3m_factor: a tensor-core product tile gave up a bounded wait (its results were discarded)";
     return D3M_ETIMEOUT;
   }
-  c.stats.flops_update = fc[0];
-  c.stats.flops_panel = fc[1];
+  int32_t fin = 0;
+  CUDA_TRY(cudaMemcpy(&fin, d->fin_err, sizeof fin, cudaMemcpyDeviceToHost));
   c.lvl_cs = d->lvl_cs;
   c.lvl_tc.assign(P.n_levels, 0);
-  for (int l = 0; l < P.n_levels; ++l)
+  double ftc = 0.0;
+  for (int l = 0; l < P.n_levels; ++l) {
     c.lvl_tc[l] = sizeof(T) == 4 && (c.opt.update_kernel == 2 || (c.opt.update_kernel == 0 && d->lvl_tc[l]));
+    if (c.lvl_tc[l] && !d->tcl.empty()) ftc += d->tcl[l].flops;
+  }
+  // the panels count each step's whole trailing triangle; on deferred levels
+  // the update rows and Schur complements are the tensor-core products' share
+  c.stats.flops_tc = ftc;
+  c.stats.flops_update = fc[0] - ftc;
+  c.stats.flops_panel = fc[1];
   if (c.opt.panel_kernel == 1) c.lvl_cs.assign(P.n_levels, 0);
   if (d->prof.on) {
     d->tune_panel = d->prof.per_level(PC_PANEL, P.n_levels);
     d->tune_update = d->prof.per_level(PC_UPDATE, P.n_levels);
+    d->tune_inv = d->prof.per_level(PC_INV, P.n_levels);
+    d->tune_tc = d->prof.per_level(PC_TC, P.n_levels);
     c.lvl_ms_panel = d->tune_panel;
     c.lvl_ms_update = d->tune_update;
+    c.lvl_ms_inv = d->tune_inv;
+    c.lvl_ms_tc = d->tune_tc;
     double ms[PC_N];
     d->prof.collect(ms);
     c.stats.ms_assemble = ms[PC_ASSEMBLE];
     c.stats.ms_panel = ms[PC_PANEL];
     c.stats.ms_update = ms[PC_UPDATE];
     c.stats.ms_inverse = ms[PC_INV];
+    c.stats.ms_tc = ms[PC_TC];
+  }
+  if (fin) {
+    c.err = "d3m_factor: a pivot is not finite (non-finite entries in the operator or its factors)";
+    return D3M_ESINGULAR;
   }
   for (int64_t q = 0; q < nsn; ++q)
     if (info[q] != 0) {
@@ -2980,20 +3080,36 @@ static int autotune(Ctx &c) {
   const int uk = c.opt.update_kernel;
   d->prof.on = true;
   d->lookahead_off = true;  // per-kernel times without the overlap
-  // trial A: fp32-FMA updates, smallest cluster
+  // trial A: right-looking fp32/fp64-FMA updates, smallest cluster
   std::vector<int> csA = d->lvl_cs, csB(nlev);
   // (clusters stay within the portable size 8)
   for (int l = 0; l < nlev; ++l) csB[l] = csA[l] > 0 && csA[l] <= 4 ? csA[l] * 2 : csA[l];
+  const bool mixed = c.opt.precision == D3M_MIXED;
   c.opt.update_kernel = 1;
   int rc = factor_any(c);
-  std::vector<double> pA = d->tune_panel, uA = d->tune_update;
-  // trial B: tensor-core updates (mixed), doubled cluster
-  if (rc == D3M_OK) {
+  auto total = [&]() {  // per-level time of everything but the assembly
+    std::vector<double> t(nlev, 0.0);
+    for (int l = 0; l < nlev; ++l)
+      t[l] = d->tune_panel[l] + d->tune_update[l] + (d->tune_inv.empty() ? 0.0 : d->tune_inv[l]) +
+             (d->tune_tc.empty() ? 0.0 : d->tune_tc[l]);
+    return t;
+  };
+  std::vector<double> tA = total(), pA = d->tune_panel, tB(nlev, 1e300), pB(nlev, 1e300);
+  // trial B (mixed): deferred tensor-core products, smallest cluster
+  if (rc == D3M_OK && mixed) {
     c.opt.update_kernel = 2;
+    rc = factor_any(c);
+    tB = total();
+    pB = d->tune_panel;
+  }
+  // trial C: doubled cluster, with the faster update scheme of each level
+  if (rc == D3M_OK) {
+    c.opt.update_kernel = 0;
+    for (int l = 0; l < nlev; ++l) d->lvl_tc[l] = mixed && tB[l] < tA[l] ? 1 : 0;
     d->lvl_cs = csB;
     rc = factor_any(c);
   }
-  std::vector<double> pB = d->tune_panel, uB = d->tune_update;
+  std::vector<double> pC = d->tune_panel;
   c.opt.update_kernel = uk;
   d->prof.on = prof;
   d->lookahead_off = false;
@@ -3001,10 +3117,12 @@ static int autotune(Ctx &c) {
     d->lvl_cs = csA;
     return rc;
   }
+  // cluster size per level: trial C's panels against the smallest cluster's
+  // panels under the same update scheme (trial B for deferred levels, A else)
   int64_t ntc = 0, ncs2 = 0;
   for (int l = 0; l < nlev; ++l) {
-    d->lvl_tc[l] = c.opt.precision == D3M_MIXED && uB[l] < uA[l] ? 1 : 0;
-    d->lvl_cs[l] = pB[l] < pA[l] ? csB[l] : csA[l];
+    const double ref = d->lvl_tc[l] ? pB[l] : pA[l];
+    d->lvl_cs[l] = pC[l] < ref ? csB[l] : csA[l];
     ntc += d->lvl_tc[l];
     ncs2 += d->lvl_cs[l] != csA[l];
   }
@@ -3312,6 +3430,159 @@ static int64_t run_sweeps(Ctx &c, int r) {
 
 static unsigned grid1(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
+static int gmres_buffers(Ctx &c, int r, int m) {
+  DeviceState *d = c.dev;
+  if (d->gm_r >= r && d->gm_m >= m) return D3M_OK;
+  for (void *p : {(void *)d->gm_V, (void *)d->gm_Z, (void *)d->gm_lamZ, (void *)d->gm_w, (void *)d->gm_y,
+                  (void *)d->gm_h, (void *)d->gm_s})
+    if (p) {
+      cudaFree(p);
+      d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), p), d->allocs.end());
+    }
+  const int64_t n = c.plan.n_edges, nlm = std::max<int64_t>((int64_t)c.plan.lm_edge.size(), 1);
+  CUDA_TRY(dalloc(d, &d->gm_V, (size_t)(m + 1) * n * r));
+  CUDA_TRY(dalloc(d, &d->gm_Z, (size_t)m * n * r));
+  CUDA_TRY(dalloc(d, &d->gm_lamZ, (size_t)m * nlm * r));
+  CUDA_TRY(dalloc(d, &d->gm_w, (size_t)n * r));
+  CUDA_TRY(dalloc(d, &d->gm_y, (size_t)m * r));
+  CUDA_TRY(dalloc(d, &d->gm_h, (size_t)2 * (m + 1) * r));
+  CUDA_TRY(dalloc(d, &d->gm_s, (size_t)r));
+  d->gm_r = r;
+  d->gm_m = m;
+  return D3M_OK;
+}
+
+// One GMRES-IR correction: solve A d = re (the current fp64 residual) by
+// flexible GMRES with right preconditioner M^{-1} (the factors, through the
+// substitution sweeps) to a relative 2-norm reduction gmres_tol per column,
+// at most gmres_restart steps, then x += d and lambda += its multipliers.
+// Adds the Krylov steps taken to `inner`.
+template <typename T>
+static int gmres_correction(Ctx &c, int r, int &inner, int64_t &nl) {
+  DeviceState *d = c.dev;
+  const Plan &P = c.plan;
+  cudaStream_t s = d->stream;
+  const int m = c.opt.gmres_restart;
+  const int64_t n = P.n_edges, nlm = (int64_t)P.lm_edge.size();
+  const int64_t vst = n * r, lst = std::max<int64_t>(nlm, 1) * r;
+  const size_t esz = sizeof(cx<T>);
+  int rc = gmres_buffers(c, r, m);
+  if (rc) return rc;
+  const unsigned gd = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, 304));
+  auto dots = [&](int nv, const double2 *V, const double2 *w) -> int {  // -> d->gm_h
+    CUDA_TRY(cudaMemsetAsync(d->gm_h, 0, sizeof(double) * 2 * nv * r, s));
+    k_dots<<<gd, 256, 0, s>>>(n, r, nv, V, vst, w, d->gm_h);
+    ++nl;
+    return D3M_OK;
+  };
+  std::vector<double> hh(2 * (m + 1) * r), h1(2 * (m + 1) * r);
+  // v_0 = r / beta
+  k_mask_rows<<<grid1(n * r), 256, 0, s>>>(n, r, d->pec, d->re);
+  if ((rc = dots(1, d->re, d->re))) return rc;
+  CUDA_TRY(cudaMemcpyAsync(hh.data(), d->gm_h, sizeof(double) * 2 * r, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> beta(r), sc(r);
+  for (int q = 0; q < r; ++q) {
+    beta[q] = std::sqrt(std::max(hh[2 * q], 0.0));
+    sc[q] = beta[q] > 0 ? 1.0 / beta[q] : 0.0;
+  }
+  CUDA_TRY(cudaMemcpyAsync(d->gm_s, sc.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  k_scale_cols<<<grid1(n * r), 256, 0, s>>>(n, r, d->re, d->gm_s, d->gm_V);
+  nl += 3;
+  // per column: Hessenberg (column-major (m+1) x m), Givens rotations, g
+  std::vector<cplx> H((size_t)(m + 1) * m * r, 0.0), cs((size_t)m * r, 0.0), sn((size_t)m * r, 0.0),
+      g((size_t)(m + 1) * r, 0.0);
+  for (int q = 0; q < r; ++q) g[(size_t)q * (m + 1)] = beta[q];
+  int kdone = 0;
+  for (int k = 0; k < m; ++k) {
+    double2 *Vk = d->gm_V + (int64_t)k * vst, *Zk = d->gm_Z + (int64_t)k * vst;
+    // z_k = M^{-1} v_k (and its multiplier part)
+    CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
+    k_scatter<T><<<grid1(n * r), 256, 0, s>>>(Vk, d->owner, (cx<T> *)d->bM, n, r);
+    nl += run_sweeps<T>(c, r) + 1;
+    k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, Zk, n, r, 0);
+    if (nlm)
+      k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r,
+                                                     d->gm_lamZ + (int64_t)k * lst, 0);
+    // w = A z_k, orthogonalised twice against v_0..v_k
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 8));
+    k_spmv<<<gs, 256, 0, s>>>(n, d->csr_ptr, d->csr_col, d->csr_re, d->csi_ptr, d->csi_col, d->csi_val, Zk, d->gm_w,
+                               r);
+    nl += 3;
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((rc = dots(k + 1, d->gm_V, d->gm_w))) return rc;
+      k_sub_many<<<grid1(n * r), 256, 0, s>>>(n, r, k + 1, d->gm_V, vst, (const double2 *)d->gm_h, d->gm_w);
+      CUDA_TRY(cudaMemcpyAsync(pass == 0 ? h1.data() : hh.data(), d->gm_h, sizeof(double) * 2 * (k + 1) * r,
+                               cudaMemcpyDeviceToHost, s));
+      ++nl;
+    }
+    if ((rc = dots(1, d->gm_w, d->gm_w))) return rc;
+    std::vector<double> nn(2 * r);
+    CUDA_TRY(cudaMemcpyAsync(nn.data(), d->gm_h, sizeof(double) * 2 * r, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int q = 0; q < r; ++q) {
+      const double hn = std::sqrt(std::max(nn[2 * q], 0.0));
+      sc[q] = hn > 0 ? 1.0 / hn : 0.0;
+      if (beta[q] == 0) continue;
+      cplx *Hq = &H[(size_t)q * (m + 1) * m + (size_t)k * (m + 1)];
+      for (int i = 0; i <= k; ++i)
+        Hq[i] = cplx(h1[2 * ((size_t)i * r + q)] + hh[2 * ((size_t)i * r + q)],
+                     h1[2 * ((size_t)i * r + q) + 1] + hh[2 * ((size_t)i * r + q) + 1]);
+      Hq[k + 1] = hn;
+      cplx *cq = &cs[(size_t)q * m], *sq = &sn[(size_t)q * m], *gq = &g[(size_t)q * (m + 1)];
+      for (int i = 0; i < k; ++i) {  // earlier rotations
+        const cplx t = cq[i] * Hq[i] + sq[i] * Hq[i + 1];
+        Hq[i + 1] = -std::conj(sq[i]) * Hq[i] + std::conj(cq[i]) * Hq[i + 1];
+        Hq[i] = t;
+      }
+      const cplx a = Hq[k], b = Hq[k + 1];
+      const double den = std::sqrt(std::norm(a) + std::norm(b));
+      if (den == 0) {
+        cq[k] = 1.0;
+        sq[k] = 0.0;
+      } else {
+        cq[k] = std::conj(a) / den;
+        sq[k] = std::conj(b) / den;
+      }
+      Hq[k] = cq[k] * a + sq[k] * b;
+      Hq[k + 1] = 0.0;
+      gq[k + 1] = -std::conj(sq[k]) * gq[k];
+      gq[k] = cq[k] * gq[k];
+      if (std::abs(gq[k + 1]) > c.opt.gmres_tol * beta[q] && Hq[k] != cplx(0.0)) all = false;
+    }
+    CUDA_TRY(cudaMemcpyAsync(d->gm_s, sc.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
+    k_scale_cols<<<grid1(n * r), 256, 0, s>>>(n, r, d->gm_w, d->gm_s, d->gm_V + (int64_t)(k + 1) * vst);
+    nl += 2;
+    ++inner;
+    kdone = k + 1;
+    if (all) break;
+  }
+  // y = H^{-1} g per column (upper triangular), then x += Z y, lambda += ...
+  std::vector<double> yv(2 * (size_t)kdone * r, 0.0);
+  for (int q = 0; q < r; ++q) {
+    if (beta[q] == 0) continue;
+    const cplx *Hq = &H[(size_t)q * (m + 1) * m];
+    std::vector<cplx> y(kdone);
+    for (int i = kdone - 1; i >= 0; --i) {
+      cplx acc = g[(size_t)q * (m + 1) + i];
+      for (int j = i + 1; j < kdone; ++j) acc -= Hq[(size_t)j * (m + 1) + i] * y[j];
+      const cplx dg = Hq[(size_t)i * (m + 1) + i];
+      y[i] = dg != cplx(0.0) ? acc / dg : cplx(0.0);
+    }
+    for (int i = 0; i < kdone; ++i) {
+      yv[2 * ((size_t)i * r + q)] = y[i].real();
+      yv[2 * ((size_t)i * r + q) + 1] = y[i].imag();
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(d->gm_y, yv.data(), yv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_add_combo<<<grid1(n * r), 256, 0, s>>>(n, r, kdone, d->gm_Z, vst, d->gm_y, d->xe);
+  if (nlm) k_add_combo<<<grid1(nlm * r), 256, 0, s>>>(nlm, r, kdone, d->gm_lamZ, lst, d->gm_y, d->lam);
+  nl += 2;
+  CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors above outlive their copies
+  return D3M_OK;
+}
+
 template <typename T>
 static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ldx, int r,
                    d3m_solve_info *info, bool host_ptrs, bool adjoint) {
@@ -3344,7 +3615,7 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 0);
   if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 0);
   std::vector<double> nh(2 * r);
-  int iters = 0;
+  int iters = 0, inner = 0;
   double maxres = 0;
   const bool refine = d->precision == D3M_MIXED;
   for (;;) {
@@ -3370,14 +3641,22 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
       if (info && info->resid) info->resid[q] = rr;
       maxres = std::max(maxres, rr);
     }
-    if (!refine || maxres <= c.opt.refine_tol || iters >= c.opt.max_refine) break;
-    // correction: solve with the residual, accumulate in fp64
-    CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
-    k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->re, d->owner, (cx<T> *)d->bM, n, r);
-    nl += run_sweeps<T>(c, r) + 3;
-    ++napply;
-    k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 1);
-    if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 1);
+    if (!refine || maxres <= c.opt.refine_tol || iters >= c.opt.max_refine || !std::isfinite(maxres)) break;
+    if (c.opt.refine_method == 1) {
+      // GMRES-IR correction (flexible GMRES on A d = r, preconditioned by the factors)
+      const int before = inner;
+      const int grc = gmres_correction<T>(c, r, inner, nl);
+      if (grc) return grc;
+      napply += inner - before;
+    } else {
+      // correction: solve with the residual, accumulate in fp64
+      CUDA_TRY(cudaMemsetAsync(d->bM, 0, P.n_m * r * esz, s));
+      k_scatter<T><<<grid1(n * r), 256, 0, s>>>(d->re, d->owner, (cx<T> *)d->bM, n, r);
+      nl += run_sweeps<T>(c, r) + 3;
+      ++napply;
+      k_gather<T><<<grid1(n * r), 256, 0, s>>>((const cx<T> *)d->xM, d->owner, d->xe, n, r, 1);
+      if (nlm) k_lambda_acc<T><<<grid1(nlm * r), 256, 0, s>>>((const cx<T> *)d->xM, P.lam_start, nlm, r, d->lam, 1);
+    }
     ++iters;
   }
   if (host_ptrs) {
@@ -3392,6 +3671,7 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   if (info) {
     info->iters = iters;
     info->max_resid = maxres;
+    info->inner_iters = inner;
   }
   c.stats.launches_solve = nl + 2;
   c.stats.solve_flops = d->solve_flops_per_rhs * r * napply;
@@ -3403,6 +3683,10 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
     c.stats.ms_residual = ms[PC_RESID];
   }
   c.lambda_nrhs = 0;
+  if (!std::isfinite(maxres)) {
+    c.err = "d3m_solve: the residual is not finite (non-finite input or factors)";
+    return D3M_ENOCONV;
+  }
   if (refine && maxres > c.opt.refine_tol) {
     char buf[128];
     snprintf(buf, sizeof buf, "d3m_solve: refinement stopped at residual %.3e after %d steps", maxres, iters);
@@ -3707,11 +3991,14 @@ static int dense_ldlt_noalloc(int m, int p, int batch, double *A, int32_t *perm,
   int32_t *kb = reinterpret_cast<int32_t *>(base + Lo.kb);
   double *mp = reinterpret_cast<double *>(base + Lo.mp);
   int8_t *ps = reinterpret_cast<int8_t *>(base + Lo.ps);
-  k_noalloc_init<<<(unsigned)std::min<int64_t>(((int64_t)batch * std::max(p, 1) + 255) / 256 + 1, 1024), 256, 0,
-                   s>>>(m, p, batch, const_cast<int32_t *>(ft.m), const_cast<int32_t *>(ft.p),
-                        const_cast<int32_t *>(ft.parent), lvl, const_cast<int64_t *>(ft.off),
-                        const_cast<int64_t *>(ft.piv), const_cast<int64_t *>(ft.soff), wofs, k0, kb, info, mp, pv);
-  if (cudaGetLastError() != cudaSuccess) return D3M_ECUDA;
+  // every launch reports its own status (cudaLaunchKernelEx), so an error
+  // left behind by the caller's earlier work is neither reported nor cleared
+  const dim3 gi((unsigned)std::min<int64_t>(((int64_t)batch * std::max(p, 1) + 255) / 256 + 1, 1024));
+  if (launch_prio(k_noalloc_init, gi, dim3(256), 0, s, 0, m, p, batch, const_cast<int32_t *>(ft.m),
+                  const_cast<int32_t *>(ft.p), const_cast<int32_t *>(ft.parent), lvl, const_cast<int64_t *>(ft.off),
+                  const_cast<int64_t *>(ft.piv), const_cast<int64_t *>(ft.soff), wofs, k0, kb, info, mp,
+                  pv) != cudaSuccess)
+    return D3M_ECUDA;
   const int steps = (p + NB - 2) / (NB - 1);
   const int cs = panel_cluster_size(p, sizeof(cx<double>));
   cx<double> *arena = reinterpret_cast<cx<double> *>(A);
@@ -3724,12 +4011,15 @@ static int dense_ldlt_noalloc(int m, int p, int batch, double *A, int32_t *perm,
     int cmin = std::min(p, (stp + 1) * (NB - 1));
     int nt = (m + UT - 1) / UT - cmin / UT;
     dim3 g(std::max(1, nt * (nt + 1) / 2), batch);
-    k_update<double><<<g, 256, 0, s>>>(lvl, ft, wofs, arena, W, snap, 0);
+    if (launch_prio(k_update<double>, g, dim3(256), 0, s, 0, (const int32_t *)lvl, ft, (const int64_t *)wofs, arena,
+                    (const cx<double> *)W, (const int2 *)snap, 0) != cudaSuccess)
+      return D3M_ECUDA;
   }
-  k_noalloc_out<<<(unsigned)std::min<int64_t>(((int64_t)batch * m + 255) / 256, 4096), 256, 0, s>>>(
-      m, p, batch, pv, dd, dof, ps, perm, dinv);
-  if (cudaGetLastError() != cudaSuccess) return D3M_ECUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return D3M_ECUDA;
+  const dim3 go((unsigned)std::min<int64_t>(((int64_t)batch * m + 255) / 256, 4096));
+  if (launch_prio(k_noalloc_out, go, dim3(256), 0, s, 0, m, p, batch, (const int32_t *)pv, (const double2 *)dd,
+                  (const double2 *)dof, (const int8_t *)ps, perm, dinv) != cudaSuccess)
+    return D3M_ECUDA;
+  // asynchronous: the results are complete when `s` reaches this point
   return D3M_OK;
 }
 

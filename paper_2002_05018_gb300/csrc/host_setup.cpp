@@ -3,6 +3,7 @@
 // orderings of main step 3 and the symbolic factorisation of main step 4.
 // Everything here runs once per problem; the numeric work is in engine.cu.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -842,9 +843,12 @@ extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double 
   Ctx &c = h->c;
   if (opt) c.opt = *opt;
   if (opt && opt->autotune_cache) c.cache_path = opt->autotune_cache;
+  if (const char *f = std::getenv("D3M_FAULT")) c.fault = f;
   c.opt.autotune_cache = nullptr;  // the context keeps its own copy
   if (c.opt.refine_tol <= 0) c.opt.refine_tol = 1e-10;
   if (c.opt.max_refine <= 0) c.opt.max_refine = 10;
+  if (c.opt.gmres_restart == 0) c.opt.gmres_restart = 20;
+  if (c.opt.gmres_tol == 0) c.opt.gmres_tol = 1e-4;
   if (c.opt.precision != D3M_FP64 && c.opt.precision != D3M_MIXED) {
     c.err = "d3m_setup: unknown precision";
     *out = h;
@@ -856,6 +860,11 @@ extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double 
   else if (c.opt.update_kernel < 0 || c.opt.update_kernel > 2) bad = "update_kernel not 0, 1 or 2";
   else if (c.opt.autotune != 0 && c.opt.autotune != 1) bad = "autotune not 0 or 1";
   else if (c.opt.lookahead != 0 && c.opt.lookahead != 1) bad = "lookahead not 0 or 1";
+  else if (c.opt.refine_method != 0 && c.opt.refine_method != 1) bad = "refine_method not 0 or 1";
+  else if (c.opt.gmres_restart < 1 || c.opt.gmres_restart > 200) bad = "gmres_restart not in 1..200";
+  else if (!(c.opt.gmres_tol > 0 && c.opt.gmres_tol < 1)) bad = "gmres_tol not in (0, 1)";
+  else if (!c.fault.empty() && c.fault != "alloc" && c.fault != "pivot" && c.fault != "nan" && c.fault != "timeout")
+    bad = "D3M_FAULT not one of alloc, pivot, nan, timeout";
   if (bad) {
     c.err = std::string("d3m_setup: ") + bad;
     *out = h;
@@ -973,9 +982,9 @@ extern "C" int d3m_structure(d3m_ctx *h, int32_t which, void *buf, size_t *bytes
     }
     case D3M_LEVELS: {
       const d3m::Ctx &c = h->c;
-      std::vector<double> d((size_t)p.n_levels * 8, 0.0);
+      std::vector<double> d((size_t)p.n_levels * 10, 0.0);
       for (int l = 0; l < p.n_levels; ++l) {
-        double *o = d.data() + (size_t)l * 8;
+        double *o = d.data() + (size_t)l * 10;
         for (int i = p.level_ptr[l]; i < p.level_ptr[l + 1]; ++i) {
           int32_t f = p.level_fronts[i];
           int64_t pp = p.sn_end[f] - p.sn_start[f];
@@ -989,6 +998,8 @@ extern "C" int d3m_structure(d3m_ctx *h, int32_t which, void *buf, size_t *bytes
         if ((size_t)l < c.lvl_ms_update.size()) o[5] = c.lvl_ms_update[l];
         if ((size_t)l < c.lvl_tc.size()) o[6] = c.lvl_tc[l];
         if ((size_t)l < c.lvl_cs.size()) o[7] = c.lvl_cs[l];
+        if ((size_t)l < c.lvl_ms_inv.size()) o[8] = c.lvl_ms_inv[l];
+        if ((size_t)l < c.lvl_ms_tc.size()) o[9] = c.lvl_ms_tc[l];
       }
       return put(buf, bytes, d);
     }

@@ -44,12 +44,13 @@ class Options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32), ("panel_kernel", ctypes.c_int32),
                 ("update_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("autotune_cache", ctypes.c_char_p), ("lookahead", ctypes.c_int32)]
+                ("autotune_cache", ctypes.c_char_p), ("lookahead", ctypes.c_int32),
+                ("refine_method", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("gmres_tol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("resid", ctypes.POINTER(ctypes.c_double)), ("iters", ctypes.c_int32),
-                ("max_resid", ctypes.c_double)]
+                ("max_resid", ctypes.c_double), ("inner_iters", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -62,7 +63,7 @@ class Stats(ctypes.Structure):
                                                "ms_update", "ms_fwd", "ms_bwd", "ms_residual", "solve_flops",
                                                "ms_inverse")] + \
                [("tuned_levels_tc", ctypes.c_int64), ("tuned_levels_cs2", ctypes.c_int64),
-                ("ms_tuning", ctypes.c_double)]
+                ("ms_tuning", ctypes.c_double), ("ms_tc", ctypes.c_double), ("flops_tc", ctypes.c_double)]
 
     def asdict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -136,7 +137,8 @@ class Solver:
 
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
-                 update_kernel=0, autotune=0, autotune_cache=None, lookahead=0):
+                 update_kernel=0, autotune=0, autotune_cache=None, lookahead=0, refine_method=0,
+                 gmres_restart=0, gmres_tol=0.0):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -151,7 +153,8 @@ class Solver:
         self.stream = stream
         self._cache = None if autotune_cache is None else str(autotune_cache).encode()
         opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile),
-                      int(panel_kernel), int(update_kernel), int(autotune), self._cache, int(lookahead))
+                      int(panel_kernel), int(update_kernel), int(autotune), self._cache, int(lookahead),
+                      int(refine_method), int(gmres_restart), float(gmres_tol))
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))
@@ -181,12 +184,12 @@ class Solver:
         if x is None:
             x = torch.empty((r, self.n_edges), dtype=torch.complex128, device=rhs.device).t()
         res = np.zeros(r)
-        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0)
+        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0, 0)
         ldx = x.stride(1) if r > 1 else self.n_edges
         rc = self.lib.d3m_solve(self.h, ctypes.c_void_p(rhs.data_ptr()), ldb,
                                 ctypes.c_void_p(x.data_ptr()), ldx, r, ctypes.byref(info))
         self._check(rc)
-        return x, dict(resid=res, iters=info.iters, max_resid=info.max_resid)
+        return x, dict(resid=res, iters=info.iters, max_resid=info.max_resid, inner_iters=info.inner_iters)
 
     def solve_adjoint(self, rhs, y=None):
         """y = A^{-H} rhs with the same factors (device tensors, layout as solve)."""
@@ -196,12 +199,12 @@ class Solver:
         if y is None:
             y = torch.empty((r, self.n_edges), dtype=torch.complex128, device=rhs.device).t()
         res = np.zeros(r)
-        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0)
+        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0, 0)
         ldy = y.stride(1) if r > 1 else self.n_edges
         rc = self.lib.d3m_solve_adjoint(self.h, ctypes.c_void_p(rhs.data_ptr()), ldb,
                                         ctypes.c_void_p(y.data_ptr()), ldy, r, ctypes.byref(info))
         self._check(rc)
-        return y, dict(resid=res, iters=info.iters, max_resid=info.max_resid)
+        return y, dict(resid=res, iters=info.iters, max_resid=info.max_resid, inner_iters=info.inner_iters)
 
     def grad_eps(self, x, y):
         """grad[c] = k^2 Re(sum_r conj(y)_c^T M_c x_c) on the device (float64, n_cells)."""
@@ -218,7 +221,7 @@ class Solver:
         """Host (ideally pinned) column-major complex128 arrays/tensors."""
         r = rhs.shape[1]
         res = np.zeros(r)
-        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0)
+        info = SolveInfo(_ptr(res, ctypes.c_double), 0, 0.0, 0)
         rp = rhs.data_ptr() if hasattr(rhs, "data_ptr") else rhs.ctypes.data
         xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
         ld_r = rhs.stride(1) if hasattr(rhs, "data_ptr") else rhs.strides[1] // 16
@@ -226,7 +229,7 @@ class Solver:
         rc = self.lib.d3m_solve_host(self.h, ctypes.c_void_p(rp), ld_r, ctypes.c_void_p(xp), ld_x, r,
                                      ctypes.byref(info))
         self._check(rc)
-        return dict(resid=res, iters=info.iters, max_resid=info.max_resid)
+        return dict(resid=res, iters=info.iters, max_resid=info.max_resid, inner_iters=info.inner_iters)
 
     def rhs_planewave(self, khat_pol6):
         kp = np.ascontiguousarray(np.asarray(khat_pol6, np.float64))
@@ -251,7 +254,7 @@ class Solver:
         if which == M_ENTRIES:
             return buf.reshape(-1, 4)
         if which == LEVELS:
-            return buf.reshape(-1, 8)
+            return buf.reshape(-1, 10)
         return buf
 
     def lam(self, nrhs):

@@ -56,33 +56,40 @@ def test_set_profile_argument_checks():
     s.close()
 
 
-def _fake_run(ms_panel, ms_update):
-    prof = {"ms_update": ms_update, "ms_panel": ms_panel, "ms_assemble": 1.0, "ms_inverse": 2.0, "ms_fwd": 3.0,
-            "ms_bwd": 4.0, "ms_residual": 0.5, "flops_update": 4.0e11, "flops_panel": 1.0e10}
+def _fake_run(ms_panel, ms_update, ms_tc=0.0):
+    prof = {"ms_update": ms_update, "ms_panel": ms_panel, "ms_assemble": 1.0, "ms_inverse": 2.0, "ms_tc": ms_tc,
+            "ms_fwd": 3.0, "ms_bwd": 4.0, "ms_residual": 0.5, "flops_update": 4.0e11, "flops_panel": 1.0e10,
+            "flops_tc": 6.0e11}
     stats = {"n_levels": 28, "tuned_levels_tc": 0, "tuned_levels_cs2": 3, "ms_tuning": 200.0}
     return dict(factor_flops=6.8e11, factor_ms=70.0, solve_ms=45.0, iters=3, max_resid=3e-11, step_ms=115.0,
                 prof=prof, stats=stats)
 
 
 def test_precision_summary_roofline_keys():
+    """The dominant class (by profiled time) gets "roofline", every other class
+    "roofline_<class>", each against the peak of its own pipe; the tensor-core
+    class reports its fraction of the 3xTF32 ceiling as well."""
     sys.path.insert(0, ROOT)
     import bench
-    for ms_panel, ms_update, dom in ((40.0, 30.0, "panel"), (20.0, 30.0, "update")):
-        sub = bench.precision_summary(_fake_run(ms_panel, ms_update), 80.55, "float", 2, 64)
-        other = "update" if dom == "panel" else "panel"
-        roof, roof2 = sub["roofline"], sub["roofline_" + other]
-        for r in (roof, roof2):
+    peaks = {"alu": 80.55, "tensor": 900.0}
+    for ms_panel, ms_update, ms_tc, dom in ((40.0, 30.0, 5.0, "panel"), (20.0, 30.0, 5.0, "update"),
+                                            (20.0, 3.0, 25.0, "tc")):
+        sub = bench.precision_summary(_fake_run(ms_panel, ms_update, ms_tc), peaks, "float", 2, 64)
+        others = [c for c in ("panel", "update", "tc") if c != dom]
+        for r in [sub["roofline"]] + [sub["roofline_" + c] for c in others]:
             for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
                 assert k in r
-            assert r["unit"] == "TFLOP/s" and r["peak"] == 80.55
-            assert abs(r["frac"] - r["achieved"] / 80.55) < 1e-3
-        ms, fl = (ms_panel, 1.0e10) if dom == "panel" else (ms_update, 4.0e11)
+            assert r["unit"] == "TFLOP/s" and r["traffic"] is None
+            assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
+        roof = sub["roofline"]
+        ms, fl = {"panel": (ms_panel, 1.0e10), "update": (ms_update, 4.0e11), "tc": (ms_tc, 6.0e11)}[dom]
         assert abs(roof["achieved"] - fl / (ms * 1e-3) / 1e12) < 1e-3
         assert roof["ms_per_step"] == ms
-        # traffic data exist for workload 2's update class only
-        assert (roof["traffic"] is not None) == (dom == "update")
+        tc = roof if dom == "tc" else sub["roofline_tc"]
+        assert tc["bound"] == "tensor" and tc["peak"] == 900.0
+        assert abs(tc["frac_of_3xtf32_ceiling"] - 3 * tc["frac"]) < 2e-3
         assert sub["solve_rhs_per_s"] == round(64 / 45e-3, 1)
         assert sub["schedule"]["doubled_cluster_levels"] == 3
-    # another workload never picks up workload 2's traffic figure
-    sub5 = bench.precision_summary(_fake_run(20.0, 30.0), 80.55, "float", 5, 128)
-    assert sub5["roofline"]["traffic"] is None
+    # a run without deferred levels (fp64 leg) reports no tensor-core class
+    sub = bench.precision_summary(_fake_run(40.0, 30.0, 0.0), peaks, "double", 2, 64)
+    assert "roofline_tc" not in sub and sub["roofline"]["bound"] == "alu"

@@ -61,3 +61,63 @@ def test_refinement_cap_reports_noconv_and_keeps_last_iterate():
     res = fem.rel_residual(w, x.cpu().numpy(), f).max()
     assert 0 < res < 1e-8
     s.close()
+
+
+# Host-side fault injection (environment D3M_FAULT, read by d3m_setup): the
+# failure is made on the host -- a refused allocation, a poisoned copy of the
+# operator's entries, or a zero bound on the tensor-core kernel's first
+# mbarrier waits -- and the library must report it through its status codes
+# while the GPU context stays usable.
+
+def _factor_with_fault(monkeypatch, fault, **kw):
+    monkeypatch.setenv("D3M_FAULT", fault)
+    w = W.make(1)
+    s = d3m.Solver.from_workload(w, **kw)
+    monkeypatch.delenv("D3M_FAULT")
+    with pytest.raises(d3m.D3MError) as e:
+        s.factor()
+    s.close()
+    return e.value
+
+
+def _still_usable():
+    w = W.tiny(4, 4, 4, 2, 1, 1, seed=1)
+    s = d3m.Solver.from_workload(w, precision=d3m.MIXED)
+    s.factor()
+    f = fem.rhs_planewave(w)
+    x, info = s.solve(torch.tensor(f.T.copy(), device="cuda").t())
+    s.close()
+    assert info["max_resid"] < 1e-10
+
+
+def test_fault_alloc_reports_enomem(monkeypatch):
+    _need_gpu()
+    e = _factor_with_fault(monkeypatch, "alloc")
+    assert e.code == d3m.D3M_ENOMEM and "D3M_FAULT" in str(e)
+    _still_usable()
+
+
+@pytest.mark.parametrize("prec", [d3m.FP64, d3m.MIXED])
+def test_fault_zero_pivot_reports_singular(monkeypatch, prec):
+    _need_gpu()
+    e = _factor_with_fault(monkeypatch, "pivot", precision=prec)
+    assert e.code == d3m.D3M_ESINGULAR and "zero pivot column" in str(e) and "front 0" in str(e)
+    _still_usable()
+
+
+def test_fault_nan_reports_non_finite_pivot(monkeypatch):
+    _need_gpu()
+    e = _factor_with_fault(monkeypatch, "nan", precision=d3m.MIXED)
+    assert e.code == d3m.D3M_ESINGULAR and "not finite" in str(e)
+    _still_usable()
+
+
+def test_fault_expired_wait_reports_timeout(monkeypatch):
+    """Every first mbarrier wait of the tensor-core product kernel is bounded
+    by zero polls: each tile raises the error flag, waits (bounded) for its own
+    loads and MMAs, frees its TMEM and returns; d3m_factor reports
+    D3M_ETIMEOUT and the next context factors and solves normally."""
+    _need_gpu()
+    e = _factor_with_fault(monkeypatch, "timeout", precision=d3m.MIXED, update_kernel=2)
+    assert e.code == d3m.D3M_ETIMEOUT
+    _still_usable()

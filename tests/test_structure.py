@@ -70,6 +70,13 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, nme), nme
 
 
+def test_setup_rejects_unknown_fault(monkeypatch):
+    monkeypatch.setenv("D3M_FAULT", "meteor")
+    with pytest.raises(d3m.D3MError) as e:
+        d3m.Solver.from_workload(W.tiny(4, 4, 4, 2, 1, 1))
+    assert e.value.code == d3m.D3M_EINVAL and "D3M_FAULT" in str(e.value)
+
+
 def test_setup_rejects_bad_input():
     w = W.tiny(4, 4, 4, 2, 1, 1)
     with pytest.raises(d3m.D3MError) as e:
@@ -102,7 +109,7 @@ def test_level_table_matches_tree_heights():
             h[plan.parent[q]] = max(h[plan.parent[q]], h[q] + 1)
     s = d3m.Solver.from_workload(w, leaf_max=64)
     lv = s.structure(d3m.LEVELS)
-    assert lv.shape == (h.max() + 1, 8)
+    assert lv.shape == (h.max() + 1, 10)
     pp = np.asarray(plan.sn_end) - np.asarray(plan.sn_start)
     mm = pp + np.array([len(plan.struct[q]) for q in range(n)])
     for L in range(h.max() + 1):
@@ -116,7 +123,9 @@ def test_level_table_matches_tree_heights():
 
 
 @pytest.mark.parametrize("kw", [dict(update_kernel=3), dict(panel_kernel=2), dict(autotune=-1),
-                                dict(lookahead=2), dict(leaf_max=-5)])
+                                dict(lookahead=2), dict(leaf_max=-5), dict(refine_method=2),
+                                dict(gmres_restart=201), dict(gmres_restart=-1), dict(gmres_tol=1.5),
+                                dict(gmres_tol=-1e-3)])
 def test_setup_rejects_bad_options(kw):
     """Option values outside their documented sets are refused at set-up."""
     w = W.make(1)
