@@ -19,9 +19,16 @@ and then E_i = A_i^{-1} (f_i - D_i lambda).
   step 6  forward / diagonal / backward substitution for lambda
   step 7  recover E_i and take each edge from its owner copy.
 
+A second, independent route to the same solution (solve_primal_schur): the
+classical primal substructuring of the same decomposed operators, with one
+unknown per interface edge instead of multipliers -- eliminate every
+subdomain's interior, sum the interface Schur complements (the +-alpha
+interface terms cancel there), solve, recover the interiors.
+
 Parity pins (tests/test_oracle_d3m.py): E equals the undecomposed global
-solution; K equals brute-force D^T A^{-1} D with dense inverses; the block
-LDL^T reproduces K and solves it like numpy.linalg.solve.
+solution, for several interface coefficients alpha; K equals brute-force
+D^T A^{-1} D with dense inverses; the block LDL^T reproduces K and solves it
+like numpy.linalg.solve; the primal Schur route equals both.
 """
 from __future__ import annotations
 
@@ -176,4 +183,40 @@ def solve(w, f=None, dense_inverse=False, return_all=False):
                    default=0.0)
     if return_all:
         return dict(x=x, lam=lam, K=K, g=g, dec=dec, kd=kd, fac=fac, copy_mismatch=mismatch)
+    return x
+
+
+def solve_primal_schur(w, f=None):
+    """Primal substructuring of the decomposed operators: per subdomain i with
+    interior dofs I (edges held by no other subdomain) and interface dofs G,
+    S = sum_i R_i^T (A_GG - A_GI A_II^{-1} A_IG) R_i and
+    g = sum_i R_i^T (f_G - A_GI A_II^{-1} f_I) over the global interface
+    edges (R_i: restriction to subdomain i's copies; RHS by the owner rule),
+    then u_G = S^{-1} g and u_I = A_II^{-1} (f_I - A_IG u_G).  Dense Schur
+    complements, for small meshes."""
+    f = fem.rhs_planewave(w) if f is None else f
+    dec = decomp.decompose(w)
+    gam = np.array(sorted(e for e, cs in dec.copies.items() if len(cs) > 1), np.int64)
+    gpos = {int(e): i for i, e in enumerate(gam)}
+    nrhs = f.shape[1]
+    S = np.zeros((len(gam), len(gam)), np.complex128)
+    g = np.zeros((len(gam), nrhs), np.complex128)
+    parts = []
+    for sd in dec.subs:
+        A = sd.A.toarray()
+        isg = np.array([len(dec.copies[int(e)]) > 1 for e in sd.edges])
+        I, G = np.flatnonzero(~isg), np.flatnonzero(isg)
+        fi = decomp.split_rhs(dec, sd, f)
+        AII, AIG, AGI, AGG = A[np.ix_(I, I)], A[np.ix_(I, G)], A[np.ix_(G, I)], A[np.ix_(G, G)]
+        X = np.linalg.solve(AII, np.concatenate([AIG, fi[I]], axis=1)) if len(I) else np.zeros((0, len(G) + nrhs))
+        rg = np.array([gpos[int(e)] for e in sd.edges[G]], np.int64)
+        S[np.ix_(rg, rg)] += AGG - AGI @ X[:, :len(G)]
+        g[rg] += fi[G] - AGI @ X[:, len(G):]
+        parts.append((sd, I, G, rg, AII, AIG, fi))
+    uG = np.linalg.solve(S, g)
+    x = np.zeros((dec.grid.n_edges, nrhs), np.complex128)
+    x[gam] = uG
+    for sd, I, G, rg, AII, AIG, fi in parts:
+        if len(I):
+            x[sd.edges[I]] = np.linalg.solve(AII, fi[I] - AIG @ uG[rg])
     return x

@@ -145,13 +145,15 @@ def interface_faces(dec: Decomposition, sd: Subdomain, alpha):
 
 
 def subdomain_matrix(w, dec: Decomposition, sd: Subdomain):
-    """A_i on the subdomain's local dofs (sorted global edge order)."""
+    """A_i on the subdomain's local dofs (sorted global edge order); the interface coefficient
+    is w.alpha when given, else jk (the decomposed solution does not depend on it)."""
     g = dec.grid
     ci, cj, ck = g.cell_ijk()
     lo, hi = sd.cell_lo, sd.cell_hi
     cells = np.flatnonzero((ci >= lo[0]) & (ci < hi[0]) & (cj >= lo[1]) & (cj < hi[1])
                            & (ck >= lo[2]) & (ck < hi[2]))
-    faces = fem.abc_faces(g, w.k, lo, hi) + interface_faces(dec, sd, 1j * w.k)
+    alpha = 1j * w.k if getattr(w, "alpha", None) is None else complex(w.alpha)
+    faces = fem.abc_faces(g, w.k, lo, hi) + interface_faces(dec, sd, alpha)
     r, c, v = fem.assemble(g, w.eps, w.k, cells=cells, extra_faces=faces)
     loc = -np.ones(g.n_edges, np.int64)
     loc[sd.edges] = np.arange(len(sd.edges))

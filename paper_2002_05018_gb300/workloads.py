@@ -49,6 +49,7 @@ class Workload:
     probes: np.ndarray | None = None    # int64 global edge ids (objective)
     fd_cells: np.ndarray | None = None  # int64 cell ids (finite differences)
     seed: int = 0
+    alpha: complex | None = None  # interface loss/gain coefficient (None: jk)
 
     @property
     def n_cells(self) -> int:

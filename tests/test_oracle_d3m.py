@@ -119,3 +119,35 @@ def test_config1_structure_numbers():
     dec = decomp.decompose(w)
     assert [len(s.edges) for s in dec.subs] == [1680] * 4
     assert len(dec.lm_edge) == 636 and len(dec.blocks) == 4
+
+
+@pytest.mark.parametrize("alpha_scale", [1.0, 0.3, 4.0, 1.0 - 1.0j])
+def test_interface_coefficient_does_not_change_the_solution(alpha_scale):
+    """The interface loss/gain alpha T_f cancels between the two sides of every
+    cut face, so the decomposed solution equals the global one for any alpha
+    (here alpha = scale * jk); the multipliers and K do depend on it."""
+    w = W.tiny(6, 5, 4, 3, 2, 1, seed=12, nrhs=2, jitter=True)
+    w.alpha = alpha_scale * 1j * w.k
+    f = fem.rhs_planewave(w)
+    r = d3m.solve(w, f, return_all=True)
+    xg = fem.solve_global(w, f)
+    assert np.abs(r["x"] - xg).max() < 1e-10 * np.abs(xg).max()
+    if alpha_scale != 1.0:
+        w.alpha = None
+        r1 = d3m.solve(w, f, return_all=True)
+        assert np.abs(r1["lam"] - r["lam"]).max() > 1e-3 * np.abs(r1["lam"]).max()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_primal_schur_equals_global_and_d3m(case):
+    """The primal substructuring route (interface edges as unknowns) and the
+    multiplier route of Eq. (1) reach the same solution as the global solve."""
+    c = dict(case)
+    jit = c.pop("jitter", False)
+    w = W.tiny(c["nx"], c["ny"], c["nz"], c["px"], c["py"], c["pz"], seed=5, nrhs=2, jitter=jit)
+    f = fem.rhs_planewave(w)
+    xs = d3m.solve_primal_schur(w, f)
+    xg = fem.solve_global(w, f)
+    xd = d3m.solve(w, f)
+    assert np.abs(xs - xg).max() < 1e-10 * np.abs(xg).max()
+    assert np.abs(xs - xd).max() < 1e-10 * np.abs(xg).max()
