@@ -96,7 +96,7 @@ __device__ __forceinline__ cx<T> from_d(double2 a) {
   } while (0)
 
 constexpr int NB = 32;         // panel width (columns per panel kernel)
-constexpr int LSTR = NB + 1;   // shared-memory row stride of the cluster panel (bank spread)
+constexpr int LSTR = NB + 2;   // shared-memory row stride of the cluster panel (16-byte rows, bank spread)
 constexpr int UT = 64;         // trailing-update tile edge
 constexpr int UK = 16;         // trailing-update k chunk
 constexpr int PANEL_THREADS = 512;
@@ -506,6 +506,32 @@ __device__ __forceinline__ ArgMaxT<T> block_argmax1(ArgMaxT<T> x, ArgMaxT<T> *sh
   return warp_argmaxT(x);
 }
 
+// acc - sum_{t<j} L[t] w[t]: the column update of one panel row.  For fp32,
+// two complex terms per 16-byte shared-memory load and two independent
+// accumulators (the dependent FMA chain halves); rows and w are 16-byte aligned.
+__device__ __forceinline__ cx<float> col_update(cx<float> acc, const cx<float> *__restrict__ L,
+                                                const cx<float> *__restrict__ w, int j) {
+  cx<float> acc1 = mk<float>(0.f, 0.f);
+  int t = 0;
+#pragma unroll 4
+  for (; t + 1 < j; t += 2) {
+    const float4 l = *reinterpret_cast<const float4 *>(L + t);
+    const float4 v = *reinterpret_cast<const float4 *>(w + t);
+    acc = cfms(acc, mk<float>(l.x, l.y), mk<float>(v.x, v.y));
+    acc1 = cfms(acc1, mk<float>(l.z, l.w), mk<float>(v.z, v.w));
+  }
+  if (t < j) acc = cfms(acc, L[t], w[t]);
+  acc.re += acc1.re;
+  acc.im += acc1.im;
+  return acc;
+}
+__device__ __forceinline__ cx<double> col_update(cx<double> acc, const cx<double> *__restrict__ L,
+                                                 const cx<double> *__restrict__ w, int j) {
+#pragma unroll 4
+  for (int t = 0; t < j; ++t) acc = cfms(acc, L[t], w[t]);
+  return acc;
+}
+
 // the pivot decision of one column
 template <typename T>
 struct PivotDec {
@@ -624,7 +650,8 @@ __global__ void __launch_bounds__(512)
   int *spos = reinterpret_cast<int *>(wr + rcap);         // [rcap] logical row of each own slot
   int *p2s = spos + rcap;                                 // [mcap] logical row - k0 -> global slot
   __shared__ PanelBox<T> box[2];
-  __shared__ cx<T> wrow[NB], wrow2[NB];
+  __shared__ __align__(16) cx<T> wrow[NB];
+  __shared__ __align__(16) cx<T> wrow2[NB];
   __shared__ cx<T> Dd[NB], Do[NB];    // D of the panel's pivots: diag / 2x2 coupling
   __shared__ PivotDec<T> pd;          // fp64 path: the decision of thread 0
   __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
@@ -693,8 +720,7 @@ __global__ void __launch_bounds__(512)
       if (i < k) continue;
       cx<T> acc = qi == 0 ? cur0 : cur1;
       const cx<T> *Lq = Ls + (size_t)q * LSTR;
-#pragma unroll 4
-      for (int t = 0; t < j; ++t) acc = cfms(acc, Lq[t], wrow[t]);  // j terms (not NB predicated)
+      acc = col_update(acc, Lq, wrow, j);  // j terms (not NB predicated)
       wk[q] = acc;
       if (i > k && i < p) loc = amaxT(loc, ArgMaxT<T>{cabs1T(acc), i});
     }
@@ -752,8 +778,7 @@ __global__ void __launch_bounds__(512)
         if (i < k) continue;
         cx<T> acc = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
         const cx<T> *Lq = Ls + (size_t)q * LSTR;
-#pragma unroll 4
-        for (int t = 0; t < j; ++t) acc = cfms(acc, Lq[t], wrow2[t]);
+        acc = col_update(acc, Lq, wrow2, j);
         wr[q] = acc;
         if (i != imax && i < p) rl = amaxT(rl, ArgMaxT<T>{cabs1T(acc), i});
       }
@@ -1604,16 +1629,19 @@ constexpr int BSPLIT = 256;
 // coalesce for column- and row-major operands alike.  Triangular operands
 // (stored with explicit zeros) bound the k range of a tile: mode 1 A lower
 // (k <= i), 2 B lower (k >= j), 3 A upper (k >= i).
+// koff: the item's first k in the full product (split-K pieces of a
+// triangular product bound their k range with the global index).
 struct CgItem {
   int64_t a, b, c, gath;
   int32_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
   int32_t M, N, K, mode, abuf, bbuf, cbuf, beta;
   float alpha;
   int32_t tile0;
+  int32_t koff;
 };
 template <typename T>
 struct CgBufs {
-  cx<T> *p[6];
+  cx<T> *p[7];
 };
 constexpr int CG_BN = 64;
 // K chunk: 48 for the small fp32 tiles (the launches of the levels with few
@@ -1644,9 +1672,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
   const int ti = t - it.tile0, tm = ti % ntm, tn = ti / ntm;
   const int i0 = tm * BM, j0 = tn * BN;
   int klo = 0, khi = it.K;
-  if (it.mode == 1) khi = min(it.K, i0 + BM);
-  if (it.mode == 2) klo = j0;
-  if (it.mode == 3) klo = i0;
+  if (it.mode == 1) khi = min(it.K, i0 + BM - it.koff);
+  if (it.mode == 2) klo = max(0, j0 - it.koff);
+  if (it.mode == 3) klo = max(0, i0 - it.koff);
   __shared__ cx<T> As[KC][BM + 1];
   __shared__ cx<T> Bs[KC][BN + 1];
   // thread -> (row, column) of its outputs: rows fast for column-major C
@@ -1745,6 +1773,45 @@ static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, co
     k_cgemm<T, 64><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
   else
     k_cgemm<T, (sizeof(T) == 4 ? 128 : 64)><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
+}
+
+// Split-K: a product whose launch has few output tiles and a long k range is
+// cut into S pieces along k, each written (scaled by alpha, beta = 0) to its
+// own M x N block of a partial buffer (row-major, RHS fastest); this item
+// list then adds them to the target in a fixed order (deterministic).
+struct SkItem {
+  int64_t c, p;        // target offset in buffer cbuf; first partial block in the partial buffer
+  int32_t c_rs, c_cs, M, N, S, cbuf, beta;
+  int32_t elem0;       // first element index of this item in the launch
+};
+template <typename T>
+__global__ void k_splitk_reduce(const SkItem *__restrict__ items, int nitems, int64_t nelem, CgBufs<T> bufs,
+                                const cx<T> *__restrict__ part) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nelem; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nitems - 1;  // last item with elem0 <= e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].elem0 <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const SkItem it = items[lo];
+    const int64_t q = e - it.elem0;
+    const int i = (int)(q / it.N), j = (int)(q % it.N);
+    const int64_t mn = (int64_t)it.M * it.N;
+    cx<T> acc = mk<T>(0, 0);
+    for (int s2 = 0; s2 < it.S; ++s2) {
+      const cx<T> v = part[it.p + s2 * mn + q];
+      acc.re += v.re;
+      acc.im += v.im;
+    }
+    cx<T> *d = bufs.p[it.cbuf] + it.c + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
+    if (it.beta) {
+      const cx<T> o = *d;
+      acc.re += o.re;
+      acc.im += o.im;
+    }
+    *d = acc;
+  }
 }
 
 // Inverse of each 32x32 unit-lower diagonal block of L11 (2x2 couplings are
@@ -2143,6 +2210,9 @@ struct DeviceState {
   // per level, (item0, nitems, ntiles) of: forward L11^{-1}, forward L21,
   // backward L21^T (split partials), backward L11^{-T}
   std::vector<std::array<int, 16>> sol_lvl;  // (item0, nitems, ntiles, row tile) per kind
+  std::vector<std::array<int, 12>> sk_lvl;   // per kind: split-K reduce (item0, nitems, elements)
+  SkItem *sk_items = nullptr;
+  void *skp = nullptr;                       // split-K partial blocks
   int sol_r = 0;
   void *Y2 = nullptr;
   cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;  // captured substitution sweeps
@@ -2871,7 +2941,7 @@ static int factor_t(Ctx &c) {
         dim3 gd((unsigned)((d->level_maxp[l] + 31) / 32), nf);
         k_trinv_diag<T><<<gd, 32, 0, si>>>(lvl, ft, arena, d->linv_off + P.level_ptr[l], Li);
         ++nl;
-        const CgBufs<T> ib{{arena, Li, (cx<T> *)d->tmp_inv, nullptr, nullptr, nullptr}};
+        const CgBufs<T> ib{{arena, Li, (cx<T> *)d->tmp_inv, nullptr, nullptr, nullptr, nullptr}};
         for (auto &st : d->inv_stage[l]) {
           launch_cgemm<T>(st[3], st[2], d->inv_items + st[0], st[1], ib, nullptr, si);
           ++nl;
@@ -3200,7 +3270,10 @@ static int solve_items(Ctx &c, int r) {
   const Plan &P = c.plan;
   const bool mixed = c.opt.precision == D3M_MIXED;
   std::vector<CgItem> items;
+  std::vector<SkItem> skitems;
+  int64_t skmax = 0;
   d->sol_lvl.assign(P.n_levels, {});
+  d->sk_lvl.assign(P.n_levels, {});
   int BM = 128;
   auto tiles_of = [&](const CgItem &g) { return ((g.M + BM - 1) / BM) * ((g.N + CG_BN - 1) / CG_BN); };
   for (int l = 0; l < P.n_levels; ++l) {
@@ -3232,6 +3305,7 @@ static int solve_items(Ctx &c, int r) {
       }
       BM = best;
       int first = (int)items.size(), tiles = 0;
+      std::vector<CgItem> kitems;  // this launch's items before any split
       for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
         const int f = P.level_fronts[i];
         const int pf = (int)(P.sn_end[f] - P.sn_start[f]);
@@ -3251,9 +3325,7 @@ static int solve_items(Ctx &c, int r) {
           g.c = P.y_off[f] * r; g.c_rs = r; g.c_cs = 1;
           g.M = pf; g.K = pf;
           g.abuf = 1; g.bbuf = 2; g.cbuf = 3; g.beta = 0; g.alpha = 1.f;
-          g.tile0 = tiles;
-          tiles += tiles_of(g);
-          items.push_back(g);
+          kitems.push_back(g);
         } else if (kind == 1) {  // Y[p:m] -= L21 y[0:p]
           if (mf == pf || pf == 0) continue;
           g.a = P.front_off[f] + pf; g.a_rs = 1; g.a_cs = mf;
@@ -3261,9 +3333,7 @@ static int solve_items(Ctx &c, int r) {
           g.c = (P.y_off[f] + pf) * r; g.c_rs = r; g.c_cs = 1;
           g.M = mf - pf; g.K = pf;
           g.abuf = 0; g.bbuf = mixed ? 3 : 2; g.cbuf = 2; g.beta = 1; g.alpha = -1.f;
-          g.tile0 = tiles;
-          tiles += tiles_of(g);
-          items.push_back(g);
+          kitems.push_back(g);
         } else {  // partials of L21^T x over row splits
           if (mf == pf || pf == 0) continue;
           const int S = (mf - pf + BSPLIT - 1) / BSPLIT;
@@ -3275,12 +3345,69 @@ static int solve_items(Ctx &c, int r) {
             h.c = (d->part_off_h[i] + (int64_t)q * pf) * r; h.c_rs = r; h.c_cs = 1;
             h.M = pf; h.K = std::min(BSPLIT, mf - pf - rb);
             h.abuf = 0; h.bbuf = 4; h.cbuf = 5; h.beta = 0; h.alpha = 1.f;
-            h.tile0 = tiles;
-            tiles += tiles_of(h);
-            items.push_back(h);
+            kitems.push_back(h);
           }
         }
       }
+      // split-K for narrow launches with a long k range (the top levels of
+      // the tree: few fronts, p of a few hundred): S pieces along k into the
+      // partial buffer, added to their targets by k_splitk_reduce
+      int64_t nt0 = 0, kmax = 0;
+      for (const CgItem &g : kitems) {
+        nt0 += tiles_of(g);
+        kmax = std::max<int64_t>(kmax, g.K);
+      }
+      int S = 1;
+      if (kind != 2 && nt0 > 0 && nt0 < 152 && kmax >= 96)
+        S = (int)std::min<int64_t>({8, (304 + nt0 - 1) / nt0, kmax / 48});
+      const int sk_first = (int)skitems.size();
+      int64_t sk_elems = 0, pofs = 0;
+      for (const CgItem &g : kitems) {
+        if (S <= 1) {
+          CgItem h = g;
+          h.tile0 = tiles;
+          tiles += tiles_of(h);
+          items.push_back(h);
+          continue;
+        }
+        const int Kc = ((g.K + S - 1) / S + 15) / 16 * 16;
+        const int64_t mn = (int64_t)g.M * g.N;
+        int pieces = 0;
+        for (int kb = 0; kb < g.K; kb += Kc, ++pieces) {
+          CgItem h = g;
+          h.koff = kb;
+          h.K = std::min(Kc, g.K - kb);
+          h.a += (int64_t)kb * g.a_cs;
+          if (g.gath >= 0) h.gath += kb;
+          else h.b += (int64_t)kb * g.b_rs;
+          h.c = pofs + (int64_t)pieces * mn;
+          h.c_rs = g.N;
+          h.c_cs = 1;
+          h.cbuf = 6;
+          h.beta = 0;
+          h.tile0 = tiles;
+          tiles += tiles_of(h);
+          items.push_back(h);
+        }
+        SkItem q{};
+        q.c = g.c;
+        q.p = pofs;
+        q.c_rs = g.c_rs;
+        q.c_cs = g.c_cs;
+        q.M = g.M;
+        q.N = g.N;
+        q.S = pieces;
+        q.cbuf = g.cbuf;
+        q.beta = g.beta;
+        q.elem0 = (int32_t)sk_elems;
+        skitems.push_back(q);
+        sk_elems += mn;
+        pofs += (int64_t)pieces * mn;
+      }
+      skmax = std::max(skmax, pofs);
+      d->sk_lvl[l][3 * kind + 0] = sk_first;
+      d->sk_lvl[l][3 * kind + 1] = (int)skitems.size() - sk_first;
+      d->sk_lvl[l][3 * kind + 2] = (int)sk_elems;
       d->sol_lvl[l][4 * kind + 0] = first;
       d->sol_lvl[l][4 * kind + 1] = (int)items.size() - first;
       d->sol_lvl[l][4 * kind + 2] = tiles;
@@ -3294,6 +3421,18 @@ static int solve_items(Ctx &c, int r) {
   }
   if (items.empty()) items.push_back(CgItem{});
   CUDA_TRY(upload(d, &d->sol_items, items));
+  for (void *q : {(void *)d->sk_items, d->skp})
+    if (q) {
+      cudaFree(q);
+      d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), q), d->allocs.end());
+    }
+  d->sk_items = nullptr;
+  d->skp = nullptr;
+  if (skitems.empty()) skitems.push_back(SkItem{});
+  CUDA_TRY(upload(d, &d->sk_items, skitems));
+  const size_t esz = c.opt.precision == D3M_FP64 ? sizeof(cx<double>) : sizeof(cx<float>);
+  CUDA_TRY(cudaMalloc(&d->skp, std::max<int64_t>(skmax, 1) * esz));
+  d->allocs.push_back(d->skp);
   d->sol_r = r;
   return D3M_OK;
 }
@@ -3312,7 +3451,16 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
   cx<T> *Li = (cx<T> *)d->linv;
   const bool use_inv = sizeof(T) == 4;  // L11^{-1} exists for the mixed factors only
   constexpr int RC = 8;
-  const CgBufs<T> bufs{{arena, Li, Y, Y2, (cx<T> *)d->xM, (cx<T> *)d->part}};
+  const CgBufs<T> bufs{{arena, Li, Y, Y2, (cx<T> *)d->xM, (cx<T> *)d->part, (cx<T> *)d->skp}};
+  // the split-K reduction of launch `kind` of level l (if that launch was split)
+  auto reduce = [&](int l, int kind) -> int64_t {
+    const auto &k3 = d->sk_lvl[l];
+    if (k3[3 * kind + 1] == 0) return 0;
+    const int64_t ne = k3[3 * kind + 2];
+    k_splitk_reduce<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((ne + 255) / 256, 1216)), 256, 0, s>>>(
+        d->sk_items + k3[3 * kind + 0], k3[3 * kind + 1], ne, bufs, (const cx<T> *)d->skp);
+    return 1;
+  };
   int64_t nl = 0;
   if (dir & 1) {
   PROF_BEGIN(PC_FWD);
@@ -3333,6 +3481,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const auto &sl = d->sol_lvl[l];
     if (use_inv) {
       launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s);
+      nl += reduce(l, 0);
       dim3 gdv((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
     } else {
@@ -3342,6 +3491,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     nl += 2;
     if (sl[5] > 0) {
       launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s);
+      nl += reduce(l, 1);
       ++nl;
     }
   }
@@ -3363,6 +3513,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
       dim3 gw((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
       launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s);
+      nl += reduce(l, 3);
       k_bwd_out<T><<<gw, 256, 0, s>>>(lvl, ft, d->perm, Y2, (cx<T> *)d->xM, r);
       nl += 3;
     } else {
