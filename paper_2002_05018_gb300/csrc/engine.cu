@@ -450,10 +450,13 @@ namespace cg = cooperative_groups;
 // inverse of a pivot in the factor precision (scales the panel's L columns);
 // fp32 scales against overflow, fp64 uses the Newton reciprocal below
 __device__ __forceinline__ cx<float> cinv_t(cx<float> a) {
+  // conj(a) / |a|^2 with a scaled by its largest component (no overflow);
+  // two correctly rounded reciprocals instead of three divisions
   float s = fmaxf(fabsf(a.re), fabsf(a.im));
   if (s == 0.0f) return mk<float>(0, 0);
-  float ar = a.re / s, ai = a.im / s;
-  float r = 1.0f / (s * (ar * ar + ai * ai));
+  const float is = __frcp_rn(s);
+  float ar = a.re * is, ai = a.im * is;
+  float r = __frcp_rn(s * (ar * ar + ai * ai));
   return mk<float>(ar * r, -ai * r);
 }
 __device__ __forceinline__ cx<double> cinv_t(cx<double> a) {
@@ -477,7 +480,7 @@ __device__ __forceinline__ bool bk_less(T lhs, T rhs, Exact exact) {
   return exact();
 }
 
-// warp arg-max, the result broadcast from lane 0 (uniform even for NaN input)
+// warp arg-max, the same result in every lane (uniform even for NaN input)
 template <typename T>
 __device__ __forceinline__ ArgMaxT<T> warp_argmaxT(ArgMaxT<T> x) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -489,6 +492,19 @@ __device__ __forceinline__ ArgMaxT<T> warp_argmaxT(ArgMaxT<T> x) {
   x.v = __shfl_sync(0xffffffffu, x.v, 0);
   x.i = __shfl_sync(0xffffffffu, x.i, 0);
   return x;
+}
+// fp32: two warp reductions (redux.sync).  Non-negative floats order like
+// their bit patterns; "no candidate" (-1) and NaN map to key 0, so they never
+// beat a real candidate; among equal maxima the lowest index wins, as in amaxT.
+template <>
+__device__ __forceinline__ ArgMaxT<float> warp_argmaxT<float>(ArgMaxT<float> x) {
+  const unsigned key = x.v >= 0.0f ? __float_as_uint(x.v) : 0u;
+  const unsigned km = __reduce_max_sync(0xffffffffu, key);
+  const unsigned idx = __reduce_min_sync(0xffffffffu, key == km ? (unsigned)x.i : 0x7fffffffu);
+  ArgMaxT<float> r;
+  r.i = (int)idx;
+  r.v = idx == 0x7fffffffu ? -1.0f : __uint_as_float(km);
+  return r;
 }
 // Block arg-max with one barrier: the warp results go to half `par` of sh
 // (2 x 32 entries) and every warp reduces them itself.  Consecutive calls use
@@ -650,8 +666,8 @@ __global__ void __launch_bounds__(512)
   int *spos = reinterpret_cast<int *>(wr + rcap);         // [rcap] logical row of each own slot
   int *p2s = spos + rcap;                                 // [mcap] logical row - k0 -> global slot
   __shared__ PanelBox<T> box[2];
-  __shared__ __align__(16) cx<T> wrow[NB];
-  __shared__ __align__(16) cx<T> wrow2[NB];
+  __shared__ __align__(16) cx<T> wrow[(512 / 32) * NB];   // one staged row per warp
+  __shared__ __align__(16) cx<T> wrow2[(512 / 32) * NB];
   __shared__ cx<T> Dd[NB], Do[NB];    // D of the panel's pivots: diag / 2x2 coupling
   __shared__ PivotDec<T> pd;          // fp64 path: the decision of thread 0
   __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
@@ -684,14 +700,17 @@ __global__ void __launch_bounds__(512)
   long long cmac = 0;        // complex MACs of the column updates (thread 0)
   float minpiv = 3.0e38f;    // smallest |d| / colmax of the 1x1 pivots (thread 0)
   // W row of logical row `row` for the panel columns 0..j-1: L[row, :] D
+  // Every warp stages the row into its own buffer (lane t: element t), so
+  // only a warp barrier separates the staging from its use.
   auto load_wrow = [&](int row, cx<T> *dst) {
     int g = p2s[row - k0];
     int o = g / R, sl = g - o * R;
     const cx<T> *Lr = (CS == 1 ? Ls : cl.map_shared_rank(Ls, o)) + (size_t)sl * LSTR;
-    if (tid < NB) {
+    const int lane = tid & 31;
+    {
       cx<T> v = mk<T>(0, 0);
-      if (tid < j) {
-        int t = tid;
+      if (lane < j) {
+        int t = lane;
         cx<T> l = Lr[t];
         if (Dz[t] == 1) {
           v = cmul(l, Dd[t]);
@@ -701,8 +720,9 @@ __global__ void __launch_bounds__(512)
           v = cfma(cmul(Lr[t - 1], Do[t]), l, Dd[t]);
         }
       }
-      dst[tid] = v;
+      dst[(tid >> 5) * NB + lane] = v;
     }
+    __syncwarp();
   };
   // value of own-CTA slot array a at logical row `row` (CS == 1: any row)
   auto own_at = [&](const cx<T> *a, int row) { return a[p2s[row - k0] - rank * R]; };
@@ -713,14 +733,14 @@ __global__ void __launch_bounds__(512)
     }
     // ---- (1) updated column k for own slots, local pivot search
     load_wrow(k, wrow);
-    __syncthreads();
+    const cx<T> *wrw = wrow + (tid >> 5) * NB;  // this warp's copy
     ArgMaxT<T> loc{(T)-1, 0x7fffffff};
     for (int q = tid, qi = 0; q < ns; q += nth, ++qi) {
       int i = spos[q];
       if (i < k) continue;
       cx<T> acc = qi == 0 ? cur0 : cur1;
       const cx<T> *Lq = Ls + (size_t)q * LSTR;
-      acc = col_update(acc, Lq, wrow, j);  // j terms (not NB predicated)
+      acc = col_update(acc, Lq, wrw, j);  // j terms (not NB predicated)
       wk[q] = acc;
       if (i > k && i < p) loc = amaxT(loc, ArgMaxT<T>{cabs1T(acc), i});
     }
@@ -771,14 +791,14 @@ __global__ void __launch_bounds__(512)
       const int imax = d.imax;
       // ---- (2) updated column imax for own slots
       load_wrow(imax, wrow2);
-      __syncthreads();
+      const cx<T> *wrw2 = wrow2 + (tid >> 5) * NB;
       ArgMaxT<T> rl{(T)-1, 0x7fffffff};
       for (int q = tid; q < ns; q += nth) {
         int i = spos[q];
         if (i < k) continue;
         cx<T> acc = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
         const cx<T> *Lq = Ls + (size_t)q * LSTR;
-        acc = col_update(acc, Lq, wrow2, j);
+        acc = col_update(acc, Lq, wrw2, j);
         wr[q] = acc;
         if (i != imax && i < p) rl = amaxT(rl, ArgMaxT<T>{cabs1T(acc), i});
       }
