@@ -1239,9 +1239,13 @@ static cudaError_t launch_panel(int cs, int pmax, int mmax, int nf, const int32_
   int rcap = (pmax + cs - 1) / cs;
   if (rcap > 2 * 512) return cudaErrorInvalidValue;  // k_panel_cl keeps two slots per thread
   const int mcap = pmax;
+  // as many threads as one slot per row needs (whole warps, 64 to 512): warps
+  // without rows would only add their share of every column's staging,
+  // reductions and decision to the issue slots
+  const int nth = std::min(512, std::max(64, (rcap + 31) / 32 * 32));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nf * cs));
-  cfg.blockDim = dim3(512);
+  cfg.blockDim = dim3(nth);
   cfg.dynamicSmemBytes = panel_cl_smem(rcap, mcap, sizeof(cx<T>));
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
