@@ -134,13 +134,14 @@ def _sum_over_ranks(ws, v):
     return v if ws == 1 else _reduce(ws, v, dist.ReduceOp.SUM)
 
 
-def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=False, dev_index=0, cache=None):
+def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=False, dev_index=0, cache=None,
+                  update_kernel=0):
     """Times `steps` steps (factor + solve) of one precision, then runs the same
     steps again with the library's per-kernel-class CUDA events on (eager
     launches) for the kernel breakdown and the roofline.  Returns a dict."""
     import torch
     from paper_2002_05018_gb300 import d3m
-    s = d3m.Solver.from_workload(w, precision=prec, stream=stream, profile=False,
+    s = d3m.Solver.from_workload(w, precision=prec, stream=stream, profile=False, update_kernel=update_kernel,
                                  autotune_cache=None if cache is None else f"{cache}.{'mixed' if prec else 'fp64'}")
     st0 = s.stats()
     factor_flops = st0["flops_interior"] + st0["flops_domain"] + st0["flops_k"]
@@ -430,6 +431,9 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--update-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="mixed update scheme: 0 per-level autotuned (default), 1 right-looking FMA, "
+                         "2 deferred tensor-core Schur products on every level (for profiling a small workload)")
     ap.add_argument("--ncu-range", action="store_true",
                     help="after the timed steps, run one more mixed step (factor graph + solve) between "
                          "cudaProfilerStart/Stop, for ncu --profile-from-start off")
@@ -493,7 +497,7 @@ def main():
     torch.cuda.synchronize()
 
     mixed = run_precision(w, d3m.MIXED, args.steps, args.warmup, ws, stream, rhs_dev, sample_clocks=(rank == 0),
-                          dev_index=dev, cache=args.autotune_cache)
+                          dev_index=dev, cache=args.autotune_cache, update_kernel=args.update_kernel)
     if args.ncu_range:
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
