@@ -109,8 +109,9 @@ typedef struct {
                            the update rows (W21 = F21 P^T L11^{-T}, L21 = W21
                            D^{-1}) and the Schur complement (F22 - L21 W21^T)
                            of every front of the level are two batched complex
-                           products on the tcgen05 tensor cores with 3xTF32 split
-                           operands staged by TMA */
+                           products on the tcgen05 tensor cores: each fp32 operand
+                           split into three bf16 planes (BF16x3), staged by TMA,
+                           fp32 accumulation in tensor memory */
   int32_t autotune;     /* 0 = tune on the first d3m_factor (default): the update
                            kernel and the panel cluster size of every tree level
                            are timed with CUDA events over two trial
@@ -136,6 +137,12 @@ typedef struct {
   int32_t gmres_restart;/* GMRES-IR: Krylov steps per correction; 0 -> 20 (<= 200) */
   double gmres_tol;     /* GMRES-IR: relative 2-norm reduction of each correction
                            equation's residual; 0 -> 1e-4 */
+  double alpha_re, alpha_im; /* interface loss/gain coefficient alpha of the
+                           subdomain matrices (+alpha T_f on the side facing the
+                           higher subdomain index, -alpha T_f on the other; the
+                           Theory section's "loss or gain at the interfaces"):
+                           0, 0 -> jk.  The two sides cancel, so the solution E
+                           does not depend on alpha; K_D, K and lambda do. */
 } d3m_options;
 /* d3m_setup returns D3M_EINVAL (and the context, for d3m_last_error) when an
  * option lies outside the values listed above. */

@@ -461,6 +461,9 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   for (int axis = 0; axis < 3; ++axis)
     for (int side = 0; side < 2; ++side) face_matrix(p.h, axis, side, T[2 * axis + side]);
   const cplx jk(0.0, k);
+  // interface loss/gain coefficient (d3m_options.alpha_re/im; 0 -> jk)
+  const cplx alpha = (ctx.opt.alpha_re == 0.0 && ctx.opt.alpha_im == 0.0) ? jk
+                                                                         : cplx(ctx.opt.alpha_re, ctx.opt.alpha_im);
   std::vector<Trip> trips;
   for (int s = 0; s < p.nsub; ++s) {
     int64_t m0 = sub_m0[s];
@@ -510,7 +513,7 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
                 int npos[3] = {pos[0], pos[1], pos[2]};
                 npos[axis] += side ? 1 : -1;
                 int nb = sub_id(p, npos[0], npos[1], npos[2]);
-                add_block(e, T[2 * axis + side], nb > s ? jk : -jk);  // interface loss / gain
+                add_block(e, T[2 * axis + side], nb > s ? alpha : -alpha);  // interface loss / gain
               }
             }
         }

@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32), ("panel_kernel", ctypes.c_int32),
                 ("update_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("autotune_cache", ctypes.c_char_p), ("lookahead", ctypes.c_int32),
-                ("refine_method", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("gmres_tol", ctypes.c_double)]
+                ("refine_method", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("gmres_tol", ctypes.c_double),
+                ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -138,7 +139,7 @@ class Solver:
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
                  update_kernel=0, autotune=0, autotune_cache=None, lookahead=0, refine_method=0,
-                 gmres_restart=0, gmres_tol=0.0):
+                 gmres_restart=0, gmres_tol=0.0, alpha=None):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -154,7 +155,8 @@ class Solver:
         self._cache = None if autotune_cache is None else str(autotune_cache).encode()
         opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile),
                       int(panel_kernel), int(update_kernel), int(autotune), self._cache, int(lookahead),
-                      int(refine_method), int(gmres_restart), float(gmres_tol))
+                      int(refine_method), int(gmres_restart), float(gmres_tol),
+                      0.0 if alpha is None else complex(alpha).real, 0.0 if alpha is None else complex(alpha).imag)
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))
@@ -163,6 +165,7 @@ class Solver:
 
     @classmethod
     def from_workload(cls, w, precision=FP64, **kw):
+        kw.setdefault("alpha", getattr(w, "alpha", None))
         return cls(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.eps, w.k, w.cx, w.cy, w.cz, pec=w.pec_edge,
                    precision=precision, **kw)
 

@@ -68,7 +68,7 @@ def _fake_run(ms_panel, ms_update, ms_tc=0.0):
 def test_precision_summary_roofline_keys():
     """The dominant class (by profiled time) gets "roofline", every other class
     "roofline_<class>", each against the peak of its own pipe; the tensor-core
-    class reports its fraction of the 3xTF32 ceiling as well."""
+    class reports its fraction of the BF16x3 ceiling as well."""
     sys.path.insert(0, ROOT)
     import bench
     peaks = {"alu": 80.55, "tensor": 900.0}
@@ -87,7 +87,7 @@ def test_precision_summary_roofline_keys():
         assert roof["ms_per_step"] == ms
         tc = roof if dom == "tc" else sub["roofline_tc"]
         assert tc["bound"] == "tensor" and tc["peak"] == 900.0
-        assert abs(tc["frac_of_3xtf32_ceiling"] - 3 * tc["frac"]) < 2e-3
+        assert abs(tc["frac_of_bf16x3_ceiling"] - 6 * tc["frac"]) < 4e-3
         assert sub["solve_rhs_per_s"] == round(64 / 45e-3, 1)
         assert sub["schedule"]["doubled_cluster_levels"] == 3
     # a run without deferred levels (fp64 leg) reports no tensor-core class

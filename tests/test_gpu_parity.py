@@ -436,3 +436,25 @@ def test_factor_graph_replay_bitwise(prec):
     x, info = s.solve(torch.tensor(f.T.copy(), device="cuda").t())
     assert info["max_resid"] < 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_interface_coefficient_sweep(precision):
+    """E does not depend on the interface loss/gain coefficient alpha (the two
+    sides of every cut face cancel): workload 1 with alpha = s jk for several
+    s, and a complex alpha, against the oracle's global solution; the
+    multipliers do change with alpha."""
+    _need_gpu()
+    w = W.make(1)
+    f = fem.rhs_planewave(w)
+    xg = fem.solve_global(w, f)
+    tol = 1e-10 if precision == d3m.FP64 else 1e-8
+    lams = []
+    for a in (None, 0.3j * w.k, 4j * w.k, (1 - 1j) * w.k):
+        w.alpha = a
+        s, x, info, _ = _solve_case(w, precision, f=f)
+        assert np.abs(x - xg).max() < tol * np.abs(xg).max(), a
+        lams.append(s.lam(1))
+        s.close()
+    w.alpha = None
+    assert np.abs(lams[1] - lams[0]).max() > 1e-3 * np.abs(lams[0]).max()

@@ -133,3 +133,24 @@ def test_setup_rejects_bad_options(kw):
         d3m.Solver.from_workload(w, **kw)
     assert ei.value.code == d3m.D3M_EINVAL
     assert "d3m_setup" in str(ei.value)
+
+
+def test_interface_coefficient_matches_oracle_entries():
+    """d3m_options.alpha sets the interface loss/gain term: the library's
+    assembled entries of M equal the oracle's subdomain matrices for a
+    non-default alpha (same check as for the default, row by row)."""
+    from oracle import decomp
+    w = W.tiny(4, 3, 3, 2, 1, 1, seed=6)
+    w.alpha = 2.5 - 0.7j
+    s = d3m.Solver.from_workload(w)
+    ent = s.structure(d3m.M_ENTRIES)
+    mm = s.structure(d3m.M_MAP)
+    s.close()
+    dec = decomp.decompose(w)
+    for sd in dec.subs:
+        A = sd.A.toarray()
+        loc = {int(e): i for i, e in enumerate(sd.edges)}
+        sel = (mm[ent[:, 0].astype(int), 0] == sd.index) & (mm[ent[:, 1].astype(int), 0] == sd.index)
+        for r, c, re, im in ent[sel]:
+            er, ec = mm[int(r), 1], mm[int(c), 1]
+            assert abs(A[loc[er], loc[ec]] - (re + 1j * im)) < 1e-12 * np.abs(A).max()
