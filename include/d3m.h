@@ -143,6 +143,12 @@ typedef struct {
                            Theory section's "loss or gain at the interfaces"):
                            0, 0 -> jk.  The two sides cancel, so the solution E
                            does not depend on alpha; K_D, K and lambda do. */
+  int32_t solve_kernel; /* MIXED substitution products (L11^{-1}, L21, their
+                           transposes times the right-hand sides): 0 = complex
+                           BF16x3 on the tcgen05 tensor cores (default), the
+                           complex64 operands split into bf16 planes in the
+                           kernel, fp32 accumulation in tensor memory; 1 = fp32
+                           FMA.  FP64 always uses fp64 FMA. */
 } d3m_options;
 /* d3m_setup returns D3M_EINVAL (and the context, for d3m_last_error) when an
  * option lies outside the values listed above. */

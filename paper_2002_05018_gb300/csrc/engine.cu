@@ -1788,9 +1788,20 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
   }
 }
 
+#include "tc_solve.cuh"
+
+// bm: the row tile of the FMA kernel (32, 64 or 128), or 0 for the tensor-core
+// kernel (128 x 64 tiles, complex64 operands only); err / wait_cap are that
+// kernel's error flag and first-wait bound.
 template <typename T>
 static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, const CgBufs<T> &bufs,
-                         const int64_t *gidx, cudaStream_t s) {
+                         const int64_t *gidx, cudaStream_t s, int32_t *err = nullptr, int wait_cap = 0) {
+  if constexpr (sizeof(T) == 4) {
+    if (bm == 0) {
+      k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, err, wait_cap);
+      return;
+    }
+  }
   if (bm == 32)
     k_cgemm<T, 32><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
   else if (bm == 64 || sizeof(T) == 8)
@@ -2248,6 +2259,8 @@ struct DeviceState {
   int32_t *tc_err = nullptr;     // set by k_tc_gemm when a bounded wait expires
   int32_t *fin_err = nullptr;    // set when a pivot inverse is not finite
   int tc_wait_cap = 1 << 22;     // first-attempt bound of k_tc_gemm's mbarrier waits
+  int32_t *sv_err = nullptr;     // set by k_tc_cgemm (substitution products) when a bounded wait expires
+  int sv_wait_cap = 1 << 22;     // first-attempt bound of k_tc_cgemm's mbarrier waits
   std::vector<uint8_t> lvl_tc;   // per level: deferred tensor-core products (mixed)
   std::vector<int> lvl_cs;       // per level: panel cluster size (0 = global panel)
   bool tuned = false;
@@ -2688,7 +2701,10 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(dalloc(d, &d->swp, (size_t)3 * nsn * 2 * NB));  // three look-ahead slots
   CUDA_TRY(dalloc(d, &d->tc_err, 1));
   CUDA_TRY(dalloc(d, &d->fin_err, 1));
+  CUDA_TRY(dalloc(d, &d->sv_err, 1));
+  CUDA_TRY(cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, Q_SMEM));
   if (c.fault == "timeout") d->tc_wait_cap = 0;  // every first wait of k_tc_gemm expires at once
+  if (c.fault == "solve_timeout") d->sv_wait_cap = 0;  // the same for k_tc_cgemm (the substitution)
   d->update_grid_p.assign(P.n_levels, {});
   d->update_grid_r.assign(P.n_levels, {});
   for (int l = 0; l < P.n_levels; ++l)
@@ -3293,6 +3309,7 @@ static int solve_items(Ctx &c, int r) {
   if (d->sol_r == r && d->sol_items) return D3M_OK;
   const Plan &P = c.plan;
   const bool mixed = c.opt.precision == D3M_MIXED;
+  const bool tcs = mixed && c.opt.solve_kernel == 0;  // complex64 products on the tensor cores
   std::vector<CgItem> items;
   std::vector<SkItem> skitems;
   int64_t skmax = 0;
@@ -3309,6 +3326,7 @@ static int solve_items(Ctx &c, int r) {
       double bcost = 1e300;
       for (int bm : {32, 64, 128}) {
         if (bm == 128 && !mixed) continue;
+        if (tcs && bm != 128) continue;  // the tensor-core kernel's tiles are 128 rows
         BM = bm;
         int64_t t = 0;
         for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
@@ -3435,7 +3453,7 @@ static int solve_items(Ctx &c, int r) {
       d->sol_lvl[l][4 * kind + 0] = first;
       d->sol_lvl[l][4 * kind + 1] = (int)items.size() - first;
       d->sol_lvl[l][4 * kind + 2] = tiles;
-      d->sol_lvl[l][4 * kind + 3] = BM;
+      d->sol_lvl[l][4 * kind + 3] = tcs ? 0 : BM;  // 0: k_tc_cgemm
     }
   }
   if (d->sol_items) {
@@ -3504,7 +3522,8 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     }
     const auto &sl = d->sol_lvl[l];
     if (use_inv) {
-      launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s);
+      launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->sv_err,
+                      d->sv_wait_cap);
       nl += reduce(l, 0);
       dim3 gdv((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
@@ -3514,7 +3533,8 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     }
     nl += 2;
     if (sl[5] > 0) {
-      launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s);
+      launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s, d->sv_err,
+                      d->sv_wait_cap);
       nl += reduce(l, 1);
       ++nl;
     }
@@ -3530,13 +3550,15 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const int64_t *po = d->part_off + P.level_ptr[l];
     const auto &sl = d->sol_lvl[l];
     if (sl[9] > 0) {
-      launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s);
+      launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s, d->sv_err,
+                      d->sv_wait_cap);
       ++nl;
     }
     if (use_inv) {
       dim3 gw((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
-      launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s);
+      launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->sv_err,
+                      d->sv_wait_cap);
       nl += reduce(l, 3);
       k_bwd_out<T><<<gw, 256, 0, s>>>(lvl, ft, d->perm, Y2, (cx<T> *)d->xM, r);
       nl += 3;
@@ -3776,6 +3798,7 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   } else {
     k_cm_to_rm<<<grid1(n * r), 256, 0, s>>>((const double2 *)rhs, ldb, d->fe, n, r, cj);
   }
+  CUDA_TRY(cudaMemsetAsync(d->sv_err, 0, sizeof(int32_t), s));
   // first solve from f
   d->prof.reset();
   int64_t nl = 3;
@@ -3843,6 +3866,12 @@ static int solve_t(Ctx &c, const double *rhs, int64_t ldb, double *x, int64_t ld
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
+  int32_t sve = 0;
+  CUDA_TRY(cudaMemcpy(&sve, d->sv_err, sizeof sve, cudaMemcpyDeviceToHost));
+  if (sve) {
+    c.err = "d3m_solve: a tensor-core substitution tile gave up a bounded wait (its results were discarded)";
+    return D3M_ETIMEOUT;
+  }
   if (info) {
     info->iters = iters;
     info->max_resid = maxres;

@@ -866,8 +866,10 @@ extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double 
   else if (c.opt.refine_method != 0 && c.opt.refine_method != 1) bad = "refine_method not 0 or 1";
   else if (c.opt.gmres_restart < 1 || c.opt.gmres_restart > 200) bad = "gmres_restart not in 1..200";
   else if (!(c.opt.gmres_tol > 0 && c.opt.gmres_tol < 1)) bad = "gmres_tol not in (0, 1)";
-  else if (!c.fault.empty() && c.fault != "alloc" && c.fault != "pivot" && c.fault != "nan" && c.fault != "timeout")
-    bad = "D3M_FAULT not one of alloc, pivot, nan, timeout";
+  else if (c.opt.solve_kernel != 0 && c.opt.solve_kernel != 1) bad = "solve_kernel not 0 or 1";
+  else if (!c.fault.empty() && c.fault != "alloc" && c.fault != "pivot" && c.fault != "nan" && c.fault != "timeout" &&
+           c.fault != "solve_timeout")
+    bad = "D3M_FAULT not one of alloc, pivot, nan, timeout, solve_timeout";
   if (bad) {
     c.err = std::string("d3m_setup: ") + bad;
     *out = h;

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("update_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("autotune_cache", ctypes.c_char_p), ("lookahead", ctypes.c_int32),
                 ("refine_method", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("gmres_tol", ctypes.c_double),
-                ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double)]
+                ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double), ("solve_kernel", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -139,7 +139,7 @@ class Solver:
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
                  update_kernel=0, autotune=0, autotune_cache=None, lookahead=0, refine_method=0,
-                 gmres_restart=0, gmres_tol=0.0, alpha=None):
+                 gmres_restart=0, gmres_tol=0.0, alpha=None, solve_kernel=0):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -156,7 +156,8 @@ class Solver:
         opt = Options(precision, leaf_max, refine_tol, max_refine, _stream_handle(stream), int(profile),
                       int(panel_kernel), int(update_kernel), int(autotune), self._cache, int(lookahead),
                       int(refine_method), int(gmres_restart), float(gmres_tol),
-                      0.0 if alpha is None else complex(alpha).real, 0.0 if alpha is None else complex(alpha).imag)
+                      0.0 if alpha is None else complex(alpha).real, 0.0 if alpha is None else complex(alpha).imag,
+                      int(solve_kernel))
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))

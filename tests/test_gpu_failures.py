@@ -121,3 +121,21 @@ def test_fault_expired_wait_reports_timeout(monkeypatch):
     e = _factor_with_fault(monkeypatch, "timeout", precision=d3m.MIXED, update_kernel=2)
     assert e.code == d3m.D3M_ETIMEOUT
     _still_usable()
+
+
+def test_fault_expired_wait_in_solve_reports_timeout(monkeypatch):
+    """The same bound on the tensor-core substitution products: the factor
+    completes, d3m_solve reports D3M_ETIMEOUT (every tile gave up and wrote
+    nothing), and the next context factors and solves normally."""
+    _need_gpu()
+    monkeypatch.setenv("D3M_FAULT", "solve_timeout")
+    w = W.make(1)
+    s = d3m.Solver.from_workload(w, precision=d3m.MIXED)
+    monkeypatch.delenv("D3M_FAULT")
+    s.factor()
+    f = fem.rhs_planewave(w)
+    with pytest.raises(d3m.D3MError) as e:
+        s.solve(torch.tensor(f.T.copy(), device="cuda").t())
+    assert e.value.code == d3m.D3M_ETIMEOUT and "substitution" in str(e.value)
+    s.close()
+    _still_usable()

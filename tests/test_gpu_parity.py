@@ -342,6 +342,45 @@ def test_tensor_core_update_matches_fp32_fma(wk):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("wk", ["config3", "tiny70"])
+def test_tensor_core_substitution_matches_fp32_fma(wk):
+    """The substitution products on the tensor cores (complex BF16x3, operands
+    split in the kernel) against the fp32-FMA products on the same factors
+    (fixed schedule, so both contexts factor bitwise alike): one unrefined pass
+    agrees to fp32 rounding amplified by the factors' conditioning, both passes
+    are equally far from the fp64 solution, and refinement takes both to the
+    same tolerance in the same number of passes (give or take one)."""
+    _need_gpu()
+    # one right-hand side; 70 (two column tiles of 64, the second ragged)
+    w = W.make(3) if wk == "config3" else W.tiny(14, 12, 10, 2, 2, 2, seed=5, nrhs=70)
+    f = fem.rhs_planewave(w)
+    b = torch.tensor(f.T.copy(), device="cuda").t()
+    one, full = {}, {}
+    for sk in (0, 1):
+        s = d3m.Solver.from_workload(w, precision=d3m.MIXED, autotune=1, solve_kernel=sk, refine_tol=0.5)
+        s.factor()
+        x, info = s.solve(b)
+        assert info["iters"] == 0
+        one[sk] = x.cpu().numpy()
+        s.close()
+        s = d3m.Solver.from_workload(w, precision=d3m.MIXED, autotune=1, solve_kernel=sk)
+        s.factor()
+        x, info = s.solve(b)
+        assert info["max_resid"] < 1e-10
+        full[sk] = (x.cpu().numpy(), info["iters"])
+        s.close()
+    ref = full[1][0]
+    scale = np.abs(ref).max()
+    d01 = np.abs(one[0] - one[1]).max() / scale
+    e0 = np.abs(one[0] - ref).max() / scale
+    e1 = np.abs(one[1] - ref).max() / scale
+    assert d01 < 1e-3
+    assert e0 < 3 * e1 + 1e-6
+    assert np.abs(full[0][0] - ref).max() / scale < 1e-8
+    assert abs(full[0][1] - full[1][1]) <= 1
+
+
+@pytest.mark.gpu
 def test_autotuner_choices_and_cache(tmp_path):
     """The per-level autotuner: its schedule gives the same refined solution as
     the fixed fp32-FMA schedule, its choices round-trip through the cache file,

@@ -125,7 +125,7 @@ def test_level_table_matches_tree_heights():
 @pytest.mark.parametrize("kw", [dict(update_kernel=3), dict(panel_kernel=2), dict(autotune=-1),
                                 dict(lookahead=2), dict(leaf_max=-5), dict(refine_method=2),
                                 dict(gmres_restart=201), dict(gmres_restart=-1), dict(gmres_tol=1.5),
-                                dict(gmres_tol=-1e-3)])
+                                dict(gmres_tol=-1e-3), dict(solve_kernel=2)])
 def test_setup_rejects_bad_options(kw):
     """Option values outside their documented sets are refused at set-up."""
     w = W.make(1)
