@@ -437,6 +437,9 @@ def main():
     ap.add_argument("--ncu-range", action="store_true",
                     help="after the timed steps, run one more mixed step (factor graph + solve) between "
                          "cudaProfilerStart/Stop, for ncu --profile-from-start off")
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="replace the workload's plane waves by this many seeded random ones "
+                         "(profiling the substitution of a small workload with many right-hand sides)")
     ap.add_argument("--autotune-cache", default=None,
                     help="file prefix for the tuned factor schedules (read when they match, else written); "
                          "lets a profiler run reuse the schedule of a plain run")
@@ -444,6 +447,8 @@ def main():
     ws, rank, local = _dist()
     from paper_2002_05018_gb300 import workloads as W
     w = W.make(args.config)
+    if args.nrhs > 0:
+        w = W.with_waves(w, args.nrhs, seed=args.config)
     if args.impl == "reference":
         # the reference arm is the CPU oracle (no GPU, no library): rank 0 only
         if rank != 0:

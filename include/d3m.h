@@ -145,10 +145,14 @@ typedef struct {
                            does not depend on alpha; K_D, K and lambda do. */
   int32_t solve_kernel; /* MIXED substitution products (L11^{-1}, L21, their
                            transposes times the right-hand sides): 0 = complex
-                           BF16x3 on the tcgen05 tensor cores (default), the
-                           complex64 operands split into bf16 planes in the
+                           BF16x3 on the tcgen05 tensor cores (default): each
+                           factorisation also writes these operands as bf16
+                           planes in 128 x 32 blocks (about 12 bytes per complex
+                           entry, blocks padded; extra device memory), the
+                           right-hand sides are split inside the product
                            kernel, fp32 accumulation in tensor memory; 1 = fp32
-                           FMA.  FP64 always uses fp64 FMA. */
+                           FMA on the complex64 factors.  FP64 always uses fp64
+                           FMA. */
 } d3m_options;
 /* d3m_setup returns D3M_EINVAL (and the context, for d3m_last_error) when an
  * option lies outside the values listed above. */
@@ -180,7 +184,9 @@ typedef struct {
   double ms_assemble, ms_panel, ms_update;        /* summed kernel durations */
   double ms_fwd, ms_bwd, ms_residual;             /* last solve, all refinement steps */
   double solve_flops;     /* real flops of the last solve's substitutions */
-  double ms_inverse;      /* factor: building L11^{-1} of every front (profile=1) */
+  double ms_inverse;      /* factor: building L11^{-1} of every front and, with
+                             solve_kernel 0, the substitution's bf16 operand
+                             blocks (profile=1) */
   int64_t tuned_levels_tc;/* levels whose updates the autotuner put on tensor cores */
   int64_t tuned_levels_cs2; /* levels whose panels run with the doubled cluster size */
   double ms_tuning;       /* wall time of the trial factorisations */

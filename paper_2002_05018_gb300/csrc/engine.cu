@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -1662,6 +1663,10 @@ struct CgItem {
   float alpha;
   int32_t tile0;
   int32_t koff;
+  // tensor-core kernel only: the pre-split block of the item's A operand for
+  // row tile 0 and its first k chunk, and the blocks per row tile (k chunks)
+  int64_t qa;
+  int32_t qnk;
 };
 template <typename T>
 struct CgBufs {
@@ -1791,14 +1796,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
 #include "tc_solve.cuh"
 
 // bm: the row tile of the FMA kernel (32, 64 or 128), or 0 for the tensor-core
-// kernel (128 x 64 tiles, complex64 operands only); err / wait_cap are that
-// kernel's error flag and first-wait bound.
+// kernel (128 x 64 tiles, complex64 operands only); qpl / err / wait_cap are
+// that kernel's pre-split A blocks, error flag and first-wait bound.
 template <typename T>
 static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, const CgBufs<T> &bufs,
-                         const int64_t *gidx, cudaStream_t s, int32_t *err = nullptr, int wait_cap = 0) {
+                         const int64_t *gidx, cudaStream_t s, const uint16_t *qpl = nullptr,
+                         int32_t *err = nullptr, int wait_cap = 0) {
   if constexpr (sizeof(T) == 4) {
     if (bm == 0) {
-      k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, err, wait_cap);
+      k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, qpl, err, wait_cap);
       return;
     }
   }
@@ -2281,6 +2287,15 @@ struct DeviceState {
   TcTile *tc_tiles = nullptr;
   int64_t *w21_off = nullptr;     // per level position: the front's W21 block in tc_w
   uint16_t *planesA = nullptr, *planesB = nullptr;  // bf16 operand planes
+  // tensor-core substitution: pre-split 48 KB blocks of the A operands
+  // (L11^{-1}, L21 and their transposes, per level position and kind 0-3),
+  // written after each level is factored (k_tc_presplit)
+  uint16_t *qpl = nullptr;
+  QPre *qpre = nullptr;
+  std::vector<std::array<int64_t, 4>> qblk_h;  // first block of each operand
+  std::vector<std::array<int32_t, 4>> qnk_h;   // its k chunks (blocks per row tile)
+  std::vector<std::array<int64_t, 2>> qpre_lvl;  // per level: first job, job count
+  int64_t qblocks = 0;
   float2 *tc_w = nullptr;         // W21 of every front of a level (fp32 complex)
   std::vector<int> level_maxp;   // largest pivot block per level
   int32_t *nsplit = nullptr;     // per level position: row splits of the backward partials
@@ -2392,6 +2407,24 @@ static bool encode_planes(CUtensorMap *tm, uint16_t *base, int kpitch, int64_t r
 // written by the update-row solve), the 32 x 32 split blocks of both operands
 // and the 128 x 128 tiles of the lower triangle of the Schur product
 // C = F22 - L21 W21^T.
+// Whether substitution product `kind` (0: L11^{-1} y, 1: L21 y, 2: L21^T x,
+// 3: L11^{-T} w) of tree level l runs on the tensor cores: when its fronts'
+// operands fill at least 30 % of the padded 128 x 32 blocks they take (the
+// bf16x3 kernel then outruns fp32 FMA; the small fronts near the leaves
+// stay on FMA, which also spares their mostly-padding operand blocks).
+static bool tc_solve_launch(const Plan &P, int l, int kind) {
+  double use = 0, pad = 0;
+  for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+    const int f = P.level_fronts[i];
+    const int64_t pf = P.sn_end[f] - P.sn_start[f], uf = P.struct_ptr[f + 1] - P.struct_ptr[f];
+    const int64_t M = kind == 1 ? uf : pf, K = kind == 2 ? uf : pf;
+    if (M <= 0 || K <= 0) continue;
+    use += (double)M * K;
+    pad += (double)((M + Q_BM - 1) / Q_BM * Q_BM) * ((K + Q_BK - 1) / Q_BK * Q_BK);
+  }
+  return pad > 0 && use >= 0.3 * pad;
+}
+
 static int tc_plan(Ctx &c, DeviceState *d, const std::vector<int32_t> &m, const std::vector<int32_t> &pp) {
   const Plan &P = c.plan;
   std::vector<TcSplit> sp;
@@ -2678,6 +2711,61 @@ static int dev_init(Ctx &c) {
     d->allocs.push_back(d->tmp_inv);
     CUDA_TRY(upload(d, &d->inv_items, items));
     CUDA_TRY(upload(d, &d->linv_off, d->linv_off_h));
+    if (mixed && c.opt.solve_kernel == 0) {
+      // the A operands of the tensor-core substitution, as 128 x 32 blocks
+      // (only the blocks inside the k range of each row tile of the
+      // triangular L11^{-1} and L11^{-T} are written and read)
+      std::vector<QPre> pre;
+      d->qblk_h.assign(nsn, {});
+      d->qnk_h.assign(nsn, {});
+      d->qpre_lvl.assign(P.n_levels, {});
+      int64_t nb = 0;
+      for (int l = 0; l < P.n_levels; ++l) {
+        d->qpre_lvl[l][0] = (int64_t)pre.size();
+        bool on[4];
+        for (int kind = 0; kind < 4; ++kind) on[kind] = tc_solve_launch(P, l, kind);
+        for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+          const int f = P.level_fronts[i];
+          const int pf = pp[f], mf = m[f];
+          for (int kind = 0; kind < 4; ++kind) {
+            QPre q{};
+            int mode = 0;
+            if (kind == 0 || kind == 3) {
+              q.src = d->linv_off_h[i]; q.abuf = 1; q.M = pf; q.K = pf;
+              q.a_rs = kind == 0 ? 1 : pf; q.a_cs = kind == 0 ? pf : 1;
+              mode = kind == 0 ? 1 : 3;
+            } else {
+              q.src = P.front_off[f] + pf; q.abuf = 0;
+              q.M = kind == 1 ? mf - pf : pf; q.K = kind == 1 ? pf : mf - pf;
+              q.a_rs = kind == 1 ? 1 : mf; q.a_cs = kind == 1 ? mf : 1;
+            }
+            if (q.M <= 0 || q.K <= 0 || !on[kind]) continue;
+            const int nkc = (q.K + Q_BK - 1) / Q_BK, ntm = (q.M + Q_BM - 1) / Q_BM;
+            d->qblk_h[i][kind] = nb;
+            d->qnk_h[i][kind] = nkc;
+            for (int tm = 0; tm < ntm; ++tm) {
+              // the chunks the row tile's k range reaches (all, or those of a triangle)
+              const int c0 = mode == 3 ? tm * (Q_BM / Q_BK) : 0;
+              const int c1 = mode == 1 ? std::min(nkc, (tm + 1) * (Q_BM / Q_BK)) : nkc;
+              for (int kc = c0; kc < c1; ++kc) {
+                QPre b = q;
+                b.blk = nb + q_rowbase(mode, nkc, tm) + kc;
+                b.r0 = tm * Q_BM;
+                b.k0 = kc * Q_BK;
+                pre.push_back(b);
+              }
+            }
+            nb += q_rowbase(mode, nkc, ntm) + (mode == 3 ? (int64_t)ntm * (Q_BM / Q_BK) : 0);
+          }
+        }
+        d->qpre_lvl[l][1] = (int64_t)pre.size() - d->qpre_lvl[l][0];
+      }
+      d->qblocks = nb;
+      if (!pre.empty()) {
+        CUDA_TRY(upload(d, &d->qpre, pre));
+        CUDA_TRY(dalloc(d, &d->qpl, (size_t)nb * (Q_ABLK / 2)));
+      }
+    }
   }
   CUDA_TRY(upload(d, &d->nsplit, nsplit_h));
   CUDA_TRY(upload(d, &d->part_off, d->part_off_h));
@@ -2984,6 +3072,13 @@ static int factor_t(Ctx &c) {
         const CgBufs<T> ib{{arena, Li, (cx<T> *)d->tmp_inv, nullptr, nullptr, nullptr, nullptr}};
         for (auto &st : d->inv_stage[l]) {
           launch_cgemm<T>(st[3], st[2], d->inv_items + st[0], st[1], ib, nullptr, si);
+          ++nl;
+        }
+        // the level's substitution operands as pre-split tensor-core blocks
+        if (d->qpl && d->qpre_lvl[l][1] > 0) {
+          CgBufs<float> fb;
+          for (int q = 0; q < 7; ++q) fb.p[q] = reinterpret_cast<cx<float> *>(ib.p[q]);
+          k_tc_presplit<<<(unsigned)d->qpre_lvl[l][1], 256, 0, si>>>(d->qpre + d->qpre_lvl[l][0], fb, d->qpl);
           ++nl;
         }
         PROF_END(PC_INV);
@@ -3324,9 +3419,10 @@ static int solve_items(Ctx &c, int r) {
       // the smaller ones, by their register use)
       int best = 64;
       double bcost = 1e300;
+      const bool tcl = tcs && tc_solve_launch(P, l, kind);  // this launch on the tensor cores
       for (int bm : {32, 64, 128}) {
         if (bm == 128 && !mixed) continue;
-        if (tcs && bm != 128) continue;  // the tensor-core kernel's tiles are 128 rows
+        if (tcl && bm != 128) continue;  // the tensor-core kernel's tiles are 128 rows
         BM = bm;
         int64_t t = 0;
         for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
@@ -3367,6 +3463,7 @@ static int solve_items(Ctx &c, int r) {
           g.c = P.y_off[f] * r; g.c_rs = r; g.c_cs = 1;
           g.M = pf; g.K = pf;
           g.abuf = 1; g.bbuf = 2; g.cbuf = 3; g.beta = 0; g.alpha = 1.f;
+          if (tcl) { g.qa = d->qblk_h[i][kind]; g.qnk = d->qnk_h[i][kind]; }
           kitems.push_back(g);
         } else if (kind == 1) {  // Y[p:m] -= L21 y[0:p]
           if (mf == pf || pf == 0) continue;
@@ -3375,6 +3472,7 @@ static int solve_items(Ctx &c, int r) {
           g.c = (P.y_off[f] + pf) * r; g.c_rs = r; g.c_cs = 1;
           g.M = mf - pf; g.K = pf;
           g.abuf = 0; g.bbuf = mixed ? 3 : 2; g.cbuf = 2; g.beta = 1; g.alpha = -1.f;
+          if (tcl) { g.qa = d->qblk_h[i][1]; g.qnk = d->qnk_h[i][1]; }
           kitems.push_back(g);
         } else {  // partials of L21^T x over row splits
           if (mf == pf || pf == 0) continue;
@@ -3387,6 +3485,7 @@ static int solve_items(Ctx &c, int r) {
             h.c = (d->part_off_h[i] + (int64_t)q * pf) * r; h.c_rs = r; h.c_cs = 1;
             h.M = pf; h.K = std::min(BSPLIT, mf - pf - rb);
             h.abuf = 0; h.bbuf = 4; h.cbuf = 5; h.beta = 0; h.alpha = 1.f;
+            if (tcl) { h.qa = d->qblk_h[i][2] + rb / Q_BK; h.qnk = d->qnk_h[i][2]; }
             kitems.push_back(h);
           }
         }
@@ -3412,13 +3511,15 @@ static int solve_items(Ctx &c, int r) {
           items.push_back(h);
           continue;
         }
-        const int Kc = ((g.K + S - 1) / S + 15) / 16 * 16;
+        const int kq = tcl ? Q_BK : 16;  // the tensor-core pieces start on A-block boundaries
+        const int Kc = ((g.K + S - 1) / S + kq - 1) / kq * kq;
         const int64_t mn = (int64_t)g.M * g.N;
         int pieces = 0;
         for (int kb = 0; kb < g.K; kb += Kc, ++pieces) {
           CgItem h = g;
           h.koff = kb;
           h.K = std::min(Kc, g.K - kb);
+          h.qa = g.qa + kb / Q_BK;
           h.a += (int64_t)kb * g.a_cs;
           if (g.gath >= 0) h.gath += kb;
           else h.b += (int64_t)kb * g.b_rs;
@@ -3453,7 +3554,7 @@ static int solve_items(Ctx &c, int r) {
       d->sol_lvl[l][4 * kind + 0] = first;
       d->sol_lvl[l][4 * kind + 1] = (int)items.size() - first;
       d->sol_lvl[l][4 * kind + 2] = tiles;
-      d->sol_lvl[l][4 * kind + 3] = tcs ? 0 : BM;  // 0: k_tc_cgemm
+      d->sol_lvl[l][4 * kind + 3] = tcl ? 0 : BM;  // 0: k_tc_cgemm
     }
   }
   if (d->sol_items) {
@@ -3522,8 +3623,8 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     }
     const auto &sl = d->sol_lvl[l];
     if (use_inv) {
-      launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->sv_err,
-                      d->sv_wait_cap);
+      launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->qpl,
+                      d->sv_err, d->sv_wait_cap);
       nl += reduce(l, 0);
       dim3 gdv((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
@@ -3533,8 +3634,8 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     }
     nl += 2;
     if (sl[5] > 0) {
-      launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s, d->sv_err,
-                      d->sv_wait_cap);
+      launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s, d->qpl,
+                      d->sv_err, d->sv_wait_cap);
       nl += reduce(l, 1);
       ++nl;
     }
@@ -3550,15 +3651,15 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const int64_t *po = d->part_off + P.level_ptr[l];
     const auto &sl = d->sol_lvl[l];
     if (sl[9] > 0) {
-      launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s, d->sv_err,
-                      d->sv_wait_cap);
+      launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s, d->qpl,
+                      d->sv_err, d->sv_wait_cap);
       ++nl;
     }
     if (use_inv) {
       dim3 gw((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
-      launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->sv_err,
-                      d->sv_wait_cap);
+      launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->qpl,
+                      d->sv_err, d->sv_wait_cap);
       nl += reduce(l, 3);
       k_bwd_out<T><<<gw, 256, 0, s>>>(lvl, ft, d->perm, Y2, (cx<T> *)d->xM, r);
       nl += 3;

@@ -12,28 +12,55 @@
 // products and the five correction products in separate TMEM accumulators,
 // the minus of Re = Ar Br - Ai Bi through the A-negate bit).
 //
-// One CTA per 128 x 64 output tile, 288 threads.  Warps 0-7 load the tile's
-// A (128 x 32) and B (32 x 64) chunks of complex64 from global memory with
-// the item's strides (B's rows optionally gathered), split them into the six
-// bf16 planes in registers and store them to shared memory in the K-major
-// layout with the 64-byte swizzle that the MMA descriptors read (the layout
-// TMA's SWIZZLE_64B writes), two stages deep; the global loads of the next
-// chunk are in flight while the current one is split and stored.  One thread
-// of warp 8 issues the MMAs (M = 128, N = 64, K = 16; 24 per k-step of 16).
-// The epilogue stages the accumulators through shared memory and writes C
-// one row at a time, coalesced along the right-hand sides.  Every mbarrier
-// wait is bounded as in k_tc_gemm: on expiry the tile raises `err`, stops,
-// waits (bounded) for the MMAs it has issued, frees its TMEM and writes
-// nothing.
+// The A operands do not change between the factorisation and the solves,
+// so they are split once, right after each tree level is factored
+// (k_tc_presplit, on the inverse stream): every 128-row x 32-k block of
+// every A operand becomes one 48 KB image of its six bf16 planes in exactly
+// the K-major, 64-byte-swizzled shared-memory layout the MMA descriptors
+// read.  The product kernel then moves A with one bulk copy per k chunk
+// (cp.async.bulk, mbarrier transaction count), three stages deep, and its
+// producer warps only split the small right-hand-side block B.
+//
+// k_tc_cgemm: one CTA per 128 x 64 output tile, 320 threads.  Warps 0-7
+// load the tile's B chunks (32 x 64 complex64, rows optionally gathered),
+// two chunks ahead in registers, split them and store their planes; one
+// thread of warp 8 issues the A bulk copies; one thread of warp 9 issues the
+// MMAs (M = 128, N = 64, K = 16; 24 per k-step of 16).  The epilogue stages
+// the accumulators through shared memory and writes C one row at a time,
+// coalesced along the right-hand sides.  Every mbarrier wait is bounded: on
+// expiry the tile raises `err`, stops, waits (bounded) for its MMAs and bulk
+// copies in flight, frees its TMEM and writes nothing.
 
-constexpr int Q_BM = 128, Q_BN = 64, Q_BK = 32, Q_STAGES = 2, Q_NPROD = 256, Q_THREADS = 288;
+constexpr int Q_BM = 128, Q_BN = 64, Q_BK = 32, Q_STAGES = 3, Q_NPROD = 256, Q_THREADS = 320;
 constexpr int Q_APL = Q_BM * Q_BK * 2;                    // bytes of one A plane tile (8 KB)
 constexpr int Q_BPL = Q_BN * Q_BK * 2;                    // bytes of one B plane tile (4 KB)
-constexpr int Q_STAGE_BYTES = G_NPL * (Q_APL + Q_BPL);    // 72 KB
+constexpr int Q_ABLK = G_NPL * Q_APL;                     // one pre-split A block (48 KB)
+constexpr int Q_STAGE_BYTES = Q_ABLK + G_NPL * Q_BPL;     // 72 KB
 constexpr int Q_CPITCH = Q_BN + 1;                        // epilogue staging row pitch (complex)
-constexpr int Q_SMEM = Q_STAGES * Q_STAGE_BYTES + 1024 + 128;
+constexpr int Q_SMEM = Q_STAGES * Q_STAGE_BYTES + 1024 + 256;
 constexpr int Q_TMEM_COLS = 256;  // Re, Im of the h.h products; Re, Im of the corrections (64 each)
 static_assert(Q_BM * Q_CPITCH * 8 <= Q_STAGES * Q_STAGE_BYTES, "the epilogue staging reuses the stages");
+static_assert(Q_SMEM <= 227 * 1024, "shared memory per CTA");
+
+// One 128 x 32 block of an A operand to pre-split: rows [r0, r0 + 128) and
+// k [k0, k0 + 32) of the operand at `src` in buffer `abuf` (element (i, k) at
+// src + i a_rs + k a_cs, M x K), written as block `blk` of the plane buffer.
+struct QPre {
+  int64_t src, blk;
+  int32_t a_rs, a_cs, abuf, M, K, r0, k0;
+};
+
+// First block of row tile tm of a pre-split operand with nkc k chunks, minus
+// the tile's first stored chunk: mode 0 stores every chunk of every row tile;
+// mode 1 (lower triangular) chunks [0, min(nkc, 4 (tm + 1))); mode 3 (upper)
+// chunks [4 tm, nkc) -- the chunks a 128-row tile's k range can reach.
+__host__ __device__ inline int64_t q_rowbase(int mode, int nkc, int tm) {
+  constexpr int R = Q_BM / Q_BK;
+  if (mode != 1 && mode != 3) return (int64_t)tm * nkc;
+  int64_t r = 0;
+  for (int t = 0; t < tm; ++t) r += mode == 1 ? (nkc < R * (t + 1) ? nkc : R * (t + 1)) : nkc - R * t;
+  return mode == 3 ? r - (int64_t)R * tm : r;
+}
 
 // Byte offset of 16-byte chunk c (8 bf16 along k) of row `row` in a K-major
 // plane tile of 64-byte rows with the 64-byte swizzle: the chunk index is
@@ -71,22 +98,59 @@ __device__ __forceinline__ void q_split8(const cx<float> *v, uint4 (&out)[6]) {
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// Pre-split of A blocks (one CTA of 256 threads per block): thread ->
+// (row, 16 consecutive k), the fast thread index along the operand's
+// contiguous dimension; entries outside the operand are written as zeros.
+__global__ void __launch_bounds__(256)
+    k_tc_presplit(const QPre *__restrict__ jobs, CgBufs<float> bufs, uint16_t *__restrict__ qpl) {
+  const QPre j = jobs[blockIdx.x];
+  const cx<float> *A = bufs.p[j.abuf] + j.src;
+  const int tid = threadIdx.x;
+  const bool afast = j.a_rs == 1;
+  const int ax = afast ? (tid & 127) : (tid >> 1), akh = afast ? (tid >> 7) : (tid & 1);
+  const int i = j.r0 + ax;
+  const cx<float> *Arow = A + (int64_t)i * j.a_rs;
+  cx<float> v[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const int k = j.k0 + akh * 16 + e;
+    v[e] = (i < j.M && k < j.K) ? Arow[(int64_t)k * j.a_cs] : mk<float>(0.f, 0.f);
+  }
+  unsigned char *dst = reinterpret_cast<unsigned char *>(qpl) + j.blk * (int64_t)Q_ABLK;
+  uint4 pl[6];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    q_split8(v + 8 * h, pl);
+    const uint32_t o = q_swz(ax, akh * 2 + h);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) *reinterpret_cast<uint4 *>(dst + q * Q_APL + o) = pl[q];
+  }
+}
 
 __global__ void __launch_bounds__(Q_THREADS, 1)
     k_tc_cgemm(const CgItem *__restrict__ items, int nitems, int ntiles, CgBufs<float> bufs,
-               const int64_t *__restrict__ gidx, int32_t *__restrict__ err, int wait_cap) {
+               const int64_t *__restrict__ gidx, const uint16_t *__restrict__ qpl, int32_t *__restrict__ err,
+               int wait_cap) {
   constexpr int FULL_CAP = 1 << 22;
   extern __shared__ __align__(16) unsigned char q_raw[];
   const int t = blockIdx.x;
   if (t >= ntiles) return;
   // stage tiles start on a 1024-byte boundary of the shared window (swizzle atoms)
   unsigned char *sm = q_raw + ((1024u - (smem_u32(q_raw) & 1023u)) & 1023u);
-  uint64_t *full = reinterpret_cast<uint64_t *>(sm + Q_STAGES * Q_STAGE_BYTES);
-  uint64_t *empty = full + Q_STAGES;
+  uint64_t *afull = reinterpret_cast<uint64_t *>(sm + Q_STAGES * Q_STAGE_BYTES);
+  uint64_t *bfull = afull + Q_STAGES;
+  uint64_t *empty = bfull + Q_STAGES;
   uint64_t *done = empty + Q_STAGES;
   uint32_t *taddr_s = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort_s = reinterpret_cast<volatile int *>(taddr_s + 1);
-  volatile int *issued_s = abort_s + 1;  // k chunks whose MMAs were issued
+  volatile int *issued_s = abort_s + 1;   // k chunks whose MMAs were issued
+  volatile int *issuedA_s = abort_s + 2;  // k chunks whose A bulk copies were issued
   int lo = 0, hi = nitems - 1;  // last item with tile0 <= t
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -97,9 +161,9 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   const int ntm = (it.M + Q_BM - 1) / Q_BM;
   const int ti = t - it.tile0, tm = ti % ntm, tn = ti / ntm;
   const int i0 = tm * Q_BM, j0 = tn * Q_BN;
+  // k range of the tile (triangular operands); klo is a multiple of Q_BK
   int klo = 0, khi = it.K;
   if (it.mode == 1) khi = min(it.K, i0 + Q_BM - it.koff);
-  if (it.mode == 2) klo = max(0, j0 - it.koff);
   if (it.mode == 3) klo = max(0, i0 - it.koff);
   const int nk = khi > klo ? (khi - klo + Q_BK - 1) / Q_BK : 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -110,12 +174,14 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   }
   if (tid == 0) {
     for (int s = 0; s < Q_STAGES; ++s) {
-      mbar_init(smem_u32(full + s), Q_NPROD);
+      mbar_init(smem_u32(afull + s), 1);
+      mbar_init(smem_u32(bfull + s), Q_NPROD);
       mbar_init(smem_u32(empty + s), 1);
     }
     mbar_init(smem_u32(done), 1);
     *abort_s = 0;
     *issued_s = 0;
+    *issuedA_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -124,27 +190,20 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   const uint32_t tmem = *taddr_s;
   const uint32_t sbase = smem_u32(sm);
   if (tid < Q_NPROD) {
-    // ---- producers: thread -> (A row, 16 consecutive k) and (B column, 8
-    // consecutive k), the fast thread index along each operand's contiguous
-    // dimension so that every warp-wide load is coalesced
-    const cx<float> *A = bufs.p[it.abuf] + it.a;
+    // ---- B producers: thread -> (B column, 8 consecutive k), the fast
+    // thread index along B's contiguous dimension (coalesced loads); two
+    // chunks in flight in registers
     const cx<float> *B = bufs.p[it.bbuf] + it.b;
     const int64_t *G = it.gath >= 0 ? gidx + it.gath : nullptr;
-    const bool afast = it.a_rs == 1, bfast = it.b_cs == 1;
-    const int ax = afast ? (tid & 127) : (tid >> 1), akh = afast ? (tid >> 7) : (tid & 1);
+    const bool bfast = it.b_cs == 1;
     const int bn = bfast ? (tid & 63) : (tid >> 2), bkq = bfast ? (tid >> 6) : (tid & 3);
-    const int ai = i0 + ax, bj = j0 + bn;
-    const cx<float> *Arow = A + (int64_t)ai * it.a_rs;
-    cx<float> ra[16], rb[8];
-    auto load = [&](int k0) {
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int k = k0 + akh * 16 + e;
-        ra[e] = (ai < it.M && k < khi) ? Arow[(int64_t)k * it.a_cs] : mk<float>(0.f, 0.f);
-      }
+    const int bj = j0 + bn;
+    const uint32_t ob = q_swz(bn, bkq);
+    auto load = [&](cx<float>(&rb)[8], int kc) {
+      const int k0 = klo + kc * Q_BK + bkq * 8;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const int k = k0 + bkq * 8 + e;
+        const int k = k0 + e;
         cx<float> v = mk<float>(0.f, 0.f);
         if (bj < it.N && k < khi) {
           const int64_t kr = G ? G[k] : (int64_t)k;
@@ -153,34 +212,53 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
         rb[e] = v;
       }
     };
-    if (nk > 0) load(klo);
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc & 1;
+    auto produce = [&](const cx<float>(&rb)[8], int kc) -> bool {
+      const int s = kc % Q_STAGES;
       if (kc >= Q_STAGES &&
-          !mbar_wait_bounded(smem_u32(empty + s), (uint32_t)(((kc >> 1) - 1) & 1), wait_cap)) {
+          !mbar_wait_bounded(smem_u32(empty + s), (uint32_t)((kc / Q_STAGES - 1) & 1), wait_cap)) {
+        *abort_s = 1;
+        return false;
+      }
+      if (*abort_s) return false;
+      unsigned char *st = sm + s * Q_STAGE_BYTES + Q_ABLK;
+      uint4 pl[6];
+      q_split8(rb, pl);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) *reinterpret_cast<uint4 *>(st + q * Q_BPL + ob) = pl[q];
+      // the generic-proxy stores become visible to the tensor cores (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(bfull + s));
+      return true;
+    };
+    cx<float> r0[8], r1[8];
+    if (nk > 0) load(r0, 0);
+    if (nk > 1) load(r1, 1);
+    for (int kc = 0; kc < nk; kc += 2) {
+      if (!produce(r0, kc)) break;
+      if (kc + 2 < nk) load(r0, kc + 2);
+      if (kc + 1 < nk) {
+        if (!produce(r1, kc + 1)) break;
+        if (kc + 3 < nk) load(r1, kc + 3);
+      }
+    }
+  } else if (tid == Q_NPROD) {
+    // ---- A loader: one bulk copy of a pre-split 48 KB block per k chunk
+    const uint16_t *src = qpl + (it.qa + q_rowbase(it.mode, it.qnk, tm) + klo / Q_BK) * (int64_t)(Q_ABLK / 2);
+    int kc = 0;
+    for (; kc < nk; ++kc) {
+      const int s = kc % Q_STAGES;
+      if (kc >= Q_STAGES &&
+          !mbar_wait_bounded(smem_u32(empty + s), (uint32_t)((kc / Q_STAGES - 1) & 1), wait_cap)) {
         *abort_s = 1;
         break;
       }
       if (*abort_s) break;
-      unsigned char *st = sm + s * Q_STAGE_BYTES;
-      uint4 pl[6];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        q_split8(ra + 8 * h, pl);
-        const uint32_t o = q_swz(ax, akh * 2 + h);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) *reinterpret_cast<uint4 *>(st + q * Q_APL + o) = pl[q];
-      }
-      q_split8(rb, pl);
-      const uint32_t ob = q_swz(bn, bkq);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) *reinterpret_cast<uint4 *>(st + G_NPL * Q_APL + q * Q_BPL + ob) = pl[q];
-      // the generic-proxy stores become visible to the tensor cores (async proxy)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(smem_u32(full + s));
-      if (kc + 1 < nk) load(klo + (kc + 1) * Q_BK);
+      const uint32_t fa = smem_u32(afull + s);
+      mbar_expect_tx(fa, Q_ABLK);
+      bulk_load(sbase + s * Q_STAGE_BYTES, src + (int64_t)kc * (Q_ABLK / 2), Q_ABLK, fa);
     }
-  } else if (tid == Q_NPROD) {
+    *issuedA_s = kc;
+  } else if (tid == Q_NPROD + 32) {
     // ---- MMA issuer: 2 k-steps of 16 per chunk, 24 bf16 MMAs per k-step
     // (pieces h, m, l = 0, 1, 2); leading products to TMEM columns 0-127
     // (Re, Im), the correction products to 128-255
@@ -188,13 +266,15 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
     constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
     int kc = 0;
     for (; kc < nk; ++kc) {
-      const int s = kc & 1;
-      if (*abort_s || !mbar_wait_bounded(smem_u32(full + s), (uint32_t)((kc >> 1) & 1), wait_cap)) {
+      const int s = kc % Q_STAGES;
+      const uint32_t ph = (uint32_t)((kc / Q_STAGES) & 1);
+      if (*abort_s || !mbar_wait_bounded(smem_u32(afull + s), ph, wait_cap) ||
+          !mbar_wait_bounded(smem_u32(bfull + s), ph, wait_cap)) {
         *abort_s = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = sbase + s * Q_STAGE_BYTES, sb = st + G_NPL * Q_APL;
+      const uint32_t st = sbase + s * Q_STAGE_BYTES, sb = st + Q_ABLK;
 #pragma unroll
       for (int kk = 0; kk < Q_BK / 16; ++kk) {
         const uint32_t ko = (uint32_t)kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
@@ -269,6 +349,13 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
     }
   } else if (tid == 0) {
     atomicExch(err, 1);
+  }
+  // bulk copies still in flight after an expiry land before the CTA's shared
+  // memory is released: wait (bounded) for the last phase of every stage used
+  if (tid == Q_NPROD) {
+    const int n = *issuedA_s;
+    for (int kc = max(0, n - Q_STAGES); kc < n; ++kc)
+      mbar_wait_bounded(smem_u32(afull + kc % Q_STAGES), (uint32_t)((kc / Q_STAGES) & 1), FULL_CAP);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

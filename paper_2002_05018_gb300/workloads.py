@@ -119,6 +119,12 @@ def _random_waves(rng, n):
     return _angles_to_waves(np.arccos(ct), phi, psi)
 
 
+def with_waves(w: Workload, n: int, seed: int = 0) -> Workload:
+    """A copy of w with n seeded random plane waves as its right-hand sides."""
+    khat, pol = _random_waves(np.random.default_rng(seed), n)
+    return dataclasses.replace(w, khat=khat, pol=pol)
+
+
 def _cell_centres(nx, ny, nz, lx, ly, lz):
     i = (np.arange(nx) + 0.5) * lx / nx
     j = (np.arange(ny) + 0.5) * ly / ny
