@@ -1679,23 +1679,47 @@ template <typename T, int BM>
 __host__ __device__ constexpr int cg_kc() {
   return sizeof(T) == 4 && BM == 32 ? 48 : 16;
 }
-template <typename T, int BM>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_cgemm(const CgItem *__restrict__ items, int nitems, int ntiles,
-                                               CgBufs<T> bufs, const int64_t *__restrict__ gidx) {
-  constexpr int BN = CG_BN, KC = cg_kc<T, BM>(), RA = BM / 16, RB = BN / 16;
-  constexpr int LA = BM * KC / 256, LB = BN * KC / 256;  // staged elements per thread
-  const int t = blockIdx.x;
-  if (t >= ntiles) return;
+// Buffer i of a launch's buffer table, read from the kernel parameters by a
+// switch (an indexed read would copy the table to local memory first).
+template <typename T>
+__device__ __forceinline__ cx<T> *cg_buf(const CgBufs<T> &b, int i) {
+  switch (i) {
+    case 0: return b.p[0];
+    case 1: return b.p[1];
+    case 2: return b.p[2];
+    case 3: return b.p[3];
+    case 4: return b.p[4];
+    case 5: return b.p[5];
+    default: return b.p[6];
+  }
+}
+// The item of output tile t of a launch: one load from the launch's
+// tile -> item map when there is one, else a binary search over the items'
+// first tiles (a chain of dependent loads, kept for the small launches of
+// the factor-time inverse).
+__device__ __forceinline__ int cg_item_of(const CgItem *__restrict__ items, int nitems, int t,
+                                          const int32_t *__restrict__ tmap) {
+  if (tmap) return tmap[t];
   int lo = 0, hi = nitems - 1;  // last item with tile0 <= t
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (items[mid].tile0 <= t) lo = mid;
     else hi = mid - 1;
   }
-  const CgItem it = items[lo];
-  const cx<T> *A = bufs.p[it.abuf] + it.a;
-  const cx<T> *B = bufs.p[it.bbuf] + it.b;
-  cx<T> *C = bufs.p[it.cbuf] + it.c;
+  return lo;
+}
+template <typename T, int BM>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_cgemm(const CgItem *__restrict__ items, int nitems, int ntiles,
+                                               CgBufs<T> bufs, const int64_t *__restrict__ gidx,
+                                               const int32_t *__restrict__ tmap) {
+  constexpr int BN = CG_BN, KC = cg_kc<T, BM>(), RA = BM / 16, RB = BN / 16;
+  constexpr int LA = BM * KC / 256, LB = BN * KC / 256;  // staged elements per thread
+  const int t = blockIdx.x;
+  if (t >= ntiles) return;
+  const CgItem it = items[cg_item_of(items, nitems, t, tmap)];
+  const cx<T> *A = cg_buf(bufs, it.abuf) + it.a;
+  const cx<T> *B = cg_buf(bufs, it.bbuf) + it.b;
+  cx<T> *C = cg_buf(bufs, it.cbuf) + it.c;
   const int64_t *G = it.gath >= 0 ? gidx + it.gath : nullptr;
   const int ntm = (it.M + BM - 1) / BM;
   const int ti = t - it.tile0, tm = ti % ntm, tn = ti / ntm;
@@ -1797,23 +1821,24 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
 
 // bm: the row tile of the FMA kernel (32, 64 or 128), or 0 for the tensor-core
 // kernel (128 x 64 tiles, complex64 operands only); qpl / err / wait_cap are
-// that kernel's pre-split A blocks, error flag and first-wait bound.
+// that kernel's pre-split A blocks, error flag and first-wait bound; tmap, if
+// given, maps each output tile to its item (index relative to `items`).
 template <typename T>
 static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, const CgBufs<T> &bufs,
                          const int64_t *gidx, cudaStream_t s, const uint16_t *qpl = nullptr,
-                         int32_t *err = nullptr, int wait_cap = 0) {
+                         int32_t *err = nullptr, int wait_cap = 0, const int32_t *tmap = nullptr) {
   if constexpr (sizeof(T) == 4) {
     if (bm == 0) {
-      k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, qpl, err, wait_cap);
+      k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, tmap, qpl, err, wait_cap);
       return;
     }
   }
   if (bm == 32)
-    k_cgemm<T, 32><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
+    k_cgemm<T, 32><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
   else if (bm == 64 || sizeof(T) == 8)
-    k_cgemm<T, 64><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
+    k_cgemm<T, 64><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
   else
-    k_cgemm<T, (sizeof(T) == 4 ? 128 : 64)><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx);
+    k_cgemm<T, (sizeof(T) == 4 ? 128 : 64)><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
 }
 
 // Split-K: a product whose launch has few output tiles and a long k range is
@@ -1845,7 +1870,7 @@ __global__ void k_splitk_reduce(const SkItem *__restrict__ items, int nitems, in
       acc.re += v.re;
       acc.im += v.im;
     }
-    cx<T> *d = bufs.p[it.cbuf] + it.c + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
+    cx<T> *d = cg_buf(bufs, it.cbuf) + it.c + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
     if (it.beta) {
       const cx<T> o = *d;
       acc.re += o.re;
@@ -2251,6 +2276,8 @@ struct DeviceState {
   // per level, (item0, nitems, ntiles) of: forward L11^{-1}, forward L21,
   // backward L21^T (split partials), backward L11^{-T}
   std::vector<std::array<int, 16>> sol_lvl;  // (item0, nitems, ntiles, row tile) per kind
+  int32_t *sol_tmap = nullptr;               // per solve launch: output tile -> item (relative)
+  std::vector<std::array<int64_t, 4>> sol_tofs;  // per level and kind: offset in sol_tmap
   std::vector<std::array<int, 12>> sk_lvl;   // per kind: split-K reduce (item0, nitems, elements)
   SkItem *sk_items = nullptr;
   void *skp = nullptr;                       // split-K partial blocks
@@ -3562,6 +3589,27 @@ static int solve_items(Ctx &c, int r) {
     d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), (void *)d->sol_items), d->allocs.end());
     d->sol_items = nullptr;
   }
+  // tile -> item maps of every launch (an item's tiles run from its tile0 to
+  // the next item's tile0, or to the launch's tile count)
+  std::vector<int32_t> tmap;
+  d->sol_tofs.assign(P.n_levels, {});
+  for (int l = 0; l < P.n_levels; ++l)
+    for (int kind = 0; kind < 4; ++kind) {
+      const auto &sl = d->sol_lvl[l];
+      const int first = sl[4 * kind], n = sl[4 * kind + 1], tiles = sl[4 * kind + 2];
+      d->sol_tofs[l][kind] = (int64_t)tmap.size();
+      for (int q = 0; q < n; ++q) {
+        const int t1 = q + 1 < n ? items[first + q + 1].tile0 : tiles;
+        for (int t = items[first + q].tile0; t < t1; ++t) tmap.push_back(q);
+      }
+    }
+  if (d->sol_tmap) {
+    cudaFree(d->sol_tmap);
+    d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), (void *)d->sol_tmap), d->allocs.end());
+    d->sol_tmap = nullptr;
+  }
+  if (tmap.empty()) tmap.push_back(0);
+  CUDA_TRY(upload(d, &d->sol_tmap, tmap));
   if (items.empty()) items.push_back(CgItem{});
   CUDA_TRY(upload(d, &d->sol_items, items));
   for (void *q : {(void *)d->sk_items, d->skp})
@@ -3624,7 +3672,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const auto &sl = d->sol_lvl[l];
     if (use_inv) {
       launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][0]);
       nl += reduce(l, 0);
       dim3 gdv((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
@@ -3635,7 +3683,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     nl += 2;
     if (sl[5] > 0) {
       launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][1]);
       nl += reduce(l, 1);
       ++nl;
     }
@@ -3652,14 +3700,14 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const auto &sl = d->sol_lvl[l];
     if (sl[9] > 0) {
       launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][2]);
       ++nl;
     }
     if (use_inv) {
       dim3 gw((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
       k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
       launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][3]);
       nl += reduce(l, 3);
       k_bwd_out<T><<<gw, 256, 0, s>>>(lvl, ft, d->perm, Y2, (cx<T> *)d->xM, r);
       nl += 3;

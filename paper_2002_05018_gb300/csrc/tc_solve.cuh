@@ -110,7 +110,7 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 __global__ void __launch_bounds__(256)
     k_tc_presplit(const QPre *__restrict__ jobs, CgBufs<float> bufs, uint16_t *__restrict__ qpl) {
   const QPre j = jobs[blockIdx.x];
-  const cx<float> *A = bufs.p[j.abuf] + j.src;
+  const cx<float> *A = cg_buf(bufs, j.abuf) + j.src;
   const int tid = threadIdx.x;
   const bool afast = j.a_rs == 1;
   const int ax = afast ? (tid & 127) : (tid >> 1), akh = afast ? (tid >> 7) : (tid & 1);
@@ -135,8 +135,8 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(Q_THREADS, 1)
     k_tc_cgemm(const CgItem *__restrict__ items, int nitems, int ntiles, CgBufs<float> bufs,
-               const int64_t *__restrict__ gidx, const uint16_t *__restrict__ qpl, int32_t *__restrict__ err,
-               int wait_cap) {
+               const int64_t *__restrict__ gidx, const int32_t *__restrict__ tmap,
+               const uint16_t *__restrict__ qpl, int32_t *__restrict__ err, int wait_cap) {
   constexpr int FULL_CAP = 1 << 22;
   extern __shared__ __align__(16) unsigned char q_raw[];
   const int t = blockIdx.x;
@@ -151,13 +151,7 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   volatile int *abort_s = reinterpret_cast<volatile int *>(taddr_s + 1);
   volatile int *issued_s = abort_s + 1;   // k chunks whose MMAs were issued
   volatile int *issuedA_s = abort_s + 2;  // k chunks whose A bulk copies were issued
-  int lo = 0, hi = nitems - 1;  // last item with tile0 <= t
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (items[mid].tile0 <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  const CgItem it = items[lo];
+  const CgItem it = items[cg_item_of(items, nitems, t, tmap)];
   const int ntm = (it.M + Q_BM - 1) / Q_BM;
   const int ti = t - it.tile0, tm = ti % ntm, tn = ti / ntm;
   const int i0 = tm * Q_BM, j0 = tn * Q_BN;
@@ -167,6 +161,33 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   if (it.mode == 3) klo = max(0, i0 - it.koff);
   const int nk = khi > klo ? (khi - klo + Q_BK - 1) / Q_BK : 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // B producers (threads < Q_NPROD): thread -> (B column, 8 consecutive k),
+  // the fast thread index along B's contiguous dimension (coalesced loads);
+  // two chunks in flight in registers, the first two issued before the set-up
+  const cx<float> *B = cg_buf(bufs, it.bbuf) + it.b;
+  const int64_t *G = it.gath >= 0 ? gidx + it.gath : nullptr;
+  const bool bfast = it.b_cs == 1;
+  const int bn = bfast ? (tid & 63) : (tid >> 2), bkq = bfast ? (tid >> 6) : (tid & 3);
+  const int bj = j0 + bn;
+  const uint32_t ob = q_swz(bn, bkq);
+  auto load = [&](cx<float>(&rb)[8], int kc) {
+    const int k0 = klo + kc * Q_BK + bkq * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      cx<float> v = mk<float>(0.f, 0.f);
+      if (bj < it.N && k < khi) {
+        const int64_t kr = G ? G[k] : (int64_t)k;
+        v = B[kr * it.b_rs + (int64_t)bj * it.b_cs];
+      }
+      rb[e] = v;
+    }
+  };
+  cx<float> r0[8], r1[8];
+  if (tid < Q_NPROD) {
+    if (nk > 0) load(r0, 0);
+    if (nk > 1) load(r1, 1);
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
                  "r"(Q_TMEM_COLS));
@@ -190,28 +211,7 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   const uint32_t tmem = *taddr_s;
   const uint32_t sbase = smem_u32(sm);
   if (tid < Q_NPROD) {
-    // ---- B producers: thread -> (B column, 8 consecutive k), the fast
-    // thread index along B's contiguous dimension (coalesced loads); two
-    // chunks in flight in registers
-    const cx<float> *B = bufs.p[it.bbuf] + it.b;
-    const int64_t *G = it.gath >= 0 ? gidx + it.gath : nullptr;
-    const bool bfast = it.b_cs == 1;
-    const int bn = bfast ? (tid & 63) : (tid >> 2), bkq = bfast ? (tid >> 6) : (tid & 3);
-    const int bj = j0 + bn;
-    const uint32_t ob = q_swz(bn, bkq);
-    auto load = [&](cx<float>(&rb)[8], int kc) {
-      const int k0 = klo + kc * Q_BK + bkq * 8;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = k0 + e;
-        cx<float> v = mk<float>(0.f, 0.f);
-        if (bj < it.N && k < khi) {
-          const int64_t kr = G ? G[k] : (int64_t)k;
-          v = B[kr * it.b_rs + (int64_t)bj * it.b_cs];
-        }
-        rb[e] = v;
-      }
-    };
+    // ---- B producers (the first two chunks were loaded above)
     auto produce = [&](const cx<float>(&rb)[8], int kc) -> bool {
       const int s = kc % Q_STAGES;
       if (kc >= Q_STAGES &&
@@ -230,9 +230,6 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
       mbar_arrive(smem_u32(bfull + s));
       return true;
     };
-    cx<float> r0[8], r1[8];
-    if (nk > 0) load(r0, 0);
-    if (nk > 1) load(r1, 1);
     for (int kc = 0; kc < nk; kc += 2) {
       if (!produce(r0, kc)) break;
       if (kc + 2 < nk) load(r0, kc + 2);
@@ -328,25 +325,33 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   }
   __syncthreads();
   if (ok) {
-    cx<float> *C = bufs.p[it.cbuf] + it.c;
+    // thread -> columns lane, lane + 32 of rows warp, warp + 10, ...; with
+    // beta every old value of C is loaded before the first store, so the
+    // loads are in flight together
+    constexpr int NW = Q_THREADS / 32, RPW = (Q_BM + NW - 1) / NW;
+    cx<float> *C = cg_buf(bufs, it.cbuf) + it.c;
     const float al = it.alpha;
-    for (int row = warp; row < Q_BM; row += Q_THREADS / 32) {
-      const int i = i0 + row;
-      if (i >= it.M) continue;
-      for (int cc = lane; cc < Q_BN; cc += 32) {
-        const int j = j0 + cc;
-        if (j >= it.N) continue;
-        const float2 a = stg[row * Q_CPITCH + cc];
-        cx<float> *d = C + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
-        cx<float> v = mk<float>(al * a.x, al * a.y);
-        if (it.beta) {
-          const cx<float> o = *d;
-          v.re += o.re;
-          v.im += o.im;
-        }
-        *d = v;
+    cx<float> old[RPW][2];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = warp + NW * q, i = i0 + row, j = j0 + lane + 32 * h;
+        old[q][h] = (it.beta && row < Q_BM && i < it.M && j < it.N)
+                        ? C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs]
+                        : mk<float>(0.f, 0.f);
       }
-    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = warp + NW * q, i = i0 + row, cc = lane + 32 * h, j = j0 + cc;
+        if (row < Q_BM && i < it.M && j < it.N) {
+          const float2 a = stg[row * Q_CPITCH + cc];
+          C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs] =
+              mk<float>(al * a.x + old[q][h].re, al * a.y + old[q][h].im);
+        }
+      }
   } else if (tid == 0) {
     atomicExch(err, 1);
   }
