@@ -258,17 +258,20 @@ __global__ void __launch_bounds__(128, 1)
               W[(int64_t)(c0 + q) * t.ldc] = make_float2(__uint_as_float(vr[q]) + __uint_as_float(cr[q]),
                                                          __uint_as_float(vi[q]) + __uint_as_float(ci[q]));
         } else {
+          // every old value is loaded before the first store (one round of
+          // loads in flight instead of 32 load-store round trips)
           cx<float> *C = front + t.c_off + r;
           const int cmax = t.diag ? min(t.N, r + 1) : t.N;
+          cx<float> old[32];
 #pragma unroll
           for (int q = 0; q < 32; ++q)
-            if (c0 + q < cmax) {
-              cx<float> *d = C + (int64_t)(c0 + q) * t.ldc;
-              cx<float> v = *d;
-              v.re -= __uint_as_float(vr[q]) + __uint_as_float(cr[q]);
-              v.im -= __uint_as_float(vi[q]) + __uint_as_float(ci[q]);
-              *d = v;
-            }
+            old[q] = c0 + q < cmax ? C[(int64_t)(c0 + q) * t.ldc] : mk<float>(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (c0 + q < cmax)
+              C[(int64_t)(c0 + q) * t.ldc] =
+                  mk<float>(old[q].re - (__uint_as_float(vr[q]) + __uint_as_float(cr[q])),
+                            old[q].im - (__uint_as_float(vi[q]) + __uint_as_float(ci[q])));
         }
       }
     }
