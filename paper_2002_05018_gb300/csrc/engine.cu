@@ -140,14 +140,22 @@ __global__ void __launch_bounds__(256) k_extend_add(const int32_t *__restrict__ 
   const int i = I * 32 + (threadIdx.x & 31);
   if (i >= n) return;
   const int64_t ri = map[i];
-  for (int jj = threadIdx.x >> 5; jj < 32; jj += 8) {
-    int j = J * 32 + jj;
-    if (j > i || j >= n) continue;
-    cx<T> v = C[(int64_t)(pc + i) + (int64_t)(pc + j) * mc];
-    cx<T> *dst = F + ri + (int64_t)map[j] * mq;
-    dst->re += v.re;
-    dst->im += v.im;
+  // all loads (child entries, map, parent entries) before the first store
+  cx<T> v[4], o[4];
+  int64_t cj[4];
+  bool ok[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = J * 32 + (threadIdx.x >> 5) + 8 * u;
+    ok[u] = j <= i && j < n;
+    v[u] = ok[u] ? C[(int64_t)(pc + i) + (int64_t)(pc + j) * mc] : mk<T>(0, 0);
+    cj[u] = ok[u] ? (int64_t)map[j] : 0;
   }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) o[u] = ok[u] ? F[ri + cj[u] * mq] : mk<T>(0, 0);
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (ok[u]) F[ri + cj[u] * mq] = mk<T>(o[u].re + v[u].re, o[u].im + v[u].im);
 }
 
 // ------------------------------------------------------------ reciprocal
@@ -1101,9 +1109,19 @@ __global__ void __launch_bounds__(128) k_l21(const int32_t *__restrict__ lvl, Fr
   __shared__ int s_src[NB];   // source column of panel column t
   __shared__ int2 s_out[NB];  // moves right of the panel: (destination, source)
   __shared__ int s_nout;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    int a = e % NB, b = e / NB;
-    L11[a][b] = (a < kb && b < a) ? F[k0 + a + (int64_t)(k0 + b) * ld] : mk<T>(0, 0);
+  {  // L11 of the panel: every load issued before the first shared store
+    constexpr int NE = NB * NB / 128;
+    cx<T> v[NE];
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      const int e = threadIdx.x + 128 * u, a = e % NB, b = e / NB;
+      v[u] = (a < kb && b < a) ? F[k0 + a + (int64_t)(k0 + b) * ld] : mk<T>(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      const int e = threadIdx.x + 128 * u;
+      L11[e % NB][e / NB] = v[u];
+    }
   }
   if (threadIdx.x < NB) {
     int t = threadIdx.x;
@@ -1335,13 +1353,24 @@ __global__ void __launch_bounds__(256)
     }
   }
   for (int t0 = 0; t0 < kb; t0 += KC) {
-    if (t0 > 0) __syncthreads();
-    for (int e = threadIdx.x; e < KC * UT; e += 256) {
+    // every load of the chunk is issued before the first shared store
+    constexpr int NE = KC * UT / 256;
+    cx<T> lr[NE], wr[NE];
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      const int e = threadIdx.x + 256 * u;
       const int r = e % UT, tt = e / UT;
       const int gi = r0 + r, gc = cc0 + r;
       const bool ok = t0 + tt < kb;
-      Ls[tt][r] = (ok && gi >= rlo && gi < rhi) ? F[gi + (int64_t)(k0 + t0 + tt) * ld] : mk<T>(0, 0);
-      Ws[tt][r] = (ok && gc < chi) ? W[gc + (int64_t)(t0 + tt) * ld] : mk<T>(0, 0);
+      lr[u] = (ok && gi >= rlo && gi < rhi) ? F[gi + (int64_t)(k0 + t0 + tt) * ld] : mk<T>(0, 0);
+      wr[u] = (ok && gc < chi) ? W[gc + (int64_t)(t0 + tt) * ld] : mk<T>(0, 0);
+    }
+    if (t0 > 0) __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      Ls[e / UT][e % UT] = lr[u];
+      Ws[e / UT][e % UT] = wr[u];
     }
     __syncthreads();
     const int nt = min(KC, kb - t0);
@@ -1797,6 +1826,20 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
     }
   }
   const T al = (T)it.alpha;
+  // beta: every old value is loaded before the first store (the stores could
+  // alias later loads, so the compiler would otherwise serialise them)
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      const int i = i0 + tr + 16 * a, j = j0 + tc + 16 * b;
+      acc[a][b] = mk<T>(al * acc[a][b].re, al * acc[a][b].im);
+      if (it.beta && i < it.M && j < it.N) {
+        const cx<T> o = C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs];
+        acc[a][b].re += o.re;
+        acc[a][b].im += o.im;
+      }
+    }
 #pragma unroll
   for (int a = 0; a < RA; ++a) {
     const int i = i0 + tr + 16 * a;
@@ -1805,14 +1848,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
     for (int b = 0; b < RB; ++b) {
       const int j = j0 + tc + 16 * b;
       if (j >= it.N) continue;
-      cx<T> *d = C + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs;
-      cx<T> v = mk<T>(al * acc[a][b].re, al * acc[a][b].im);
-      if (it.beta) {
-        const cx<T> o = *d;
-        v.re += o.re;
-        v.im += o.im;
-      }
-      *d = v;
+      C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs] = acc[a][b];
     }
   }
 }
@@ -3628,6 +3664,15 @@ static int solve_items(Ctx &c, int r) {
   return D3M_OK;
 }
 
+// x-extent of the grid of a per-front sweep kernel (256 threads, grid-strided
+// over `work` elements of each of nf fronts): one element per thread up to
+// about 2048 CTAs in all (every grid-stride step of these kernels is a chain
+// of dependent loads), at least 64 CTAs per front.
+static unsigned sweep_grid(int64_t work, int nf) {
+  const int64_t cap = std::max<int64_t>(64, 2048 / std::max(1, nf));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, cap));
+}
+
 // One pass of the factored operator: xM = M^{-1} bM (in the factor precision).
 // dir: 1 forward sweep only, 2 backward sweep only, 3 both (eager).
 template <typename T>
@@ -3660,12 +3705,12 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const int32_t *lvl = d->lvl_fronts + P.level_ptr[l];
     int64_t work = (int64_t)d->level_maxm[l] * r;
     ++nl;
-    dim3 gi((unsigned)std::min<int64_t>((work + 255) / 256, 64), nf);
+    dim3 gi(sweep_grid(work, nf), nf);
     k_fwd_init<T><<<gi, 256, 0, s>>>(lvl, ft, d->perm, (const cx<T> *)d->bM, Y, r);
     for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
       int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
       if (nk == 0) continue;
-      dim3 g((unsigned)std::min<int64_t>(((int64_t)d->level_maxm[l] * r + 255) / 256, 64), nk);
+      dim3 g(sweep_grid((int64_t)d->level_maxm[l] * r, nk), nk);
       k_fwd_ea<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, d->iperm, Y, r);
       ++nl;
     }
@@ -3674,7 +3719,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
       launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->qpl,
                       d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][0]);
       nl += reduce(l, 0);
-      dim3 gdv((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
+      dim3 gdv(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
       k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
@@ -3704,7 +3749,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
       ++nl;
     }
     if (use_inv) {
-      dim3 gw((unsigned)std::min<int64_t>(((int64_t)d->level_maxp[l] * r + 255) / 256, 64), nf);
+      dim3 gw(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
       k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
       launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->qpl,
                       d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][3]);
