@@ -1037,9 +1037,19 @@ __global__ void __launch_bounds__(512)
     const int ncol = (k0 + CS - 1) / CS, c_lo = rank * ncol, c_hi = min(k0, c_lo + ncol);
     for (int cb = c_lo; cb < c_hi; cb += cpc) {
       const int nc = min(cpc, c_hi - cb), ne = nc * nmv;
-      for (int e = tid; e < ne; e += nth) {
-        const int2 mv = s_mv[e % nmv];
-        Ls[e] = F[mv.y + (int64_t)(cb + e / nmv) * ld];
+      for (int e0 = tid; e0 < ne; e0 += 8 * nth) {  // 8 loads in flight per thread
+        cx<T> v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * nth;
+          if (e < ne) {
+            const int2 mv = s_mv[e % nmv];
+            v[u] = F[mv.y + (int64_t)(cb + e / nmv) * ld];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (e0 + u * nth < ne) Ls[e0 + u * nth] = v[u];
       }
       __syncthreads();
       for (int e = tid; e < ne; e += nth) {
@@ -1204,6 +1214,30 @@ static int panel_cluster_size(int mmax, size_t esz) {
 // Kernel launch with an optional scheduling priority (lower = more urgent, as
 // for streams; 0 = the stream's own).  The attribute travels with the launch
 // into a captured graph's kernel node, where stream priorities do not.
+// Programmatic dependent launch (the substitution sweeps): a kernel launched
+// with launch_pdl may start while its predecessor in the stream finishes;
+// pdl_wait() blocks the calling thread until the predecessor grid has
+// completed and its writes are visible, so every thread calls it before it
+// touches memory the predecessor writes or reads.  pdl_trigger() lets the
+// successor launch.  Both are no-ops in a kernel launched without the
+// attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_prio(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, int prio,
                                Args... args) {
@@ -1444,6 +1478,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 template <typename T>
 __global__ void k_fwd_init(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ perm,
                            const cx<T> *__restrict__ bM, cx<T> *__restrict__ Y, int r) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   const int f = lvl[blockIdx.y];
   const int m = ft.m[f], p = ft.p[f];
   const int64_t n = (int64_t)m * r;
@@ -1459,6 +1495,8 @@ __global__ void k_fwd_init(const int32_t *__restrict__ lvl, FrontTab ft, const i
 template <typename T>
 __global__ void k_fwd_ea(const int32_t *__restrict__ kids, FrontTab ft, const int32_t *__restrict__ emap,
                          const int32_t *__restrict__ iperm, cx<T> *__restrict__ Y, int r) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   const int c = kids[blockIdx.y];
   const int q = ft.parent[c];
   const int mc = ft.m[c], pc = ft.p[c], pq = ft.p[q];
@@ -1487,6 +1525,8 @@ __global__ void __launch_bounds__(256) k_fwd_solve(const int32_t *__restrict__ l
                                                    const double2 *__restrict__ dinv_o,
                                                    const int8_t *__restrict__ psize, cx<T> *__restrict__ Y,
                                                    cx<T> *__restrict__ zM, int r) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   const int f = lvl[blockIdx.y];
   const int m = ft.m[f], p = ft.p[f];
   const int c0 = blockIdx.x * RC;
@@ -1587,6 +1627,8 @@ __global__ void __launch_bounds__(256) k_bwd_solve(const int32_t *__restrict__ l
                                                    const int64_t *__restrict__ part_off,
                                                    const cx<T> *__restrict__ part, cx<T> *__restrict__ Y,
                                                    const cx<T> *__restrict__ zM, cx<T> *__restrict__ xM, int r) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   const int f = lvl[blockIdx.y];
   const int m = ft.m[f], p = ft.p[f];
   (void)m;
@@ -1745,7 +1787,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
   constexpr int LA = BM * KC / 256, LB = BN * KC / 256;  // staged elements per thread
   const int t = blockIdx.x;
   if (t >= ntiles) return;
-  const CgItem it = items[cg_item_of(items, nitems, t, tmap)];
+  const CgItem it = items[cg_item_of(items, nitems, t, tmap)];  // static tables: before the wait
+  pdl_wait();
+  pdl_trigger();
   const cx<T> *A = cg_buf(bufs, it.abuf) + it.a;
   const cx<T> *B = cg_buf(bufs, it.bbuf) + it.b;
   cx<T> *C = cg_buf(bufs, it.cbuf) + it.c;
@@ -1858,23 +1902,29 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
 // bm: the row tile of the FMA kernel (32, 64 or 128), or 0 for the tensor-core
 // kernel (128 x 64 tiles, complex64 operands only); qpl / err / wait_cap are
 // that kernel's pre-split A blocks, error flag and first-wait bound; tmap, if
-// given, maps each output tile to its item (index relative to `items`).
+// given, maps each output tile to its item (index relative to `items`);
+// pdl: launched as a programmatic dependent of the stream's previous kernel.
 template <typename T>
 static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, const CgBufs<T> &bufs,
                          const int64_t *gidx, cudaStream_t s, const uint16_t *qpl = nullptr,
-                         int32_t *err = nullptr, int wait_cap = 0, const int32_t *tmap = nullptr) {
+                         int32_t *err = nullptr, int wait_cap = 0, const int32_t *tmap = nullptr,
+                         bool pdl = false) {
   if constexpr (sizeof(T) == 4) {
     if (bm == 0) {
-      k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, tmap, qpl, err, wait_cap);
+      if (pdl)
+        launch_pdl(k_tc_cgemm, dim3(ntiles), dim3(Q_THREADS), Q_SMEM, s, items, nitems, ntiles, bufs, gidx, tmap, qpl,
+                   err, wait_cap);
+      else
+        k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, tmap, qpl, err, wait_cap);
       return;
     }
   }
-  if (bm == 32)
-    k_cgemm<T, 32><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
-  else if (bm == 64 || sizeof(T) == 8)
-    k_cgemm<T, 64><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
+  void (*k)(const CgItem *, int, int, CgBufs<T>, const int64_t *, const int32_t *) =
+      bm == 32 ? k_cgemm<T, 32> : (bm == 64 || sizeof(T) == 8) ? k_cgemm<T, 64> : k_cgemm<T, (sizeof(T) == 4 ? 128 : 64)>;
+  if (pdl)
+    launch_pdl(k, dim3(ntiles), dim3(256), 0, s, items, nitems, ntiles, bufs, gidx, tmap);
   else
-    k_cgemm<T, (sizeof(T) == 4 ? 128 : 64)><<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
+    k<<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
 }
 
 // Split-K: a product whose launch has few output tiles and a long k range is
@@ -1889,6 +1939,8 @@ struct SkItem {
 template <typename T>
 __global__ void k_splitk_reduce(const SkItem *__restrict__ items, int nitems, int64_t nelem, CgBufs<T> bufs,
                                 const cx<T> *__restrict__ part) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nelem; e += (int64_t)gridDim.x * blockDim.x) {
     int lo = 0, hi = nitems - 1;  // last item with elem0 <= e
     while (lo < hi) {
@@ -1953,6 +2005,8 @@ template <typename T>
 __global__ void k_fwd_dinv(const int32_t *__restrict__ lvl, FrontTab ft, const double2 *__restrict__ dinv_d,
                            const double2 *__restrict__ dinv_o, const int8_t *__restrict__ psize,
                            const cx<T> *__restrict__ Y2, cx<T> *__restrict__ zM, int r) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   const int f = lvl[blockIdx.y];
   const int p = ft.p[f];
   const cx<T> *Yf = Y2 + ft.yoff[f] * r;
@@ -1978,6 +2032,8 @@ template <typename T>
 __global__ void k_bwd_w(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ nsplit,
                         const int64_t *__restrict__ part_off, const cx<T> *__restrict__ part,
                         const cx<T> *__restrict__ zM, cx<T> *__restrict__ Y, int r) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   const int f = lvl[blockIdx.y];
   const int p = ft.p[f];
   cx<T> *Yf = Y + ft.yoff[f] * r;
@@ -2001,6 +2057,8 @@ __global__ void k_bwd_w(const int32_t *__restrict__ lvl, FrontTab ft, const int3
 template <typename T>
 __global__ void k_bwd_out(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ perm,
                           const cx<T> *__restrict__ Y2, cx<T> *__restrict__ xM, int r) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
   const int f = lvl[blockIdx.y];
   const int p = ft.p[f];
   const cx<T> *Yf = Y2 + ft.yoff[f] * r;
@@ -3693,8 +3751,9 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const auto &k3 = d->sk_lvl[l];
     if (k3[3 * kind + 1] == 0) return 0;
     const int64_t ne = k3[3 * kind + 2];
-    k_splitk_reduce<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((ne + 255) / 256, 1216)), 256, 0, s>>>(
-        d->sk_items + k3[3 * kind + 0], k3[3 * kind + 1], ne, bufs, (const cx<T> *)d->skp);
+    launch_pdl(k_splitk_reduce<T>, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ne + 255) / 256, 1216))),
+               dim3(256), 0, s, (const SkItem *)(d->sk_items + k3[3 * kind + 0]), k3[3 * kind + 1], ne, bufs,
+               (const cx<T> *)d->skp);
     return 1;
   };
   int64_t nl = 0;
@@ -3706,29 +3765,32 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     int64_t work = (int64_t)d->level_maxm[l] * r;
     ++nl;
     dim3 gi(sweep_grid(work, nf), nf);
-    k_fwd_init<T><<<gi, 256, 0, s>>>(lvl, ft, d->perm, (const cx<T> *)d->bM, Y, r);
+    launch_pdl(k_fwd_init<T>, gi, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)d->bM, Y, r);
     for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
       int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
       if (nk == 0) continue;
       dim3 g(sweep_grid((int64_t)d->level_maxm[l] * r, nk), nk);
-      k_fwd_ea<T><<<g, 256, 0, s>>>(d->ea_child + P.ea_ptr[q], ft, d->emap, d->iperm, Y, r);
+      launch_pdl(k_fwd_ea<T>, g, dim3(256), 0, s, (const int32_t *)(d->ea_child + P.ea_ptr[q]), ft,
+                 (const int32_t *)d->emap, (const int32_t *)d->iperm, Y, r);
       ++nl;
     }
     const auto &sl = d->sol_lvl[l];
     if (use_inv) {
       launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][0]);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][0], true);
       nl += reduce(l, 0);
       dim3 gdv(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
-      k_fwd_dinv<T><<<gdv, 256, 0, s>>>(lvl, ft, d->dinv_d, d->dinv_o, d->psize, Y2, (cx<T> *)d->zM, r);
+      launch_pdl(k_fwd_dinv<T>, gdv, dim3(256), 0, s, lvl, ft, (const double2 *)d->dinv_d,
+                 (const double2 *)d->dinv_o, (const int8_t *)d->psize, (const cx<T> *)Y2, (cx<T> *)d->zM, r);
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
-      k_fwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->dinv_d, d->dinv_o, d->psize, Y, (cx<T> *)d->zM, r);
+      launch_pdl(k_fwd_solve<T, RC>, gs, dim3(256), 0, s, lvl, ft, (const cx<T> *)arena, (const double2 *)d->dinv_d,
+                 (const double2 *)d->dinv_o, (const int8_t *)d->psize, Y, (cx<T> *)d->zM, r);
     }
     nl += 2;
     if (sl[5] > 0) {
       launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][1]);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][1], true);
       nl += reduce(l, 1);
       ++nl;
     }
@@ -3745,21 +3807,24 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const auto &sl = d->sol_lvl[l];
     if (sl[9] > 0) {
       launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][2]);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][2], true);
       ++nl;
     }
     if (use_inv) {
       dim3 gw(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
-      k_bwd_w<T><<<gw, 256, 0, s>>>(lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y, r);
+      launch_pdl(k_bwd_w<T>, gw, dim3(256), 0, s, lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y,
+                 r);
       launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][3]);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][3], true);
       nl += reduce(l, 3);
-      k_bwd_out<T><<<gw, 256, 0, s>>>(lvl, ft, d->perm, Y2, (cx<T> *)d->xM, r);
+      launch_pdl(k_bwd_out<T>, gw, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)Y2,
+                 (cx<T> *)d->xM, r);
       nl += 3;
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
-      k_bwd_solve<T, RC><<<gs, 256, 0, s>>>(lvl, ft, arena, d->perm, d->psize, ns, po, (const cx<T> *)d->part, Y,
-                                            (const cx<T> *)d->zM, (cx<T> *)d->xM, r);
+      launch_pdl(k_bwd_solve<T, RC>, gs, dim3(256), 0, s, lvl, ft, (const cx<T> *)arena, (const int32_t *)d->perm,
+                 (const int8_t *)d->psize, ns, po, (const cx<T> *)d->part, Y, (const cx<T> *)d->zM, (cx<T> *)d->xM,
+                 r);
       ++nl;
     }
   }

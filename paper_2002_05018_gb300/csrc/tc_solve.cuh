@@ -24,8 +24,10 @@
 // k_tc_cgemm: one CTA per 128 x 64 output tile, 320 threads.  Warps 0-7
 // load the tile's B chunks (32 x 64 complex64, rows optionally gathered),
 // two chunks ahead in registers, split them and store their planes; one
-// thread of warp 8 issues the A bulk copies; one thread of warp 9 issues the
-// MMAs (M = 128, N = 64, K = 16; 24 per k-step of 16).  The epilogue stages
+// thread of warp 8 issues the A bulk copies (the first three before the
+// programmatic wait for the preceding kernel of the sweep, since A is
+// static); one thread of warp 9 issues the MMAs (M = 128, N = 64, K = 16;
+// 24 per k-step of 16).  The epilogue stages
 // the accumulators through shared memory and writes C one row at a time,
 // coalesced along the right-hand sides.  Every mbarrier wait is bounded: on
 // expiry the tile raises `err`, stops, waits (bounded) for its MMAs and bulk
@@ -184,10 +186,6 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
     }
   };
   cx<float> r0[8], r1[8];
-  if (tid < Q_NPROD) {
-    if (nk > 0) load(r0, 0);
-    if (nk > 1) load(r1, 1);
-  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
                  "r"(Q_TMEM_COLS));
@@ -210,8 +208,22 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *taddr_s;
   const uint32_t sbase = smem_u32(sm);
+  // the A blocks are static (written by the factorisation): the first stages
+  // are requested before waiting for the predecessor in the sweep
+  const uint16_t *asrc = qpl + (it.qa + q_rowbase(it.mode, it.qnk, tm) + klo / Q_BK) * (int64_t)(Q_ABLK / 2);
+  const int kpre = min(nk, Q_STAGES);
+  if (tid == Q_NPROD)
+    for (int kc = 0; kc < kpre; ++kc) {
+      const uint32_t fa = smem_u32(afull + kc);
+      mbar_expect_tx(fa, Q_ABLK);
+      bulk_load(sbase + kc * Q_STAGE_BYTES, asrc + (int64_t)kc * (Q_ABLK / 2), Q_ABLK, fa);
+    }
+  pdl_wait();  // B and C are written by the preceding kernels of the sweep
+  pdl_trigger();
   if (tid < Q_NPROD) {
-    // ---- B producers (the first two chunks were loaded above)
+    // ---- B producers
+    if (nk > 0) load(r0, 0);
+    if (nk > 1) load(r1, 1);
     auto produce = [&](const cx<float>(&rb)[8], int kc) -> bool {
       const int s = kc % Q_STAGES;
       if (kc >= Q_STAGES &&
@@ -240,8 +252,8 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
     }
   } else if (tid == Q_NPROD) {
     // ---- A loader: one bulk copy of a pre-split 48 KB block per k chunk
-    const uint16_t *src = qpl + (it.qa + q_rowbase(it.mode, it.qnk, tm) + klo / Q_BK) * (int64_t)(Q_ABLK / 2);
-    int kc = 0;
+    // (the first kpre were issued before the wait)
+    int kc = kpre;
     for (; kc < nk; ++kc) {
       const int s = kc % Q_STAGES;
       if (kc >= Q_STAGES &&
@@ -252,7 +264,7 @@ __global__ void __launch_bounds__(Q_THREADS, 1)
       if (*abort_s) break;
       const uint32_t fa = smem_u32(afull + s);
       mbar_expect_tx(fa, Q_ABLK);
-      bulk_load(sbase + s * Q_STAGE_BYTES, src + (int64_t)kc * (Q_ABLK / 2), Q_ABLK, fa);
+      bulk_load(sbase + s * Q_STAGE_BYTES, asrc + (int64_t)kc * (Q_ABLK / 2), Q_ABLK, fa);
     }
     *issuedA_s = kc;
   } else if (tid == Q_NPROD + 32) {
