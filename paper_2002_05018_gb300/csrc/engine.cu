@@ -1224,7 +1224,8 @@ static int panel_cluster_size(int mmax, size_t esz) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args... args) {
+static cudaError_t launch_pdl(bool on, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                              Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = g;
   cfg.blockDim = b;
@@ -1234,7 +1235,7 @@ static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, 
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = on ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
@@ -1475,44 +1476,36 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 
 // ------------------------------------------------------------ solve kernels
 // Vectors in M space and front-local vectors are row-major (RHS fastest).
+// The forward sweep's right-hand side of every front of a level, in one
+// pass: row k (pivot order) of front f is its entry of bM (pivot rows) plus
+// the child update rows that extend-add into it, listed in a static CSR
+// keyed by the parent's original row (gptr / gsrc: Y rows of the children);
+// the pivot order maps position k to original row pv[k] at run time.
+// One read of each source and one write of each row (no read-modify-write
+// passes over the parent rows, one launch per level).
 template <typename T>
-__global__ void k_fwd_init(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ perm,
-                           const cx<T> *__restrict__ bM, cx<T> *__restrict__ Y, int r) {
+__global__ void k_fwd_gather(const int32_t *__restrict__ lvl, FrontTab ft, const int32_t *__restrict__ perm,
+                             const cx<T> *__restrict__ bM, const int64_t *__restrict__ gptr,
+                             const int64_t *__restrict__ gsrc, cx<T> *__restrict__ Y, int r) {
   pdl_wait();  // the predecessor in the sweep has finished
   pdl_trigger();
   const int f = lvl[blockIdx.y];
   const int m = ft.m[f], p = ft.p[f];
-  const int64_t n = (int64_t)m * r;
-  cx<T> *Yf = Y + ft.yoff[f] * r;
+  const int64_t n = (int64_t)m * r, y0 = ft.yoff[f];
+  cx<T> *Yf = Y + y0 * r;
   const int32_t *pv = perm + ft.piv[f];
   const int64_t st = ft.start[f];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / r), c = (int)(e % r);
-    Yf[e] = i < p ? bM[(st + pv[i]) * r + c] : mk<T>(0, 0);
-  }
-}
-
-template <typename T>
-__global__ void k_fwd_ea(const int32_t *__restrict__ kids, FrontTab ft, const int32_t *__restrict__ emap,
-                         const int32_t *__restrict__ iperm, cx<T> *__restrict__ Y, int r) {
-  pdl_wait();  // the predecessor in the sweep has finished
-  pdl_trigger();
-  const int c = kids[blockIdx.y];
-  const int q = ft.parent[c];
-  const int mc = ft.m[c], pc = ft.p[c], pq = ft.p[q];
-  const int64_t n = (int64_t)(mc - pc) * r;
-  const cx<T> *Yc = Y + (ft.yoff[c] + pc) * r;
-  cx<T> *Yq = Y + ft.yoff[q] * r;
-  const int32_t *map = emap + ft.soff[c];
-  const int32_t *ip = iperm + ft.piv[q];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / r), cc = (int)(e % r);
-    int tgt = map[i];
-    if (tgt < pq) tgt = ip[tgt];
-    cx<T> v = Yc[e];
-    cx<T> *d = Yq + (int64_t)tgt * r + cc;
-    d->re += v.re;
-    d->im += v.im;
+    const int k = (int)(e / r), c = (int)(e % r);
+    const int o = k < p ? pv[k] : k;
+    cx<T> v = k < p ? bM[(st + o) * r + c] : mk<T>(0, 0);
+    const int64_t q0 = gptr[y0 + o], q1 = gptr[y0 + o + 1];
+    for (int64_t q = q0; q < q1; ++q) {
+      const cx<T> u = Y[gsrc[q] * r + c];
+      v.re += u.re;
+      v.im += u.im;
+    }
+    Yf[e] = v;
   }
 }
 
@@ -1870,29 +1863,35 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && BM <= 64) ? 2 : 1) k_c
     }
   }
   const T al = (T)it.alpha;
-  // beta: every old value is loaded before the first store (the stores could
-  // alias later loads, so the compiler would otherwise serialise them)
+  // beta: the old values are loaded before the stores (the stores could alias
+  // later loads, so the compiler would otherwise serialise every element):
+  // all of them at once in fp32; one tile row (RB values) at a time in fp64,
+  // whose wider accumulators leave no registers for all of them
+  constexpr int GA = sizeof(T) == 4 ? RA : 1;
 #pragma unroll
-  for (int a = 0; a < RA; ++a)
+  for (int a0 = 0; a0 < RA; a0 += GA) {
 #pragma unroll
-    for (int b = 0; b < RB; ++b) {
-      const int i = i0 + tr + 16 * a, j = j0 + tc + 16 * b;
-      acc[a][b] = mk<T>(al * acc[a][b].re, al * acc[a][b].im);
-      if (it.beta && i < it.M && j < it.N) {
-        const cx<T> o = C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs];
-        acc[a][b].re += o.re;
-        acc[a][b].im += o.im;
+    for (int a = a0; a < a0 + GA; ++a)
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const int i = i0 + tr + 16 * a, j = j0 + tc + 16 * b;
+        acc[a][b] = mk<T>(al * acc[a][b].re, al * acc[a][b].im);
+        if (it.beta && i < it.M && j < it.N) {
+          const cx<T> o = C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs];
+          acc[a][b].re += o.re;
+          acc[a][b].im += o.im;
+        }
       }
-    }
 #pragma unroll
-  for (int a = 0; a < RA; ++a) {
-    const int i = i0 + tr + 16 * a;
-    if (i >= it.M) continue;
+    for (int a = a0; a < a0 + GA; ++a) {
+      const int i = i0 + tr + 16 * a;
+      if (i >= it.M) continue;
 #pragma unroll
-    for (int b = 0; b < RB; ++b) {
-      const int j = j0 + tc + 16 * b;
-      if (j >= it.N) continue;
-      C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs] = acc[a][b];
+      for (int b = 0; b < RB; ++b) {
+        const int j = j0 + tc + 16 * b;
+        if (j >= it.N) continue;
+        C[(int64_t)i * it.c_rs + (int64_t)j * it.c_cs] = acc[a][b];
+      }
     }
   }
 }
@@ -1912,7 +1911,7 @@ static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, co
   if constexpr (sizeof(T) == 4) {
     if (bm == 0) {
       if (pdl)
-        launch_pdl(k_tc_cgemm, dim3(ntiles), dim3(Q_THREADS), Q_SMEM, s, items, nitems, ntiles, bufs, gidx, tmap, qpl,
+        launch_pdl(true, k_tc_cgemm, dim3(ntiles), dim3(Q_THREADS), Q_SMEM, s, items, nitems, ntiles, bufs, gidx, tmap, qpl,
                    err, wait_cap);
       else
         k_tc_cgemm<<<ntiles, Q_THREADS, Q_SMEM, s>>>(items, nitems, ntiles, bufs, gidx, tmap, qpl, err, wait_cap);
@@ -1922,7 +1921,7 @@ static void launch_cgemm(int bm, int ntiles, const CgItem *items, int nitems, co
   void (*k)(const CgItem *, int, int, CgBufs<T>, const int64_t *, const int32_t *) =
       bm == 32 ? k_cgemm<T, 32> : (bm == 64 || sizeof(T) == 8) ? k_cgemm<T, 64> : k_cgemm<T, (sizeof(T) == 4 ? 128 : 64)>;
   if (pdl)
-    launch_pdl(k, dim3(ntiles), dim3(256), 0, s, items, nitems, ntiles, bufs, gidx, tmap);
+    launch_pdl(true, k, dim3(ntiles), dim3(256), 0, s, items, nitems, ntiles, bufs, gidx, tmap);
   else
     k<<<ntiles, 256, 0, s>>>(items, nitems, ntiles, bufs, gidx, tmap);
 }
@@ -2330,6 +2329,7 @@ struct DeviceState {
   int32_t *f_m = nullptr, *f_p = nullptr, *f_parent = nullptr;
   int64_t *f_off = nullptr, *f_piv = nullptr, *f_soff = nullptr, *f_start = nullptr, *f_y = nullptr;
   int32_t *lvl_fronts = nullptr, *ea_child = nullptr, *emap = nullptr;
+  int64_t *g_ptr = nullptr, *g_src = nullptr;  // forward gather: parent row -> child Y rows (CSR)
   int64_t *sidx = nullptr, *ent_off = nullptr, *wofs = nullptr, *owner = nullptr;
   double2 *ent_val = nullptr;
   // factors
@@ -2679,6 +2679,30 @@ static int dev_init(Ctx &c) {
   CUDA_TRY(upload(d, &d->lvl_fronts, P.level_fronts));
   CUDA_TRY(upload(d, &d->ea_child, P.ea_child));
   CUDA_TRY(upload(d, &d->emap, P.emap));
+  {
+    // forward gather: for every front row (original order, Y row y_off + o)
+    // the Y rows of the child update rows that extend-add into it
+    int64_t ny = 0;
+    for (int64_t s2 = 0; s2 < nsn; ++s2) ny = std::max<int64_t>(ny, P.y_off[s2] + m[s2]);
+    std::vector<int64_t> gp((size_t)ny + 1, 0), gs;
+    for (int64_t c2 = 0; c2 < nsn; ++c2) {
+      const int64_t q = P.parent[c2];
+      if (q < 0) continue;
+      for (int i = 0; i < m[c2] - pp[c2]; ++i) gp[(size_t)(P.y_off[q] + P.emap[P.struct_ptr[c2] + i]) + 1]++;
+    }
+    for (int64_t g = 0; g < ny; ++g) gp[(size_t)g + 1] += gp[(size_t)g];
+    gs.resize((size_t)gp[(size_t)ny]);
+    std::vector<int64_t> fill(gp.begin(), gp.end() - 1);
+    for (int64_t c2 = 0; c2 < nsn; ++c2) {
+      const int64_t q = P.parent[c2];
+      if (q < 0) continue;
+      for (int i = 0; i < m[c2] - pp[c2]; ++i)
+        gs[(size_t)fill[(size_t)(P.y_off[q] + P.emap[P.struct_ptr[c2] + i])]++] = P.y_off[c2] + pp[c2] + i;
+    }
+    if (gs.empty()) gs.push_back(0);
+    CUDA_TRY(upload(d, &d->g_ptr, gp));
+    CUDA_TRY(upload(d, &d->g_src, gs));
+  }
   CUDA_TRY(upload(d, &d->sidx, P.struct_idx));
   CUDA_TRY(upload(d, &d->ent_off, P.ent_off));
   CUDA_TRY(upload(d, &d->owner, P.owner_m));
@@ -3744,6 +3768,10 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
   cx<T> *Y2 = (cx<T> *)d->Y2;
   cx<T> *Li = (cx<T> *)d->linv;
   const bool use_inv = sizeof(T) == 4;  // L11^{-1} exists for the mixed factors only
+  // programmatic dependent launches on the mixed sweeps only: the fp64
+  // sweep's long triangular-solve kernels ran slower beside the early
+  // launched, waiting CTAs of their successors
+  const bool pdl = sizeof(T) == 4;
   constexpr int RC = 8;
   const CgBufs<T> bufs{{arena, Li, Y, Y2, (cx<T> *)d->xM, (cx<T> *)d->part, (cx<T> *)d->skp}};
   // the split-K reduction of launch `kind` of level l (if that launch was split)
@@ -3751,7 +3779,7 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const auto &k3 = d->sk_lvl[l];
     if (k3[3 * kind + 1] == 0) return 0;
     const int64_t ne = k3[3 * kind + 2];
-    launch_pdl(k_splitk_reduce<T>, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ne + 255) / 256, 1216))),
+    launch_pdl(pdl, k_splitk_reduce<T>, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ne + 255) / 256, 1216))),
                dim3(256), 0, s, (const SkItem *)(d->sk_items + k3[3 * kind + 0]), k3[3 * kind + 1], ne, bufs,
                (const cx<T> *)d->skp);
     return 1;
@@ -3765,32 +3793,25 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     int64_t work = (int64_t)d->level_maxm[l] * r;
     ++nl;
     dim3 gi(sweep_grid(work, nf), nf);
-    launch_pdl(k_fwd_init<T>, gi, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)d->bM, Y, r);
-    for (int q = P.ea_pass_ptr[l]; q < P.ea_pass_ptr[l + 1]; ++q) {
-      int nk = P.ea_ptr[q + 1] - P.ea_ptr[q];
-      if (nk == 0) continue;
-      dim3 g(sweep_grid((int64_t)d->level_maxm[l] * r, nk), nk);
-      launch_pdl(k_fwd_ea<T>, g, dim3(256), 0, s, (const int32_t *)(d->ea_child + P.ea_ptr[q]), ft,
-                 (const int32_t *)d->emap, (const int32_t *)d->iperm, Y, r);
-      ++nl;
-    }
+    launch_pdl(pdl, k_fwd_gather<T>, gi, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)d->bM,
+               (const int64_t *)d->g_ptr, (const int64_t *)d->g_src, Y, r);
     const auto &sl = d->sol_lvl[l];
     if (use_inv) {
       launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][0], true);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][0], pdl);
       nl += reduce(l, 0);
       dim3 gdv(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
-      launch_pdl(k_fwd_dinv<T>, gdv, dim3(256), 0, s, lvl, ft, (const double2 *)d->dinv_d,
+      launch_pdl(pdl, k_fwd_dinv<T>, gdv, dim3(256), 0, s, lvl, ft, (const double2 *)d->dinv_d,
                  (const double2 *)d->dinv_o, (const int8_t *)d->psize, (const cx<T> *)Y2, (cx<T> *)d->zM, r);
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
-      launch_pdl(k_fwd_solve<T, RC>, gs, dim3(256), 0, s, lvl, ft, (const cx<T> *)arena, (const double2 *)d->dinv_d,
+      launch_pdl(pdl, k_fwd_solve<T, RC>, gs, dim3(256), 0, s, lvl, ft, (const cx<T> *)arena, (const double2 *)d->dinv_d,
                  (const double2 *)d->dinv_o, (const int8_t *)d->psize, Y, (cx<T> *)d->zM, r);
     }
     nl += 2;
     if (sl[5] > 0) {
       launch_cgemm<T>(sl[7], sl[6], d->sol_items + sl[4], sl[5], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][1], true);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][1], pdl);
       nl += reduce(l, 1);
       ++nl;
     }
@@ -3807,22 +3828,22 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     const auto &sl = d->sol_lvl[l];
     if (sl[9] > 0) {
       launch_cgemm<T>(sl[11], sl[10], d->sol_items + sl[8], sl[9], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][2], true);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][2], pdl);
       ++nl;
     }
     if (use_inv) {
       dim3 gw(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
-      launch_pdl(k_bwd_w<T>, gw, dim3(256), 0, s, lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y,
+      launch_pdl(pdl, k_bwd_w<T>, gw, dim3(256), 0, s, lvl, ft, ns, po, (const cx<T> *)d->part, (const cx<T> *)d->zM, Y,
                  r);
       launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->qpl,
-                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][3], true);
+                      d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][3], pdl);
       nl += reduce(l, 3);
-      launch_pdl(k_bwd_out<T>, gw, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)Y2,
+      launch_pdl(pdl, k_bwd_out<T>, gw, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)Y2,
                  (cx<T> *)d->xM, r);
       nl += 3;
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
-      launch_pdl(k_bwd_solve<T, RC>, gs, dim3(256), 0, s, lvl, ft, (const cx<T> *)arena, (const int32_t *)d->perm,
+      launch_pdl(pdl, k_bwd_solve<T, RC>, gs, dim3(256), 0, s, lvl, ft, (const cx<T> *)arena, (const int32_t *)d->perm,
                  (const int8_t *)d->psize, ns, po, (const cx<T> *)d->part, Y, (const cx<T> *)d->zM, (cx<T> *)d->xM,
                  r);
       ++nl;
