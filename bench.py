@@ -141,6 +141,8 @@ def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=Fal
     launches) for the kernel breakdown and the roofline.  Returns a dict."""
     import torch
     from paper_2002_05018_gb300 import d3m
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     s = d3m.Solver.from_workload(w, precision=prec, stream=stream, profile=False, update_kernel=update_kernel,
                                  autotune_cache=None if cache is None else f"{cache}.{'mixed' if prec else 'fp64'}")
     st0 = s.stats()
@@ -153,6 +155,9 @@ def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=Fal
         s.solve(rhs_dev, x)
     _barrier(ws)
     torch.cuda.synchronize()
+    # device memory held by this context after its first factor + solve (the
+    # library allocates with cudaMalloc, outside torch's allocator)
+    device_bytes = free0 - torch.cuda.mem_get_info()[0]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     acc = {k: 0.0 for k in ("ms_update", "ms_panel", "ms_assemble", "ms_inverse", "ms_tc", "ms_fwd", "ms_bwd",
@@ -204,7 +209,7 @@ def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=Fal
                step_ms_each=[round(v, 3) for v in step_ms], factor_ms_each=[round(v, 3) for v in fac_ms],
                step_ms=statistics.mean(step_ms), max_step_ms=max(step_ms), wall_s=t_wall,
                iters=max(i["iters"] for i in infos), max_resid=max(i["max_resid"] for i in infos),
-               launches=launches, clocks=clocks, stats=stats,
+               launches=launches, clocks=clocks, stats=stats, device_bytes=device_bytes,
                prof={k: v / steps for k, v in acc.items()})
     return out
 
@@ -397,6 +402,7 @@ def precision_summary(r, peaks, prec_tag, config, nrhs):
             "solve_ms": round(r["solve_ms"], 3), "refine_steps": r["iters"],
             "max_resid": r["max_resid"], "ms_per_step": round(r["step_ms"], 3),
             "ms_each_step": r.get("step_ms_each"), "factor_ms_each_step": r.get("factor_ms_each"),
+            "device_gb": (round(r["device_bytes"] / 1e9, 2) if r.get("device_bytes") is not None else None),
             "kernel_ms": {k: round(v, 3) for k, v in r["prof"].items() if k.startswith("ms_")},
             "schedule": {"levels": r["stats"]["n_levels"],
                          "tcgen05_update_levels": r["stats"]["tuned_levels_tc"],

@@ -153,6 +153,15 @@ typedef struct {
                            kernel, fp32 accumulation in tensor memory; 1 = fp32
                            FMA on the complex64 factors.  FP64 always uses fp64
                            FMA. */
+  int32_t lm_weight;    /* multiplier map D of Eq. (1): 0 = signed Boolean (+1 on
+                           the lower-index copy of an interface edge, -1 on the
+                           other; default); 1 = the Galerkin form of the Theory
+                           section's lambda = j +- e in the tangential edge basis:
+                           D = D_bool T_lambda with T_lambda the tangential face
+                           mass int_f N_m . N_l dS between the multipliers of one
+                           interface block.  Symmetric positive definite per
+                           block, so E does not change; lambda, K_D and K do
+                           (lambda_1 = T_lambda^{-1} lambda_0). */
 } d3m_options;
 /* d3m_setup returns D3M_EINVAL (and the context, for d3m_last_error) when an
  * option lies outside the values listed above. */

@@ -51,6 +51,8 @@ class Decomposition:
     lm_minus: np.ndarray       # subdomain with -1
     blocks: list               # list of (a, b) pairs, block id = position
     block_lms: list            # block id -> array of multiplier ids
+    lm_weight: int = 0         # 0: signed Boolean D; 1: D_bool T_lambda (see multiplier_mass)
+    T_lambda: sp.csr_matrix | None = None
 
 
 def sub_index(pos, parts):
@@ -119,7 +121,9 @@ def decompose(w, with_matrices=True) -> Decomposition:
         lm_minus += [b] * len(es)
     dec = Decomposition(g, parts, subs, copies, np.array(lm_edge, np.int64),
                         np.array(lm_plus, np.int64), np.array(lm_minus, np.int64),
-                        list(block_order), block_lms)
+                        list(block_order), block_lms, int(getattr(w, "lm_weight", 0) or 0))
+    if dec.lm_weight:
+        dec.T_lambda = multiplier_mass(dec)
     if with_matrices:
         for sd in subs:
             sd.A = subdomain_matrix(w, dec, sd)
@@ -162,7 +166,51 @@ def subdomain_matrix(w, dec: Decomposition, sd: Subdomain):
     return sp.csr_matrix((v[keep], (loc[r[keep]], loc[c[keep]])), shape=(n, n))
 
 
+def multiplier_mass(dec: Decomposition):
+    """T_lambda (n_lambda x n_lambda): the Galerkin reading of the Theory
+    section's multiplier lambda = j +- e.  With lambda expanded in the same
+    tangential edge basis as the trace of E, the coupling of multipliers m and
+    l of one interface block (a, b) is the tangential face mass
+    int_f N_m . N_l dS over the cut face between subdomains a and b; there is
+    no coupling across blocks.  D = D_bool T_lambda."""
+    g = dec.grid
+    lm_of = {(int(a), int(b), int(e)): l
+             for l, (e, a, b) in enumerate(zip(dec.lm_edge, dec.lm_plus, dec.lm_minus))}
+    ce_all = g.cell_edges()
+    rows, cols, vals = [], [], []
+    for (a, b) in dec.blocks:
+        sd = dec.subs[a]
+        for axis, side, cid, _ in interface_faces(dec, sd, 1.0):
+            npos = list(sd.grid_pos)
+            npos[axis] += -1 if side == 0 else 1
+            if sub_index(npos, dec.parts) != b:
+                continue
+            T = fem.face_matrix(g.h, axis, side)
+            for c in cid:
+                ce = ce_all[c]
+                for i in range(12):
+                    m = lm_of.get((a, b, int(ce[i])))
+                    if m is None:
+                        continue
+                    for j in range(12):
+                        l = lm_of.get((a, b, int(ce[j])))
+                        if l is None or T[i, j] == 0.0:
+                            continue
+                        rows.append(m)
+                        cols.append(l)
+                        vals.append(T[i, j])
+    n = len(dec.lm_edge)
+    return sp.csr_matrix((np.array(vals, float), (rows, cols)), shape=(n, n))
+
+
 def D_matrix(dec: Decomposition, sd: Subdomain):
+    """Sparse D_i (n_i x n_lambda): the signed Boolean map, or (lm_weight 1)
+    the signed Boolean map times T_lambda."""
+    Db = D_bool(dec, sd)
+    return (Db @ dec.T_lambda).tocsr() if dec.lm_weight else Db
+
+
+def D_bool(dec: Decomposition, sd: Subdomain):
     """Sparse signed Boolean D_i (n_i x n_lambda)."""
     loc = {int(e): i for i, e in enumerate(sd.edges)}
     rows, cols, vals = [], [], []

@@ -10,6 +10,8 @@
 #include <numeric>
 #include <set>
 #include <stdexcept>
+#include <array>
+#include <tuple>
 
 #include "d3m_internal.h"
 
@@ -519,24 +521,73 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
         }
     for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = -1;
   }
-  // multiplier couplings (+1 on the lower-index copy, -1 on the other)
+  // multiplier couplings.  lm_weight 0: D is the signed Boolean map (+1 on
+  // the lower-index copy, -1 on the other).  lm_weight 1: D = D_bool T_lambda,
+  // the Galerkin form of the Theory section's multiplier lambda = j +- e
+  // expanded in the same tangential edge basis: T_lambda couples the
+  // multipliers of one interface block (a, b) by the tangential face mass
+  // int_f N_m . N_l dS over the cut face between a and b, so column l of D
+  // holds +T(m, l) on a's copy and -T(m, l) on b's copy of every multiplier
+  // edge m of the block.  T_lambda is symmetric positive definite per block,
+  // so E is unchanged and lambda becomes T_lambda^{-1} lambda_bool.
   {
-    // M index of copy (s, e): binary search in the subdomain's M range is
-    // avoided with a per-subdomain scratch pass
-    std::vector<std::vector<std::pair<int64_t, int64_t>>> by_sub(p.nsub);  // (edge, lm)
-    for (int64_t l = 0; l < n_lm; ++l) {
-      by_sub[p.lm_plus[l]].push_back({p.lm_edge[l], l});
-      by_sub[p.lm_minus[l]].push_back({p.lm_edge[l], ~l});
+    // (edge, lm, value) per subdomain; M indices are resolved with a
+    // per-subdomain scratch pass (no binary search per entry)
+    std::vector<std::vector<std::tuple<int64_t, int64_t, double>>> by_sub(p.nsub);
+    if (ctx.opt.lm_weight == 0) {
+      for (int64_t l = 0; l < n_lm; ++l) {
+        by_sub[p.lm_plus[l]].push_back({p.lm_edge[l], l, 1.0});
+        by_sub[p.lm_minus[l]].push_back({p.lm_edge[l], l, -1.0});
+      }
+    } else {
+      // multiplier of edge e in block (a, b): sorted (edge, a, b, l) records
+      std::vector<std::array<int64_t, 4>> key(n_lm);
+      for (int64_t l = 0; l < n_lm; ++l) key[l] = {p.lm_edge[l], p.lm_plus[l], p.lm_minus[l], l};
+      std::sort(key.begin(), key.end());
+      auto find_lm = [&](int64_t e, int64_t a, int64_t b) -> int64_t {
+        auto it = std::lower_bound(key.begin(), key.end(), std::array<int64_t, 4>{e, a, b, -1});
+        return (it != key.end() && (*it)[0] == e && (*it)[1] == a && (*it)[2] == b) ? (*it)[3] : -1;
+      };
+      for (int a = 0; a < p.nsub; ++a) {
+        const auto &lo = p.sub_lo[a];
+        const auto &hi = p.sub_hi[a];
+        int pos[3];
+        sub_pos(p, a, pos);
+        for (int axis = 0; axis < 3; ++axis)
+          for (int side = 0; side < 2; ++side) {
+            int npos[3] = {pos[0], pos[1], pos[2]};
+            npos[axis] += side ? 1 : -1;
+            if (npos[axis] < 0 || npos[axis] >= p.parts[axis]) continue;
+            const int b = sub_id(p, npos[0], npos[1], npos[2]);
+            if (b < a) continue;  // each cut face once, from its lower-index side
+            const int layer = side ? hi[axis] - 1 : lo[axis];
+            int c0[3] = {lo[0], lo[1], lo[2]}, c1[3] = {hi[0], hi[1], hi[2]};
+            c0[axis] = layer;
+            c1[axis] = layer + 1;
+            for (int ck = c0[2]; ck < c1[2]; ++ck)
+              for (int cj = c0[1]; cj < c1[1]; ++cj)
+                for (int ci = c0[0]; ci < c1[0]; ++ci) {
+                  int64_t e[12];
+                  cell_edges(p, ci, cj, ck, e);
+                  const double (*Tf)[12] = T[2 * axis + side];
+                  for (int j = 0; j < 12; ++j) {
+                    const int64_t l = find_lm(e[j], a, b);
+                    if (l < 0) continue;
+                    for (int i = 0; i < 12; ++i) {
+                      if (Tf[i][j] == 0.0 || find_lm(e[i], a, b) < 0) continue;
+                      by_sub[a].push_back({e[i], l, Tf[i][j]});
+                      by_sub[b].push_back({e[i], l, -Tf[i][j]});
+                    }
+                  }
+                }
+          }
+      }
     }
     for (int s = 0; s < p.nsub; ++s) {
       int64_t m0 = sub_m0[s];
       int64_t m1_ = s + 1 < p.nsub ? sub_m0[s + 1] : p.lam_start;
       for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = v;
-      for (auto &q : by_sub[s]) {
-        int64_t l = q.second >= 0 ? q.second : ~q.second;
-        double sign = q.second >= 0 ? 1.0 : -1.0;
-        trips.push_back({p.lam_start + l, gm[q.first], cplx(sign, 0.0)});
-      }
+      for (auto &q : by_sub[s]) trips.push_back({p.lam_start + std::get<1>(q), gm[std::get<0>(q)], cplx(std::get<2>(q), 0.0)});
       for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = -1;
     }
   }
@@ -867,6 +918,7 @@ extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double 
   else if (c.opt.gmres_restart < 1 || c.opt.gmres_restart > 200) bad = "gmres_restart not in 1..200";
   else if (!(c.opt.gmres_tol > 0 && c.opt.gmres_tol < 1)) bad = "gmres_tol not in (0, 1)";
   else if (c.opt.solve_kernel != 0 && c.opt.solve_kernel != 1) bad = "solve_kernel not 0 or 1";
+  else if (c.opt.lm_weight != 0 && c.opt.lm_weight != 1) bad = "lm_weight not 0 or 1";
   else if (!c.fault.empty() && c.fault != "alloc" && c.fault != "pivot" && c.fault != "nan" && c.fault != "timeout" &&
            c.fault != "solve_timeout")
     bad = "D3M_FAULT not one of alloc, pivot, nan, timeout, solve_timeout";

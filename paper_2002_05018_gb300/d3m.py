@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("update_kernel", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("autotune_cache", ctypes.c_char_p), ("lookahead", ctypes.c_int32),
                 ("refine_method", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("gmres_tol", ctypes.c_double),
-                ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double), ("solve_kernel", ctypes.c_int32)]
+                ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double), ("solve_kernel", ctypes.c_int32),
+                ("lm_weight", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -139,7 +140,7 @@ class Solver:
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
                  update_kernel=0, autotune=0, autotune_cache=None, lookahead=0, refine_method=0,
-                 gmres_restart=0, gmres_tol=0.0, alpha=None, solve_kernel=0):
+                 gmres_restart=0, gmres_tol=0.0, alpha=None, solve_kernel=0, lm_weight=0):
         self.lib = load()
         self.n_cells = nx * ny * nz
         self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
@@ -157,7 +158,7 @@ class Solver:
                       int(panel_kernel), int(update_kernel), int(autotune), self._cache, int(lookahead),
                       int(refine_method), int(gmres_restart), float(gmres_tol),
                       0.0 if alpha is None else complex(alpha).real, 0.0 if alpha is None else complex(alpha).imag,
-                      int(solve_kernel))
+                      int(solve_kernel), int(lm_weight))
         h = ctypes.c_void_p()
         rc = self.lib.d3m_setup(ctypes.byref(mesh), ctypes.byref(mat), float(k), ctypes.byref(part),
                                 ctypes.byref(opt), ctypes.byref(h))
@@ -167,6 +168,7 @@ class Solver:
     @classmethod
     def from_workload(cls, w, precision=FP64, **kw):
         kw.setdefault("alpha", getattr(w, "alpha", None))
+        kw.setdefault("lm_weight", getattr(w, "lm_weight", 0))
         return cls(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.eps, w.k, w.cx, w.cy, w.cz, pec=w.pec_edge,
                    precision=precision, **kw)
 

@@ -50,6 +50,7 @@ class Workload:
     fd_cells: np.ndarray | None = None  # int64 cell ids (finite differences)
     seed: int = 0
     alpha: complex | None = None  # interface loss/gain coefficient (None: jk)
+    lm_weight: int = 0            # multiplier map D: 0 signed Boolean, 1 tangential-face-mass weighted
 
     @property
     def n_cells(self) -> int:

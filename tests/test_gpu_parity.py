@@ -194,6 +194,24 @@ def test_config1_against_oracle(precision):
     assert info["max_resid"] < (1e-12 if precision == d3m.FP64 else 1e-10)
 
 
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_mass_weighted_multipliers(precision):
+    """lm_weight = 1 (the Galerkin multiplier map D = D_bool T_lambda): the
+    GPU solution still equals the global solve, and the multipliers equal the
+    oracle's for the weighted map (a partition with cross-lines)."""
+    _need_gpu()
+    w = W.tiny(6, 6, 4, 2, 2, 1, seed=4, nrhs=3)
+    w.lm_weight = 1
+    s, x, info, f = _solve_case(w, precision)
+    ref = od3m.solve(w, f, return_all=True)
+    xg = fem.solve_global(w, f)
+    tol = 1e-10 if precision == d3m.FP64 else 1e-8
+    assert np.abs(x - xg).max() < tol * np.abs(xg).max()
+    lam = s.lam(f.shape[1])
+    ltol = 1e-9 if precision == d3m.FP64 else 1e-4
+    assert np.abs(lam - ref["lam"]).max() < ltol * np.abs(ref["lam"]).max()
+
+
 def test_config3_fp64():
     _need_gpu()
     w = W.make(3)

@@ -151,3 +151,60 @@ def test_primal_schur_equals_global_and_d3m(case):
     xd = d3m.solve(w, f)
     assert np.abs(xs - xg).max() < 1e-10 * np.abs(xg).max()
     assert np.abs(xs - xd).max() < 1e-10 * np.abs(xg).max()
+
+
+def test_multiplier_mass_closed_form():
+    """T_lambda (the Galerkin reading of lambda = j +- e): symmetric positive
+    definite, no coupling between y- and z-directed multipliers on an x cut
+    plane, and on a single interface whose tangential edges all carry a
+    multiplier, 1^T T_yy 1 = 1^T T_zz 1 = the face area (the basis functions
+    of one direction sum to the unit vector on the face)."""
+    w = W.tiny(6, 4, 4, 2, 1, 1, seed=3, nrhs=1)
+    w.lm_weight = 1
+    dec = decomp.decompose(w)
+    T = dec.T_lambda.toarray()
+    g = dec.grid
+    assert np.array_equal(T, T.T)
+    assert np.linalg.eigvalsh(T).min() > 0
+    ey = [l for l, e in enumerate(dec.lm_edge) if g.nex <= e < g.nex + g.ney]
+    ez = [l for l, e in enumerate(dec.lm_edge) if e >= g.nex + g.ney]
+    assert len(ey) + len(ez) == len(dec.lm_edge)  # an x cut plane carries y and z edges only
+    area = w.ly * w.lz
+    assert abs(T[np.ix_(ey, ey)].sum() - area) < 1e-13 * area
+    assert abs(T[np.ix_(ez, ez)].sum() - area) < 1e-13 * area
+    assert np.abs(T[np.ix_(ey, ez)]).max() == 0.0
+
+
+def test_multiplier_mass_is_block_diagonal():
+    """Multipliers of different interface blocks are not coupled (cross-lines
+    tie a copy to one face-adjacent neighbour only)."""
+    w = W.tiny(4, 4, 4, 2, 2, 2, seed=5, nrhs=1)
+    w.lm_weight = 1
+    dec = decomp.decompose(w)
+    blk = np.empty(len(dec.lm_edge), int)
+    for b, ids in enumerate(dec.block_lms):
+        blk[ids] = b
+    T = dec.T_lambda.tocoo()
+    assert np.all(blk[T.row] == blk[T.col])
+    for ids in dec.block_lms:  # every block's own mass is positive definite
+        Tb = dec.T_lambda[ids][:, ids].toarray()
+        assert np.linalg.eigvalsh(Tb).min() > 0
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_mass_weighted_multipliers_leave_the_solution(case):
+    """D = D_bool T_lambda differs from the Boolean map by an invertible
+    congruence per block: the decomposed solution still equals the global
+    one, and the multipliers satisfy T_lambda lambda_1 = lambda_0."""
+    c = dict(case)
+    jit = c.pop("jitter", False)
+    w = W.tiny(c["nx"], c["ny"], c["nz"], c["px"], c["py"], c["pz"], seed=5, nrhs=2, jitter=jit)
+    f = fem.rhs_planewave(w)
+    xg = fem.solve_global(w, f)
+    r0 = d3m.solve(w, f, return_all=True)
+    w.lm_weight = 1
+    r1 = d3m.solve(w, f, return_all=True)
+    assert np.abs(r1["x"] - xg).max() < 1e-10 * np.abs(xg).max()
+    T = r1["dec"].T_lambda
+    assert np.abs(T @ r1["lam"] - r0["lam"]).max() < 1e-10 * np.abs(r0["lam"]).max()
+    assert np.abs(r1["lam"] - r0["lam"]).max() > 1e-3 * np.abs(r0["lam"]).max()

@@ -125,7 +125,7 @@ def test_level_table_matches_tree_heights():
 @pytest.mark.parametrize("kw", [dict(update_kernel=3), dict(panel_kernel=2), dict(autotune=-1),
                                 dict(lookahead=2), dict(leaf_max=-5), dict(refine_method=2),
                                 dict(gmres_restart=201), dict(gmres_restart=-1), dict(gmres_tol=1.5),
-                                dict(gmres_tol=-1e-3), dict(solve_kernel=2)])
+                                dict(gmres_tol=-1e-3), dict(solve_kernel=2), dict(lm_weight=2)])
 def test_setup_rejects_bad_options(kw):
     """Option values outside their documented sets are refused at set-up."""
     w = W.make(1)
@@ -154,3 +154,27 @@ def test_interface_coefficient_matches_oracle_entries():
         for r, c, re, im in ent[sel]:
             er, ec = mm[int(r), 1], mm[int(c), 1]
             assert abs(A[loc[er], loc[ec]] - (re + 1j * im)) < 1e-12 * np.abs(A).max()
+
+
+def test_mass_weighted_multiplier_map_matches_oracle_entries():
+    """d3m_options.lm_weight = 1: the library's multiplier couplings (rows of
+    lambda, columns of the subdomain copies) equal the oracle's D_i = D_bool,i
+    T_lambda entry for entry, on a partition with cross-lines."""
+    from oracle import decomp
+    w = W.tiny(6, 6, 4, 2, 2, 1, seed=4)
+    w.lm_weight = 1
+    s = d3m.Solver.from_workload(w)
+    ent = s.structure(d3m.M_ENTRIES)
+    mm = s.structure(d3m.M_MAP)
+    st = s.stats()
+    s.close()
+    dec = decomp.decompose(w)
+    lam_start = st["n_m"] - st["n_lm"]
+    sel = (ent[:, 0] >= lam_start) & (ent[:, 1] < lam_start)
+    Ds = {sd.index: (decomp.D_matrix(dec, sd).toarray(), {int(e): i for i, e in enumerate(sd.edges)})
+          for sd in dec.subs}
+    for r, c, re, im in ent[sel]:
+        sub, e = mm[int(c)]
+        D, loc = Ds[int(sub)]
+        assert abs(D[loc[int(e)], int(r) - lam_start] - (re + 1j * im)) < 1e-15
+    assert sel.sum() == sum(int((np.abs(D) > 0).sum()) for D, _ in Ds.values())
