@@ -135,7 +135,7 @@ def _sum_over_ranks(ws, v):
 
 
 def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=False, dev_index=0, cache=None,
-                  update_kernel=0):
+                  update_kernel=0, solve_kernel=0):
     """Times `steps` steps (factor + solve) of one precision, then runs the same
     steps again with the library's per-kernel-class CUDA events on (eager
     launches) for the kernel breakdown and the roofline.  Returns a dict."""
@@ -144,6 +144,7 @@ def run_precision(w, prec, steps, warmup, ws, stream, rhs_dev, sample_clocks=Fal
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     s = d3m.Solver.from_workload(w, precision=prec, stream=stream, profile=False, update_kernel=update_kernel,
+                                 solve_kernel=solve_kernel,
                                  autotune_cache=None if cache is None else f"{cache}.{'mixed' if prec else 'fp64'}")
     st0 = s.stats()
     factor_flops = st0["flops_interior"] + st0["flops_domain"] + st0["flops_k"]
@@ -443,6 +444,8 @@ def main():
     ap.add_argument("--ncu-range", action="store_true",
                     help="after the timed steps, run one more mixed step (factor graph + solve) between "
                          "cudaProfilerStart/Stop, for ncu --profile-from-start off")
+    ap.add_argument("--solve-kernel", type=int, default=0, choices=[0, 1],
+                    help="mixed substitution products: 0 tensor cores (default), 1 fp32 FMA (profiling)")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="replace the workload's plane waves by this many seeded random ones "
                          "(profiling the substitution of a small workload with many right-hand sides)")
@@ -508,7 +511,8 @@ def main():
     torch.cuda.synchronize()
 
     mixed = run_precision(w, d3m.MIXED, args.steps, args.warmup, ws, stream, rhs_dev, sample_clocks=(rank == 0),
-                          dev_index=dev, cache=args.autotune_cache, update_kernel=args.update_kernel)
+                          dev_index=dev, cache=args.autotune_cache, update_kernel=args.update_kernel,
+                          solve_kernel=args.solve_kernel)
     if args.ncu_range:
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()

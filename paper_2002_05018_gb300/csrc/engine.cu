@@ -1934,6 +1934,7 @@ struct SkItem {
   int64_t c, p;        // target offset in buffer cbuf; first partial block in the partial buffer
   int32_t c_rs, c_cs, M, N, S, cbuf, beta;
   int32_t elem0;       // first element index of this item in the launch
+  int32_t f;           // front of the item (its rows are the front's pivot rows for kinds 0 and 3)
 };
 template <typename T>
 __global__ void k_splitk_reduce(const SkItem *__restrict__ items, int nitems, int64_t nelem, CgBufs<T> bufs,
@@ -1964,6 +1965,55 @@ __global__ void k_splitk_reduce(const SkItem *__restrict__ items, int nitems, in
       acc.im += o.im;
     }
     *d = acc;
+  }
+}
+
+// The split-K reduction of a level's L11^{-1} product fused with the next
+// sweep step (levels whose products are split, the narrow ones near the
+// root): mode 0 (forward) writes y = L11^{-1} b to Y2 and z = D^{-1} y to
+// zM, summing the partials of a 2x2 pivot's partner row as well (the same
+// operations in the same order as the reduction followed by k_fwd_dinv);
+// mode 3 (backward) writes x = L11^{-T} w straight to its original
+// positions in xM (the reduction followed by k_bwd_out).  Kind-0 and kind-3
+// items have beta = 0 and row-major targets.
+template <typename T>
+__global__ void k_splitk_reduce_sweep(const SkItem *__restrict__ items, int nitems, int64_t nelem, CgBufs<T> bufs,
+                                      const cx<T> *__restrict__ part, FrontTab ft, const double2 *__restrict__ dinv_d,
+                                      const double2 *__restrict__ dinv_o, const int8_t *__restrict__ psize,
+                                      const int32_t *__restrict__ perm, cx<T> *__restrict__ zM, cx<T> *__restrict__ xM,
+                                      int r, int mode) {
+  pdl_wait();  // the predecessor in the sweep has finished
+  pdl_trigger();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nelem; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nitems - 1;  // last item with elem0 <= e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].elem0 <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const SkItem it = items[lo];
+    const int64_t q = e - it.elem0, mn = (int64_t)it.M * it.N;
+    const int i = (int)(q / it.N), j = (int)(q % it.N);
+    auto sum_row = [&](int row) {
+      cx<T> acc = mk<T>(0, 0);
+      for (int s2 = 0; s2 < it.S; ++s2) {
+        const cx<T> v = part[it.p + s2 * mn + (int64_t)row * it.N + j];
+        acc.re += v.re;
+        acc.im += v.im;
+      }
+      return acc;
+    };
+    const cx<T> y = sum_row(i);
+    const int64_t piv = ft.piv[it.f], st = ft.start[it.f];
+    if (mode == 0) {
+      cg_buf(bufs, it.cbuf)[it.c + (int64_t)i * it.c_rs + (int64_t)j * it.c_cs] = y;
+      cx<T> z = cmul(y, from_d<T>(dinv_d[piv + i]));
+      const int sz = psize[piv + i];
+      if (sz == 2 || sz == -2) z = cfma(z, sum_row(sz == 2 ? i + 1 : i - 1), from_d<T>(dinv_o[piv + i]));
+      zM[(st + i) * r + j] = z;
+    } else {
+      xM[(st + perm[piv + i]) * r + j] = y;
+    }
   }
 }
 
@@ -3589,6 +3639,7 @@ static int solve_items(Ctx &c, int r) {
       BM = best;
       int first = (int)items.size(), tiles = 0;
       std::vector<CgItem> kitems;  // this launch's items before any split
+      std::vector<int32_t> kfront;  // the front of each of them
       for (int i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
         const int f = P.level_fronts[i];
         const int pf = (int)(P.sn_end[f] - P.sn_start[f]);
@@ -3610,6 +3661,7 @@ static int solve_items(Ctx &c, int r) {
           g.abuf = 1; g.bbuf = 2; g.cbuf = 3; g.beta = 0; g.alpha = 1.f;
           if (tcl) { g.qa = d->qblk_h[i][kind]; g.qnk = d->qnk_h[i][kind]; }
           kitems.push_back(g);
+          kfront.push_back(f);
         } else if (kind == 1) {  // Y[p:m] -= L21 y[0:p]
           if (mf == pf || pf == 0) continue;
           g.a = P.front_off[f] + pf; g.a_rs = 1; g.a_cs = mf;
@@ -3619,6 +3671,7 @@ static int solve_items(Ctx &c, int r) {
           g.abuf = 0; g.bbuf = mixed ? 3 : 2; g.cbuf = 2; g.beta = 1; g.alpha = -1.f;
           if (tcl) { g.qa = d->qblk_h[i][1]; g.qnk = d->qnk_h[i][1]; }
           kitems.push_back(g);
+          kfront.push_back(f);
         } else {  // partials of L21^T x over row splits
           if (mf == pf || pf == 0) continue;
           const int S = (mf - pf + BSPLIT - 1) / BSPLIT;
@@ -3632,6 +3685,7 @@ static int solve_items(Ctx &c, int r) {
             h.abuf = 0; h.bbuf = 4; h.cbuf = 5; h.beta = 0; h.alpha = 1.f;
             if (tcl) { h.qa = d->qblk_h[i][2] + rb / Q_BK; h.qnk = d->qnk_h[i][2]; }
             kitems.push_back(h);
+            kfront.push_back(f);
           }
         }
       }
@@ -3648,7 +3702,8 @@ static int solve_items(Ctx &c, int r) {
         S = (int)std::min<int64_t>({8, (304 + nt0 - 1) / nt0, kmax / 48});
       const int sk_first = (int)skitems.size();
       int64_t sk_elems = 0, pofs = 0;
-      for (const CgItem &g : kitems) {
+      for (size_t ki = 0; ki < kitems.size(); ++ki) {
+        const CgItem &g = kitems[ki];
         if (S <= 1) {
           CgItem h = g;
           h.tile0 = tiles;
@@ -3688,6 +3743,7 @@ static int solve_items(Ctx &c, int r) {
         q.cbuf = g.cbuf;
         q.beta = g.beta;
         q.elem0 = (int32_t)sk_elems;
+        q.f = kfront[ki];
         skitems.push_back(q);
         sk_elems += mn;
         pofs += (int64_t)pieces * mn;
@@ -3784,6 +3840,17 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
                (const cx<T> *)d->skp);
     return 1;
   };
+  // the split-K reduction of kind 0 (mode 0) or 3 (mode 3) fused with the
+  // sweep step that follows it (k_splitk_reduce_sweep)
+  auto reduce_sweep = [&](int l, int kind) {
+    const auto &k3 = d->sk_lvl[l];
+    const int64_t ne = k3[3 * kind + 2];
+    launch_pdl(pdl, k_splitk_reduce_sweep<T>,
+               dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((ne + 255) / 256, 1216))), dim3(256), 0, s,
+               (const SkItem *)(d->sk_items + k3[3 * kind + 0]), k3[3 * kind + 1], ne, bufs, (const cx<T> *)d->skp,
+               ft, (const double2 *)d->dinv_d, (const double2 *)d->dinv_o, (const int8_t *)d->psize,
+               (const int32_t *)d->perm, (cx<T> *)d->zM, (cx<T> *)d->xM, r, kind);
+  };
   int64_t nl = 0;
   if (dir & 1) {
   PROF_BEGIN(PC_FWD);
@@ -3799,10 +3866,13 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
     if (use_inv) {
       launch_cgemm<T>(sl[3], sl[2], d->sol_items + sl[0], sl[1], bufs, d->sidx, s, d->qpl,
                       d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][0], pdl);
-      nl += reduce(l, 0);
-      dim3 gdv(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
-      launch_pdl(pdl, k_fwd_dinv<T>, gdv, dim3(256), 0, s, lvl, ft, (const double2 *)d->dinv_d,
-                 (const double2 *)d->dinv_o, (const int8_t *)d->psize, (const cx<T> *)Y2, (cx<T> *)d->zM, r);
+      if (d->sk_lvl[l][1] > 0) {  // split: the reduction also applies D^{-1}
+        reduce_sweep(l, 0);
+      } else {
+        dim3 gdv(sweep_grid((int64_t)d->level_maxp[l] * r, nf), nf);
+        launch_pdl(pdl, k_fwd_dinv<T>, gdv, dim3(256), 0, s, lvl, ft, (const double2 *)d->dinv_d,
+                   (const double2 *)d->dinv_o, (const int8_t *)d->psize, (const cx<T> *)Y2, (cx<T> *)d->zM, r);
+      }
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
       launch_pdl(pdl, k_fwd_solve<T, RC>, gs, dim3(256), 0, s, lvl, ft, (const cx<T> *)arena, (const double2 *)d->dinv_d,
@@ -3837,9 +3907,11 @@ static int64_t apply_inverse(Ctx &c, int r, int dir = 3) {
                  r);
       launch_cgemm<T>(sl[15], sl[14], d->sol_items + sl[12], sl[13], bufs, d->sidx, s, d->qpl,
                       d->sv_err, d->sv_wait_cap, d->sol_tmap + d->sol_tofs[l][3], pdl);
-      nl += reduce(l, 3);
-      launch_pdl(pdl, k_bwd_out<T>, gw, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)Y2,
-                 (cx<T> *)d->xM, r);
+      if (d->sk_lvl[l][3 * 3 + 1] > 0)  // split: the reduction also scatters x to xM
+        reduce_sweep(l, 3);
+      else
+        launch_pdl(pdl, k_bwd_out<T>, gw, dim3(256), 0, s, lvl, ft, (const int32_t *)d->perm, (const cx<T> *)Y2,
+                   (cx<T> *)d->xM, r);
       nl += 3;
     } else {
       dim3 gs((r + RC - 1) / RC, nf);
