@@ -674,7 +674,11 @@ __global__ void __launch_bounds__(512)
   cx<T> *wr = wk + rcap;                                  // [rcap]
   int *spos = reinterpret_cast<int *>(wr + rcap);         // [rcap] logical row of each own slot
   int *p2s = spos + rcap;                                 // [mcap] logical row - k0 -> global slot
-  __shared__ PanelBox<T> box[2];
+  // per-column mailbox of the cluster: every CTA's thread 0 writes its record
+  // into slot [rank] of every CTA's copy before the cluster barrier, so the
+  // records are read from local shared memory after it ([0]: the column
+  // arg-max, [1]: the row arg-max of the 2x2 test)
+  __shared__ PanelBox<T> box[2][16];
   __shared__ __align__(16) cx<T> wrow[(512 / 32) * NB];   // one staged row per warp
   __shared__ __align__(16) cx<T> wrow2[(512 / 32) * NB];
   __shared__ cx<T> Dd[NB], Do[NB];    // D of the panel's pivots: diag / 2x2 coupling
@@ -762,18 +766,21 @@ __global__ void __launch_bounds__(512)
     } else {
       const int gk = p2s[k - k0];
       if (tid == 0) {
-        box[0].cmax = cm.v;
-        box[0].cidx = cm.i;
-        box[0].has = gk / R == rank;
-        box[0].v1 = gk / R == rank ? wk[gk - rank * R] : mk<T>(0, 0);
-        box[0].vmax = cm.i < p ? own_at(wk, cm.i) : mk<T>(0, 0);
+        PanelBox<T> mb;
+        mb.cmax = cm.v;
+        mb.cidx = cm.i;
+        mb.has = gk / R == rank;
+        mb.v1 = gk / R == rank ? wk[gk - rank * R] : mk<T>(0, 0);
+        mb.vmax = cm.i < p ? own_at(wk, cm.i) : mk<T>(0, 0);
+        mb.v2 = mk<T>(0, 0);
+        for (int c = 0; c < CS; ++c) cl.map_shared_rank(&box[0][0], c)[rank] = mb;
       }
       cl.sync();  // #1
       ArgMaxT<T> best{(T)-1, 0x7fffffff};
       vmax = mk<T>(0, 0);
       akk = mk<T>(0, 0);
       for (int c = 0; c < CS; ++c) {
-        const PanelBox<T> *b = cl.map_shared_rank(&box[0], c);
+        const PanelBox<T> *b = &box[0][c];
         const T v = b->cmax;
         const int i = b->cidx;
         if (v > best.v || (v == best.v && i < best.i)) {
@@ -799,13 +806,24 @@ __global__ void __launch_bounds__(512)
     if (d.need2) {
       const int imax = d.imax;
       // ---- (2) updated column imax for own slots
+      // original column imax of the own rows: loads issued first, in flight
+      // while row imax's W entries are staged
+      cx<T> g0 = mk<T>(0, 0), g1 = mk<T>(0, 0);
+      if (tid < ns) {
+        const int i = spos[tid];
+        if (i >= k) g0 = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
+      }
+      if (tid + nth < ns) {
+        const int i = spos[tid + nth];
+        if (i >= k) g1 = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
+      }
       load_wrow(imax, wrow2);
       const cx<T> *wrw2 = wrow2 + (tid >> 5) * NB;
       ArgMaxT<T> rl{(T)-1, 0x7fffffff};
-      for (int q = tid; q < ns; q += nth) {
+      for (int q = tid, qi = 0; q < ns; q += nth, ++qi) {
         int i = spos[q];
         if (i < k) continue;
-        cx<T> acc = i < imax ? F[imax + (int64_t)i * ld] : F[i + (int64_t)imax * ld];
+        cx<T> acc = qi == 0 ? g0 : g1;
         const cx<T> *Lq = Ls + (size_t)q * LSTR;
         acc = col_update(acc, Lq, wrw2, j);
         wr[q] = acc;
@@ -823,12 +841,14 @@ __global__ void __launch_bounds__(512)
       } else {
         const int gi = p2s[imax - k0];
         if (tid == 0) {
-          box[1].cmax = rm.i < p ? rm.v : (T)-1;
-          box[1].cidx = rm.i;
-          box[1].vmax = rm.i < p ? own_at(wr, rm.i) : mk<T>(0, 0);
-          box[1].has = gi / R == rank;
-          box[1].v1 = gi / R == rank ? wk[gi - rank * R] : mk<T>(0, 0);  // w_k at row imax
-          box[1].v2 = gi / R == rank ? wr[gi - rank * R] : mk<T>(0, 0);  // w_r at row imax
+          PanelBox<T> mb;
+          mb.cmax = rm.i < p ? rm.v : (T)-1;
+          mb.cidx = rm.i;
+          mb.vmax = rm.i < p ? own_at(wr, rm.i) : mk<T>(0, 0);
+          mb.has = gi / R == rank;
+          mb.v1 = gi / R == rank ? wk[gi - rank * R] : mk<T>(0, 0);  // w_k at row imax
+          mb.v2 = gi / R == rank ? wr[gi - rank * R] : mk<T>(0, 0);  // w_r at row imax
+          for (int c = 0; c < CS; ++c) cl.map_shared_rank(&box[1][0], c)[rank] = mb;
         }
         cl.sync();  // #2
         rowmax = (T)0;
@@ -836,7 +856,7 @@ __global__ void __launch_bounds__(512)
         rwin = mk<T>(0, 0);
         wki = wri = mk<T>(0, 0);
         for (int c = 0; c < CS; ++c) {
-          const PanelBox<T> *b = cl.map_shared_rank(&box[1], c);
+          const PanelBox<T> *b = &box[1][c];
           if (b->cmax > rowmax) rowmax = b->cmax;
           if (b->cmax >= (T)0 && cabs1_d(b->vmax) > rex) {
             rex = cabs1_d(b->vmax);
