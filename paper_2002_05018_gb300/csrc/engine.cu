@@ -682,6 +682,7 @@ __global__ void __launch_bounds__(512)
   __shared__ __align__(16) cx<T> wrow[(512 / 32) * NB];   // one staged row per warp
   __shared__ __align__(16) cx<T> wrow2[(512 / 32) * NB];
   __shared__ cx<T> Dd[NB], Do[NB];    // D of the panel's pivots: diag / 2x2 coupling
+  __shared__ cx<T> Ei[NB], Eo[NB];    // D^{-1} in the factor precision (fp32 path): diag / 2x2 coupling
   __shared__ PivotDec<T> pd;          // fp64 path: the decision of thread 0
   __shared__ int Dz[NB];              // 1, 2 (first of a pair), -2
   __shared__ ArgMaxT<T> red[64];
@@ -943,6 +944,8 @@ __global__ void __launch_bounds__(512)
         Dd[j] = d.d11;
         Do[j] = mk<T>(0, 0);
         Dz[j] = 1;
+        Ei[j] = d.a11;
+        Eo[j] = mk<T>(0, 0);
       }
     } else {
       const cx<T> a11 = d.a11, a21 = d.a21, a22 = d.a22;
@@ -971,14 +974,26 @@ __global__ void __launch_bounds__(512)
         Do[j + 1] = d.d21;
         Dz[j] = 2;
         Dz[j + 1] = -2;
+        Ei[j] = d.a11;
+        Ei[j + 1] = d.a22;
+        Eo[j] = d.a21;
+        Eo[j + 1] = d.a21;
       }
     }
     csync();  // #3: L rows, D and the tables are consistent for the next column
     k += kstep;
     j += kstep;
   }
-  // ---- fp64 D^{-1} of the panel's pivots (one thread per pivot)
-  if (rank == 0 && tid < j) {
+  // ---- D^{-1} of the panel's pivots (one thread per pivot), stored in fp64.
+  // fp32 path: the inverses the decisions computed (every consumer of the
+  // complex64 factors uses D^{-1} in fp32); fp64 path: computed here.
+  if (sizeof(T) == 4 && rank == 0 && tid < j) {
+    const int t = tid, z = Dz[t];
+    const bool zero = z == 1 && Dd[t].re == (T)0 && Dd[t].im == (T)0;
+    dd[k0 + t] = zero ? make_double2(0, 0) : to_d(Ei[t]);
+    dof[k0 + t] = to_d(Eo[t]);
+    ps[k0 + t] = (int8_t)z;
+  } else if (rank == 0 && tid < j) {
     const int t = tid, z = Dz[t];
     if (z == 1) {
       const double2 d11 = to_d(Dd[t]);
@@ -1003,9 +1018,12 @@ __global__ void __launch_bounds__(512)
   // D on it (the coupling entry L(k+1, k) of a 2x2 pair is stored as 0, so
   // every consumer may read the pivot columns as a plain unit-lower L), and
   // W = L D for the rows below the panel (trailing update input)
-  for (int q = tid; q < ns; q += nth) {
-    const int i = spos[q];
-    const cx<T> *Lq = Ls + (size_t)q * LSTR;
+  // (thread -> logical rows k0 + tid, k0 + tid + nth, ...: consecutive threads
+  // write consecutive rows; the slot of a row comes from p2s)
+  for (int i = k0 + tid; i < p; i += nth) {
+    const int g = p2s[i - k0];
+    if (g / R != rank) continue;  // another CTA of the cluster holds the row
+    const cx<T> *Lq = Ls + (size_t)(g - rank * R) * LSTR;
     for (int t = 0; t < j; ++t) {
       const int c = k0 + t;
       if (c < i) F[i + (int64_t)c * ld] = Lq[t];
