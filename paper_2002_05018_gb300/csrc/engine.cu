@@ -1024,12 +1024,14 @@ __global__ void __launch_bounds__(512)
     const int g = p2s[i - k0];
     if (g / R != rank) continue;  // another CTA of the cluster holds the row
     const cx<T> *Lq = Ls + (size_t)(g - rank * R) * LSTR;
+#pragma unroll 4
     for (int t = 0; t < j; ++t) {
       const int c = k0 + t;
       if (c < i) F[i + (int64_t)c * ld] = Lq[t];
       else if (c == i) F[i + (int64_t)c * ld] = Dd[t];
     }
     if (i < k) continue;
+#pragma unroll 4
     for (int t = 0; t < j; ++t) {
       cx<T> l = Lq[t], acc;
       if (Dz[t] == 1) {
