@@ -1481,20 +1481,6 @@ __global__ void __launch_bounds__(256)
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-// D (TMEM) (+)= A B^T for shared-memory descriptors a, b (acc = 0 overwrites D)
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
 // Bounded wait on phase `parity` of an mbarrier: true once the phase has
 // completed, false after `iters` unsuccessful polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int iters) {
