@@ -4,7 +4,8 @@ Objective J = sum_{m in probes} |x_m|^2 with x = A(eps)^{-1} f and A =
 S - k^2 sum_c eps_c M_c + jk T (Theory section discretisation).  With
 dA/d(Re eps_c) = -k^2 M_c and A = A^T,
     dJ/d(Re eps_c) = 2 k^2 Re( u_c^T M_c x_c ),   u = A^{-1} (P conj(x)),
-P the probe selector, u_c and x_c the 12 local edge values of cell c.  The
+P the probe selector, u_c and x_c the local edge values of cell c (12 on
+bricks, 19 on the six tetrahedra of a tetrahedral cell).  The
 adjoint solve is a plain second sparse LU solve; no code is shared with the
 library.  Pinned by central finite differences (tests/test_oracle_adjoint.py).
 """
@@ -26,11 +27,15 @@ def gradient(w, f, probes):
     rhs = np.zeros_like(x)
     rhs[probes] = np.conj(x[probes])
     u = fem.solve_global(w, rhs)
-    _, M = fem.element_matrices(g.h)
+    if g.element == "brick":
+        _, M = fem.element_matrices(g.h)
+        M = np.broadcast_to(M, (g.n_cells, 12, 12))
+    else:
+        _, M = fem.tet_cell_matrices(g, np.arange(g.n_cells))
     ce = g.cell_edges()
     grad = np.zeros(g.n_cells)
     for col in range(x.shape[1]):
-        xc = x[ce, col]          # (ncell, 12)
+        xc = x[ce, col]          # (ncell, 12 or 19)
         uc = u[ce, col]
-        grad += 2.0 * w.k ** 2 * np.real(np.einsum("ca,ab,cb->c", uc, M, xc))
+        grad += 2.0 * w.k ** 2 * np.real(np.einsum("ca,cab,cb->c", uc, M, xc))
     return objective(x, probes), grad

@@ -70,15 +70,14 @@ def face_adjacent(a, b, parts):
 
 
 def box_edges(g: fem.Grid, lo, hi):
-    """All edges of the cells in the box [lo, hi) (sorted)."""
+    """All edges of the cells in the box [lo, hi) (sorted): per edge family
+    with direction d, the start nodes in [lo, hi - d] along each axis."""
     out = []
     r = lambda a, b: np.arange(a, b)
-    i, j, k = np.meshgrid(r(lo[0], hi[0]), r(lo[1], hi[1] + 1), r(lo[2], hi[2] + 1), indexing="ij")
-    out.append(g.ex(i, j, k).ravel())
-    i, j, k = np.meshgrid(r(lo[0], hi[0] + 1), r(lo[1], hi[1]), r(lo[2], hi[2] + 1), indexing="ij")
-    out.append(g.ey(i, j, k).ravel())
-    i, j, k = np.meshgrid(r(lo[0], hi[0] + 1), r(lo[1], hi[1] + 1), r(lo[2], hi[2]), indexing="ij")
-    out.append(g.ez(i, j, k).ravel())
+    for f, d in enumerate(g.dirs):
+        i, j, k = np.meshgrid(r(lo[0], hi[0] + 1 - d[0]), r(lo[1], hi[1] + 1 - d[1]),
+                              r(lo[2], hi[2] + 1 - d[2]), indexing="ij")
+        out.append(g.edge_id(f, i, j, k).ravel())
     return np.sort(np.concatenate(out))
 
 
@@ -185,14 +184,14 @@ def multiplier_mass(dec: Decomposition):
             npos[axis] += -1 if side == 0 else 1
             if sub_index(npos, dec.parts) != b:
                 continue
-            T = fem.face_matrix(g.h, axis, side)
-            for c in cid:
+            Tc = fem.face_block(g, axis, side, cid)
+            for c, T in zip(cid, Tc):
                 ce = ce_all[c]
-                for i in range(12):
+                for i in range(len(ce)):
                     m = lm_of.get((a, b, int(ce[i])))
                     if m is None:
                         continue
-                    for j in range(12):
+                    for j in range(len(ce)):
                         l = lm_of.get((a, b, int(ce[j])))
                         if l is None or T[i, j] == 0.0:
                             continue

@@ -94,7 +94,7 @@ def subdomain_nd(grid, sd, interface_edges, leaf_max=LEAF_MAX):
         c = lo[axis] + ext[axis] // 2
         d = info[E, 0]
         coord = info[E, 1 + axis]
-        sep = E[(d != axis) & (coord == c)]
+        sep = E[(grid.dirs[d, axis] == 0) & (coord == c)]
         avail[sep] = False
         lhi = list(hi); lhi[axis] = c
         rlo = list(lo); rlo[axis] = c

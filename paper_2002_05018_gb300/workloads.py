@@ -18,6 +18,18 @@ dielectric spheres of growing electrical size) with brick meshes:
 Random draws, in this order, from numpy.random.default_rng(seed): interior
 cut jitter (x cuts, then y, then z; integers in [-3, 3]), per-cell
 permittivities, plane-wave angles and polarisations, probe edges, FD cells.
+
+tetrahedral(w) turns any of them into a tetrahedral mesh of the same cells
+(the general FEM setting of the paper's Introduction): each cell is split into
+six tetrahedra along its (0,0,0)-(1,1,1) diagonal, and the lattice vertices
+are moved by a seeded uniform jitter of up to +-jitter*h per axis (vertices on
+the outer boundary move only within their boundary planes).
+
+Edge families (global numbering, family after family, each x-fastest over the
+start nodes (i, j, k) of its own box): directions (1,0,0), (0,1,0), (0,0,1)
+on brick meshes; tetrahedral meshes add the face diagonals (1,1,0), (1,0,1),
+(0,1,1) and the cell diagonal (1,1,1).  Every edge points from its start node
+to start + direction.
 """
 from __future__ import annotations
 
@@ -27,6 +39,14 @@ import math
 import numpy as np
 
 K0 = 2.0 * math.pi  # free-space wavenumber for wavelength 1
+
+EDGE_DIRS = {"brick": ((1, 0, 0), (0, 1, 0), (0, 0, 1)),
+             "tet": ((1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1))}
+
+
+def family_sizes(nx, ny, nz, element="brick"):
+    """Number of edges in each edge family of the mesh (see the module docstring)."""
+    return [(nx + 1 - d[0]) * (ny + 1 - d[1]) * (nz + 1 - d[2]) for d in EDGE_DIRS[element]]
 
 
 @dataclasses.dataclass
@@ -51,6 +71,8 @@ class Workload:
     seed: int = 0
     alpha: complex | None = None  # interface loss/gain coefficient (None: jk)
     lm_weight: int = 0            # multiplier map D: 0 signed Boolean, 1 tangential-face-mass weighted
+    element: str = "brick"        # "brick" or "tet" (six tetrahedra per cell)
+    vertices: np.ndarray | None = None  # (n_nodes, 3) float64 positions, x-fastest; None: lattice
 
     @property
     def n_cells(self) -> int:
@@ -58,8 +80,11 @@ class Workload:
 
     @property
     def n_edges(self) -> int:
-        nx, ny, nz = self.nx, self.ny, self.nz
-        return nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
+        return sum(family_sizes(self.nx, self.ny, self.nz, self.element))
+
+    @property
+    def n_nodes(self) -> int:
+        return (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
 
     @property
     def nrhs(self) -> int:
@@ -204,6 +229,34 @@ def make(index: int, seed: int | None = None) -> Workload:
         w.probes = np.sort(rng.choice(w.n_edges, 16, replace=False)).astype(np.int64)
         w.fd_cells = np.sort(rng.choice(w.n_cells, 20, replace=False)).astype(np.int64)
     return w
+
+
+def lattice_vertices(w: Workload) -> np.ndarray:
+    """(n_nodes, 3) positions of the regular lattice, x-fastest."""
+    kk, jj, ii = np.meshgrid(np.arange(w.nz + 1), np.arange(w.ny + 1), np.arange(w.nx + 1),
+                             indexing="ij")
+    return np.stack([ii.ravel() * (w.lx / w.nx), jj.ravel() * (w.ly / w.ny),
+                     kk.ravel() * (w.lz / w.nz)], 1).astype(np.float64)
+
+
+def tetrahedral(w: Workload, jitter: float = 0.1, seed: int | None = None) -> Workload:
+    """A copy of w on six tetrahedra per cell, with seeded jittered vertices
+    (uniform in [-jitter, jitter] * h per axis; none on an outer boundary
+    plane's normal axis).  PEC masks of the brick numbering do not carry over."""
+    if w.pec_edge is not None:
+        raise ValueError("tetrahedral(): the brick PEC mask has no tetrahedral counterpart")
+    rng = np.random.default_rng(w.seed if seed is None else seed)
+    v = lattice_vertices(w)
+    h = np.array([w.lx / w.nx, w.ly / w.ny, w.lz / w.nz])
+    kk, jj, ii = np.meshgrid(np.arange(w.nz + 1), np.arange(w.ny + 1), np.arange(w.nx + 1),
+                             indexing="ij")
+    idx = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1)
+    n = np.array([w.nx, w.ny, w.nz])
+    movable = (idx > 0) & (idx < n[None, :])
+    d = rng.uniform(-jitter, jitter, v.shape) * h[None, :]
+    v = v + np.where(movable, d, 0.0)
+    return dataclasses.replace(w, name=w.name + "-tet", element="tet", vertices=v, probes=None,
+                               fd_cells=None)
 
 
 def tiny(nx, ny, nz, px, py, pz, seed=0, lossy=True, nrhs=1, pec=None, jitter=False,
