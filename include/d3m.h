@@ -3,8 +3,9 @@
  * for finite-element electromagnetics, Moshfegh & Vouvakis, ICEAA 2016).
  *
  * Problem (Theory section, decomposed BVP): curl curl E - k^2 eps_r E = 0 in
- * an axis-aligned box meshed by nx*ny*nz bricks with lowest-order Nedelec
- * edge elements, a first-order absorbing boundary condition on the whole
+ * an axis-aligned box of nx*ny*nz lattice cells, meshed by bricks or by six
+ * tetrahedra per cell (d3m_mesh) with lowest-order Nedelec edge elements, a
+ * first-order absorbing boundary condition on the whole
  * outer boundary driven by incident plane waves, mu_r = 1.  The box is cut
  * into px*py*pz subdomains; the library assembles the decomposed system of
  * Eq. (1), [[A, D], [D^T, 0]] [E; lambda] = [f; 0], and factors it with the
@@ -16,11 +17,12 @@
  *
  * Conventions for every entry point:
  *  - complex numbers are pairs of doubles (re, im) in consecutive memory;
- *  - global edge numbering: x-edges, then y-edges, then z-edges; each family
- *    runs its start node (i, j, k) x-fastest: x-edge (i,j,k) = i + nx*(j +
- *    (ny+1)*k), y-edge = NX + i + (nx+1)*(j + ny*k), z-edge = NX + NY + i +
- *    (nx+1)*(j + (ny+1)*k), NX = nx(ny+1)(nz+1), NY = (nx+1)ny(nz+1); every
- *    edge is oriented along +axis;
+ *  - global edge numbering: x-edges, then y-edges, then z-edges (then, on
+ *    tetrahedral meshes, the diagonal families listed at d3m_mesh); each
+ *    family runs its start node (i, j, k) x-fastest: x-edge (i,j,k) = i +
+ *    nx*(j + (ny+1)*k), y-edge = NX + i + (nx+1)*(j + ny*k), z-edge = NX + NY
+ *    + i + (nx+1)*(j + (ny+1)*k), NX = nx(ny+1)(nz+1), NY = (nx+1)ny(nz+1);
+ *    every edge points from its start node towards increasing coordinates;
  *  - cells are numbered i + nx*(j + ny*k); subdomains ix + px*(iy + py*iz);
  *  - RHS / solution blocks are column-major n_edges x nrhs with a leading
  *    dimension >= n_edges, in global edge numbering with PEC edges present
@@ -60,17 +62,40 @@ enum d3m_precision {
   D3M_MIXED = 1       /* factors in complex64; the pivot tests decide as fp64
                          tests on the complex64 values (fp32 comparisons,
                          re-evaluated in fp64 when within 2^-20 of a tie); the
-                         1x1/2x2 pivot inverses kept for the substitution in
-                         fp64; fp64 residuals and iterative refinement against
-                         the fp64 sparse operator */
+                         1x1/2x2 pivot inverses are the fp32 inverses those
+                         decisions computed; fp64 residuals and iterative
+                         refinement against the fp64 sparse operator */
 };
 
 typedef struct d3m_ctx d3m_ctx;
 
-/* Axis-aligned brick grid [0,lx] x [0,ly] x [0,lz], nx*ny*nz cells. */
+enum d3m_element {
+  D3M_BRICK = 0,      /* lowest-order Nedelec bricks on the axis-aligned grid */
+  D3M_TET = 1         /* lowest-order Nedelec (Whitney) tetrahedra, six per
+                         cell (the Introduction's general FEM setting) */
+};
+
+/* Mesh of [0,lx] x [0,ly] x [0,lz] with nx*ny*nz lattice cells.
+ * element D3M_BRICK: axis-aligned bricks; vertices must be NULL.
+ * element D3M_TET: every cell is split into six tetrahedra along its
+ *   (0,0,0)-(1,1,1) diagonal (each cell face along its lowest-to-highest
+ *   corner diagonal, so neighbouring cells conform).  The dof of an edge is
+ *   the line average of E . t along it, as for bricks.  vertices: NULL for
+ *   the regular lattice, or 3*(nx+1)*(ny+1)*(nz+1) doubles, the (x, y, z)
+ *   position of node (i, j, k) at index i + (nx+1)*(j + (ny+1)*k), read
+ *   during d3m_setup only (the caller keeps ownership).  Every tetrahedron
+ *   must keep the orientation it has in the regular lattice, and nodes on the
+ *   outer boundary must stay in their boundary planes (the absorbing
+ *   condition takes the box's face normals): D3M_EINVAL otherwise.
+ * Global edge numbering: edge families one after another, each x-fastest
+ * over its own box of start nodes (i, j, k); directions (1,0,0), (0,1,0),
+ * (0,0,1), and for D3M_TET then (1,1,0), (1,0,1), (0,1,1), (1,1,1).  Every
+ * edge points from its start node to start + direction. */
 typedef struct {
   int32_t nx, ny, nz;
   double lx, ly, lz;
+  int32_t element;          /* d3m_element */
+  const double *vertices;   /* D3M_TET only; NULL: regular lattice */
 } d3m_mesh;
 
 /* Materials.  eps_r: 2*n_cells doubles (re, im) per cell, time convention
@@ -270,7 +295,8 @@ int d3m_solve_adjoint(d3m_ctx *ctx, const double *rhs, int64_t ldb, double *y, i
  *   grad[c] = k^2 * Re( sum_r conj(y_r)_c^T M_c x_r,c ),
  * where x = A^{-1} f is the forward solution, y = A^{-H} (dJ/dx) the adjoint
  * solution from d3m_solve_adjoint (dJ/dx in PyTorch's convention, e.g. 2 x at
- * the probes for J = sum |x_probe|^2), M_c the 12x12 mass matrix of cell c
+ * the probes for J = sum |x_probe|^2), M_c the mass matrix of cell c over its
+ * 12 edges (bricks) or 19 edges (the six tetrahedra of a D3M_TET cell)
  * (dA/deps_c = -k^2 M_c) and the sum runs over the nrhs columns.  DEVICE
  * pointers: x, y as in d3m_solve (PEC rows ignored), grad: n_cells doubles,
  * overwritten.  FP64 regardless of the factor precision.

@@ -25,6 +25,14 @@ struct Plan {
   int parts[3] = {1, 1, 1};
   std::vector<int> cuts[3];
   int64_t nex = 0, ney = 0, nez = 0, n_edges = 0, n_free = 0;
+  // ---- element kind and edge families (d3m_mesh)
+  int element = 0;                    // D3M_BRICK or D3M_TET
+  int nfam = 3;                       // edge families: 3 (bricks) or 7 (tetrahedra)
+  int cell_ne = 12;                   // edges per cell: 12 or 19
+  int64_t fam_off[8] = {0};           // first edge id of each family
+  int64_t fam_n[7][3] = {};           // start-node box of each family
+  std::vector<double> vert;           // tetrahedra: 3 doubles per node (empty: lattice)
+  double bS[12][12], bM[12][12], bT[6][12][12];  // brick element and face matrices
 
   // ---- decomposition
   int nsub = 0;
@@ -90,7 +98,10 @@ int build_plan(Ctx &c, const d3m_mesh *mesh, const d3m_materials *mat, double k,
                const d3m_partition *part);
 void element_matrices(const double h[3], double S[12][12], double M[12][12]);
 void face_matrix(const double h[3], int axis, int side, double T[12][12]);
-void cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[12]);
+constexpr int MAX_CELL_NE = 19;
+int cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[MAX_CELL_NE]);
+int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][MAX_CELL_NE],
+                  double M[MAX_CELL_NE][MAX_CELL_NE]);
 int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb);
 
 // engine.cu

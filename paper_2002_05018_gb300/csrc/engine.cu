@@ -2207,6 +2207,36 @@ __global__ void k_grad_eps(int nx, int ny, int nz, double k2, ElemMass Me, const
     grad[c] = k2 * acc;
   }
 }
+// The same gradient with per-cell edge lists and mass matrices (ne edges per
+// cell; the six Whitney tetrahedra of a cell have ne = 19).
+__global__ void k_grad_eps_cells(int64_t ncell, int ne, const int64_t *__restrict__ cell_edge,
+                                 const double *__restrict__ cell_mass, double k2, const double2 *__restrict__ x,
+                                 int64_t ldx, const double2 *__restrict__ y, int64_t ldy, int r,
+                                 const uint8_t *__restrict__ pec, double *__restrict__ grad) {
+  constexpr int NE = 19;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t *e = cell_edge + c * ne;
+    const double *Mc = cell_mass + c * ne * ne;
+    double acc = 0.0;
+    for (int rr = 0; rr < r; ++rr) {
+      double2 xv[NE], yv[NE];
+      for (int a = 0; a < ne; ++a) {
+        bool z = pec[e[a]] != 0;
+        xv[a] = z ? make_double2(0, 0) : x[e[a] + ldx * rr];
+        yv[a] = z ? make_double2(0, 0) : y[e[a] + ldy * rr];
+      }
+      for (int a = 0; a < ne; ++a) {
+        double2 mx = make_double2(0, 0);
+        for (int b = 0; b < ne; ++b) {
+          mx.x += Mc[a * ne + b] * xv[b].x;
+          mx.y += Mc[a * ne + b] * xv[b].y;
+        }
+        acc += yv[a].x * mx.x + yv[a].y * mx.y;  // Re(conj(y) * mx)
+      }
+    }
+    grad[c] = k2 * acc;
+  }
+}
 template <typename T>
 __global__ void k_scatter(const double2 *__restrict__ fe, const int64_t *__restrict__ owner, cx<T> *__restrict__ bM,
                           int64_t n, int r) {
@@ -2424,6 +2454,8 @@ struct DeviceState {
   int32_t *csi_col = nullptr;
   double *csi_val = nullptr;
   uint8_t *pec = nullptr;
+  int64_t *gc_edge = nullptr;  // tetrahedral meshes: per cell its 19 edges and
+  double *gc_mass = nullptr;   // 19 x 19 mass matrix (uploaded by the first gradient)
   // solve buffers (capacity in RHS)
   int cap = 0;
   void *bM = nullptr, *zM = nullptr, *xM = nullptr, *Y = nullptr;
@@ -4317,13 +4349,38 @@ int dev_grad_eps(Ctx &c, const double *x, int64_t ldx, const double *y, int64_t 
   rc = enter(c);
   if (rc) return rc;
   const Plan &P = c.plan;
-  ElemMass Me;
-  double S[12][12];
-  element_matrices(P.h, S, Me.M);
   cudaStream_t s = c.dev->stream;
   const int64_t ncell = (int64_t)P.nx * P.ny * P.nz;
-  k_grad_eps<<<grid1(ncell), 256, 0, s>>>(P.nx, P.ny, P.nz, P.k * P.k, Me, (const double2 *)x, ldx,
-                                          (const double2 *)y, ldy, nrhs, c.dev->pec, grad);
+  if (P.element == D3M_TET) {
+    DeviceState *d = c.dev;
+    if (!d->gc_edge) {
+      const int ne = P.cell_ne;
+      std::vector<int64_t> ce((size_t)ncell * ne);
+      std::vector<double> cm((size_t)ncell * ne * ne);
+      double S[MAX_CELL_NE][MAX_CELL_NE], M[MAX_CELL_NE][MAX_CELL_NE];
+      for (int64_t cc = 0; cc < ncell; ++cc) {
+        const int ci = (int)(cc % P.nx), cj = (int)((cc / P.nx) % P.ny), ck = (int)(cc / ((int64_t)P.nx * P.ny));
+        int64_t e[MAX_CELL_NE];
+        cell_edges(P, ci, cj, ck, e);
+        cell_matrices(P, ci, cj, ck, S, M);
+        for (int a = 0; a < ne; ++a) {
+          ce[cc * ne + a] = e[a];
+          for (int b = 0; b < ne; ++b) cm[(cc * ne + a) * ne + b] = M[a][b];
+        }
+      }
+      CUDA_TRY(upload(d, &d->gc_edge, ce));
+      CUDA_TRY(upload(d, &d->gc_mass, cm));
+    }
+    k_grad_eps_cells<<<grid1(ncell), 128, 0, s>>>(ncell, P.cell_ne, d->gc_edge, d->gc_mass, P.k * P.k,
+                                                 (const double2 *)x, ldx, (const double2 *)y, ldy, nrhs, d->pec,
+                                                 grad);
+  } else {
+    ElemMass Me;
+    double S[12][12];
+    element_matrices(P.h, S, Me.M);
+    k_grad_eps<<<grid1(ncell), 256, 0, s>>>(P.nx, P.ny, P.nz, P.k * P.k, Me, (const double2 *)x, ldx,
+                                            (const double2 *)y, ldy, nrhs, c.dev->pec, grad);
+  }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
   return D3M_OK;

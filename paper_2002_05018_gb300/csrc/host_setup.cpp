@@ -78,63 +78,272 @@ void face_matrix(const double h[3], int axis, int side, double T[12][12]) {
     }
 }
 
-static inline int64_t EX(const Plan &p, int64_t i, int64_t j, int64_t k) {
-  return i + p.nx * (j + (int64_t)(p.ny + 1) * k);
-}
-static inline int64_t EY(const Plan &p, int64_t i, int64_t j, int64_t k) {
-  return p.nex + i + (int64_t)(p.nx + 1) * (j + (int64_t)p.ny * k);
-}
-static inline int64_t EZ(const Plan &p, int64_t i, int64_t j, int64_t k) {
-  return p.nex + p.ney + i + (int64_t)(p.nx + 1) * (j + (int64_t)(p.ny + 1) * k);
-}
+// ------------------------------------------------------------ edge families
+// Directions of the edge families; bricks use the first three.
+static const int DIRS[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0},
+                               {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
 
-void cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[12]) {
+static inline int64_t EID(const Plan &p, int d, int64_t i, int64_t j, int64_t k) {
+  return p.fam_off[d] + i + p.fam_n[d][0] * (j + p.fam_n[d][1] * k);
+}
+static inline int64_t EX(const Plan &p, int64_t i, int64_t j, int64_t k) { return EID(p, 0, i, j, k); }
+static inline int64_t EY(const Plan &p, int64_t i, int64_t j, int64_t k) { return EID(p, 1, i, j, k); }
+static inline int64_t EZ(const Plan &p, int64_t i, int64_t j, int64_t k) { return EID(p, 2, i, j, k); }
+
+// Edges of cell (ci, cj, ck): the 12 brick edges (x-edges at (dy, dz) =
+// OFF[q], y-edges at (dx, dz), z-edges at (dx, dy)); tetrahedral cells add
+// the (1,1,0) diagonals at dz = 0, 1, the (1,0,1) diagonals at dy = 0, 1, the
+// (0,1,1) diagonals at dx = 0, 1 and the cell diagonal.  Returns the count.
+int cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[MAX_CELL_NE]) {
   for (int q = 0; q < 4; ++q) {
     int a = OFF[q][0], b = OFF[q][1];
     e[q] = EX(p, ci, cj + a, ck + b);
     e[4 + q] = EY(p, ci + a, cj, ck + b);
     e[8 + q] = EZ(p, ci + a, cj + b, ck);
   }
+  if (p.element != D3M_TET) return 12;
+  for (int b = 0; b < 2; ++b) {
+    e[12 + b] = EID(p, 3, ci, cj, ck + b);
+    e[14 + b] = EID(p, 4, ci, cj + b, ck);
+    e[16 + b] = EID(p, 5, ci + b, cj, ck);
+  }
+  e[18] = EID(p, 6, ci, cj, ck);
+  return 19;
 }
 
-// direction and start node of an edge
-static inline void edge_info(const Plan &p, int64_t e, int &d, int64_t &i, int64_t &j,
-                             int64_t &k) {
-  if (e < p.nex) {
-    d = 0;
-    i = e % p.nx;
-    int64_t r = e / p.nx;
-    j = r % (p.ny + 1);
-    k = r / (p.ny + 1);
-  } else if (e < p.nex + p.ney) {
-    d = 1;
-    int64_t q = e - p.nex;
-    i = q % (p.nx + 1);
-    int64_t r = q / (p.nx + 1);
-    j = r % p.ny;
-    k = r / p.ny;
-  } else {
-    d = 2;
-    int64_t q = e - p.nex - p.ney;
-    i = q % (p.nx + 1);
-    int64_t r = q / (p.nx + 1);
-    j = r % (p.ny + 1);
-    k = r / (p.ny + 1);
+// Position in cell_edges of the cell edge that starts at vertex offset o
+// (each 0/1) with direction d.
+static int local_edge(const int o[3], const int d[3]) {
+  switch (d[0] + 2 * d[1] + 4 * d[2]) {
+    case 1: return o[1] + 2 * o[2];      // (1,0,0)
+    case 2: return 4 + o[0] + 2 * o[2];  // (0,1,0)
+    case 4: return 8 + o[0] + 2 * o[1];  // (0,0,1)
+    case 3: return 12 + o[2];            // (1,1,0)
+    case 5: return 14 + o[1];            // (1,0,1)
+    case 6: return 16 + o[0];            // (0,1,1)
+    default: return 18;                  // (1,1,1)
   }
 }
 
-// All edges of the cells in box [lo, hi), increasing global id.
+// family and start node of an edge
+static inline void edge_info(const Plan &p, int64_t e, int &d, int64_t &i, int64_t &j,
+                             int64_t &k) {
+  d = 0;
+  while (d + 1 < p.nfam && e >= p.fam_off[d + 1]) ++d;
+  const int64_t q = e - p.fam_off[d];
+  i = q % p.fam_n[d][0];
+  const int64_t r = q / p.fam_n[d][0];
+  j = r % p.fam_n[d][1];
+  k = r / p.fam_n[d][1];
+}
+
+// All edges of the cells in box [lo, hi), increasing global id: per family,
+// the start nodes in [lo, hi - direction].
 template <class F>
 static void for_box_edges(const Plan &p, const int lo[3], const int hi[3], F &&fn) {
-  for (int64_t k = lo[2]; k <= hi[2]; ++k)
-    for (int64_t j = lo[1]; j <= hi[1]; ++j)
-      for (int64_t i = lo[0]; i < hi[0]; ++i) fn(EX(p, i, j, k));
-  for (int64_t k = lo[2]; k <= hi[2]; ++k)
-    for (int64_t j = lo[1]; j < hi[1]; ++j)
-      for (int64_t i = lo[0]; i <= hi[0]; ++i) fn(EY(p, i, j, k));
-  for (int64_t k = lo[2]; k < hi[2]; ++k)
-    for (int64_t j = lo[1]; j <= hi[1]; ++j)
-      for (int64_t i = lo[0]; i <= hi[0]; ++i) fn(EZ(p, i, j, k));
+  for (int d = 0; d < p.nfam; ++d)
+    for (int64_t k = lo[2]; k <= hi[2] - DIRS[d][2]; ++k)
+      for (int64_t j = lo[1]; j <= hi[1] - DIRS[d][1]; ++j)
+        for (int64_t i = lo[0]; i <= hi[0] - DIRS[d][0]; ++i) fn(EID(p, d, i, j, k));
+}
+
+// ------------------------------------------------------------ Whitney tetrahedra
+// Six tetrahedra per cell: the monotone lattice paths (0,0,0) -> e_a ->
+// e_a + e_b -> (1,1,1), one per order (a, b, c) of the axes.  With
+// barycentric coordinates lam_i, the edge (a, b) of a tetrahedron carries
+// N_ab = l_ab (lam_a grad lam_b - lam_b grad lam_a) (l_ab its length, so the
+// dof is the line average of E . t), curl N_ab = 2 l_ab grad lam_a x grad lam_b,
+// and int lam_i lam_j = V (1 + [i == j]) / 20 (/ 12 on a triangle of area A).
+static const int TET_AXES[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+static const int TET_E[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+static const int TRI_E[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+
+static inline void sub3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[0] - b[0];
+  o[1] = a[1] - b[1];
+  o[2] = a[2] - b[2];
+}
+static inline void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static inline double dot3(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static inline void node_pos(const Plan &p, int64_t i, int64_t j, int64_t k, double x[3]) {
+  if (p.vert.empty()) {
+    x[0] = (double)i * p.h[0];
+    x[1] = (double)j * p.h[1];
+    x[2] = (double)k * p.h[2];
+  } else {
+    const double *v = p.vert.data() + 3 * (i + (int64_t)(p.nx + 1) * (j + (int64_t)(p.ny + 1) * k));
+    x[0] = v[0];
+    x[1] = v[1];
+    x[2] = v[2];
+  }
+}
+
+// Vertex offsets of tetrahedron t of a cell.
+static void tet_offsets(int t, int o[4][3]) {
+  for (int q = 0; q < 3; ++q) o[0][q] = 0;
+  for (int v = 1; v < 4; ++v) {
+    for (int q = 0; q < 3; ++q) o[v][q] = o[v - 1][q];
+    o[v][TET_AXES[t][v - 1]] = 1;
+  }
+}
+
+// Barycentric gradients and signed 6 x volume of tetrahedron X.
+static double tet_grads(const double X[4][3], double g[4][3]) {
+  double e1[3], e2[3], e3[3], c[3];
+  sub3(X[1], X[0], e1);
+  sub3(X[2], X[0], e2);
+  sub3(X[3], X[0], e3);
+  cross3(e2, e3, c);
+  const double det = dot3(e1, c);
+  cross3(e2, e3, g[1]);
+  cross3(e3, e1, g[2]);
+  cross3(e1, e2, g[3]);
+  for (int q = 0; q < 3; ++q) {
+    g[1][q] /= det;
+    g[2][q] /= det;
+    g[3][q] /= det;
+    g[0][q] = -(g[1][q] + g[2][q] + g[3][q]);
+  }
+  return det;
+}
+
+// int (lam_a grad lam_b - lam_b grad lam_a) . (lam_c grad lam_d - lam_d grad lam_c)
+// in units of the simplex measure / (20 or 12): the bracket of the mass formula.
+static inline double whitney_pair(const double g[][3], int a, int b, int c, int d) {
+  return (1.0 + (a == c)) * dot3(g[b], g[d]) - (1.0 + (a == d)) * dot3(g[b], g[c]) -
+         (1.0 + (b == c)) * dot3(g[a], g[d]) + (1.0 + (b == d)) * dot3(g[a], g[c]);
+}
+
+// Orientation sign of tetrahedron t in the regular lattice.
+static double tet_parity(int t) {
+  int o[4][3];
+  tet_offsets(t, o);
+  double X[4][3], g[4][3];
+  for (int v = 0; v < 4; ++v)
+    for (int q = 0; q < 3; ++q) X[v][q] = o[v][q];
+  return tet_grads(X, g) > 0 ? 1.0 : -1.0;
+}
+
+static void cell_tet(const Plan &p, int ci, int cj, int ck, int t, int o[4][3], double X[4][3]) {
+  tet_offsets(t, o);
+  for (int v = 0; v < 4; ++v) node_pos(p, ci + o[v][0], cj + o[v][1], ck + o[v][2], X[v]);
+}
+
+// S = int curl N . curl N and M = int N . N of a cell, in cell_edges order.
+int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][MAX_CELL_NE],
+                  double M[MAX_CELL_NE][MAX_CELL_NE]) {
+  if (p.element != D3M_TET) {
+    for (int a = 0; a < 12; ++a)
+      for (int b = 0; b < 12; ++b) {
+        S[a][b] = p.bS[a][b];
+        M[a][b] = p.bM[a][b];
+      }
+    return 12;
+  }
+  std::memset(S, 0, sizeof(double) * MAX_CELL_NE * MAX_CELL_NE);
+  std::memset(M, 0, sizeof(double) * MAX_CELL_NE * MAX_CELL_NE);
+  for (int t = 0; t < 6; ++t) {
+    int o[4][3];
+    double X[4][3], g[4][3];
+    cell_tet(p, ci, cj, ck, t, o, X);
+    const double vol = std::fabs(tet_grads(X, g)) / 6.0;
+    int loc[6];
+    double ell[6], cu[6][3];
+    for (int q = 0; q < 6; ++q) {
+      const int a = TET_E[q][0], b = TET_E[q][1];
+      int d[3] = {o[b][0] - o[a][0], o[b][1] - o[a][1], o[b][2] - o[a][2]};
+      loc[q] = local_edge(o[a], d);
+      double ev[3];
+      sub3(X[b], X[a], ev);
+      ell[q] = std::sqrt(dot3(ev, ev));
+      cross3(g[a], g[b], cu[q]);
+      for (int r = 0; r < 3; ++r) cu[q][r] *= 2.0 * ell[q];
+    }
+    for (int q = 0; q < 6; ++q)
+      for (int r = 0; r < 6; ++r) {
+        S[loc[q]][loc[r]] += vol * dot3(cu[q], cu[r]);
+        M[loc[q]][loc[r]] += vol / 20.0 * ell[q] * ell[r] *
+                             whitney_pair(g, TET_E[q][0], TET_E[q][1], TET_E[r][0], TET_E[r][1]);
+      }
+  }
+  return 19;
+}
+
+// The two triangles of cell face {axis = side}, split along the diagonal
+// from its lowest to its highest corner: vertex offsets.
+static void face_tris(int axis, int side, int o[2][3][3]) {
+  const int u = axis == 0 ? 1 : 0, v = axis == 2 ? 1 : 2;
+  for (int t = 0; t < 2; ++t) {
+    for (int w = 0; w < 3; ++w)
+      for (int q = 0; q < 3; ++q) o[t][w][q] = 0;
+    for (int w = 0; w < 3; ++w) o[t][w][axis] = side;
+    o[t][1][t ? v : u] = 1;
+    o[t][2][u] = 1;
+    o[t][2][v] = 1;
+  }
+}
+
+// In-plane barycentric gradients of triangle Q: grad mu_i = n x (Q_{i+2} -
+// Q_{i+1}) / (2A), n the unit normal; returns the area.
+static double tri_grads(const double Q[3][3], double g[3][3]) {
+  double e1[3], e2[3], nrm[3];
+  sub3(Q[1], Q[0], e1);
+  sub3(Q[2], Q[0], e2);
+  cross3(e1, e2, nrm);
+  const double twoA = std::sqrt(dot3(nrm, nrm));
+  for (int q = 0; q < 3; ++q) nrm[q] /= twoA;
+  for (int i = 0; i < 3; ++i) {
+    double ev[3];
+    sub3(Q[(i + 2) % 3], Q[(i + 1) % 3], ev);
+    cross3(nrm, ev, g[i]);
+    for (int q = 0; q < 3; ++q) g[i][q] /= twoA;
+  }
+  return 0.5 * twoA;
+}
+
+struct FaceTri {
+  double Q[3][3], g[3][3], area, ell[3];
+  int loc[3];
+};
+static void cell_face_tri(const Plan &p, int ci, int cj, int ck, const int o[3][3], FaceTri &f) {
+  for (int w = 0; w < 3; ++w) node_pos(p, ci + o[w][0], cj + o[w][1], ck + o[w][2], f.Q[w]);
+  f.area = tri_grads(f.Q, f.g);
+  for (int q = 0; q < 3; ++q) {
+    const int a = TRI_E[q][0], b = TRI_E[q][1];
+    int d[3] = {o[b][0] - o[a][0], o[b][1] - o[a][1], o[b][2] - o[a][2]};
+    f.loc[q] = local_edge(o[a], d);
+    double ev[3];
+    sub3(f.Q[b], f.Q[a], ev);
+    f.ell[q] = std::sqrt(dot3(ev, ev));
+  }
+}
+
+// Tangential face mass int_face N_t . N_t dS of face {axis = side} of a cell.
+static void cell_face_matrix(const Plan &p, int ci, int cj, int ck, int axis, int side,
+                             double T[MAX_CELL_NE][MAX_CELL_NE]) {
+  if (p.element != D3M_TET) {
+    for (int a = 0; a < 12; ++a)
+      for (int b = 0; b < 12; ++b) T[a][b] = p.bT[2 * axis + side][a][b];
+    return;
+  }
+  std::memset(T, 0, sizeof(double) * MAX_CELL_NE * MAX_CELL_NE);
+  int o[2][3][3];
+  face_tris(axis, side, o);
+  for (int t = 0; t < 2; ++t) {
+    FaceTri f;
+    cell_face_tri(p, ci, cj, ck, o[t], f);
+    for (int q = 0; q < 3; ++q)
+      for (int r = 0; r < 3; ++r)
+        T[f.loc[q]][f.loc[r]] += f.area / 12.0 * f.ell[q] * f.ell[r] *
+                                 whitney_pair(f.g, TRI_E[q][0], TRI_E[q][1], TRI_E[r][0], TRI_E[r][1]);
+  }
 }
 
 static inline int sub_id(const Plan &p, int x, int y, int z) {
@@ -215,7 +424,7 @@ static void sub_nd(const Plan &p, std::vector<char> &avail, const int lo[3], con
     int d;
     int64_t ijk[3];
     edge_info(p, e, d, ijk[0], ijk[1], ijk[2]);
-    if (d != axis && ijk[axis] == c) sep.push_back(e);
+    if (!DIRS[d][axis] && ijk[axis] == c) sep.push_back(e);  // the edges lying in plane c
   }
   for (int64_t e : sep) avail[e] = 0;
   int lhi[3] = {hi[0], hi[1], hi[2]}, rlo[3] = {lo[0], lo[1], lo[2]};
@@ -270,11 +479,73 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   p.h[0] = p.lx / p.nx;
   p.h[1] = p.ly / p.ny;
   p.h[2] = p.lz / p.nz;
-  p.nex = (int64_t)p.nx * (p.ny + 1) * (p.nz + 1);
-  p.ney = (int64_t)(p.nx + 1) * p.ny * (p.nz + 1);
-  p.nez = (int64_t)(p.nx + 1) * (p.ny + 1) * p.nz;
-  p.n_edges = p.nex + p.ney + p.nez;
+  p.element = mesh->element;
+  if (p.element != D3M_BRICK && p.element != D3M_TET) {
+    ctx.err = "d3m_setup: mesh element must be D3M_BRICK or D3M_TET";
+    return D3M_EINVAL;
+  }
+  if (mesh->vertices && p.element != D3M_TET) {
+    ctx.err = "d3m_setup: vertex positions are for tetrahedral meshes only";
+    return D3M_EINVAL;
+  }
+  p.nfam = p.element == D3M_TET ? 7 : 3;
+  p.cell_ne = p.element == D3M_TET ? 19 : 12;
+  p.fam_off[0] = 0;
+  for (int d = 0; d < p.nfam; ++d) {
+    p.fam_n[d][0] = p.nx + 1 - DIRS[d][0];
+    p.fam_n[d][1] = p.ny + 1 - DIRS[d][1];
+    p.fam_n[d][2] = p.nz + 1 - DIRS[d][2];
+    p.fam_off[d + 1] = p.fam_off[d] + p.fam_n[d][0] * p.fam_n[d][1] * p.fam_n[d][2];
+  }
+  p.nex = p.fam_off[1];
+  p.ney = p.fam_off[2] - p.fam_off[1];
+  p.nez = p.fam_off[3] - p.fam_off[2];
+  p.n_edges = p.fam_off[p.nfam];
   const int64_t ncell = (int64_t)p.nx * p.ny * p.nz;
+  p.vert.clear();
+  if (mesh->vertices) {
+    const int64_t nn3 = 3 * (int64_t)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+    p.vert.assign(mesh->vertices, mesh->vertices + nn3);
+    const int nmax[3] = {p.nx, p.ny, p.nz};
+    const double len[3] = {p.lx, p.ly, p.lz};
+    for (int64_t k = 0; k <= p.nz; ++k)
+      for (int64_t j = 0; j <= p.ny; ++j)
+        for (int64_t i = 0; i <= p.nx; ++i) {
+          const int64_t ijk[3] = {i, j, k};
+          double x[3];
+          node_pos(p, i, j, k, x);
+          for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(x[a])) {
+              ctx.err = "d3m_setup: non-finite vertex position";
+              return D3M_EINVAL;
+            }
+            const bool lo = ijk[a] == 0, hi = ijk[a] == nmax[a];
+            if ((lo && std::fabs(x[a]) > 1e-12 * len[a]) || (hi && std::fabs(x[a] - len[a]) > 1e-12 * len[a])) {
+              ctx.err = "d3m_setup: a boundary vertex left its boundary plane";
+              return D3M_EINVAL;
+            }
+          }
+        }
+  }
+  if (p.element == D3M_TET) {
+    for (int t = 0; t < 6; ++t) {
+      const double par = tet_parity(t);
+      for (int ck = 0; ck < p.nz; ++ck)
+        for (int cj = 0; cj < p.ny; ++cj)
+          for (int ci = 0; ci < p.nx; ++ci) {
+            int o[4][3];
+            double X[4][3], g[4][3];
+            cell_tet(p, ci, cj, ck, t, o, X);
+            if (!(par * tet_grads(X, g) > 0.0)) {
+              ctx.err = "d3m_setup: a tetrahedron is inverted or degenerate";
+              return D3M_EINVAL;
+            }
+          }
+    }
+  }
+  element_matrices(p.h, p.bS, p.bM);
+  for (int axis = 0; axis < 3; ++axis)
+    for (int side = 0; side < 2; ++side) face_matrix(p.h, axis, side, p.bT[2 * axis + side]);
   if (!mat || !mat->eps_r) {
     ctx.err = "d3m_setup: eps_r is required";
     return D3M_EINVAL;
@@ -336,7 +607,7 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
     edge_info(p, e, d, ijk[0], ijk[1], ijk[2]);
     int iv[3][2], cnt[3];
     for (int a = 0; a < 3; ++a) {
-      if (a == d) {
+      if (DIRS[d][a]) {
         iv[a][0] = cell_interval(p.cuts[a], ijk[a]);
         cnt[a] = 1;
       } else {
@@ -458,24 +729,21 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   }
 
   // ---- entries of M (lower triangle), per subdomain
-  double S[12][12], Me[12][12], T[6][12][12];
-  element_matrices(p.h, S, Me);
-  for (int axis = 0; axis < 3; ++axis)
-    for (int side = 0; side < 2; ++side) face_matrix(p.h, axis, side, T[2 * axis + side]);
   const cplx jk(0.0, k);
   // interface loss/gain coefficient (d3m_options.alpha_re/im; 0 -> jk)
   const cplx alpha = (ctx.opt.alpha_re == 0.0 && ctx.opt.alpha_im == 0.0) ? jk
                                                                          : cplx(ctx.opt.alpha_re, ctx.opt.alpha_im);
   std::vector<Trip> trips;
+  double Sc[MAX_CELL_NE][MAX_CELL_NE], Mc[MAX_CELL_NE][MAX_CELL_NE], Tf[MAX_CELL_NE][MAX_CELL_NE];
   for (int s = 0; s < p.nsub; ++s) {
     int64_t m0 = sub_m0[s];
     int64_t m1_ = s + 1 < p.nsub ? sub_m0[s + 1] : p.lam_start;
     for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = v;
-    auto add_block = [&](const int64_t e[12], const double (*X)[12], cplx coef) {
-      for (int a = 0; a < 12; ++a) {
+    auto add_block = [&](const int64_t *e, int ne, const double (*X)[MAX_CELL_NE], cplx coef) {
+      for (int a = 0; a < ne; ++a) {
         int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
         if (ra < 0) continue;
-        for (int b = 0; b < 12; ++b) {
+        for (int b = 0; b < ne; ++b) {
           if (X[a][b] == 0.0) continue;
           int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
           if (rb < 0 || ra < rb) continue;
@@ -490,16 +758,17 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
     for (int ck = lo[2]; ck < hi[2]; ++ck)
       for (int cj = lo[1]; cj < hi[1]; ++cj)
         for (int ci = lo[0]; ci < hi[0]; ++ci) {
-          int64_t e[12];
-          cell_edges(p, ci, cj, ck, e);
+          int64_t e[MAX_CELL_NE];
+          const int ne = cell_edges(p, ci, cj, ck, e);
+          cell_matrices(p, ci, cj, ck, Sc, Mc);
           cplx eps = p.eps[ci + (int64_t)p.nx * (cj + (int64_t)p.ny * ck)];
-          for (int a = 0; a < 12; ++a) {
+          for (int a = 0; a < ne; ++a) {
             int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
             if (ra < 0) continue;
-            for (int b = 0; b < 12; ++b) {
+            for (int b = 0; b < ne; ++b) {
               int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
               if (rb < 0 || ra < rb) continue;
-              cplx v = S[a][b] - k * k * eps * Me[a][b];
+              cplx v = Sc[a][b] - k * k * eps * Mc[a][b];
               if (v != cplx(0.0)) trips.push_back({ra, rb, v});
             }
           }
@@ -509,13 +778,14 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
               int layer = side ? hi[axis] - 1 : lo[axis];
               if (c3[axis] != layer) continue;
               int node = side ? hi[axis] : lo[axis];
+              cell_face_matrix(p, ci, cj, ck, axis, side, Tf);
               if (node == 0 || node == nn[axis]) {
-                add_block(e, T[2 * axis + side], jk);  // first-order ABC
+                add_block(e, ne, Tf, jk);  // first-order ABC
               } else {
                 int npos[3] = {pos[0], pos[1], pos[2]};
                 npos[axis] += side ? 1 : -1;
                 int nb = sub_id(p, npos[0], npos[1], npos[2]);
-                add_block(e, T[2 * axis + side], nb > s ? alpha : -alpha);  // interface loss / gain
+                add_block(e, ne, Tf, nb > s ? alpha : -alpha);  // interface loss / gain
               }
             }
         }
@@ -567,13 +837,13 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
             for (int ck = c0[2]; ck < c1[2]; ++ck)
               for (int cj = c0[1]; cj < c1[1]; ++cj)
                 for (int ci = c0[0]; ci < c1[0]; ++ci) {
-                  int64_t e[12];
-                  cell_edges(p, ci, cj, ck, e);
-                  const double (*Tf)[12] = T[2 * axis + side];
-                  for (int j = 0; j < 12; ++j) {
+                  int64_t e[MAX_CELL_NE];
+                  const int ne = cell_edges(p, ci, cj, ck, e);
+                  cell_face_matrix(p, ci, cj, ck, axis, side, Tf);
+                  for (int j = 0; j < ne; ++j) {
                     const int64_t l = find_lm(e[j], a, b);
                     if (l < 0) continue;
-                    for (int i = 0; i < 12; ++i) {
+                    for (int i = 0; i < ne; ++i) {
                       if (Tf[i][j] == 0.0 || find_lm(e[i], a, b) < 0) continue;
                       by_sub[a].push_back({e[i], l, Tf[i][j]});
                       by_sub[b].push_back({e[i], l, -Tf[i][j]});
@@ -763,23 +1033,30 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   // ---- global operator A on free edges (full CSR) for fp64 residuals
   {
     std::vector<Trip> g;
-    g.reserve((size_t)ncell * 144);
+    g.reserve((size_t)ncell * p.cell_ne * p.cell_ne);
+    static thread_local double Tb[6][MAX_CELL_NE][MAX_CELL_NE];
     for (int ck = 0; ck < p.nz; ++ck)
       for (int cj = 0; cj < p.ny; ++cj)
         for (int ci = 0; ci < p.nx; ++ci) {
-          int64_t e[12];
-          cell_edges(p, ci, cj, ck, e);
+          int64_t e[MAX_CELL_NE];
+          const int ne = cell_edges(p, ci, cj, ck, e);
+          cell_matrices(p, ci, cj, ck, Sc, Mc);
           cplx eps = p.eps[ci + (int64_t)p.nx * (cj + (int64_t)p.ny * ck)];
           int c3[3] = {ci, cj, ck};
-          for (int a = 0; a < 12; ++a) {
+          bool bnd[6];
+          for (int axis = 0; axis < 3; ++axis) {
+            bnd[2 * axis] = c3[axis] == 0;
+            bnd[2 * axis + 1] = c3[axis] == nn[axis] - 1;
+            for (int side = 0; side < 2; ++side)
+              if (bnd[2 * axis + side]) cell_face_matrix(p, ci, cj, ck, axis, side, Tb[2 * axis + side]);
+          }
+          for (int a = 0; a < ne; ++a) {
             if (p.pec[e[a]]) continue;
-            for (int b = 0; b < 12; ++b) {
+            for (int b = 0; b < ne; ++b) {
               if (p.pec[e[b]]) continue;
-              cplx v = S[a][b] - k * k * eps * Me[a][b];
-              for (int axis = 0; axis < 3; ++axis) {
-                if (c3[axis] == 0) v += jk * T[2 * axis][a][b];
-                if (c3[axis] == nn[axis] - 1) v += jk * T[2 * axis + 1][a][b];
-              }
+              cplx v = Sc[a][b] - k * k * eps * Mc[a][b];
+              for (int f = 0; f < 6; ++f)
+                if (bnd[f]) v += jk * Tb[f][a][b];
               if (v != cplx(0.0)) g.push_back({e[a], e[b], v});
             }
           }
@@ -805,16 +1082,97 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
 }
 
 // ------------------------------------------------------------ plane-wave RHS
-int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
-  const double gq[3] = {0.5 - 0.5 * std::sqrt(0.6), 0.5, 0.5 + 0.5 * std::sqrt(0.6)};
-  const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
-  const int nn[3] = {p.nx, p.ny, p.nz};
+// U = n x curl E_inc - jk (E_inc)_t at point xyz for the plane wave kp (3
+// direction components, complex polarisation as re/im pairs), outward normal n.
+static void incident_u(const Plan &p, const double *kp, const double xyz[3], const double nvec[3], cplx U[3]) {
   const cplx J(0.0, 1.0);
+  cplx pol[3] = {cplx(kp[3], kp[4]), cplx(kp[5], kp[6]), cplx(kp[7], kp[8])};
+  double kr = kp[0] * xyz[0] + kp[1] * xyz[1] + kp[2] * xyz[2];
+  cplx ph = std::exp(-J * p.k * kr);
+  cplx E[3] = {pol[0] * ph, pol[1] * ph, pol[2] * ph};
+  // curl E = -jk khat x E
+  cplx cE[3] = {-J * p.k * (kp[1] * E[2] - kp[2] * E[1]), -J * p.k * (kp[2] * E[0] - kp[0] * E[2]),
+                -J * p.k * (kp[0] * E[1] - kp[1] * E[0])};
+  cplx ndotE = nvec[0] * E[0] + nvec[1] * E[1] + nvec[2] * E[2];
+  cplx nxc[3] = {nvec[1] * cE[2] - nvec[2] * cE[1], nvec[2] * cE[0] - nvec[0] * cE[2],
+                 nvec[0] * cE[1] - nvec[1] * cE[0]};
+  for (int a = 0; a < 3; ++a) U[a] = nxc[a] - J * p.k * (E[a] - nvec[a] * ndotE);
+}
+
+// Tetrahedral meshes: f_v = -int U . N_v dS over the outer-boundary triangles,
+// each by Radon's 7-point degree-5 rule (barycentric points (1/3,1/3,1/3) and
+// the permutations of (a, a, 1 - 2a), a = (6 -+ sqrt 15)/21; weights 9/40 and
+// (155 -+ sqrt 15)/1200 of the area).
+static int rhs_planewave_tet(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
+  const double r15 = std::sqrt(15.0);
+  double qb[7][3], qw[7];
+  qb[0][0] = qb[0][1] = qb[0][2] = 1.0 / 3.0;
+  qw[0] = 9.0 / 40.0;
+  for (int g = 0; g < 2; ++g) {
+    const double a = g ? (6.0 + r15) / 21.0 : (6.0 - r15) / 21.0;
+    const double wt = g ? (155.0 + r15) / 1200.0 : (155.0 - r15) / 1200.0;
+    for (int r = 0; r < 3; ++r) {
+      double *b = qb[1 + 3 * g + r];
+      b[0] = b[1] = b[2] = a;
+      b[2 - r] = 1.0 - 2.0 * a;
+      qw[1 + 3 * g + r] = wt;
+    }
+  }
+  const int nn[3] = {p.nx, p.ny, p.nz};
+  for (int axis = 0; axis < 3; ++axis)
+    for (int side = 0; side < 2; ++side) {
+      double nvec[3] = {0, 0, 0};
+      nvec[axis] = side ? 1.0 : -1.0;
+      int o[2][3][3];
+      face_tris(axis, side, o);
+      const int layer = side ? nn[axis] - 1 : 0;
+      for (int ck = 0; ck < p.nz; ++ck)
+        for (int cj = 0; cj < p.ny; ++cj)
+          for (int ci = 0; ci < p.nx; ++ci) {
+            const int c3[3] = {ci, cj, ck};
+            if (c3[axis] != layer) continue;
+            int64_t e[MAX_CELL_NE];
+            cell_edges(p, ci, cj, ck, e);
+            for (int t = 0; t < 2; ++t) {
+              FaceTri f;
+              cell_face_tri(p, ci, cj, ck, o[t], f);
+              for (int q = 0; q < 7; ++q) {
+                const double *mu = qb[q];
+                double xyz[3], N[3][3];
+                for (int a = 0; a < 3; ++a) xyz[a] = mu[0] * f.Q[0][a] + mu[1] * f.Q[1][a] + mu[2] * f.Q[2][a];
+                for (int m = 0; m < 3; ++m) {
+                  const int a = TRI_E[m][0], b = TRI_E[m][1];
+                  for (int c = 0; c < 3; ++c) N[m][c] = f.ell[m] * (mu[a] * f.g[b][c] - mu[b] * f.g[a][c]);
+                }
+                const double w = qw[q] * f.area;
+                for (int r = 0; r < nrhs; ++r) {
+                  cplx U[3];
+                  incident_u(p, khat_pol + 9 * r, xyz, nvec, U);
+                  for (int m = 0; m < 3; ++m) {
+                    cplx dot = U[0] * N[m][0] + U[1] * N[m][1] + U[2] * N[m][2];
+                    int64_t idx = e[f.loc[m]] + ldb * r;
+                    rhs[2 * idx] -= w * dot.real();
+                    rhs[2 * idx + 1] -= w * dot.imag();
+                  }
+                }
+              }
+            }
+          }
+    }
+  return D3M_OK;
+}
+
+int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
   for (int r = 0; r < nrhs; ++r)
     for (int64_t e = 0; e < p.n_edges; ++e) {
       rhs[2 * (e + ldb * r)] = 0.0;
       rhs[2 * (e + ldb * r) + 1] = 0.0;
     }
+  if (p.element == D3M_TET) return rhs_planewave_tet(p, khat_pol, nrhs, rhs, ldb);
+  const double gq[3] = {0.5 - 0.5 * std::sqrt(0.6), 0.5, 0.5 + 0.5 * std::sqrt(0.6)};
+  const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  const int nn[3] = {p.nx, p.ny, p.nz};
+  const cplx J(0.0, 1.0);
   for (int axis = 0; axis < 3; ++axis) {
     int u = axis == 0 ? 1 : 0, v = axis == 2 ? 1 : 2;
     double area = p.h[u] * p.h[v];
@@ -828,7 +1186,7 @@ int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, 
           for (int ci = 0; ci < lim[0]; ++ci) {
             int c3[3] = {ci, cj, ck};
             if (c3[axis] != layer) continue;
-            int64_t e[12];
+            int64_t e[MAX_CELL_NE];
             cell_edges(p, ci, cj, ck, e);
             for (int qa = 0; qa < 3; ++qa)
               for (int qb = 0; qb < 3; ++qb) {

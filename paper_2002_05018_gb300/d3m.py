@@ -24,9 +24,13 @@ _SYMBOLS = ["d3m_setup", "d3m_factor", "d3m_solve", "d3m_solve_host", "d3m_rhs_p
             "d3m_last_error", "d3m_free", "d3m_solve_adjoint", "d3m_grad_eps", "d3m_set_profile"]
 
 
+BRICK, TET = 0, 1
+
+
 class Mesh(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("element", ctypes.c_int32), ("vertices", ctypes.POINTER(ctypes.c_double))]
 
 
 class Materials(ctypes.Structure):
@@ -140,14 +144,16 @@ class Solver:
     def __init__(self, nx, ny, nz, lx, ly, lz, eps, k, cx, cy, cz, pec=None, precision=FP64,
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
                  update_kernel=0, autotune=0, autotune_cache=None, lookahead=0, refine_method=0,
-                 gmres_restart=0, gmres_tol=0.0, alpha=None, solve_kernel=0, lm_weight=0):
+                 gmres_restart=0, gmres_tol=0.0, alpha=None, solve_kernel=0, lm_weight=0, element=BRICK,
+                 vertices=None):
         self.lib = load()
         self.n_cells = nx * ny * nz
-        self.n_edges = nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
         self._eps = np.ascontiguousarray(np.asarray(eps, np.complex128).view(np.float64))
+        self._vert = None if vertices is None else np.ascontiguousarray(np.asarray(vertices, np.float64))
         self._cuts = [np.ascontiguousarray(np.asarray(c, np.int32)) for c in (cx, cy, cz)]
         self._pec = None if pec is None else np.ascontiguousarray(np.asarray(pec, np.uint8))
-        mesh = Mesh(nx, ny, nz, lx, ly, lz)
+        mesh = Mesh(nx, ny, nz, lx, ly, lz, int(element),
+                    None if self._vert is None else _ptr(self._vert, ctypes.c_double))
         mat = Materials(_ptr(self._eps, ctypes.c_double),
                         None if self._pec is None else _ptr(self._pec, ctypes.c_uint8))
         part = Partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, *[_ptr(c, ctypes.c_int32) for c in self._cuts])
@@ -164,11 +170,14 @@ class Solver:
                                 ctypes.byref(opt), ctypes.byref(h))
         self.h = h
         self._check(rc)
+        self.n_edges = int(self.stats()["n_edges"])
 
     @classmethod
     def from_workload(cls, w, precision=FP64, **kw):
         kw.setdefault("alpha", getattr(w, "alpha", None))
         kw.setdefault("lm_weight", getattr(w, "lm_weight", 0))
+        kw.setdefault("element", TET if getattr(w, "element", "brick") == "tet" else BRICK)
+        kw.setdefault("vertices", getattr(w, "vertices", None))
         return cls(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.eps, w.k, w.cx, w.cy, w.cz, pec=w.pec_edge,
                    precision=precision, **kw)
 

@@ -85,3 +85,22 @@ def test_gradcheck_tiny_mesh():
         return _J(ag.solve(e, ff.t().contiguous().t(), geom), probes)
 
     assert torch.autograd.gradcheck(fn, (eps, ft), eps=1e-6, atol=1e-6, rtol=1e-5, fast_mode=True)
+
+
+def test_tetrahedral_gradient_vs_oracle():
+    """d3m_grad_eps on six tetrahedra per cell (per-cell 19 x 19 masses)
+    against the oracle adjoint gradient."""
+    _need_gpu()
+    w = W.tetrahedral(W.tiny(5, 4, 4, 2, 2, 1, seed=12, nrhs=2), 0.1)
+    f = fem.rhs_planewave(w)
+    rng = np.random.default_rng(5)
+    probes = np.sort(rng.choice(w.n_edges, 8, replace=False))
+    eps = torch.tensor(w.eps.real.copy(), device="cuda", requires_grad=True)
+    fd_t = torch.tensor(f.T.copy(), device="cuda").t()
+    x = ag.solve(eps, fd_t, ag.geom_of(w))
+    J = _J(x, torch.tensor(probes, device="cuda"))
+    J.backward()
+    g = eps.grad.cpu().numpy()
+    Jo, go = adjoint.gradient(w, f, probes)
+    assert abs(J.item() - Jo) < 1e-9 * Jo
+    assert np.abs(g - go).max() < 1e-8 * np.abs(go).max()

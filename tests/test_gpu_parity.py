@@ -212,6 +212,47 @@ def test_mass_weighted_multipliers(precision):
     assert np.abs(lam - ref["lam"]).max() < ltol * np.abs(ref["lam"]).max()
 
 
+TET = [
+    lambda: W.tetrahedral(W.tiny(4, 4, 4, 2, 2, 2, seed=1, nrhs=2), 0.1, seed=2),
+    lambda: W.tetrahedral(W.tiny(7, 6, 5, 3, 2, 2, seed=4, jitter=True, nrhs=3), 0.1),
+    lambda: W.tetrahedral(W.tiny(8, 3, 3, 4, 1, 1, seed=3, nrhs=2), 0.15),   # a chain
+]
+
+
+@pytest.mark.parametrize("mk", TET)
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_tetrahedral_meshes(mk, precision):
+    """Six Whitney tetrahedra per cell on jittered vertices: the GPU solution
+    equals the oracle's global solve element by element and its multipliers
+    equal the oracle's D3M multipliers."""
+    _need_gpu()
+    w = mk()
+    s, x, info, f = _solve_case(w, precision)
+    _check_tiny(w, x, f, precision)
+    ref = od3m.solve(w, f, return_all=True)
+    lam = s.lam(f.shape[1])
+    ltol = 1e-9 if precision == d3m.FP64 else 1e-4
+    assert np.abs(lam - ref["lam"]).max() < ltol * np.abs(ref["lam"]).max()
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_tetrahedral_uneven_partition(precision):
+    """A 14x12x12-cell box on six jittered tetrahedra per cell (15,590
+    edges), jittered uneven 3x2x2 cuts, per-cell eps, against the oracle's
+    global solve element by element (the 20^3 tetrahedral mesh takes the
+    oracle's sparse LU minutes, so this is the largest tetrahedral case
+    checked element by element)."""
+    _need_gpu()
+    w = W.tetrahedral(W.tiny(14, 12, 12, 3, 2, 2, seed=3, nrhs=2, jitter=True), 0.1)
+    s, x, info, f = _solve_case(w, precision)
+    xg = fem.solve_global(w, f)
+    tol = 1e-10 if precision == d3m.FP64 else 1e-8
+    assert np.abs(x - xg).max() < tol * np.abs(xg).max()
+    assert fem.rel_residual(w, x, f).max() < (1e-12 if precision == d3m.FP64 else 1e-10)
+    s.close()
+
+
 def test_config3_fp64():
     _need_gpu()
     w = W.make(3)

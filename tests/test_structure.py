@@ -21,8 +21,13 @@ CASES = [
     ("config2", lambda: W.make(2), 64),
     ("config3", lambda: W.make(3), 64),
     ("config4", lambda: W.make(4), 64),
+    # six tetrahedra per cell on jittered vertices: seven edge families, the
+    # face diagonals of the cut planes among the interface edges
+    ("tet-2x2x2", lambda: W.tetrahedral(W.tiny(4, 4, 4, 2, 2, 2, seed=1), 0.1, seed=2), 16),
+    ("tet-jitter", lambda: W.tetrahedral(W.tiny(7, 6, 5, 3, 2, 2, seed=4, jitter=True), 0.1), 24),
+    ("tet-config3", lambda: W.tetrahedral(W.make(3), 0.1), 64),
 ]
-LARGE = {"config2", "config3", "config4"}
+LARGE = {"config2", "config3", "config4", "tet-config3"}
 
 
 def _pec_case():
@@ -84,13 +89,44 @@ def test_setup_rejects_bad_input():
     assert e.value.code == d3m.D3M_EINVAL
 
 
-def test_rhs_planewave_matches_oracle():
+@pytest.mark.parametrize("tet", [False, True])
+def test_rhs_planewave_matches_oracle(tet):
     from oracle import fem
     w = W.tiny(5, 4, 3, 1, 1, 1, seed=8, nrhs=3)
+    if tet:
+        w = W.tetrahedral(w, 0.1)
     s = d3m.Solver.from_workload(w)
+    assert s.n_edges == w.n_edges
     f = s.rhs_planewave(w.khat_pol6())
     fo = fem.rhs_planewave(w)
     assert np.abs(f - fo).max() < 1e-13 * np.abs(fo).max()
+
+
+def _tet_vertices(w, move):
+    v = W.lattice_vertices(w)
+    for node, delta in move:
+        v[node] += delta
+    return v
+
+
+@pytest.mark.parametrize("what", ["inverted", "off-plane", "brick-with-vertices", "element"])
+def test_setup_rejects_bad_tetrahedral_meshes(what):
+    """Inverted tetrahedra, boundary vertices moved off their plane, vertex
+    positions with bricks and unknown element kinds are refused at set-up."""
+    w = W.tiny(3, 3, 3, 1, 1, 1, seed=1)
+    n = lambda i, j, k: i + 4 * (j + 4 * k)
+    kw = dict(element=d3m.TET)
+    if what == "inverted":      # interior node pushed through its neighbour
+        kw["vertices"] = _tet_vertices(w, [(n(1, 1, 1), np.array([0.15, 0.15, 0.15]))])
+    elif what == "off-plane":   # a node of the face x = 0 moved in x
+        kw["vertices"] = _tet_vertices(w, [(n(0, 1, 1), np.array([0.01, 0.0, 0.0]))])
+    elif what == "brick-with-vertices":
+        kw = dict(element=d3m.BRICK, vertices=W.lattice_vertices(w))
+    else:
+        kw = dict(element=7)
+    with pytest.raises(d3m.D3MError) as ei:
+        d3m.Solver.from_workload(w, **kw)
+    assert ei.value.code == d3m.D3M_EINVAL and "d3m_setup" in str(ei.value)
 
 
 def test_level_table_matches_tree_heights():
@@ -135,12 +171,17 @@ def test_setup_rejects_bad_options(kw):
     assert "d3m_setup" in str(ei.value)
 
 
-def test_interface_coefficient_matches_oracle_entries():
+@pytest.mark.parametrize("tet", [False, True])
+def test_interface_coefficient_matches_oracle_entries(tet):
     """d3m_options.alpha sets the interface loss/gain term: the library's
     assembled entries of M equal the oracle's subdomain matrices for a
-    non-default alpha (same check as for the default, row by row)."""
+    non-default alpha (same check as for the default, row by row); on
+    tetrahedra the element and face matrices are the library's closed forms
+    against the oracle's quadrature."""
     from oracle import decomp
     w = W.tiny(4, 3, 3, 2, 1, 1, seed=6)
+    if tet:
+        w = W.tetrahedral(W.tiny(4, 3, 3, 2, 2, 1, seed=6), 0.1)
     w.alpha = 2.5 - 0.7j
     s = d3m.Solver.from_workload(w)
     ent = s.structure(d3m.M_ENTRIES)
@@ -156,12 +197,15 @@ def test_interface_coefficient_matches_oracle_entries():
             assert abs(A[loc[er], loc[ec]] - (re + 1j * im)) < 1e-12 * np.abs(A).max()
 
 
-def test_mass_weighted_multiplier_map_matches_oracle_entries():
+@pytest.mark.parametrize("tet", [False, True])
+def test_mass_weighted_multiplier_map_matches_oracle_entries(tet):
     """d3m_options.lm_weight = 1: the library's multiplier couplings (rows of
     lambda, columns of the subdomain copies) equal the oracle's D_i = D_bool,i
     T_lambda entry for entry, on a partition with cross-lines."""
     from oracle import decomp
     w = W.tiny(6, 6, 4, 2, 2, 1, seed=4)
+    if tet:
+        w = W.tetrahedral(w, 0.1)
     w.lm_weight = 1
     s = d3m.Solver.from_workload(w)
     ent = s.structure(d3m.M_ENTRIES)
