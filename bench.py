@@ -418,7 +418,9 @@ def precision_summary(r, peaks, prec_tag, config, nrhs):
 def bench_config(w, config, arena_bytes):
     """The `config` object of the JSON line (the same for both arms);
     arena_bytes = 8 sum m^2 over the fronts (complex64 front storage)."""
-    return {"workload": (f"config{config}: {w.nx}x{w.ny}x{w.nz} bricks ({w.n_edges} edges), "
+    cells = ("bricks" if getattr(w, "element", "brick") == "brick"
+             else "cells x 6 jittered tetrahedra")
+    return {"workload": (f"config{config}: {w.nx}x{w.ny}x{w.nz} {cells} ({w.n_edges} edges), "
                          f"{w.lx:g}x{w.ly:g}x{w.lz:g} wavelengths, {'x'.join(map(str, w.partition))} subdomains "
                          f"(cuts {[int(v) for v in w.cx]}/{[int(v) for v in w.cy]}/{[int(v) for v in w.cz]}), "
                          f"{w.nrhs} plane waves"),
@@ -452,12 +454,16 @@ def main():
     ap.add_argument("--autotune-cache", default=None,
                     help="file prefix for the tuned factor schedules (read when they match, else written); "
                          "lets a profiler run reuse the schedule of a plain run")
+    ap.add_argument("--element", default="brick", choices=["brick", "tet"],
+                    help="tet: the same workload on six jittered tetrahedra per cell")
     args = ap.parse_args()
     ws, rank, local = _dist()
     from paper_2002_05018_gb300 import workloads as W
     w = W.make(args.config)
     if args.nrhs > 0:
         w = W.with_waves(w, args.nrhs, seed=args.config)
+    if args.element == "tet":
+        w = W.tetrahedral(w, 0.1)
     if args.impl == "reference":
         # the reference arm is the CPU oracle (no GPU, no library): rank 0 only
         if rank != 0:
