@@ -82,6 +82,9 @@ def box_edges(g: fem.Grid, lo, hi):
 
 
 def decompose(w, with_matrices=True) -> Decomposition:
+    if getattr(w, "element", "brick") == "mesh":
+        from . import tetmesh
+        return tetmesh.decompose(w, with_matrices)
     g = fem.Grid.of(w)
     cuts = (np.asarray(w.cx), np.asarray(w.cy), np.asarray(w.cz))
     parts = tuple(len(c) - 1 for c in cuts)

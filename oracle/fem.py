@@ -500,6 +500,9 @@ def abc_faces(g: Grid, k, cells_lo=(0, 0, 0), cells_hi=None):
 
 def global_matrix(w):
     """Sparse CSR A (all edges, PEC rows not yet removed)."""
+    if getattr(w, "element", "brick") == "mesh":
+        from . import tetmesh
+        return tetmesh.global_matrix(w)
     g = Grid.of(w)
     r, c, v = assemble(g, w.eps, w.k, extra_faces=abc_faces(g, w.k))
     return sp.csr_matrix((v, (r, c)), shape=(g.n_edges, g.n_edges))
@@ -507,6 +510,9 @@ def global_matrix(w):
 
 def free_edges(w):
     """Indices of edges that carry a dof (PEC edges removed)."""
+    if getattr(w, "element", "brick") == "mesh":
+        from . import tetmesh
+        return tetmesh.free_edges(w)
     n = Grid.of(w).n_edges
     if w.pec_edge is None:
         return np.arange(n)
@@ -528,6 +534,9 @@ def rhs_planewave(w, which=None):
     """f (n_edges, nrhs): f_v = -sum_faces int U . N_v dS; bricks: 3x3
     Gauss-Legendre per outer-boundary face; tets: the 7-point rule per
     boundary triangle."""
+    if getattr(w, "element", "brick") == "mesh":
+        from . import tetmesh
+        return tetmesh.rhs_planewave(w, which)
     g = Grid.of(w)
     which = range(w.nrhs) if which is None else which
     which = list(which)
@@ -583,6 +592,9 @@ def _rhs_planewave_tet(w, g: Grid, which):
 def edge_interpolant(w, khat, pol):
     """Line averages of E_inc . t along every edge (the exact dof of E_inc),
     computed by 4-point Gauss-Legendre along the edge."""
+    if getattr(w, "element", "brick") == "mesh":
+        from . import tetmesh
+        return tetmesh.edge_interpolant(w, khat, pol)
     g = Grid.of(w)
     q, wq = gauss01(4)
     out = np.zeros(g.n_edges, np.complex128)
@@ -622,6 +634,9 @@ def discrete_gradient(g: Grid):
 def solve_global(w, f=None):
     """Reference solution of the undecomposed system by sparse LU (SuperLU),
     PEC dofs fixed to zero.  Returns x (n_edges, nrhs)."""
+    if getattr(w, "element", "brick") == "mesh":
+        from . import tetmesh
+        return tetmesh.solve_global(w, f)
     import scipy.sparse.linalg as spla
     A = global_matrix(w)
     f = rhs_planewave(w) if f is None else f
@@ -635,6 +650,9 @@ def solve_global(w, f=None):
 def rel_residual(w, x, f):
     """||A x - f||_inf / ||f||_inf per column on the free dofs (Numerical
     Results section's accuracy measure; |z| is the modulus)."""
+    if getattr(w, "element", "brick") == "mesh":
+        from . import tetmesh
+        return tetmesh.rel_residual(w, x, f)
     A = global_matrix(w)
     keep = free_edges(w)
     r = A[keep][:, keep] @ x[keep] - f[keep]

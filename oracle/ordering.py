@@ -36,13 +36,17 @@ LEAF_MAX = 64
 
 
 def block_nested_dissection(parts, pairs):
-    """Order of the interface blocks (pairs (a, b), a < b) by block ND."""
+    """Order of the interface blocks (pairs (a, b), a < b) by block ND: the
+    separator of a box is every block of the box whose two subdomains lie on
+    opposite sides of its middle cut (on lattice meshes these are the face
+    neighbours across the cut; on general meshes a block may also join
+    subdomains that touch only along an edge or at a point)."""
     px, py, pz = parts
 
-    def sid(x, y, z):
-        return x + px * (y + py * z)
+    def pos(s):
+        return (s % px, (s // px) % py, s // (px * py))
 
-    def rec(lo, hi):
+    def rec(lo, hi, P):
         ext = [hi[a] - lo[a] for a in range(3)]
         if max(ext) <= 1:
             return []
@@ -50,20 +54,12 @@ def block_nested_dissection(parts, pairs):
         mid = lo[axis] + ext[axis] // 2
         lhi = list(hi); lhi[axis] = mid
         rlo = list(lo); rlo[axis] = mid
-        sep = []
-        ranges = [range(lo[a], hi[a]) for a in range(3)]
-        ranges[axis] = [mid - 1]
-        for z in ranges[2]:
-            for y in ranges[1]:
-                for x in ranges[0]:
-                    q = [x, y, z]
-                    q2 = list(q); q2[axis] += 1
-                    pr = (sid(*q), sid(*q2))
-                    if pr in pairs:
-                        sep.append(pr)
-        return rec(lo, lhi) + rec(rlo, hi) + sorted(sep)
+        left = [p for p in P if pos(p[0])[axis] < mid and pos(p[1])[axis] < mid]
+        right = [p for p in P if pos(p[0])[axis] >= mid and pos(p[1])[axis] >= mid]
+        sep = [p for p in P if p not in left and p not in right]
+        return rec(lo, lhi, left) + rec(rlo, hi, right) + sorted(sep)
 
-    order = rec([0, 0, 0], [px, py, pz])
+    order = rec([0, 0, 0], [px, py, pz], sorted(pairs))
     assert sorted(order) == sorted(pairs)
     return order
 
@@ -129,7 +125,11 @@ def build_plan(dec, leaf_max=LEAF_MAX):
     for sd in dec.subs:
         iface = set(int(e) for e, a, b in zip(dec.lm_edge, dec.lm_plus, dec.lm_minus)
                     if a == sd.index or b == sd.index)
-        for node in subdomain_nd(dec.grid, sd, iface, leaf_max):
+        if getattr(dec.grid, "element", "brick") == "mesh":
+            from .tetmesh import subdomain_nd as nd
+        else:
+            nd = subdomain_nd
+        for node in nd(dec.grid, sd, iface, leaf_max):
             starts.append(pos); pos += len(node); ends.append(pos)
             kinds.append(0); owners.append(sd.index)
             m_sub += [sd.index] * len(node); m_edge += list(node)

@@ -19,6 +19,10 @@ Random draws, in this order, from numpy.random.default_rng(seed): interior
 cut jitter (x cuts, then y, then z; integers in [-3, 3]), per-cell
 permittivities, plane-wave angles and polarisations, probe edges, FD cells.
 
+delaunay() makes an unstructured tetrahedral mesh of a box (general
+connectivity: vertex positions and vertex ids per tetrahedron), as_mesh()
+passes a lattice-tetrahedral workload in that general form.
+
 tetrahedral(w) turns any of them into a tetrahedral mesh of the same cells
 (the general FEM setting of the paper's Introduction): each cell is split into
 six tetrahedra along its (0,0,0)-(1,1,1) diagonal, and the lattice vertices
@@ -71,15 +75,21 @@ class Workload:
     seed: int = 0
     alpha: complex | None = None  # interface loss/gain coefficient (None: jk)
     lm_weight: int = 0            # multiplier map D: 0 signed Boolean, 1 tangential-face-mass weighted
-    element: str = "brick"        # "brick" or "tet" (six tetrahedra per cell)
-    vertices: np.ndarray | None = None  # (n_nodes, 3) float64 positions, x-fastest; None: lattice
+    element: str = "brick"        # "brick", "tet" (six tetrahedra per cell) or "mesh"
+    vertices: np.ndarray | None = None  # (n_nodes, 3) float64 positions (x-fastest for "tet"); None: lattice
+    tets: np.ndarray | None = None      # "mesh": (n_tets, 4) int64 vertex ids
+    gcuts: tuple | None = None          # "mesh": subdomain cut coordinates per axis (px+1, py+1, pz+1)
 
     @property
     def n_cells(self) -> int:
+        if self.element == "mesh":
+            return len(self.tets)
         return self.nx * self.ny * self.nz
 
     @property
     def n_edges(self) -> int:
+        if self.element == "mesh":
+            return len(mesh_edge_pairs(self.tets))
         return sum(family_sizes(self.nx, self.ny, self.nz, self.element))
 
     @property
@@ -92,6 +102,8 @@ class Workload:
 
     @property
     def partition(self) -> tuple[int, int, int]:
+        if self.element == "mesh":
+            return tuple(len(g) - 1 for g in self.gcuts)
         return len(self.cx) - 1, len(self.cy) - 1, len(self.cz) - 1
 
     def khat_pol6(self) -> np.ndarray:
@@ -257,6 +269,71 @@ def tetrahedral(w: Workload, jitter: float = 0.1, seed: int | None = None) -> Wo
     v = v + np.where(movable, d, 0.0)
     return dataclasses.replace(w, name=w.name + "-tet", element="tet", vertices=v, probes=None,
                                fd_cells=None)
+
+
+def mesh_edge_pairs(tets) -> np.ndarray:
+    """Distinct vertex pairs (i < j) of the tetrahedra, lexicographic: the
+    global edge numbering of a general mesh (edge (i, j) points from i to j)."""
+    t = np.asarray(tets, np.int64)
+    p = np.concatenate([np.sort(t[:, [a, b]], axis=1) for a, b in
+                        ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))])
+    return np.unique(p, axis=0)
+
+
+def as_mesh(w: Workload) -> Workload:
+    """A lattice-tetrahedral workload as a general mesh: the same vertices and
+    tetrahedra (cell by cell, the six of a cell in the order of the axis
+    permutations (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x)), the
+    cell's eps on each of its six, cut planes at the lattice cut coordinates."""
+    if w.element != "tet":
+        raise ValueError("as_mesh(): needs a lattice-tetrahedral workload")
+    v = lattice_vertices(w) if w.vertices is None else np.asarray(w.vertices, np.float64)
+    nid = lambda i, j, k: i + (w.nx + 1) * (j + (w.ny + 1) * k)
+    kk, jj, ii = np.meshgrid(np.arange(w.nz), np.arange(w.ny), np.arange(w.nx), indexing="ij")
+    ci, cj, ck = ii.ravel(), jj.ravel(), kk.ravel()
+    perms = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+    tets = np.zeros((len(ci), 6, 4), np.int64)
+    for t, perm in enumerate(perms):
+        o = np.zeros(3, np.int64)
+        tets[:, t, 0] = nid(ci, cj, ck)
+        for q, ax in enumerate(perm):
+            o[ax] = 1
+            tets[:, t, q + 1] = nid(ci + o[0], cj + o[1], ck + o[2])
+    h = (w.lx / w.nx, w.ly / w.ny, w.lz / w.nz)
+    gcuts = tuple(np.asarray(c, np.float64) * hh for c, hh in zip((w.cx, w.cy, w.cz), h))
+    return dataclasses.replace(w, name=w.name + "-mesh", element="mesh", vertices=v,
+                               tets=tets.reshape(-1, 4), eps=np.repeat(w.eps, 6), gcuts=gcuts)
+
+
+def delaunay(nx, ny, nz, px, py, pz, seed=0, nrhs=1, h=0.1, jitter=0.3, lossy=True) -> Workload:
+    """An unstructured tetrahedral mesh of the box [0, nx h] x [0, ny h] x
+    [0, nz h]: the Delaunay tetrahedralisation (scipy.spatial.Delaunay) of
+    the lattice points moved by a seeded uniform jitter of up to jitter*h per
+    axis (boundary points only within their boundary planes, box edges along
+    the edge, corners fixed); per-tetrahedron eps ~ U[1, 3] (lossy: times
+    1 - 0.05j); px x py x pz subdomains cut at equal coordinates; random plane
+    waves.  Draw order: jitter, eps, waves."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    kk, jj, ii = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    idx = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1)
+    n = np.array([nx, ny, nz])
+    movable = (idx > 0) & (idx < n[None, :])
+    pts = idx * h + np.where(movable, rng.uniform(-jitter, jitter, idx.shape) * h, 0.0)
+    tets = Delaunay(pts).simplices.astype(np.int64)
+    e = [pts[tets[:, q]] - pts[tets[:, 0]] for q in (1, 2, 3)]
+    vol = np.abs(np.einsum("ij,ij->i", e[0], np.cross(e[1], e[2]))) / 6.0
+    if vol.min() < 1e-6 * h ** 3:
+        raise ValueError("delaunay(): degenerate tetrahedron")
+    eps = rng.uniform(1.0, 3.0, len(tets)).astype(np.complex128)
+    if lossy:
+        eps = eps * (1.0 - 0.05j)
+    khat, pol = _random_waves(rng, nrhs)
+    L = (nx * h, ny * h, nz * h)
+    gcuts = tuple(np.linspace(0.0, L[a], p + 1) for a, p in enumerate((px, py, pz)))
+    empty = np.zeros(1, np.int32)
+    return Workload(f"delaunay{nx}x{ny}x{nz}", nx, ny, nz, *L, K0, eps, None, empty, empty, empty,
+                    khat, pol, seed=seed, element="mesh", vertices=pts, tets=tets, gcuts=gcuts)
 
 
 def tiny(nx, ny, nz, px, py, pz, seed=0, lossy=True, nrhs=1, pec=None, jitter=False,

@@ -1,0 +1,164 @@
+"""Pins of the oracle's general tetrahedral meshes (oracle/tetmesh.py): the
+lattice-tetrahedral path and the general-mesh path are two independent
+numberings and assemblies of the same discretisation; the Whitney energy
+identities hold on an unstructured (Delaunay) mesh; D3M is exact there too,
+including multiplier blocks between subdomains that touch only along an edge."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import adjoint, d3m, decomp, fem, ordering, tetmesh
+from paper_2002_05018_gb300 import workloads as W
+
+
+def _lattice_ids(wt, wm):
+    g = fem.Grid.of(wt)
+    s0, s1 = g.edge_nodes()
+    gm = tetmesh.grid_of(wm)
+    ids = gm.edge_id(np.minimum(s0, s1), np.maximum(s0, s1))
+    assert np.array_equal(gm.edges[ids], np.stack([s0, s1], 1))   # same orientation too
+    return ids
+
+
+def test_lattice_mesh_equals_lattice_path():
+    wt = W.tetrahedral(W.tiny(4, 3, 3, 2, 2, 1, seed=1, nrhs=2), 0.1)
+    wm = W.as_mesh(wt)
+    ids = _lattice_ids(wt, wm)
+    assert wm.n_edges == wt.n_edges and len(np.unique(ids)) == len(ids)
+    At, Am = fem.global_matrix(wt), fem.global_matrix(wm)
+    assert abs(Am[ids][:, ids] - At).max() < 1e-13 * abs(At).max()
+    ft, fm = fem.rhs_planewave(wt), fem.rhs_planewave(wm)
+    assert np.abs(fm[ids] - ft).max() < 1e-13 * np.abs(ft).max()
+    xt, xm = fem.solve_global(wt, ft), fem.solve_global(wm, fm)
+    assert np.abs(xm[ids] - xt).max() < 1e-12 * np.abs(xt).max()
+    # decomposed: the same multipliers (same blocks, the same edges in each;
+    # inside a block they follow each numbering's own edge order)
+    dt, dm = decomp.decompose(wt, False), decomp.decompose(wm, False)
+    assert dt.blocks == dm.blocks
+    for lt, lm in zip(dt.block_lms, dm.block_lms):
+        assert np.array_equal(np.sort(ids[dt.lm_edge[lt]]), dm.lm_edge[lm])
+
+
+def _delaunay(**kw):
+    args = dict(nx=5, ny=4, nz=4, px=2, py=2, pz=2, seed=3, nrhs=2)
+    args.update(kw)
+    return W.delaunay(**args)
+
+
+def _tangents(g):
+    t = g.V[g.edges[:, 1]] - g.V[g.edges[:, 0]]
+    return t / np.linalg.norm(t, axis=1)[:, None], 0.5 * (g.V[g.edges[:, 0]] + g.V[g.edges[:, 1]])
+
+
+def test_energy_identities_on_an_unstructured_mesh():
+    w = _delaunay()
+    g = tetmesh.grid_of(w)
+    V = w.lx * w.ly * w.lz
+    X = g.V[g.T]
+    vol = np.abs(np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]))) / 6
+    assert np.isclose(vol.sum(), V, rtol=1e-12)
+    S, M = tetmesh.mass_stiffness(g)
+    G = sp.diags(1.0 / tetmesh.edge_lengths(g)) @ tetmesh.discrete_gradient(g)
+    assert abs(S @ G).max() < 1e-12 * abs(S).max()
+    t, mid = _tangents(g)
+    E0 = np.array([0.3, -0.7, 0.5])
+    x = t @ E0
+    assert np.isclose(x @ M @ x, V * E0 @ E0, rtol=1e-12)
+    B, r0 = np.array([0.2, 0.5, -0.4]), np.array([0.1, 0.2, 0.3])
+    xl = np.sum(np.cross(B, mid - r0) * t, 1)
+    assert np.isclose(xl @ S @ xl, V * 4.0 * B @ B, rtol=1e-11)
+    # boundary face mass of a constant field: sum of area |E0_t|^2 over the box faces
+    bf = tetmesh.boundary_faces(g)
+    r, c, v = tetmesh.assemble(g, w.eps, 0.0, tets=np.zeros(0, np.int64), faces=[(bf, 1.0)])
+    T = sp.csr_matrix((v.real, (r, c)), shape=(g.n_edges, g.n_edges))
+    lx, ly, lz = w.lx, w.ly, w.lz
+    exact = 2.0 * (ly * lz * (E0[1] ** 2 + E0[2] ** 2) + lx * lz * (E0[0] ** 2 + E0[2] ** 2)
+                   + lx * ly * (E0[0] ** 2 + E0[1] ** 2))
+    assert np.isclose(x @ T @ x, exact, rtol=1e-12)
+    # outward normals of the box faces are the axis directions
+    n = tetmesh.outward_normals(g, bf)
+    assert np.allclose(np.sort(np.abs(n), axis=1)[:, :2], 0.0, atol=1e-12)
+
+
+def test_planewave_convergence_on_delaunay_meshes():
+    errs = []
+    for n in (3, 6):
+        w = W.delaunay(n, n, n, 1, 1, 1, seed=4, lossy=False, h=1.0 / n)
+        w.eps[:] = 1.0
+        f = fem.rhs_planewave(w)
+        x = fem.solve_global(w, f)[:, 0]
+        xi = fem.edge_interpolant(w, w.khat[0], w.pol[0])
+        errs.append(np.linalg.norm(x - xi) / np.linalg.norm(xi))
+    assert errs[0] < 0.5 and errs[1] < errs[0] / 2.0
+
+
+def test_reciprocity_and_symmetry():
+    w = _delaunay(px=1, py=1, pz=1)
+    A = fem.global_matrix(w)
+    assert abs(A - A.T).max() < 1e-14 * abs(A).max()
+    f = fem.rhs_planewave(w)
+    x = fem.solve_global(w, f)
+    assert abs(x[:, 0] @ f[:, 1] - x[:, 1] @ f[:, 0]) < 1e-10 * abs(x[:, 0] @ f[:, 1])
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(nx=6, ny=5, nz=4, px=3, py=2, pz=1, seed=5)])
+def test_decomposed_equals_global_on_delaunay_meshes(kw):
+    w = _delaunay(**kw)
+    f = fem.rhs_planewave(w)
+    r = d3m.solve(w, f, return_all=True)
+    xg = fem.solve_global(w, f)
+    assert np.abs(r["x"] - xg).max() < 1e-10 * np.abs(xg).max()
+    assert r["copy_mismatch"] < 1e-10 * np.abs(xg).max()
+    xs = d3m.solve_primal_schur(w, f)
+    assert np.abs(xs - xg).max() < 1e-10 * np.abs(xg).max()
+
+
+def test_jagged_interfaces_tie_non_neighbour_copies():
+    """On a Delaunay mesh some edge is shared by two subdomains that are not
+    face neighbours in the grid (the fallback of the multiplier rule), and
+    the block order still lists every block once."""
+    w = _delaunay()
+    dec = decomp.decompose(w, False)
+    assert any(not decomp.face_adjacent(a, b, dec.parts) for a, b in dec.blocks)
+    assert sorted(dec.blocks) == sorted(set(dec.blocks))
+
+
+def test_mesh_nested_dissection_is_a_partition_with_separators():
+    w = _delaunay(nx=6, ny=6, nz=5, px=2, py=1, pz=1)
+    dec = decomp.decompose(w)
+    plan = ordering.build_plan(dec, leaf_max=24)
+    keys = set(zip(plan.m_sub.tolist(), plan.m_edge.tolist()))
+    assert len(keys) == plan.n == sum(len(s.edges) for s in dec.subs) + len(dec.lm_edge)
+    r, c = ordering.saddle_pattern(dec, plan)
+    ordering.symbolic(plan, r, c)
+    sn_of = np.repeat(np.arange(len(plan.sn_start)), plan.sn_end - plan.sn_start)
+    a, b = sn_of[r], sn_of[c]
+    leaf = np.zeros(len(plan.sn_start), bool)
+    leaf[plan.sn_kind == 0] = True
+    leaf[plan.parent[plan.parent >= 0]] = False
+    assert leaf.sum() > 4
+    assert not (leaf[a] & leaf[b] & (a != b)).any()
+    ids = np.arange(len(plan.parent))
+    assert np.all((plan.parent > ids) | (plan.parent == -1))
+
+
+def test_adjoint_matches_central_differences():
+    w = _delaunay(nx=3, ny=3, nz=2, px=1, py=1, pz=1, seed=21)
+    f = fem.rhs_planewave(w)
+    rng = np.random.default_rng(0)
+    probes = np.sort(rng.choice(w.n_edges, 6, replace=False))
+    J, g = adjoint.gradient(w, f, probes)
+    assert g.shape == (w.n_cells,)
+    h = 1e-6
+    for c in rng.choice(w.n_cells, 5, replace=False):
+        e0 = w.eps.copy()
+        w.eps = e0.copy(); w.eps[c] += h
+        Jp = adjoint.objective(fem.solve_global(w, f), probes)
+        w.eps = e0.copy(); w.eps[c] -= h
+        Jm = adjoint.objective(fem.solve_global(w, f), probes)
+        w.eps = e0
+        fd = (Jp - Jm) / (2 * h)
+        # 1e-5 relative, plus the rounding floor of a 1e-6 central difference
+        # (about 1e-16 J / 1e-6) relative to the largest gradient entry: the
+        # per-tetrahedron entries are small next to J
+        assert abs(fd - g[c]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max(), (c, fd, g[c], J)
