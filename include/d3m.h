@@ -71,11 +71,14 @@ typedef struct d3m_ctx d3m_ctx;
 
 enum d3m_element {
   D3M_BRICK = 0,      /* lowest-order Nedelec bricks on the axis-aligned grid */
-  D3M_TET = 1         /* lowest-order Nedelec (Whitney) tetrahedra, six per
+  D3M_TET = 1,        /* lowest-order Nedelec (Whitney) tetrahedra, six per
                          cell (the Introduction's general FEM setting) */
+  D3M_TET_MESH = 2    /* the same elements on a general tetrahedral mesh
+                         (vertex and tetrahedron lists, any connectivity) */
 };
 
-/* Mesh of [0,lx] x [0,ly] x [0,lz] with nx*ny*nz lattice cells.
+/* Mesh of [0,lx] x [0,ly] x [0,lz] with nx*ny*nz lattice cells, or (element
+ * D3M_TET_MESH) a general tetrahedral mesh.
  * element D3M_BRICK: axis-aligned bricks; vertices must be NULL.
  * element D3M_TET: every cell is split into six tetrahedra along its
  *   (0,0,0)-(1,1,1) diagonal (each cell face along its lowest-to-highest
@@ -90,12 +93,25 @@ enum d3m_element {
  * Global edge numbering: edge families one after another, each x-fastest
  * over its own box of start nodes (i, j, k); directions (1,0,0), (0,1,0),
  * (0,0,1), and for D3M_TET then (1,1,0), (1,0,1), (0,1,1), (1,1,1).  Every
- * edge points from its start node to start + direction. */
+ * edge points from its start node to start + direction.
+ * element D3M_TET_MESH: n_vertices positions in vertices (3 doubles each) and
+ *   n_tets tetrahedra in tets (4 vertex ids each, any orientation, nonzero
+ *   volume); nx..lz are not read.  Cells are the tetrahedra (eps_r has one
+ *   value per tetrahedron, d3m_grad_eps one entry per tetrahedron).  Edges
+ *   are the distinct vertex pairs (i < j) of the tetrahedra in lexicographic
+ *   order, each pointing from vertex i to vertex j; boundary triangles (faces
+ *   of one tetrahedron) carry the absorbing condition with their outward
+ *   normal.  Subdomains are set by the coordinate cuts gx, gy, gz of the
+ *   partition.  Both arrays are read during d3m_setup only. */
 typedef struct {
   int32_t nx, ny, nz;
   double lx, ly, lz;
   int32_t element;          /* d3m_element */
-  const double *vertices;   /* D3M_TET only; NULL: regular lattice */
+  const double *vertices;   /* D3M_TET: NULL (regular lattice) or the lattice nodes;
+                               D3M_TET_MESH: 3 * n_vertices doubles */
+  int64_t n_vertices;       /* D3M_TET_MESH only */
+  int64_t n_tets;           /* D3M_TET_MESH only */
+  const int64_t *tets;      /* D3M_TET_MESH only: 4 * n_tets vertex ids */
 } d3m_mesh;
 
 /* Materials.  eps_r: 2*n_cells doubles (re, im) per cell, time convention
@@ -109,10 +125,18 @@ typedef struct {
 
 /* Subdomain cuts: cx has px+1 strictly increasing cell indices from 0 to nx
  * (likewise cy, cz).  Edges on an interior cut plane are copied into every
- * subdomain containing them. */
+ * subdomain containing them.
+ * General meshes (D3M_TET_MESH) use gx, gy, gz instead: px+1 (py+1, pz+1)
+ * strictly increasing coordinates; a tetrahedron belongs to subdomain
+ * (ix, iy, iz) when its centroid ((v0 + v1) + v2) + v3 over 4 satisfies
+ * c_x >= gx[ix] (or ix = 0) and c_x < gx[ix+1] (or ix = px - 1), likewise in
+ * y and z.  An edge is copied into every subdomain holding one of its
+ * tetrahedra; an extra copy with no earlier copy in a grid-face-adjacent
+ * subdomain is tied by its multiplier to the lowest-index copy. */
 typedef struct {
   int32_t px, py, pz;
   const int32_t *cx, *cy, *cz;
+  const double *gx, *gy, *gz;  /* D3M_TET_MESH only */
 } d3m_partition;
 
 typedef struct {
@@ -186,7 +210,9 @@ typedef struct {
                            mass int_f N_m . N_l dS between the multipliers of one
                            interface block.  Symmetric positive definite per
                            block, so E does not change; lambda, K_D and K do
-                           (lambda_1 = T_lambda^{-1} lambda_0). */
+                           (lambda_1 = T_lambda^{-1} lambda_0).  Lattice meshes
+                           only (D3M_EINVAL with D3M_TET_MESH, where a block
+                           may join subdomains without a common face). */
 } d3m_options;
 /* d3m_setup returns D3M_EINVAL (and the context, for d3m_last_error) when an
  * option lies outside the values listed above. */

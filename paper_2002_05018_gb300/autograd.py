@@ -22,12 +22,12 @@ class D3MSolve(torch.autograd.Function):
         """eps_re: real float64 tensor (n_cells), the real part of eps_r (the
         imaginary part comes from geom['eps_im']); f: complex128 CUDA tensor
         (n_edges, nrhs); geom: dict(nx, ny, nz, lx, ly, lz, k, cx, cy, cz,
-        eps_im, pec, precision[, element, vertices])."""
+        eps_im, pec, precision[, element, vertices, tets, gcuts])."""
         eps = eps_re.detach().cpu().numpy() + 1j * np.asarray(geom.get("eps_im", 0.0))
         s = d3m.Solver(geom["nx"], geom["ny"], geom["nz"], geom["lx"], geom["ly"], geom["lz"], eps, geom["k"],
                        geom["cx"], geom["cy"], geom["cz"], pec=geom.get("pec"),
                        precision=geom.get("precision", d3m.FP64), element=geom.get("element", d3m.BRICK),
-                       vertices=geom.get("vertices"))
+                       vertices=geom.get("vertices"), tets=geom.get("tets"), gcuts=geom.get("gcuts"))
         s.factor()
         x, _ = s.solve(f)
         x = x.clone()
@@ -54,5 +54,6 @@ def solve(eps_re, f, geom):
 def geom_of(w, precision=d3m.FP64):
     return dict(nx=w.nx, ny=w.ny, nz=w.nz, lx=w.lx, ly=w.ly, lz=w.lz, k=w.k, cx=w.cx, cy=w.cy, cz=w.cz,
                 eps_im=np.asarray(w.eps).imag.copy(), pec=w.pec_edge, precision=precision,
-                element=d3m.TET if getattr(w, "element", "brick") == "tet" else d3m.BRICK,
-                vertices=getattr(w, "vertices", None))
+                element={"tet": d3m.TET, "mesh": d3m.TET_MESH}.get(getattr(w, "element", "brick"), d3m.BRICK),
+                vertices=getattr(w, "vertices", None), tets=getattr(w, "tets", None),
+                gcuts=getattr(w, "gcuts", None))

@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/d3m.h"
@@ -32,6 +33,13 @@ struct Plan {
   int64_t fam_off[8] = {0};           // first edge id of each family
   int64_t fam_n[7][3] = {};           // start-node box of each family
   std::vector<double> vert;           // tetrahedra: 3 doubles per node (empty: lattice)
+  int64_t n_cells = 0;                // lattice cells, or the tetrahedra of a general mesh
+  // ---- general tetrahedral meshes (D3M_TET_MESH)
+  std::vector<int64_t> tet_v;         // 4 vertex ids per tetrahedron
+  std::vector<int64_t> tet_e;         // 6 edge ids per tetrahedron (local pairs 01 02 03 12 13 23)
+  std::vector<int8_t> tet_s;          // 6 orientation signs per tetrahedron
+  std::vector<std::array<int64_t, 4>> bface;  // boundary triangles: sorted vertices + opposite vertex
+  std::vector<std::pair<int64_t, int64_t>> medge;  // vertex pair (i < j) of each edge
   double bS[12][12], bM[12][12], bT[6][12][12];  // brick element and face matrices
 
   // ---- decomposition
@@ -102,6 +110,9 @@ constexpr int MAX_CELL_NE = 19;
 int cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[MAX_CELL_NE]);
 int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][MAX_CELL_NE],
                   double M[MAX_CELL_NE][MAX_CELL_NE]);
+// Edges and mass matrix of cell c (any element kind; c = i + nx*(j + ny*k)
+// on lattices, the tetrahedron index on general meshes); returns the count.
+int cell_dofs_mass(const Plan &p, int64_t c, int64_t e[MAX_CELL_NE], double M[MAX_CELL_NE][MAX_CELL_NE]);
 int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb);
 
 // engine.cu

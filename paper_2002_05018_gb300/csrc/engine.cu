@@ -2208,7 +2208,8 @@ __global__ void k_grad_eps(int nx, int ny, int nz, double k2, ElemMass Me, const
   }
 }
 // The same gradient with per-cell edge lists and mass matrices (ne edges per
-// cell; the six Whitney tetrahedra of a cell have ne = 19).
+// cell: 19 for the six Whitney tetrahedra of a lattice cell, 6 for a
+// tetrahedron of a general mesh, its orientation signs inside the mass).
 __global__ void k_grad_eps_cells(int64_t ncell, int ne, const int64_t *__restrict__ cell_edge,
                                  const double *__restrict__ cell_mass, double k2, const double2 *__restrict__ x,
                                  int64_t ldx, const double2 *__restrict__ y, int64_t ldy, int r,
@@ -4350,19 +4351,17 @@ int dev_grad_eps(Ctx &c, const double *x, int64_t ldx, const double *y, int64_t 
   if (rc) return rc;
   const Plan &P = c.plan;
   cudaStream_t s = c.dev->stream;
-  const int64_t ncell = (int64_t)P.nx * P.ny * P.nz;
-  if (P.element == D3M_TET) {
+  const int64_t ncell = P.n_cells;
+  if (P.element != D3M_BRICK) {
     DeviceState *d = c.dev;
     if (!d->gc_edge) {
       const int ne = P.cell_ne;
       std::vector<int64_t> ce((size_t)ncell * ne);
       std::vector<double> cm((size_t)ncell * ne * ne);
-      double S[MAX_CELL_NE][MAX_CELL_NE], M[MAX_CELL_NE][MAX_CELL_NE];
+      double M[MAX_CELL_NE][MAX_CELL_NE];
       for (int64_t cc = 0; cc < ncell; ++cc) {
-        const int ci = (int)(cc % P.nx), cj = (int)((cc / P.nx) % P.ny), ck = (int)(cc / ((int64_t)P.nx * P.ny));
         int64_t e[MAX_CELL_NE];
-        cell_edges(P, ci, cj, ck, e);
-        cell_matrices(P, ci, cj, ck, S, M);
+        cell_dofs_mass(P, cc, e, M);
         for (int a = 0; a < ne; ++a) {
           ce[cc * ne + a] = e[a];
           for (int b = 0; b < ne; ++b) cm[(cc * ne + a) * ne + b] = M[a][b];

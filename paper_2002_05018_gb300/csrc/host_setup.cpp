@@ -236,6 +236,26 @@ static void cell_tet(const Plan &p, int ci, int cj, int ck, int t, int o[4][3], 
   for (int v = 0; v < 4; ++v) node_pos(p, ci + o[v][0], cj + o[v][1], ck + o[v][2], X[v]);
 }
 
+// Local S and M (6 x 6, edge pairs 01 02 03 12 13 23, each local function
+// pointing from its lower to its higher local vertex) of tetrahedron X.
+static void tet_local(const double X[4][3], double S[6][6], double M[6][6]) {
+  double g[4][3], ell[6], cu[6][3];
+  const double vol = std::fabs(tet_grads(X, g)) / 6.0;
+  for (int q = 0; q < 6; ++q) {
+    const int a = TET_E[q][0], b = TET_E[q][1];
+    double ev[3];
+    sub3(X[b], X[a], ev);
+    ell[q] = std::sqrt(dot3(ev, ev));
+    cross3(g[a], g[b], cu[q]);
+    for (int r = 0; r < 3; ++r) cu[q][r] *= 2.0 * ell[q];
+  }
+  for (int q = 0; q < 6; ++q)
+    for (int r = 0; r < 6; ++r) {
+      S[q][r] = vol * dot3(cu[q], cu[r]);
+      M[q][r] = vol / 20.0 * ell[q] * ell[r] * whitney_pair(g, TET_E[q][0], TET_E[q][1], TET_E[r][0], TET_E[r][1]);
+    }
+}
+
 // S = int curl N . curl N and M = int N . N of a cell, in cell_edges order.
 int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][MAX_CELL_NE],
                   double M[MAX_CELL_NE][MAX_CELL_NE]) {
@@ -251,29 +271,58 @@ int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][M
   std::memset(M, 0, sizeof(double) * MAX_CELL_NE * MAX_CELL_NE);
   for (int t = 0; t < 6; ++t) {
     int o[4][3];
-    double X[4][3], g[4][3];
+    double X[4][3], Sl[6][6], Ml[6][6];
     cell_tet(p, ci, cj, ck, t, o, X);
-    const double vol = std::fabs(tet_grads(X, g)) / 6.0;
+    tet_local(X, Sl, Ml);
     int loc[6];
-    double ell[6], cu[6][3];
     for (int q = 0; q < 6; ++q) {
       const int a = TET_E[q][0], b = TET_E[q][1];
       int d[3] = {o[b][0] - o[a][0], o[b][1] - o[a][1], o[b][2] - o[a][2]};
       loc[q] = local_edge(o[a], d);
-      double ev[3];
-      sub3(X[b], X[a], ev);
-      ell[q] = std::sqrt(dot3(ev, ev));
-      cross3(g[a], g[b], cu[q]);
-      for (int r = 0; r < 3; ++r) cu[q][r] *= 2.0 * ell[q];
     }
     for (int q = 0; q < 6; ++q)
       for (int r = 0; r < 6; ++r) {
-        S[loc[q]][loc[r]] += vol * dot3(cu[q], cu[r]);
-        M[loc[q]][loc[r]] += vol / 20.0 * ell[q] * ell[r] *
-                             whitney_pair(g, TET_E[q][0], TET_E[q][1], TET_E[r][0], TET_E[r][1]);
+        S[loc[q]][loc[r]] += Sl[q][r];
+        M[loc[q]][loc[r]] += Ml[q][r];
       }
   }
   return 19;
+}
+
+// Signed local matrices of tetrahedron t of a general mesh (global edge
+// orientation: from the lower to the higher vertex id).
+static void mesh_tet_matrices(const Plan &p, int64_t t, double S[6][6], double M[6][6]) {
+  double X[4][3];
+  for (int v = 0; v < 4; ++v) {
+    const double *x = p.vert.data() + 3 * p.tet_v[4 * t + v];
+    X[v][0] = x[0];
+    X[v][1] = x[1];
+    X[v][2] = x[2];
+  }
+  tet_local(X, S, M);
+  const int8_t *sg = p.tet_s.data() + 6 * t;
+  for (int q = 0; q < 6; ++q)
+    for (int r = 0; r < 6; ++r) {
+      const double s = (double)(sg[q] * sg[r]);
+      S[q][r] *= s;
+      M[q][r] *= s;
+    }
+}
+
+int cell_dofs_mass(const Plan &p, int64_t c, int64_t e[MAX_CELL_NE], double M[MAX_CELL_NE][MAX_CELL_NE]) {
+  if (p.element == D3M_TET_MESH) {
+    double S6[6][6], M6[6][6];
+    mesh_tet_matrices(p, c, S6, M6);
+    for (int q = 0; q < 6; ++q) {
+      e[q] = p.tet_e[6 * c + q];
+      for (int r = 0; r < 6; ++r) M[q][r] = M6[q][r];
+    }
+    return 6;
+  }
+  const int ci = (int)(c % p.nx), cj = (int)((c / p.nx) % p.ny), ck = (int)(c / ((int64_t)p.nx * p.ny));
+  double S[MAX_CELL_NE][MAX_CELL_NE];
+  cell_edges(p, ci, cj, ck, e);
+  return cell_matrices(p, ci, cj, ck, S, M);
 }
 
 // The two triangles of cell face {axis = side}, split along the diagonal
@@ -306,6 +355,20 @@ static double tri_grads(const double Q[3][3], double g[3][3]) {
     for (int q = 0; q < 3; ++q) g[i][q] /= twoA;
   }
   return 0.5 * twoA;
+}
+
+// Local tangential face mass (3 x 3, pairs 01 02 12) of triangle Q.
+static void tri_local(const double Q[3][3], double T[3][3]) {
+  double g[3][3], ell[3];
+  const double area = tri_grads(Q, g);
+  for (int q = 0; q < 3; ++q) {
+    double ev[3];
+    sub3(Q[TRI_E[q][1]], Q[TRI_E[q][0]], ev);
+    ell[q] = std::sqrt(dot3(ev, ev));
+  }
+  for (int q = 0; q < 3; ++q)
+    for (int r = 0; r < 3; ++r)
+      T[q][r] = area / 12.0 * ell[q] * ell[r] * whitney_pair(g, TRI_E[q][0], TRI_E[q][1], TRI_E[r][0], TRI_E[r][1]);
 }
 
 struct FaceTri {
@@ -368,33 +431,37 @@ static bool face_adj(const Plan &p, int a, int b) {
 }
 
 // ------------------------------------------------------------ orderings
-// Block nested dissection of the subdomain grid (main step 3 reading).
-static void block_nd(const Plan &p, const std::set<std::pair<int, int>> &pairs, int lo[3],
-                     int hi[3], std::vector<std::pair<int, int>> &out) {
+// Block nested dissection of the subdomain grid (main step 3 reading): split
+// the box at the middle cut of its longest axis (ties x < y < z); the
+// separator is every block of the box whose two subdomains lie on opposite
+// sides of the cut (face neighbours across it on lattice meshes; on general
+// meshes also subdomains meeting only along an edge or at a point); order =
+// left, right, separator sorted by (a, b).
+static void block_nd(const Plan &p, const std::vector<std::pair<int, int>> &pairs, const int lo[3],
+                     const int hi[3], std::vector<std::pair<int, int>> &out) {
   int ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
   int axis = 0;
   for (int q = 1; q < 3; ++q)
     if (ext[q] > ext[axis]) axis = q;
   if (ext[axis] <= 1) return;
-  int mid = lo[axis] + ext[axis] / 2;
-  std::vector<std::pair<int, int>> sep;
-  int r0[3] = {lo[0], lo[1], lo[2]}, r1[3] = {hi[0], hi[1], hi[2]};
-  r0[axis] = mid - 1;
-  r1[axis] = mid;
-  for (int z = r0[2]; z < r1[2]; ++z)
-    for (int y = r0[1]; y < r1[1]; ++y)
-      for (int x = r0[0]; x < r1[0]; ++x) {
-        int q[3] = {x, y, z};
-        int a = sub_id(p, q[0], q[1], q[2]);
-        q[axis] += 1;
-        int b = sub_id(p, q[0], q[1], q[2]);
-        if (pairs.count({a, b})) sep.push_back({a, b});
-      }
+  const int mid = lo[axis] + ext[axis] / 2;
+  std::vector<std::pair<int, int>> left, right, sep;
+  for (auto &ab : pairs) {
+    int pa[3], pb[3];
+    sub_pos(p, ab.first, pa);
+    sub_pos(p, ab.second, pb);
+    if (pa[axis] < mid && pb[axis] < mid)
+      left.push_back(ab);
+    else if (pa[axis] >= mid && pb[axis] >= mid)
+      right.push_back(ab);
+    else
+      sep.push_back(ab);
+  }
   int lhi[3] = {hi[0], hi[1], hi[2]}, rlo[3] = {lo[0], lo[1], lo[2]};
   lhi[axis] = mid;
   rlo[axis] = mid;
-  block_nd(p, pairs, lo, lhi, out);
-  block_nd(p, pairs, rlo, hi, out);
+  block_nd(p, left, lo, lhi, out);
+  block_nd(p, right, rlo, hi, out);
   std::sort(sep.begin(), sep.end());
   out.insert(out.end(), sep.begin(), sep.end());
 }
@@ -461,8 +528,420 @@ static int cell_interval(const std::vector<int> &cut, int64_t x) {
 }
 
 // ------------------------------------------------------------ build
+static int finish_plan(Ctx &ctx, std::vector<Trip> &trips, std::vector<Trip> &g);
+
+// ------------------------------------------------------------ general tetrahedral meshes
+static inline int64_t mesh_edge_id(const Plan &p, int64_t a, int64_t b) {
+  auto it = std::lower_bound(p.medge.begin(), p.medge.end(), std::make_pair(a, b));
+  return (it != p.medge.end() && it->first == a && it->second == b) ? (int64_t)(it - p.medge.begin()) : -1;
+}
+
+static inline void mesh_vertex(const Plan &p, int64_t v, double x[3]) {
+  x[0] = p.vert[3 * v];
+  x[1] = p.vert[3 * v + 1];
+  x[2] = p.vert[3 * v + 2];
+}
+
+// Centroid of tetrahedron t: ((v0 + v1) + v2) + v3 over 4.
+static void mesh_centroid(const Plan &p, int64_t t, double c[3]) {
+  for (int a = 0; a < 3; ++a) {
+    double s = p.vert[3 * p.tet_v[4 * t] + a];
+    s += p.vert[3 * p.tet_v[4 * t + 1] + a];
+    s += p.vert[3 * p.tet_v[4 * t + 2] + a];
+    s += p.vert[3 * p.tet_v[4 * t + 3] + a];
+    c[a] = s / 4.0;
+  }
+}
+
+// Face mass of a triangle with sorted vertices (every local edge along its
+// global orientation) and its three edge ids (pairs 01 02 12).
+static void mesh_face(const Plan &p, const int64_t v[3], double T[3][3], int64_t e[3]) {
+  double Q[3][3];
+  for (int w = 0; w < 3; ++w) mesh_vertex(p, v[w], Q[w]);
+  tri_local(Q, T);
+  for (int q = 0; q < 3; ++q) e[q] = mesh_edge_id(p, v[TRI_E[q][0]], v[TRI_E[q][1]]);
+}
+
+// Interior ordering of a subdomain of a general mesh: bisection of its
+// tetrahedra T at the middle of their centroids' bounding box along its
+// longest axis (ties x < y < z; left: centroid below the middle); the still
+// unassigned edges shared by both halves form the separator; left, right,
+// separator; a region of at most leaf_max unassigned edges, or one that does
+// not split, is a leaf.  Inside a node edges follow the global index.
+static void mesh_nd(const Plan &p, const std::vector<double> &cent, std::vector<char> &avail,
+                    const std::vector<int64_t> &T, int leaf_max, std::vector<std::vector<int64_t>> &nodes) {
+  auto edges_of = [&](const std::vector<int64_t> &TT, bool only_avail) {
+    std::vector<int64_t> E;
+    E.reserve(TT.size() * 6);
+    for (int64_t t : TT)
+      for (int q = 0; q < 6; ++q) {
+        const int64_t e = p.tet_e[6 * t + q];
+        if (!only_avail || avail[e]) E.push_back(e);
+      }
+    std::sort(E.begin(), E.end());
+    E.erase(std::unique(E.begin(), E.end()), E.end());
+    return E;
+  };
+  std::vector<int64_t> E = edges_of(T, true);
+  auto leaf = [&]() {
+    if (E.empty()) return;
+    for (int64_t e : E) avail[e] = 0;
+    nodes.push_back(std::move(E));
+  };
+  if ((int64_t)E.size() <= leaf_max || T.size() < 2) return leaf();
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) lo[a] = hi[a] = cent[3 * T[0] + a];
+  for (int64_t t : T)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], cent[3 * t + a]);
+      hi[a] = std::max(hi[a], cent[3 * t + a]);
+    }
+  const double ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+  int axis = 0;
+  for (int q = 1; q < 3; ++q)
+    if (ext[q] > ext[axis]) axis = q;
+  const double mid = (lo[axis] + hi[axis]) / 2.0;
+  std::vector<int64_t> L, R;
+  for (int64_t t : T) (cent[3 * t + axis] < mid ? L : R).push_back(t);
+  if (L.empty() || R.empty()) return leaf();
+  const std::vector<int64_t> EL = edges_of(L, false), ER = edges_of(R, false);
+  std::vector<int64_t> both, sep;
+  std::set_intersection(EL.begin(), EL.end(), ER.begin(), ER.end(), std::back_inserter(both));
+  for (int64_t e : both)
+    if (avail[e]) sep.push_back(e);
+  for (int64_t e : sep) avail[e] = 0;
+  mesh_nd(p, cent, avail, L, leaf_max, nodes);
+  mesh_nd(p, cent, avail, R, leaf_max, nodes);
+  if (!sep.empty()) nodes.push_back(std::move(sep));
+}
+
+// Front half of the plan for a general tetrahedral mesh: edges, faces,
+// subdomains by centroid, copies and multipliers, the ordering of M, its
+// entries and the global operator.
+static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double k,
+                           const d3m_partition *part) {
+  Plan &p = ctx.plan;
+  const int leaf_max = ctx.opt.leaf_max > 0 ? ctx.opt.leaf_max : 64;
+  p.k = k;
+  p.element = D3M_TET_MESH;
+  p.nfam = 0;
+  p.cell_ne = 6;
+  p.nx = p.ny = p.nz = 0;
+  const int64_t nv = mesh->n_vertices, nt = mesh->n_tets;
+  if (nv < 4 || nt < 1 || !mesh->vertices || !mesh->tets) {
+    ctx.err = "d3m_setup: a general mesh needs n_vertices >= 4, n_tets >= 1, vertices and tets";
+    return D3M_EINVAL;
+  }
+  if (ctx.opt.lm_weight != 0) {
+    ctx.err = "d3m_setup: lm_weight = 1 needs a lattice mesh";
+    return D3M_EINVAL;
+  }
+  p.vert.assign(mesh->vertices, mesh->vertices + 3 * nv);
+  for (double x : p.vert)
+    if (!std::isfinite(x)) {
+      ctx.err = "d3m_setup: non-finite vertex position";
+      return D3M_EINVAL;
+    }
+  p.tet_v.assign(mesh->tets, mesh->tets + 4 * nt);
+  p.n_cells = nt;
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t *v = p.tet_v.data() + 4 * t;
+    double X[4][3], g[4][3], lmax = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      if (v[a] < 0 || v[a] >= nv) {
+        ctx.err = "d3m_setup: tetrahedron vertex id out of range";
+        return D3M_EINVAL;
+      }
+      mesh_vertex(p, v[a], X[a]);
+    }
+    for (int q = 0; q < 6; ++q) {
+      double ev[3];
+      sub3(X[TET_E[q][1]], X[TET_E[q][0]], ev);
+      lmax = std::max(lmax, std::sqrt(dot3(ev, ev)));
+    }
+    const double det = tet_grads(X, g);
+    if (!(std::fabs(det) > 1e-12 * lmax * lmax * lmax)) {
+      ctx.err = "d3m_setup: a tetrahedron is degenerate";
+      return D3M_EINVAL;
+    }
+  }
+  // ---- edges: distinct vertex pairs, lexicographic
+  p.medge.clear();
+  p.medge.reserve(6 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int q = 0; q < 6; ++q) {
+      const int64_t a = p.tet_v[4 * t + TET_E[q][0]], b = p.tet_v[4 * t + TET_E[q][1]];
+      p.medge.push_back({std::min(a, b), std::max(a, b)});
+    }
+  std::sort(p.medge.begin(), p.medge.end());
+  p.medge.erase(std::unique(p.medge.begin(), p.medge.end()), p.medge.end());
+  p.n_edges = (int64_t)p.medge.size();
+  p.tet_e.resize(6 * nt);
+  p.tet_s.resize(6 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int q = 0; q < 6; ++q) {
+      const int64_t a = p.tet_v[4 * t + TET_E[q][0]], b = p.tet_v[4 * t + TET_E[q][1]];
+      p.tet_e[6 * t + q] = mesh_edge_id(p, std::min(a, b), std::max(a, b));
+      p.tet_s[6 * t + q] = a < b ? 1 : -1;
+    }
+  // ---- faces: boundary triangles (one tetrahedron) and shared ones (two)
+  struct FRec {
+    std::array<int64_t, 3> v;
+    int64_t t, opp;
+  };
+  std::vector<FRec> fr;
+  fr.reserve(4 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int q = 0; q < 4; ++q) {
+      std::array<int64_t, 3> v;
+      int w = 0;
+      for (int a = 0; a < 4; ++a)
+        if (a != q) v[w++] = p.tet_v[4 * t + a];
+      std::sort(v.begin(), v.end());
+      fr.push_back({v, t, p.tet_v[4 * t + q]});
+    }
+  std::sort(fr.begin(), fr.end(), [](const FRec &a, const FRec &b) { return a.v != b.v ? a.v < b.v : a.t < b.t; });
+  p.bface.clear();
+  std::vector<int64_t> bface_tet;
+  std::vector<std::array<int64_t, 5>> iface;  // sorted vertices, the two tetrahedra
+  for (size_t i = 0; i < fr.size();) {
+    size_t j = i;
+    while (j < fr.size() && fr[j].v == fr[i].v) ++j;
+    if (j - i == 1) {
+      p.bface.push_back({fr[i].v[0], fr[i].v[1], fr[i].v[2], fr[i].opp});
+      bface_tet.push_back(fr[i].t);
+    } else if (j - i == 2) {
+      iface.push_back({fr[i].v[0], fr[i].v[1], fr[i].v[2], fr[i].t, fr[i + 1].t});
+    } else {
+      ctx.err = "d3m_setup: a triangle is shared by more than two tetrahedra";
+      return D3M_EINVAL;
+    }
+    i = j;
+  }
+  // ---- materials
+  if (!mat || !mat->eps_r) {
+    ctx.err = "d3m_setup: eps_r is required";
+    return D3M_EINVAL;
+  }
+  p.eps.resize(nt);
+  for (int64_t t = 0; t < nt; ++t) p.eps[t] = cplx(mat->eps_r[2 * t], mat->eps_r[2 * t + 1]);
+  p.pec.assign(p.n_edges, 0);
+  if (mat->pec_edge)
+    for (int64_t e = 0; e < p.n_edges; ++e) p.pec[e] = mat->pec_edge[e] ? 1 : 0;
+  p.n_free = 0;
+  for (int64_t e = 0; e < p.n_edges; ++e) p.n_free += !p.pec[e];
+  // ---- subdomains: coordinate boxes, a tetrahedron goes where its centroid is
+  p.parts[0] = part->px;
+  p.parts[1] = part->py;
+  p.parts[2] = part->pz;
+  const double *gc[3] = {part->gx, part->gy, part->gz};
+  std::vector<double> gcut[3];
+  for (int a = 0; a < 3; ++a) {
+    if (p.parts[a] < 1 || !gc[a]) {
+      ctx.err = "d3m_setup: a general mesh needs partition counts >= 1 with coordinate cuts gx, gy, gz";
+      return D3M_EINVAL;
+    }
+    gcut[a].assign(gc[a], gc[a] + p.parts[a] + 1);
+    for (int q = 0; q < p.parts[a]; ++q)
+      if (!(gcut[a][q + 1] > gcut[a][q])) {
+        ctx.err = "d3m_setup: coordinate cuts must be strictly increasing";
+        return D3M_EINVAL;
+      }
+  }
+  p.nsub = p.parts[0] * p.parts[1] * p.parts[2];
+  std::vector<double> cent(3 * nt);
+  std::vector<int> tsub(nt);
+  std::vector<std::vector<int64_t>> sub_tets(p.nsub);
+  for (int64_t t = 0; t < nt; ++t) {
+    mesh_centroid(p, t, &cent[3 * t]);
+    int ix[3];
+    for (int a = 0; a < 3; ++a)
+      ix[a] = (int)(std::upper_bound(gcut[a].begin() + 1, gcut[a].end() - 1, cent[3 * t + a]) - (gcut[a].begin() + 1));
+    tsub[t] = sub_id(p, ix[0], ix[1], ix[2]);
+    sub_tets[tsub[t]].push_back(t);
+  }
+  p.sub_lo.assign(p.nsub, {0, 0, 0});
+  p.sub_hi.assign(p.nsub, {0, 0, 0});
+  p.sub_edges.assign(p.nsub, {});
+  for (int s = 0; s < p.nsub; ++s) {
+    auto &E = p.sub_edges[s];
+    for (int64_t t : sub_tets[s])
+      for (int q = 0; q < 6; ++q)
+        if (!p.pec[p.tet_e[6 * t + q]]) E.push_back(p.tet_e[6 * t + q]);
+    std::sort(E.begin(), E.end());
+    E.erase(std::unique(E.begin(), E.end()), E.end());
+  }
+  // ---- copies and multipliers
+  std::vector<std::vector<int>> copies(p.n_edges);
+  for (int s = 0; s < p.nsub; ++s)
+    for (int64_t e : p.sub_edges[s]) copies[e].push_back(s);
+  std::map<std::pair<int, int>, std::vector<int64_t>> pair_edges;
+  for (int64_t e = 0; e < p.n_edges; ++e) {
+    const auto &cs = copies[e];
+    for (size_t kk = 1; kk < cs.size(); ++kk) {
+      int sj = cs[0];
+      for (size_t j = 0; j < kk; ++j)
+        if (face_adj(p, cs[j], cs[kk])) {
+          sj = cs[j];
+          break;
+        }
+      pair_edges[{sj, cs[kk]}].push_back(e);
+    }
+  }
+  std::vector<std::pair<int, int>> pairs, border;
+  for (auto &kv : pair_edges) pairs.push_back(kv.first);
+  {
+    int lo[3] = {0, 0, 0}, hi[3] = {p.parts[0], p.parts[1], p.parts[2]};
+    block_nd(p, pairs, lo, hi, border);
+  }
+  p.lm_edge.clear();
+  p.lm_plus.clear();
+  p.lm_minus.clear();
+  p.blocks.clear();
+  for (auto &ab : border) {
+    auto &es = pair_edges[ab];
+    p.blocks.push_back({ab.first, ab.second, (int64_t)p.lm_edge.size()});
+    for (int64_t e : es) {
+      p.lm_edge.push_back(e);
+      p.lm_plus.push_back(ab.first);
+      p.lm_minus.push_back(ab.second);
+    }
+  }
+  const int64_t n_lm = (int64_t)p.lm_edge.size();
+  // ---- ordering of M and supernodes
+  p.m_sub.clear();
+  p.m_edge.clear();
+  p.sn_start.clear();
+  p.sn_end.clear();
+  p.sn_kind.clear();
+  p.sn_owner.clear();
+  auto push_node = [&](int s, const std::vector<int64_t> &nd, int kind, int64_t owner) {
+    p.sn_start.push_back((int64_t)p.m_sub.size());
+    for (int64_t e : nd) {
+      p.m_sub.push_back(s);
+      p.m_edge.push_back(e);
+    }
+    p.sn_end.push_back((int64_t)p.m_sub.size());
+    p.sn_kind.push_back(kind);
+    p.sn_owner.push_back(owner);
+  };
+  std::vector<char> avail(p.n_edges, 0);
+  std::vector<int64_t> sub_m0(p.nsub);
+  for (int s = 0; s < p.nsub; ++s) {
+    sub_m0[s] = (int64_t)p.m_sub.size();
+    for (int64_t e : p.sub_edges[s]) avail[e] = copies[e].size() < 2;
+    std::vector<std::vector<int64_t>> nodes;
+    mesh_nd(p, cent, avail, sub_tets[s], leaf_max, nodes);
+    for (auto &nd : nodes) push_node(s, nd, 0, s);
+    for (int64_t e : p.sub_edges[s]) avail[e] = 0;
+    std::vector<int64_t> B;
+    for (int64_t e : p.sub_edges[s])
+      if (copies[e].size() >= 2) B.push_back(e);
+    if (!B.empty()) push_node(s, B, 1, s);
+  }
+  p.lam_start = (int64_t)p.m_sub.size();
+  for (size_t b = 0; b < p.blocks.size(); ++b) {
+    const int64_t first = p.blocks[b][2], last = b + 1 < p.blocks.size() ? p.blocks[b + 1][2] : n_lm;
+    std::vector<int64_t> ls;
+    for (int64_t l = first; l < last; ++l) ls.push_back(l);
+    push_node(-1, ls, 2, (int64_t)b);
+  }
+  p.n_m = (int64_t)p.m_sub.size();
+  std::vector<int64_t> gm(p.n_edges, -1);
+  p.owner_m.assign(p.n_edges, -1);
+  for (int64_t v = 0; v < p.lam_start; ++v) {
+    const int64_t e = p.m_edge[v];
+    const int s = (int)p.m_sub[v];
+    if (!copies[e].empty() && copies[e][0] == s) p.owner_m[e] = v;
+  }
+  // ---- entries of M (lower triangle), per subdomain
+  const cplx jk(0.0, k);
+  const cplx alpha = (ctx.opt.alpha_re == 0.0 && ctx.opt.alpha_im == 0.0) ? jk
+                                                                         : cplx(ctx.opt.alpha_re, ctx.opt.alpha_im);
+  // faces of each subdomain: (face record, coefficient)
+  std::vector<std::vector<std::pair<std::array<int64_t, 3>, cplx>>> sub_faces(p.nsub);
+  for (size_t f = 0; f < p.bface.size(); ++f)
+    sub_faces[tsub[bface_tet[f]]].push_back({{p.bface[f][0], p.bface[f][1], p.bface[f][2]}, jk});
+  for (auto &f : iface) {
+    const int s0 = tsub[f[3]], s1 = tsub[f[4]];
+    if (s0 == s1) continue;
+    sub_faces[s0].push_back({{f[0], f[1], f[2]}, s1 > s0 ? alpha : -alpha});
+    sub_faces[s1].push_back({{f[0], f[1], f[2]}, s0 > s1 ? alpha : -alpha});
+  }
+  std::vector<Trip> trips;
+  for (int s = 0; s < p.nsub; ++s) {
+    const int64_t m0 = sub_m0[s];
+    const int64_t m1_ = s + 1 < p.nsub ? sub_m0[s + 1] : p.lam_start;
+    for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = v;
+    for (int64_t t : sub_tets[s]) {
+      double S6[6][6], M6[6][6];
+      mesh_tet_matrices(p, t, S6, M6);
+      const int64_t *e = p.tet_e.data() + 6 * t;
+      for (int a = 0; a < 6; ++a) {
+        const int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
+        if (ra < 0) continue;
+        for (int b = 0; b < 6; ++b) {
+          const int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
+          if (rb < 0 || ra < rb) continue;
+          const cplx v = S6[a][b] - k * k * p.eps[t] * M6[a][b];
+          if (v != cplx(0.0)) trips.push_back({ra, rb, v});
+        }
+      }
+    }
+    for (auto &fc : sub_faces[s]) {
+      double T3[3][3];
+      int64_t e[3];
+      mesh_face(p, fc.first.data(), T3, e);
+      for (int a = 0; a < 3; ++a) {
+        const int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
+        if (ra < 0) continue;
+        for (int b = 0; b < 3; ++b) {
+          const int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
+          if (rb < 0 || ra < rb || T3[a][b] == 0.0) continue;
+          trips.push_back({ra, rb, fc.second * T3[a][b]});
+        }
+      }
+    }
+    // multipliers: +1 on the lower-index copy, -1 on the other
+    for (int64_t l = 0; l < n_lm; ++l) {
+      if (p.lm_plus[l] == s) trips.push_back({p.lam_start + l, gm[p.lm_edge[l]], cplx(1.0, 0.0)});
+      if (p.lm_minus[l] == s) trips.push_back({p.lam_start + l, gm[p.lm_edge[l]], cplx(-1.0, 0.0)});
+    }
+    for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = -1;
+  }
+  // ---- global operator: every tetrahedron and the boundary triangles
+  std::vector<Trip> g;
+  g.reserve((size_t)nt * 36);
+  for (int64_t t = 0; t < nt; ++t) {
+    double S6[6][6], M6[6][6];
+    mesh_tet_matrices(p, t, S6, M6);
+    const int64_t *e = p.tet_e.data() + 6 * t;
+    for (int a = 0; a < 6; ++a) {
+      if (p.pec[e[a]]) continue;
+      for (int b = 0; b < 6; ++b) {
+        if (p.pec[e[b]]) continue;
+        const cplx v = S6[a][b] - k * k * p.eps[t] * M6[a][b];
+        if (v != cplx(0.0)) g.push_back({e[a], e[b], v});
+      }
+    }
+  }
+  for (auto &bf : p.bface) {
+    double T3[3][3];
+    int64_t e[3];
+    mesh_face(p, bf.data(), T3, e);
+    for (int a = 0; a < 3; ++a) {
+      if (p.pec[e[a]]) continue;
+      for (int b = 0; b < 3; ++b)
+        if (!p.pec[e[b]] && T3[a][b] != 0.0) g.push_back({e[a], e[b], jk * T3[a][b]});
+    }
+  }
+  return finish_plan(ctx, trips, g);
+}
+
+
 int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double k,
                const d3m_partition *part) {
+  if (mesh->element == D3M_TET_MESH) return build_plan_mesh(ctx, mesh, mat, k, part);
   Plan &p = ctx.plan;
   const int leaf_max = ctx.opt.leaf_max > 0 ? ctx.opt.leaf_max : 64;
   p.nx = mesh->nx;
@@ -502,6 +981,7 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   p.nez = p.fam_off[3] - p.fam_off[2];
   p.n_edges = p.fam_off[p.nfam];
   const int64_t ncell = (int64_t)p.nx * p.ny * p.nz;
+  p.n_cells = ncell;
   p.vert.clear();
   if (mesh->vertices) {
     const int64_t nn3 = 3 * (int64_t)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
@@ -638,8 +1118,8 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
       pair_edges[{sj, sk}].push_back(e);
     }
   }
-  std::set<std::pair<int, int>> pairs;
-  for (auto &kv : pair_edges) pairs.insert(kv.first);
+  std::vector<std::pair<int, int>> pairs;
+  for (auto &kv : pair_edges) pairs.push_back(kv.first);
   std::vector<std::pair<int, int>> border;
   {
     int lo[3] = {0, 0, 0}, hi[3] = {p.parts[0], p.parts[1], p.parts[2]};
@@ -714,10 +1194,6 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
     p.sn_owner.push_back((int64_t)b);
   }
   p.n_m = (int64_t)p.m_sub.size();
-  const int64_t nsn = (int64_t)p.sn_start.size();
-  std::vector<int64_t> sn_of(p.n_m);
-  for (int64_t s = 0; s < nsn; ++s)
-    for (int64_t v = p.sn_start[s]; v < p.sn_end[s]; ++v) sn_of[v] = s;
 
   // per subdomain: global edge -> M index (dense scratch reused)
   std::vector<int64_t> gm(p.n_edges, -1);
@@ -861,6 +1337,52 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
       for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = -1;
     }
   }
+  // ---- global operator A on free edges (all cells and the outer boundary),
+  // summed and stored as CSR by finish_plan
+  std::vector<Trip> g;
+  {
+    g.reserve((size_t)ncell * p.cell_ne * p.cell_ne);
+    static thread_local double Tb[6][MAX_CELL_NE][MAX_CELL_NE];
+    for (int ck = 0; ck < p.nz; ++ck)
+      for (int cj = 0; cj < p.ny; ++cj)
+        for (int ci = 0; ci < p.nx; ++ci) {
+          int64_t e[MAX_CELL_NE];
+          const int ne = cell_edges(p, ci, cj, ck, e);
+          cell_matrices(p, ci, cj, ck, Sc, Mc);
+          cplx eps = p.eps[ci + (int64_t)p.nx * (cj + (int64_t)p.ny * ck)];
+          int c3[3] = {ci, cj, ck};
+          bool bnd[6];
+          for (int axis = 0; axis < 3; ++axis) {
+            bnd[2 * axis] = c3[axis] == 0;
+            bnd[2 * axis + 1] = c3[axis] == nn[axis] - 1;
+            for (int side = 0; side < 2; ++side)
+              if (bnd[2 * axis + side]) cell_face_matrix(p, ci, cj, ck, axis, side, Tb[2 * axis + side]);
+          }
+          for (int a = 0; a < ne; ++a) {
+            if (p.pec[e[a]]) continue;
+            for (int b = 0; b < ne; ++b) {
+              if (p.pec[e[b]]) continue;
+              cplx v = Sc[a][b] - k * k * eps * Mc[a][b];
+              for (int f = 0; f < 6; ++f)
+                if (bnd[f]) v += jk * Tb[f][a][b];
+              if (v != cplx(0.0)) g.push_back({e[a], e[b], v});
+            }
+          }
+        }
+  }
+  return finish_plan(ctx, trips, g);
+}
+
+// Symbolic factorisation, assembly tree, arena layout and the entries of M
+// grouped by level (main step 4), from the entries of M (trips, lower
+// triangle, M indices) and the triplets of the global operator (g, global
+// edge ids); common to every element kind.
+static int finish_plan(Ctx &ctx, std::vector<Trip> &trips, std::vector<Trip> &g) {
+  Plan &p = ctx.plan;
+  const int64_t nsn = (int64_t)p.sn_start.size();
+  std::vector<int64_t> sn_of(p.n_m);
+  for (int64_t s = 0; s < nsn; ++s)
+    for (int64_t v = p.sn_start[s]; v < p.sn_end[s]; ++v) sn_of[v] = s;
   std::sort(trips.begin(), trips.end(), [](const Trip &a, const Trip &b) {
     return a.c != b.c ? a.c < b.c : a.r < b.r;
   });
@@ -1031,53 +1553,22 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   }
 
   // ---- global operator A on free edges (full CSR) for fp64 residuals
-  {
-    std::vector<Trip> g;
-    g.reserve((size_t)ncell * p.cell_ne * p.cell_ne);
-    static thread_local double Tb[6][MAX_CELL_NE][MAX_CELL_NE];
-    for (int ck = 0; ck < p.nz; ++ck)
-      for (int cj = 0; cj < p.ny; ++cj)
-        for (int ci = 0; ci < p.nx; ++ci) {
-          int64_t e[MAX_CELL_NE];
-          const int ne = cell_edges(p, ci, cj, ck, e);
-          cell_matrices(p, ci, cj, ck, Sc, Mc);
-          cplx eps = p.eps[ci + (int64_t)p.nx * (cj + (int64_t)p.ny * ck)];
-          int c3[3] = {ci, cj, ck};
-          bool bnd[6];
-          for (int axis = 0; axis < 3; ++axis) {
-            bnd[2 * axis] = c3[axis] == 0;
-            bnd[2 * axis + 1] = c3[axis] == nn[axis] - 1;
-            for (int side = 0; side < 2; ++side)
-              if (bnd[2 * axis + side]) cell_face_matrix(p, ci, cj, ck, axis, side, Tb[2 * axis + side]);
-          }
-          for (int a = 0; a < ne; ++a) {
-            if (p.pec[e[a]]) continue;
-            for (int b = 0; b < ne; ++b) {
-              if (p.pec[e[b]]) continue;
-              cplx v = Sc[a][b] - k * k * eps * Mc[a][b];
-              for (int f = 0; f < 6; ++f)
-                if (bnd[f]) v += jk * Tb[f][a][b];
-              if (v != cplx(0.0)) g.push_back({e[a], e[b], v});
-            }
-          }
-        }
-    std::sort(g.begin(), g.end(), [](const Trip &a, const Trip &b) {
-      return a.r != b.r ? a.r < b.r : a.c < b.c;
-    });
-    p.csr_ptr.assign(p.n_edges + 1, 0);
-    p.csr_col.clear();
-    p.csr_val.clear();
-    for (size_t i = 0; i < g.size();) {
-      size_t j = i;
-      cplx v = 0;
-      while (j < g.size() && g[j].r == g[i].r && g[j].c == g[i].c) v += g[j++].v;
-      p.csr_col.push_back((int32_t)g[i].c);
-      p.csr_val.push_back(v);
-      p.csr_ptr[g[i].r + 1]++;
-      i = j;
-    }
-    for (int64_t r = 0; r < p.n_edges; ++r) p.csr_ptr[r + 1] += p.csr_ptr[r];
+  std::sort(g.begin(), g.end(), [](const Trip &a, const Trip &b) {
+    return a.r != b.r ? a.r < b.r : a.c < b.c;
+  });
+  p.csr_ptr.assign(p.n_edges + 1, 0);
+  p.csr_col.clear();
+  p.csr_val.clear();
+  for (size_t i = 0; i < g.size();) {
+    size_t j = i;
+    cplx v = 0;
+    while (j < g.size() && g[j].r == g[i].r && g[j].c == g[i].c) v += g[j++].v;
+    p.csr_col.push_back((int32_t)g[i].c);
+    p.csr_val.push_back(v);
+    p.csr_ptr[g[i].r + 1]++;
+    i = j;
   }
+  for (int64_t r = 0; r < p.n_edges; ++r) p.csr_ptr[r + 1] += p.csr_ptr[r];
   return D3M_OK;
 }
 
@@ -1099,25 +1590,67 @@ static void incident_u(const Plan &p, const double *kp, const double xyz[3], con
   for (int a = 0; a < 3; ++a) U[a] = nxc[a] - J * p.k * (E[a] - nvec[a] * ndotE);
 }
 
-// Tetrahedral meshes: f_v = -int U . N_v dS over the outer-boundary triangles,
-// each by Radon's 7-point degree-5 rule (barycentric points (1/3,1/3,1/3) and
-// the permutations of (a, a, 1 - 2a), a = (6 -+ sqrt 15)/21; weights 9/40 and
-// (155 -+ sqrt 15)/1200 of the area).
-static int rhs_planewave_tet(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
+// Radon's 7-point degree-5 triangle rule: barycentric points (1/3,1/3,1/3)
+// and the permutations of (a, a, 1 - 2a), a = (6 -+ sqrt 15)/21; weights 9/40
+// and (155 -+ sqrt 15)/1200 of the area.
+struct TriRule {
+  double b[7][3], w[7];
+};
+static TriRule radon7() {
+  TriRule R;
   const double r15 = std::sqrt(15.0);
-  double qb[7][3], qw[7];
-  qb[0][0] = qb[0][1] = qb[0][2] = 1.0 / 3.0;
-  qw[0] = 9.0 / 40.0;
+  R.b[0][0] = R.b[0][1] = R.b[0][2] = 1.0 / 3.0;
+  R.w[0] = 9.0 / 40.0;
   for (int g = 0; g < 2; ++g) {
     const double a = g ? (6.0 + r15) / 21.0 : (6.0 - r15) / 21.0;
     const double wt = g ? (155.0 + r15) / 1200.0 : (155.0 - r15) / 1200.0;
     for (int r = 0; r < 3; ++r) {
-      double *b = qb[1 + 3 * g + r];
+      double *b = R.b[1 + 3 * g + r];
       b[0] = b[1] = b[2] = a;
       b[2 - r] = 1.0 - 2.0 * a;
-      qw[1 + 3 * g + r] = wt;
+      R.w[1 + 3 * g + r] = wt;
     }
   }
+  return R;
+}
+
+// f_v -= int U . N_v dS over triangle Q with outward normal nvec; eids: the
+// edges of the vertex pairs 01 02 12, each pointing from the lower to the
+// higher local vertex.
+static void rhs_triangle(const Plan &p, const TriRule &R, const double Q[3][3], const double nvec[3],
+                         const int64_t eids[3], const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
+  double g[3][3], ell[3];
+  const double area = tri_grads(Q, g);
+  for (int m = 0; m < 3; ++m) {
+    double ev[3];
+    sub3(Q[TRI_E[m][1]], Q[TRI_E[m][0]], ev);
+    ell[m] = std::sqrt(dot3(ev, ev));
+  }
+  for (int q = 0; q < 7; ++q) {
+    const double *mu = R.b[q];
+    double xyz[3], N[3][3];
+    for (int a = 0; a < 3; ++a) xyz[a] = mu[0] * Q[0][a] + mu[1] * Q[1][a] + mu[2] * Q[2][a];
+    for (int m = 0; m < 3; ++m) {
+      const int a = TRI_E[m][0], b = TRI_E[m][1];
+      for (int c = 0; c < 3; ++c) N[m][c] = ell[m] * (mu[a] * g[b][c] - mu[b] * g[a][c]);
+    }
+    const double w = R.w[q] * area;
+    for (int r = 0; r < nrhs; ++r) {
+      cplx U[3];
+      incident_u(p, khat_pol + 9 * r, xyz, nvec, U);
+      for (int m = 0; m < 3; ++m) {
+        const cplx dot = U[0] * N[m][0] + U[1] * N[m][1] + U[2] * N[m][2];
+        const int64_t idx = eids[m] + ldb * r;
+        rhs[2 * idx] -= w * dot.real();
+        rhs[2 * idx + 1] -= w * dot.imag();
+      }
+    }
+  }
+}
+
+// Lattice tetrahedra: the two triangles of every outer-boundary cell face.
+static int rhs_planewave_tet(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
+  const TriRule R = radon7();
   const int nn[3] = {p.nx, p.ny, p.nz};
   for (int axis = 0; axis < 3; ++axis)
     for (int side = 0; side < 2; ++side) {
@@ -1136,29 +1669,35 @@ static int rhs_planewave_tet(const Plan &p, const double *khat_pol, int nrhs, do
             for (int t = 0; t < 2; ++t) {
               FaceTri f;
               cell_face_tri(p, ci, cj, ck, o[t], f);
-              for (int q = 0; q < 7; ++q) {
-                const double *mu = qb[q];
-                double xyz[3], N[3][3];
-                for (int a = 0; a < 3; ++a) xyz[a] = mu[0] * f.Q[0][a] + mu[1] * f.Q[1][a] + mu[2] * f.Q[2][a];
-                for (int m = 0; m < 3; ++m) {
-                  const int a = TRI_E[m][0], b = TRI_E[m][1];
-                  for (int c = 0; c < 3; ++c) N[m][c] = f.ell[m] * (mu[a] * f.g[b][c] - mu[b] * f.g[a][c]);
-                }
-                const double w = qw[q] * f.area;
-                for (int r = 0; r < nrhs; ++r) {
-                  cplx U[3];
-                  incident_u(p, khat_pol + 9 * r, xyz, nvec, U);
-                  for (int m = 0; m < 3; ++m) {
-                    cplx dot = U[0] * N[m][0] + U[1] * N[m][1] + U[2] * N[m][2];
-                    int64_t idx = e[f.loc[m]] + ldb * r;
-                    rhs[2 * idx] -= w * dot.real();
-                    rhs[2 * idx + 1] -= w * dot.imag();
-                  }
-                }
-              }
+              const int64_t eids[3] = {e[f.loc[0]], e[f.loc[1]], e[f.loc[2]]};
+              rhs_triangle(p, R, f.Q, nvec, eids, khat_pol, nrhs, rhs, ldb);
             }
           }
     }
+  return D3M_OK;
+}
+
+// General meshes: every boundary triangle with the outward normal of its
+// tetrahedron.
+static int rhs_planewave_mesh(const Plan &p, const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
+  const TriRule R = radon7();
+  for (const auto &bf : p.bface) {
+    double Q[3][3], X[3], e1[3], e2[3], nvec[3];
+    for (int w = 0; w < 3; ++w) mesh_vertex(p, bf[w], Q[w]);
+    mesh_vertex(p, bf[3], X);
+    sub3(Q[1], Q[0], e1);
+    sub3(Q[2], Q[0], e2);
+    cross3(e1, e2, nvec);
+    const double len = std::sqrt(dot3(nvec, nvec));
+    for (int a = 0; a < 3; ++a) nvec[a] /= len;
+    double to_opp[3];
+    sub3(X, Q[0], to_opp);
+    if (dot3(nvec, to_opp) > 0)
+      for (int a = 0; a < 3; ++a) nvec[a] *= -1.0;
+    int64_t eids[3];
+    for (int m = 0; m < 3; ++m) eids[m] = mesh_edge_id(p, bf[TRI_E[m][0]], bf[TRI_E[m][1]]);
+    rhs_triangle(p, R, Q, nvec, eids, khat_pol, nrhs, rhs, ldb);
+  }
   return D3M_OK;
 }
 
@@ -1169,6 +1708,7 @@ int rhs_planewave(const Plan &p, const double *khat_pol, int nrhs, double *rhs, 
       rhs[2 * (e + ldb * r) + 1] = 0.0;
     }
   if (p.element == D3M_TET) return rhs_planewave_tet(p, khat_pol, nrhs, rhs, ldb);
+  if (p.element == D3M_TET_MESH) return rhs_planewave_mesh(p, khat_pol, nrhs, rhs, ldb);
   const double gq[3] = {0.5 - 0.5 * std::sqrt(0.6), 0.5, 0.5 + 0.5 * std::sqrt(0.6)};
   const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
   const int nn[3] = {p.nx, p.ny, p.nz};

@@ -24,13 +24,15 @@ _SYMBOLS = ["d3m_setup", "d3m_factor", "d3m_solve", "d3m_solve_host", "d3m_rhs_p
             "d3m_last_error", "d3m_free", "d3m_solve_adjoint", "d3m_grad_eps", "d3m_set_profile"]
 
 
-BRICK, TET = 0, 1
+BRICK, TET, TET_MESH = 0, 1, 2
 
 
 class Mesh(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
-                ("element", ctypes.c_int32), ("vertices", ctypes.POINTER(ctypes.c_double))]
+                ("element", ctypes.c_int32), ("vertices", ctypes.POINTER(ctypes.c_double)),
+                ("n_vertices", ctypes.c_int64), ("n_tets", ctypes.c_int64),
+                ("tets", ctypes.POINTER(ctypes.c_int64))]
 
 
 class Materials(ctypes.Structure):
@@ -40,7 +42,8 @@ class Materials(ctypes.Structure):
 class Partition(ctypes.Structure):
     _fields_ = [("px", ctypes.c_int32), ("py", ctypes.c_int32), ("pz", ctypes.c_int32),
                 ("cx", ctypes.POINTER(ctypes.c_int32)), ("cy", ctypes.POINTER(ctypes.c_int32)),
-                ("cz", ctypes.POINTER(ctypes.c_int32))]
+                ("cz", ctypes.POINTER(ctypes.c_int32)), ("gx", ctypes.POINTER(ctypes.c_double)),
+                ("gy", ctypes.POINTER(ctypes.c_double)), ("gz", ctypes.POINTER(ctypes.c_double))]
 
 
 class Options(ctypes.Structure):
@@ -145,18 +148,29 @@ class Solver:
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
                  update_kernel=0, autotune=0, autotune_cache=None, lookahead=0, refine_method=0,
                  gmres_restart=0, gmres_tol=0.0, alpha=None, solve_kernel=0, lm_weight=0, element=BRICK,
-                 vertices=None):
+                 vertices=None, tets=None, gcuts=None):
+        """Lattice meshes: nx..lz, cuts cx, cy, cz (cell indices).  General
+        tetrahedral meshes (element=TET_MESH): vertices (n, 3), tets (m, 4)
+        and gcuts = (gx, gy, gz) coordinate cuts; nx..lz and cx..cz unused."""
         self.lib = load()
-        self.n_cells = nx * ny * nz
         self._eps = np.ascontiguousarray(np.asarray(eps, np.complex128).view(np.float64))
         self._vert = None if vertices is None else np.ascontiguousarray(np.asarray(vertices, np.float64))
+        self._tets = None if tets is None else np.ascontiguousarray(np.asarray(tets, np.int64))
+        self.n_cells = len(self._tets) if element == TET_MESH else nx * ny * nz
+        self._gcuts = None if gcuts is None else [np.ascontiguousarray(np.asarray(g, np.float64)) for g in gcuts]
         self._cuts = [np.ascontiguousarray(np.asarray(c, np.int32)) for c in (cx, cy, cz)]
         self._pec = None if pec is None else np.ascontiguousarray(np.asarray(pec, np.uint8))
         mesh = Mesh(nx, ny, nz, lx, ly, lz, int(element),
-                    None if self._vert is None else _ptr(self._vert, ctypes.c_double))
+                    None if self._vert is None else _ptr(self._vert, ctypes.c_double),
+                    0 if self._vert is None else len(self._vert), 0 if self._tets is None else len(self._tets),
+                    None if self._tets is None else _ptr(self._tets, ctypes.c_int64))
         mat = Materials(_ptr(self._eps, ctypes.c_double),
                         None if self._pec is None else _ptr(self._pec, ctypes.c_uint8))
-        part = Partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, *[_ptr(c, ctypes.c_int32) for c in self._cuts])
+        if self._gcuts is not None:
+            part = Partition(*[len(g) - 1 for g in self._gcuts], *[_ptr(c, ctypes.c_int32) for c in self._cuts],
+                             *[_ptr(g, ctypes.c_double) for g in self._gcuts])
+        else:
+            part = Partition(len(cx) - 1, len(cy) - 1, len(cz) - 1, *[_ptr(c, ctypes.c_int32) for c in self._cuts])
         self.precision = precision
         self.stream = stream
         self._cache = None if autotune_cache is None else str(autotune_cache).encode()
@@ -176,8 +190,10 @@ class Solver:
     def from_workload(cls, w, precision=FP64, **kw):
         kw.setdefault("alpha", getattr(w, "alpha", None))
         kw.setdefault("lm_weight", getattr(w, "lm_weight", 0))
-        kw.setdefault("element", TET if getattr(w, "element", "brick") == "tet" else BRICK)
+        kw.setdefault("element", {"tet": TET, "mesh": TET_MESH}.get(getattr(w, "element", "brick"), BRICK))
         kw.setdefault("vertices", getattr(w, "vertices", None))
+        kw.setdefault("tets", getattr(w, "tets", None))
+        kw.setdefault("gcuts", getattr(w, "gcuts", None))
         return cls(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.eps, w.k, w.cx, w.cy, w.cz, pec=w.pec_edge,
                    precision=precision, **kw)
 

@@ -253,6 +253,45 @@ def test_tetrahedral_uneven_partition(precision):
     s.close()
 
 
+MESH = [
+    lambda: W.delaunay(5, 4, 4, 2, 2, 2, seed=3, nrhs=2),
+    lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6, nrhs=2),
+]
+
+
+@pytest.mark.parametrize("mk", MESH)
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_general_tetrahedral_meshes(mk, precision):
+    """Delaunay meshes (arbitrary connectivity, subdomains by centroid, blocks
+    between grid-diagonal subdomains): E against the oracle's global solve
+    element by element, lambda against the oracle's D3M multipliers."""
+    _need_gpu()
+    w = mk()
+    s, x, info, f = _solve_case(w, precision)
+    _check_tiny(w, x, f, precision)
+    ref = od3m.solve(w, f, return_all=True)
+    lam = s.lam(f.shape[1])
+    ltol = 1e-9 if precision == d3m.FP64 else 1e-4
+    assert np.abs(lam - ref["lam"]).max() < ltol * np.abs(ref["lam"]).max()
+    s.close()
+
+
+def test_lattice_mesh_through_the_general_path():
+    """A lattice-tetrahedral workload through D3M_TET and, as vertex and
+    tetrahedron lists, through D3M_TET_MESH: the same solution edge for edge
+    (different numberings, orderings and assemblies)."""
+    _need_gpu()
+    wt = W.tetrahedral(W.tiny(6, 5, 4, 2, 2, 1, seed=1, nrhs=2), 0.1)
+    wm = W.as_mesh(wt)
+    _, xt, _, ft = _solve_case(wt, d3m.FP64)
+    _, xm, _, fm = _solve_case(wm, d3m.FP64)
+    g = fem.Grid.of(wt)
+    s0, s1 = g.edge_nodes()
+    from oracle import tetmesh
+    ids = tetmesh.grid_of(wm).edge_id(s0, s1)
+    assert np.abs(xm[ids] - xt).max() < 1e-10 * np.abs(xt).max()
+
+
 def test_config3_fp64():
     _need_gpu()
     w = W.make(3)

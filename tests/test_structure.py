@@ -26,6 +26,12 @@ CASES = [
     ("tet-2x2x2", lambda: W.tetrahedral(W.tiny(4, 4, 4, 2, 2, 2, seed=1), 0.1, seed=2), 16),
     ("tet-jitter", lambda: W.tetrahedral(W.tiny(7, 6, 5, 3, 2, 2, seed=4, jitter=True), 0.1), 24),
     ("tet-config3", lambda: W.tetrahedral(W.make(3), 0.1), 64),
+    # general tetrahedral meshes: a lattice mesh passed as vertex and
+    # tetrahedron lists, and Delaunay meshes whose subdomains meet along
+    # jagged interfaces (blocks between grid-diagonal subdomains)
+    ("mesh-lattice", lambda: W.as_mesh(W.tetrahedral(W.tiny(6, 5, 4, 2, 2, 1, seed=1), 0.1)), 16),
+    ("delaunay-2x2x2", lambda: W.delaunay(5, 4, 4, 2, 2, 2, seed=3), 16),
+    ("delaunay-3x2x2", lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6), 32),
 ]
 LARGE = {"config2", "config3", "config4", "tet-config3"}
 
@@ -89,11 +95,13 @@ def test_setup_rejects_bad_input():
     assert e.value.code == d3m.D3M_EINVAL
 
 
-@pytest.mark.parametrize("tet", [False, True])
+@pytest.mark.parametrize("tet", [False, True, "mesh"])
 def test_rhs_planewave_matches_oracle(tet):
     from oracle import fem
     w = W.tiny(5, 4, 3, 1, 1, 1, seed=8, nrhs=3)
-    if tet:
+    if tet == "mesh":
+        w = W.delaunay(5, 4, 3, 2, 1, 1, seed=8, nrhs=3)
+    elif tet:
         w = W.tetrahedral(w, 0.1)
     s = d3m.Solver.from_workload(w)
     assert s.n_edges == w.n_edges
@@ -107,6 +115,49 @@ def _tet_vertices(w, move):
     for node, delta in move:
         v[node] += delta
     return v
+
+
+def _mesh_kw(w, **over):
+    kw = dict(element=d3m.TET_MESH, vertices=w.vertices, tets=w.tets, gcuts=w.gcuts)
+    kw.update(over)
+    return kw
+
+
+@pytest.mark.parametrize("what", ["degenerate", "vertex-id", "no-cuts", "cuts-order", "lm_weight", "nonmanifold"])
+def test_setup_rejects_bad_general_meshes(what):
+    """A degenerate tetrahedron, a vertex id out of range, missing or
+    unordered coordinate cuts, the mass-weighted multiplier map and a
+    triangle shared by three tetrahedra are refused at set-up."""
+    w = W.delaunay(3, 3, 3, 2, 1, 1, seed=2)
+    tets = w.tets.copy()
+    if what == "degenerate":
+        v = w.vertices.copy()
+        t = tets[0]
+        v[t[3]] = v[t[0]] + 0.5 * (v[t[1]] - v[t[0]]) + 0.5 * (v[t[2]] - v[t[0]])  # coplanar
+        kw = _mesh_kw(w, vertices=v)
+    elif what == "vertex-id":
+        tets[3, 2] = len(w.vertices)
+        kw = _mesh_kw(w, tets=tets)
+    elif what == "no-cuts":
+        kw = _mesh_kw(w, gcuts=None)
+    elif what == "cuts-order":
+        kw = _mesh_kw(w, gcuts=(w.gcuts[0][::-1], w.gcuts[1], w.gcuts[2]))
+    elif what == "lm_weight":
+        kw = _mesh_kw(w, lm_weight=1)
+    else:   # two more tetrahedra on the face (t0, t1, t2) of tetrahedron 0
+        t, V = tets[0], w.vertices
+        n = np.cross(V[t[1]] - V[t[0]], V[t[2]] - V[t[0]])
+        far = np.argsort(-np.abs((V - V[t[0]]) @ n))[:2]   # off the face plane
+        extra = np.array([[t[0], t[1], t[2], far[0]], [t[0], t[1], t[2], far[1]]])
+        kw = _mesh_kw(w, tets=np.concatenate([tets, extra]))
+    eps = np.ones(len(kw["tets"]), np.complex128)
+    with pytest.raises(d3m.D3MError) as ei:
+        d3m.Solver(0, 0, 0, 0.0, 0.0, 0.0, eps, w.k, w.cx, w.cy, w.cz, **kw)
+    assert ei.value.code == d3m.D3M_EINVAL and "d3m_setup" in str(ei.value)
+    if what == "nonmanifold":
+        assert "more than two" in str(ei.value)
+    if what == "degenerate":
+        assert "degenerate" in str(ei.value)
 
 
 @pytest.mark.parametrize("what", ["inverted", "off-plane", "brick-with-vertices", "element"])
@@ -171,7 +222,7 @@ def test_setup_rejects_bad_options(kw):
     assert "d3m_setup" in str(ei.value)
 
 
-@pytest.mark.parametrize("tet", [False, True])
+@pytest.mark.parametrize("tet", [False, True, "mesh"])
 def test_interface_coefficient_matches_oracle_entries(tet):
     """d3m_options.alpha sets the interface loss/gain term: the library's
     assembled entries of M equal the oracle's subdomain matrices for a
@@ -180,7 +231,9 @@ def test_interface_coefficient_matches_oracle_entries(tet):
     against the oracle's quadrature."""
     from oracle import decomp
     w = W.tiny(4, 3, 3, 2, 1, 1, seed=6)
-    if tet:
+    if tet == "mesh":
+        w = W.delaunay(5, 4, 4, 2, 2, 2, seed=3)
+    elif tet:
         w = W.tetrahedral(W.tiny(4, 3, 3, 2, 2, 1, seed=6), 0.1)
     w.alpha = 2.5 - 0.7j
     s = d3m.Solver.from_workload(w)
