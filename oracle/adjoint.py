@@ -5,8 +5,8 @@ S - k^2 sum_c eps_c M_c + jk T (Theory section discretisation).  With
 dA/d(Re eps_c) = -k^2 M_c and A = A^T,
     dJ/d(Re eps_c) = 2 k^2 Re( u_c^T M_c x_c ),   u = A^{-1} (P conj(x)),
 P the probe selector, u_c and x_c the local edge values of cell c (12 on
-bricks, 19 on the six tetrahedra of a tetrahedral cell, 6 per tetrahedron
-of a general mesh).  The
+bricks, 19 on the six tetrahedra of a tetrahedral cell, 6 (12 at order 2)
+per tetrahedron of a general mesh).  The
 adjoint solve is a plain second sparse LU solve; no code is shared with the
 library.  Pinned by central finite differences (tests/test_oracle_adjoint.py).
 """
@@ -32,7 +32,7 @@ def gradient(w, f, probes):
         from . import tetmesh
         g = tetmesh.grid_of(w)
         _, M = tetmesh.tet_matrices(g, np.arange(g.n_cells))
-        ce = g.tet_edges
+        ce = g.tet_dofs
     elif g.element == "brick":
         _, M = fem.element_matrices(g.h)
         M = np.broadcast_to(M, (g.n_cells, 12, 12))

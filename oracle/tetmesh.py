@@ -10,6 +10,11 @@ orientation).  Discretisation as for the lattice tetrahedra of fem.py:
   of E . t; inside a tetrahedron with local vertices (v_a, v_b), a < b, the
   local function points from v_a to v_b and carries the sign +1 when
   v_a < v_b, else -1;
+- order 2 (complete first order, hierarchical; the second-kind space of
+  degree 1): each edge also carries l_ij grad(lam_i lam_j), whose tangential
+  component along its own edge is 1 - 2 s / l_ij (s from i) and which has no
+  curl and no orientation sign; dof 2 e is the edge's Whitney function, dof
+  2 e + 1 its gradient function;
 - element integrals by the degree-2 four-point rule, face integrals by the
   edge-midpoint rule (both exact here), the incident-field RHS by the 7-point
   rule per boundary triangle (fem.tri_quadrature);
@@ -51,21 +56,31 @@ _FACE_OF = [(1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)]   # face q omits vertex 
 
 
 class MeshGrid:
-    """Topology and geometry of a general tetrahedral mesh."""
+    """Topology and geometry of a general tetrahedral mesh; n_edges counts
+    the dofs (order per edge), n_geo the edges themselves."""
 
     element = "mesh"
 
-    def __init__(self, vertices, tets):
+    def __init__(self, vertices, tets, order=1):
         self.V = np.asarray(vertices, np.float64)
         self.T = np.asarray(tets, np.int64)
+        self.order = int(order)
+        if self.order not in (1, 2):
+            raise ValueError("order must be 1 or 2")
         nt = len(self.T)
         self.n_nodes = len(self.V)
         self.n_cells = nt
         loc = np.stack([np.sort(self.T[:, [a, b]], axis=1) for a, b in PAIRS], 1)
         self.edges, inv = np.unique(loc.reshape(-1, 2), axis=0, return_inverse=True)
-        self.n_edges = len(self.edges)
+        self.n_geo = len(self.edges)
+        self.n_edges = self.order * self.n_geo
         self.tet_edges = inv.reshape(nt, 6)
-        self.tet_sign = np.stack([np.where(self.T[:, a] < self.T[:, b], 1.0, -1.0) for a, b in PAIRS], 1)
+        sg = np.stack([np.where(self.T[:, a] < self.T[:, b], 1.0, -1.0) for a, b in PAIRS], 1)
+        if self.order == 1:
+            self.tet_dofs, self.tet_sign = self.tet_edges, sg
+        else:
+            self.tet_dofs = np.concatenate([2 * self.tet_edges, 2 * self.tet_edges + 1], 1)
+            self.tet_sign = np.concatenate([sg, np.ones_like(sg)], 1)
         fl = np.stack([np.sort(self.T[:, list(f)], axis=1) for f in _FACE_OF], 1).reshape(-1, 3)
         self.faces, finv, cnt = np.unique(fl, axis=0, return_inverse=True, return_counts=True)
         finv = finv.ravel()
@@ -90,14 +105,24 @@ class MeshGrid:
 
 
 def grid_of(w) -> MeshGrid:
-    return MeshGrid(w.vertices, w.tets)
+    return MeshGrid(w.vertices, w.tets, getattr(w, "order", 1))
+
+
+def _basis(lam, G, ell, pairs, order):
+    """Edge functions at barycentric point lam: the Whitney functions of the
+    pairs, then (order 2) the gradient functions: (n, order * len(pairs), 3)."""
+    N = [np.stack([lam[a] * G[:, b] - lam[b] * G[:, a] for a, b in pairs], 1) * ell[..., None]]
+    if order == 2:
+        N.append(np.stack([lam[a] * G[:, b] + lam[b] * G[:, a] for a, b in pairs], 1) * ell[..., None])
+    return np.concatenate(N, 1)
 
 
 # ------------------------------------------------------------------ elements
 
 
 def tet_matrices(g: MeshGrid, tets):
-    """S and M (n, 6, 6) of the given tetrahedra in PAIRS order, signs of the
+    """S and M (n, 6 order, 6 order) of the given tetrahedra (the Whitney
+    functions in PAIRS order, then the gradient functions), signs of the
     global edge orientation applied."""
     tets = np.asarray(tets)
     X = g.V[g.T[tets]]
@@ -105,11 +130,13 @@ def tet_matrices(g: MeshGrid, tets):
     vol = np.abs(vol)
     ell = np.stack([np.linalg.norm(X[:, b] - X[:, a], axis=1) for a, b in PAIRS], 1)
     curl = np.stack([2.0 * np.cross(G[:, a], G[:, b]) for a, b in PAIRS], 1) * ell[..., None]
+    if g.order == 2:
+        curl = np.concatenate([curl, np.zeros_like(curl)], 1)   # gradients have no curl
     S = vol[:, None, None] * np.einsum("cid,cjd->cij", curl, curl)
     M = np.zeros_like(S)
     qp, qw = fem.tet_quadrature()
     for lam, wt in zip(qp, qw):
-        N = np.stack([lam[a] * G[:, b] - lam[b] * G[:, a] for a, b in PAIRS], 1) * ell[..., None]
+        N = _basis(lam, G, ell, PAIRS, g.order)
         M += wt * vol[:, None, None] * np.einsum("cid,cjd->cij", N, N)
     sg = g.tet_sign[tets]
     sgn = sg[:, :, None] * sg[:, None, :]
@@ -121,19 +148,21 @@ def _tri(g: MeshGrid, faces):
     G, area = fem.tri_frame(Q)
     ell = np.stack([np.linalg.norm(Q[:, b] - Q[:, a], axis=1) for a, b in TRI], 1)
     ids = np.stack([g.edge_id(g.faces[faces, a], g.faces[faces, b]) for a, b in TRI], 1)
+    if g.order == 2:
+        ids = np.concatenate([2 * ids, 2 * ids + 1], 1)
     return Q, G, area, ell, ids
 
 
 def face_matrices(g: MeshGrid, faces):
-    """Tangential face mass (n, 3, 3) of the given faces (TRI order of the
-    sorted vertices, every local edge along its global orientation) and the
-    global edge ids (n, 3)."""
+    """Tangential face mass (n, 3 order, 3 order) of the given faces (TRI
+    order of the sorted vertices, every local edge along its global
+    orientation; then the gradient functions) and the global dof ids."""
     faces = np.asarray(faces)
     Q, G, area, ell, ids = _tri(g, faces)
-    T = np.zeros((len(faces), 3, 3))
+    T = np.zeros((len(faces), 3 * g.order, 3 * g.order))
     qp, qw = fem.tri_quadrature(2)
     for mu, wt in zip(qp, qw):
-        N = np.stack([mu[a] * G[:, b] - mu[b] * G[:, a] for a, b in TRI], 1) * ell[..., None]
+        N = _basis(mu, G, ell, TRI, g.order)
         T += wt * area[:, None, None] * np.einsum("cid,cjd->cij", N, N)
     return T, ids
 
@@ -156,26 +185,29 @@ def assemble(g: MeshGrid, eps, k, tets=None, faces=()):
     coeff * T_f for each (face ids, coeff) in faces."""
     tets = np.arange(g.n_cells) if tets is None else np.asarray(tets)
     S, M = tet_matrices(g, tets)
-    ce = g.tet_edges[tets]
-    R = [np.repeat(ce, 6, axis=1).ravel()]
-    C = [np.tile(ce, (1, 6)).ravel()]
-    V = [(S.reshape(len(tets), 36) - (k * k) * eps[tets][:, None] * M.reshape(len(tets), 36))
+    ce = g.tet_dofs[tets]
+    nl = ce.shape[1]
+    R = [np.repeat(ce, nl, axis=1).ravel()]
+    C = [np.tile(ce, (1, nl)).ravel()]
+    V = [(S.reshape(len(tets), nl * nl) - (k * k) * eps[tets][:, None] * M.reshape(len(tets), nl * nl))
          .ravel().astype(np.complex128)]
+    nf = 3 * g.order
     for fids, coeff in faces:
         fids = np.asarray(fids)
         if len(fids) == 0:
             continue
         T, ids = face_matrices(g, fids)
-        R.append(np.repeat(ids, 3, axis=1).ravel())
-        C.append(np.tile(ids, (1, 3)).ravel())
-        V.append((coeff * T.reshape(len(fids), 9)).ravel().astype(np.complex128))
+        R.append(np.repeat(ids, nf, axis=1).ravel())
+        C.append(np.tile(ids, (1, nf)).ravel())
+        V.append((coeff * T.reshape(len(fids), nf * nf)).ravel().astype(np.complex128))
     return np.concatenate(R), np.concatenate(C), np.concatenate(V)
 
 
 def mass_stiffness(g: MeshGrid):
     S, M = tet_matrices(g, np.arange(g.n_cells))
-    ce = g.tet_edges
-    r, c = np.repeat(ce, 6, axis=1).ravel(), np.tile(ce, (1, 6)).ravel()
+    ce = g.tet_dofs
+    nl = ce.shape[1]
+    r, c = np.repeat(ce, nl, axis=1).ravel(), np.tile(ce, (1, nl)).ravel()
     shape = (g.n_edges, g.n_edges)
     return sp.csr_matrix((S.ravel(), (r, c)), shape=shape), sp.csr_matrix((M.ravel(), (r, c)), shape=shape)
 
@@ -197,7 +229,7 @@ def rhs_planewave(w, which=None):
     qp, qw = fem.tri_quadrature(5)
     for mu, wt in zip(qp, qw):
         pts = np.einsum("i,cid->cd", mu, Q)
-        N = np.stack([mu[a] * G[:, b] - mu[b] * G[:, a] for a, b in TRI], 1) * ell[..., None]
+        N = _basis(mu, G, ell, TRI, g.order)
         for col, r in enumerate(which):
             E, cE = fem.incident(pts, w.khat[r], w.pol[r], w.k)
             Et = E - np.einsum("cd,cd->c", E, n)[:, None] * n
@@ -208,15 +240,25 @@ def rhs_planewave(w, which=None):
 
 
 def edge_interpolant(w, khat, pol):
+    """Dofs of E_inc: the line average of E . t along every edge and (order
+    2) the moment 3 <E . t (1 - 2 s / l)> (the projection onto the edge's
+    linear tangential variation), 4-point Gauss-Legendre along the edge."""
     g = grid_of(w)
     P0, P1 = g.V[g.edges[:, 0]], g.V[g.edges[:, 1]]
     t = P1 - P0
     that = t / np.linalg.norm(t, axis=1)[:, None]
     q, wq = fem.gauss01(4)
-    out = np.zeros(g.n_edges, np.complex128)
+    avg = np.zeros(g.n_geo, np.complex128)
+    mom = np.zeros(g.n_geo, np.complex128)
     for tq, wt in zip(q, wq):
         E, _ = fem.incident(P0 + tq * t, khat, pol, w.k)
-        out += wt * np.sum(E * that, 1)
+        et = np.sum(E * that, 1)
+        avg += wt * et
+        mom += wt * et * (1.0 - 2.0 * tq)
+    if g.order == 1:
+        return avg
+    out = np.zeros(g.n_edges, np.complex128)
+    out[0::2], out[1::2] = avg, 3.0 * mom
     return out
 
 
@@ -225,7 +267,8 @@ def edge_lengths(g: MeshGrid):
 
 
 def discrete_gradient(g: MeshGrid):
-    ne = g.n_edges
+    """Edge-node incidence (geometric edges x nodes)."""
+    ne = g.n_geo
     rows = np.concatenate([np.arange(ne)] * 2)
     return sp.csr_matrix((np.concatenate([-np.ones(ne), np.ones(ne)]),
                           (rows, np.concatenate([g.edges[:, 0], g.edges[:, 1]]))), shape=(ne, g.n_nodes))
@@ -250,12 +293,12 @@ def decompose(w, with_matrices=True):
     sub, parts = subdomain_of(w, g)
     nsub = parts[0] * parts[1] * parts[2]
     free = np.ones(g.n_edges, bool)
-    if w.pec_edge is not None:
+    if w.pec_edge is not None:   # one byte per dof
         free[np.asarray(w.pec_edge) != 0] = False
     subs = []
     for s in range(nsub):
         tets = np.flatnonzero(sub == s)
-        e = np.unique(g.tet_edges[tets].ravel()) if len(tets) else np.zeros(0, np.int64)
+        e = np.unique(g.tet_dofs[tets].ravel()) if len(tets) else np.zeros(0, np.int64)
         sd = decomp.Subdomain(s, decomp.sub_pos(s, parts), None, None, e[free[e]])
         sd.tets = tets
         subs.append(sd)
@@ -316,17 +359,21 @@ def subdomain_matrix(w, dec, sd):
 
 
 def subdomain_nd(g: MeshGrid, sd, interface_edges, leaf_max):
-    """ND nodes (sorted global edge arrays, post-order) of the non-interface
-    dofs of sd: centroid bisection (module docstring)."""
-    avail = np.zeros(g.n_edges, bool)
-    avail[sd.edges] = True
-    avail[np.asarray(sorted(interface_edges), dtype=np.int64)] = False
+    """ND nodes (sorted global dof arrays, post-order) of the non-interface
+    dofs of sd: centroid bisection over the edges (module docstring); an
+    edge's dofs stay together."""
+    avail = np.zeros(g.n_geo, bool)
+    avail[np.asarray(sd.edges, np.int64) // g.order] = True
+    avail[np.asarray(sorted(interface_edges), dtype=np.int64) // g.order] = False
     nodes = []
+
+    def dofs(E):
+        return (g.order * E[:, None] + np.arange(g.order)[None, :]).ravel()
 
     def leaf(E):
         if len(E):
             avail[E] = False
-            nodes.append(E)
+            nodes.append(dofs(E))
 
     def rec(T):
         E = np.unique(g.tet_edges[T].ravel()) if len(T) else np.zeros(0, np.int64)
@@ -347,7 +394,7 @@ def subdomain_nd(g: MeshGrid, sd, interface_edges, leaf_max):
         rec(left)
         rec(right)
         if len(sep):
-            nodes.append(np.sort(sep))
+            nodes.append(dofs(np.sort(sep)))
 
     rec(np.asarray(sd.tets, np.int64))
     return nodes
@@ -357,9 +404,9 @@ def subdomain_nd(g: MeshGrid, sd, interface_edges, leaf_max):
 
 
 def free_edges(w):
-    n = grid_of(w).n_edges
+    g = grid_of(w)
     if w.pec_edge is None:
-        return np.arange(n)
+        return np.arange(g.n_edges)
     return np.flatnonzero(np.asarray(w.pec_edge) == 0)
 
 

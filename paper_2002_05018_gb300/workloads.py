@@ -79,6 +79,7 @@ class Workload:
     vertices: np.ndarray | None = None  # (n_nodes, 3) float64 positions (x-fastest for "tet"); None: lattice
     tets: np.ndarray | None = None      # "mesh": (n_tets, 4) int64 vertex ids
     gcuts: tuple | None = None          # "mesh": subdomain cut coordinates per axis (px+1, py+1, pz+1)
+    order: int = 1                      # "mesh": 1 Whitney; 2 also the edge gradient functions (2 dofs per edge)
 
     @property
     def n_cells(self) -> int:
@@ -89,7 +90,7 @@ class Workload:
     @property
     def n_edges(self) -> int:
         if self.element == "mesh":
-            return len(mesh_edge_pairs(self.tets))
+            return self.order * len(mesh_edge_pairs(self.tets))
         return sum(family_sizes(self.nx, self.ny, self.nz, self.element))
 
     @property
@@ -305,14 +306,15 @@ def as_mesh(w: Workload) -> Workload:
                                tets=tets.reshape(-1, 4), eps=np.repeat(w.eps, 6), gcuts=gcuts)
 
 
-def delaunay(nx, ny, nz, px, py, pz, seed=0, nrhs=1, h=0.1, jitter=0.3, lossy=True) -> Workload:
+def delaunay(nx, ny, nz, px, py, pz, seed=0, nrhs=1, h=0.1, jitter=0.3, lossy=True, order=1) -> Workload:
     """An unstructured tetrahedral mesh of the box [0, nx h] x [0, ny h] x
     [0, nz h]: the Delaunay tetrahedralisation (scipy.spatial.Delaunay) of
     the lattice points moved by a seeded uniform jitter of up to jitter*h per
     axis (boundary points only within their boundary planes, box edges along
     the edge, corners fixed); per-tetrahedron eps ~ U[1, 3] (lossy: times
     1 - 0.05j); px x py x pz subdomains cut at equal coordinates; random plane
-    waves.  Draw order: jitter, eps, waves."""
+    waves; order 2: two dofs per edge (Whitney and edge-gradient functions).
+    Draw order: jitter, eps, waves."""
     from scipy.spatial import Delaunay
     rng = np.random.default_rng(seed)
     kk, jj, ii = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
@@ -332,8 +334,9 @@ def delaunay(nx, ny, nz, px, py, pz, seed=0, nrhs=1, h=0.1, jitter=0.3, lossy=Tr
     L = (nx * h, ny * h, nz * h)
     gcuts = tuple(np.linspace(0.0, L[a], p + 1) for a, p in enumerate((px, py, pz)))
     empty = np.zeros(1, np.int32)
-    return Workload(f"delaunay{nx}x{ny}x{nz}", nx, ny, nz, *L, K0, eps, None, empty, empty, empty,
-                    khat, pol, seed=seed, element="mesh", vertices=pts, tets=tets, gcuts=gcuts)
+    return Workload(f"delaunay{nx}x{ny}x{nz}" + ("-o2" if order == 2 else ""), nx, ny, nz, *L, K0, eps, None,
+                    empty, empty, empty, khat, pol, seed=seed, element="mesh", vertices=pts, tets=tets,
+                    gcuts=gcuts, order=order)
 
 
 def tiny(nx, ny, nz, px, py, pz, seed=0, lossy=True, nrhs=1, pec=None, jitter=False,

@@ -162,3 +162,97 @@ def test_adjoint_matches_central_differences():
         # (about 1e-16 J / 1e-6) relative to the largest gradient entry: the
         # per-tetrahedron entries are small next to J
         assert abs(fd - g[c]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max(), (c, fd, g[c], J)
+
+
+# ------------------------------------------------------- complete first order
+
+
+def _linear_field_dofs(g, a, C):
+    """Dofs of E = a + C r: the line average of E . t and the coefficient of
+    1 - 2 s / l (half the difference of E . t between the edge's ends)."""
+    P0, P1 = g.V[g.edges[:, 0]], g.V[g.edges[:, 1]]
+    t = (P1 - P0) / np.linalg.norm(P1 - P0, axis=1)[:, None]
+    E0, E1 = a + P0 @ C.T, a + P1 @ C.T
+    x = np.zeros(g.n_edges)
+    x[0::2] = 0.5 * np.sum((E0 + E1) * t, 1)
+    x[1::2] = 0.5 * np.sum((E0 - E1) * t, 1)
+    return x
+
+
+def test_order2_holds_every_linear_field():
+    """The order-2 space contains every field a + C r: its energies are exact
+    (the integral of |a + C r|^2 over the box by tensor Gauss-Legendre, exact
+    for the quadratic integrand), the Whitney space alone does not."""
+    w = W.delaunay(5, 4, 4, 1, 1, 1, seed=3, order=2)
+    g = tetmesh.grid_of(w)
+    assert g.n_edges == 2 * g.n_geo == w.n_edges
+    S, M = tetmesh.mass_stiffness(g)
+    a = np.array([0.3, -0.2, 0.5])
+    C = np.array([[0.1, 0.4, -0.3], [0.2, -0.5, 0.6], [-0.7, 0.3, 0.2]])
+    x = _linear_field_dofs(g, a, C)
+    L = np.array([w.lx, w.ly, w.lz])
+    q, wq = fem.gauss01(2)
+    exact = 0.0
+    for i, xi in enumerate(q):
+        for j, yj in enumerate(q):
+            for k, zk in enumerate(q):
+                e = a + C @ (np.array([xi, yj, zk]) * L)
+                exact += wq[i] * wq[j] * wq[k] * (e @ e)
+    exact *= L.prod()
+    assert np.isclose(x @ M @ x, exact, rtol=1e-12)
+    curl = np.array([C[2, 1] - C[1, 2], C[0, 2] - C[2, 0], C[1, 0] - C[0, 1]])
+    assert np.isclose(x @ S @ x, L.prod() * curl @ curl, rtol=1e-11)
+    # the edge-gradient functions have no curl: their stiffness rows are zero
+    assert abs(S[1::2]).max() == 0.0
+    # a symmetric C (a gradient field) leaves no curl energy
+    xs = _linear_field_dofs(g, a, C + C.T)
+    assert abs(xs @ S @ xs) < 1e-12 * abs(S).max()
+    # Whitney functions alone miss the linear field's energy
+    g1 = tetmesh.grid_of(W.delaunay(5, 4, 4, 1, 1, 1, seed=3))
+    _, M1 = tetmesh.mass_stiffness(g1)
+    assert not np.isclose(x[0::2] @ M1 @ x[0::2], exact, rtol=1e-3)
+
+
+def test_order2_converges_faster_than_whitney():
+    err = {}
+    for order in (1, 2):
+        err[order] = []
+        for n in (3, 6):
+            w = W.delaunay(n, n, n, 1, 1, 1, seed=4, lossy=False, h=1.0 / n, order=order)
+            w.eps[:] = 1.0
+            f = fem.rhs_planewave(w)
+            x = fem.solve_global(w, f)[:, 0]
+            xi = fem.edge_interpolant(w, w.khat[0], w.pol[0])
+            err[order].append(np.linalg.norm(x - xi) / np.linalg.norm(xi))
+    assert err[2][1] < err[2][0] / 3.0
+    assert all(e2 < e1 for e1, e2 in zip(err[1], err[2]))
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(nx=6, ny=5, nz=4, px=3, py=2, pz=1, seed=5)])
+def test_order2_decomposed_equals_global(kw):
+    w = _delaunay(order=2, **kw)
+    f = fem.rhs_planewave(w)
+    r = d3m.solve(w, f, return_all=True)
+    xg = fem.solve_global(w, f)
+    assert np.abs(r["x"] - xg).max() < 1e-10 * np.abs(xg).max()
+    assert r["copy_mismatch"] < 1e-10 * np.abs(xg).max()
+    xs = d3m.solve_primal_schur(w, f)
+    assert np.abs(xs - xg).max() < 1e-10 * np.abs(xg).max()
+
+
+def test_order2_adjoint_matches_central_differences():
+    w = _delaunay(nx=3, ny=3, nz=2, px=1, py=1, pz=1, seed=21, order=2)
+    f = fem.rhs_planewave(w)
+    rng = np.random.default_rng(0)
+    probes = np.sort(rng.choice(w.n_edges, 6, replace=False))
+    J, g = adjoint.gradient(w, f, probes)
+    h = 1e-6
+    for c in rng.choice(w.n_cells, 4, replace=False):
+        e0 = w.eps.copy()
+        w.eps = e0.copy(); w.eps[c] += h
+        Jp = adjoint.objective(fem.solve_global(w, f), probes)
+        w.eps = e0.copy(); w.eps[c] -= h
+        Jm = adjoint.objective(fem.solve_global(w, f), probes)
+        w.eps = e0
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - g[c]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max(), (c, fd, g[c], J)
