@@ -112,6 +112,16 @@ typedef struct {
   int64_t n_vertices;       /* D3M_TET_MESH only */
   int64_t n_tets;           /* D3M_TET_MESH only */
   const int64_t *tets;      /* D3M_TET_MESH only: 4 * n_tets vertex ids */
+  int32_t order;            /* D3M_TET_MESH: 0 or 1 = Whitney functions, one dof per
+                               edge; 2 = complete first order (hierarchical): each
+                               edge (i, j) also carries l_ij grad(lam_i lam_j) (no
+                               curl, tangential component 1 - 2 s / l_ij along its
+                               edge, s from i), dof 2e the Whitney function of edge
+                               e and dof 2e+1 its gradient function; the "n_edges"
+                               rows of every RHS/solution block and of pec_edge's
+                               count are then 2 * edges (pec_edge: one byte per
+                               dof, both dofs of an edge alike).  Other elements:
+                               0 or 1. */
 } d3m_mesh;
 
 /* Materials.  eps_r: 2*n_cells doubles (re, im) per cell, time convention

@@ -22,12 +22,13 @@ class D3MSolve(torch.autograd.Function):
         """eps_re: real float64 tensor (n_cells), the real part of eps_r (the
         imaginary part comes from geom['eps_im']); f: complex128 CUDA tensor
         (n_edges, nrhs); geom: dict(nx, ny, nz, lx, ly, lz, k, cx, cy, cz,
-        eps_im, pec, precision[, element, vertices, tets, gcuts])."""
+        eps_im, pec, precision[, element, vertices, tets, gcuts, order])."""
         eps = eps_re.detach().cpu().numpy() + 1j * np.asarray(geom.get("eps_im", 0.0))
         s = d3m.Solver(geom["nx"], geom["ny"], geom["nz"], geom["lx"], geom["ly"], geom["lz"], eps, geom["k"],
                        geom["cx"], geom["cy"], geom["cz"], pec=geom.get("pec"),
                        precision=geom.get("precision", d3m.FP64), element=geom.get("element", d3m.BRICK),
-                       vertices=geom.get("vertices"), tets=geom.get("tets"), gcuts=geom.get("gcuts"))
+                       vertices=geom.get("vertices"), tets=geom.get("tets"), gcuts=geom.get("gcuts"),
+                       order=geom.get("order", 1))
         s.factor()
         x, _ = s.solve(f)
         x = x.clone()
@@ -56,4 +57,4 @@ def geom_of(w, precision=d3m.FP64):
                 eps_im=np.asarray(w.eps).imag.copy(), pec=w.pec_edge, precision=precision,
                 element={"tet": d3m.TET, "mesh": d3m.TET_MESH}.get(getattr(w, "element", "brick"), d3m.BRICK),
                 vertices=getattr(w, "vertices", None), tets=getattr(w, "tets", None),
-                gcuts=getattr(w, "gcuts", None))
+                gcuts=getattr(w, "gcuts", None), order=getattr(w, "order", 1))

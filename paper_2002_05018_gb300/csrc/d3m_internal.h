@@ -38,6 +38,7 @@ struct Plan {
   std::vector<int64_t> tet_v;         // 4 vertex ids per tetrahedron
   std::vector<int64_t> tet_e;         // 6 edge ids per tetrahedron (local pairs 01 02 03 12 13 23)
   std::vector<int8_t> tet_s;          // 6 orientation signs per tetrahedron
+  int dpe = 1;                        // dofs per edge (mesh order): dof dpe*e + q
   std::vector<std::array<int64_t, 4>> bface;  // boundary triangles: sorted vertices + opposite vertex
   std::vector<std::pair<int64_t, int64_t>> medge;  // vertex pair (i < j) of each edge
   double bS[12][12], bM[12][12], bT[6][12][12];  // brick element and face matrices

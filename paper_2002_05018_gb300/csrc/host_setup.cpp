@@ -256,6 +256,40 @@ static void tet_local(const double X[4][3], double S[6][6], double M[6][6]) {
     }
 }
 
+// int (lam_a grad lam_b + s1 lam_b grad lam_a) . (lam_c grad lam_d + s2 lam_d grad lam_c)
+// in units of the simplex measure / (20 or 12); s = -1 for a Whitney
+// function, +1 for an edge-gradient function l grad(lam_a lam_b) / l.
+static inline double pair_mass(const double g[][3], int a, int b, double s1, int c, int d, double s2) {
+  return (1.0 + (a == c)) * dot3(g[b], g[d]) + s2 * (1.0 + (a == d)) * dot3(g[b], g[c]) +
+         s1 * (1.0 + (b == c)) * dot3(g[a], g[d]) + s1 * s2 * (1.0 + (b == d)) * dot3(g[a], g[c]);
+}
+
+// Order 2: local S and M (12 x 12) of tetrahedron X, the six Whitney functions
+// (pairs 01 02 03 12 13 23) then the six edge-gradient functions.
+static void tet_local2(const double X[4][3], double S[12][12], double M[12][12]) {
+  double S6[6][6], M6[6][6], g[4][3], ell[6];
+  tet_local(X, S6, M6);
+  const double vol = std::fabs(tet_grads(X, g)) / 6.0;
+  for (int q = 0; q < 6; ++q) {
+    double ev[3];
+    sub3(X[TET_E[q][1]], X[TET_E[q][0]], ev);
+    ell[q] = std::sqrt(dot3(ev, ev));
+  }
+  for (int q = 0; q < 12; ++q)
+    for (int r = 0; r < 12; ++r) {
+      if (q < 6 && r < 6) {
+        S[q][r] = S6[q][r];
+        M[q][r] = M6[q][r];
+        continue;
+      }
+      S[q][r] = 0.0;  // the gradient functions have no curl
+      const int qq = q % 6, rr = r % 6;
+      M[q][r] = vol / 20.0 * ell[qq] * ell[rr] *
+                pair_mass(g, TET_E[qq][0], TET_E[qq][1], q < 6 ? -1.0 : 1.0, TET_E[rr][0], TET_E[rr][1],
+                          r < 6 ? -1.0 : 1.0);
+    }
+}
+
 // S = int curl N . curl N and M = int N . N of a cell, in cell_edges order.
 int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][MAX_CELL_NE],
                   double M[MAX_CELL_NE][MAX_CELL_NE]) {
@@ -290,8 +324,9 @@ int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][M
 }
 
 // Signed local matrices of tetrahedron t of a general mesh (global edge
-// orientation: from the lower to the higher vertex id).
-static void mesh_tet_matrices(const Plan &p, int64_t t, double S[6][6], double M[6][6]) {
+// orientation: from the lower to the higher vertex id; the edge-gradient
+// functions of order 2 carry no sign); returns the local dof count.
+static int mesh_tet_matrices(const Plan &p, int64_t t, double S[12][12], double M[12][12]) {
   double X[4][3];
   for (int v = 0; v < 4; ++v) {
     const double *x = p.vert.data() + 3 * p.tet_v[4 * t + v];
@@ -299,25 +334,42 @@ static void mesh_tet_matrices(const Plan &p, int64_t t, double S[6][6], double M
     X[v][1] = x[1];
     X[v][2] = x[2];
   }
-  tet_local(X, S, M);
+  const int nl = 6 * p.dpe;
+  if (p.dpe == 2) {
+    tet_local2(X, S, M);
+  } else {
+    double S6[6][6], M6[6][6];
+    tet_local(X, S6, M6);
+    for (int q = 0; q < 6; ++q)
+      for (int r = 0; r < 6; ++r) {
+        S[q][r] = S6[q][r];
+        M[q][r] = M6[q][r];
+      }
+  }
   const int8_t *sg = p.tet_s.data() + 6 * t;
-  for (int q = 0; q < 6; ++q)
-    for (int r = 0; r < 6; ++r) {
-      const double s = (double)(sg[q] * sg[r]);
+  for (int q = 0; q < nl; ++q)
+    for (int r = 0; r < nl; ++r) {
+      const double s = (double)((q < 6 ? sg[q] : 1) * (r < 6 ? sg[r] : 1));
       S[q][r] *= s;
       M[q][r] *= s;
     }
+  return nl;
+}
+
+// Global dof of local function q of tetrahedron t (Whitney q < 6, gradient q >= 6).
+static inline int64_t mesh_tet_dof(const Plan &p, int64_t t, int q) {
+  return q < 6 ? p.dpe * p.tet_e[6 * t + q] : p.dpe * p.tet_e[6 * t + q - 6] + 1;
 }
 
 int cell_dofs_mass(const Plan &p, int64_t c, int64_t e[MAX_CELL_NE], double M[MAX_CELL_NE][MAX_CELL_NE]) {
   if (p.element == D3M_TET_MESH) {
-    double S6[6][6], M6[6][6];
-    mesh_tet_matrices(p, c, S6, M6);
-    for (int q = 0; q < 6; ++q) {
-      e[q] = p.tet_e[6 * c + q];
-      for (int r = 0; r < 6; ++r) M[q][r] = M6[q][r];
+    double S12[12][12], M12[12][12];
+    const int nl = mesh_tet_matrices(p, c, S12, M12);
+    for (int q = 0; q < nl; ++q) {
+      e[q] = mesh_tet_dof(p, c, q);
+      for (int r = 0; r < nl; ++r) M[q][r] = M12[q][r];
     }
-    return 6;
+    return nl;
   }
   const int ci = (int)(c % p.nx), cj = (int)((c / p.nx) % p.ny), ck = (int)(c / ((int64_t)p.nx * p.ny));
   double S[MAX_CELL_NE][MAX_CELL_NE];
@@ -369,6 +421,24 @@ static void tri_local(const double Q[3][3], double T[3][3]) {
   for (int q = 0; q < 3; ++q)
     for (int r = 0; r < 3; ++r)
       T[q][r] = area / 12.0 * ell[q] * ell[r] * whitney_pair(g, TRI_E[q][0], TRI_E[q][1], TRI_E[r][0], TRI_E[r][1]);
+}
+
+// Order 2: local tangential face mass (6 x 6) of triangle Q (Whitney, then gradients).
+static void tri_local2(const double Q[3][3], double T[6][6]) {
+  double g[3][3], ell[3];
+  const double area = tri_grads(Q, g);
+  for (int q = 0; q < 3; ++q) {
+    double ev[3];
+    sub3(Q[TRI_E[q][1]], Q[TRI_E[q][0]], ev);
+    ell[q] = std::sqrt(dot3(ev, ev));
+  }
+  for (int q = 0; q < 6; ++q)
+    for (int r = 0; r < 6; ++r) {
+      const int qq = q % 3, rr = r % 3;
+      T[q][r] = area / 12.0 * ell[qq] * ell[rr] *
+                pair_mass(g, TRI_E[qq][0], TRI_E[qq][1], q < 3 ? -1.0 : 1.0, TRI_E[rr][0], TRI_E[rr][1],
+                          r < 3 ? -1.0 : 1.0);
+    }
 }
 
 struct FaceTri {
@@ -554,12 +624,25 @@ static void mesh_centroid(const Plan &p, int64_t t, double c[3]) {
 }
 
 // Face mass of a triangle with sorted vertices (every local edge along its
-// global orientation) and its three edge ids (pairs 01 02 12).
-static void mesh_face(const Plan &p, const int64_t v[3], double T[3][3], int64_t e[3]) {
+// global orientation) and its dofs (Whitney functions of the pairs 01 02 12,
+// then at order 2 their gradient functions); returns the dof count.
+static int mesh_face(const Plan &p, const int64_t v[3], double T[6][6], int64_t e[6]) {
   double Q[3][3];
   for (int w = 0; w < 3; ++w) mesh_vertex(p, v[w], Q[w]);
-  tri_local(Q, T);
-  for (int q = 0; q < 3; ++q) e[q] = mesh_edge_id(p, v[TRI_E[q][0]], v[TRI_E[q][1]]);
+  if (p.dpe == 2) {
+    tri_local2(Q, T);
+  } else {
+    double T3[3][3];
+    tri_local(Q, T3);
+    for (int q = 0; q < 3; ++q)
+      for (int r = 0; r < 3; ++r) T[q][r] = T3[q][r];
+  }
+  for (int q = 0; q < 3; ++q) {
+    const int64_t ge = mesh_edge_id(p, v[TRI_E[q][0]], v[TRI_E[q][1]]);
+    e[q] = p.dpe * ge;
+    if (p.dpe == 2) e[3 + q] = 2 * ge + 1;
+  }
+  return 3 * p.dpe;
 }
 
 // Interior ordering of a subdomain of a general mesh: bisection of its
@@ -625,8 +708,14 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   p.k = k;
   p.element = D3M_TET_MESH;
   p.nfam = 0;
-  p.cell_ne = 6;
   p.nx = p.ny = p.nz = 0;
+  if (mesh->order < 0 || mesh->order > 2) {
+    ctx.err = "d3m_setup: mesh order must be 0, 1 or 2";
+    return D3M_EINVAL;
+  }
+  p.dpe = mesh->order == 2 ? 2 : 1;
+  p.cell_ne = 6 * p.dpe;
+  const int dpe = p.dpe;
   const int64_t nv = mesh->n_vertices, nt = mesh->n_tets;
   if (nv < 4 || nt < 1 || !mesh->vertices || !mesh->tets) {
     ctx.err = "d3m_setup: a general mesh needs n_vertices >= 4, n_tets >= 1, vertices and tets";
@@ -675,7 +764,8 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     }
   std::sort(p.medge.begin(), p.medge.end());
   p.medge.erase(std::unique(p.medge.begin(), p.medge.end()), p.medge.end());
-  p.n_edges = (int64_t)p.medge.size();
+  const int64_t n_geo = (int64_t)p.medge.size();
+  p.n_edges = dpe * n_geo;  // dofs
   p.tet_e.resize(6 * nt);
   p.tet_s.resize(6 * nt);
   for (int64_t t = 0; t < nt; ++t)
@@ -728,6 +818,11 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   p.pec.assign(p.n_edges, 0);
   if (mat->pec_edge)
     for (int64_t e = 0; e < p.n_edges; ++e) p.pec[e] = mat->pec_edge[e] ? 1 : 0;
+  for (int64_t e = 0; e < n_geo; ++e)
+    if (dpe == 2 && p.pec[2 * e] != p.pec[2 * e + 1]) {
+      ctx.err = "d3m_setup: pec_edge must mark both dofs of an edge alike";
+      return D3M_EINVAL;
+    }
   p.n_free = 0;
   for (int64_t e = 0; e < p.n_edges; ++e) p.n_free += !p.pec[e];
   // ---- subdomains: coordinate boxes, a tetrahedron goes where its centroid is
@@ -762,16 +857,19 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   }
   p.sub_lo.assign(p.nsub, {0, 0, 0});
   p.sub_hi.assign(p.nsub, {0, 0, 0});
-  p.sub_edges.assign(p.nsub, {});
+  p.sub_edges.assign(p.nsub, {});  // free dofs of each subdomain
+  std::vector<std::vector<int64_t>> sub_geo(p.nsub);
   for (int s = 0; s < p.nsub; ++s) {
-    auto &E = p.sub_edges[s];
+    auto &G = sub_geo[s];
     for (int64_t t : sub_tets[s])
-      for (int q = 0; q < 6; ++q)
-        if (!p.pec[p.tet_e[6 * t + q]]) E.push_back(p.tet_e[6 * t + q]);
-    std::sort(E.begin(), E.end());
-    E.erase(std::unique(E.begin(), E.end()), E.end());
+      for (int q = 0; q < 6; ++q) G.push_back(p.tet_e[6 * t + q]);
+    std::sort(G.begin(), G.end());
+    G.erase(std::unique(G.begin(), G.end()), G.end());
+    for (int64_t e : G)
+      for (int q = 0; q < dpe; ++q)
+        if (!p.pec[dpe * e + q]) p.sub_edges[s].push_back(dpe * e + q);
   }
-  // ---- copies and multipliers
+  // ---- copies and multipliers (per dof)
   std::vector<std::vector<int>> copies(p.n_edges);
   for (int s = 0; s < p.nsub; ++s)
     for (int64_t e : p.sub_edges[s]) copies[e].push_back(s);
@@ -825,15 +923,24 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     p.sn_kind.push_back(kind);
     p.sn_owner.push_back(owner);
   };
-  std::vector<char> avail(p.n_edges, 0);
+  std::vector<char> avail(n_geo, 0);  // per geometric edge
   std::vector<int64_t> sub_m0(p.nsub);
   for (int s = 0; s < p.nsub; ++s) {
     sub_m0[s] = (int64_t)p.m_sub.size();
-    for (int64_t e : p.sub_edges[s]) avail[e] = copies[e].size() < 2;
+    // an edge is ordered inside the subdomain when it has a free dof there
+    // and none of its dofs is an interface dof
+    for (int64_t d : p.sub_edges[s]) avail[d / dpe] = 1;
+    for (int64_t d : p.sub_edges[s])
+      if (copies[d].size() >= 2) avail[d / dpe] = 0;
     std::vector<std::vector<int64_t>> nodes;
     mesh_nd(p, cent, avail, sub_tets[s], leaf_max, nodes);
-    for (auto &nd : nodes) push_node(s, nd, 0, s);
-    for (int64_t e : p.sub_edges[s]) avail[e] = 0;
+    for (auto &nd : nodes) {
+      std::vector<int64_t> dofs;
+      for (int64_t e : nd)
+        for (int q = 0; q < dpe; ++q) dofs.push_back(dpe * e + q);
+      push_node(s, dofs, 0, s);
+    }
+    for (int64_t e : sub_geo[s]) avail[e] = 0;
     std::vector<int64_t> B;
     for (int64_t e : p.sub_edges[s])
       if (copies[e].size() >= 2) B.push_back(e);
@@ -874,31 +981,32 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     const int64_t m1_ = s + 1 < p.nsub ? sub_m0[s + 1] : p.lam_start;
     for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = v;
     for (int64_t t : sub_tets[s]) {
-      double S6[6][6], M6[6][6];
-      mesh_tet_matrices(p, t, S6, M6);
-      const int64_t *e = p.tet_e.data() + 6 * t;
-      for (int a = 0; a < 6; ++a) {
+      double S12[12][12], M12[12][12];
+      const int nl = mesh_tet_matrices(p, t, S12, M12);
+      int64_t e[12];
+      for (int q = 0; q < nl; ++q) e[q] = mesh_tet_dof(p, t, q);
+      for (int a = 0; a < nl; ++a) {
         const int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
         if (ra < 0) continue;
-        for (int b = 0; b < 6; ++b) {
+        for (int b = 0; b < nl; ++b) {
           const int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
           if (rb < 0 || ra < rb) continue;
-          const cplx v = S6[a][b] - k * k * p.eps[t] * M6[a][b];
+          const cplx v = S12[a][b] - k * k * p.eps[t] * M12[a][b];
           if (v != cplx(0.0)) trips.push_back({ra, rb, v});
         }
       }
     }
     for (auto &fc : sub_faces[s]) {
-      double T3[3][3];
-      int64_t e[3];
-      mesh_face(p, fc.first.data(), T3, e);
-      for (int a = 0; a < 3; ++a) {
+      double T6[6][6];
+      int64_t e[6];
+      const int nf = mesh_face(p, fc.first.data(), T6, e);
+      for (int a = 0; a < nf; ++a) {
         const int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
         if (ra < 0) continue;
-        for (int b = 0; b < 3; ++b) {
+        for (int b = 0; b < nf; ++b) {
           const int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
-          if (rb < 0 || ra < rb || T3[a][b] == 0.0) continue;
-          trips.push_back({ra, rb, fc.second * T3[a][b]});
+          if (rb < 0 || ra < rb || T6[a][b] == 0.0) continue;
+          trips.push_back({ra, rb, fc.second * T6[a][b]});
         }
       }
     }
@@ -911,28 +1019,29 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   }
   // ---- global operator: every tetrahedron and the boundary triangles
   std::vector<Trip> g;
-  g.reserve((size_t)nt * 36);
+  g.reserve((size_t)nt * 36 * dpe * dpe);
   for (int64_t t = 0; t < nt; ++t) {
-    double S6[6][6], M6[6][6];
-    mesh_tet_matrices(p, t, S6, M6);
-    const int64_t *e = p.tet_e.data() + 6 * t;
-    for (int a = 0; a < 6; ++a) {
+    double S12[12][12], M12[12][12];
+    const int nl = mesh_tet_matrices(p, t, S12, M12);
+    int64_t e[12];
+    for (int q = 0; q < nl; ++q) e[q] = mesh_tet_dof(p, t, q);
+    for (int a = 0; a < nl; ++a) {
       if (p.pec[e[a]]) continue;
-      for (int b = 0; b < 6; ++b) {
+      for (int b = 0; b < nl; ++b) {
         if (p.pec[e[b]]) continue;
-        const cplx v = S6[a][b] - k * k * p.eps[t] * M6[a][b];
+        const cplx v = S12[a][b] - k * k * p.eps[t] * M12[a][b];
         if (v != cplx(0.0)) g.push_back({e[a], e[b], v});
       }
     }
   }
   for (auto &bf : p.bface) {
-    double T3[3][3];
-    int64_t e[3];
-    mesh_face(p, bf.data(), T3, e);
-    for (int a = 0; a < 3; ++a) {
+    double T6[6][6];
+    int64_t e[6];
+    const int nf = mesh_face(p, bf.data(), T6, e);
+    for (int a = 0; a < nf; ++a) {
       if (p.pec[e[a]]) continue;
-      for (int b = 0; b < 3; ++b)
-        if (!p.pec[e[b]] && T3[a][b] != 0.0) g.push_back({e[a], e[b], jk * T3[a][b]});
+      for (int b = 0; b < nf; ++b)
+        if (!p.pec[e[b]] && T6[a][b] != 0.0) g.push_back({e[a], e[b], jk * T6[a][b]});
     }
   }
   return finish_plan(ctx, trips, g);
@@ -960,7 +1069,11 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   p.h[2] = p.lz / p.nz;
   p.element = mesh->element;
   if (p.element != D3M_BRICK && p.element != D3M_TET) {
-    ctx.err = "d3m_setup: mesh element must be D3M_BRICK or D3M_TET";
+    ctx.err = "d3m_setup: mesh element must be D3M_BRICK, D3M_TET or D3M_TET_MESH";
+    return D3M_EINVAL;
+  }
+  if (mesh->order != 0 && mesh->order != 1) {
+    ctx.err = "d3m_setup: order 2 is for general meshes (D3M_TET_MESH)";
     return D3M_EINVAL;
   }
   if (mesh->vertices && p.element != D3M_TET) {
@@ -1615,10 +1728,12 @@ static TriRule radon7() {
 }
 
 // f_v -= int U . N_v dS over triangle Q with outward normal nvec; eids: the
-// edges of the vertex pairs 01 02 12, each pointing from the lower to the
-// higher local vertex.
+// dofs of the Whitney functions of the vertex pairs 01 02 12 (each pointing
+// from the lower to the higher local vertex), then, when nfun = 6, of their
+// edge-gradient functions.
 static void rhs_triangle(const Plan &p, const TriRule &R, const double Q[3][3], const double nvec[3],
-                         const int64_t eids[3], const double *khat_pol, int nrhs, double *rhs, int64_t ldb) {
+                         const int64_t *eids, int nfun, const double *khat_pol, int nrhs, double *rhs,
+                         int64_t ldb) {
   double g[3][3], ell[3];
   const double area = tri_grads(Q, g);
   for (int m = 0; m < 3; ++m) {
@@ -1628,17 +1743,18 @@ static void rhs_triangle(const Plan &p, const TriRule &R, const double Q[3][3], 
   }
   for (int q = 0; q < 7; ++q) {
     const double *mu = R.b[q];
-    double xyz[3], N[3][3];
+    double xyz[3], N[6][3];
     for (int a = 0; a < 3; ++a) xyz[a] = mu[0] * Q[0][a] + mu[1] * Q[1][a] + mu[2] * Q[2][a];
-    for (int m = 0; m < 3; ++m) {
-      const int a = TRI_E[m][0], b = TRI_E[m][1];
-      for (int c = 0; c < 3; ++c) N[m][c] = ell[m] * (mu[a] * g[b][c] - mu[b] * g[a][c]);
+    for (int m = 0; m < nfun; ++m) {
+      const int mm = m % 3, a = TRI_E[mm][0], b = TRI_E[mm][1];
+      const double sb = m < 3 ? -1.0 : 1.0;
+      for (int c = 0; c < 3; ++c) N[m][c] = ell[mm] * (mu[a] * g[b][c] + sb * mu[b] * g[a][c]);
     }
     const double w = R.w[q] * area;
     for (int r = 0; r < nrhs; ++r) {
       cplx U[3];
       incident_u(p, khat_pol + 9 * r, xyz, nvec, U);
-      for (int m = 0; m < 3; ++m) {
+      for (int m = 0; m < nfun; ++m) {
         const cplx dot = U[0] * N[m][0] + U[1] * N[m][1] + U[2] * N[m][2];
         const int64_t idx = eids[m] + ldb * r;
         rhs[2 * idx] -= w * dot.real();
@@ -1670,7 +1786,7 @@ static int rhs_planewave_tet(const Plan &p, const double *khat_pol, int nrhs, do
               FaceTri f;
               cell_face_tri(p, ci, cj, ck, o[t], f);
               const int64_t eids[3] = {e[f.loc[0]], e[f.loc[1]], e[f.loc[2]]};
-              rhs_triangle(p, R, f.Q, nvec, eids, khat_pol, nrhs, rhs, ldb);
+              rhs_triangle(p, R, f.Q, nvec, eids, 3, khat_pol, nrhs, rhs, ldb);
             }
           }
     }
@@ -1694,9 +1810,13 @@ static int rhs_planewave_mesh(const Plan &p, const double *khat_pol, int nrhs, d
     sub3(X, Q[0], to_opp);
     if (dot3(nvec, to_opp) > 0)
       for (int a = 0; a < 3; ++a) nvec[a] *= -1.0;
-    int64_t eids[3];
-    for (int m = 0; m < 3; ++m) eids[m] = mesh_edge_id(p, bf[TRI_E[m][0]], bf[TRI_E[m][1]]);
-    rhs_triangle(p, R, Q, nvec, eids, khat_pol, nrhs, rhs, ldb);
+    int64_t eids[6];
+    for (int m = 0; m < 3; ++m) {
+      const int64_t ge = mesh_edge_id(p, bf[TRI_E[m][0]], bf[TRI_E[m][1]]);
+      eids[m] = p.dpe * ge;
+      eids[3 + m] = 2 * ge + 1;
+    }
+    rhs_triangle(p, R, Q, nvec, eids, 3 * p.dpe, khat_pol, nrhs, rhs, ldb);
   }
   return D3M_OK;
 }

@@ -32,7 +32,7 @@ class Mesh(ctypes.Structure):
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
                 ("element", ctypes.c_int32), ("vertices", ctypes.POINTER(ctypes.c_double)),
                 ("n_vertices", ctypes.c_int64), ("n_tets", ctypes.c_int64),
-                ("tets", ctypes.POINTER(ctypes.c_int64))]
+                ("tets", ctypes.POINTER(ctypes.c_int64)), ("order", ctypes.c_int32)]
 
 
 class Materials(ctypes.Structure):
@@ -148,10 +148,11 @@ class Solver:
                  leaf_max=64, refine_tol=1e-10, max_refine=10, stream=None, profile=False, panel_kernel=0,
                  update_kernel=0, autotune=0, autotune_cache=None, lookahead=0, refine_method=0,
                  gmres_restart=0, gmres_tol=0.0, alpha=None, solve_kernel=0, lm_weight=0, element=BRICK,
-                 vertices=None, tets=None, gcuts=None):
+                 vertices=None, tets=None, gcuts=None, order=1):
         """Lattice meshes: nx..lz, cuts cx, cy, cz (cell indices).  General
         tetrahedral meshes (element=TET_MESH): vertices (n, 3), tets (m, 4)
-        and gcuts = (gx, gy, gz) coordinate cuts; nx..lz and cx..cz unused."""
+        and gcuts = (gx, gy, gz) coordinate cuts, order 1 (Whitney) or 2 (two
+        dofs per edge); nx..lz and cx..cz unused."""
         self.lib = load()
         self._eps = np.ascontiguousarray(np.asarray(eps, np.complex128).view(np.float64))
         self._vert = None if vertices is None else np.ascontiguousarray(np.asarray(vertices, np.float64))
@@ -163,7 +164,7 @@ class Solver:
         mesh = Mesh(nx, ny, nz, lx, ly, lz, int(element),
                     None if self._vert is None else _ptr(self._vert, ctypes.c_double),
                     0 if self._vert is None else len(self._vert), 0 if self._tets is None else len(self._tets),
-                    None if self._tets is None else _ptr(self._tets, ctypes.c_int64))
+                    None if self._tets is None else _ptr(self._tets, ctypes.c_int64), int(order))
         mat = Materials(_ptr(self._eps, ctypes.c_double),
                         None if self._pec is None else _ptr(self._pec, ctypes.c_uint8))
         if self._gcuts is not None:
@@ -194,6 +195,7 @@ class Solver:
         kw.setdefault("vertices", getattr(w, "vertices", None))
         kw.setdefault("tets", getattr(w, "tets", None))
         kw.setdefault("gcuts", getattr(w, "gcuts", None))
+        kw.setdefault("order", getattr(w, "order", 1))
         return cls(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, w.eps, w.k, w.cx, w.cy, w.cz, pec=w.pec_edge,
                    precision=precision, **kw)
 

@@ -256,6 +256,9 @@ def test_tetrahedral_uneven_partition(precision):
 MESH = [
     lambda: W.delaunay(5, 4, 4, 2, 2, 2, seed=3, nrhs=2),
     lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6, nrhs=2),
+    # complete first order (two dofs per edge)
+    lambda: W.delaunay(5, 4, 4, 2, 2, 2, seed=3, nrhs=2, order=2),
+    lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6, nrhs=2, order=2),
 ]
 
 
@@ -263,8 +266,9 @@ MESH = [
 @pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
 def test_general_tetrahedral_meshes(mk, precision):
     """Delaunay meshes (arbitrary connectivity, subdomains by centroid, blocks
-    between grid-diagonal subdomains): E against the oracle's global solve
-    element by element, lambda against the oracle's D3M multipliers."""
+    between grid-diagonal subdomains), Whitney and complete first-order
+    functions: E against the oracle's global solve element by element, lambda
+    against the oracle's D3M multipliers."""
     _need_gpu()
     w = mk()
     s, x, info, f = _solve_case(w, precision)

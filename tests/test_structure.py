@@ -32,6 +32,8 @@ CASES = [
     ("mesh-lattice", lambda: W.as_mesh(W.tetrahedral(W.tiny(6, 5, 4, 2, 2, 1, seed=1), 0.1)), 16),
     ("delaunay-2x2x2", lambda: W.delaunay(5, 4, 4, 2, 2, 2, seed=3), 16),
     ("delaunay-3x2x2", lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6), 32),
+    # complete first order: two dofs per edge, kept together by the ordering
+    ("delaunay-order2", lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6, order=2), 32),
 ]
 LARGE = {"config2", "config3", "config4", "tet-config3"}
 
@@ -95,12 +97,12 @@ def test_setup_rejects_bad_input():
     assert e.value.code == d3m.D3M_EINVAL
 
 
-@pytest.mark.parametrize("tet", [False, True, "mesh"])
+@pytest.mark.parametrize("tet", [False, True, "mesh", "order2"])
 def test_rhs_planewave_matches_oracle(tet):
     from oracle import fem
     w = W.tiny(5, 4, 3, 1, 1, 1, seed=8, nrhs=3)
-    if tet == "mesh":
-        w = W.delaunay(5, 4, 3, 2, 1, 1, seed=8, nrhs=3)
+    if tet in ("mesh", "order2"):
+        w = W.delaunay(5, 4, 3, 2, 1, 1, seed=8, nrhs=3, order=2 if tet == "order2" else 1)
     elif tet:
         w = W.tetrahedral(w, 0.1)
     s = d3m.Solver.from_workload(w)
@@ -123,7 +125,8 @@ def _mesh_kw(w, **over):
     return kw
 
 
-@pytest.mark.parametrize("what", ["degenerate", "vertex-id", "no-cuts", "cuts-order", "lm_weight", "nonmanifold"])
+@pytest.mark.parametrize("what", ["degenerate", "vertex-id", "no-cuts", "cuts-order", "lm_weight", "nonmanifold",
+                                  "order", "pec-split"])
 def test_setup_rejects_bad_general_meshes(what):
     """A degenerate tetrahedron, a vertex id out of range, missing or
     unordered coordinate cuts, the mass-weighted multiplier map and a
@@ -144,6 +147,12 @@ def test_setup_rejects_bad_general_meshes(what):
         kw = _mesh_kw(w, gcuts=(w.gcuts[0][::-1], w.gcuts[1], w.gcuts[2]))
     elif what == "lm_weight":
         kw = _mesh_kw(w, lm_weight=1)
+    elif what == "order":
+        kw = _mesh_kw(w, order=3)
+    elif what == "pec-split":   # order 2: the two dofs of an edge marked differently
+        pec = np.zeros(2 * w.n_edges, np.uint8)
+        pec[4] = 1
+        kw = _mesh_kw(w, order=2, pec=pec)
     else:   # two more tetrahedra on the face (t0, t1, t2) of tetrahedron 0
         t, V = tets[0], w.vertices
         n = np.cross(V[t[1]] - V[t[0]], V[t[2]] - V[t[0]])
@@ -158,6 +167,15 @@ def test_setup_rejects_bad_general_meshes(what):
         assert "more than two" in str(ei.value)
     if what == "degenerate":
         assert "degenerate" in str(ei.value)
+    if what == "pec-split":
+        assert "both dofs" in str(ei.value)
+
+
+def test_order2_is_for_general_meshes():
+    w = W.tetrahedral(W.tiny(3, 3, 3, 1, 1, 1, seed=1), 0.1)
+    with pytest.raises(d3m.D3MError) as ei:
+        d3m.Solver.from_workload(w, order=2)
+    assert ei.value.code == d3m.D3M_EINVAL and "D3M_TET_MESH" in str(ei.value)
 
 
 @pytest.mark.parametrize("what", ["inverted", "off-plane", "brick-with-vertices", "element"])
@@ -222,7 +240,7 @@ def test_setup_rejects_bad_options(kw):
     assert "d3m_setup" in str(ei.value)
 
 
-@pytest.mark.parametrize("tet", [False, True, "mesh"])
+@pytest.mark.parametrize("tet", [False, True, "mesh", "order2"])
 def test_interface_coefficient_matches_oracle_entries(tet):
     """d3m_options.alpha sets the interface loss/gain term: the library's
     assembled entries of M equal the oracle's subdomain matrices for a
@@ -231,8 +249,8 @@ def test_interface_coefficient_matches_oracle_entries(tet):
     against the oracle's quadrature."""
     from oracle import decomp
     w = W.tiny(4, 3, 3, 2, 1, 1, seed=6)
-    if tet == "mesh":
-        w = W.delaunay(5, 4, 4, 2, 2, 2, seed=3)
+    if tet in ("mesh", "order2"):
+        w = W.delaunay(5, 4, 4, 2, 2, 2, seed=3, order=2 if tet == "order2" else 1)
     elif tet:
         w = W.tetrahedral(W.tiny(4, 3, 3, 2, 2, 1, seed=6), 0.1)
     w.alpha = 2.5 - 0.7j
