@@ -140,9 +140,10 @@ typedef struct {
  * strictly increasing coordinates; a tetrahedron belongs to subdomain
  * (ix, iy, iz) when its centroid ((v0 + v1) + v2) + v3 over 4 satisfies
  * c_x >= gx[ix] (or ix = 0) and c_x < gx[ix+1] (or ix = px - 1), likewise in
- * y and z.  An edge is copied into every subdomain holding one of its
- * tetrahedra; an extra copy with no earlier copy in a grid-face-adjacent
- * subdomain is tied by its multiplier to the lowest-index copy. */
+ * y and z; every box must hold a tetrahedron (D3M_EINVAL otherwise).  An
+ * edge is copied into every subdomain holding one of its tetrahedra; an
+ * extra copy with no earlier copy in a grid-face-adjacent subdomain is tied
+ * by its multiplier to the lowest-index copy. */
 typedef struct {
   int32_t px, py, pz;
   const int32_t *cx, *cy, *cz;

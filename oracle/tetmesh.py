@@ -292,6 +292,8 @@ def decompose(w, with_matrices=True):
     g = grid_of(w)
     sub, parts = subdomain_of(w, g)
     nsub = parts[0] * parts[1] * parts[2]
+    if np.bincount(sub, minlength=nsub).min() == 0:
+        raise ValueError("a subdomain box holds no tetrahedron")
     free = np.ones(g.n_edges, bool)
     if w.pec_edge is not None:   # one byte per dof
         free[np.asarray(w.pec_edge) != 0] = False

@@ -855,6 +855,11 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     tsub[t] = sub_id(p, ix[0], ix[1], ix[2]);
     sub_tets[tsub[t]].push_back(t);
   }
+  for (int s = 0; s < p.nsub; ++s)
+    if (sub_tets[s].empty()) {
+      ctx.err = "d3m_setup: a subdomain box holds no tetrahedron";
+      return D3M_EINVAL;
+    }
   p.sub_lo.assign(p.nsub, {0, 0, 0});
   p.sub_hi.assign(p.nsub, {0, 0, 0});
   p.sub_edges.assign(p.nsub, {});  // free dofs of each subdomain

@@ -126,7 +126,7 @@ def _mesh_kw(w, **over):
 
 
 @pytest.mark.parametrize("what", ["degenerate", "vertex-id", "no-cuts", "cuts-order", "lm_weight", "nonmanifold",
-                                  "order", "pec-split"])
+                                  "order", "pec-split", "empty-box"])
 def test_setup_rejects_bad_general_meshes(what):
     """A degenerate tetrahedron, a vertex id out of range, missing or
     unordered coordinate cuts, the mass-weighted multiplier map and a
@@ -149,6 +149,9 @@ def test_setup_rejects_bad_general_meshes(what):
         kw = _mesh_kw(w, lm_weight=1)
     elif what == "order":
         kw = _mesh_kw(w, order=3)
+    elif what == "empty-box":   # a box too thin to hold a centroid
+        gx = np.array([0.0, 0.15, 0.1501, 0.3])
+        kw = _mesh_kw(w, gcuts=(gx, w.gcuts[1], w.gcuts[2]))
     elif what == "pec-split":   # order 2: the two dofs of an edge marked differently
         pec = np.zeros(2 * w.n_edges, np.uint8)
         pec[4] = 1
@@ -169,6 +172,36 @@ def test_setup_rejects_bad_general_meshes(what):
         assert "degenerate" in str(ei.value)
     if what == "pec-split":
         assert "both dofs" in str(ei.value)
+    if what == "empty-box":
+        assert "no tetrahedron" in str(ei.value)
+
+
+def test_general_mesh_with_pec_region_matches_oracle():
+    """A PEC block inside a Delaunay mesh (the dofs of every edge whose
+    midpoint lies in it removed): plan bit-exact against the oracle, and the
+    oracle's D3M solution equals its global solution with zero field there."""
+    from oracle import d3m as od3m, fem, tetmesh
+    w = W.delaunay(6, 5, 5, 2, 2, 1, seed=7, nrhs=2)
+    g = tetmesh.grid_of(w)
+    mid = 0.5 * (g.V[g.edges[:, 0]] + g.V[g.edges[:, 1]])
+    inside = np.all((mid > [0.2, 0.15, 0.15]) & (mid < [0.35, 0.3, 0.3]), axis=1)
+    assert inside.sum() > 10
+    w.pec_edge = inside.astype(np.uint8)
+    f = fem.rhs_planewave(w)
+    xg = fem.solve_global(w, f)
+    r = od3m.solve(w, f, return_all=True)
+    assert np.abs(r["x"] - xg).max() < 1e-10 * np.abs(xg).max() and np.all(xg[inside] == 0)
+    dec = decomp.decompose(w)
+    plan = ordering.build_plan(dec, leaf_max=16)
+    rr, cc = ordering.saddle_pattern(dec, plan)
+    ordering.symbolic(plan, rr, cc)
+    s = d3m.Solver.from_workload(w, leaf_max=16)
+    rng, mm = s.structure(d3m.SN_RANGE), s.structure(d3m.M_MAP)
+    assert np.array_equal(rng[:, 0], plan.sn_start) and np.array_equal(rng[:, 1], plan.sn_end)
+    assert np.array_equal(mm[:, 0], plan.m_sub) and np.array_equal(mm[:, 1], plan.m_edge)
+    assert np.array_equal(s.structure(d3m.SN_PARENT), plan.parent)
+    assert s.stats()["n_free"] == w.n_edges - inside.sum()
+    s.close()
 
 
 def test_order2_is_for_general_meshes():
