@@ -418,8 +418,18 @@ def precision_summary(r, peaks, prec_tag, config, nrhs):
 def bench_config(w, config, arena_bytes):
     """The `config` object of the JSON line (the same for both arms);
     arena_bytes = 8 sum m^2 over the fronts (complex64 front storage)."""
-    cells = ("bricks" if getattr(w, "element", "brick") == "brick"
-             else "cells x 6 jittered tetrahedra")
+    el = getattr(w, "element", "brick")
+    if el == "mesh":
+        return {"workload": (f"config{config} box as a Delaunay mesh of {(w.nx + 1) * (w.ny + 1) * (w.nz + 1)} "
+                             f"jittered points ({w.n_cells} tetrahedra, order {w.order}, {w.n_edges} dofs), "
+                             f"{w.lx:g}x{w.ly:g}x{w.lz:g} wavelengths, {'x'.join(map(str, w.partition))} "
+                             f"coordinate-box subdomains, {w.nrhs} plane waves"),
+                "nrhs": w.nrhs, "precision": "mixed+refine (headline)",
+                "l2": ("every step refactors the whole front arena (%.2f GB in complex64; L2 is 0.13 GB)"
+                       % (arena_bytes / 1e9)),
+                "step": f"d3m_factor + d3m_solve({w.nrhs} RHS) incl. refinement to resid<=1e-10",
+                "value_def": "algorithmic flops (factor + one substitution pass) / step time"}
+    cells = "bricks" if el == "brick" else "cells x 6 jittered tetrahedra"
     return {"workload": (f"config{config}: {w.nx}x{w.ny}x{w.nz} {cells} ({w.n_edges} edges), "
                          f"{w.lx:g}x{w.ly:g}x{w.lz:g} wavelengths, {'x'.join(map(str, w.partition))} subdomains "
                          f"(cuts {[int(v) for v in w.cx]}/{[int(v) for v in w.cy]}/{[int(v) for v in w.cz]}), "
@@ -454,8 +464,12 @@ def main():
     ap.add_argument("--autotune-cache", default=None,
                     help="file prefix for the tuned factor schedules (read when they match, else written); "
                          "lets a profiler run reuse the schedule of a plain run")
-    ap.add_argument("--element", default="brick", choices=["brick", "tet"],
-                    help="tet: the same workload on six jittered tetrahedra per cell")
+    ap.add_argument("--element", default="brick", choices=["brick", "tet", "mesh"],
+                    help="tet: the same workload on six jittered tetrahedra per cell; mesh: its box as a "
+                         "Delaunay mesh of the jittered lattice points (general connectivity), the same "
+                         "subdomain counts as equal coordinate cuts, the same plane waves")
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
+                    help="--element mesh: 2 = complete first-order elements (two dofs per edge)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     from paper_2002_05018_gb300 import workloads as W
@@ -464,6 +478,10 @@ def main():
         w = W.with_waves(w, args.nrhs, seed=args.config)
     if args.element == "tet":
         w = W.tetrahedral(w, 0.1)
+    elif args.element == "mesh":
+        import dataclasses
+        wm = W.delaunay(w.nx, w.ny, w.nz, *w.partition, seed=args.config, h=w.lx / w.nx, order=args.order)
+        w = dataclasses.replace(wm, k=w.k, khat=w.khat, pol=w.pol)
     if args.impl == "reference":
         # the reference arm is the CPU oracle (no GPU, no library): rank 0 only
         if rank != 0:

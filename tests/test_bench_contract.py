@@ -46,6 +46,19 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
+def test_reference_arm_on_a_general_mesh():
+    """--element mesh: the reference arm runs the oracle on the Delaunay form
+    of the workload and reports the same config the GPU arm would."""
+    code = ("import runpy, sys; sys.argv = ['bench.py', '--impl', 'reference', '--config', '1', '--element', "
+            "'mesh', '--order', '2', '--steps', '1', '--warmup', '3']; runpy.run_path('bench.py', run_name='__main__')")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["value"] > 0 and "Delaunay mesh" in d["config"]["workload"] and "order 2" in d["config"]["workload"]
+
+
 def test_set_profile_argument_checks():
     lib = d3m.load()
     assert lib.d3m_set_profile(None, 1) == d3m.D3M_EINVAL
