@@ -4,9 +4,10 @@
  *
  * Problem (Theory section, decomposed BVP): curl curl E - k^2 eps_r E = 0 in
  * an axis-aligned box of nx*ny*nz lattice cells, meshed by bricks or by six
- * tetrahedra per cell (d3m_mesh) with lowest-order Nedelec edge elements, a
- * first-order absorbing boundary condition on the whole
- * outer boundary driven by incident plane waves, mu_r = 1.  The box is cut
+ * tetrahedra per cell, or on a general tetrahedral mesh (d3m_mesh), with
+ * lowest-order Nedelec edge elements (complete first-order ones on general
+ * meshes if asked), a first-order absorbing boundary condition on the whole
+ * outer boundary driven by incident plane waves, mu_r = 1.  The domain is cut
  * into px*py*pz subdomains; the library assembles the decomposed system of
  * Eq. (1), [[A, D], [D^T, 0]] [E; lambda] = [f; 0], and factors it with the
  * paper's seven main steps: dense domain matrices K_D, assembly of the
@@ -23,7 +24,8 @@
  *    nx*(j + (ny+1)*k), y-edge = NX + i + (nx+1)*(j + ny*k), z-edge = NX + NY
  *    + i + (nx+1)*(j + (ny+1)*k), NX = nx(ny+1)(nz+1), NY = (nx+1)ny(nz+1);
  *    every edge points from its start node towards increasing coordinates;
- *  - cells are numbered i + nx*(j + ny*k); subdomains ix + px*(iy + py*iz);
+ *  - cells are numbered i + nx*(j + ny*k) (on general meshes: the
+ *    tetrahedra in input order); subdomains ix + px*(iy + py*iz);
  *  - RHS / solution blocks are column-major n_edges x nrhs with a leading
  *    dimension >= n_edges, in global edge numbering with PEC edges present
  *    (their solution rows are returned as 0);
