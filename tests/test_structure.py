@@ -231,11 +231,13 @@ def test_setup_rejects_bad_tetrahedral_meshes(what):
     assert ei.value.code == d3m.D3M_EINVAL and "d3m_setup" in str(ei.value)
 
 
-def test_level_table_matches_tree_heights():
+@pytest.mark.parametrize("mk", [lambda: W.make(1), lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6, order=2)])
+def test_level_table_matches_tree_heights(mk):
     """D3M_LEVELS: fronts grouped by height in the supernodal elimination tree
     (leaves 0, a parent one above its highest child), computed here from the
-    oracle's plan; per-level flops add up to the factorisation's total."""
-    w = W.make(1)
+    oracle's plan; per-level flops add up to the factorisation's total (bricks
+    and a complete first-order Delaunay mesh)."""
+    w = mk()
     dec = decomp.decompose(w)
     plan = ordering.build_plan(dec, leaf_max=64)
     r, c = ordering.saddle_pattern(dec, plan)
