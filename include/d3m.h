@@ -176,8 +176,9 @@ typedef struct {
                            fp32 accumulation in tensor memory */
   int32_t autotune;     /* 0 = tune on the first d3m_factor (default): the update
                            kernel and the panel cluster size of every tree level
-                           are timed with CUDA events over two trial
-                           factorisations and the faster kept; 1 = off (fixed
+                           are timed with CUDA events over trial factorisations
+                           (three in MIXED, two in FP64) and the faster kept; 1 =
+                           off (fixed
                            defaults: FMA updates, smallest fitting cluster) */
   const char *autotune_cache; /* optional file: read the tuned schedule from it when
                            it matches this problem, write it after tuning; NULL = none */

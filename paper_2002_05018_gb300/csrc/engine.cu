@@ -3472,7 +3472,8 @@ static int enter(Ctx &c) {
 
 // ---- autotuner: per tree level, the trailing-update kernel (mixed: fp32 FMA
 // or tcgen05) and the panel cluster size (smallest that fits, or twice that),
-// chosen by timing two trial factorisations with CUDA events per level.
+// chosen by timing trial factorisations with CUDA events per level (three in
+// mixed precision, two in fp64: trials A, B and C below).
 static std::string tune_signature(const Ctx &c) {
   const Plan &P = c.plan;
   char buf[256];
