@@ -328,3 +328,44 @@ def test_mass_weighted_multiplier_map_matches_oracle_entries(tet):
         D, loc = Ds[int(sub)]
         assert abs(D[loc[int(e)], int(r) - lam_start] - (re + 1j * im)) < 1e-15
     assert sel.sum() == sum(int((np.abs(D) > 0).sum()) for D, _ in Ds.values())
+
+
+def test_c_program_drives_the_abi(tmp_path):
+    """tests/c_abi/abi_check.c, compiled with gcc against include/d3m.h and
+    linked to libd3m.so, sets up a brick mesh and a complete first-order
+    general mesh from plain C; its counts and RHS norms equal the binding's for
+    the same inputs (the header's struct layouts as C sees them)."""
+    import math
+    import os
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2002_05018_gb300")
+    d3m.load()   # the library must have been built (raises otherwise)
+    exe = str(tmp_path / "abi_check")
+    cc = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+                         os.path.join(root, "tests", "c_abi", "abi_check.c"), "-L", pkg, "-ld3m",
+                         "-Wl,-rpath," + pkg, "-lm", "-o", exe], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, run.stdout + run.stderr
+    out = dict(ln.split() for ln in run.stdout.splitlines())
+    assert out["ok"] == "1"
+    kp = np.array([[0, 0, 1, 1, 0, 0, 0, 0, 0]], float)
+    k = 2.0 * math.pi
+    eps = (1.0 + 0.1 * np.arange(16)) - 0.05j
+    brick = d3m.Solver(4, 2, 2, 0.4, 0.2, 0.2, eps, k, [0, 2, 4], [0, 2], [0, 2])
+    v = np.array([[0.2 * (n & 1), 0.2 * ((n >> 1) & 1), 0.2 * ((n >> 2) & 1)] for n in range(8)])
+    tets = np.array([[0, 1, 3, 7], [0, 1, 5, 7], [0, 2, 3, 7], [0, 2, 6, 7], [0, 4, 5, 7], [0, 4, 6, 7]])
+    mesh = d3m.Solver(0, 0, 0, 0.0, 0.0, 0.0, np.full(6, 2.0 + 0j), k, [0], [0], [0], element=d3m.TET_MESH,
+                      vertices=v, tets=tets, gcuts=([0.0, 0.1, 0.2], [0.0, 0.2], [0.0, 0.2]), order=2)
+    for tag, s in (("brick", brick), ("mesh", mesh)):
+        st = s.stats()
+        for key in ("n_edges", "n_lm", "n_m", "n_fronts"):
+            assert int(out[f"{tag}_{key}"]) == st[key], (tag, key)
+        assert int(out[f"{tag}_m_map_bytes"]) == 16 * st["n_m"]
+        f = s.rhs_planewave(kp)
+        assert abs(float(out[f"{tag}_rhs_l1"]) - (np.abs(f.real).sum() + np.abs(f.imag).sum())) < 1e-12
+        s.close()
