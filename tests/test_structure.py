@@ -369,3 +369,43 @@ def test_c_program_drives_the_abi(tmp_path):
         f = s.rhs_planewave(kp)
         assert abs(float(out[f"{tag}_rhs_l1"]) - (np.abs(f.real).sum() + np.abs(f.imag).sum())) < 1e-12
         s.close()
+
+
+def test_entry_points_refuse_bad_arguments_before_any_device_work():
+    """Host-side argument checks of the ABI (run on CPU: each returns before
+    any CUDA call): null pointers, nrhs <= 0, leading dimensions shorter than
+    n_edges, out-of-range fronts and structure kinds, bad dense-front sizes."""
+    import ctypes
+    lib = d3m.load()
+    s = d3m.Solver.from_workload(W.tiny(4, 3, 3, 2, 1, 1, seed=2))
+    h, n = s.h, s.n_edges
+    buf = np.zeros(4 * n + 64)
+    p = buf.ctypes.data
+    E = d3m.D3M_EINVAL
+    for fn in (lib.d3m_solve, lib.d3m_solve_host, lib.d3m_solve_adjoint):
+        assert fn(h, p, n, p, n, 0, None) == E            # no right-hand side
+        assert fn(h, p, n, p, n, -3, None) == E
+        assert fn(h, p, n - 1, p, n, 1, None) == E        # ldb < n_edges
+        assert fn(h, p, n, p, n - 1, 1, None) == E        # ldx < n_edges
+        assert fn(h, None, n, p, n, 1, None) == E
+        assert fn(h, p, n, None, n, 1, None) == E
+        assert fn(None, p, n, p, n, 1, None) == E
+    assert lib.d3m_grad_eps(h, p, n, p, n, 0, p) == E
+    assert lib.d3m_grad_eps(h, p, n - 1, p, n, 1, p) == E
+    assert lib.d3m_grad_eps(h, p, n, p, n, 1, None) == E
+    assert lib.d3m_rhs_planewave(h, p, 1, p, n - 1) == E
+    assert lib.d3m_rhs_planewave(h, p, -1, p, n) == E
+    assert lib.d3m_rhs_planewave(h, None, 1, p, n) == E
+    m_out, p_out = ctypes.c_int32(), ctypes.c_int32()
+    nf = s.stats()["n_fronts"]
+    assert lib.d3m_export_front(h, nf, ctypes.byref(m_out), ctypes.byref(p_out), None, None, None) == E
+    assert lib.d3m_export_front(h, -1, ctypes.byref(m_out), ctypes.byref(p_out), None, None, None) == E
+    nbytes = ctypes.c_size_t(0)
+    assert lib.d3m_structure(h, 99, None, ctypes.byref(nbytes)) == E
+    assert lib.d3m_structure(h, d3m.SN_RANGE, None, None) == E
+    assert lib.d3m_stats_get(h, None) == E
+    ip = np.zeros(8, np.int32).ctypes.data
+    for m, pp, batch in ((0, 0, 1), (4, 5, 1), (4, -1, 1), (4, 2, 0)):
+        assert lib.d3m_dense_ldlt(m, pp, batch, p, ip, p, ip, None, 0) == E, (m, pp, batch)
+    assert lib.d3m_dense_ldlt(4, 2, 1, None, ip, p, ip, None, 0) == E
+    s.close()
