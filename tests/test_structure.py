@@ -409,3 +409,37 @@ def test_entry_points_refuse_bad_arguments_before_any_device_work():
         assert lib.d3m_dense_ldlt(m, pp, batch, p, ip, p, ip, None, 0) == E, (m, pp, batch)
     assert lib.d3m_dense_ldlt(4, 2, 1, None, ip, p, ip, None, 0) == E
     s.close()
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_structure_bit_exact_on_random_meshes(case):
+    """Seeded random meshes (bricks, lattice tetrahedra, Delaunay meshes of
+    order 1 and 2; random sizes, partitions, cut jitter and leaf sizes): the
+    library's plan equals the oracle's bit for bit."""
+    rng = np.random.default_rng(1000 + case)
+    nx, ny, nz = [int(v) for v in rng.integers(2, 8, 3)]
+    px, py, pz = [int(rng.integers(1, min(3, n) + 1)) for n in (nx, ny, nz)]
+    kind, seed, leaf = case % 4, int(rng.integers(0, 1000)), int(rng.integers(4, 40))
+    if kind < 2:
+        w = W.tiny(nx, ny, nz, px, py, pz, seed=seed)
+        if kind == 1:
+            w = W.tetrahedral(w, 0.1)
+    else:
+        w = W.delaunay(nx, ny, nz, px, py, pz, seed=seed, order=kind - 1,
+                       jitter=float(rng.uniform(0.05, 0.35)))
+    dec = decomp.decompose(w)
+    plan = ordering.build_plan(dec, leaf_max=leaf)
+    r, c = ordering.saddle_pattern(dec, plan)
+    ordering.symbolic_merge(plan, r, c)
+    s = d3m.Solver.from_workload(w, leaf_max=leaf)
+    rng_, mm = s.structure(d3m.SN_RANGE), s.structure(d3m.M_MAP)
+    assert np.array_equal(rng_[:, 0], plan.sn_start) and np.array_equal(rng_[:, 1], plan.sn_end)
+    assert np.array_equal(mm[:, 0], plan.m_sub) and np.array_equal(mm[:, 1], plan.m_edge)
+    assert np.array_equal(s.structure(d3m.SN_PARENT), plan.parent)
+    st = s.structure(d3m.SN_STRUCT)
+    n = len(plan.sn_start)
+    for q in range(n):
+        assert np.array_equal(st[n + 1:][st[q]:st[q + 1]], plan.struct[q]), q
+    lm = s.structure(d3m.LM)
+    assert np.array_equal(lm[:, 0], dec.lm_edge) and np.array_equal(lm[:, 1], dec.lm_plus)
+    s.close()
