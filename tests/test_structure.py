@@ -443,3 +443,38 @@ def test_structure_bit_exact_on_random_meshes(case):
     lm = s.structure(d3m.LM)
     assert np.array_equal(lm[:, 0], dec.lm_edge) and np.array_equal(lm[:, 1], dec.lm_plus)
     s.close()
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_entries_match_oracle_on_random_meshes(case):
+    """Every assembled entry of M (element, interface and absorbing terms,
+    multiplier couplings) on seeded random lattice-tetrahedral and Delaunay
+    meshes equals the oracle's subdomain matrices and D_i."""
+    rng = np.random.default_rng(2000 + case)
+    nx, ny, nz = [int(v) for v in rng.integers(2, 6, 3)]
+    px, py, pz = [int(rng.integers(1, min(3, n) + 1)) for n in (nx, ny, nz)]
+    seed = int(rng.integers(0, 1000))
+    if case % 3 == 0:
+        w = W.tetrahedral(W.tiny(nx, ny, nz, px, py, pz, seed=seed), 0.1)
+    else:
+        w = W.delaunay(nx, ny, nz, px, py, pz, seed=seed, order=1 if case % 3 == 1 else 2)
+    s = d3m.Solver.from_workload(w)
+    ent, mm, st = s.structure(d3m.M_ENTRIES), s.structure(d3m.M_MAP), s.stats()
+    s.close()
+    dec = decomp.decompose(w)
+    lam0 = st["n_m"] - st["n_lm"]
+    A = {sd.index: (sd.A.toarray(), {int(e): i for i, e in enumerate(sd.edges)}) for sd in dec.subs}
+    Ds = {sd.index: decomp.D_matrix(dec, sd).toarray() for sd in dec.subs}
+    scale = max(np.abs(a).max() for a, _ in A.values())
+    for r, c, re, im in ent:
+        r, c = int(r), int(c)
+        v = re + 1j * im
+        if r < lam0:
+            sub, er = mm[r]
+            _, ec = mm[c]
+            Ai, loc = A[int(sub)]
+            assert abs(Ai[loc[int(er)], loc[int(ec)]] - v) < 1e-12 * scale
+        else:
+            sub, e = mm[c]
+            _, loc = A[int(sub)]
+            assert abs(Ds[int(sub)][loc[int(e)], r - lam0] - v) < 1e-15
