@@ -1460,7 +1460,7 @@ int build_plan(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *mat, double 
   std::vector<Trip> g;
   {
     g.reserve((size_t)ncell * p.cell_ne * p.cell_ne);
-    static thread_local double Tb[6][MAX_CELL_NE][MAX_CELL_NE];
+    double Tb[6][MAX_CELL_NE][MAX_CELL_NE];  // the cell's outer-boundary face matrices
     for (int ck = 0; ck < p.nz; ++ck)
       for (int cj = 0; cj < p.ny; ++cj)
         for (int ci = 0; ci < p.nx; ++ci) {
