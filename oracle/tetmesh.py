@@ -15,6 +15,12 @@ orientation).  Discretisation as for the lattice tetrahedra of fem.py:
   component along its own edge is 1 - 2 s / l_ij (s from i) and which has no
   curl and no orientation sign; dof 2 e is the edge's Whitney function, dof
   2 e + 1 its gradient function;
+- order 3 (curl-complete second order, hierarchical; the first-kind space of
+  degree 2): order 2 plus two functions per face with vertices a < b < c
+  (global ids): l_ab lam_c W_ab and l_ac lam_b W_ac (W the unscaled Whitney
+  function), whose tangential traces vanish on every edge and every other
+  face; face dofs follow the edge dofs (2 n_edges + 2 f, + 1); element and face
+  integrals by collapsed-coordinate Gauss rules exact to degree 5;
 - element integrals by the degree-2 four-point rule, face integrals by the
   edge-midpoint rule (both exact here), the incident-field RHS by the 7-point
   rule per boundary triangle (fem.tri_quadrature);
@@ -65,25 +71,37 @@ class MeshGrid:
         self.V = np.asarray(vertices, np.float64)
         self.T = np.asarray(tets, np.int64)
         self.order = int(order)
-        if self.order not in (1, 2):
-            raise ValueError("order must be 1 or 2")
+        if self.order not in (1, 2, 3):
+            raise ValueError("order must be 1, 2 or 3")
         nt = len(self.T)
         self.n_nodes = len(self.V)
         self.n_cells = nt
         loc = np.stack([np.sort(self.T[:, [a, b]], axis=1) for a, b in PAIRS], 1)
         self.edges, inv = np.unique(loc.reshape(-1, 2), axis=0, return_inverse=True)
         self.n_geo = len(self.edges)
-        self.n_edges = self.order * self.n_geo
         self.tet_edges = inv.reshape(nt, 6)
-        sg = np.stack([np.where(self.T[:, a] < self.T[:, b], 1.0, -1.0) for a, b in PAIRS], 1)
-        if self.order == 1:
-            self.tet_dofs, self.tet_sign = self.tet_edges, sg
-        else:
-            self.tet_dofs = np.concatenate([2 * self.tet_edges, 2 * self.tet_edges + 1], 1)
-            self.tet_sign = np.concatenate([sg, np.ones_like(sg)], 1)
         fl = np.stack([np.sort(self.T[:, list(f)], axis=1) for f in _FACE_OF], 1).reshape(-1, 3)
         self.faces, finv, cnt = np.unique(fl, axis=0, return_inverse=True, return_counts=True)
         finv = finv.ravel()
+        self.tet_faces = finv.reshape(nt, 4)
+        # local vertex indices of each face, sorted by global id
+        self.face_loc = np.stack([np.array(f)[np.argsort(self.T[:, list(f)], axis=1)] for f in _FACE_OF], 1)
+        sg = np.stack([np.where(self.T[:, a] < self.T[:, b], 1.0, -1.0) for a, b in PAIRS], 1)
+        dpe = min(self.order, 2)
+        self.dpe = dpe
+        self.n_edges = dpe * self.n_geo + (2 * len(self.faces) if self.order == 3 else 0)   # dofs
+        if self.order == 1:
+            self.tet_dofs, self.tet_sign = self.tet_edges, sg
+            self.tet_ents = self.tet_edges
+        else:
+            self.tet_dofs = np.concatenate([2 * self.tet_edges, 2 * self.tet_edges + 1], 1)
+            self.tet_sign = np.concatenate([sg, np.ones_like(sg)], 1)
+            self.tet_ents = self.tet_edges
+        if self.order == 3:
+            fd = 2 * self.n_geo + 2 * self.tet_faces
+            self.tet_dofs = np.concatenate([self.tet_dofs, np.stack([fd, fd + 1], 2).reshape(nt, 8)], 1)
+            self.tet_sign = np.concatenate([self.tet_sign, np.ones((nt, 8))], 1)
+            self.tet_ents = np.concatenate([self.tet_edges, self.n_geo + self.tet_faces], 1)
         owner = np.repeat(np.arange(nt), 4)
         opp = self.T.ravel()                  # the vertex each face omits
         order = np.argsort(finv, kind="stable")
@@ -103,6 +121,21 @@ class MeshGrid:
         key = self.edges[:, 0] * self.n_nodes + self.edges[:, 1]
         return np.searchsorted(key, np.asarray(i) * self.n_nodes + np.asarray(j))
 
+    def ent_dofs(self, E):
+        """Dofs of entities E (edges e < n_geo, faces n_geo + f), in order."""
+        E = np.asarray(E, np.int64)
+        if self.order == 1:
+            return E
+        d = np.where(E < self.n_geo, 2 * E, 2 * self.n_geo + 2 * (E - self.n_geo))
+        return np.stack([d, d + 1], 1).ravel()
+
+    def dof_ent(self, D):
+        """Entity of each dof."""
+        D = np.asarray(D, np.int64)
+        if self.order == 1:
+            return D
+        return np.where(D < 2 * self.n_geo, D // 2, self.n_geo + (D - 2 * self.n_geo) // 2)
+
 
 def grid_of(w) -> MeshGrid:
     return MeshGrid(w.vertices, w.tets, getattr(w, "order", 1))
@@ -110,11 +143,72 @@ def grid_of(w) -> MeshGrid:
 
 def _basis(lam, G, ell, pairs, order):
     """Edge functions at barycentric point lam: the Whitney functions of the
-    pairs, then (order 2) the gradient functions: (n, order * len(pairs), 3)."""
+    pairs, then (order >= 2) the gradient functions: (n, dpe * len(pairs), 3)."""
     N = [np.stack([lam[a] * G[:, b] - lam[b] * G[:, a] for a, b in pairs], 1) * ell[..., None]]
-    if order == 2:
+    if order >= 2:
         N.append(np.stack([lam[a] * G[:, b] + lam[b] * G[:, a] for a, b in pairs], 1) * ell[..., None])
     return np.concatenate(N, 1)
+
+
+def duffy_tet(n):
+    """Collapsed-coordinate Gauss rule on a tetrahedron: x = u, y = v (1 - u),
+    z = w (1 - u)(1 - v) with n Gauss-Legendre points per direction (exact to
+    degree 2 n - 3); barycentric points (n^3, 4), weights as fractions of the
+    volume."""
+    q, wq = fem.gauss01(n)
+    P, Wt = [], []
+    for i, u in enumerate(q):
+        for j, v in enumerate(q):
+            for k, t in enumerate(q):
+                x, y, z = u, v * (1 - u), t * (1 - u) * (1 - v)
+                P.append([1 - x - y - z, x, y, z])
+                Wt.append(6.0 * wq[i] * wq[j] * wq[k] * (1 - u) ** 2 * (1 - v))
+    return np.array(P), np.array(Wt)
+
+
+def duffy_tri(n):
+    """The same on a triangle: x = u, y = v (1 - u) (exact to degree 2 n - 2);
+    barycentric points (n^2, 3), weights as fractions of the area."""
+    q, wq = fem.gauss01(n)
+    P, Wt = [], []
+    for i, u in enumerate(q):
+        for j, v in enumerate(q):
+            x, y = u, v * (1 - u)
+            P.append([1 - x - y, x, y])
+            Wt.append(2.0 * wq[i] * wq[j] * (1 - u))
+    return np.array(P), np.array(Wt)
+
+
+def _face_fns(lam, G, X, A, B, C):
+    """The two face functions of a face with vertices A < B < C (global order;
+    local indices per simplex) and their curls at barycentric point lam:
+    l_AB lam_C W_AB and l_AC lam_B W_AC.  X: vertex positions (n, k, 3)."""
+    r = np.arange(len(A))
+    la, lb, lc = lam[A], lam[B], lam[C]
+    ga, gb, gc = G[r, A], G[r, B], G[r, C]
+    lab = np.linalg.norm(X[r, B] - X[r, A], axis=1)[:, None]
+    lac = np.linalg.norm(X[r, C] - X[r, A], axis=1)[:, None]
+    wab = la[:, None] * gb - lb[:, None] * ga
+    wac = la[:, None] * gc - lc[:, None] * ga
+    f1, f2 = lab * lc[:, None] * wab, lac * lb[:, None] * wac
+    c1 = lab * (np.cross(gc, wab) + 2.0 * lc[:, None] * np.cross(ga, gb))
+    c2 = lac * (np.cross(gb, wac) + 2.0 * lb[:, None] * np.cross(ga, gc))
+    return f1, f2, c1, c2
+
+
+def _tet_basis3(g, lam, G, X, ell, tets):
+    """Order 3: the 20 functions of each tetrahedron and their curls at
+    barycentric point lam (edge functions, then two per face)."""
+    N = _basis(lam, G, ell, PAIRS, 3)
+    Cw = np.stack([2.0 * np.cross(G[:, a], G[:, b]) for a, b in PAIRS], 1) * ell[..., None]
+    C = [Cw, np.zeros_like(Cw)]
+    Nf = [N]
+    fl = g.face_loc[tets]
+    for q in range(4):
+        f1, f2, c1, c2 = _face_fns(lam, G, X, fl[:, q, 0], fl[:, q, 1], fl[:, q, 2])
+        Nf.append(np.stack([f1, f2], 1))
+        C.append(np.stack([c1, c2], 1))
+    return np.concatenate(Nf, 1), np.concatenate(C, 1)
 
 
 # ------------------------------------------------------------------ elements
@@ -129,6 +223,18 @@ def tet_matrices(g: MeshGrid, tets):
     G, vol = fem.tet_barycentric(X)
     vol = np.abs(vol)
     ell = np.stack([np.linalg.norm(X[:, b] - X[:, a], axis=1) for a, b in PAIRS], 1)
+    if g.order == 3:
+        nl = 20
+        S = np.zeros((len(tets), nl, nl))
+        M = np.zeros_like(S)
+        qp, qw = duffy_tet(4)
+        for lam, wt in zip(qp, qw):
+            N, C = _tet_basis3(g, lam, G, X, ell, tets)
+            M += wt * vol[:, None, None] * np.einsum("cid,cjd->cij", N, N)
+            S += wt * vol[:, None, None] * np.einsum("cid,cjd->cij", C, C)
+        sg = g.tet_sign[tets]
+        sgn = sg[:, :, None] * sg[:, None, :]
+        return S * sgn, M * sgn
     curl = np.stack([2.0 * np.cross(G[:, a], G[:, b]) for a, b in PAIRS], 1) * ell[..., None]
     if g.order == 2:
         curl = np.concatenate([curl, np.zeros_like(curl)], 1)   # gradients have no curl
@@ -148,9 +254,23 @@ def _tri(g: MeshGrid, faces):
     G, area = fem.tri_frame(Q)
     ell = np.stack([np.linalg.norm(Q[:, b] - Q[:, a], axis=1) for a, b in TRI], 1)
     ids = np.stack([g.edge_id(g.faces[faces, a], g.faces[faces, b]) for a, b in TRI], 1)
-    if g.order == 2:
+    if g.order >= 2:
         ids = np.concatenate([2 * ids, 2 * ids + 1], 1)
+    if g.order == 3:
+        fd = 2 * g.n_geo + 2 * np.asarray(faces)
+        ids = np.concatenate([ids, fd[:, None], fd[:, None] + 1], 1)
     return Q, G, area, ell, ids
+
+
+def _tri_basis(g, mu, G, Q, ell):
+    """Tangential traces on a triangle (sorted vertices): Whitney, gradient
+    and (order 3) the face's two functions."""
+    N = _basis(mu, G, ell, TRI, g.order)
+    if g.order == 3:
+        z = np.zeros(len(Q), np.int64)
+        f1, f2, _, _ = _face_fns(mu, G, Q, z, z + 1, z + 2)
+        N = np.concatenate([N, f1[:, None], f2[:, None]], 1)
+    return N
 
 
 def face_matrices(g: MeshGrid, faces):
@@ -159,10 +279,10 @@ def face_matrices(g: MeshGrid, faces):
     orientation; then the gradient functions) and the global dof ids."""
     faces = np.asarray(faces)
     Q, G, area, ell, ids = _tri(g, faces)
-    T = np.zeros((len(faces), 3 * g.order, 3 * g.order))
-    qp, qw = fem.tri_quadrature(2)
+    T = np.zeros((len(faces), ids.shape[1], ids.shape[1]))
+    qp, qw = fem.tri_quadrature(2) if g.order < 3 else duffy_tri(3)
     for mu, wt in zip(qp, qw):
-        N = _basis(mu, G, ell, TRI, g.order)
+        N = _tri_basis(g, mu, G, Q, ell)
         T += wt * area[:, None, None] * np.einsum("cid,cjd->cij", N, N)
     return T, ids
 
@@ -191,12 +311,12 @@ def assemble(g: MeshGrid, eps, k, tets=None, faces=()):
     C = [np.tile(ce, (1, nl)).ravel()]
     V = [(S.reshape(len(tets), nl * nl) - (k * k) * eps[tets][:, None] * M.reshape(len(tets), nl * nl))
          .ravel().astype(np.complex128)]
-    nf = 3 * g.order
     for fids, coeff in faces:
         fids = np.asarray(fids)
         if len(fids) == 0:
             continue
         T, ids = face_matrices(g, fids)
+        nf = ids.shape[1]
         R.append(np.repeat(ids, nf, axis=1).ravel())
         C.append(np.tile(ids, (1, nf)).ravel())
         V.append((coeff * T.reshape(len(fids), nf * nf)).ravel().astype(np.complex128))
@@ -229,7 +349,7 @@ def rhs_planewave(w, which=None):
     qp, qw = fem.tri_quadrature(5)
     for mu, wt in zip(qp, qw):
         pts = np.einsum("i,cid->cd", mu, Q)
-        N = _basis(mu, G, ell, TRI, g.order)
+        N = _tri_basis(g, mu, G, Q, ell)
         for col, r in enumerate(which):
             E, cE = fem.incident(pts, w.khat[r], w.pol[r], w.k)
             Et = E - np.einsum("cd,cd->c", E, n)[:, None] * n
@@ -244,6 +364,8 @@ def edge_interpolant(w, khat, pol):
     2) the moment 3 <E . t (1 - 2 s / l)> (the projection onto the edge's
     linear tangential variation), 4-point Gauss-Legendre along the edge."""
     g = grid_of(w)
+    if g.order == 3:
+        raise NotImplementedError("order 3: use an L2 projection (face moments are not defined here)")
     P0, P1 = g.V[g.edges[:, 0]], g.V[g.edges[:, 1]]
     t = P1 - P0
     that = t / np.linalg.norm(t, axis=1)[:, None]
@@ -362,15 +484,18 @@ def subdomain_matrix(w, dec, sd):
 
 def subdomain_nd(g: MeshGrid, sd, interface_edges, leaf_max):
     """ND nodes (sorted global dof arrays, post-order) of the non-interface
-    dofs of sd: centroid bisection over the edges (module docstring); an
-    edge's dofs stay together."""
-    avail = np.zeros(g.n_geo, bool)
-    avail[np.asarray(sd.edges, np.int64) // g.order] = True
-    avail[np.asarray(sorted(interface_edges), dtype=np.int64) // g.order] = False
+    dofs of sd: centroid bisection over the entities carrying dofs (edges;
+    at order 3 also faces, after all edges) (module docstring); an entity's
+    dofs stay together."""
+    n_ent = g.n_geo + (len(g.faces) if g.order == 3 else 0)
+    avail = np.zeros(n_ent, bool)
+    avail[g.dof_ent(sd.edges)] = True
+    avail[g.dof_ent(np.asarray(sorted(interface_edges), dtype=np.int64))] = False
     nodes = []
+    ents = g.tet_ents
 
     def dofs(E):
-        return (g.order * E[:, None] + np.arange(g.order)[None, :]).ravel()
+        return g.ent_dofs(E)
 
     def leaf(E):
         if len(E):
@@ -378,7 +503,7 @@ def subdomain_nd(g: MeshGrid, sd, interface_edges, leaf_max):
             nodes.append(dofs(E))
 
     def rec(T):
-        E = np.unique(g.tet_edges[T].ravel()) if len(T) else np.zeros(0, np.int64)
+        E = np.unique(ents[T].ravel()) if len(T) else np.zeros(0, np.int64)
         E = E[avail[E]]
         if len(E) <= leaf_max or len(T) < 2:
             return leaf(E)
@@ -390,7 +515,7 @@ def subdomain_nd(g: MeshGrid, sd, interface_edges, leaf_max):
         left, right = T[below], T[~below]
         if len(left) == 0 or len(right) == 0:
             return leaf(E)
-        sep = np.intersect1d(g.tet_edges[left].ravel(), g.tet_edges[right].ravel())
+        sep = np.intersect1d(ents[left].ravel(), ents[right].ravel())
         sep = sep[avail[sep]]
         avail[sep] = False
         rec(left)

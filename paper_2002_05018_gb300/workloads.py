@@ -79,7 +79,8 @@ class Workload:
     vertices: np.ndarray | None = None  # (n_nodes, 3) float64 positions (x-fastest for "tet"); None: lattice
     tets: np.ndarray | None = None      # "mesh": (n_tets, 4) int64 vertex ids
     gcuts: tuple | None = None          # "mesh": subdomain cut coordinates per axis (px+1, py+1, pz+1)
-    order: int = 1                      # "mesh": 1 Whitney; 2 also the edge gradient functions (2 dofs per edge)
+    order: int = 1                      # "mesh": 1 Whitney; 2 also the edge gradient functions (2 dofs per edge);
+                                        # 3 also two functions per face (oracle only)
 
     @property
     def n_cells(self) -> int:
@@ -90,7 +91,10 @@ class Workload:
     @property
     def n_edges(self) -> int:
         if self.element == "mesh":
-            return self.order * len(mesh_edge_pairs(self.tets))
+            ne = len(mesh_edge_pairs(self.tets))
+            if self.order == 3:
+                return 2 * ne + 2 * len(mesh_face_triples(self.tets))
+            return self.order * ne
         return sum(family_sizes(self.nx, self.ny, self.nz, self.element))
 
     @property
@@ -279,6 +283,13 @@ def mesh_edge_pairs(tets) -> np.ndarray:
     p = np.concatenate([np.sort(t[:, [a, b]], axis=1) for a, b in
                         ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))])
     return np.unique(p, axis=0)
+
+
+def mesh_face_triples(tets) -> np.ndarray:
+    """Distinct vertex triples (i < j < k) of the tetrahedra, lexicographic."""
+    t = np.asarray(tets, np.int64)
+    f = np.concatenate([np.sort(t[:, list(q)], axis=1) for q in ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))])
+    return np.unique(f, axis=0)
 
 
 def as_mesh(w: Workload) -> Workload:

@@ -123,8 +123,12 @@ def test_jagged_interfaces_tie_non_neighbour_copies():
     assert sorted(dec.blocks) == sorted(set(dec.blocks))
 
 
-def test_mesh_nested_dissection_is_a_partition_with_separators():
-    w = _delaunay(nx=6, ny=6, nz=5, px=2, py=1, pz=1)
+@pytest.mark.parametrize("order", [1, 3])
+def test_mesh_nested_dissection_is_a_partition_with_separators(order):
+    """The centroid bisection over edges (and, at order 3, faces): every dof
+    in exactly one supernode, no two ND leaves of a subdomain coupled."""
+    import dataclasses
+    w = dataclasses.replace(_delaunay(nx=6, ny=6, nz=5, px=2, py=1, pz=1), order=order)
     dec = decomp.decompose(w)
     plan = ordering.build_plan(dec, leaf_max=24)
     keys = set(zip(plan.m_sub.tolist(), plan.m_edge.tolist()))
@@ -256,3 +260,120 @@ def test_order2_adjoint_matches_central_differences():
         w.eps = e0
         fd = (Jp - Jm) / (2 * h)
         assert abs(fd - g[c]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g).max(), (c, fd, g[c], J)
+
+
+# ------------------------------------------------- curl-complete second order
+
+
+def test_collapsed_coordinate_rules_are_exact():
+    import math
+    P, Wt = tetmesh.duffy_tet(4)
+    for a in range(6):
+        for b in range(6 - a):
+            for c in range(6 - a - b):
+                q = np.sum(Wt * P[:, 1] ** a * P[:, 2] ** b * P[:, 3] ** c) / 6.0
+                exact = math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 3)
+                assert abs(q - exact) < 1e-14 * exact, (a, b, c)
+    P, Wt = tetmesh.duffy_tri(3)
+    for a in range(5):
+        for b in range(5 - a):
+            q = 0.5 * np.sum(Wt * P[:, 1] ** a * P[:, 2] ** b)
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs(q - exact) < 1e-14 * exact, (a, b)
+
+
+def _order3(**kw):
+    import dataclasses
+    return dataclasses.replace(_delaunay(**kw), order=3)
+
+
+def _projection(g, E):
+    """L2 projection of the field E(points) onto the mesh's space: dofs x and
+    the energy defect int |E|^2 - x^T M x (zero when E lies in the space)."""
+    import scipy.sparse.linalg as spla
+    X = g.V[g.T]
+    G, vol = fem.tet_barycentric(X)
+    vol = np.abs(vol)
+    ell = np.stack([np.linalg.norm(X[:, b] - X[:, a], axis=1) for a, b in tetmesh.PAIRS], 1)
+    tets = np.arange(g.n_cells)
+    b = np.zeros(g.n_edges)
+    energy = 0.0
+    for lam, wt in zip(*tetmesh.duffy_tet(4)):
+        if g.order == 3:
+            N, _ = tetmesh._tet_basis3(g, lam, G, X, ell, tets)
+        else:
+            N = tetmesh._basis(lam, G, ell, tetmesh.PAIRS, g.order)
+        N = N * g.tet_sign[:, :, None]
+        e = E(np.einsum("i,cid->cd", lam, X))
+        np.add.at(b, g.tet_dofs.ravel(), (wt * vol[:, None] * np.einsum("cid,cd->ci", N, e)).ravel())
+        energy += np.sum(wt * vol * np.sum(e * e, 1))
+    _, M = tetmesh.mass_stiffness(g)
+    x = spla.spsolve(M.tocsc(), b)
+    return x, (energy - x @ M @ x) / energy
+
+
+def test_order3_holds_the_curl_complete_quadratic_fields():
+    """E = d x (C d), d = r - r0, is a homogeneous quadratic field with
+    E . d = 0, in the first-kind space of degree 2: its L2 projection keeps
+    all of its energy, and the projection's curl energy is the exact
+    int |tr(C) d - 3 C d|^2 (curl E in closed form).  The order-2 space
+    misses it."""
+    C = np.array([[0.3, -0.2, 0.5], [0.1, 0.4, -0.6], [0.7, 0.2, -0.1]])
+    r0 = np.array([0.1, 0.05, 0.12])
+
+    def E(r):
+        d = r - r0
+        return np.cross(d, d @ C.T)
+
+    w = _order3(nx=4, ny=3, nz=3, px=1, py=1, pz=1)
+    g = tetmesh.grid_of(w)
+    x, defect = _projection(g, E)
+    assert abs(defect) < 1e-12
+    S, _ = tetmesh.mass_stiffness(g)
+    L = np.array([w.lx, w.ly, w.lz])
+    q, wq = fem.gauss01(2)
+    exact = 0.0
+    for i, xi in enumerate(q):
+        for j, yj in enumerate(q):
+            for k, zk in enumerate(q):
+                d = np.array([xi, yj, zk]) * L - r0
+                c = np.trace(C) * d - 3.0 * C @ d
+                exact += wq[i] * wq[j] * wq[k] * (c @ c)
+    exact *= L.prod()
+    assert np.isclose(x @ S @ x, exact, rtol=1e-11)
+    g2 = tetmesh.MeshGrid(w.vertices, w.tets, 2)
+    _, defect2 = _projection(g2, E)
+    assert defect2 > 1e-4
+
+
+def test_order3_keeps_the_linear_fields_and_the_gradient_kernel():
+    w = _order3(nx=4, ny=3, nz=3, px=1, py=1, pz=1)
+    g = tetmesh.grid_of(w)
+    S, M = tetmesh.mass_stiffness(g)
+    a = np.array([0.3, -0.2, 0.5])
+    C = np.array([[0.1, 0.4, -0.3], [0.2, -0.5, 0.6], [-0.7, 0.3, 0.2]])
+    x = np.zeros(g.n_edges)
+    g2 = tetmesh.MeshGrid(w.vertices, w.tets, 2)
+    x[:2 * g.n_geo] = _linear_field_dofs(g2, a, C)       # face dofs zero: hierarchical
+    L = np.array([w.lx, w.ly, w.lz])
+    q, wq = fem.gauss01(2)
+    exact = sum(wq[i] * wq[j] * wq[k] * np.sum((a + C @ (np.array([xi, yj, zk]) * L)) ** 2)
+                for i, xi in enumerate(q) for j, yj in enumerate(q) for k, zk in enumerate(q)) * L.prod()
+    assert np.isclose(x @ M @ x, exact, rtol=1e-12)
+    xs = np.zeros(g.n_edges)
+    xs[:2 * g.n_geo] = _linear_field_dofs(g2, a, C + C.T)  # a gradient field
+    assert abs(S @ xs).max() < 1e-12 * abs(S).max()
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(nx=6, ny=5, nz=4, px=3, py=2, pz=1, seed=5)])
+def test_order3_decomposed_equals_global(kw):
+    """Face dofs on the interfaces are copied and tied like edge dofs."""
+    w = _order3(**kw)
+    f = fem.rhs_planewave(w)
+    r = d3m.solve(w, f, return_all=True)
+    xg = fem.solve_global(w, f)
+    assert np.abs(r["x"] - xg).max() < 1e-10 * np.abs(xg).max()
+    assert r["copy_mismatch"] < 1e-10 * np.abs(xg).max()
+    assert any(e >= 2 * tetmesh.grid_of(w).n_geo for e in r["dec"].lm_edge)   # face multipliers exist
+    xs = d3m.solve_primal_schur(w, f)
+    assert np.abs(xs - xg).max() < 1e-10 * np.abs(xg).max()
