@@ -122,8 +122,14 @@ typedef struct {
                                e and dof 2e+1 its gradient function; the "n_edges"
                                rows of every RHS/solution block and of pec_edge's
                                count are then 2 * edges (pec_edge: one byte per
-                               dof, both dofs of an edge alike).  Other elements:
-                               0 or 1. */
+                               dof, both dofs of an edge alike); 3 = curl-complete
+                               second order: order 2 plus, on every face with
+                               vertices a < b < c, l_ab lam_c W_ab and l_ac lam_b
+                               W_ac (W the Whitney function without the length
+                               factor), dofs 2*edges + 2f and + 1 for face f
+                               (faces numbered as sorted vertex triples,
+                               lexicographic); d3m_grad_eps refuses order 3.
+                               Other elements: 0 or 1. */
 } d3m_mesh;
 
 /* Materials.  eps_r: 2*n_cells doubles (re, im) per cell, time convention

@@ -39,6 +39,10 @@ struct Plan {
   std::vector<int64_t> tet_e;         // 6 edge ids per tetrahedron (local pairs 01 02 03 12 13 23)
   std::vector<int8_t> tet_s;          // 6 orientation signs per tetrahedron
   int dpe = 1;                        // dofs per edge (mesh order): dof dpe*e + q
+  int order = 1;                      // mesh order 1, 2 or 3 (3: two dofs per face too)
+  int64_t n_geo = 0, n_faces = 0;     // edges and faces of a general mesh
+  std::vector<int64_t> tet_f;         // 4 face ids per tetrahedron (face q omits vertex q)
+  std::vector<std::array<int64_t, 3>> mface;  // sorted vertex triple of each face
   std::vector<std::array<int64_t, 4>> bface;  // boundary triangles: sorted vertices + opposite vertex
   std::vector<std::pair<int64_t, int64_t>> medge;  // vertex pair (i < j) of each edge
   double bS[12][12], bM[12][12], bT[6][12][12];  // brick element and face matrices

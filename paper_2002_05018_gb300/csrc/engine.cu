@@ -4757,6 +4757,10 @@ extern "C" int d3m_solve_adjoint(d3m_ctx *h, const double *rhs, int64_t ldb, dou
 extern "C" int d3m_grad_eps(d3m_ctx *h, const double *x, int64_t ldx, const double *y, int64_t ldy, int32_t nrhs,
                             double *grad) {
   if (!h || !x || !y || !grad || nrhs <= 0 || ldx < h->c.plan.n_edges || ldy < h->c.plan.n_edges) return D3M_EINVAL;
+  if (h->c.plan.cell_ne > d3m::MAX_CELL_NE) {
+    h->c.err = "d3m_grad_eps: the adjoint gradient of order-3 meshes is not built";
+    return D3M_EINVAL;
+  }
   return d3m::dev_grad_eps(h->c, x, ldx, y, ldy, nrhs, grad);
 }
 

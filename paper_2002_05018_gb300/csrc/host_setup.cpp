@@ -290,6 +290,118 @@ static void tet_local2(const double X[4][3], double S[12][12], double M[12][12])
     }
 }
 
+// ---- order 3 (curl-complete second order): functions as sums of terms
+// c lam^a v (a monomial in the barycentric coordinates times a constant
+// vector); products integrate in closed form,
+//   int_T lam^a = (d! |T|) prod a_i! / (|a| + d)!   (d = 3 tetrahedra, 2 triangles).
+struct VTerm {
+  double c;
+  int a[4];
+  double v[3];
+};
+struct VFun {
+  int n = 0;
+  VTerm t[4];
+  void add(double c, const int a[4], const double v[3]) {
+    t[n].c = c;
+    for (int i = 0; i < 4; ++i) t[n].a[i] = a[i];
+    for (int i = 0; i < 3; ++i) t[n].v[i] = v[i];
+    ++n;
+  }
+};
+
+static double fact(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+// int lam^a over a simplex of dimension d and measure meas (k vertices)
+static double mono_int(const int a[4], int k, int d, double meas) {
+  double num = 1.0;
+  int deg = 0;
+  for (int i = 0; i < k; ++i) {
+    num *= fact(a[i]);
+    deg += a[i];
+  }
+  return meas * fact(d) * num / fact(deg + d);
+}
+
+static double vfun_dot(const VFun &f, const VFun &g, int k, int d, double meas) {
+  double s = 0.0;
+  for (int i = 0; i < f.n; ++i)
+    for (int j = 0; j < g.n; ++j) {
+      int a[4];
+      for (int q = 0; q < 4; ++q) a[q] = f.t[i].a[q] + g.t[j].a[q];
+      s += f.t[i].c * g.t[j].c * dot3(f.t[i].v, g.t[j].v) * mono_int(a, k, d, meas);
+    }
+  return s;
+}
+
+// curl(lam^a v) = sum_i a_i lam^(a - e_i) grad lam_i x v
+static VFun vfun_curl(const VFun &f, const double g[][3]) {
+  VFun c;
+  for (int i = 0; i < f.n; ++i)
+    for (int q = 0; q < 4; ++q)
+      if (f.t[i].a[q] > 0) {
+        int a[4];
+        for (int r = 0; r < 4; ++r) a[r] = f.t[i].a[r];
+        a[q] -= 1;
+        double v[3];
+        cross3(g[q], f.t[i].v, v);
+        if (c.n < 4) c.add(f.t[i].c * f.t[i].a[q], a, v);
+      }
+  return c;
+}
+
+// The functions of order 3 on a simplex with barycentric gradients g and
+// vertex positions X: the Whitney and the gradient function of each pair
+// in `pairs`, then the face functions l_AB lam_C W_AB and l_AC lam_B W_AC of
+// the faces listed in `faces` (local vertex indices sorted by global id).
+static int order3_functions(const double X[][3], const double g[][3], const int (*pairs)[2], int np,
+                            const int (*faces)[3], int nf, VFun *F) {
+  int n = 0;
+  auto e = [](int i, int j, int a[4]) {
+    for (int q = 0; q < 4; ++q) a[q] = 0;
+    a[i] += 1;
+    if (j >= 0) a[j] += 1;
+  };
+  auto len = [&](int i, int j) {
+    double ev[3];
+    sub3(X[j], X[i], ev);
+    return std::sqrt(dot3(ev, ev));
+  };
+  for (int sgn = -1; sgn <= 1; sgn += 2)
+    for (int q = 0; q < np; ++q) {
+      const int a = pairs[q][0], b = pairs[q][1];
+      const double l = len(a, b);
+      int ea[4], eb[4];
+      e(a, -1, ea);
+      e(b, -1, eb);
+      VFun f;
+      f.add(l, ea, g[b]);
+      f.add(sgn * l, eb, g[a]);
+      F[n++] = f;
+    }
+  for (int q = 0; q < nf; ++q) {
+    const int A = faces[q][0], B = faces[q][1], C = faces[q][2];
+    int e1[4], e2[4];
+    VFun f1, f2;
+    const double lab = len(A, B), lac = len(A, C);
+    e(A, C, e1);
+    e(B, C, e2);
+    f1.add(lab, e1, g[B]);
+    f1.add(-lab, e2, g[A]);
+    e(A, B, e1);
+    e(C, B, e2);
+    f2.add(lac, e1, g[C]);
+    f2.add(-lac, e2, g[A]);
+    F[n++] = f1;
+    F[n++] = f2;
+  }
+  return n;
+}
+
 // S = int curl N . curl N and M = int N . N of a cell, in cell_edges order.
 int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][MAX_CELL_NE],
                   double M[MAX_CELL_NE][MAX_CELL_NE]) {
@@ -326,7 +438,9 @@ int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][M
 // Signed local matrices of tetrahedron t of a general mesh (global edge
 // orientation: from the lower to the higher vertex id; the edge-gradient
 // functions of order 2 carry no sign); returns the local dof count.
-static int mesh_tet_matrices(const Plan &p, int64_t t, double S[12][12], double M[12][12]) {
+static const int FACE_OF[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};  // face q omits vertex q
+
+static int mesh_tet_matrices(const Plan &p, int64_t t, double S[20][20], double M[20][20]) {
   double X[4][3];
   for (int v = 0; v < 4; ++v) {
     const double *x = p.vert.data() + 3 * p.tet_v[4 * t + v];
@@ -334,9 +448,33 @@ static int mesh_tet_matrices(const Plan &p, int64_t t, double S[12][12], double 
     X[v][1] = x[1];
     X[v][2] = x[2];
   }
-  const int nl = 6 * p.dpe;
-  if (p.dpe == 2) {
-    tet_local2(X, S, M);
+  const int nl = p.order == 3 ? 20 : 6 * p.dpe;
+  if (p.order == 3) {
+    // the local vertices of each face in the order of their global ids
+    int faces[4][3];
+    for (int q = 0; q < 4; ++q) {
+      for (int w = 0; w < 3; ++w) faces[q][w] = FACE_OF[q][w];
+      std::sort(faces[q], faces[q] + 3,
+                [&](int a, int b) { return p.tet_v[4 * t + a] < p.tet_v[4 * t + b]; });
+    }
+    double g[4][3];
+    const double vol = std::fabs(tet_grads(X, g)) / 6.0;
+    VFun F[20], Cu[20];
+    order3_functions(X, g, TET_E, 6, faces, 4, F);
+    for (int q = 0; q < 20; ++q) Cu[q] = vfun_curl(F[q], g);
+    for (int q = 0; q < 20; ++q)
+      for (int r = 0; r < 20; ++r) {
+        M[q][r] = vfun_dot(F[q], F[r], 4, 3, vol);
+        S[q][r] = vfun_dot(Cu[q], Cu[r], 4, 3, vol);
+      }
+  } else if (p.dpe == 2) {
+    double S12[12][12], M12[12][12];
+    tet_local2(X, S12, M12);
+    for (int q = 0; q < 12; ++q)
+      for (int r = 0; r < 12; ++r) {
+        S[q][r] = S12[q][r];
+        M[q][r] = M12[q][r];
+      }
   } else {
     double S6[6][6], M6[6][6];
     tet_local(X, S6, M6);
@@ -356,18 +494,22 @@ static int mesh_tet_matrices(const Plan &p, int64_t t, double S[12][12], double 
   return nl;
 }
 
-// Global dof of local function q of tetrahedron t (Whitney q < 6, gradient q >= 6).
+// Global dof of local function q of tetrahedron t (Whitney q < 6, gradient
+// 6 <= q < 12, face functions 12 + 2 k + j of local face k).
 static inline int64_t mesh_tet_dof(const Plan &p, int64_t t, int q) {
-  return q < 6 ? p.dpe * p.tet_e[6 * t + q] : p.dpe * p.tet_e[6 * t + q - 6] + 1;
+  if (q < 6) return p.dpe * p.tet_e[6 * t + q];
+  if (q < 12) return p.dpe * p.tet_e[6 * t + q - 6] + 1;
+  return 2 * p.n_geo + 2 * p.tet_f[4 * t + (q - 12) / 2] + (q - 12) % 2;
 }
 
 int cell_dofs_mass(const Plan &p, int64_t c, int64_t e[MAX_CELL_NE], double M[MAX_CELL_NE][MAX_CELL_NE]) {
   if (p.element == D3M_TET_MESH) {
-    double S12[12][12], M12[12][12];
-    const int nl = mesh_tet_matrices(p, c, S12, M12);
+    if (6 * p.dpe + (p.order == 3 ? 8 : 0) > MAX_CELL_NE) return 0;  // order 3: no per-cell table
+    double S20[20][20], M20[20][20];
+    const int nl = mesh_tet_matrices(p, c, S20, M20);
     for (int q = 0; q < nl; ++q) {
       e[q] = mesh_tet_dof(p, c, q);
-      for (int r = 0; r < nl; ++r) M[q][r] = M12[q][r];
+      for (int r = 0; r < nl; ++r) M[q][r] = M20[q][r];
     }
     return nl;
   }
@@ -439,6 +581,19 @@ static void tri_local2(const double Q[3][3], double T[6][6]) {
                 pair_mass(g, TRI_E[qq][0], TRI_E[qq][1], q < 3 ? -1.0 : 1.0, TRI_E[rr][0], TRI_E[rr][1],
                           r < 3 ? -1.0 : 1.0);
     }
+}
+
+// Order 3: local tangential face mass (8 x 8) of triangle Q with vertices in
+// the order of their global ids: Whitney and gradient functions of the pairs
+// 01 02 12, then the face's l_01 mu_2 W_01 and l_02 mu_1 W_02.
+static void tri_local3(const double Q[3][3], double T[8][8]) {
+  double g[3][3];
+  const double area = tri_grads(Q, g);
+  static const int face[1][3] = {{0, 1, 2}};
+  VFun F[8];
+  order3_functions(Q, g, TRI_E, 3, face, 1, F);
+  for (int q = 0; q < 8; ++q)
+    for (int r = 0; r < 8; ++r) T[q][r] = vfun_dot(F[q], F[r], 3, 2, area);
 }
 
 struct FaceTri {
@@ -626,11 +781,27 @@ static void mesh_centroid(const Plan &p, int64_t t, double c[3]) {
 // Face mass of a triangle with sorted vertices (every local edge along its
 // global orientation) and its dofs (Whitney functions of the pairs 01 02 12,
 // then at order 2 their gradient functions); returns the dof count.
-static int mesh_face(const Plan &p, const int64_t v[3], double T[6][6], int64_t e[6]) {
+static int mesh_face(const Plan &p, const int64_t v[3], double T[8][8], int64_t e[8]) {
   double Q[3][3];
   for (int w = 0; w < 3; ++w) mesh_vertex(p, v[w], Q[w]);
+  if (p.order == 3) {
+    tri_local3(Q, T);
+    const std::array<int64_t, 3> key = {v[0], v[1], v[2]};
+    const int64_t f = std::lower_bound(p.mface.begin(), p.mface.end(), key) - p.mface.begin();
+    for (int q = 0; q < 3; ++q) {
+      const int64_t ge = mesh_edge_id(p, v[TRI_E[q][0]], v[TRI_E[q][1]]);
+      e[q] = 2 * ge;
+      e[3 + q] = 2 * ge + 1;
+    }
+    e[6] = 2 * p.n_geo + 2 * f;
+    e[7] = e[6] + 1;
+    return 8;
+  }
   if (p.dpe == 2) {
-    tri_local2(Q, T);
+    double T6[6][6];
+    tri_local2(Q, T6);
+    for (int q = 0; q < 6; ++q)
+      for (int r = 0; r < 6; ++r) T[q][r] = T6[q][r];
   } else {
     double T3[3][3];
     tri_local(Q, T3);
@@ -648,17 +819,20 @@ static int mesh_face(const Plan &p, const int64_t v[3], double T[6][6], int64_t 
 // Interior ordering of a subdomain of a general mesh: bisection of its
 // tetrahedra T at the middle of their centroids' bounding box along its
 // longest axis (ties x < y < z; left: centroid below the middle); the still
-// unassigned edges shared by both halves form the separator; left, right,
-// separator; a region of at most leaf_max unassigned edges, or one that does
-// not split, is a leaf.  Inside a node edges follow the global index.
+// unassigned entities (edges; at order 3 also faces, numbered after the
+// edges) shared by both halves form the separator; left, right, separator; a
+// region of at most leaf_max unassigned entities, or one that does not
+// split, is a leaf.  Inside a node entities follow their index.  tent: ept
+// entities per tetrahedron.
 static void mesh_nd(const Plan &p, const std::vector<double> &cent, std::vector<char> &avail,
-                    const std::vector<int64_t> &T, int leaf_max, std::vector<std::vector<int64_t>> &nodes) {
+                    const std::vector<int64_t> &tent, int ept, const std::vector<int64_t> &T, int leaf_max,
+                    std::vector<std::vector<int64_t>> &nodes) {
   auto edges_of = [&](const std::vector<int64_t> &TT, bool only_avail) {
     std::vector<int64_t> E;
-    E.reserve(TT.size() * 6);
+    E.reserve(TT.size() * ept);
     for (int64_t t : TT)
-      for (int q = 0; q < 6; ++q) {
-        const int64_t e = p.tet_e[6 * t + q];
+      for (int q = 0; q < ept; ++q) {
+        const int64_t e = tent[ept * t + q];
         if (!only_avail || avail[e]) E.push_back(e);
       }
     std::sort(E.begin(), E.end());
@@ -693,8 +867,8 @@ static void mesh_nd(const Plan &p, const std::vector<double> &cent, std::vector<
   for (int64_t e : both)
     if (avail[e]) sep.push_back(e);
   for (int64_t e : sep) avail[e] = 0;
-  mesh_nd(p, cent, avail, L, leaf_max, nodes);
-  mesh_nd(p, cent, avail, R, leaf_max, nodes);
+  mesh_nd(p, cent, avail, tent, ept, L, leaf_max, nodes);
+  mesh_nd(p, cent, avail, tent, ept, R, leaf_max, nodes);
   if (!sep.empty()) nodes.push_back(std::move(sep));
 }
 
@@ -709,12 +883,13 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   p.element = D3M_TET_MESH;
   p.nfam = 0;
   p.nx = p.ny = p.nz = 0;
-  if (mesh->order < 0 || mesh->order > 2) {
-    ctx.err = "d3m_setup: mesh order must be 0, 1 or 2";
+  if (mesh->order < 0 || mesh->order > 3) {
+    ctx.err = "d3m_setup: mesh order must be 0, 1, 2 or 3";
     return D3M_EINVAL;
   }
-  p.dpe = mesh->order == 2 ? 2 : 1;
-  p.cell_ne = 6 * p.dpe;
+  p.order = mesh->order <= 1 ? 1 : mesh->order;
+  p.dpe = p.order >= 2 ? 2 : 1;
+  p.cell_ne = 6 * p.dpe + (p.order == 3 ? 8 : 0);
   const int dpe = p.dpe;
   const int64_t nv = mesh->n_vertices, nt = mesh->n_tets;
   if (nv < 4 || nt < 1 || !mesh->vertices || !mesh->tets) {
@@ -765,7 +940,7 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   std::sort(p.medge.begin(), p.medge.end());
   p.medge.erase(std::unique(p.medge.begin(), p.medge.end()), p.medge.end());
   const int64_t n_geo = (int64_t)p.medge.size();
-  p.n_edges = dpe * n_geo;  // dofs
+  p.n_geo = n_geo;
   p.tet_e.resize(6 * nt);
   p.tet_s.resize(6 * nt);
   for (int64_t t = 0; t < nt; ++t)
@@ -778,6 +953,7 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   struct FRec {
     std::array<int64_t, 3> v;
     int64_t t, opp;
+    int q;
   };
   std::vector<FRec> fr;
   fr.reserve(4 * nt);
@@ -788,15 +964,19 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
       for (int a = 0; a < 4; ++a)
         if (a != q) v[w++] = p.tet_v[4 * t + a];
       std::sort(v.begin(), v.end());
-      fr.push_back({v, t, p.tet_v[4 * t + q]});
+      fr.push_back({v, t, p.tet_v[4 * t + q], q});
     }
   std::sort(fr.begin(), fr.end(), [](const FRec &a, const FRec &b) { return a.v != b.v ? a.v < b.v : a.t < b.t; });
   p.bface.clear();
+  p.mface.clear();
+  p.tet_f.assign(4 * nt, -1);
   std::vector<int64_t> bface_tet;
   std::vector<std::array<int64_t, 5>> iface;  // sorted vertices, the two tetrahedra
   for (size_t i = 0; i < fr.size();) {
     size_t j = i;
     while (j < fr.size() && fr[j].v == fr[i].v) ++j;
+    for (size_t r = i; r < j; ++r) p.tet_f[4 * fr[r].t + fr[r].q] = (int64_t)p.mface.size();
+    p.mface.push_back(fr[i].v);
     if (j - i == 1) {
       p.bface.push_back({fr[i].v[0], fr[i].v[1], fr[i].v[2], fr[i].opp});
       bface_tet.push_back(fr[i].t);
@@ -808,6 +988,8 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     }
     i = j;
   }
+  p.n_faces = (int64_t)p.mface.size();
+  p.n_edges = dpe * n_geo + (p.order == 3 ? 2 * p.n_faces : 0);  // dofs
   // ---- materials
   if (!mat || !mat->eps_r) {
     ctx.err = "d3m_setup: eps_r is required";
@@ -818,9 +1000,9 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   p.pec.assign(p.n_edges, 0);
   if (mat->pec_edge)
     for (int64_t e = 0; e < p.n_edges; ++e) p.pec[e] = mat->pec_edge[e] ? 1 : 0;
-  for (int64_t e = 0; e < n_geo; ++e)
-    if (dpe == 2 && p.pec[2 * e] != p.pec[2 * e + 1]) {
-      ctx.err = "d3m_setup: pec_edge must mark both dofs of an edge alike";
+  for (int64_t e = 0; dpe == 2 && e < p.n_edges / 2; ++e)
+    if (p.pec[2 * e] != p.pec[2 * e + 1]) {
+      ctx.err = "d3m_setup: pec_edge must mark both dofs of an edge (or face) alike";
       return D3M_EINVAL;
     }
   p.n_free = 0;
@@ -862,17 +1044,29 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     }
   p.sub_lo.assign(p.nsub, {0, 0, 0});
   p.sub_hi.assign(p.nsub, {0, 0, 0});
+  // entities carrying dofs: the edges, then (order 3) the faces
+  const int ept = p.order == 3 ? 10 : 6;
+  const int64_t n_ent = n_geo + (p.order == 3 ? p.n_faces : 0);
+  std::vector<int64_t> tent((size_t)ept * nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    for (int q = 0; q < 6; ++q) tent[ept * t + q] = p.tet_e[6 * t + q];
+    if (p.order == 3)
+      for (int q = 0; q < 4; ++q) tent[ept * t + 6 + q] = n_geo + p.tet_f[4 * t + q];
+  }
+  const int de = p.order == 1 ? 1 : 2;  // dofs per entity
+  auto ent_dof = [&](int64_t e, int q) { return e < n_geo ? dpe * e + q : 2 * n_geo + 2 * (e - n_geo) + q; };
+  auto dof_ent = [&](int64_t d) { return d < dpe * n_geo ? d / dpe : n_geo + (d - 2 * n_geo) / 2; };
   p.sub_edges.assign(p.nsub, {});  // free dofs of each subdomain
-  std::vector<std::vector<int64_t>> sub_geo(p.nsub);
+  std::vector<std::vector<int64_t>> sub_geo(p.nsub);  // its entities
   for (int s = 0; s < p.nsub; ++s) {
     auto &G = sub_geo[s];
     for (int64_t t : sub_tets[s])
-      for (int q = 0; q < 6; ++q) G.push_back(p.tet_e[6 * t + q]);
+      for (int q = 0; q < ept; ++q) G.push_back(tent[ept * t + q]);
     std::sort(G.begin(), G.end());
     G.erase(std::unique(G.begin(), G.end()), G.end());
     for (int64_t e : G)
-      for (int q = 0; q < dpe; ++q)
-        if (!p.pec[dpe * e + q]) p.sub_edges[s].push_back(dpe * e + q);
+      for (int q = 0; q < de; ++q)
+        if (!p.pec[ent_dof(e, q)]) p.sub_edges[s].push_back(ent_dof(e, q));
   }
   // ---- copies and multipliers (per dof)
   std::vector<std::vector<int>> copies(p.n_edges);
@@ -928,21 +1122,21 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     p.sn_kind.push_back(kind);
     p.sn_owner.push_back(owner);
   };
-  std::vector<char> avail(n_geo, 0);  // per geometric edge
+  std::vector<char> avail(n_ent, 0);  // per entity
   std::vector<int64_t> sub_m0(p.nsub);
   for (int s = 0; s < p.nsub; ++s) {
     sub_m0[s] = (int64_t)p.m_sub.size();
-    // an edge is ordered inside the subdomain when it has a free dof there
+    // an entity is ordered inside the subdomain when it has a free dof there
     // and none of its dofs is an interface dof
-    for (int64_t d : p.sub_edges[s]) avail[d / dpe] = 1;
+    for (int64_t d : p.sub_edges[s]) avail[dof_ent(d)] = 1;
     for (int64_t d : p.sub_edges[s])
-      if (copies[d].size() >= 2) avail[d / dpe] = 0;
+      if (copies[d].size() >= 2) avail[dof_ent(d)] = 0;
     std::vector<std::vector<int64_t>> nodes;
-    mesh_nd(p, cent, avail, sub_tets[s], leaf_max, nodes);
+    mesh_nd(p, cent, avail, tent, ept, sub_tets[s], leaf_max, nodes);
     for (auto &nd : nodes) {
       std::vector<int64_t> dofs;
       for (int64_t e : nd)
-        for (int q = 0; q < dpe; ++q) dofs.push_back(dpe * e + q);
+        for (int q = 0; q < de; ++q) dofs.push_back(ent_dof(e, q));
       push_node(s, dofs, 0, s);
     }
     for (int64_t e : sub_geo[s]) avail[e] = 0;
@@ -986,9 +1180,9 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
     const int64_t m1_ = s + 1 < p.nsub ? sub_m0[s + 1] : p.lam_start;
     for (int64_t v = m0; v < m1_; ++v) gm[p.m_edge[v]] = v;
     for (int64_t t : sub_tets[s]) {
-      double S12[12][12], M12[12][12];
-      const int nl = mesh_tet_matrices(p, t, S12, M12);
-      int64_t e[12];
+      double S20[20][20], M20[20][20];
+      const int nl = mesh_tet_matrices(p, t, S20, M20);
+      int64_t e[20];
       for (int q = 0; q < nl; ++q) e[q] = mesh_tet_dof(p, t, q);
       for (int a = 0; a < nl; ++a) {
         const int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
@@ -996,22 +1190,22 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
         for (int b = 0; b < nl; ++b) {
           const int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
           if (rb < 0 || ra < rb) continue;
-          const cplx v = S12[a][b] - k * k * p.eps[t] * M12[a][b];
+          const cplx v = S20[a][b] - k * k * p.eps[t] * M20[a][b];
           if (v != cplx(0.0)) trips.push_back({ra, rb, v});
         }
       }
     }
     for (auto &fc : sub_faces[s]) {
-      double T6[6][6];
-      int64_t e[6];
-      const int nf = mesh_face(p, fc.first.data(), T6, e);
+      double T8[8][8];
+      int64_t e[8];
+      const int nf = mesh_face(p, fc.first.data(), T8, e);
       for (int a = 0; a < nf; ++a) {
         const int64_t ra = p.pec[e[a]] ? -1 : gm[e[a]];
         if (ra < 0) continue;
         for (int b = 0; b < nf; ++b) {
           const int64_t rb = p.pec[e[b]] ? -1 : gm[e[b]];
-          if (rb < 0 || ra < rb || T6[a][b] == 0.0) continue;
-          trips.push_back({ra, rb, fc.second * T6[a][b]});
+          if (rb < 0 || ra < rb || T8[a][b] == 0.0) continue;
+          trips.push_back({ra, rb, fc.second * T8[a][b]});
         }
       }
     }
@@ -1026,27 +1220,27 @@ static int build_plan_mesh(Ctx &ctx, const d3m_mesh *mesh, const d3m_materials *
   std::vector<Trip> g;
   g.reserve((size_t)nt * 36 * dpe * dpe);
   for (int64_t t = 0; t < nt; ++t) {
-    double S12[12][12], M12[12][12];
-    const int nl = mesh_tet_matrices(p, t, S12, M12);
-    int64_t e[12];
+    double S20[20][20], M20[20][20];
+    const int nl = mesh_tet_matrices(p, t, S20, M20);
+    int64_t e[20];
     for (int q = 0; q < nl; ++q) e[q] = mesh_tet_dof(p, t, q);
     for (int a = 0; a < nl; ++a) {
       if (p.pec[e[a]]) continue;
       for (int b = 0; b < nl; ++b) {
         if (p.pec[e[b]]) continue;
-        const cplx v = S12[a][b] - k * k * p.eps[t] * M12[a][b];
+        const cplx v = S20[a][b] - k * k * p.eps[t] * M20[a][b];
         if (v != cplx(0.0)) g.push_back({e[a], e[b], v});
       }
     }
   }
   for (auto &bf : p.bface) {
-    double T6[6][6];
-    int64_t e[6];
-    const int nf = mesh_face(p, bf.data(), T6, e);
+    double T8[8][8];
+    int64_t e[8];
+    const int nf = mesh_face(p, bf.data(), T8, e);
     for (int a = 0; a < nf; ++a) {
       if (p.pec[e[a]]) continue;
       for (int b = 0; b < nf; ++b)
-        if (!p.pec[e[b]] && T6[a][b] != 0.0) g.push_back({e[a], e[b], jk * T6[a][b]});
+        if (!p.pec[e[b]] && T8[a][b] != 0.0) g.push_back({e[a], e[b], jk * T8[a][b]});
     }
   }
   return finish_plan(ctx, trips, g);
@@ -1734,8 +1928,9 @@ static TriRule radon7() {
 
 // f_v -= int U . N_v dS over triangle Q with outward normal nvec; eids: the
 // dofs of the Whitney functions of the vertex pairs 01 02 12 (each pointing
-// from the lower to the higher local vertex), then, when nfun = 6, of their
-// edge-gradient functions.
+// from the lower to the higher local vertex), then, when nfun >= 6, of their
+// edge-gradient functions, and when nfun = 8 of the face functions
+// l_01 mu_2 W_01 and l_02 mu_1 W_02 (vertices in the order of their ids).
 static void rhs_triangle(const Plan &p, const TriRule &R, const double Q[3][3], const double nvec[3],
                          const int64_t *eids, int nfun, const double *khat_pol, int nrhs, double *rhs,
                          int64_t ldb) {
@@ -1748,13 +1943,18 @@ static void rhs_triangle(const Plan &p, const TriRule &R, const double Q[3][3], 
   }
   for (int q = 0; q < 7; ++q) {
     const double *mu = R.b[q];
-    double xyz[3], N[6][3];
+    double xyz[3], N[8][3];
     for (int a = 0; a < 3; ++a) xyz[a] = mu[0] * Q[0][a] + mu[1] * Q[1][a] + mu[2] * Q[2][a];
-    for (int m = 0; m < nfun; ++m) {
+    for (int m = 0; m < nfun && m < 6; ++m) {
       const int mm = m % 3, a = TRI_E[mm][0], b = TRI_E[mm][1];
       const double sb = m < 3 ? -1.0 : 1.0;
       for (int c = 0; c < 3; ++c) N[m][c] = ell[mm] * (mu[a] * g[b][c] + sb * mu[b] * g[a][c]);
     }
+    if (nfun == 8)
+      for (int c = 0; c < 3; ++c) {
+        N[6][c] = ell[0] * mu[2] * (mu[0] * g[1][c] - mu[1] * g[0][c]);
+        N[7][c] = ell[1] * mu[1] * (mu[0] * g[2][c] - mu[2] * g[0][c]);
+      }
     const double w = R.w[q] * area;
     for (int r = 0; r < nrhs; ++r) {
       cplx U[3];
@@ -1815,13 +2015,21 @@ static int rhs_planewave_mesh(const Plan &p, const double *khat_pol, int nrhs, d
     sub3(X, Q[0], to_opp);
     if (dot3(nvec, to_opp) > 0)
       for (int a = 0; a < 3; ++a) nvec[a] *= -1.0;
-    int64_t eids[6];
+    int64_t eids[8];
     for (int m = 0; m < 3; ++m) {
       const int64_t ge = mesh_edge_id(p, bf[TRI_E[m][0]], bf[TRI_E[m][1]]);
       eids[m] = p.dpe * ge;
       eids[3 + m] = 2 * ge + 1;
     }
-    rhs_triangle(p, R, Q, nvec, eids, 3 * p.dpe, khat_pol, nrhs, rhs, ldb);
+    int nfun = 3 * p.dpe;
+    if (p.order == 3) {
+      const std::array<int64_t, 3> key = {bf[0], bf[1], bf[2]};
+      const int64_t f = std::lower_bound(p.mface.begin(), p.mface.end(), key) - p.mface.begin();
+      eids[6] = 2 * p.n_geo + 2 * f;
+      eids[7] = eids[6] + 1;
+      nfun = 8;
+    }
+    rhs_triangle(p, R, Q, nvec, eids, nfun, khat_pol, nrhs, rhs, ldb);
   }
   return D3M_OK;
 }

@@ -34,6 +34,8 @@ CASES = [
     ("delaunay-3x2x2", lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6), 32),
     # complete first order: two dofs per edge, kept together by the ordering
     ("delaunay-order2", lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6, order=2), 32),
+    # curl-complete second order: face dofs, ordered with the edges
+    ("delaunay-order3", lambda: W.delaunay(9, 7, 6, 3, 2, 2, seed=6, order=3), 32),
 ]
 LARGE = {"config2", "config3", "config4", "tet-config3"}
 
@@ -97,12 +99,12 @@ def test_setup_rejects_bad_input():
     assert e.value.code == d3m.D3M_EINVAL
 
 
-@pytest.mark.parametrize("tet", [False, True, "mesh", "order2"])
+@pytest.mark.parametrize("tet", [False, True, "mesh", "order2", "order3"])
 def test_rhs_planewave_matches_oracle(tet):
     from oracle import fem
     w = W.tiny(5, 4, 3, 1, 1, 1, seed=8, nrhs=3)
-    if tet in ("mesh", "order2"):
-        w = W.delaunay(5, 4, 3, 2, 1, 1, seed=8, nrhs=3, order=2 if tet == "order2" else 1)
+    if tet in ("mesh", "order2", "order3"):
+        w = W.delaunay(5, 4, 3, 2, 1, 1, seed=8, nrhs=3, order={"mesh": 1, "order2": 2, "order3": 3}[tet])
     elif tet:
         w = W.tetrahedral(w, 0.1)
     s = d3m.Solver.from_workload(w)
@@ -148,7 +150,7 @@ def test_setup_rejects_bad_general_meshes(what):
     elif what == "lm_weight":
         kw = _mesh_kw(w, lm_weight=1)
     elif what == "order":
-        kw = _mesh_kw(w, order=3)
+        kw = _mesh_kw(w, order=4)
     elif what == "empty-box":   # a box too thin to hold a centroid
         gx = np.array([0.0, 0.15, 0.1501, 0.3])
         kw = _mesh_kw(w, gcuts=(gx, w.gcuts[1], w.gcuts[2]))
@@ -275,7 +277,7 @@ def test_setup_rejects_bad_options(kw):
     assert "d3m_setup" in str(ei.value)
 
 
-@pytest.mark.parametrize("tet", [False, True, "mesh", "order2"])
+@pytest.mark.parametrize("tet", [False, True, "mesh", "order2", "order3"])
 def test_interface_coefficient_matches_oracle_entries(tet):
     """d3m_options.alpha sets the interface loss/gain term: the library's
     assembled entries of M equal the oracle's subdomain matrices for a
@@ -284,8 +286,8 @@ def test_interface_coefficient_matches_oracle_entries(tet):
     against the oracle's quadrature."""
     from oracle import decomp
     w = W.tiny(4, 3, 3, 2, 1, 1, seed=6)
-    if tet in ("mesh", "order2"):
-        w = W.delaunay(5, 4, 4, 2, 2, 2, seed=3, order=2 if tet == "order2" else 1)
+    if tet in ("mesh", "order2", "order3"):
+        w = W.delaunay(5, 4, 4, 2, 2, 2, seed=3, order={"mesh": 1, "order2": 2, "order3": 3}[tet])
     elif tet:
         w = W.tetrahedral(W.tiny(4, 3, 3, 2, 2, 1, seed=6), 0.1)
     w.alpha = 2.5 - 0.7j
@@ -295,12 +297,16 @@ def test_interface_coefficient_matches_oracle_entries(tet):
     s.close()
     dec = decomp.decompose(w)
     for sd in dec.subs:
-        A = sd.A.toarray()
-        loc = {int(e): i for i, e in enumerate(sd.edges)}
-        sel = (mm[ent[:, 0].astype(int), 0] == sd.index) & (mm[ent[:, 1].astype(int), 0] == sd.index)
-        for r, c, re, im in ent[sel]:
-            er, ec = mm[int(r), 1], mm[int(c), 1]
-            assert abs(A[loc[er], loc[ec]] - (re + 1j * im)) < 1e-12 * np.abs(A).max()
+        A = sd.A.tocsr()
+        loc = -np.ones(int(mm[:, 1].max()) + 1, np.int64)
+        loc[sd.edges] = np.arange(len(sd.edges))
+        rows, cols = ent[:, 0].astype(np.int64), ent[:, 1].astype(np.int64)
+        sel = (mm[rows, 0] == sd.index) & (mm[cols, 0] == sd.index)
+        ar, ac = loc[mm[rows[sel], 1]], loc[mm[cols[sel], 1]]
+        assert (ar >= 0).all() and (ac >= 0).all()
+        ref = np.asarray(A[ar, ac]).ravel()
+        got = ent[sel, 2] + 1j * ent[sel, 3]
+        assert np.abs(ref - got).max() < 1e-12 * abs(A).max()
 
 
 @pytest.mark.parametrize("tet", [False, True])
@@ -411,15 +417,15 @@ def test_entry_points_refuse_bad_arguments_before_any_device_work():
     s.close()
 
 
-@pytest.mark.parametrize("case", range(12))
+@pytest.mark.parametrize("case", range(15))
 def test_structure_bit_exact_on_random_meshes(case):
     """Seeded random meshes (bricks, lattice tetrahedra, Delaunay meshes of
-    order 1 and 2; random sizes, partitions, cut jitter and leaf sizes): the
+    orders 1 to 3; random sizes, partitions, cut jitter and leaf sizes): the
     library's plan equals the oracle's bit for bit."""
     rng = np.random.default_rng(1000 + case)
     nx, ny, nz = [int(v) for v in rng.integers(2, 8, 3)]
     px, py, pz = [int(rng.integers(1, min(3, n) + 1)) for n in (nx, ny, nz)]
-    kind, seed, leaf = case % 4, int(rng.integers(0, 1000)), int(rng.integers(4, 40))
+    kind, seed, leaf = case % 5, int(rng.integers(0, 1000)), int(rng.integers(4, 40))
     if kind < 2:
         w = W.tiny(nx, ny, nz, px, py, pz, seed=seed)
         if kind == 1:
@@ -445,19 +451,19 @@ def test_structure_bit_exact_on_random_meshes(case):
     s.close()
 
 
-@pytest.mark.parametrize("case", range(6))
+@pytest.mark.parametrize("case", range(8))
 def test_entries_match_oracle_on_random_meshes(case):
     """Every assembled entry of M (element, interface and absorbing terms,
     multiplier couplings) on seeded random lattice-tetrahedral and Delaunay
-    meshes equals the oracle's subdomain matrices and D_i."""
+    meshes (orders 1 to 3) equals the oracle's subdomain matrices and D_i."""
     rng = np.random.default_rng(2000 + case)
     nx, ny, nz = [int(v) for v in rng.integers(2, 6, 3)]
     px, py, pz = [int(rng.integers(1, min(3, n) + 1)) for n in (nx, ny, nz)]
     seed = int(rng.integers(0, 1000))
-    if case % 3 == 0:
+    if case % 4 == 0:
         w = W.tetrahedral(W.tiny(nx, ny, nz, px, py, pz, seed=seed), 0.1)
     else:
-        w = W.delaunay(nx, ny, nz, px, py, pz, seed=seed, order=1 if case % 3 == 1 else 2)
+        w = W.delaunay(nx, ny, nz, px, py, pz, seed=seed, order=case % 4)
     s = d3m.Solver.from_workload(w)
     ent, mm, st = s.structure(d3m.M_ENTRIES), s.structure(d3m.M_MAP), s.stats()
     s.close()
@@ -478,3 +484,14 @@ def test_entries_match_oracle_on_random_meshes(case):
             sub, e = mm[c]
             _, loc = A[int(sub)]
             assert abs(Ds[int(sub)][loc[int(e)], r - lam0] - v) < 1e-15
+
+
+def test_order3_gradient_is_refused_on_the_host():
+    """d3m_grad_eps refuses order-3 meshes before any device work."""
+    lib = d3m.load()
+    s = d3m.Solver.from_workload(W.delaunay(3, 3, 2, 1, 1, 1, seed=4, order=3))
+    buf = np.zeros(2 * s.n_edges + 64)
+    p, n = buf.ctypes.data, s.n_edges
+    assert lib.d3m_grad_eps(s.h, p, n, p, n, 1, p) == d3m.D3M_EINVAL
+    assert b"order-3" in lib.d3m_last_error(s.h)
+    s.close()
