@@ -151,8 +151,8 @@ class Solver:
                  vertices=None, tets=None, gcuts=None, order=1):
         """Lattice meshes: nx..lz, cuts cx, cy, cz (cell indices).  General
         tetrahedral meshes (element=TET_MESH): vertices (n, 3), tets (m, 4)
-        and gcuts = (gx, gy, gz) coordinate cuts, order 1 (Whitney) or 2 (two
-        dofs per edge); nx..lz and cx..cz unused."""
+        and gcuts = (gx, gy, gz) coordinate cuts, order 1 (Whitney), 2 (two
+        dofs per edge) or 3 (also two per face); nx..lz and cx..cz unused."""
         self.lib = load()
         self._eps = np.ascontiguousarray(np.asarray(eps, np.complex128).view(np.float64))
         self._vert = None if vertices is None else np.ascontiguousarray(np.asarray(vertices, np.float64))

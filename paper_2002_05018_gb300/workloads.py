@@ -80,7 +80,7 @@ class Workload:
     tets: np.ndarray | None = None      # "mesh": (n_tets, 4) int64 vertex ids
     gcuts: tuple | None = None          # "mesh": subdomain cut coordinates per axis (px+1, py+1, pz+1)
     order: int = 1                      # "mesh": 1 Whitney; 2 also the edge gradient functions (2 dofs per edge);
-                                        # 3 also two functions per face (oracle only)
+                                        # 3 also two functions per face
 
     @property
     def n_cells(self) -> int:
@@ -324,7 +324,8 @@ def delaunay(nx, ny, nz, px, py, pz, seed=0, nrhs=1, h=0.1, jitter=0.3, lossy=Tr
     axis (boundary points only within their boundary planes, box edges along
     the edge, corners fixed); per-tetrahedron eps ~ U[1, 3] (lossy: times
     1 - 0.05j); px x py x pz subdomains cut at equal coordinates; random plane
-    waves; order 2: two dofs per edge (Whitney and edge-gradient functions).
+    waves; order 2: two dofs per edge (Whitney and edge-gradient functions);
+    order 3: also two per face (curl-complete second order).
     Draw order: jitter, eps, waves."""
     from scipy.spatial import Delaunay
     rng = np.random.default_rng(seed)
