@@ -1,6 +1,6 @@
 /*
  * The C ABI driven from plain C (no Python): set-up of a brick mesh and of a
- * general tetrahedral mesh of complete first order, the plane-wave RHS, the
+ * general tetrahedral mesh of orders 2 and 3, the plane-wave RHS, the
  * problem counts and a structure export.  Host calls only (d3m_setup makes
  * no CUDA call), so it runs without a GPU.  Prints "key value" lines that the
  * test compares with the Python binding's view of the same problems.
@@ -77,6 +77,13 @@ int main(void) {
     return 1;
   }
   if (report("mesh", ctx)) return 1;
+  d3m_free(ctx);
+  tm.order = 3; /* curl-complete second order: two more dofs per face */
+  if (d3m_setup(&tm, &tmat, k, &tpart, &opt, &ctx) != D3M_OK) {
+    printf("setup_error %s\n", ctx ? d3m_last_error(ctx) : "");
+    return 1;
+  }
+  if (report("mesh3", ctx)) return 1;
   d3m_free(ctx);
   printf("ok 1\n");
   return 0;

@@ -367,7 +367,10 @@ def test_c_program_drives_the_abi(tmp_path):
     tets = np.array([[0, 1, 3, 7], [0, 1, 5, 7], [0, 2, 3, 7], [0, 2, 6, 7], [0, 4, 5, 7], [0, 4, 6, 7]])
     mesh = d3m.Solver(0, 0, 0, 0.0, 0.0, 0.0, np.full(6, 2.0 + 0j), k, [0], [0], [0], element=d3m.TET_MESH,
                       vertices=v, tets=tets, gcuts=([0.0, 0.1, 0.2], [0.0, 0.2], [0.0, 0.2]), order=2)
-    for tag, s in (("brick", brick), ("mesh", mesh)):
+    mesh3 = d3m.Solver(0, 0, 0, 0.0, 0.0, 0.0, np.full(6, 2.0 + 0j), k, [0], [0], [0], element=d3m.TET_MESH,
+                       vertices=v, tets=tets, gcuts=([0.0, 0.1, 0.2], [0.0, 0.2], [0.0, 0.2]), order=3)
+    assert mesh3.n_edges == 2 * 19 + 2 * 18   # 19 edges and 18 faces of a cube's six tetrahedra
+    for tag, s in (("brick", brick), ("mesh", mesh), ("mesh3", mesh3)):
         st = s.stats()
         for key in ("n_edges", "n_lm", "n_m", "n_fronts"):
             assert int(out[f"{tag}_{key}"]) == st[key], (tag, key)
