@@ -468,8 +468,9 @@ def main():
                     help="tet: the same workload on six jittered tetrahedra per cell; mesh: its box as a "
                          "Delaunay mesh of the jittered lattice points (general connectivity), the same "
                          "subdomain counts as equal coordinate cuts, the same plane waves")
-    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
-                    help="--element mesh: 2 = complete first-order elements (two dofs per edge)")
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2, 3],
+                    help="--element mesh: 2 = complete first-order elements (two dofs per edge), "
+                         "3 = curl-complete second order (also two per face)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     from paper_2002_05018_gb300 import workloads as W
