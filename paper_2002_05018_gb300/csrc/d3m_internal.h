@@ -9,9 +9,20 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/d3m.h"
 
 namespace d3m {
+
+// Named range over one call of the ABI (NVTX; free unless a profiler such as
+// Nsight Systems is attached): d3m_setup, d3m_factor, d3m_solve, ...
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 using cplx = std::complex<double>;
 

@@ -4680,6 +4680,7 @@ extern "C" int d3m_set_profile(d3m_ctx *h, int32_t on) {
 
 extern "C" int d3m_factor(d3m_ctx *h) {
   if (!h) return D3M_EINVAL;
+  d3m::NvtxRange range("d3m_factor");
   try {
     return d3m::dev_factor(h->c);
   } catch (const std::bad_alloc &) {
@@ -4691,12 +4692,14 @@ extern "C" int d3m_factor(d3m_ctx *h) {
 extern "C" int d3m_solve(d3m_ctx *h, const double *rhs, int64_t ldb, double *x, int64_t ldx, int32_t nrhs,
                          d3m_solve_info *info) {
   if (!h || !rhs || !x || nrhs <= 0 || ldb < h->c.plan.n_edges || ldx < h->c.plan.n_edges) return D3M_EINVAL;
+  d3m::NvtxRange range("d3m_solve");
   return d3m::dev_solve(h->c, rhs, ldb, x, ldx, nrhs, info, false);
 }
 
 extern "C" int d3m_solve_host(d3m_ctx *h, const double *rhs, int64_t ldb, double *x, int64_t ldx, int32_t nrhs,
                               d3m_solve_info *info) {
   if (!h || !rhs || !x || nrhs <= 0 || ldb < h->c.plan.n_edges || ldx < h->c.plan.n_edges) return D3M_EINVAL;
+  d3m::NvtxRange range("d3m_solve_host");
   return d3m::dev_solve(h->c, rhs, ldb, x, ldx, nrhs, info, true);
 }
 
@@ -4751,6 +4754,7 @@ extern "C" int d3m_export_front(d3m_ctx *h, int64_t front, int32_t *m_out, int32
 extern "C" int d3m_solve_adjoint(d3m_ctx *h, const double *rhs, int64_t ldb, double *y, int64_t ldy,
                                  int32_t nrhs, d3m_solve_info *info) {
   if (!h || !rhs || !y || nrhs <= 0 || ldb < h->c.plan.n_edges || ldy < h->c.plan.n_edges) return D3M_EINVAL;
+  d3m::NvtxRange range("d3m_solve_adjoint");
   return d3m::dev_solve(h->c, rhs, ldb, y, ldy, nrhs, info, false, true);
 }
 
@@ -4761,6 +4765,7 @@ extern "C" int d3m_grad_eps(d3m_ctx *h, const double *x, int64_t ldx, const doub
     h->c.err = "d3m_grad_eps: the adjoint gradient of order-3 meshes is not built";
     return D3M_EINVAL;
   }
+  d3m::NvtxRange range("d3m_grad_eps");
   return d3m::dev_grad_eps(h->c, x, ldx, y, ldy, nrhs, grad);
 }
 

@@ -2159,6 +2159,7 @@ extern "C" int d3m_setup(const d3m_mesh *mesh, const d3m_materials *mat, double 
     return D3M_EINVAL;
   }
   int rc;
+  d3m::NvtxRange range("d3m_setup");
   try {
     rc = d3m::build_plan(c, mesh, mat, k, part);
   } catch (const std::bad_alloc &) {
