@@ -441,6 +441,15 @@ def bench_config(w, config, arena_bytes):
             "value_def": "algorithmic flops (factor + one substitution pass) / step time"}
 
 
+def _emit(line, log_path):
+    """Print the run's JSON line; with --log also append it to that file."""
+    text = json.dumps(line)
+    print(text)
+    if log_path:
+        with open(log_path, "a") as fh:
+            fh.write(text + "\n")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -464,6 +473,10 @@ def main():
     ap.add_argument("--autotune-cache", default=None,
                     help="file prefix for the tuned factor schedules (read when they match, else written); "
                          "lets a profiler run reuse the schedule of a plain run")
+    ap.add_argument("--seed", type=int, default=None,
+                    help="seed of the synthetic workload (default: the workload's index, as everywhere else)")
+    ap.add_argument("--log", default=None,
+                    help="also append the JSON line to this file (one run per line)")
     ap.add_argument("--element", default="brick", choices=["brick", "tet", "mesh"],
                     help="tet: the same workload on six jittered tetrahedra per cell; mesh: its box as a "
                          "Delaunay mesh of the jittered lattice points (general connectivity), the same "
@@ -474,7 +487,7 @@ def main():
     args = ap.parse_args()
     ws, rank, local = _dist()
     from paper_2002_05018_gb300 import workloads as W
-    w = W.make(args.config)
+    w = W.make(args.config, seed=args.seed)
     if args.nrhs > 0:
         w = W.with_waves(w, args.nrhs, seed=args.config)
     if args.element == "tet":
@@ -514,7 +527,7 @@ def main():
                 "e2e": {"value": round(v, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0},
                 "wall_s": round(time.perf_counter() - t0, 1)}
-        print(json.dumps(line))
+        _emit(line, args.log)
         return
 
     import torch
@@ -603,7 +616,7 @@ def main():
     }
     if line["fp64"]:
         line["mixed_speedup_vs_fp64"] = round(fp64["step_ms"] / mixed["step_ms"], 2)
-    print(json.dumps(line))
+    _emit(line, args.log)
     if ws > 1:
         torch.distributed.destroy_process_group()
 

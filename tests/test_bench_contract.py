@@ -7,6 +7,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 from paper_2002_05018_gb300 import d3m
@@ -44,6 +45,26 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_seed_and_log(tmp_path):
+    """--seed is accepted and --log appends each printed line to a JSONL
+    file; the seed reaches the workload generator (workload 2's cut jitter
+    differs between seeds)."""
+    log = tmp_path / "runs.jsonl"
+    outs = []
+    for seed in (2, 7):
+        code = ("import runpy, sys; sys.argv = ['bench.py', '--impl', 'reference', '--config', '1', '--seed', "
+                f"'{seed}', '--steps', '1', '--warmup', '3', '--log', '{log}']; "
+                "runpy.run_path('bench.py', run_name='__main__')")
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
+        assert out.returncode == 0, out.stderr[-2000:]
+        outs.append([ln for ln in out.stdout.splitlines() if ln.startswith("{")][0])
+    logged = log.read_text().splitlines()
+    assert logged == outs
+    from paper_2002_05018_gb300 import workloads as W
+    a, b = W.make(2, seed=2), W.make(2, seed=7)
+    assert any(not np.array_equal(x, y) for x, y in ((a.cx, b.cx), (a.cy, b.cy), (a.cz, b.cz)))
 
 
 def test_reference_arm_on_a_general_mesh():
