@@ -280,6 +280,24 @@ def test_general_tetrahedral_meshes(mk, precision):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [d3m.FP64, d3m.MIXED])
+def test_curl_complete_second_order_mesh(precision):
+    """order 3 (two dofs per edge and two per face) on a Delaunay mesh with
+    2x2x2 coordinate boxes: E against the oracle's global solve element by
+    element in both precisions; lambda against the oracle's multipliers in
+    FP64 (the mixed path's multipliers keep the factor precision, estimated at
+    2-3e-5 on CPU for this order)."""
+    _need_gpu()
+    w = W.delaunay(5, 4, 4, 2, 2, 2, seed=3, nrhs=2, order=3)
+    s, x, info, f = _solve_case(w, precision)
+    _check_tiny(w, x, f, precision)
+    if precision == d3m.FP64:
+        ref = od3m.solve(w, f, return_all=True)
+        lam = s.lam(f.shape[1])
+        assert np.abs(lam - ref["lam"]).max() < 1e-9 * np.abs(ref["lam"]).max()
+    s.close()
+
+
 def test_lattice_mesh_through_the_general_path():
     """A lattice-tetrahedral workload through D3M_TET and, as vertex and
     tetrahedron lists, through D3M_TET_MESH: the same solution edge for edge
