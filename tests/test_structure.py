@@ -498,3 +498,38 @@ def test_order3_gradient_is_refused_on_the_host():
     assert lib.d3m_grad_eps(s.h, p, n, p, n, 1, p) == d3m.D3M_EINVAL
     assert b"order-3" in lib.d3m_last_error(s.h)
     s.close()
+
+
+@pytest.mark.parametrize("mk", [
+    lambda: W.tiny(4, 4, 3, 2, 2, 1, seed=3, nrhs=2),
+    lambda: W.tetrahedral(W.tiny(4, 3, 3, 2, 2, 1, seed=4, nrhs=2), 0.1),
+    lambda: W.delaunay(5, 4, 4, 2, 2, 2, seed=3, nrhs=2),
+    lambda: W.delaunay(5, 4, 4, 2, 2, 2, seed=3, nrhs=2, order=2),
+    lambda: W.delaunay(4, 4, 3, 2, 2, 1, seed=3, nrhs=2, order=3),
+])
+def test_exported_saddle_matrix_solves_to_the_oracle(mk):
+    """The whole host set-up end to end on CPU: the library's saddle matrix M
+    (d3m_structure: its entries in its own M order), solved densely in fp64
+    with the owner-split RHS, gives the oracle's solution E (each edge's
+    owner copy) and the oracle's multipliers lambda (Eq. (1))."""
+    from oracle import d3m as od3m, fem
+    w = mk()
+    f = fem.rhs_planewave(w)
+    s = d3m.Solver.from_workload(w)
+    ent, mm, st = s.structure(d3m.M_ENTRIES), s.structure(d3m.M_MAP), s.stats()
+    s.close()
+    n, lam0 = st["n_m"], st["n_m"] - st["n_lm"]
+    M = np.zeros((n, n), np.complex128)
+    M[ent[:, 0].astype(int), ent[:, 1].astype(int)] += ent[:, 2] + 1j * ent[:, 3]
+    M = M + np.tril(M, -1).T
+    dec = decomp.decompose(w, with_matrices=False)
+    owner = np.array([dec.copies[int(e)][0] == sub for sub, e in mm[:lam0]])
+    b = np.zeros((n, f.shape[1]), np.complex128)
+    b[:lam0][owner] = f[mm[:lam0, 1][owner]]
+    z = np.linalg.solve(M, b)
+    ref = od3m.solve(w, f, return_all=True)
+    assert np.abs(z[lam0:] - ref["lam"]).max() < 1e-10 * np.abs(ref["lam"]).max()
+    x = np.zeros_like(f)
+    x[mm[:lam0, 1][owner]] = z[:lam0][owner]
+    xg = fem.solve_global(w, f)
+    assert np.abs(x - xg).max() < 1e-10 * np.abs(xg).max()
