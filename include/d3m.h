@@ -128,8 +128,7 @@ typedef struct {
                                W_ac (W the Whitney function without the length
                                factor), dofs 2*edges + 2f and + 1 for face f
                                (faces numbered as sorted vertex triples,
-                               lexicographic); d3m_grad_eps refuses order 3.
-                               Other elements: 0 or 1. */
+                               lexicographic).  Other elements: 0 or 1. */
 } d3m_mesh;
 
 /* Materials.  eps_r: 2*n_cells doubles (re, im) per cell, time convention
@@ -342,7 +341,8 @@ int d3m_solve_adjoint(d3m_ctx *ctx, const double *rhs, int64_t ldb, double *y, i
  * where x = A^{-1} f is the forward solution, y = A^{-H} (dJ/dx) the adjoint
  * solution from d3m_solve_adjoint (dJ/dx in PyTorch's convention, e.g. 2 x at
  * the probes for J = sum |x_probe|^2), M_c the mass matrix of cell c over its
- * 12 edges (bricks) or 19 edges (the six tetrahedra of a D3M_TET cell)
+ * 12 edges (bricks), 19 edges (the six tetrahedra of a D3M_TET cell) or the
+ * 6, 12 or 20 dofs of a D3M_TET_MESH tetrahedron of order 1, 2 or 3
  * (dA/deps_c = -k^2 M_c) and the sum runs over the nrhs columns.  DEVICE
  * pointers: x, y as in d3m_solve (PEC rows ignored), grad: n_cells doubles,
  * overwritten.  FP64 regardless of the factor precision.

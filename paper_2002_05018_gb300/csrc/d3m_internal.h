@@ -122,7 +122,7 @@ int build_plan(Ctx &c, const d3m_mesh *mesh, const d3m_materials *mat, double k,
                const d3m_partition *part);
 void element_matrices(const double h[3], double S[12][12], double M[12][12]);
 void face_matrix(const double h[3], int axis, int side, double T[12][12]);
-constexpr int MAX_CELL_NE = 19;
+constexpr int MAX_CELL_NE = 20;  // dofs per cell: 12 bricks, 19 lattice tetrahedra, 6/12/20 mesh orders 1-3
 int cell_edges(const Plan &p, int ci, int cj, int ck, int64_t e[MAX_CELL_NE]);
 int cell_matrices(const Plan &p, int ci, int cj, int ck, double S[MAX_CELL_NE][MAX_CELL_NE],
                   double M[MAX_CELL_NE][MAX_CELL_NE]);

@@ -2207,14 +2207,15 @@ __global__ void k_grad_eps(int nx, int ny, int nz, double k2, ElemMass Me, const
     grad[c] = k2 * acc;
   }
 }
-// The same gradient with per-cell edge lists and mass matrices (ne edges per
-// cell: 19 for the six Whitney tetrahedra of a lattice cell, 6 for a
-// tetrahedron of a general mesh, its orientation signs inside the mass).
+// The same gradient with per-cell dof lists and mass matrices (ne <=
+// MAX_CELL_NE dofs per cell, checked on the host: 19 for the six Whitney
+// tetrahedra of a lattice cell, 6, 12 or 20 for a tetrahedron of a general
+// mesh of order 1, 2 or 3, its orientation signs inside the mass).
 __global__ void k_grad_eps_cells(int64_t ncell, int ne, const int64_t *__restrict__ cell_edge,
                                  const double *__restrict__ cell_mass, double k2, const double2 *__restrict__ x,
                                  int64_t ldx, const double2 *__restrict__ y, int64_t ldy, int r,
                                  const uint8_t *__restrict__ pec, double *__restrict__ grad) {
-  constexpr int NE = 19;
+  constexpr int NE = MAX_CELL_NE;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t *e = cell_edge + c * ne;
     const double *Mc = cell_mass + c * ne * ne;
@@ -4761,8 +4762,8 @@ extern "C" int d3m_solve_adjoint(d3m_ctx *h, const double *rhs, int64_t ldb, dou
 extern "C" int d3m_grad_eps(d3m_ctx *h, const double *x, int64_t ldx, const double *y, int64_t ldy, int32_t nrhs,
                             double *grad) {
   if (!h || !x || !y || !grad || nrhs <= 0 || ldx < h->c.plan.n_edges || ldy < h->c.plan.n_edges) return D3M_EINVAL;
-  if (h->c.plan.cell_ne > d3m::MAX_CELL_NE) {
-    h->c.err = "d3m_grad_eps: the adjoint gradient of order-3 meshes is not built";
+  if (h->c.plan.cell_ne > d3m::MAX_CELL_NE) {  // the per-cell table's bound (not reached by any element kind)
+    h->c.err = "d3m_grad_eps: more dofs per cell than the gradient's per-cell table holds";
     return D3M_EINVAL;
   }
   d3m::NvtxRange range("d3m_grad_eps");

@@ -504,7 +504,7 @@ static inline int64_t mesh_tet_dof(const Plan &p, int64_t t, int q) {
 
 int cell_dofs_mass(const Plan &p, int64_t c, int64_t e[MAX_CELL_NE], double M[MAX_CELL_NE][MAX_CELL_NE]) {
   if (p.element == D3M_TET_MESH) {
-    if (6 * p.dpe + (p.order == 3 ? 8 : 0) > MAX_CELL_NE) return 0;  // order 3: no per-cell table
+    if (6 * p.dpe + (p.order == 3 ? 8 : 0) > MAX_CELL_NE) return 0;
     double S20[20][20], M20[20][20];
     const int nl = mesh_tet_matrices(p, c, S20, M20);
     for (int q = 0; q < nl; ++q) {

@@ -106,11 +106,11 @@ def test_tetrahedral_gradient_vs_oracle():
     assert np.abs(g - go).max() < 1e-8 * np.abs(go).max()
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_general_mesh_gradient_vs_oracle(order):
     """d3m_grad_eps on a Delaunay mesh (one entry per tetrahedron, orientation
-    signs inside the per-tetrahedron masses; 6 or 12 dofs per tetrahedron)
-    against the oracle adjoint."""
+    signs inside the per-tetrahedron masses; 6, 12 or 20 dofs per
+    tetrahedron) against the oracle adjoint."""
     _need_gpu()
     w = W.delaunay(5, 4, 4, 2, 2, 1, seed=12, nrhs=2, order=order)
     f = fem.rhs_planewave(w)

@@ -489,17 +489,6 @@ def test_entries_match_oracle_on_random_meshes(case):
             assert abs(Ds[int(sub)][loc[int(e)], r - lam0] - v) < 1e-15
 
 
-def test_order3_gradient_is_refused_on_the_host():
-    """d3m_grad_eps refuses order-3 meshes before any device work."""
-    lib = d3m.load()
-    s = d3m.Solver.from_workload(W.delaunay(3, 3, 2, 1, 1, 1, seed=4, order=3))
-    buf = np.zeros(2 * s.n_edges + 64)
-    p, n = buf.ctypes.data, s.n_edges
-    assert lib.d3m_grad_eps(s.h, p, n, p, n, 1, p) == d3m.D3M_EINVAL
-    assert b"order-3" in lib.d3m_last_error(s.h)
-    s.close()
-
-
 @pytest.mark.parametrize("mk", [
     lambda: W.tiny(4, 4, 3, 2, 2, 1, seed=3, nrhs=2),
     lambda: W.tetrahedral(W.tiny(4, 3, 3, 2, 2, 1, seed=4, nrhs=2), 0.1),
